@@ -1,0 +1,174 @@
+"""Seeded synthetic plasma loads shared by the CUDA path and the oracle.
+
+This module only draws initial particle states (cell index, in-cell offsets, momenta) from a
+seed.  It holds none of the PIC step's arithmetic; both the CUDA library and the oracle take
+its arrays unchanged, so both sides start from bit-identical FP32-representable inputs.
+
+Physics of the load (simulation section of arXiv:0808.4078): a relativistic electron beam of
+density nb drifting along z through background electrons of density np = n0 - nb that carry
+the return current, so the initial net current is zero; immobile ions of density n0.  Units:
+density n0, momentum u = gamma v / c, length c/w_p.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+ELECTRON_Q = -1.0
+ELECTRON_M = 1.0
+
+
+@dataclass
+class SpeciesLoad:
+    """Initial state of one species.
+
+    cell   int32 [N]      linear cell index, x fastest: (k*ny + j)*nx + i
+    offset float32 [ndim, N]  in-cell offsets in [0, 1) along x, y(, z)
+    u      float32 [3, N] momentum gamma*v/c
+    w      density carried by one macro-particle (units n0)
+    nu     Krook collision rate acting on this species' cell-mean momentum (units w_p)
+    """
+    name: str
+    q: float
+    m: float
+    w: float
+    nu: float
+    cell: np.ndarray
+    offset: np.ndarray
+    u: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.cell.shape[0])
+
+
+@dataclass
+class Workload:
+    name: str
+    ndim: int
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    dz: float
+    dt: float
+    steps: int
+    species: list = field(default_factory=list)
+
+    @property
+    def ncell(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def nparticles(self) -> int:
+        return sum(s.n for s in self.species)
+
+
+def _cells_and_offsets(rng, ndim, nx, ny, nz, ppc, lattice=False):
+    ncell = nx * ny * nz
+    cell = np.repeat(np.arange(ncell, dtype=np.int32), ppc)
+    n = cell.shape[0]
+    if lattice:
+        # quiet start: ppc = m^ndim particles per cell on a sub-lattice
+        m = round(ppc ** (1.0 / ndim))
+        if m ** ndim != ppc:
+            raise ValueError("lattice loading needs ppc = m**ndim")
+        sub = (np.arange(m, dtype=np.float64) + 0.5) / m
+        grids = np.meshgrid(*([sub] * ndim), indexing="ij")
+        pat = np.stack([g.reshape(-1) for g in grids])
+        offset = np.tile(pat, (1, ncell)).astype(np.float32)
+    else:
+        offset = rng.random((ndim, n), dtype=np.float32)
+    return cell, offset
+
+
+def _zero_mean(a):
+    return a - a.mean() if a.size else a
+
+
+def _solve_drift(target_sum, duz, uperp2):
+    """Drift d (FP64, Newton) with sum_p (d + duz_p) / sqrt(1 + uperp2_p + (d + duz_p)^2) = target."""
+    d = 0.0
+    for _ in range(60):
+        uz = d + duz
+        g = np.sqrt(1.0 + uperp2 + uz * uz)
+        f = np.sum(uz / g) - target_sum
+        fp = np.sum((1.0 + uperp2) / g ** 3)
+        step = f / fp
+        d -= step
+        if abs(step) < 1e-15 * max(1.0, abs(d)):
+            break
+    return d
+
+
+def weibel_load(*, ndim=2, nx, ny, nz=1, ppc, gamma_b=3.0, nb=0.1, T_perp_beam=0.0,
+                T_par_beam=0.0, T_bg=0.0, nu=0.0, seed=1, dx=0.1, dt=0.05, steps=0,
+                lattice=False, name=None) -> Workload:
+    """Beam + return-current background electrons with zero initial net current along z.
+
+    Beam: u_z = sqrt(gamma_b^2 - 1) (cold along z unless T_par_beam > 0), transverse
+    u ~ N(0, sqrt(T_perp_beam)) per component.  Background: each component ~ N(0, sqrt(T_bg))
+    around a drift along -z chosen so the sampled current sum_p w v_z vanishes (FP64 solve,
+    stored in FP32).  Exactly ppc particles per cell per species; offsets U[0,1).
+    """
+    if ndim == 2:
+        nz = 1
+    dz = dx
+    ss = np.random.SeedSequence(seed)
+    rb, rp = [np.random.default_rng(s) for s in ss.spawn(2)]
+    np_ = 1.0 - nb
+    wb, wp = nb / ppc, np_ / ppc
+
+    cb, ob = _cells_and_offsets(rb, ndim, nx, ny, nz, ppc, lattice)
+    cp, op = _cells_and_offsets(rp, ndim, nx, ny, nz, ppc, lattice)
+    nbp, npp = cb.shape[0], cp.shape[0]
+
+    uz0 = math.sqrt(gamma_b * gamma_b - 1.0)
+    sb = math.sqrt(T_perp_beam)
+    ubx = _zero_mean(rb.standard_normal(nbp) * sb) if sb > 0 else np.zeros(nbp)
+    uby = _zero_mean(rb.standard_normal(nbp) * sb) if sb > 0 else np.zeros(nbp)
+    spar = math.sqrt(T_par_beam)
+    ubz = uz0 + (_zero_mean(rb.standard_normal(nbp) * spar) if spar > 0 else 0.0)
+    ub = np.stack([ubx, uby, np.broadcast_to(ubz, (nbp,))]).astype(np.float32)
+
+    sp = math.sqrt(T_bg)
+    upx = _zero_mean(rp.standard_normal(npp) * sp) if sp > 0 else np.zeros(npp)
+    upy = _zero_mean(rp.standard_normal(npp) * sp) if sp > 0 else np.zeros(npp)
+    duz = _zero_mean(rp.standard_normal(npp) * sp) if sp > 0 else np.zeros(npp)
+    upx = upx.astype(np.float32).astype(np.float64)
+    upy = upy.astype(np.float32).astype(np.float64)
+
+    ub64 = ub.astype(np.float64)
+    gb = np.sqrt(1.0 + (ub64 * ub64).sum(0))
+    beam_current = wb * np.sum(ub64[2] / gb)
+    d = _solve_drift(-beam_current / wp, duz, upx * upx + upy * upy)
+    up = np.stack([upx, upy, d + duz]).astype(np.float32)
+
+    beam = SpeciesLoad("beam", ELECTRON_Q, ELECTRON_M, wb, 0.0, cb, ob, ub)
+    bg = SpeciesLoad("background", ELECTRON_Q, ELECTRON_M, wp, nu, cp, op, up)
+    if name is None:
+        dims = f"{nx}x{ny}" + (f"x{nz}" if ndim == 3 else "")
+        name = f"weibel_{ndim}d_{dims}_ppc{ppc}"
+    return Workload(name, ndim, nx, ny, nz, dx, dx, dz, dt, steps, [beam, bg])
+
+
+# Named workloads (sizes in the names).  Seeds 1..3 are fixed per workload.
+def cold_beam_2d_64(seed=1, steps=500):
+    """64x64 2D3V, cold gamma=3 beam (nb=0.1), cold background, 16 ppc/species, collisionless."""
+    return weibel_load(ndim=2, nx=64, ny=64, ppc=16, seed=seed, steps=steps,
+                       name="cold_beam_2d_64x64_ppc16")
+
+
+def warm_beam_krook_2d(n=1024, ppc=64, seed=2, steps=4000):
+    """n x n 2D3V, beam T_perp=0.1, background T=0.001, Krook nu=0.1, 64 ppc/species."""
+    return weibel_load(ndim=2, nx=n, ny=n, ppc=ppc, T_perp_beam=0.1, T_bg=0.001, nu=0.1,
+                       seed=seed, steps=steps, name=f"warm_beam_krook_2d_{n}x{n}_ppc{ppc}")
+
+
+def hot_beam_3d(nx=256, ny=256, nz=512, ppc=8, seed=3, steps=2000):
+    """3D3V, beam along z, T_perp=0.2, cold collisionless background, 8 ppc/species."""
+    return weibel_load(ndim=3, nx=nx, ny=ny, nz=nz, ppc=ppc, T_perp_beam=0.2, seed=seed,
+                       steps=steps, name=f"hot_beam_3d_{nx}x{ny}x{nz}_ppc{ppc}")
