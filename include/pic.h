@@ -1,0 +1,176 @@
+/*
+ * pic.h -- C ABI of libpic, a single-GPU (sm_103a) electromagnetic particle-in-cell engine for
+ * the relativistic-electron-beam Weibel / filamentation problem of Karmakar, Kumar, Shvets,
+ * Polomarov & Pukhov, "On collisions driven negative energy waves and Weibel instability of a
+ * relativistic electron beam in a quasi-neutral plasma" (arXiv:0808.4078).
+ *
+ * Physics covered (paper passages):
+ *   - 2D geometry: the plane transverse to a beam along z, no z dependence; 3D runs with the
+ *     beam along z (simulation section);
+ *   - beam and background (return-current) electrons, immobile ions of density n0, initial
+ *     current neutralisation (simulation section);
+ *   - collisional friction on the return current, Eq. (3) (d v_pz/dt + nu v_pz = ...), applied
+ *     as a per-cell relaxation of the drag species' mean momentum at rate nu (Krook reading);
+ *   - field-energy diagnostic, integral of F_i^2 dx dy per component (simulation section);
+ *   - growth rate of the exponential stage of the magnetic energy (results section).
+ * The paper gives no PIC algorithm; the discretisation is CIC gather + relativistic Boris push,
+ * charge-conserving Esirkepov current deposit, Yee FDTD, periodic boundaries.
+ *
+ * Units: time 1/w_p, length c/w_p, momentum u = gamma v / c, fields m c w_p / e, density n0,
+ * current e n0 c.  Particles are stored as an int32 cell index (x fastest) plus FP32 in-cell
+ * offsets in [0, 1); push and gather are FP32; the current is accumulated in int64 fixed point
+ * (bit-reproducible); global energy/momentum reductions are FP64.
+ *
+ * Conventions
+ *   - Every function returns PIC_OK (0) or a negative PIC_E* code; pic_last_error() gives text.
+ *     No C++ exception crosses this boundary.
+ *   - Device memory: the caller allocates ONE device arena of pic_required_bytes() bytes and
+ *     keeps it (and the CUDA stream) alive until pic_free().  The library never calls
+ *     cudaMalloc for state; it carves the arena.  Host buffers passed in are copied during the
+ *     call; host buffers passed out are written before the call returns.
+ *   - All GPU work is issued on the caller's stream, asynchronously, except where a function
+ *     says it synchronises.  Device-side error flags are sticky and reported by the next call
+ *     that synchronises (pic_sync, pic_diag, pic_get_*).
+ *   - Arrays of fields are [nz][ny][nx] (x fastest).  Yee staggering (2D):
+ *     Ex(i+1/2,j) Ey(i,j+1/2) Ez(i,j) Bx(i,j+1/2) By(i+1/2,j) Bz(i+1/2,j+1/2); J like E.
+ *     3D: Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2) Bx(i,j+1/2,k+1/2) By(i+1/2,j,k+1/2)
+ *     Bz(i+1/2,j+1/2,k).
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_OK 0
+#define PIC_EINVAL (-1)     /* bad argument or configuration */
+#define PIC_ENOMEM (-2)     /* arena smaller than pic_required_bytes(), or capacity exceeded */
+#define PIC_ECUDA (-3)      /* a CUDA runtime call failed */
+#define PIC_EOVERFLOW (-4)  /* fixed-point headroom exceeded or a particle moved >= 1 cell */
+#define PIC_EBADPART (-5)   /* non-finite or out-of-range particle data */
+#define PIC_ETIMEOUT (-6)   /* a bounded device wait gave up */
+#define PIC_ESTATE (-7)     /* call not valid in the current state */
+
+#define PIC_MAX_SPECIES 2
+
+/* Flags for pic_config.flags */
+#define PIC_FLAG_PROFILE 1   /* time each kernel phase with CUDA events (disables graphs) */
+#define PIC_FLAG_NO_GRAPH 2  /* launch steps directly instead of replaying a CUDA graph */
+#define PIC_FLAG_KEEP_J 4    /* keep a copy of the last step's J for pic_get_fields (tests) */
+
+typedef struct pic_ctx pic_ctx;
+
+typedef struct pic_config {
+    int32_t ndim;              /* 2 (2D3V) or 3 (3D3V) */
+    int32_t nx, ny, nz;        /* cells per axis; nz = 1 in 2D; multiples of the tile sizes */
+    double dx, dy, dz, dt;     /* cell sizes (c/w_p) and time step (1/w_p); dt < min(dx,dy,dz) */
+    int32_t nspecies;          /* 1..PIC_MAX_SPECIES */
+    int64_t capacity[PIC_MAX_SPECIES]; /* particle capacity per species */
+    int32_t sort_interval;     /* steps between counting sorts (>= 1); 0 = default (8) */
+    int32_t diag_interval;     /* steps between diagnostic records; 0 = no diagnostics */
+    int32_t diag_capacity;     /* records kept in the device history ring (>= 1 if diag) */
+    int32_t track_ids;         /* 1: carry an int32 id per particle through sorts */
+    int32_t flags;             /* PIC_FLAG_* */
+    int32_t tile_x, tile_y, tile_z; /* 0 = default (16 x 16 in 2D) */
+} pic_config;
+
+typedef struct pic_species {
+    double q;      /* charge in units of e (electrons: -1) */
+    double m;      /* mass in units of m_e (electrons: 1) */
+    double w;      /* density carried by one macro-particle, units n0 (n_s / ppc) */
+    double nu;     /* Krook rate on this species' cell-mean momentum (Eq. (3) friction); 0 = none */
+} pic_species;
+
+typedef struct pic_diag_rec {
+    int64_t step;                    /* n */
+    double t;                        /* n dt */
+    double WE[3], WB[3];             /* sum over cells of F_i^2 dx dy (dz) at time n */
+    double Ekin[PIC_MAX_SPECIES];    /* sum w (gamma(u^n) - 1) dx dy (dz), u^n = (u^{n-1/2}+u^{n+1/2})/2 */
+    double P[3];                     /* sum over all species of w u^n dx dy (dz) */
+    int32_t flags;                   /* device error flags seen by this step */
+    int32_t reserved;
+} pic_diag_rec;
+
+typedef struct pic_kernel_time {
+    char name[32];
+    int64_t launches;
+    double total_ms;                 /* sum of CUDA-event intervals on the context stream */
+} pic_kernel_time;
+
+/* Bytes of device arena needed for cfg.  Host-only; no CUDA call. */
+int pic_required_bytes(const pic_config* cfg, size_t* bytes_out);
+
+/* Create a context on the current CUDA device.  device_arena: caller-owned device memory of
+ * arena_bytes >= pic_required_bytes(cfg), aligned to 256 bytes; cuda_stream: a cudaStream_t
+ * (not the legacy default stream if graphs are used).  Fields start at E = B = 0. */
+int pic_init(const pic_config* cfg, void* device_arena, size_t arena_bytes, void* cuda_stream,
+             pic_ctx** out);
+
+/* Load n particles of species index s (0-based) from HOST arrays: cell[n] (linear index,
+ * x fastest), offset[ndim*n] (component-major: all x offsets, then y, then z; each in [0,1)),
+ * u[3*n] (component-major u_x, u_y, u_z).  Copies, validates (PIC_EBADPART on a bad value),
+ * sorts by tile and computes the cell-mean momentum used by the drag.  The initial u is
+ * u^{-1/2}.  Synchronises the stream. */
+int pic_load_species(pic_ctx* ctx, int s, const pic_species* sp, int64_t n, const int32_t* cell,
+                     const float* offset, const float* u);
+
+/* Advance nsteps steps: gather + Boris + drag + move + Esirkepov deposit, Yee update, counting
+ * sort every sort_interval steps, diagnostics every diag_interval steps.  Asynchronous. */
+int pic_step(pic_ctx* ctx, int nsteps);
+
+/* Wait for the stream; report sticky device errors. */
+int pic_sync(pic_ctx* ctx);
+
+/* Copy up to max_recs diagnostic records (oldest first) to out.  Synchronises. */
+int pic_diag(pic_ctx* ctx, pic_diag_rec* out, int max_recs, int* n_out);
+
+/* Copy species s to HOST arrays (any may be NULL): cell[n], offset[ndim*n], u[3*n], id[n]
+ * (id requires track_ids).  Particle order is the current (sorted) storage order; n must equal
+ * the loaded count.  Synchronises. */
+int pic_get_particles(pic_ctx* ctx, int s, int32_t* cell, float* offset, float* u, int32_t* id,
+                      int64_t n);
+
+/* Copy fields to HOST arrays (any may be NULL): E[3*ncell], B[3*ncell] component-major FP32;
+ * J[3*ncell] int64 fixed point of the last step's current (J = value * 2^-shift, shift from
+ * pic_fixed_point_shift); J needs PIC_FLAG_KEEP_J (PIC_ESTATE otherwise).  Synchronises. */
+int pic_get_fields(pic_ctx* ctx, float* E, float* B, int64_t* J);
+
+/* Overwrite E and B from HOST arrays (component-major FP32, 3*ncell each).  Test and restart
+ * use.  Synchronises. */
+int pic_set_fields(pic_ctx* ctx, const float* E, const float* B);
+
+/* Fixed-point shift S of the current accumulator (J_int = round(J * 2^S)). */
+int pic_fixed_point_shift(const pic_ctx* ctx, int* shift_out);
+
+/* Growth rate of W_B_perp = WB[0] + WB[1] from the device history (FP64 fit on the GPU):
+ * noise level W0 = mean over t <= t_noise; windows of `width` records with all
+ * W > start_factor * W0 and W < end_factor * max(W) (end_factor <= 0: no upper bound);
+ * least-squares slope of ln W, largest over windows; Gamma = slope / 2.  gamma_out is NaN if
+ * no window qualifies.  Synchronises. */
+int pic_fit_growth(pic_ctx* ctx, int width, double t_noise, double start_factor,
+                   double end_factor, double* gamma_out, double* t0_out, double* t1_out);
+
+/* Per-phase CUDA-event timings (PIC_FLAG_PROFILE).  Synchronises. */
+int pic_kernel_times(pic_ctx* ctx, pic_kernel_time* out, int max, int* n_out);
+
+/* Kernel launches issued so far by this context (graph replays count their kernel nodes). */
+int64_t pic_launch_count(const pic_ctx* ctx);
+
+/* Steps taken so far. */
+int64_t pic_step_count(const pic_ctx* ctx);
+
+/* Last error message of ctx (or of the last failed pic_init when ctx is NULL). */
+const char* pic_last_error(const pic_ctx* ctx);
+
+/* Destroy the context (does not free the caller's arena or stream). */
+void pic_free(pic_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

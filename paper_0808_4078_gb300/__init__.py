@@ -1,0 +1,249 @@
+"""Python binding of libpic (include/pic.h): argument marshalling only.
+
+Every step of the particle-in-cell path runs in the CUDA kernels of libpic.so; PyTorch only
+provides the device arena (one uint8 tensor) and the CUDA stream.  There is no CPU fallback:
+if libpic.so is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpic.so")
+_lib = None
+
+PIC_MAX_SPECIES = 2
+PIC_FLAG_PROFILE = 1
+PIC_FLAG_NO_GRAPH = 2
+PIC_FLAG_KEEP_J = 4
+
+ERRORS = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA", -4: "PIC_EOVERFLOW",
+          -5: "PIC_EBADPART", -6: "PIC_ETIMEOUT", -7: "PIC_ESTATE"}
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("dz", ctypes.c_double), ("dt", ctypes.c_double), ("nspecies", ctypes.c_int32),
+                ("capacity", ctypes.c_int64 * PIC_MAX_SPECIES), ("sort_interval", ctypes.c_int32),
+                ("diag_interval", ctypes.c_int32), ("diag_capacity", ctypes.c_int32),
+                ("track_ids", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32)]
+
+
+class Species(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_double), ("m", ctypes.c_double), ("w", ctypes.c_double),
+                ("nu", ctypes.c_double)]
+
+
+class DiagRec(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("t", ctypes.c_double), ("WE", ctypes.c_double * 3),
+                ("WB", ctypes.c_double * 3), ("Ekin", ctypes.c_double * PIC_MAX_SPECIES),
+                ("P", ctypes.c_double * 3), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
+_VP = ctypes.c_void_p
+_SIGNATURES = {
+    "pic_required_bytes": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_size_t)]),
+    "pic_init": (ctypes.c_int, [ctypes.POINTER(Config), _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+    "pic_load_species": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(Species), ctypes.c_int64,
+                                        _VP, _VP, _VP]),
+    "pic_step": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "pic_sync": (ctypes.c_int, [_VP]),
+    "pic_diag": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "pic_get_particles": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.c_int64]),
+    "pic_get_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "pic_set_fields": (ctypes.c_int, [_VP, _VP, _VP]),
+    "pic_fixed_point_shift": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "pic_fit_growth": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "pic_kernel_times": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "pic_launch_count": (ctypes.c_int64, [_VP]),
+    "pic_step_count": (ctypes.c_int64, [_VP]),
+    "pic_last_error": (ctypes.c_char_p, [_VP]),
+    "pic_free": (None, [_VP]),
+}
+
+
+def lib():
+    """Load libpic.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpic.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_VP)
+
+
+def _check(rc, ctx=None):
+    if rc != 0:
+        msg = lib().pic_last_error(ctx).decode(errors="replace")
+        raise PicError(rc, msg)
+
+
+def required_bytes(cfg: Config) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().pic_required_bytes(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
+class Engine:
+    """One PIC run on one GPU.  Arena and stream come from PyTorch."""
+
+    def __init__(self, ndim, nx, ny, nz=1, dx=0.1, dy=None, dz=None, dt=0.05, capacity=(0, 0),
+                 nspecies=2, sort_interval=8, diag_interval=1, diag_capacity=4096,
+                 track_ids=False, flags=0, device="cuda", stream=None):
+        import torch
+        self._torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libpic needs a CUDA GPU")
+        cap = (ctypes.c_int64 * PIC_MAX_SPECIES)(*[int(c) for c in capacity][:PIC_MAX_SPECIES])
+        self.cfg = Config(ndim, nx, ny, nz if ndim == 3 else 1, dx, dx if dy is None else dy,
+                          dx if dz is None else dz, dt, nspecies, cap, sort_interval, diag_interval,
+                          diag_capacity, int(bool(track_ids)), flags, 0, 0, 0)
+        self.nbytes = required_bytes(self.cfg)
+        self.device = torch.device(device)
+        self.arena = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self._ctx = _VP()
+        with torch.cuda.device(self.device):
+            _check(lib().pic_init(ctypes.byref(self.cfg), _VP(self.arena.data_ptr()), self.nbytes,
+                                  _VP(self.stream.cuda_stream), ctypes.byref(self._ctx)))
+        self.loaded = [0] * PIC_MAX_SPECIES
+        self.ncell = nx * ny * (nz if ndim == 3 else 1)
+
+    # -------------------------------------------------------------- lifecycle
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().pic_free(self._ctx)
+            self._ctx = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -------------------------------------------------------------- calls
+    def load_species(self, s, q, m, w, nu, cell, offset, u):
+        cell = np.ascontiguousarray(cell, dtype=np.int32)
+        offset = np.ascontiguousarray(offset, dtype=np.float32)
+        u = np.ascontiguousarray(u, dtype=np.float32)
+        n = cell.shape[0]
+        assert offset.shape == (self.cfg.ndim, n) and u.shape == (3, n)
+        sp = Species(q, m, w, nu)
+        _check(lib().pic_load_species(self._ctx, s, ctypes.byref(sp), n, _ptr(cell), _ptr(offset),
+                                      _ptr(u)), self._ctx)
+        self.loaded[s] = n
+
+    def step(self, n=1):
+        _check(lib().pic_step(self._ctx, int(n)), self._ctx)
+
+    def sync(self):
+        _check(lib().pic_sync(self._ctx), self._ctx)
+
+    def diag(self, max_recs=None):
+        cap = self.cfg.diag_capacity if max_recs is None else max_recs
+        buf = (DiagRec * cap)()
+        n = ctypes.c_int(0)
+        _check(lib().pic_diag(self._ctx, ctypes.cast(buf, _VP), cap, ctypes.byref(n)), self._ctx)
+        out = []
+        for r in buf[:n.value]:
+            out.append(dict(step=r.step, t=r.t, WE=list(r.WE), WB=list(r.WB), Ekin=list(r.Ekin),
+                            P=list(r.P), flags=r.flags))
+        return out
+
+    def particles(self, s):
+        n = self.loaded[s]
+        cell = np.empty(n, np.int32)
+        off = np.empty((self.cfg.ndim, n), np.float32)
+        u = np.empty((3, n), np.float32)
+        ids = np.empty(n, np.int32) if self.cfg.track_ids else None
+        _check(lib().pic_get_particles(self._ctx, s, _ptr(cell), _ptr(off), _ptr(u), _ptr(ids), n),
+               self._ctx)
+        return cell, off, u, ids
+
+    def fields(self, with_J=False):
+        shape = (3, self.ncell)
+        E = np.empty(shape, np.float32)
+        B = np.empty(shape, np.float32)
+        J = np.empty(shape, np.int64) if with_J else None
+        _check(lib().pic_get_fields(self._ctx, _ptr(E), _ptr(B), _ptr(J)), self._ctx)
+        return E, B, J
+
+    def set_fields(self, E=None, B=None):
+        E = None if E is None else np.ascontiguousarray(E, dtype=np.float32)
+        B = None if B is None else np.ascontiguousarray(B, dtype=np.float32)
+        _check(lib().pic_set_fields(self._ctx, _ptr(E), _ptr(B)), self._ctx)
+
+    def fixed_point_shift(self):
+        s = ctypes.c_int(0)
+        _check(lib().pic_fixed_point_shift(self._ctx, ctypes.byref(s)), self._ctx)
+        return s.value
+
+    def fit_growth(self, width=60, t_noise=2.0, start_factor=10.0, end_factor=1.0 / 30.0):
+        g, t0, t1 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        ef = -1.0 if end_factor is None else end_factor
+        _check(lib().pic_fit_growth(self._ctx, width, t_noise, start_factor, ef, ctypes.byref(g),
+                                    ctypes.byref(t0), ctypes.byref(t1)), self._ctx)
+        return g.value, t0.value, t1.value
+
+    def kernel_times(self):
+        buf = (KernelTime * 16)()
+        n = ctypes.c_int(0)
+        _check(lib().pic_kernel_times(self._ctx, ctypes.cast(buf, _VP), 16, ctypes.byref(n)),
+               self._ctx)
+        return {b.name.decode(): (b.launches, b.total_ms) for b in buf[:n.value]}
+
+    def launch_count(self):
+        return int(lib().pic_launch_count(self._ctx))
+
+    def step_count(self):
+        return int(lib().pic_step_count(self._ctx))
+
+    # -------------------------------------------------------------- helpers
+    @classmethod
+    def from_workload(cls, wl, **kw):
+        """Engine sized for a pic_inputs.Workload, with its species loaded."""
+        cap = [s.n for s in wl.species] + [0] * (PIC_MAX_SPECIES - len(wl.species))
+        eng = cls(wl.ndim, wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, wl.dz, wl.dt, capacity=cap,
+                  nspecies=len(wl.species), **kw)
+        for i, s in enumerate(wl.species):
+            eng.load_species(i, s.q, s.m, s.w, s.nu, s.cell, s.offset, s.u)
+        return eng
+
+
+def history_array(recs, key, comp=None):
+    if comp is None:
+        return np.array([r[key] for r in recs])
+    return np.array([r[key][comp] for r in recs])

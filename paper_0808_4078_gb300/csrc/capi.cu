@@ -1,0 +1,644 @@
+// capi.cu -- the C ABI of libpic (include/pic.h): context, arena carving, particle loading,
+// step scheduling (CUDA graph of one sort period), diagnostics, growth fit, profiling.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "pic_internal.cuh"
+
+using namespace pic;
+
+static_assert(sizeof(pic_diag_rec) == sizeof(DiagRec), "diag record layout");
+static_assert(PIC_MAX_SPECIES == PIC_NS, "species slots");
+
+namespace {
+
+thread_local std::string g_init_error;
+
+enum Phase { PH_PUSH = 0, PH_YEE, PH_FINAL, PH_SORT, PH_N };
+const char* kPhaseName[PH_N] = {"push_deposit", "yee", "finalize", "sort"};
+
+struct Layout {
+    size_t total = 0;
+    size_t ctl, runs, work;
+    size_t part[PIC_NS][2][8];     // cell, o0, o1, o2, u0, u1, u2, id
+    size_t E[3], B[3], J[3], Jlast[3];
+    size_t msum[3], mcnt, ubar[3];
+    size_t start[PIC_NS], count, cursor, scan_tmp;
+    size_t partials, hist, fit;
+};
+
+size_t take(size_t& off, size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    size_t at = off;
+    off += bytes;
+    return at;
+}
+
+struct Geometry {
+    int tx, ty, tz;
+    int ntx, nty, ntz;
+    long long ncell, ntiles;
+};
+
+int geometry(const pic_config* c, Geometry* g, std::string* err) {
+    if (c->ndim != 2 && c->ndim != 3) { *err = "ndim must be 2 or 3"; return PIC_EINVAL; }
+    if (c->ndim == 3 && !pic::has_push3d()) { *err = "3D push not available in this build"; return PIC_EINVAL; }
+    const int nz = c->ndim == 3 ? c->nz : 1;
+    g->tx = c->tile_x > 0 ? c->tile_x : 16;
+    g->ty = c->tile_y > 0 ? c->tile_y : 16;
+    g->tz = c->ndim == 3 ? (c->tile_z > 0 ? c->tile_z : 4) : 1;
+    if (c->ndim == 2 && (g->tx != 16 || g->ty != 16)) { *err = "2D tiles are 16 x 16"; return PIC_EINVAL; }
+    if (c->nx <= 0 || c->ny <= 0 || nz <= 0) { *err = "grid sizes must be positive"; return PIC_EINVAL; }
+    if (c->nx % g->tx || c->ny % g->ty || nz % g->tz) { *err = "grid sizes must be multiples of the tile"; return PIC_EINVAL; }
+    g->ntx = c->nx / g->tx; g->nty = c->ny / g->ty; g->ntz = nz / g->tz;
+    g->ncell = (long long)c->nx * c->ny * nz;
+    g->ntiles = (long long)g->ntx * g->nty * g->ntz;
+    if (g->ncell >= (1ll << 31) - 1) { *err = "too many cells for int32 cell indices"; return PIC_EINVAL; }
+    if (!(c->dx > 0 && c->dy > 0 && c->dt > 0) || (c->ndim == 3 && !(c->dz > 0))) { *err = "dx, dy, dz, dt must be > 0"; return PIC_EINVAL; }
+    double inv2 = 1.0 / (c->dx * c->dx) + 1.0 / (c->dy * c->dy) + (c->ndim == 3 ? 1.0 / (c->dz * c->dz) : 0.0);
+    if (c->dt * std::sqrt(inv2) >= 1.0) { *err = "dt violates the Yee Courant condition"; return PIC_EINVAL; }
+    if (c->nspecies < 1 || c->nspecies > PIC_NS) { *err = "nspecies must be 1..2"; return PIC_EINVAL; }
+    for (int s = 0; s < c->nspecies; ++s)
+        if (c->capacity[s] < 0 || c->capacity[s] >= (1ll << 31)) { *err = "capacity must be in [0, 2^31)"; return PIC_EINVAL; }
+    if (c->diag_interval < 0 || (c->diag_interval > 0 && c->diag_capacity < 1)) { *err = "diag_capacity must be >= 1"; return PIC_EINVAL; }
+    if (c->sort_interval < 0) { *err = "sort_interval must be >= 0"; return PIC_EINVAL; }
+    return PIC_OK;
+}
+
+Layout make_layout(const pic_config* c, const Geometry& g) {
+    Layout L;
+    size_t off = 0;
+    const long long nc = g.ncell;
+    L.ctl = take(off, sizeof(Ctl));
+    L.runs = take(off, sizeof(RunDev));
+    L.work = take(off, sizeof(int2) * g.ntiles);
+    for (int s = 0; s < PIC_NS; ++s)
+        for (int b = 0; b < 2; ++b) {
+            const long long cap = s < c->nspecies ? c->capacity[s] : 0;
+            L.part[s][b][0] = take(off, 4 * cap);
+            for (int d = 0; d < 3; ++d) L.part[s][b][1 + d] = d < c->ndim ? take(off, 4 * cap) : 0;
+            for (int d = 0; d < 3; ++d) L.part[s][b][4 + d] = take(off, 4 * cap);
+            L.part[s][b][7] = c->track_ids ? take(off, 4 * cap) : 0;
+        }
+    for (int d = 0; d < 3; ++d) L.E[d] = take(off, 4 * nc);
+    for (int d = 0; d < 3; ++d) L.B[d] = take(off, 4 * nc);
+    for (int d = 0; d < 3; ++d) L.J[d] = take(off, 8 * nc);
+    for (int d = 0; d < 3; ++d) L.Jlast[d] = (c->flags & PIC_FLAG_KEEP_J) ? take(off, 8 * nc) : 0;
+    for (int d = 0; d < 3; ++d) L.msum[d] = take(off, 8 * nc);
+    L.mcnt = take(off, 4 * nc);
+    for (int d = 0; d < 3; ++d) L.ubar[d] = take(off, 4 * nc);
+    for (int s = 0; s < PIC_NS; ++s) L.start[s] = take(off, 4 * (nc + 1));
+    L.count = take(off, 4 * nc);
+    L.cursor = take(off, 4 * nc);
+    L.scan_tmp = take(off, 4 * (nc / 2048 + 2));
+    L.partials = take(off, sizeof(double) * 8 * g.ntiles);
+    L.hist = take(off, sizeof(DiagRec) * (c->diag_interval > 0 ? c->diag_capacity : 1));
+    L.fit = take(off, sizeof(double) * 4);
+    L.total = (off + 255) & ~size_t(255);
+    return L;
+}
+
+}  // namespace
+
+struct pic_ctx {
+    pic_config cfg{};
+    Geometry geo{};
+    Layout lay{};
+    cudaStream_t stream = nullptr;
+    char* arena = nullptr;
+    int sort_interval = 8;
+    RunDev run{};
+    Args args{};
+    long long loaded[PIC_NS] = {0, 0};
+    double q[PIC_NS] = {0, 0};
+    long long host_step = 0;
+    long long launches = 0;
+    std::string err;
+    // graph of one sort period
+    cudaGraphExec_t graph = nullptr;
+    long long graph_launches = 0;
+    bool graph_dirty = true;
+    // profiling
+    struct Ev { int phase; cudaEvent_t a, b; };
+    std::vector<Ev> pending;
+    std::vector<cudaEvent_t> pool;
+    double phase_ms[PH_N] = {0, 0, 0, 0};
+    long long phase_n[PH_N] = {0, 0, 0, 0};
+};
+
+namespace {
+
+int fail(pic_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_init_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(ctx, PIC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));        \
+    } while (0)
+
+template <class T> T* at(pic_ctx* c, size_t off) { return reinterpret_cast<T*>(c->arena + off); }
+
+int upload_run(pic_ctx* ctx) {
+    CK(cudaMemcpyAsync(at<RunDev>(ctx, ctx->lay.runs), &ctx->run, sizeof(RunDev),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    ctx->graph_dirty = true;
+    return PIC_OK;
+}
+
+cudaEvent_t get_event(pic_ctx* c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct PhaseScope {
+    pic_ctx* c;
+    pic_ctx::Ev ev{};
+    bool on;
+    PhaseScope(pic_ctx* c_, int ph) : c(c_), on((c_->cfg.flags & PIC_FLAG_PROFILE) != 0) {
+        if (!on) return;
+        ev.phase = ph;
+        ev.a = get_event(c);
+        ev.b = get_event(c);
+        cudaEventRecord(ev.a, c->stream);
+    }
+    ~PhaseScope() {
+        if (!on) return;
+        cudaEventRecord(ev.b, c->stream);
+        c->pending.push_back(ev);
+    }
+};
+
+int launch_one_step(pic_ctx* ctx, long long step_index) {
+    const Args& a = ctx->args;
+    {
+        PhaseScope ps(ctx, PH_PUSH);
+        CK(ctx->cfg.ndim == 2 ? launch_push2d(a, ctx->stream) : launch_push3d(a, ctx->stream));
+        ctx->launches += 1;
+    }
+    {
+        PhaseScope ps(ctx, PH_YEE);
+        CK(ctx->cfg.ndim == 2 ? launch_yee2d(a, &ctx->run, 1, ctx->stream)
+                              : launch_yee3d(a, &ctx->run, 1, ctx->stream));
+        ctx->launches += 3;
+    }
+    {
+        PhaseScope ps(ctx, PH_FINAL);
+        CK(launch_finalize(a, ctx->stream));
+        ctx->launches += 1;
+    }
+    if ((step_index + 1) % ctx->sort_interval == 0) {
+        PhaseScope ps(ctx, PH_SORT);
+        for (int s = 0; s < ctx->cfg.nspecies; ++s) {
+            if (!ctx->run.sp[s].active) continue;
+            CK(launch_sort(a, s, ctx->geo.tx, ctx->geo.ty, ctx->geo.tz, ctx->stream));
+            ctx->launches += sort_launches(a.npart[s]);
+        }
+    }
+    return PIC_OK;
+}
+
+int build_graph(pic_ctx* ctx) {
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const long long l0 = ctx->launches;
+    int rc = PIC_OK;
+    for (int i = 0; i < ctx->sort_interval && rc == PIC_OK; ++i) rc = launch_one_step(ctx, i);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    ctx->graph_launches = ctx->launches - l0;
+    ctx->launches = l0;
+    if (rc != PIC_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return fail(ctx, PIC_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, PIC_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    ctx->graph_dirty = false;
+    return PIC_OK;
+}
+
+void refresh_args(pic_ctx* ctx) {
+    Args& a = ctx->args;
+    for (int s = 0; s < PIC_NS; ++s) a.npart[s] = ctx->loaded[s];
+}
+
+int device_flags(pic_ctx* ctx) {
+    Ctl h;
+    CK(cudaMemcpyAsync(&h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (h.err & ERR_BADPART) return fail(ctx, PIC_EBADPART, "device: non-finite or out-of-range particle");
+    if (h.err & ERR_OVERFLOW) return fail(ctx, PIC_EOVERFLOW, "device: fixed-point headroom exceeded");
+    if (h.err & ERR_TIMEOUT) return fail(ctx, PIC_ETIMEOUT, "device: bounded wait gave up");
+    return PIC_OK;
+}
+
+int current_parity(pic_ctx* ctx, int s, int* par) {
+    Ctl h;
+    CK(cudaMemcpyAsync(&h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *par = h.parity[s];
+    return PIC_OK;
+}
+
+// Fixed-point shift S: every per-particle current term satisfies |term| * 2^S <= 2^21, so
+// 32 warp lanes sum without int32 overflow and one FFMA rounds it exactly.  A term is bounded
+// by |q| w max(dx/dt, dy/dt, dz/dt, 1) (|v| < c, CIC weights in [0, 1]).
+int choose_shift(const pic_ctx* ctx) {
+    const pic_config& c = ctx->cfg;
+    double vmax = std::fmax(c.dx / c.dt, c.dy / c.dt);
+    if (c.ndim == 3) vmax = std::fmax(vmax, c.dz / c.dt);
+    vmax = std::fmax(vmax, 1.0);
+    double bound = 0.0;
+    for (int s = 0; s < c.nspecies; ++s)
+        if (ctx->run.sp[s].active) bound = std::fmax(bound, std::fabs(ctx->q[s]) * ctx->run.sp[s].w * vmax);
+    if (bound <= 0) return 30;
+    int S = (int)std::floor(std::log2(2097152.0 / bound));
+    if (S > 40) S = 40;
+    if (S < 0) S = 0;
+    return S;
+}
+
+void set_species_scales(pic_ctx* ctx) {
+    const pic_config& c = ctx->cfg;
+    const int S = ctx->run.shift;
+    const double two = std::ldexp(1.0, S);
+    for (int s = 0; s < c.nspecies; ++s) {
+        SpeciesParams& P = ctx->run.sp[s];
+        if (!P.active) continue;
+        const double qw = ctx->q[s] * (double)P.w;
+        P.jx = (float)(-qw * (c.dx / c.dt) * two);
+        P.jy = (float)(-qw * (c.dy / c.dt) * two);
+        P.jz = c.ndim == 2 ? (float)(qw * two) : (float)(-qw * (c.dz / c.dt) * two);
+    }
+    ctx->run.jscale = (float)std::ldexp(1.0, -S);
+}
+
+}  // namespace
+
+// =============================================================================== C ABI
+
+extern "C" int pic_required_bytes(const pic_config* cfg, size_t* bytes_out) {
+    if (!cfg || !bytes_out) return fail(nullptr, PIC_EINVAL, "null argument");
+    Geometry g;
+    std::string err;
+    int rc = geometry(cfg, &g, &err);
+    if (rc != PIC_OK) return fail(nullptr, rc, "%s", err.c_str());
+    *bytes_out = make_layout(cfg, g).total;
+    return PIC_OK;
+}
+
+extern "C" int pic_init(const pic_config* cfg, void* device_arena, size_t arena_bytes,
+                        void* cuda_stream, pic_ctx** out) {
+    if (!cfg || !out) return fail(nullptr, PIC_EINVAL, "null argument");
+    *out = nullptr;
+    Geometry g;
+    std::string err;
+    int rc = geometry(cfg, &g, &err);
+    if (rc != PIC_OK) return fail(nullptr, rc, "%s", err.c_str());
+    Layout L = make_layout(cfg, g);
+    if (!device_arena) return fail(nullptr, PIC_EINVAL, "null arena");
+    if (arena_bytes < L.total) return fail(nullptr, PIC_ENOMEM, "arena has %zu bytes, needs %zu", arena_bytes, L.total);
+    if (reinterpret_cast<uintptr_t>(device_arena) & 255) return fail(nullptr, PIC_EINVAL, "arena must be 256-byte aligned");
+    pic_ctx* ctx = new (std::nothrow) pic_ctx;
+    if (!ctx) return fail(nullptr, PIC_ENOMEM, "host allocation failed");
+    ctx->cfg = *cfg;
+    if (ctx->cfg.ndim == 2) { ctx->cfg.nz = 1; ctx->cfg.dz = ctx->cfg.dx; }
+    ctx->geo = g;
+    ctx->lay = L;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->arena = (char*)device_arena;
+    ctx->sort_interval = cfg->sort_interval > 0 ? cfg->sort_interval : 8;
+
+    auto bail = [&](int code) { g_init_error = ctx->err; delete ctx; return code; };
+#define CKI(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { fail(ctx, PIC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); return bail(PIC_ECUDA); } } while (0)
+    // zero the whole state
+    CKI(cudaMemsetAsync(ctx->arena, 0, L.total, ctx->stream));
+
+    RunDev& R = ctx->run;
+    const pic_config& c = ctx->cfg;
+    R.nx = c.nx; R.ny = c.ny; R.nz = c.nz;
+    R.ntx = g.ntx; R.nty = g.nty; R.ntz = g.ntz;
+    R.cell_off = 0;
+    R.dtdx = (float)(c.dt / c.dx); R.dtdy = (float)(c.dt / c.dy); R.dtdz = (float)(c.dt / c.dz);
+    R.cx = R.dtdx; R.cy = R.dtdy; R.cz = R.dtdz;
+    for (int d = 0; d < 3; ++d) {
+        R.E[d] = at<float>(ctx, L.E[d]);
+        R.B[d] = at<float>(ctx, L.B[d]);
+        R.J[d] = at<long long>(ctx, L.J[d]);
+        R.Jlast[d] = L.Jlast[d] ? at<long long>(ctx, L.Jlast[d]) : nullptr;
+        R.msum[d] = nullptr;   // published when a drag species is loaded
+        R.ubar[d] = nullptr;
+    }
+    R.mcnt = nullptr;
+    R.shift = 30;
+    R.jscale = (float)std::ldexp(1.0, -30);
+
+    std::vector<int2> work(g.ntiles);
+    for (long long t = 0; t < g.ntiles; ++t) work[t] = make_int2(0, (int)t);
+    CKI(cudaMemcpyAsync(at<int2>(ctx, L.work), work.data(), sizeof(int2) * g.ntiles, cudaMemcpyHostToDevice, ctx->stream));
+
+    Args& a = ctx->args;
+    a.ctl = at<Ctl>(ctx, L.ctl);
+    a.runs = at<RunDev>(ctx, L.runs);
+    a.work = at<int2>(ctx, L.work);
+    a.nwork = (int)g.ntiles;
+    a.nspecies = c.nspecies;
+    for (int s = 0; s < PIC_NS; ++s)
+        for (int b = 0; b < 2; ++b) {
+            SpeciesBuf& B = a.buf[s][b];
+            B.cell = at<int>(ctx, L.part[s][b][0]);
+            for (int d = 0; d < 3; ++d) B.o[d] = L.part[s][b][1 + d] ? at<float>(ctx, L.part[s][b][1 + d]) : nullptr;
+            for (int d = 0; d < 3; ++d) B.u[d] = at<float>(ctx, L.part[s][b][4 + d]);
+            B.id = L.part[s][b][7] ? at<int>(ctx, L.part[s][b][7]) : nullptr;
+        }
+    for (int s = 0; s < PIC_NS; ++s) {
+        a.start[s] = at<int>(ctx, L.start[s]);
+        a.count[s] = at<int>(ctx, L.count);
+        a.cursor[s] = at<int>(ctx, L.cursor);
+        a.npart[s] = 0;
+    }
+    a.nkeys = g.ncell;
+    a.partials = at<double>(ctx, L.partials);
+    a.hist = at<DiagRec>(ctx, L.hist);
+    a.hist_cap = c.diag_interval > 0 ? c.diag_capacity : 1;
+    a.diag_interval = c.diag_interval;
+    a.dt = c.dt;
+    a.dV = c.dx * c.dy * (c.ndim == 3 ? c.dz : 1.0);
+    a.scan_tmp = at<int>(ctx, L.scan_tmp);
+    a.ndim = c.ndim;
+    a.nruns = 1;
+
+    if (upload_run(ctx) != PIC_OK) return bail(PIC_ECUDA);
+    CKI(cudaStreamSynchronize(ctx->stream));
+#undef CKI
+    *out = ctx;
+    return PIC_OK;
+}
+
+namespace {
+__global__ void iota_kernel(int* p, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = (int)i;
+}
+}  // namespace
+
+extern "C" int pic_load_species(pic_ctx* ctx, int s, const pic_species* sp, int64_t n,
+                                const int32_t* cell, const float* offset, const float* u) {
+    if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    if (!sp || s < 0 || s >= ctx->cfg.nspecies) return fail(ctx, PIC_EINVAL, "bad species index");
+    if (n < 0 || n > ctx->cfg.capacity[s]) return fail(ctx, PIC_ENOMEM, "n = %lld exceeds capacity", (long long)n);
+    if (n > 0 && (!cell || !offset || !u)) return fail(ctx, PIC_EINVAL, "null particle array");
+    if (ctx->host_step != 0) return fail(ctx, PIC_ESTATE, "species are loaded before the first step");
+    if (!(std::isfinite(sp->q) && std::isfinite(sp->m) && sp->m > 0 && std::isfinite(sp->w) && sp->w >= 0 &&
+          std::isfinite(sp->nu) && sp->nu >= 0 && std::fabs(sp->q) <= 1.0))
+        return fail(ctx, PIC_EINVAL, "bad species parameters (|q| <= 1, m > 0, w >= 0, nu >= 0)");
+    const pic_config& c = ctx->cfg;
+    // load into the species' current buffer
+    int par = 0;
+    int rc = current_parity(ctx, s, &par);
+    if (rc) return rc;
+    SpeciesBuf& B = ctx->args.buf[s][par];
+    if (n > 0) {
+        CK(cudaMemcpyAsync(B.cell, cell, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+        for (int d = 0; d < c.ndim; ++d)
+            CK(cudaMemcpyAsync(B.o[d], offset + (size_t)d * n, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+        for (int d = 0; d < 3; ++d)
+            CK(cudaMemcpyAsync(B.u[d], u + (size_t)d * n, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+        if (B.id) iota_kernel<<<1024, 256, 0, ctx->stream>>>(B.id, n);
+    }
+    ctx->loaded[s] = n;
+    refresh_args(ctx);
+    CK(launch_validate(ctx->args, s, 0, n, 0, ctx->stream));
+    rc = device_flags(ctx);
+    if (rc) { ctx->loaded[s] = 0; refresh_args(ctx); return rc; }
+
+    SpeciesParams& P = ctx->run.sp[s];
+    P.active = 1;
+    P.qmdt2 = (float)(sp->q * c.dt / (2.0 * sp->m));
+    P.w = (float)sp->w;
+    P.dragf = (float)(-std::expm1(-sp->nu * c.dt));
+    P.drag = sp->nu > 0 ? 1 : 0;
+    ctx->q[s] = sp->q;
+    ctx->run.shift = choose_shift(ctx);
+    set_species_scales(ctx);
+    if (P.drag && !ctx->run.msum[0]) {
+        for (int d = 0; d < 3; ++d) {
+            ctx->run.msum[d] = at<long long>(ctx, ctx->lay.msum[d]);
+            ctx->run.ubar[d] = at<float>(ctx, ctx->lay.ubar[d]);
+        }
+        ctx->run.mcnt = at<int>(ctx, ctx->lay.mcnt);
+    }
+    rc = upload_run(ctx);
+    if (rc) return rc;
+    // bin by tile, then the drag moments of the load
+    CK(launch_sort(ctx->args, s, ctx->geo.tx, ctx->geo.ty, ctx->geo.tz, ctx->stream));
+    if (P.drag) {
+        CK(launch_moments_init(ctx->args, s, ctx->stream));
+        CK(launch_moments_finalize(ctx->args, &ctx->run, 1, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return device_flags(ctx);
+}
+
+extern "C" int pic_step(pic_ctx* ctx, int nsteps) {
+    if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    if (nsteps < 0) return fail(ctx, PIC_EINVAL, "nsteps < 0");
+    const bool use_graph = !(ctx->cfg.flags & (PIC_FLAG_PROFILE | PIC_FLAG_NO_GRAPH));
+    while (nsteps > 0) {
+        const int K = ctx->sort_interval;
+        if (use_graph && ctx->host_step % K == 0 && nsteps >= K) {
+            if (ctx->graph_dirty || !ctx->graph) {
+                int rc = build_graph(ctx);
+                if (rc) return rc;
+            }
+            CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+            ctx->launches += ctx->graph_launches;
+            ctx->host_step += K;
+            nsteps -= K;
+        } else {
+            int rc = launch_one_step(ctx, ctx->host_step);
+            if (rc) return rc;
+            ctx->host_step += 1;
+            nsteps -= 1;
+        }
+    }
+    return PIC_OK;
+}
+
+extern "C" int pic_sync(pic_ctx* ctx) {
+    if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    CK(cudaStreamSynchronize(ctx->stream));
+    return device_flags(ctx);
+}
+
+static long long records_written(const pic_ctx* ctx) {
+    const int M = ctx->cfg.diag_interval;
+    if (M <= 0 || ctx->host_step <= 0) return 0;
+    return (ctx->host_step - 1) / M + 1;
+}
+
+extern "C" int pic_diag(pic_ctx* ctx, pic_diag_rec* out, int max_recs, int* n_out) {
+    if (!ctx || !n_out || (max_recs > 0 && !out)) return fail(ctx, PIC_EINVAL, "null argument");
+    int rc = pic_sync(ctx);
+    if (rc) return rc;
+    const long long nrec = records_written(ctx);
+    const int cap = ctx->args.hist_cap;
+    const long long first = nrec > cap ? nrec - cap : 0;
+    long long n = nrec - first;
+    if (n > max_recs) n = max_recs;
+    for (long long r = 0; r < n; ++r) {
+        const long long slot = (first + r) % cap;
+        CK(cudaMemcpyAsync(out + r, ctx->args.hist + slot, sizeof(DiagRec), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    *n_out = (int)n;
+    return PIC_OK;
+}
+
+extern "C" int pic_get_particles(pic_ctx* ctx, int s, int32_t* cell, float* offset, float* u,
+                                 int32_t* id, int64_t n) {
+    if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    if (s < 0 || s >= ctx->cfg.nspecies) return fail(ctx, PIC_EINVAL, "bad species index");
+    if (n != ctx->loaded[s]) return fail(ctx, PIC_EINVAL, "n must equal the loaded count (%lld)", ctx->loaded[s]);
+    int rc = pic_sync(ctx);
+    if (rc) return rc;
+    int par = 0;
+    rc = current_parity(ctx, s, &par);
+    if (rc) return rc;
+    const SpeciesBuf& B = ctx->args.buf[s][par];
+    if (n > 0) {
+        if (cell) CK(cudaMemcpyAsync(cell, B.cell, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+        if (offset)
+            for (int d = 0; d < ctx->cfg.ndim; ++d)
+                CK(cudaMemcpyAsync(offset + (size_t)d * n, B.o[d], 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+        if (u)
+            for (int d = 0; d < 3; ++d)
+                CK(cudaMemcpyAsync(u + (size_t)d * n, B.u[d], 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+        if (id) {
+            if (!B.id) return fail(ctx, PIC_ESTATE, "ids need track_ids");
+            CK(cudaMemcpyAsync(id, B.id, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PIC_OK;
+}
+
+extern "C" int pic_get_fields(pic_ctx* ctx, float* E, float* B, int64_t* J) {
+    if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    int rc = pic_sync(ctx);
+    if (rc) return rc;
+    const size_t nc = (size_t)ctx->geo.ncell;
+    for (int d = 0; d < 3; ++d) {
+        if (E) CK(cudaMemcpyAsync(E + d * nc, ctx->run.E[d], 4 * nc, cudaMemcpyDeviceToHost, ctx->stream));
+        if (B) CK(cudaMemcpyAsync(B + d * nc, ctx->run.B[d], 4 * nc, cudaMemcpyDeviceToHost, ctx->stream));
+        if (J) {
+            if (!ctx->run.Jlast[0]) return fail(ctx, PIC_ESTATE, "J needs PIC_FLAG_KEEP_J");
+            CK(cudaMemcpyAsync(J + d * nc, ctx->run.Jlast[d], 8 * nc, cudaMemcpyDeviceToHost, ctx->stream));
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PIC_OK;
+}
+
+extern "C" int pic_set_fields(pic_ctx* ctx, const float* E, const float* B) {
+    if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    const size_t nc = (size_t)ctx->geo.ncell;
+    for (int d = 0; d < 3; ++d) {
+        if (E) CK(cudaMemcpyAsync(ctx->run.E[d], E + d * nc, 4 * nc, cudaMemcpyHostToDevice, ctx->stream));
+        if (B) CK(cudaMemcpyAsync(ctx->run.B[d], B + d * nc, 4 * nc, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PIC_OK;
+}
+
+extern "C" int pic_fixed_point_shift(const pic_ctx* ctx, int* shift_out) {
+    if (!ctx || !shift_out) return PIC_EINVAL;
+    *shift_out = ctx->run.shift;
+    return PIC_OK;
+}
+
+extern "C" int pic_fit_growth(pic_ctx* ctx, int width, double t_noise, double start_factor,
+                              double end_factor, double* gamma_out, double* t0_out, double* t1_out) {
+    if (!ctx || !gamma_out) return fail(ctx, PIC_EINVAL, "null argument");
+    if (width < 2) return fail(ctx, PIC_EINVAL, "width must be >= 2");
+    int rc = pic_sync(ctx);
+    if (rc) return rc;
+    const long long nrec = records_written(ctx);
+    const int cap = ctx->args.hist_cap;
+    const long long first = nrec > cap ? nrec - cap : 0;
+    const int n = (int)(nrec - first);
+    double* d_out = at<double>(ctx, ctx->lay.fit);
+    CK(launch_fit(ctx->args, first, n, width, t_noise, start_factor, end_factor, d_out, ctx->stream));
+    ctx->launches += 1;
+    double h[3];
+    CK(cudaMemcpyAsync(h, d_out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *gamma_out = h[0];
+    if (t0_out) *t0_out = h[1];
+    if (t1_out) *t1_out = h[2];
+    return PIC_OK;
+}
+
+extern "C" int pic_kernel_times(pic_ctx* ctx, pic_kernel_time* out, int max, int* n_out) {
+    if (!ctx || !n_out) return fail(ctx, PIC_EINVAL, "null argument");
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (auto& ev : ctx->pending) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ev.a, ev.b));
+        ctx->phase_ms[ev.phase] += ms;
+        ctx->phase_n[ev.phase] += 1;
+        ctx->pool.push_back(ev.a);
+        ctx->pool.push_back(ev.b);
+    }
+    ctx->pending.clear();
+    int n = 0;
+    for (int p = 0; p < PH_N && n < max; ++p) {
+        if (!out) break;
+        std::snprintf(out[n].name, sizeof out[n].name, "%s", kPhaseName[p]);
+        out[n].launches = ctx->phase_n[p];
+        out[n].total_ms = ctx->phase_ms[p];
+        ++n;
+    }
+    *n_out = n;
+    return PIC_OK;
+}
+
+extern "C" int64_t pic_launch_count(const pic_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+extern "C" int64_t pic_step_count(const pic_ctx* ctx) { return ctx ? ctx->host_step : -1; }
+
+extern "C" const char* pic_last_error(const pic_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+extern "C" void pic_free(pic_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    for (auto& ev : ctx->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
+    for (auto e : ctx->pool) cudaEventDestroy(e);
+    delete ctx;
+}

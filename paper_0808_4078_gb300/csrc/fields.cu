@@ -1,0 +1,381 @@
+// fields.cu -- Yee FDTD update, drag-moment finalisation, diagnostics records, growth fit,
+// particle validation.
+//
+// Yee step (periodic):  B^n -> B^{n+1/2}: B -= (dt/2) curl E;  E^{n+1} = E^n + dt (curl B - J);
+// B^{n+1/2} -> B^{n+1}: B -= (dt/2) curl E.  J is the int64 fixed-point current of the step,
+// converted with 2^-S and cleared after use.  The E kernel also turns the drag moments
+// accumulated by the push (sum u, count per cell) into the cell-mean momentum <u> for the next
+// step's Krook drag (Eq. (3) friction) and clears the accumulators.
+#include <cfloat>
+#include <cmath>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+constexpr int NT = 256;
+
+// ------------------------------------------------------------------ 2D Yee
+__global__ void yee_b_half_2d(const RunDev* __restrict__ runs, int run) {
+    const RunDev& R = runs[run];
+    const int nx = R.nx, ny = R.ny;
+    const long long n = (long long)nx * ny;
+    const float hx = 0.5f * R.cx, hy = 0.5f * R.cy;
+    float* __restrict__ Ex = R.E[0];
+    float* __restrict__ Ey = R.E[1];
+    float* __restrict__ Ez = R.E[2];
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
+        const int ip = i + 1 == nx ? 0 : i + 1;
+        const int jp = j + 1 == ny ? 0 : j + 1;
+        const long long cxp = (long long)j * nx + ip, cyp = (long long)jp * nx + i;
+        const float ez = Ez[c];
+        R.B[0][c] -= hy * (Ez[cyp] - ez);
+        R.B[1][c] += hx * (Ez[cxp] - ez);
+        R.B[2][c] -= hx * (Ey[cxp] - Ey[c]) - hy * (Ex[cyp] - Ex[c]);
+    }
+}
+
+__global__ void yee_e_2d(const RunDev* __restrict__ runs, int run, float dt) {
+    const RunDev& R = runs[run];
+    const int nx = R.nx, ny = R.ny;
+    const long long n = (long long)nx * ny;
+    const float cx = R.cx, cy = R.cy, js = R.jscale * dt;
+    const float* __restrict__ Bx = R.B[0];
+    const float* __restrict__ By = R.B[1];
+    const float* __restrict__ Bz = R.B[2];
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
+        const int im = i == 0 ? nx - 1 : i - 1;
+        const int jm = j == 0 ? ny - 1 : j - 1;
+        const long long cxm = (long long)j * nx + im, cym = (long long)jm * nx + i;
+        const long long j0 = R.J[0][c], j1 = R.J[1][c], j2 = R.J[2][c];
+        const float jx = (float)j0 * js, jy = (float)j1 * js, jz = (float)j2 * js;
+        R.J[0][c] = 0; R.J[1][c] = 0; R.J[2][c] = 0;
+        if (R.Jlast[0]) { R.Jlast[0][c] = j0; R.Jlast[1][c] = j1; R.Jlast[2][c] = j2; }
+        const float bz = Bz[c];
+        R.E[0][c] += cy * (bz - Bz[cym]) - jx;
+        R.E[1][c] += -cx * (bz - Bz[cxm]) - jy;
+        R.E[2][c] += cx * (By[c] - By[cxm]) - cy * (Bx[c] - Bx[cym]) - jz;
+        if (R.msum[0]) {
+            const int cnt = R.mcnt[c];
+            const float inv = cnt > 0 ? 1.0f / (float)cnt : 0.f;
+            const float sc = inv * (1.0f / 1048576.0f);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                R.ubar[k][c] = (float)R.msum[k][c] * sc;
+                R.msum[k][c] = 0;
+            }
+            R.mcnt[c] = 0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ 3D Yee
+__global__ void yee_b_half_3d(const RunDev* __restrict__ runs, int run) {
+    const RunDev& R = runs[run];
+    const int nx = R.nx, ny = R.ny, nz = R.nz;
+    const long long nxy = (long long)nx * ny, n = nxy * nz;
+    const float hx = 0.5f * R.cx, hy = 0.5f * R.cy, hz = 0.5f * R.cz;
+    const float* __restrict__ Ex = R.E[0];
+    const float* __restrict__ Ey = R.E[1];
+    const float* __restrict__ Ez = R.E[2];
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(c / nxy);
+        const long long r = c - (long long)k * nxy;
+        const int j = (int)(r / nx), i = (int)(r - (long long)j * nx);
+        const long long dxp = (i + 1 == nx ? -(long long)(nx - 1) : 1);
+        const long long dyp = (j + 1 == ny ? -(long long)(ny - 1) * nx : nx);
+        const long long dzp = (k + 1 == nz ? -(long long)(nz - 1) * nxy : nxy);
+        const float ex = Ex[c], ey = Ey[c], ez = Ez[c];
+        R.B[0][c] -= hy * (Ez[c + dyp] - ez) - hz * (Ey[c + dzp] - ey);
+        R.B[1][c] -= hz * (Ex[c + dzp] - ex) - hx * (Ez[c + dxp] - ez);
+        R.B[2][c] -= hx * (Ey[c + dxp] - ey) - hy * (Ex[c + dyp] - ex);
+    }
+}
+
+__global__ void yee_e_3d(const RunDev* __restrict__ runs, int run, float dt) {
+    const RunDev& R = runs[run];
+    const int nx = R.nx, ny = R.ny, nz = R.nz;
+    const long long nxy = (long long)nx * ny, n = nxy * nz;
+    const float cx = R.cx, cy = R.cy, cz = R.cz, js = R.jscale * dt;
+    const float* __restrict__ Bx = R.B[0];
+    const float* __restrict__ By = R.B[1];
+    const float* __restrict__ Bz = R.B[2];
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(c / nxy);
+        const long long r = c - (long long)k * nxy;
+        const int j = (int)(r / nx), i = (int)(r - (long long)j * nx);
+        const long long dxm = (i == 0 ? -(long long)(nx - 1) : 1);
+        const long long dym = (j == 0 ? -(long long)(ny - 1) * nx : nx);
+        const long long dzm = (k == 0 ? -(long long)(nz - 1) * nxy : nxy);
+        const long long j0 = R.J[0][c], j1 = R.J[1][c], j2 = R.J[2][c];
+        const float jx = (float)j0 * js, jy = (float)j1 * js, jz = (float)j2 * js;
+        R.J[0][c] = 0; R.J[1][c] = 0; R.J[2][c] = 0;
+        if (R.Jlast[0]) { R.Jlast[0][c] = j0; R.Jlast[1][c] = j1; R.Jlast[2][c] = j2; }
+        const float bx = Bx[c], by = By[c], bz = Bz[c];
+        R.E[0][c] += cy * (bz - Bz[c - dym]) - cz * (by - By[c - dzm]) - jx;
+        R.E[1][c] += cz * (bx - Bx[c - dzm]) - cx * (bz - Bz[c - dxm]) - jy;
+        R.E[2][c] += cx * (by - By[c - dxm]) - cy * (bx - Bx[c - dym]) - jz;
+        if (R.msum[0]) {
+            const int cnt = R.mcnt[c];
+            const float inv = cnt > 0 ? 1.0f / (float)cnt : 0.f;
+            const float sc = inv * (1.0f / 1048576.0f);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                R.ubar[q][c] = (float)R.msum[q][c] * sc;
+                R.msum[q][c] = 0;
+            }
+            R.mcnt[c] = 0;
+        }
+    }
+}
+
+// Moments -> <u> without a field update (after loading particles).
+__global__ void moments_finalize_kernel(const RunDev* __restrict__ runs, int run) {
+    const RunDev& R = runs[run];
+    if (!R.msum[0]) return;
+    const long long n = (long long)R.nx * R.ny * R.nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int cnt = R.mcnt[c];
+        const float inv = cnt > 0 ? 1.0f / (float)cnt : 0.f;
+        const float sc = inv * (1.0f / 1048576.0f);
+        for (int q = 0; q < 3; ++q) {
+            R.ubar[q][c] = (float)R.msum[q][c] * sc;
+            R.msum[q][c] = 0;
+        }
+        R.mcnt[c] = 0;
+    }
+}
+
+// Drag moments of the loaded particles (NGP cell of the current position).
+__global__ void moments_init_kernel(Args a, int s) {
+    const SpeciesBuf B = a.buf[s][a.ctl->parity[s]];
+    const long long n = a.npart[s];
+    const RunDev& R = a.runs[0];
+    if (!R.sp[s].drag || !R.msum[0]) return;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const long long c = B.cell[p] - R.cell_off;
+        const float ms = 1048576.0f;
+        atomicAdd((unsigned long long*)&R.msum[0][c], (unsigned long long)__float2ll_rn(B.u[0][p] * ms));
+        atomicAdd((unsigned long long*)&R.msum[1][c], (unsigned long long)__float2ll_rn(B.u[1][p] * ms));
+        atomicAdd((unsigned long long*)&R.msum[2][c], (unsigned long long)__float2ll_rn(B.u[2][p] * ms));
+        atomicAdd(&R.mcnt[c], 1);
+    }
+}
+
+// Validation of loaded particles: cell in range, offsets in [0,1), finite momenta.
+__global__ void validate_kernel(Args a, int s, long long first, long long n, int run) {
+    const SpeciesBuf B = a.buf[s][a.ctl->parity[s]];
+    const RunDev& R = a.runs[run];
+    const long long ncell = (long long)R.nx * R.ny * R.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long p = first + q;
+        const long long c = (long long)B.cell[p] - R.cell_off;
+        bool ok = c >= 0 && c < ncell;
+        for (int d = 0; d < a.ndim; ++d) {
+            const float o = B.o[d][p];
+            ok = ok && o >= 0.f && o < 1.f;
+        }
+        for (int d = 0; d < 3; ++d) ok = ok && isfinite(B.u[d][p]) && fabsf(B.u[d][p]) < 1e6f;
+        if (!ok) atomicOr(&a.ctl->err, ERR_BADPART);
+    }
+}
+
+// ------------------------------------------------------------------ step finalisation
+// Reduces the per-CTA field-energy partials in a fixed order (deterministic FP64), converts the
+// int64 kinetic/momentum sums, writes one history record on diagnostic steps, and advances the
+// device step counter.
+__global__ void __launch_bounds__(NT) finalize_kernel(Args a) {
+    __shared__ double red[NT][6];
+    const long long step = a.ctl->step;
+    const bool diag = a.diag_interval > 0 && (step % a.diag_interval) == 0;
+    if (diag) {
+        double s[6] = {0, 0, 0, 0, 0, 0};
+        for (int w = threadIdx.x; w < a.nwork; w += NT)
+            for (int c = 0; c < 6; ++c) s[c] += a.partials[(size_t)w * 8 + c];
+        for (int c = 0; c < 6; ++c) red[threadIdx.x][c] = s[c];
+        __syncthreads();
+        for (int o = NT / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o)
+                for (int c = 0; c < 6; ++c) red[threadIdx.x][c] += red[threadIdx.x + o][c];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const long long r = step / a.diag_interval;
+            DiagRec& d = a.hist[r % a.hist_cap];
+            d.step = step;
+            d.t = (double)step * a.dt;
+            for (int c = 0; c < 3; ++c) {
+                d.WE[c] = red[0][c] * a.dV;
+                d.WB[c] = red[0][3 + c] * a.dV;
+            }
+            const double sc = a.dV / 4294967296.0;
+            double P[3] = {0, 0, 0};
+            for (int sp = 0; sp < PIC_NS; ++sp) {
+                d.Ekin[sp] = (double)a.ctl->kin[sp][0] * sc;
+                for (int c = 0; c < 3; ++c) P[c] += (double)a.ctl->kin[sp][1 + c] * sc;
+                for (int c = 0; c < 4; ++c) a.ctl->kin[sp][c] = 0;
+            }
+            for (int c = 0; c < 3; ++c) d.P[c] = P[c];
+            d.flags = a.ctl->err;
+            d.reserved = 0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) a.ctl->step = step + 1;
+}
+
+// ------------------------------------------------------------------ growth fit (FP64)
+// Records are in ring order starting at record index first.  Windows of `width` consecutive
+// records with all W in (lo, hi); least-squares slope of ln W; the largest slope wins.
+__global__ void __launch_bounds__(NT) fit_kernel(const DiagRec* __restrict__ hist, int cap,
+                                                 long long first, int nrec, int width,
+                                                 double t_noise, double start_factor,
+                                                 double end_factor, double* out) {
+    __shared__ double s_noise[NT], s_cnt[NT], s_max[NT];
+    __shared__ double s_best[NT];
+    __shared__ int s_bi[NT];
+    auto W = [&](int r) {
+        const DiagRec& d = hist[(first + r) % cap];
+        return d.WB[0] + d.WB[1];
+    };
+    auto T = [&](int r) { return hist[(first + r) % cap].t; };
+    double sn = 0, cn = 0, mx = -DBL_MAX;
+    for (int r = threadIdx.x; r < nrec; r += NT) {
+        const double w = W(r);
+        if (T(r) <= t_noise) { sn += w; cn += 1; }
+        mx = fmax(mx, w);
+    }
+    s_noise[threadIdx.x] = sn; s_cnt[threadIdx.x] = cn; s_max[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = NT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s_noise[threadIdx.x] += s_noise[threadIdx.x + o];
+            s_cnt[threadIdx.x] += s_cnt[threadIdx.x + o];
+            s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    const double lo = s_cnt[0] > 0 ? start_factor * s_noise[0] / s_cnt[0] : DBL_MAX;
+    const double hi = end_factor > 0 ? end_factor * s_max[0] : DBL_MAX;
+    double best = -DBL_MAX;
+    int bi = -1;
+    for (int a0 = threadIdx.x; a0 + width <= nrec; a0 += NT) {
+        bool ok = s_cnt[0] > 0;
+        double st = 0, sy = 0;
+        for (int r = a0; r < a0 + width && ok; ++r) {
+            const double w = W(r);
+            ok = w > lo && w < hi;
+            st += T(r);
+            sy += log(w);
+        }
+        if (!ok) continue;
+        const double tm = st / width, ym = sy / width;
+        double num = 0, den = 0;
+        for (int r = a0; r < a0 + width; ++r) {
+            const double dt = T(r) - tm;
+            num += dt * (log(W(r)) - ym);
+            den += dt * dt;
+        }
+        const double slope = num / den;
+        if (slope > best) { best = slope; bi = a0; }
+    }
+    s_best[threadIdx.x] = best; s_bi[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = NT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const double b2 = s_best[threadIdx.x + o];
+            const int i2 = s_bi[threadIdx.x + o];
+            // larger slope wins; ties go to the earlier window
+            if (b2 > s_best[threadIdx.x] || (b2 == s_best[threadIdx.x] && i2 >= 0 &&
+                                             (s_bi[threadIdx.x] < 0 || i2 < s_bi[threadIdx.x]))) {
+                s_best[threadIdx.x] = b2;
+                s_bi[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (s_bi[0] < 0) {
+            out[0] = nan(""); out[1] = nan(""); out[2] = nan("");
+        } else {
+            out[0] = 0.5 * s_best[0];
+            out[1] = T(s_bi[0]);
+            out[2] = T(s_bi[0] + width - 1);
+        }
+    }
+}
+
+int grid_for(long long n) {
+    long long g = (n + NT - 1) / NT;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+cudaError_t launch_yee2d(const Args& a, const RunDev* host_runs, int nruns, cudaStream_t s) {
+    for (int r = 0; r < nruns; ++r) {
+        const long long n = (long long)host_runs[r].nx * host_runs[r].ny;
+        const int g = grid_for(n);
+        yee_b_half_2d<<<g, NT, 0, s>>>(a.runs, r);
+        yee_e_2d<<<g, NT, 0, s>>>(a.runs, r, (float)a.dt);
+        yee_b_half_2d<<<g, NT, 0, s>>>(a.runs, r);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_yee3d(const Args& a, const RunDev* host_runs, int nruns, cudaStream_t s) {
+    for (int r = 0; r < nruns; ++r) {
+        const long long n = (long long)host_runs[r].nx * host_runs[r].ny * host_runs[r].nz;
+        const int g = grid_for(n);
+        yee_b_half_3d<<<g, NT, 0, s>>>(a.runs, r);
+        yee_e_3d<<<g, NT, 0, s>>>(a.runs, r, (float)a.dt);
+        yee_b_half_3d<<<g, NT, 0, s>>>(a.runs, r);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Args& a, cudaStream_t s) {
+    finalize_kernel<<<1, NT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_init(const Args& a, int species, cudaStream_t s) {
+    moments_init_kernel<<<grid_for(a.npart[species]), NT, 0, s>>>(a, species);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_finalize(const Args& a, const RunDev* host_runs, int nruns,
+                                    cudaStream_t s) {
+    for (int r = 0; r < nruns; ++r) {
+        const long long n = (long long)host_runs[r].nx * host_runs[r].ny * host_runs[r].nz;
+        moments_finalize_kernel<<<grid_for(n), NT, 0, s>>>(a.runs, r);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const Args& a, int species, long long first, long long n, int run,
+                            cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    validate_kernel<<<grid_for(n), NT, 0, s>>>(a, species, first, n, run);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit(const Args& a, long long first, int nrec, int width, double t_noise,
+                       double start_factor, double end_factor, double* out3, cudaStream_t s) {
+    fit_kernel<<<1, NT, 0, s>>>(a.hist, a.hist_cap, first, nrec, width, t_noise, start_factor,
+                                end_factor, out3);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

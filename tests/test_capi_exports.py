@@ -1,0 +1,59 @@
+"""The C-ABI library builds, loads without a GPU and exports every function of include/pic.h."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pic_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpic():
+    from paper_0808_4078_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared("pic.h")
+    for must in ("pic_init", "pic_load_species", "pic_step", "pic_diag", "pic_required_bytes",
+                 "pic_free", "pic_last_error"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(libpic):
+    missing = [n for n in _declared("pic.h") if not hasattr(libpic, n)]
+    assert not missing, missing
+
+
+def test_required_bytes_and_config_errors_without_gpu(libpic):
+    import paper_0808_4078_gb300 as pic
+    cfg = pic.Config(2, 64, 64, 1, 0.1, 0.1, 0.1, 0.05, 2,
+                     (ctypes.c_int64 * 2)(65536, 65536), 8, 1, 100, 0, 0, 0, 0, 0)
+    n = pic.required_bytes(cfg)
+    # two particle buffers x 2 species x 65536 x 24 B, plus per-cell state
+    assert n >= 2 * 2 * 65536 * 24 + 64 * 64 * (24 + 24)
+    bad = pic.Config(2, 60, 64, 1, 0.1, 0.1, 0.1, 0.05, 2, (ctypes.c_int64 * 2)(1, 1),
+                     8, 1, 100, 0, 0, 0, 0, 0)
+    with pytest.raises(pic.PicError) as e:
+        pic.required_bytes(bad)
+    assert e.value.code == -1
+    courant = pic.Config(2, 64, 64, 1, 0.1, 0.1, 0.1, 0.08, 2, (ctypes.c_int64 * 2)(1, 1),
+                         8, 1, 100, 0, 0, 0, 0, 0)
+    with pytest.raises(pic.PicError):
+        pic.required_bytes(courant)
+
+
+def test_package_fails_loudly_without_library(tmp_path, monkeypatch):
+    import paper_0808_4078_gb300 as pic
+    monkeypatch.setattr(pic, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(pic, "_lib", None)
+    with pytest.raises(RuntimeError):
+        pic.lib()
