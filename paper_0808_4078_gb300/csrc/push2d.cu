@@ -48,25 +48,39 @@ struct Win {
 
 __device__ __forceinline__ Win window(float o, int c, float no) {
     Win w;
+    const float mo = __fsub_rn(1.f, o), mno = __fsub_rn(1.f, no);
     if (c < 0) {
-        w.S0[0] = 0.f; w.S0[1] = 1.f - o; w.S0[2] = o;
-        w.S1[0] = 1.f - no; w.S1[1] = no; w.S1[2] = 0.f;
-        w.C[0] = 1.f - no; w.C[1] = o;
+        w.S0[0] = 0.f; w.S0[1] = mo; w.S0[2] = o;
+        w.S1[0] = mno; w.S1[1] = no; w.S1[2] = 0.f;
+        w.C[0] = mno; w.C[1] = o;
         w.off = -1;
     } else if (c == 0) {
-        w.S0[0] = 1.f - o; w.S0[1] = o; w.S0[2] = 0.f;
-        w.S1[0] = 1.f - no; w.S1[1] = no; w.S1[2] = 0.f;
-        w.C[0] = o - no; w.C[1] = 0.f;
+        w.S0[0] = mo; w.S0[1] = o; w.S0[2] = 0.f;
+        w.S1[0] = mno; w.S1[1] = no; w.S1[2] = 0.f;
+        w.C[0] = __fsub_rn(o, no); w.C[1] = 0.f;
         w.off = 0;
     } else {
-        w.S0[0] = 1.f - o; w.S0[1] = o; w.S0[2] = 0.f;
-        w.S1[0] = 0.f; w.S1[1] = 1.f - no; w.S1[2] = no;
-        w.C[0] = o - 1.f; w.C[1] = -no;
+        w.S0[0] = mo; w.S0[1] = o; w.S0[2] = 0.f;
+        w.S1[0] = 0.f; w.S1[1] = mno; w.S1[2] = no;
+        w.C[0] = __fsub_rn(o, 1.f); w.C[1] = -no;
         w.off = 0;
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) w.A[k] = 0.5f * (w.S0[k] + w.S1[k]);
+    for (int k = 0; k < 3; ++k) w.A[k] = __fmul_rn(0.5f, __fadd_rn(w.S0[k], w.S1[k]));
     return w;
+}
+
+// Path-averaged shape product of the out-of-plane current,
+// S0x (S0y/3 + S1y/6) + S1x (S0y/6 + S1y/3), with every rounding fixed so that all code
+// paths produce bitwise identical terms.
+__device__ __forceinline__ float zp(float s0, float s1) {
+    return __fmaf_rn(s1, 1.f / 6.f, __fmul_rn(s0, 1.f / 3.f));
+}
+__device__ __forceinline__ float zq(float s0, float s1) {
+    return __fmaf_rn(s1, 1.f / 3.f, __fmul_rn(s0, 1.f / 6.f));
+}
+__device__ __forceinline__ float zw(float s0x, float s1x, float p, float q) {
+    return __fmaf_rn(s1x, q, __fmul_rn(s0x, p));
 }
 
 // Warp sum of 16 int values; lane l returns the total of value index l >> 1.
@@ -119,67 +133,74 @@ struct GlobalFields {
     }
 };
 
-// CIC gather of the six staggered components at node (i, j) + offsets (ox, oy).
+__device__ __forceinline__ float lerp2(float w0, float w1, float a, float b) {
+    return __fmaf_rn(w1, b, __fmul_rn(w0, a));
+}
+
+// CIC gather of the six staggered components at node (i, j) + offsets (ox, oy).  Roundings
+// are explicit so that the shared-memory and global-memory instances agree bitwise.
 template <class Acc>
 __device__ __forceinline__ void gather(const Acc& F, int i, int j, float ox, float oy, float EB[6]) {
     // half-shifted lattices: position - 1/2
-    const float hx = ox - 0.5f, hy = oy - 0.5f;
+    const float hx = __fsub_rn(ox, 0.5f), hy = __fsub_rn(oy, 0.5f);
     const int ih = hx < 0.f ? i - 1 : i;
     const int jh = hy < 0.f ? j - 1 : j;
-    const float fx = hx < 0.f ? hx + 1.f : hx;
-    const float fy = hy < 0.f ? hy + 1.f : hy;
-    const float wx0 = 1.f - ox, wx1 = ox, wy0 = 1.f - oy, wy1 = oy;
-    const float hx0 = 1.f - fx, hx1 = fx, hy0 = 1.f - fy, hy1 = fy;
+    const float fx = hx < 0.f ? __fadd_rn(hx, 1.f) : hx;
+    const float fy = hy < 0.f ? __fadd_rn(hy, 1.f) : hy;
+    const float wx0 = __fsub_rn(1.f, ox), wx1 = ox, wy0 = __fsub_rn(1.f, oy), wy1 = oy;
+    const float hx0 = __fsub_rn(1.f, fx), hx1 = fx, hy0 = __fsub_rn(1.f, fy), hy1 = fy;
     // Ex (1/2, 0), By (1/2, 0)
-    EB[0] = wy0 * (hx0 * F(0, ih, j) + hx1 * F(0, ih + 1, j)) + wy1 * (hx0 * F(0, ih, j + 1) + hx1 * F(0, ih + 1, j + 1));
-    EB[4] = wy0 * (hx0 * F(4, ih, j) + hx1 * F(4, ih + 1, j)) + wy1 * (hx0 * F(4, ih, j + 1) + hx1 * F(4, ih + 1, j + 1));
+    EB[0] = lerp2(wy0, wy1, lerp2(hx0, hx1, F(0, ih, j), F(0, ih + 1, j)), lerp2(hx0, hx1, F(0, ih, j + 1), F(0, ih + 1, j + 1)));
+    EB[4] = lerp2(wy0, wy1, lerp2(hx0, hx1, F(4, ih, j), F(4, ih + 1, j)), lerp2(hx0, hx1, F(4, ih, j + 1), F(4, ih + 1, j + 1)));
     // Ey (0, 1/2), Bx (0, 1/2)
-    EB[1] = hy0 * (wx0 * F(1, i, jh) + wx1 * F(1, i + 1, jh)) + hy1 * (wx0 * F(1, i, jh + 1) + wx1 * F(1, i + 1, jh + 1));
-    EB[3] = hy0 * (wx0 * F(3, i, jh) + wx1 * F(3, i + 1, jh)) + hy1 * (wx0 * F(3, i, jh + 1) + wx1 * F(3, i + 1, jh + 1));
+    EB[1] = lerp2(hy0, hy1, lerp2(wx0, wx1, F(1, i, jh), F(1, i + 1, jh)), lerp2(wx0, wx1, F(1, i, jh + 1), F(1, i + 1, jh + 1)));
+    EB[3] = lerp2(hy0, hy1, lerp2(wx0, wx1, F(3, i, jh), F(3, i + 1, jh)), lerp2(wx0, wx1, F(3, i, jh + 1), F(3, i + 1, jh + 1)));
     // Ez (0, 0)
-    EB[2] = wy0 * (wx0 * F(2, i, j) + wx1 * F(2, i + 1, j)) + wy1 * (wx0 * F(2, i, j + 1) + wx1 * F(2, i + 1, j + 1));
+    EB[2] = lerp2(wy0, wy1, lerp2(wx0, wx1, F(2, i, j), F(2, i + 1, j)), lerp2(wx0, wx1, F(2, i, j + 1), F(2, i + 1, j + 1)));
     // Bz (1/2, 1/2)
-    EB[5] = hy0 * (hx0 * F(5, ih, jh) + hx1 * F(5, ih + 1, jh)) + hy1 * (hx0 * F(5, ih, jh + 1) + hx1 * F(5, ih + 1, jh + 1));
+    EB[5] = lerp2(hy0, hy1, lerp2(hx0, hx1, F(5, ih, jh), F(5, ih + 1, jh)), lerp2(hx0, hx1, F(5, ih, jh + 1), F(5, ih + 1, jh + 1)));
 }
 
-// Relativistic Boris rotation u^{n-1/2} -> u^{n+1/2}; h = q dt / (2 m).
+// Relativistic Boris rotation u^{n-1/2} -> u^{n+1/2}; h = q dt / (2 m).  Explicit roundings
+// keep every particle's update independent of which code path the compiler emits.
 __device__ __forceinline__ void boris(float h, const float EB[6], float& ux, float& uy, float& uz) {
-    const float umx = ux + h * EB[0], umy = uy + h * EB[1], umz = uz + h * EB[2];
-    const float ig = rsqrtf(1.f + umx * umx + umy * umy + umz * umz);
-    const float tx = h * EB[3] * ig, ty = h * EB[4] * ig, tz = h * EB[5] * ig;
-    const float sf = __fdividef(2.f, 1.f + tx * tx + ty * ty + tz * tz);
-    const float upx = umx + (umy * tz - umz * ty);
-    const float upy = umy + (umz * tx - umx * tz);
-    const float upz = umz + (umx * ty - umy * tx);
-    const float sx = sf * tx, sy = sf * ty, sz = sf * tz;
-    ux = umx + (upy * sz - upz * sy) + h * EB[0];
-    uy = umy + (upz * sx - upx * sz) + h * EB[1];
-    uz = umz + (upx * sy - upy * sx) + h * EB[2];
+    const float umx = __fmaf_rn(h, EB[0], ux), umy = __fmaf_rn(h, EB[1], uy), umz = __fmaf_rn(h, EB[2], uz);
+    const float g2 = __fmaf_rn(umz, umz, __fmaf_rn(umy, umy, __fmaf_rn(umx, umx, 1.f)));
+    const float ig = rsqrtf(g2);
+    const float hg = __fmul_rn(h, ig);
+    const float tx = __fmul_rn(hg, EB[3]), ty = __fmul_rn(hg, EB[4]), tz = __fmul_rn(hg, EB[5]);
+    const float t2 = __fmaf_rn(tz, tz, __fmaf_rn(ty, ty, __fmaf_rn(tx, tx, 1.f)));
+    const float sf = __fdividef(2.f, t2);
+    const float upx = __fadd_rn(umx, __fmaf_rn(umy, tz, -__fmul_rn(umz, ty)));
+    const float upy = __fadd_rn(umy, __fmaf_rn(umz, tx, -__fmul_rn(umx, tz)));
+    const float upz = __fadd_rn(umz, __fmaf_rn(umx, ty, -__fmul_rn(umy, tx)));
+    const float sx = __fmul_rn(sf, tx), sy = __fmul_rn(sf, ty), sz = __fmul_rn(sf, tz);
+    ux = __fmaf_rn(h, EB[0], __fadd_rn(umx, __fmaf_rn(upy, sz, -__fmul_rn(upz, sy))));
+    uy = __fmaf_rn(h, EB[1], __fadd_rn(umy, __fmaf_rn(upz, sx, -__fmul_rn(upx, sz))));
+    uz = __fmaf_rn(h, EB[2], __fadd_rn(umz, __fmaf_rn(upx, sy, -__fmul_rn(upy, sx))));
 }
 
 // Apply the up-to-21 current terms of one particle; `at(c, i, j)` returns the accumulator.
 template <class At>
 __device__ __forceinline__ void deposit_terms(const At& at, const SpeciesParams& P, int bi, int bj,
-                                              const Win& wx, const Win& wy, float vz) {
+                                              const Win& wx, const Win& wy, float zf) {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const float a = P.jx * wx.C[k];
+        const float a = __fmul_rn(P.jx, wx.C[k]);
 #pragma unroll
         for (int l = 0; l < 3; ++l) sadd(at(0, bi + k, bj + l), round_small(a, wy.A[l]));
     }
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
-        const float a = P.jy * wy.C[l];
+        const float a = __fmul_rn(P.jy, wy.C[l]);
 #pragma unroll
         for (int k = 0; k < 3; ++k) sadd(at(1, bi + k, bj + l), round_small(a, wx.A[k]));
     }
-    const float zf = P.jz * vz;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-        const float p = wy.S0[l] * (1.f / 3.f) + wy.S1[l] * (1.f / 6.f);
-        const float q = wy.S0[l] * (1.f / 6.f) + wy.S1[l] * (1.f / 3.f);
+        const float p = zp(wy.S0[l], wy.S1[l]), q = zq(wy.S0[l], wy.S1[l]);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) sadd(at(2, bi + k, bj + l), round_small(zf, wx.S0[k] * p + wx.S1[k] * q));
+        for (int k = 0; k < 3; ++k) sadd(at(2, bi + k, bj + l), round_small(zf, zw(wx.S0[k], wx.S1[k], p, q)));
     }
 }
 
@@ -286,11 +307,13 @@ __global__ void __launch_bounds__(NT) push2d_kernel(const Args a) {
                     const size_t g = (size_t)cy * nx + cx;
                     b0 = Rp->ubar[0][g]; b1 = Rp->ubar[1][g]; b2 = Rp->ubar[2][g];
                 }
-                ux -= P.dragf * b0; uy -= P.dragf * b1; uz -= P.dragf * b2;
+                ux = __fmaf_rn(-P.dragf, b0, ux);
+                uy = __fmaf_rn(-P.dragf, b1, uy);
+                uz = __fmaf_rn(-P.dragf, b2, uz);
             }
-            const float ig = rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
-            const float rx = ox + ux * ig * Rp->dtdx;
-            const float ry = oy + uy * ig * Rp->dtdy;
+            const float ig = rsqrtf(__fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmaf_rn(ux, ux, 1.f))));
+            const float rx = __fmaf_rn(__fmul_rn(ux, ig), Rp->dtdx, ox);
+            const float ry = __fmaf_rn(__fmul_rn(uy, ig), Rp->dtdy, oy);
             const bool bad = act && !(rx > -1.f && rx < 2.f && ry > -1.f && ry < 2.f);
             if (bad) atomicOr(&a.ctl->err, ERR_BADPART);
             const bool live = act && !bad;
@@ -301,7 +324,7 @@ __global__ void __launch_bounds__(NT) push2d_kernel(const Args a) {
             else if (rx >= 1.f) { nox = rx - 1.f; sx = 1; }
             if (ry < 0.f) { noy = ry + 1.f; sy = -1; if (noy >= 1.f) { noy = 0.f; sy = 0; } }
             else if (ry >= 1.f) { noy = ry - 1.f; sy = 1; }
-            const float vz = uz * ig;
+            const float vz = __fmul_rn(uz, ig);
 
             if (diag && live) {
                 const float mx = 0.5f * (u0x + ux), my = 0.5f * (u0y + uy), mz = 0.5f * (u0z + uz);
@@ -320,24 +343,21 @@ __global__ void __launch_bounds__(NT) push2d_kernel(const Args a) {
             const int ref = __shfl_sync(FULL, lc, leader);
             bool fast = live && inreg && sx == 0 && sy == 0 && lc == ref && small_u;
             const unsigned fm = __ballot_sync(FULL, fast);
+            const Win wx = window(ox, sx, nox), wy = window(oy, sy, noy);
+            const float zf = __fmul_rn(P.jz, vz);
             if (fm) {
                 int v[16];
-                const float ay0 = 1.f - 0.5f * (oy + noy), ay1 = 0.5f * (oy + noy);
-                const float ax0 = 1.f - 0.5f * (ox + nox), ax1 = 0.5f * (ox + nox);
-                const float jxa = P.jx * (ox - nox), jya = P.jy * (oy - noy);
-                const float zf = P.jz * vz;
-                const float p0 = (1.f - oy) * (1.f / 3.f) + (1.f - noy) * (1.f / 6.f);
-                const float q0 = (1.f - oy) * (1.f / 6.f) + (1.f - noy) * (1.f / 3.f);
-                const float p1 = oy * (1.f / 3.f) + noy * (1.f / 6.f);
-                const float q1 = oy * (1.f / 6.f) + noy * (1.f / 3.f);
-                v[0] = round_small(jxa, ay0);                                  // Jx (cx+1/2, cy)
-                v[1] = round_small(jxa, ay1);                                  // Jx (cx+1/2, cy+1)
-                v[2] = round_small(jya, ax0);                                  // Jy (cx, cy+1/2)
-                v[3] = round_small(jya, ax1);                                  // Jy (cx+1, cy+1/2)
-                v[4] = round_small(zf, (1.f - ox) * p0 + (1.f - nox) * q0);    // Jz (cx, cy)
-                v[5] = round_small(zf, ox * p0 + nox * q0);                    // Jz (cx+1, cy)
-                v[6] = round_small(zf, (1.f - ox) * p1 + (1.f - nox) * q1);    // Jz (cx, cy+1)
-                v[7] = round_small(zf, ox * p1 + nox * q1);                    // Jz (cx+1, cy+1)
+                const float jxa = __fmul_rn(P.jx, wx.C[0]), jya = __fmul_rn(P.jy, wy.C[0]);
+                const float p0 = zp(wy.S0[0], wy.S1[0]), q0 = zq(wy.S0[0], wy.S1[0]);
+                const float p1 = zp(wy.S0[1], wy.S1[1]), q1 = zq(wy.S0[1], wy.S1[1]);
+                v[0] = round_small(jxa, wy.A[0]);                                  // Jx (cx+1/2, cy)
+                v[1] = round_small(jxa, wy.A[1]);                                  // Jx (cx+1/2, cy+1)
+                v[2] = round_small(jya, wx.A[0]);                                  // Jy (cx, cy+1/2)
+                v[3] = round_small(jya, wx.A[1]);                                  // Jy (cx+1, cy+1/2)
+                v[4] = round_small(zf, zw(wx.S0[0], wx.S1[0], p0, q0));            // Jz (cx, cy)
+                v[5] = round_small(zf, zw(wx.S0[1], wx.S1[1], p0, q0));            // Jz (cx+1, cy)
+                v[6] = round_small(zf, zw(wx.S0[0], wx.S1[0], p1, q1));            // Jz (cx, cy+1)
+                v[7] = round_small(zf, zw(wx.S0[1], wx.S1[1], p1, q1));            // Jz (cx+1, cy+1)
                 const float ms = 1048576.0f;   // 2^20
                 v[8] = P.drag ? __float2int_rn(ux * ms) : 0;
                 v[9] = P.drag ? __float2int_rn(uy * ms) : 0;
@@ -373,9 +393,8 @@ __global__ void __launch_bounds__(NT) push2d_kernel(const Args a) {
             }
 
             if (live && !fast) {
-                const Win wx = window(ox, sx, nox), wy = window(oy, sy, noy);
                 if (inreg) {
-                    deposit_terms(sh_at, P, ix + wx.off, iy + wy.off, wx, wy, vz);
+                    deposit_terms(sh_at, P, ix + wx.off, iy + wy.off, wx, wy, zf);
                     if (P.drag) {
                         const int n1 = (iy + sy) * RX + (ix + sx);
                         const float ms = 1048576.0f;
@@ -385,7 +404,7 @@ __global__ void __launch_bounds__(NT) push2d_kernel(const Args a) {
                         atomicAdd(&sm.MC[n1], 1);
                     }
                 } else {
-                    deposit_terms(gl_at, P, cx + wx.off, cy + wy.off, wx, wy, vz);
+                    deposit_terms(gl_at, P, cx + wx.off, cy + wy.off, wx, wy, zf);
                     if (P.drag) {
                         const size_t g1 = (size_t)wrapi(cy + sy, ny) * nx + wrapi(cx + sx, nx);
                         const float ms = 1048576.0f;
