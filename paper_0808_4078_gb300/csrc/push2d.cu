@@ -1,22 +1,23 @@
 // push2d.cu -- fused 2D3V particle step: CIC field gather, relativistic Boris push, Krook drag
 // of the return-current electrons (Eq. (3) friction, per-cell mean-momentum relaxation), move
 // with cell carry, and charge-conserving Esirkepov current deposition (CIC), accumulated in
-// int64 fixed point through a shared-memory tile.
+// int64 fixed point.
 //
-// One CTA per (run, tile) of TX x TY cells.  Particles were binned by tile at the last counting
-// sort, so the CTA walks the contiguous range [start[key0], start[key0 + TX*TY]) of each
-// species.  Since then particles may have drifted up to DR cells out of the tile; the shared
-// tile covers the tile plus that drift plus the CIC stencil.  A particle farther out takes the
-// same arithmetic against global memory (global atomics), so results never depend on the sort
-// interval: every current term is rounded to an integer before it is summed, and integer sums
-// are order-independent, so J is bit-reproducible whatever the particle order.
+// One CTA per (run, tile) of 16 x 16 cells, 8 warps.  The counting sort leaves each cell's
+// particles contiguous, so a warp walks whole cells: for cell c it caches the 37 field values
+// any particle of c can touch in registers, and particles still in c that do not leave it this
+// step ("stay" particles, the large majority) are pushed from that cache and accumulate their 8
+// current terms and 4 drag moments in int32 registers; a warp transpose-reduce adds the sums
+// to the shared tile once per cell.  Particles that drifted out of c since the sort, or cross a
+// cell edge in this step, go to a per-warp queue and are processed 32 at a time with per-lane
+// atomics over their 3 x 3 node window (shared tile, or global memory beyond the tile's drift
+// margin).  Every path evaluates the same explicitly-rounded formulas and every current term
+// is an integer before it is summed, so results are bitwise independent of the particle order
+// and of the sort interval.
 //
-// Deposit per particle uses a 3-node window per axis starting at min(old cell, new cell)
-// (a particle moves less than one cell per step).  Warp aggregation: lanes that stay in the
-// warp's reference cell (the common case for cell-sorted particles) touch the same 8 current
-// nodes (and the same drag-moment cell); their integer terms are summed across the warp with a
-// transpose reduce-scatter (15 shuffles for 16 values) and applied with one shared atomic per
-// value.  Other lanes apply their up-to-21 terms individually.
+// Shared accumulators are pairs of 32-bit words (value = hi * 4096 + lo) so that all shared
+// atomics are native 32-bit adds; 64-bit shared atomics are several times slower on this GPU.
+// The tile is added to global int64 J with atomics at the end (halos overlap neighbours).
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -24,19 +25,128 @@ namespace {
 
 constexpr int TX = 16, TY = 16, DR = 2;
 constexpr int RX = TX + 2 * DR + 3, RY = TY + 2 * DR + 3, RN = RX * RY;
-constexpr int NT = 256;
+constexpr int NT = 256, NW = NT / 32, QCAP = 64;
+constexpr int CELLS = TX * TY;
+constexpr int FLUSH_CHUNKS = 8;        // register sums stay below 2^31 (8 x 32 particles)
+constexpr float MOM_SCALE = 1048576.0f;  // 2^20
 constexpr unsigned FULL = 0xffffffffu;
 
-struct __align__(16) Smem {
+struct Smem {
     float F[6][RN];                  // Ex Ey Ez Bx By Bz of the region
-    unsigned long long J[3][RN];     // current accumulator (int64 two's complement)
     float ub[3][RN];                 // previous cell-mean momentum (drag)
-    unsigned long long M[3][RN];     // new drag moments, fixed point 2^20
-    int MC[RN];                      // new drag counts
-    double red[NT / 32][6];
+    unsigned Jlo[3][RN];             // current accumulator, value = Jhi * 4096 + Jlo
+    int Jhi[3][RN];
+    unsigned Mlo[3][RN];             // drag moments (fixed point 2^20), same split
+    int Mhi[3][RN];
+    int MC[RN];                      // drag counts
+    int q[NW][QCAP];                 // per-warp queue of deferred particle indices
+    double red[NW][6];
     unsigned long long kin[4];
 };
 
+// ------------------------------------------------------------------ shared accumulators
+__device__ __forceinline__ void add_split(unsigned* lo, int* hi, long long v) {
+    if (v != 0) {
+        atomicAdd(lo, (unsigned)(v & 4095));
+        const int h = (int)(v >> 12);
+        if (h != 0) atomicAdd(hi, h);
+    }
+}
+
+// ------------------------------------------------------------------ gather
+// CIC weights of an axis for an offset o in [0,1): node lattice (nodes c, c+1) and the
+// half-shifted lattice (points c-1/2, c+1/2, c+3/2, stored at c-1, c, c+1).
+struct W3 {
+    float n[2];
+    float h[3];
+};
+__device__ __forceinline__ W3 weights(float o) {
+    W3 w;
+    const float d = __fsub_rn(o, 0.5f);
+    w.n[0] = __fsub_rn(1.f, o);
+    w.n[1] = o;
+    w.h[0] = fmaxf(-d, 0.f);
+    w.h[1] = __fsub_rn(1.f, fabsf(d));
+    w.h[2] = fmaxf(d, 0.f);
+    return w;
+}
+
+// F(c, dx, dy): component c at offset (dx, dy) from the particle's cell node.
+template <class A>
+__device__ __forceinline__ float row_h(const A& F, const W3& wx, int c, int dy) {
+    return __fmaf_rn(wx.h[2], F(c, 1, dy), __fmaf_rn(wx.h[1], F(c, 0, dy), __fmul_rn(wx.h[0], F(c, -1, dy))));
+}
+template <class A>
+__device__ __forceinline__ float row_n(const A& F, const W3& wx, int c, int dy) {
+    return __fmaf_rn(wx.n[1], F(c, 1, dy), __fmul_rn(wx.n[0], F(c, 0, dy)));
+}
+// Staggering: Ex, By (1/2, 0); Ey, Bx (0, 1/2); Ez (0, 0); Bz (1/2, 1/2).
+template <class A>
+__device__ __forceinline__ void gather(const A& F, const W3& wx, const W3& wy, float EB[6]) {
+    EB[0] = __fmaf_rn(wy.n[1], row_h(F, wx, 0, 1), __fmul_rn(wy.n[0], row_h(F, wx, 0, 0)));
+    EB[4] = __fmaf_rn(wy.n[1], row_h(F, wx, 4, 1), __fmul_rn(wy.n[0], row_h(F, wx, 4, 0)));
+    EB[1] = __fmaf_rn(wy.h[2], row_n(F, wx, 1, 1), __fmaf_rn(wy.h[1], row_n(F, wx, 1, 0), __fmul_rn(wy.h[0], row_n(F, wx, 1, -1))));
+    EB[3] = __fmaf_rn(wy.h[2], row_n(F, wx, 3, 1), __fmaf_rn(wy.h[1], row_n(F, wx, 3, 0), __fmul_rn(wy.h[0], row_n(F, wx, 3, -1))));
+    EB[2] = __fmaf_rn(wy.n[1], row_n(F, wx, 2, 1), __fmul_rn(wy.n[0], row_n(F, wx, 2, 0)));
+    EB[5] = __fmaf_rn(wy.h[2], row_h(F, wx, 5, 1), __fmaf_rn(wy.h[1], row_h(F, wx, 5, 0), __fmul_rn(wy.h[0], row_h(F, wx, 5, -1))));
+}
+
+// The 37 values of one cell, in registers.
+struct CellCache {
+    float ex[2][3], by[2][3];   // [dy 0..1][dx -1..1]
+    float ey[3][2], bx[3][2];   // [dy -1..1][dx 0..1]
+    float ez[2][2];             // [dy 0..1][dx 0..1]
+    float bz[3][3];             // [dy -1..1][dx -1..1]
+    __device__ __forceinline__ float operator()(int c, int dx, int dy) const {
+        switch (c) {
+            case 0: return ex[dy][dx + 1];
+            case 4: return by[dy][dx + 1];
+            case 1: return ey[dy + 1][dx];
+            case 3: return bx[dy + 1][dx];
+            case 2: return ez[dy][dx];
+            default: return bz[dy + 1][dx + 1];
+        }
+    }
+};
+
+struct SharedFields {
+    const Smem* s;
+    int n0;   // region index of the particle's cell node
+    __device__ __forceinline__ float operator()(int c, int dx, int dy) const {
+        return s->F[c][n0 + dy * RX + dx];
+    }
+};
+struct GlobalFields {
+    const RunDev* R;
+    int cx, cy;
+    __device__ __forceinline__ float operator()(int c, int dx, int dy) const {
+        const int gi = wrapi(cx + dx, R->nx), gj = wrapi(cy + dy, R->ny);
+        const float* p = c < 3 ? R->E[c] : R->B[c - 3];
+        return __ldg(p + (size_t)gj * R->nx + gi);
+    }
+};
+
+// ------------------------------------------------------------------ Boris
+// Relativistic Boris rotation u^{n-1/2} -> u^{n+1/2}; h = q dt / (2 m).  Explicit roundings
+// keep every particle's update independent of which code path the compiler emits.
+__device__ __forceinline__ void boris(float h, const float EB[6], float& ux, float& uy, float& uz) {
+    const float umx = __fmaf_rn(h, EB[0], ux), umy = __fmaf_rn(h, EB[1], uy), umz = __fmaf_rn(h, EB[2], uz);
+    const float g2 = __fmaf_rn(umz, umz, __fmaf_rn(umy, umy, __fmaf_rn(umx, umx, 1.f)));
+    const float ig = rsqrtf(g2);
+    const float hg = __fmul_rn(h, ig);
+    const float tx = __fmul_rn(hg, EB[3]), ty = __fmul_rn(hg, EB[4]), tz = __fmul_rn(hg, EB[5]);
+    const float t2 = __fmaf_rn(tz, tz, __fmaf_rn(ty, ty, __fmaf_rn(tx, tx, 1.f)));
+    const float sf = __fdividef(2.f, t2);
+    const float upx = __fadd_rn(umx, __fmaf_rn(umy, tz, -__fmul_rn(umz, ty)));
+    const float upy = __fadd_rn(umy, __fmaf_rn(umz, tx, -__fmul_rn(umx, tz)));
+    const float upz = __fadd_rn(umz, __fmaf_rn(umx, ty, -__fmul_rn(umy, tx)));
+    const float sx = __fmul_rn(sf, tx), sy = __fmul_rn(sf, ty), sz = __fmul_rn(sf, tz);
+    ux = __fmaf_rn(h, EB[0], __fadd_rn(umx, __fmaf_rn(upy, sz, -__fmul_rn(upz, sy))));
+    uy = __fmaf_rn(h, EB[1], __fadd_rn(umy, __fmaf_rn(upz, sx, -__fmul_rn(upx, sz))));
+    uz = __fmaf_rn(h, EB[2], __fadd_rn(umz, __fmaf_rn(upx, sy, -__fmul_rn(upy, sx))));
+}
+
+// ------------------------------------------------------------------ Esirkepov window
 // CIC weights of the 3-node window [b, b+1, b+2] with b = min(old cell, new cell), for the old
 // offset o in [0,1) and the carry c in {-1,0,1} with new offset no in [0,1).
 struct Win {
@@ -71,8 +181,7 @@ __device__ __forceinline__ Win window(float o, int c, float no) {
 }
 
 // Path-averaged shape product of the out-of-plane current,
-// S0x (S0y/3 + S1y/6) + S1x (S0y/6 + S1y/3), with every rounding fixed so that all code
-// paths produce bitwise identical terms.
+// S0x (S0y/3 + S1y/6) + S1x (S0y/6 + S1y/3), with every rounding fixed.
 __device__ __forceinline__ float zp(float s0, float s1) {
     return __fmaf_rn(s1, 1.f / 6.f, __fmul_rn(s0, 1.f / 3.f));
 }
@@ -87,125 +196,212 @@ __device__ __forceinline__ float zw(float s0x, float s1x, float p, float q) {
 __device__ __forceinline__ int transpose_reduce16(int v[16], int lane) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        bool hi = lane & 16;
-        int send = hi ? v[i] : v[i + 8];
-        int keep = hi ? v[i + 8] : v[i];
+        const bool hi = lane & 16;
+        const int send = hi ? v[i] : v[i + 8];
+        const int keep = hi ? v[i + 8] : v[i];
         v[i] = keep + __shfl_xor_sync(FULL, send, 16);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        bool hi = lane & 8;
-        int send = hi ? v[i] : v[i + 4];
-        int keep = hi ? v[i + 4] : v[i];
+        const bool hi = lane & 8;
+        const int send = hi ? v[i] : v[i + 4];
+        const int keep = hi ? v[i + 4] : v[i];
         v[i] = keep + __shfl_xor_sync(FULL, send, 8);
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        bool hi = lane & 4;
-        int send = hi ? v[i] : v[i + 2];
-        int keep = hi ? v[i + 2] : v[i];
+        const bool hi = lane & 4;
+        const int send = hi ? v[i] : v[i + 2];
+        const int keep = hi ? v[i + 2] : v[i];
         v[i] = keep + __shfl_xor_sync(FULL, send, 4);
     }
     {
-        bool hi = lane & 2;
-        int send = hi ? v[0] : v[1];
-        int keep = hi ? v[1] : v[0];
+        const bool hi = lane & 2;
+        const int send = hi ? v[0] : v[1];
+        const int keep = hi ? v[1] : v[0];
         v[0] = keep + __shfl_xor_sync(FULL, send, 2);
     }
     return v[0] + __shfl_xor_sync(FULL, v[0], 1);
 }
 
-__device__ __forceinline__ void sadd(unsigned long long* p, long long v) {
-    if (v != 0) atomicAdd(p, (unsigned long long)v);
-}
-
-// Field access: region (shared) coordinates or global (periodic) coordinates.
-struct SharedFields {
-    const Smem* s;
-    __device__ float operator()(int c, int i, int j) const { return s->F[c][j * RX + i]; }
-};
-struct GlobalFields {
-    const RunDev* R;
-    __device__ float operator()(int c, int i, int j) const {
-        int gi = wrapi(i, R->nx), gj = wrapi(j, R->ny);
-        const float* p = c < 3 ? R->E[c] : R->B[c - 3];
-        return __ldg(p + (size_t)gj * R->nx + gi);
+// Carry a new offset r (relative to the old cell, in (-1, 2)) into [0,1) and the cell step.
+__device__ __forceinline__ void carry(float r, float& no, int& c) {
+    c = 0;
+    no = r;
+    if (r < 0.f) {
+        no = __fadd_rn(r, 1.f);
+        c = -1;
+        if (no >= 1.f) { no = 0.f; c = 0; }
+    } else if (r >= 1.f) {
+        no = __fsub_rn(r, 1.f);
+        c = 1;
     }
+}
+
+struct Pushed {
+    float ux, uy, uz;     // u^{n+1/2}
+    float nox, noy;       // new offsets
+    int sx, sy;           // cell steps
+    float vz;
+    bool bad;
 };
 
-__device__ __forceinline__ float lerp2(float w0, float w1, float a, float b) {
-    return __fmaf_rn(w1, b, __fmul_rn(w0, a));
+template <class A>
+__device__ __forceinline__ Pushed push_one(const A& F, const SpeciesParams& P, const RunDev* Rp,
+                                           float ox, float oy, float ux, float uy, float uz,
+                                           float b0, float b1, float b2) {
+    Pushed r;
+    const W3 wx = weights(ox), wy = weights(oy);
+    float EB[6];
+    gather(F, wx, wy, EB);
+    boris(P.qmdt2, EB, ux, uy, uz);
+    if (P.drag) {
+        ux = __fmaf_rn(-P.dragf, b0, ux);
+        uy = __fmaf_rn(-P.dragf, b1, uy);
+        uz = __fmaf_rn(-P.dragf, b2, uz);
+    }
+    const float ig = rsqrtf(__fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmaf_rn(ux, ux, 1.f))));
+    const float rx = __fmaf_rn(__fmul_rn(ux, ig), Rp->dtdx, ox);
+    const float ry = __fmaf_rn(__fmul_rn(uy, ig), Rp->dtdy, oy);
+    r.bad = !(rx > -1.f && rx < 2.f && ry > -1.f && ry < 2.f);
+    carry(rx, r.nox, r.sx);
+    carry(ry, r.noy, r.sy);
+    r.ux = ux; r.uy = uy; r.uz = uz;
+    r.vz = __fmul_rn(uz, ig);
+    return r;
 }
 
-// CIC gather of the six staggered components at node (i, j) + offsets (ox, oy).  Roundings
-// are explicit so that the shared-memory and global-memory instances agree bitwise.
-template <class Acc>
-__device__ __forceinline__ void gather(const Acc& F, int i, int j, float ox, float oy, float EB[6]) {
-    // half-shifted lattices: position - 1/2
-    const float hx = __fsub_rn(ox, 0.5f), hy = __fsub_rn(oy, 0.5f);
-    const int ih = hx < 0.f ? i - 1 : i;
-    const int jh = hy < 0.f ? j - 1 : j;
-    const float fx = hx < 0.f ? __fadd_rn(hx, 1.f) : hx;
-    const float fy = hy < 0.f ? __fadd_rn(hy, 1.f) : hy;
-    const float wx0 = __fsub_rn(1.f, ox), wx1 = ox, wy0 = __fsub_rn(1.f, oy), wy1 = oy;
-    const float hx0 = __fsub_rn(1.f, fx), hx1 = fx, hy0 = __fsub_rn(1.f, fy), hy1 = fy;
-    // Ex (1/2, 0), By (1/2, 0)
-    EB[0] = lerp2(wy0, wy1, lerp2(hx0, hx1, F(0, ih, j), F(0, ih + 1, j)), lerp2(hx0, hx1, F(0, ih, j + 1), F(0, ih + 1, j + 1)));
-    EB[4] = lerp2(wy0, wy1, lerp2(hx0, hx1, F(4, ih, j), F(4, ih + 1, j)), lerp2(hx0, hx1, F(4, ih, j + 1), F(4, ih + 1, j + 1)));
-    // Ey (0, 1/2), Bx (0, 1/2)
-    EB[1] = lerp2(hy0, hy1, lerp2(wx0, wx1, F(1, i, jh), F(1, i + 1, jh)), lerp2(wx0, wx1, F(1, i, jh + 1), F(1, i + 1, jh + 1)));
-    EB[3] = lerp2(hy0, hy1, lerp2(wx0, wx1, F(3, i, jh), F(3, i + 1, jh)), lerp2(wx0, wx1, F(3, i, jh + 1), F(3, i + 1, jh + 1)));
-    // Ez (0, 0)
-    EB[2] = lerp2(wy0, wy1, lerp2(wx0, wx1, F(2, i, j), F(2, i + 1, j)), lerp2(wx0, wx1, F(2, i, j + 1), F(2, i + 1, j + 1)));
-    // Bz (1/2, 1/2)
-    EB[5] = lerp2(hy0, hy1, lerp2(hx0, hx1, F(5, ih, jh), F(5, ih + 1, jh)), lerp2(hx0, hx1, F(5, ih, jh + 1), F(5, ih + 1, jh + 1)));
+__device__ __forceinline__ void kin_add(long long kacc[4], float w, float u0x, float u0y, float u0z,
+                                        float ux, float uy, float uz) {
+    const float mx = 0.5f * (u0x + ux), my = 0.5f * (u0y + uy), mz = 0.5f * (u0z + uz);
+    const float gmid = sqrtf(1.f + mx * mx + my * my + mz * mz);
+    const float sc = 4294967296.0f;   // 2^32
+    kacc[0] += __float2ll_rn(w * (gmid - 1.f) * sc);
+    kacc[1] += __float2ll_rn(w * mx * sc);
+    kacc[2] += __float2ll_rn(w * my * sc);
+    kacc[3] += __float2ll_rn(w * mz * sc);
 }
 
-// Relativistic Boris rotation u^{n-1/2} -> u^{n+1/2}; h = q dt / (2 m).  Explicit roundings
-// keep every particle's update independent of which code path the compiler emits.
-__device__ __forceinline__ void boris(float h, const float EB[6], float& ux, float& uy, float& uz) {
-    const float umx = __fmaf_rn(h, EB[0], ux), umy = __fmaf_rn(h, EB[1], uy), umz = __fmaf_rn(h, EB[2], uz);
-    const float g2 = __fmaf_rn(umz, umz, __fmaf_rn(umy, umy, __fmaf_rn(umx, umx, 1.f)));
-    const float ig = rsqrtf(g2);
-    const float hg = __fmul_rn(h, ig);
-    const float tx = __fmul_rn(hg, EB[3]), ty = __fmul_rn(hg, EB[4]), tz = __fmul_rn(hg, EB[5]);
-    const float t2 = __fmaf_rn(tz, tz, __fmaf_rn(ty, ty, __fmaf_rn(tx, tx, 1.f)));
-    const float sf = __fdividef(2.f, t2);
-    const float upx = __fadd_rn(umx, __fmaf_rn(umy, tz, -__fmul_rn(umz, ty)));
-    const float upy = __fadd_rn(umy, __fmaf_rn(umz, tx, -__fmul_rn(umx, tz)));
-    const float upz = __fadd_rn(umz, __fmaf_rn(umx, ty, -__fmul_rn(umy, tx)));
-    const float sx = __fmul_rn(sf, tx), sy = __fmul_rn(sf, ty), sz = __fmul_rn(sf, tz);
-    ux = __fmaf_rn(h, EB[0], __fadd_rn(umx, __fmaf_rn(upy, sz, -__fmul_rn(upz, sy))));
-    uy = __fmaf_rn(h, EB[1], __fadd_rn(umy, __fmaf_rn(upz, sx, -__fmul_rn(upx, sz))));
-    uz = __fmaf_rn(h, EB[2], __fadd_rn(umz, __fmaf_rn(upx, sy, -__fmul_rn(upy, sx))));
-}
-
-// Apply the up-to-21 current terms of one particle; `at(c, i, j)` returns the accumulator.
-template <class At>
-__device__ __forceinline__ void deposit_terms(const At& at, const SpeciesParams& P, int bi, int bj,
+// The up-to-21 current terms of one particle, applied with `add(comp, i, j, value)`.
+template <class Add>
+__device__ __forceinline__ void deposit_terms(const Add& add, const SpeciesParams& P, int bi, int bj,
                                               const Win& wx, const Win& wy, float zf) {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const float a = __fmul_rn(P.jx, wx.C[k]);
 #pragma unroll
-        for (int l = 0; l < 3; ++l) sadd(at(0, bi + k, bj + l), round_small(a, wy.A[l]));
+        for (int l = 0; l < 3; ++l) add(0, bi + k, bj + l, round_small(a, wy.A[l]));
     }
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
         const float a = __fmul_rn(P.jy, wy.C[l]);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) sadd(at(1, bi + k, bj + l), round_small(a, wx.A[k]));
+        for (int k = 0; k < 3; ++k) add(1, bi + k, bj + l, round_small(a, wx.A[k]));
     }
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
         const float p = zp(wy.S0[l], wy.S1[l]), q = zq(wy.S0[l], wy.S1[l]);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) sadd(at(2, bi + k, bj + l), round_small(zf, zw(wx.S0[k], wx.S1[k], p, q)));
+        for (int k = 0; k < 3; ++k) add(2, bi + k, bj + l, round_small(zf, zw(wx.S0[k], wx.S1[k], p, q)));
     }
 }
 
-__global__ void __launch_bounds__(NT) push2d_kernel(const Args a) {
-    __shared__ Smem sm;
+// ------------------------------------------------------------------ deferred particles
+// Full step of up to 32 queued particles of species P (one per lane), region or global path.
+__device__ __forceinline__ void drain(Smem& sm, const RunDev* Rp, const SpeciesParams& P,
+                                      const SpeciesBuf& B, int k, int lane, int warp, int x0,
+                                      int y0, bool diag, long long kacc[4], int* err) {
+    if (lane >= k) return;
+    const int nx = Rp->nx, ny = Rp->ny;
+    const int p = sm.q[warp][lane];
+    const int lc = B.cell[p] - Rp->cell_off;
+    const float ox = B.o[0][p], oy = B.o[1][p];
+    const float u0x = B.u[0][p], u0y = B.u[1][p], u0z = B.u[2][p];
+    const int cy = lc / nx, cx = lc - cy * nx;
+    int rxi = cx - x0, ryi = cy - y0;
+    if (rxi < -DR) rxi += nx; else if (rxi >= nx - DR) rxi -= nx;
+    if (ryi < -DR) ryi += ny; else if (ryi >= ny - DR) ryi -= ny;
+    const bool inreg = rxi >= -DR && rxi < TX + DR && ryi >= -DR && ryi < TY + DR;
+    const int ix = rxi + DR + 1, iy = ryi + DR + 1;
+    const int n0 = iy * RX + ix;
+    float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+    if (P.drag) {
+        if (inreg) { b0 = sm.ub[0][n0]; b1 = sm.ub[1][n0]; b2 = sm.ub[2][n0]; }
+        else {
+            const size_t g = (size_t)cy * nx + cx;
+            b0 = Rp->ubar[0][g]; b1 = Rp->ubar[1][g]; b2 = Rp->ubar[2][g];
+        }
+    }
+    Pushed r;
+    if (inreg) r = push_one(SharedFields{&sm, n0}, P, Rp, ox, oy, u0x, u0y, u0z, b0, b1, b2);
+    else r = push_one(GlobalFields{Rp, cx, cy}, P, Rp, ox, oy, u0x, u0y, u0z, b0, b1, b2);
+    if (r.bad) { atomicOr(err, ERR_BADPART); return; }
+    if (diag) kin_add(kacc, P.w, u0x, u0y, u0z, r.ux, r.uy, r.uz);
+    const Win wx = window(ox, r.sx, r.nox), wy = window(oy, r.sy, r.noy);
+    const float zf = __fmul_rn(P.jz, r.vz);
+    if (inreg) {
+        auto add = [&](int c, int i, int j, int v) {
+            if (v != 0) add_split(&sm.Jlo[c][j * RX + i], &sm.Jhi[c][j * RX + i], v);
+        };
+        deposit_terms(add, P, ix + wx.off, iy + wy.off, wx, wy, zf);
+        if (P.drag) {
+            const int n1 = (iy + r.sy) * RX + (ix + r.sx);
+            add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], __float2ll_rn(r.ux * MOM_SCALE));
+            add_split(&sm.Mlo[1][n1], &sm.Mhi[1][n1], __float2ll_rn(r.uy * MOM_SCALE));
+            add_split(&sm.Mlo[2][n1], &sm.Mhi[2][n1], __float2ll_rn(r.uz * MOM_SCALE));
+            atomicAdd(&sm.MC[n1], 1);
+        }
+    } else {
+        auto add = [&](int c, int i, int j, int v) {
+            if (v != 0)
+                atomicAdd((unsigned long long*)&Rp->J[c][(size_t)wrapi(j, ny) * nx + wrapi(i, nx)],
+                          (unsigned long long)(long long)v);
+        };
+        deposit_terms(add, P, cx + wx.off, cy + wy.off, wx, wy, zf);
+        if (P.drag) {
+            const size_t g1 = (size_t)wrapi(cy + r.sy, ny) * nx + wrapi(cx + r.sx, nx);
+            atomicAdd((unsigned long long*)&Rp->msum[0][g1], (unsigned long long)__float2ll_rn(r.ux * MOM_SCALE));
+            atomicAdd((unsigned long long*)&Rp->msum[1][g1], (unsigned long long)__float2ll_rn(r.uy * MOM_SCALE));
+            atomicAdd((unsigned long long*)&Rp->msum[2][g1], (unsigned long long)__float2ll_rn(r.uz * MOM_SCALE));
+            atomicAdd(&Rp->mcnt[g1], 1);
+        }
+    }
+    int ncx = cx + r.sx, ncy = cy + r.sy;
+    ncx = ncx < 0 ? ncx + nx : (ncx >= nx ? ncx - nx : ncx);
+    ncy = ncy < 0 ? ncy + ny : (ncy >= ny ? ncy - ny : ncy);
+    B.cell[p] = Rp->cell_off + ncy * nx + ncx;
+    B.o[0][p] = r.nox; B.o[1][p] = r.noy;
+    B.u[0][p] = r.ux; B.u[1][p] = r.uy; B.u[2][p] = r.uz;
+}
+
+// Register sums of "stay" particles of the cell at region node n0 -> shared tile.
+__device__ __forceinline__ void flush_acc(Smem& sm, int acc[12], int n0, int lane) {
+    int v[16];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) { v[i] = acc[i]; acc[i] = 0; }
+    v[12] = v[13] = v[14] = v[15] = 0;
+    const int tot = transpose_reduce16(v, lane);
+    const int idx = lane >> 1;
+    if ((lane & 1) || tot == 0 || idx > 11) return;
+    if (idx == 11) { atomicAdd(&sm.MC[n0], tot); return; }
+    // node offsets: Jx (0,0),(0,1); Jy (0,0),(1,0); Jz (0,0),(1,0),(0,1),(1,1); moments (0,0)
+    const int off = (idx == 1 || idx == 6) ? RX : (idx == 3 || idx == 5) ? 1 : (idx == 7) ? RX + 1 : 0;
+    unsigned* lo;
+    int* hi;
+    if (idx < 8) {
+        const int c = idx < 2 ? 0 : (idx < 4 ? 1 : 2);
+        lo = &sm.Jlo[c][n0 + off];
+        hi = &sm.Jhi[c][n0 + off];
+    } else {
+        lo = &sm.Mlo[idx - 8][n0];
+        hi = &sm.Mhi[idx - 8][n0];
+    }
+    add_split(lo, hi, tot);
+}
+
+__global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const int2 wk = a.work[blockIdx.x];
     const RunDev* Rp = &a.runs[wk.x];
     const int nx = Rp->nx, ny = Rp->ny;
@@ -216,6 +412,7 @@ __global__ void __launch_bounds__(NT) push2d_kernel(const Args a) {
     const bool diag = a.diag_interval > 0 && (step % a.diag_interval) == 0;
     const bool anydrag = Rp->msum[0] != nullptr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
 
     for (int i = tid; i < RN; i += NT) {
         const int ry = i / RX, rx = i - ry * RX;
@@ -224,13 +421,15 @@ __global__ void __launch_bounds__(NT) push2d_kernel(const Args a) {
         for (int c = 0; c < 3; ++c) {
             sm.F[c][i] = Rp->E[c][g];
             sm.F[3 + c][i] = Rp->B[c][g];
-            sm.J[c][i] = 0ull;
+            sm.Jlo[c][i] = 0u;
+            sm.Jhi[c][i] = 0;
         }
         if (anydrag) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 sm.ub[c][i] = Rp->ubar[c][g];
-                sm.M[c][i] = 0ull;
+                sm.Mlo[c][i] = 0u;
+                sm.Mhi[c][i] = 0;
             }
             sm.MC[i] = 0;
         }
@@ -257,174 +456,120 @@ __global__ void __launch_bounds__(NT) push2d_kernel(const Args a) {
         __syncthreads();
         if (tid < 6) {
             double s = 0.0;
-            for (int w = 0; w < NT / 32; ++w) s += sm.red[w][tid];
+            for (int w = 0; w < NW; ++w) s += sm.red[w][tid];
             a.partials[(size_t)blockIdx.x * 8 + tid] = s;
         }
     }
-
-    const SharedFields SF{&sm};
-    const GlobalFields GF{Rp};
-    auto sh_at = [&](int c, int i, int j) { return &sm.J[c][j * RX + i]; };
-    auto gl_at = [&](int c, int i, int j) {
-        return (unsigned long long*)&Rp->J[c][(size_t)wrapi(j, ny) * nx + wrapi(i, nx)];
-    };
 
     for (int s = 0; s < a.nspecies; ++s) {
         const SpeciesParams P = Rp->sp[s];
         if (!P.active) continue;
         const SpeciesBuf B = a.buf[s][a.ctl->parity[s]];
-        const int key0 = Rp->cell_off + tile * (TX * TY);
-        const int beg = a.start[s][key0], end = a.start[s][key0 + TX * TY];
+        const int key0 = Rp->cell_off + tile * CELLS;
+        const int* __restrict__ start = a.start[s];
         long long kacc[4] = {0, 0, 0, 0};
+        int qn = 0;
 
-        for (int base = beg + warp * 32; base < end; base += NT) {
-            const int p = base + lane;
-            const bool act = p < end;
-            int lc = 0;
-            float ox = 0.f, oy = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
-            if (act) {
-                lc = B.cell[p] - Rp->cell_off;
-                ox = B.o[0][p]; oy = B.o[1][p];
-                ux = B.u[0][p]; uy = B.u[1][p]; uz = B.u[2][p];
-            }
-            const int cy = lc / nx, cx = lc - cy * nx;
-            const int rxi = wrapi(cx - x0 + DR, nx) - DR;
-            const int ryi = wrapi(cy - y0 + DR, ny) - DR;
-            const bool inreg = rxi < TX + DR && ryi < TY + DR;
-            const int ix = rxi + DR + 1, iy = ryi + DR + 1;   // shared node index of (cx, cy)
-
-            float EB[6];
-            if (inreg) gather(SF, ix, iy, ox, oy, EB);
-            else gather(GF, cx, cy, ox, oy, EB);
-            const float u0x = ux, u0y = uy, u0z = uz;
-            boris(P.qmdt2, EB, ux, uy, uz);
-            if (P.drag) {
-                float b0, b1, b2;
-                if (inreg) {
-                    const int si = iy * RX + ix;
-                    b0 = sm.ub[0][si]; b1 = sm.ub[1][si]; b2 = sm.ub[2][si];
-                } else {
-                    const size_t g = (size_t)cy * nx + cx;
-                    b0 = Rp->ubar[0][g]; b1 = Rp->ubar[1][g]; b2 = Rp->ubar[2][g];
-                }
-                ux = __fmaf_rn(-P.dragf, b0, ux);
-                uy = __fmaf_rn(-P.dragf, b1, uy);
-                uz = __fmaf_rn(-P.dragf, b2, uz);
-            }
-            const float ig = rsqrtf(__fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmaf_rn(ux, ux, 1.f))));
-            const float rx = __fmaf_rn(__fmul_rn(ux, ig), Rp->dtdx, ox);
-            const float ry = __fmaf_rn(__fmul_rn(uy, ig), Rp->dtdy, oy);
-            const bool bad = act && !(rx > -1.f && rx < 2.f && ry > -1.f && ry < 2.f);
-            if (bad) atomicOr(&a.ctl->err, ERR_BADPART);
-            const bool live = act && !bad;
-
-            int sx = 0, sy = 0;
-            float nox = rx, noy = ry;
-            if (rx < 0.f) { nox = rx + 1.f; sx = -1; if (nox >= 1.f) { nox = 0.f; sx = 0; } }
-            else if (rx >= 1.f) { nox = rx - 1.f; sx = 1; }
-            if (ry < 0.f) { noy = ry + 1.f; sy = -1; if (noy >= 1.f) { noy = 0.f; sy = 0; } }
-            else if (ry >= 1.f) { noy = ry - 1.f; sy = 1; }
-            const float vz = __fmul_rn(uz, ig);
-
-            if (diag && live) {
-                const float mx = 0.5f * (u0x + ux), my = 0.5f * (u0y + uy), mz = 0.5f * (u0z + uz);
-                const float gmid = sqrtf(1.f + mx * mx + my * my + mz * mz);
-                const float sc = 4294967296.0f;   // 2^32
-                kacc[0] += __float2ll_rn(P.w * (gmid - 1.f) * sc);
-                kacc[1] += __float2ll_rn(P.w * mx * sc);
-                kacc[2] += __float2ll_rn(P.w * my * sc);
-                kacc[3] += __float2ll_rn(P.w * mz * sc);
-            }
-
-            // ---- warp-aggregated deposit for lanes staying in the reference cell
-            const bool small_u = !P.drag || (fabsf(ux) < 32.f && fabsf(uy) < 32.f && fabsf(uz) < 32.f);
-            const unsigned am = __ballot_sync(FULL, act);
-            const int leader = am ? __ffs(am) - 1 : 0;
-            const int ref = __shfl_sync(FULL, lc, leader);
-            bool fast = live && inreg && sx == 0 && sy == 0 && lc == ref && small_u;
-            const unsigned fm = __ballot_sync(FULL, fast);
-            const Win wx = window(ox, sx, nox), wy = window(oy, sy, noy);
-            const float zf = __fmul_rn(P.jz, vz);
-            if (fm) {
-                int v[16];
-                const float jxa = __fmul_rn(P.jx, wx.C[0]), jya = __fmul_rn(P.jy, wy.C[0]);
-                const float p0 = zp(wy.S0[0], wy.S1[0]), q0 = zq(wy.S0[0], wy.S1[0]);
-                const float p1 = zp(wy.S0[1], wy.S1[1]), q1 = zq(wy.S0[1], wy.S1[1]);
-                v[0] = round_small(jxa, wy.A[0]);                                  // Jx (cx+1/2, cy)
-                v[1] = round_small(jxa, wy.A[1]);                                  // Jx (cx+1/2, cy+1)
-                v[2] = round_small(jya, wx.A[0]);                                  // Jy (cx, cy+1/2)
-                v[3] = round_small(jya, wx.A[1]);                                  // Jy (cx+1, cy+1/2)
-                v[4] = round_small(zf, zw(wx.S0[0], wx.S1[0], p0, q0));            // Jz (cx, cy)
-                v[5] = round_small(zf, zw(wx.S0[1], wx.S1[1], p0, q0));            // Jz (cx+1, cy)
-                v[6] = round_small(zf, zw(wx.S0[0], wx.S1[0], p1, q1));            // Jz (cx, cy+1)
-                v[7] = round_small(zf, zw(wx.S0[1], wx.S1[1], p1, q1));            // Jz (cx+1, cy+1)
-                const float ms = 1048576.0f;   // 2^20
-                v[8] = P.drag ? __float2int_rn(ux * ms) : 0;
-                v[9] = P.drag ? __float2int_rn(uy * ms) : 0;
-                v[10] = P.drag ? __float2int_rn(uz * ms) : 0;
-                v[11] = P.drag ? 1 : 0;
-                v[12] = v[13] = v[14] = v[15] = 0;
-                if (!fast) {
+        for (int ci = warp; ci < CELLS; ci += NW) {
+            const int cs = start[key0 + ci], ce = start[key0 + ci + 1];
+            if (cs == ce) continue;
+            const int lx = ci % TX, ly = ci / TX;
+            const int gcell = Rp->cell_off + (y0 + ly) * nx + (x0 + lx);
+            const int ix = lx + DR + 1, iy = ly + DR + 1;
+            const int n0 = iy * RX + ix;
+            CellCache cc;
 #pragma unroll
-                    for (int k = 0; k < 12; ++k) v[k] = 0;
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    cc.ex[b][d] = sm.F[0][n0 + b * RX + d - 1];
+                    cc.by[b][d] = sm.F[4][n0 + b * RX + d - 1];
                 }
-                const int tot = transpose_reduce16(v, lane);
-                const int fl = __ffs(fm) - 1;
-                const int rix = __shfl_sync(FULL, ix, fl), riy = __shfl_sync(FULL, iy, fl);
-                const int idx = lane >> 1;
-                if (!(lane & 1) && tot != 0) {
-                    const int n0 = riy * RX + rix;
-                    switch (idx) {
-                        case 0: atomicAdd(&sm.J[0][n0], (unsigned long long)(long long)tot); break;
-                        case 1: atomicAdd(&sm.J[0][n0 + RX], (unsigned long long)(long long)tot); break;
-                        case 2: atomicAdd(&sm.J[1][n0], (unsigned long long)(long long)tot); break;
-                        case 3: atomicAdd(&sm.J[1][n0 + 1], (unsigned long long)(long long)tot); break;
-                        case 4: atomicAdd(&sm.J[2][n0], (unsigned long long)(long long)tot); break;
-                        case 5: atomicAdd(&sm.J[2][n0 + 1], (unsigned long long)(long long)tot); break;
-                        case 6: atomicAdd(&sm.J[2][n0 + RX], (unsigned long long)(long long)tot); break;
-                        case 7: atomicAdd(&sm.J[2][n0 + RX + 1], (unsigned long long)(long long)tot); break;
-                        case 8: atomicAdd(&sm.M[0][n0], (unsigned long long)(long long)tot); break;
-                        case 9: atomicAdd(&sm.M[1][n0], (unsigned long long)(long long)tot); break;
-                        case 10: atomicAdd(&sm.M[2][n0], (unsigned long long)(long long)tot); break;
-                        case 11: atomicAdd(&sm.MC[n0], tot); break;
-                        default: break;
-                    }
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int d = 0; d < 2; ++d) {
+                    cc.ey[b][d] = sm.F[1][n0 + (b - 1) * RX + d];
+                    cc.bx[b][d] = sm.F[3][n0 + (b - 1) * RX + d];
                 }
-            }
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int d = 0; d < 2; ++d) cc.ez[b][d] = sm.F[2][n0 + b * RX + d];
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) cc.bz[b][d] = sm.F[5][n0 + (b - 1) * RX + d - 1];
+            float ub0 = 0.f, ub1 = 0.f, ub2 = 0.f;
+            if (P.drag) { ub0 = sm.ub[0][n0]; ub1 = sm.ub[1][n0]; ub2 = sm.ub[2][n0]; }
 
-            if (live && !fast) {
-                if (inreg) {
-                    deposit_terms(sh_at, P, ix + wx.off, iy + wy.off, wx, wy, zf);
+            int acc[12];
+#pragma unroll
+            for (int i = 0; i < 12; ++i) acc[i] = 0;
+            int nchunk = 0;
+            for (int base = cs; base < ce; base += 32) {
+                const int p = base + lane;
+                const bool act = p < ce;
+                int cell = -1;
+                float ox = 0.f, oy = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
+                if (act) {
+                    cell = B.cell[p];
+                    ox = B.o[0][p]; oy = B.o[1][p];
+                    ux = B.u[0][p]; uy = B.u[1][p]; uz = B.u[2][p];
+                }
+                const bool here = act && cell == gcell;
+                const Pushed r = push_one(cc, P, Rp, ox, oy, ux, uy, uz, ub0, ub1, ub2);
+                const bool small_u = !P.drag || (fabsf(r.ux) < 4.f && fabsf(r.uy) < 4.f && fabsf(r.uz) < 4.f);
+                const bool stay = here && !r.bad && r.sx == 0 && r.sy == 0 && small_u;
+                if (stay) {
+                    const Win wx = window(ox, 0, r.nox), wy = window(oy, 0, r.noy);
+                    const float zf = __fmul_rn(P.jz, r.vz);
+                    const float jxa = __fmul_rn(P.jx, wx.C[0]), jya = __fmul_rn(P.jy, wy.C[0]);
+                    const float p0 = zp(wy.S0[0], wy.S1[0]), q0 = zq(wy.S0[0], wy.S1[0]);
+                    const float p1 = zp(wy.S0[1], wy.S1[1]), q1 = zq(wy.S0[1], wy.S1[1]);
+                    acc[0] += round_small(jxa, wy.A[0]);                          // Jx (c+1/2, c)
+                    acc[1] += round_small(jxa, wy.A[1]);                          // Jx (c+1/2, c+1)
+                    acc[2] += round_small(jya, wx.A[0]);                          // Jy (c, c+1/2)
+                    acc[3] += round_small(jya, wx.A[1]);                          // Jy (c+1, c+1/2)
+                    acc[4] += round_small(zf, zw(wx.S0[0], wx.S1[0], p0, q0));    // Jz (c, c)
+                    acc[5] += round_small(zf, zw(wx.S0[1], wx.S1[1], p0, q0));    // Jz (c+1, c)
+                    acc[6] += round_small(zf, zw(wx.S0[0], wx.S1[0], p1, q1));    // Jz (c, c+1)
+                    acc[7] += round_small(zf, zw(wx.S0[1], wx.S1[1], p1, q1));    // Jz (c+1, c+1)
                     if (P.drag) {
-                        const int n1 = (iy + sy) * RX + (ix + sx);
-                        const float ms = 1048576.0f;
-                        sadd(&sm.M[0][n1], __float2ll_rn(ux * ms));
-                        sadd(&sm.M[1][n1], __float2ll_rn(uy * ms));
-                        sadd(&sm.M[2][n1], __float2ll_rn(uz * ms));
-                        atomicAdd(&sm.MC[n1], 1);
+                        acc[8] += __float2int_rn(r.ux * MOM_SCALE);
+                        acc[9] += __float2int_rn(r.uy * MOM_SCALE);
+                        acc[10] += __float2int_rn(r.uz * MOM_SCALE);
+                        acc[11] += 1;
                     }
-                } else {
-                    deposit_terms(gl_at, P, cx + wx.off, cy + wy.off, wx, wy, zf);
-                    if (P.drag) {
-                        const size_t g1 = (size_t)wrapi(cy + sy, ny) * nx + wrapi(cx + sx, nx);
-                        const float ms = 1048576.0f;
-                        sadd((unsigned long long*)&Rp->msum[0][g1], __float2ll_rn(ux * ms));
-                        sadd((unsigned long long*)&Rp->msum[1][g1], __float2ll_rn(uy * ms));
-                        sadd((unsigned long long*)&Rp->msum[2][g1], __float2ll_rn(uz * ms));
-                        atomicAdd(&Rp->mcnt[g1], 1);
-                    }
+                    if (diag) kin_add(kacc, P.w, ux, uy, uz, r.ux, r.uy, r.uz);
+                    B.o[0][p] = r.nox; B.o[1][p] = r.noy;
+                    B.u[0][p] = r.ux; B.u[1][p] = r.uy; B.u[2][p] = r.uz;
+                }
+                if (here && r.bad) atomicOr(&a.ctl->err, ERR_BADPART);
+                const bool defer = act && !stay && !(here && r.bad);
+                const unsigned dm = __ballot_sync(FULL, defer);
+                if (defer) sm.q[warp][qn + __popc(dm & lt)] = p;
+                qn += __popc(dm);
+                __syncwarp();
+                if (qn >= 32) {
+                    drain(sm, Rp, P, B, 32, lane, warp, x0, y0, diag, kacc, &a.ctl->err);
+                    __syncwarp();
+                    const int rest = qn - 32;
+                    const int moved = lane < rest ? sm.q[warp][32 + lane] : 0;
+                    __syncwarp();
+                    if (lane < rest) sm.q[warp][lane] = moved;
+                    __syncwarp();
+                    qn = rest;
+                }
+                if (++nchunk == FLUSH_CHUNKS) {
+                    flush_acc(sm, acc, n0, lane);
+                    nchunk = 0;
                 }
             }
-
-            if (live) {
-                int ncx = cx + sx, ncy = cy + sy;
-                ncx = ncx < 0 ? ncx + nx : (ncx >= nx ? ncx - nx : ncx);
-                ncy = ncy < 0 ? ncy + ny : (ncy >= ny ? ncy - ny : ncy);
-                B.cell[p] = Rp->cell_off + ncy * nx + ncx;
-                B.o[0][p] = nox; B.o[1][p] = noy;
-                B.u[0][p] = ux; B.u[1][p] = uy; B.u[2][p] = uz;
-            }
+            if (nchunk) flush_acc(sm, acc, n0, lane);
         }
+        if (qn > 0) drain(sm, Rp, P, B, qn, lane, warp, x0, y0, diag, kacc, &a.ctl->err);
+        __syncwarp();
 
         if (diag) {
 #pragma unroll
@@ -449,14 +594,14 @@ __global__ void __launch_bounds__(NT) push2d_kernel(const Args a) {
         const size_t g = (size_t)wrapi(gy0 + ry, ny) * nx + wrapi(gx0 + rx, nx);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const unsigned long long v = sm.J[c][i];
-            if (v) atomicAdd((unsigned long long*)&Rp->J[c][g], v);
+            const long long v = (long long)sm.Jhi[c][i] * 4096 + (long long)sm.Jlo[c][i];
+            if (v) atomicAdd((unsigned long long*)&Rp->J[c][g], (unsigned long long)v);
         }
         if (anydrag) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const unsigned long long v = sm.M[c][i];
-                if (v) atomicAdd((unsigned long long*)&Rp->msum[c][g], v);
+                const long long v = (long long)sm.Mhi[c][i] * 4096 + (long long)sm.Mlo[c][i];
+                if (v) atomicAdd((unsigned long long*)&Rp->msum[c][g], (unsigned long long)v);
             }
             if (sm.MC[i]) atomicAdd(&Rp->mcnt[g], sm.MC[i]);
         }
@@ -467,7 +612,14 @@ __global__ void __launch_bounds__(NT) push2d_kernel(const Args a) {
 
 cudaError_t launch_push2d(const Args& a, cudaStream_t s) {
     if (a.nwork == 0) return cudaSuccess;
-    push2d_kernel<<<a.nwork, NT, 0, s>>>(a);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(push2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(Smem));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    push2d_kernel<<<a.nwork, NT, sizeof(Smem), s>>>(a);
     return cudaGetLastError();
 }
 
