@@ -17,9 +17,10 @@
  * charge-conserving Esirkepov current deposit, Yee FDTD, periodic boundaries.
  *
  * Units: time 1/w_p, length c/w_p, momentum u = gamma v / c, fields m c w_p / e, density n0,
- * current e n0 c.  Particles are stored as an int32 cell index (x fastest) plus FP32 in-cell
- * offsets in [0, 1); push and gather are FP32; the current is accumulated in int64 fixed point
- * (bit-reproducible); global energy/momentum reductions are FP64.
+ * current e n0 c.  A particle is a cell (x fastest) plus FP32 in-cell offsets in [0, 1) and FP32
+ * momenta; on the device particles are binned per cell (the cell index is implied by the slot)
+ * and re-binned every step; push and gather are FP32; the current is accumulated in int64 fixed
+ * point (bit-reproducible); global energy/momentum reductions are FP64.
  *
  * Conventions
  *   - Every function returns PIC_OK (0) or a negative PIC_E* code; pic_last_error() gives text.
@@ -67,13 +68,17 @@ typedef struct pic_ctx pic_ctx;
 typedef struct pic_config {
     int32_t ndim;              /* 2 (2D3V) or 3 (3D3V) */
     int32_t nx, ny, nz;        /* cells per axis; nz = 1 in 2D; multiples of the tile sizes */
-    double dx, dy, dz, dt;     /* cell sizes (c/w_p) and time step (1/w_p); dt < min(dx,dy,dz) */
+    double dx, dy, dz, dt;     /* cell sizes (c/w_p) and time step (1/w_p); Yee Courant limit */
     int32_t nspecies;          /* 1..PIC_MAX_SPECIES */
-    int64_t capacity[PIC_MAX_SPECIES]; /* particle capacity per species */
-    int32_t sort_interval;     /* steps between counting sorts (>= 1); 0 = default (8) */
+    int64_t capacity[PIC_MAX_SPECIES];      /* particle capacity per species (< 2^31) */
+    int32_t cell_capacity[PIC_MAX_SPECIES]; /* particle slots per cell per species; 0 = automatic
+                                               (4 x the mean per cell, multiple of 32, >= 32);
+                                               must be >= 2 x capacity / cells */
+    int32_t sort_interval;     /* steps between full counting sorts that repack spilled particles
+                                  (particles whose cell's slots were full); 0 = default (8) */
     int32_t diag_interval;     /* steps between diagnostic records; 0 = no diagnostics */
     int32_t diag_capacity;     /* records kept in the device history ring (>= 1 if diag) */
-    int32_t track_ids;         /* 1: carry an int32 id per particle through sorts */
+    int32_t track_ids;         /* 1: carry an int32 id per particle (its load index) */
     int32_t flags;             /* PIC_FLAG_* */
     int32_t tile_x, tile_y, tile_z; /* 0 = default (16 x 16 in 2D) */
 } pic_config;
@@ -113,13 +118,15 @@ int pic_init(const pic_config* cfg, void* device_arena, size_t arena_bytes, void
 /* Load n particles of species index s (0-based) from HOST arrays: cell[n] (linear index,
  * x fastest), offset[ndim*n] (component-major: all x offsets, then y, then z; each in [0,1)),
  * u[3*n] (component-major u_x, u_y, u_z).  Copies, validates (PIC_EBADPART on a bad value),
- * sorts by tile and computes the cell-mean momentum used by the drag.  The initial u is
- * u^{-1/2}.  Synchronises the stream. */
+ * bins the particles by cell (counting sort) and computes the cell-mean momentum used by the
+ * drag.  The initial u is u^{-1/2}; particle i gets id i.  Each species is loaded once, before
+ * the first step.  Synchronises the stream. */
 int pic_load_species(pic_ctx* ctx, int s, const pic_species* sp, int64_t n, const int32_t* cell,
                      const float* offset, const float* u);
 
-/* Advance nsteps steps: gather + Boris + drag + move + Esirkepov deposit, Yee update, counting
- * sort every sort_interval steps, diagnostics every diag_interval steps.  Asynchronous. */
+/* Advance nsteps steps: gather + Boris + drag + move + Esirkepov deposit + re-binning of every
+ * particle into its new cell, Yee update, a full counting sort every sort_interval steps when
+ * particles have spilled, diagnostics every diag_interval steps.  Asynchronous. */
 int pic_step(pic_ctx* ctx, int nsteps);
 
 /* Wait for the stream; report sticky device errors. */
@@ -129,8 +136,8 @@ int pic_sync(pic_ctx* ctx);
 int pic_diag(pic_ctx* ctx, pic_diag_rec* out, int max_recs, int* n_out);
 
 /* Copy species s to HOST arrays (any may be NULL): cell[n], offset[ndim*n], u[3*n], id[n]
- * (id requires track_ids).  Particle order is the current (sorted) storage order; n must equal
- * the loaded count.  Synchronises. */
+ * (id requires track_ids).  Particles come in cell order (the order within a cell is not
+ * fixed), then the spill list; n must equal the loaded count.  Synchronises. */
 int pic_get_particles(pic_ctx* ctx, int s, int32_t* cell, float* offset, float* u, int32_t* id,
                       int64_t n);
 
@@ -156,6 +163,18 @@ int pic_fit_growth(pic_ctx* ctx, int width, double t_noise, double start_factor,
 
 /* Per-phase CUDA-event timings (PIC_FLAG_PROFILE).  Synchronises. */
 int pic_kernel_times(pic_ctx* ctx, pic_kernel_time* out, int max, int* n_out);
+
+typedef struct pic_stats {
+    int64_t particles[PIC_MAX_SPECIES];   /* particles held (slots + spill list) */
+    int32_t max_cell[PIC_MAX_SPECIES];    /* largest per-cell count (may exceed the capacity) */
+    int32_t spilled[PIC_MAX_SPECIES];     /* particles in the spill list */
+    int32_t cell_capacity[PIC_MAX_SPECIES];
+    int32_t flags;                        /* sticky device error flags */
+    int32_t reserved;
+} pic_stats;
+
+/* Occupancy of the particle bins of the current buffer.  Synchronises. */
+int pic_get_stats(pic_ctx* ctx, pic_stats* out);
 
 /* Kernel launches issued so far by this context (graph replays count their kernel nodes). */
 int64_t pic_launch_count(const pic_ctx* ctx);

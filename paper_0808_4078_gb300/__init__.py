@@ -34,7 +34,8 @@ class Config(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("nz", ctypes.c_int32), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
                 ("dz", ctypes.c_double), ("dt", ctypes.c_double), ("nspecies", ctypes.c_int32),
-                ("capacity", ctypes.c_int64 * PIC_MAX_SPECIES), ("sort_interval", ctypes.c_int32),
+                ("capacity", ctypes.c_int64 * PIC_MAX_SPECIES),
+                ("cell_capacity", ctypes.c_int32 * PIC_MAX_SPECIES), ("sort_interval", ctypes.c_int32),
                 ("diag_interval", ctypes.c_int32), ("diag_capacity", ctypes.c_int32),
                 ("track_ids", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32)]
@@ -49,6 +50,14 @@ class DiagRec(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("t", ctypes.c_double), ("WE", ctypes.c_double * 3),
                 ("WB", ctypes.c_double * 3), ("Ekin", ctypes.c_double * PIC_MAX_SPECIES),
                 ("P", ctypes.c_double * 3), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("particles", ctypes.c_int64 * PIC_MAX_SPECIES),
+                ("max_cell", ctypes.c_int32 * PIC_MAX_SPECIES),
+                ("spilled", ctypes.c_int32 * PIC_MAX_SPECIES),
+                ("cell_capacity", ctypes.c_int32 * PIC_MAX_SPECIES),
+                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -73,6 +82,7 @@ _SIGNATURES = {
                                       ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "pic_kernel_times": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "pic_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(Stats)]),
     "pic_launch_count": (ctypes.c_int64, [_VP]),
     "pic_step_count": (ctypes.c_int64, [_VP]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
@@ -116,15 +126,16 @@ class Engine:
 
     def __init__(self, ndim, nx, ny, nz=1, dx=0.1, dy=None, dz=None, dt=0.05, capacity=(0, 0),
                  nspecies=2, sort_interval=8, diag_interval=1, diag_capacity=4096,
-                 track_ids=False, flags=0, device="cuda", stream=None):
+                 track_ids=False, flags=0, device="cuda", stream=None, cell_capacity=(0, 0)):
         import torch
         self._torch = torch
         if not torch.cuda.is_available():
             raise RuntimeError("libpic needs a CUDA GPU")
         cap = (ctypes.c_int64 * PIC_MAX_SPECIES)(*[int(c) for c in capacity][:PIC_MAX_SPECIES])
+        ccap = (ctypes.c_int32 * PIC_MAX_SPECIES)(*[int(c) for c in cell_capacity][:PIC_MAX_SPECIES])
         self.cfg = Config(ndim, nx, ny, nz if ndim == 3 else 1, dx, dx if dy is None else dy,
-                          dx if dz is None else dz, dt, nspecies, cap, sort_interval, diag_interval,
-                          diag_capacity, int(bool(track_ids)), flags, 0, 0, 0)
+                          dx if dz is None else dz, dt, nspecies, cap, ccap, sort_interval,
+                          diag_interval, diag_capacity, int(bool(track_ids)), flags, 0, 0, 0)
         self.nbytes = required_bytes(self.cfg)
         self.device = torch.device(device)
         self.arena = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
@@ -224,6 +235,14 @@ class Engine:
         _check(lib().pic_kernel_times(self._ctx, ctypes.cast(buf, _VP), 16, ctypes.byref(n)),
                self._ctx)
         return {b.name.decode(): (b.launches, b.total_ms) for b in buf[:n.value]}
+
+    def stats(self):
+        st = Stats()
+        _check(lib().pic_get_stats(self._ctx, ctypes.byref(st)), self._ctx)
+        n = self.cfg.nspecies
+        return dict(particles=list(st.particles)[:n], max_cell=list(st.max_cell)[:n],
+                    spilled=list(st.spilled)[:n], cell_capacity=list(st.cell_capacity)[:n],
+                    flags=st.flags)
 
     def launch_count(self):
         return int(lib().pic_launch_count(self._ctx))

@@ -1,0 +1,276 @@
+// bins.cu -- counting-sort binning of particles into per-cell slots, and the inverse compaction.
+//
+// Binning (load): each particle takes the next free slot of its cell with an atomic per-cell
+// counter (a counting sort into fixed-capacity bins); a particle whose cell is full goes to the
+// species' spill list.  Counters may exceed the capacity; readers clamp them.  The step kernels
+// rebin every particle into the other buffer the same way, fused into the push.
+// Compaction (read-back): exclusive scan of the clamped counts, then each cell's particles are
+// copied to a dense array in cell order, followed by the spill list.
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+constexpr int NT = 256;
+constexpr int ITEMS = 8;                 // scan items per thread
+constexpr int CHUNK = NT * ITEMS;        // keys per scan block
+constexpr unsigned FULL = 0xffffffffu;
+
+int grid_for(long long n) {
+    long long g = (n + NT - 1) / NT;
+    if (g > 152 * 16) g = 152 * 16;
+    return (int)(g < 1 ? 1 : g);
+}
+
+__global__ void __launch_bounds__(NT) bin_kernel(Args a, int s, long long n, bool with_ids, const int* gate) {
+    if (gate && *gate == 0) return;
+    const int par = a.ctl->parity;
+    const Slots S = a.slot[s][par];
+    const Stage T = stage_of(a, s, par);
+    const int cap = a.cap[s];
+    if (n < 0) n = a.ctl->staged[s];   // after a compaction
+    for (long long p = blockIdx.x * (long long)NT + threadIdx.x; p < n; p += (long long)gridDim.x * NT) {
+        const int c = T.cell[p];
+        bool ok = c >= 0 && c < a.ncell;
+        float ov[3] = {0.f, 0.f, 0.f};
+        for (int d = 0; d < a.ndim; ++d) {
+            ov[d] = T.o[d][p];
+            ok = ok && ov[d] >= 0.f && ov[d] < 1.f;
+        }
+        const float uv[3] = {T.u[0][p], T.u[1][p], T.u[2][p]};
+        for (int d = 0; d < 3; ++d) ok = ok && isfinite(uv[d]) && fabsf(uv[d]) < 1e6f;
+        if (!ok) { atomicOr(&a.ctl->err, ERR_BADPART); continue; }
+        const int id = with_ids ? T.id[p] : (int)p;
+        const int pos = atomicAdd(&S.count[c], 1);
+        if (pos < cap) {
+            const size_t q = (size_t)c * cap + pos;
+            for (int d = 0; d < a.ndim; ++d) S.o[d][q] = ov[d];
+            for (int d = 0; d < 3; ++d) S.u[d][q] = uv[d];
+            if (S.id) S.id[q] = id;
+        } else {
+            const int sp = atomicAdd(S.sn, 1);
+            if (sp < a.spill_cap[s]) {
+                S.scell[sp] = c;
+                for (int d = 0; d < a.ndim; ++d) S.so[d][sp] = ov[d];
+                for (int d = 0; d < 3; ++d) S.su[d][sp] = uv[d];
+                if (S.sid) S.sid[sp] = id;
+            } else {
+                atomicOr(&a.ctl->err, ERR_SPILL_FULL);
+            }
+        }
+    }
+}
+
+// Exclusive scan of min(count, cap) over n entries into start, block sums into tmp.
+__global__ void __launch_bounds__(NT) scan_blocks(Args a, int s, int* __restrict__ start,
+                                                  int* __restrict__ tmp, long long n, const int* gate) {
+    if (gate && *gate == 0) return;
+    const int* __restrict__ count = a.slot[s][a.ctl->parity].count;
+    const int cap = a.cap[s];
+    __shared__ int warp_sums[NT / 32];
+    const long long off = (long long)blockIdx.x * CHUNK + (long long)threadIdx.x * ITEMS;
+    int v[ITEMS];
+    int sum = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        v[i] = off + i < n ? min(count[off + i], cap) : 0;
+        sum += v[i];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < NT / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane < NT / 32) warp_sums[lane] = w;   // inclusive
+    }
+    __syncthreads();
+    int run = incl - sum + (warp > 0 ? warp_sums[warp - 1] : 0);
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        if (off + i < n) start[off + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == NT - 1) tmp[blockIdx.x] = warp_sums[NT / 32 - 1];
+}
+
+// In-place exclusive scan of tmp[0..m) by one block, chunk by chunk with a running carry.
+__global__ void __launch_bounds__(NT) scan_tmp(int* __restrict__ tmp, int m, int* __restrict__ total,
+                                               const int* gate) {
+    if (gate && *gate == 0) return;
+    __shared__ int warp_sums[NT / 32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < m; base += NT) {
+        const int i = base + threadIdx.x;
+        const int x = i < m ? tmp[i] : 0;
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < NT / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULL, w, o);
+                if (lane >= o) w += t;
+            }
+            if (lane < NT / 32) warp_sums[lane] = w;
+        }
+        __syncthreads();
+        const int excl = carry + incl - x + (warp > 0 ? warp_sums[warp - 1] : 0);
+        if (i < m) tmp[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == NT - 1) carry = excl + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(NT) scan_add(int* __restrict__ start, const int* __restrict__ tmp, long long n,
+                                               const int* gate) {
+    if (gate && *gate == 0) return;
+    const long long off = (long long)blockIdx.x * CHUNK;
+    const int add = tmp[blockIdx.x];
+    for (int i = threadIdx.x; i < CHUNK; i += NT) {
+        const long long k = off + i;
+        if (k < n) start[k] += add;
+    }
+}
+
+// One thread per cell: copy its slots to the staging arrays at start[c] ... in cell order, with
+// the cell index; the spill list follows at start[ncell].
+__global__ void __launch_bounds__(NT) compact_kernel(Args a, int s, const int* gate) {
+    if (gate && *gate == 0) return;
+    const int par = a.ctl->parity;
+    const Slots S = a.slot[s][par];
+    const Stage T = stage_of(a, s, par);
+    const int cap = a.cap[s];
+    const int* __restrict__ start = a.start;
+    for (long long c = blockIdx.x * (long long)NT + threadIdx.x; c < a.ncell; c += (long long)gridDim.x * NT) {
+        const int n = min(S.count[c], cap);
+        const int b = start[c];
+        for (int i = 0; i < n; ++i) {
+            const size_t q = (size_t)c * cap + i;
+            T.cell[b + i] = (int)c;
+            for (int d = 0; d < a.ndim; ++d) T.o[d][b + i] = S.o[d][q];
+            for (int d = 0; d < 3; ++d) T.u[d][b + i] = S.u[d][q];
+            T.id[b + i] = S.id ? S.id[q] : 0;
+        }
+    }
+    const int ns = min(*S.sn, a.spill_cap[s]);
+    const int b = start[a.ncell];
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->staged[s] = b + ns;
+    for (int k = blockIdx.x * NT + threadIdx.x; k < ns; k += gridDim.x * NT) {
+        T.cell[b + k] = S.scell[k];
+        for (int d = 0; d < a.ndim; ++d) T.o[d][b + k] = S.so[d][k];
+        for (int d = 0; d < 3; ++d) T.u[d][b + k] = S.su[d][k];
+        T.id[b + k] = S.sid ? S.sid[k] : 0;
+    }
+}
+
+// Gate of the periodic re-sort: 1 if any species has spilled particles in the current buffer.
+__global__ void spill_gate_kernel(Args a) {
+    int any = 0;
+    for (int s = 0; s < a.nspecies; ++s) any |= *a.slot[s][a.ctl->parity].sn > 0;
+    *a.gate = any;
+}
+
+// Zero the counts and spill counter of species s in the current buffer (before re-binning).
+__global__ void clear_current_kernel(Args a, int s, const int* gate) {
+    if (gate && *gate == 0) return;
+    const Slots S = a.slot[s][a.ctl->parity];
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
+         c += (long long)gridDim.x * blockDim.x)
+        S.count[c] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *S.sn = 0;
+}
+
+// Zero the per-cell counts and spill counters of the buffer the next step writes.
+__global__ void clear_next_kernel(Args a) {
+    const int nb = a.ctl->parity ^ 1;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
+         c += (long long)gridDim.x * blockDim.x)
+        for (int s = 0; s < a.nspecies; ++s) a.slot[s][nb].count[c] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < a.nspecies) *a.slot[threadIdx.x][nb].sn = 0;
+}
+
+}  // namespace
+
+cudaError_t launch_bin(const Args& a, int s, long long n, bool with_ids, const int* gate, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int g = n > 0 ? grid_for(n) : 152 * 16;
+    bin_kernel<<<g, NT, 0, st>>>(a, s, n, with_ids, gate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const Args& a, int s, const int* gate, cudaStream_t st) {
+    const long long n = a.ncell;
+    const int nb = (int)((n + CHUNK - 1) / CHUNK);
+    scan_blocks<<<nb, NT, 0, st>>>(a, s, a.start, a.scan_tmp, n, gate);
+    scan_tmp<<<1, NT, 0, st>>>(a.scan_tmp, nb, a.start + n, gate);
+    scan_add<<<nb, NT, 0, st>>>(a.start, a.scan_tmp, n, gate);
+    compact_kernel<<<grid_for(n), NT, 0, st>>>(a, s, gate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spill_gate(const Args& a, cudaStream_t st) {
+    spill_gate_kernel<<<1, 1, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clear_current(const Args& a, int s, const int* gate, cudaStream_t st) {
+    clear_current_kernel<<<grid_for(a.ncell), NT, 0, st>>>(a, s, gate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clear_next(const Args& a, cudaStream_t st) {
+    clear_next_kernel<<<grid_for(a.ncell), NT, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t preload_bins() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, bin_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, scan_blocks);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, scan_tmp);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, scan_add);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, compact_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, spill_gate_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, clear_current_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, clear_next_kernel);
+    return e;
+}
+
+cudaError_t launch_resort(const Args& a, cudaStream_t st, int* launches) {
+    spill_gate_kernel<<<1, 1, 0, st>>>(a);
+    int l = 1;
+    for (int s = 0; s < a.nspecies; ++s) {
+        cudaError_t e = launch_compact(a, s, a.gate, st);
+        if (e != cudaSuccess) return e;
+        clear_current_kernel<<<grid_for(a.ncell), NT, 0, st>>>(a, s, a.gate);
+        // n < 0: the bin kernel takes the staged count recorded by the compaction
+        bin_kernel<<<152 * 16, NT, 0, st>>>(a, s, -1, true, a.gate);
+        l += 6;
+    }
+    *launches += l;
+    return cudaGetLastError();
+}
+
+}  // namespace pic

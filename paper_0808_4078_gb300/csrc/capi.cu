@@ -26,10 +26,13 @@ const char* kPhaseName[PH_N] = {"push_deposit", "yee", "finalize", "sort"};
 struct Layout {
     size_t total = 0;
     size_t ctl, runs, work;
-    size_t part[PIC_NS][2][8];     // cell, o0, o1, o2, u0, u1, u2, id
+    // per species, per buffer: slot arrays o[0..2], u[0..2], id; count; spill arrays
+    size_t so[PIC_NS][2][3], su[PIC_NS][2][3], sid[PIC_NS][2], scount[PIC_NS][2];
+    size_t sp_cell[PIC_NS][2], sp_o[PIC_NS][2][3], sp_u[PIC_NS][2][3], sp_id[PIC_NS][2], sp_n[PIC_NS][2];
+    size_t slot_region[PIC_NS][2];   // start of the contiguous slot arrays (staging view)
     size_t E[3], B[3], J[3], Jlast[3];
     size_t msum[3], mcnt, ubar[3];
-    size_t start[PIC_NS], count, cursor, scan_tmp;
+    size_t start, scan_tmp, gate;
     size_t partials, hist, fit;
 };
 
@@ -44,6 +47,8 @@ struct Geometry {
     int tx, ty, tz;
     int ntx, nty, ntz;
     long long ncell, ntiles;
+    int cap[PIC_NS];          // slots per cell per species
+    int spill_cap[PIC_NS];
 };
 
 int geometry(const pic_config* c, Geometry* g, std::string* err) {
@@ -68,23 +73,47 @@ int geometry(const pic_config* c, Geometry* g, std::string* err) {
         if (c->capacity[s] < 0 || c->capacity[s] >= (1ll << 31)) { *err = "capacity must be in [0, 2^31)"; return PIC_EINVAL; }
     if (c->diag_interval < 0 || (c->diag_interval > 0 && c->diag_capacity < 1)) { *err = "diag_capacity must be >= 1"; return PIC_EINVAL; }
     if (c->sort_interval < 0) { *err = "sort_interval must be >= 0"; return PIC_EINVAL; }
+    for (int s = 0; s < PIC_NS; ++s) {
+        g->cap[s] = 0;
+        g->spill_cap[s] = 0;
+        if (s >= c->nspecies) continue;
+        const long long mean = (c->capacity[s] + g->ncell - 1) / g->ncell;
+        long long cap = c->cell_capacity[s] > 0 ? c->cell_capacity[s] : ((4 * mean + 31) / 32) * 32;
+        if (cap < 32 && c->cell_capacity[s] <= 0) cap = 32;
+        if (cap < 1 || cap > 65535) { *err = "cell_capacity must be in [1, 65535]"; return PIC_EINVAL; }
+        if (cap * g->ncell < 2 * c->capacity[s]) { *err = "cell_capacity must be >= 2 x capacity / cells"; return PIC_EINVAL; }
+        if (cap * g->ncell >= (1ll << 31)) { *err = "cells x cell_capacity must be < 2^31"; return PIC_EINVAL; }
+        g->cap[s] = (int)cap;
+        long long sc = c->capacity[s] / 16;
+        if (sc < 65536) sc = 65536;
+        if (sc > c->capacity[s] + 1) sc = c->capacity[s] + 1;
+        g->spill_cap[s] = (int)sc;
+    }
     return PIC_OK;
 }
 
 Layout make_layout(const pic_config* c, const Geometry& g) {
-    Layout L;
+    Layout L{};
     size_t off = 0;
     const long long nc = g.ncell;
     L.ctl = take(off, sizeof(Ctl));
     L.runs = take(off, sizeof(RunDev));
     L.work = take(off, sizeof(int2) * g.ntiles);
-    for (int s = 0; s < PIC_NS; ++s)
+    for (int s = 0; s < c->nspecies; ++s)
         for (int b = 0; b < 2; ++b) {
-            const long long cap = s < c->nspecies ? c->capacity[s] : 0;
-            L.part[s][b][0] = take(off, 4 * cap);
-            for (int d = 0; d < 3; ++d) L.part[s][b][1 + d] = d < c->ndim ? take(off, 4 * cap) : 0;
-            for (int d = 0; d < 3; ++d) L.part[s][b][4 + d] = take(off, 4 * cap);
-            L.part[s][b][7] = c->track_ids ? take(off, 4 * cap) : 0;
+            const long long ns = nc * g.cap[s];
+            off = (off + 255) & ~size_t(255);
+            L.slot_region[s][b] = off;
+            for (int d = 0; d < 3; ++d) L.so[s][b][d] = d < c->ndim ? take(off, 4 * ns) : 0;
+            for (int d = 0; d < 3; ++d) L.su[s][b][d] = take(off, 4 * ns);
+            L.sid[s][b] = c->track_ids ? take(off, 4 * ns) : 0;
+            L.scount[s][b] = take(off, 4 * nc);
+            const long long sp = g.spill_cap[s];
+            L.sp_cell[s][b] = take(off, 4 * sp);
+            for (int d = 0; d < 3; ++d) L.sp_o[s][b][d] = d < c->ndim ? take(off, 4 * sp) : 0;
+            for (int d = 0; d < 3; ++d) L.sp_u[s][b][d] = take(off, 4 * sp);
+            L.sp_id[s][b] = c->track_ids ? take(off, 4 * sp) : 0;
+            L.sp_n[s][b] = take(off, 4);
         }
     for (int d = 0; d < 3; ++d) L.E[d] = take(off, 4 * nc);
     for (int d = 0; d < 3; ++d) L.B[d] = take(off, 4 * nc);
@@ -93,10 +122,9 @@ Layout make_layout(const pic_config* c, const Geometry& g) {
     for (int d = 0; d < 3; ++d) L.msum[d] = take(off, 8 * nc);
     L.mcnt = take(off, 4 * nc);
     for (int d = 0; d < 3; ++d) L.ubar[d] = take(off, 4 * nc);
-    for (int s = 0; s < PIC_NS; ++s) L.start[s] = take(off, 4 * (nc + 1));
-    L.count = take(off, 4 * nc);
-    L.cursor = take(off, 4 * nc);
+    L.start = take(off, 4 * (nc + 1));
     L.scan_tmp = take(off, 4 * (nc / 2048 + 2));
+    L.gate = take(off, 4);
     L.partials = take(off, sizeof(double) * 8 * g.ntiles);
     L.hist = take(off, sizeof(DiagRec) * (c->diag_interval > 0 ? c->diag_capacity : 1));
     L.fit = take(off, sizeof(double) * 4);
@@ -193,8 +221,10 @@ int launch_one_step(pic_ctx* ctx, long long step_index) {
     const Args& a = ctx->args;
     {
         PhaseScope ps(ctx, PH_PUSH);
+        CK(launch_clear_next(a, ctx->stream));
         CK(ctx->cfg.ndim == 2 ? launch_push2d(a, ctx->stream) : launch_push3d(a, ctx->stream));
-        ctx->launches += 1;
+        CK(launch_spill2d(a, ctx->stream));
+        ctx->launches += 3;
     }
     {
         PhaseScope ps(ctx, PH_YEE);
@@ -209,11 +239,9 @@ int launch_one_step(pic_ctx* ctx, long long step_index) {
     }
     if ((step_index + 1) % ctx->sort_interval == 0) {
         PhaseScope ps(ctx, PH_SORT);
-        for (int s = 0; s < ctx->cfg.nspecies; ++s) {
-            if (!ctx->run.sp[s].active) continue;
-            CK(launch_sort(a, s, ctx->geo.tx, ctx->geo.ty, ctx->geo.tz, ctx->stream));
-            ctx->launches += sort_launches(a.npart[s]);
-        }
+        int l = 0;
+        CK(launch_resort(a, ctx->stream, &l));
+        ctx->launches += l;
     }
     return PIC_OK;
 }
@@ -240,11 +268,6 @@ int build_graph(pic_ctx* ctx) {
     return PIC_OK;
 }
 
-void refresh_args(pic_ctx* ctx) {
-    Args& a = ctx->args;
-    for (int s = 0; s < PIC_NS; ++s) a.npart[s] = ctx->loaded[s];
-}
-
 int device_flags(pic_ctx* ctx) {
     Ctl h;
     CK(cudaMemcpyAsync(&h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
@@ -252,6 +275,7 @@ int device_flags(pic_ctx* ctx) {
     if (h.err & ERR_BADPART) return fail(ctx, PIC_EBADPART, "device: non-finite or out-of-range particle");
     if (h.err & ERR_OVERFLOW) return fail(ctx, PIC_EOVERFLOW, "device: fixed-point headroom exceeded");
     if (h.err & ERR_TIMEOUT) return fail(ctx, PIC_ETIMEOUT, "device: bounded wait gave up");
+    if (h.err & ERR_SPILL_FULL) return fail(ctx, PIC_ENOMEM, "device: spill list full (raise cell_capacity)");
     return PIC_OK;
 }
 
@@ -259,7 +283,8 @@ int current_parity(pic_ctx* ctx, int s, int* par) {
     Ctl h;
     CK(cudaMemcpyAsync(&h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    *par = h.parity[s];
+    (void)s;
+    *par = h.parity;
     return PIC_OK;
 }
 
@@ -334,6 +359,9 @@ extern "C" int pic_init(const pic_config* cfg, void* device_arena, size_t arena_
 
     auto bail = [&](int code) { g_init_error = ctx->err; delete ctx; return code; };
 #define CKI(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { fail(ctx, PIC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); return bail(PIC_ECUDA); } } while (0)
+    CKI(preload_push2d());
+    CKI(preload_bins());
+    CKI(preload_fields());
     // zero the whole state
     CKI(cudaMemsetAsync(ctx->arena, 0, L.total, ctx->stream));
 
@@ -366,21 +394,30 @@ extern "C" int pic_init(const pic_config* cfg, void* device_arena, size_t arena_
     a.work = at<int2>(ctx, L.work);
     a.nwork = (int)g.ntiles;
     a.nspecies = c.nspecies;
-    for (int s = 0; s < PIC_NS; ++s)
+    a.nruns = 1;
+    a.ndim = c.ndim;
+    for (int s = 0; s < c.nspecies; ++s) {
+        a.cap[s] = g.cap[s];
+        a.spill_cap[s] = g.spill_cap[s];
+        a.stage_n[s] = c.capacity[s];
         for (int b = 0; b < 2; ++b) {
-            SpeciesBuf& B = a.buf[s][b];
-            B.cell = at<int>(ctx, L.part[s][b][0]);
-            for (int d = 0; d < 3; ++d) B.o[d] = L.part[s][b][1 + d] ? at<float>(ctx, L.part[s][b][1 + d]) : nullptr;
-            for (int d = 0; d < 3; ++d) B.u[d] = at<float>(ctx, L.part[s][b][4 + d]);
-            B.id = L.part[s][b][7] ? at<int>(ctx, L.part[s][b][7]) : nullptr;
+            Slots& S = a.slot[s][b];
+            for (int d = 0; d < 3; ++d) {
+                S.o[d] = L.so[s][b][d] ? at<float>(ctx, L.so[s][b][d]) : nullptr;
+                S.u[d] = at<float>(ctx, L.su[s][b][d]);
+                S.so[d] = L.sp_o[s][b][d] ? at<float>(ctx, L.sp_o[s][b][d]) : nullptr;
+                S.su[d] = at<float>(ctx, L.sp_u[s][b][d]);
+            }
+            S.id = L.sid[s][b] ? at<int>(ctx, L.sid[s][b]) : nullptr;
+            S.count = at<int>(ctx, L.scount[s][b]);
+            S.scell = at<int>(ctx, L.sp_cell[s][b]);
+            S.sid = L.sp_id[s][b] ? at<int>(ctx, L.sp_id[s][b]) : nullptr;
+            S.sn = at<int>(ctx, L.sp_n[s][b]);
+            // staging when b is current = the slot memory of the other buffer
+            a.stage[s][b ^ 1] = ctx->arena + L.slot_region[s][b];
         }
-    for (int s = 0; s < PIC_NS; ++s) {
-        a.start[s] = at<int>(ctx, L.start[s]);
-        a.count[s] = at<int>(ctx, L.count);
-        a.cursor[s] = at<int>(ctx, L.cursor);
-        a.npart[s] = 0;
     }
-    a.nkeys = g.ncell;
+    a.ncell = g.ncell;
     a.partials = at<double>(ctx, L.partials);
     a.hist = at<DiagRec>(ctx, L.hist);
     a.hist_cap = c.diag_interval > 0 ? c.diag_capacity : 1;
@@ -388,8 +425,8 @@ extern "C" int pic_init(const pic_config* cfg, void* device_arena, size_t arena_
     a.dt = c.dt;
     a.dV = c.dx * c.dy * (c.ndim == 3 ? c.dz : 1.0);
     a.scan_tmp = at<int>(ctx, L.scan_tmp);
-    a.ndim = c.ndim;
-    a.nruns = 1;
+    a.start = at<int>(ctx, L.start);
+    a.gate = at<int>(ctx, L.gate);
 
     if (upload_run(ctx) != PIC_OK) return bail(PIC_ECUDA);
     CKI(cudaStreamSynchronize(ctx->stream));
@@ -398,12 +435,6 @@ extern "C" int pic_init(const pic_config* cfg, void* device_arena, size_t arena_
     return PIC_OK;
 }
 
-namespace {
-__global__ void iota_kernel(int* p, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        p[i] = (int)i;
-}
-}  // namespace
 
 extern "C" int pic_load_species(pic_ctx* ctx, int s, const pic_species* sp, int64_t n,
                                 const int32_t* cell, const float* offset, const float* u) {
@@ -412,28 +443,38 @@ extern "C" int pic_load_species(pic_ctx* ctx, int s, const pic_species* sp, int6
     if (n < 0 || n > ctx->cfg.capacity[s]) return fail(ctx, PIC_ENOMEM, "n = %lld exceeds capacity", (long long)n);
     if (n > 0 && (!cell || !offset || !u)) return fail(ctx, PIC_EINVAL, "null particle array");
     if (ctx->host_step != 0) return fail(ctx, PIC_ESTATE, "species are loaded before the first step");
+    if (ctx->run.sp[s].active) return fail(ctx, PIC_ESTATE, "species %d is already loaded", s);
     if (!(std::isfinite(sp->q) && std::isfinite(sp->m) && sp->m > 0 && std::isfinite(sp->w) && sp->w >= 0 &&
           std::isfinite(sp->nu) && sp->nu >= 0 && std::fabs(sp->q) <= 1.0))
         return fail(ctx, PIC_EINVAL, "bad species parameters (|q| <= 1, m > 0, w >= 0, nu >= 0)");
     const pic_config& c = ctx->cfg;
-    // load into the species' current buffer
     int par = 0;
     int rc = current_parity(ctx, s, &par);
     if (rc) return rc;
-    SpeciesBuf& B = ctx->args.buf[s][par];
+    // host -> staging (the other buffer's slot memory), then counting-sort into the slots
+    const Stage T = stage_of(ctx->args, s, par);
     if (n > 0) {
-        CK(cudaMemcpyAsync(B.cell, cell, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(T.cell, cell, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
         for (int d = 0; d < c.ndim; ++d)
-            CK(cudaMemcpyAsync(B.o[d], offset + (size_t)d * n, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(T.o[d], offset + (size_t)d * n, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
         for (int d = 0; d < 3; ++d)
-            CK(cudaMemcpyAsync(B.u[d], u + (size_t)d * n, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
-        if (B.id) iota_kernel<<<1024, 256, 0, ctx->stream>>>(B.id, n);
+            CK(cudaMemcpyAsync(T.u[d], u + (size_t)d * n, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CK(launch_bin(ctx->args, s, n, false, nullptr, ctx->stream));
+    rc = device_flags(ctx);
+    if (rc) {
+        // undo: empty the species' slots
+        CK(cudaMemsetAsync(ctx->args.slot[s][par].count, 0, 4 * ctx->geo.ncell, ctx->stream));
+        CK(cudaMemsetAsync(ctx->args.slot[s][par].sn, 0, 4, ctx->stream));
+        Ctl h;
+        CK(cudaMemcpyAsync(&h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        h.err = 0;
+        CK(cudaMemcpyAsync(at<Ctl>(ctx, ctx->lay.ctl), &h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return rc;
     }
     ctx->loaded[s] = n;
-    refresh_args(ctx);
-    CK(launch_validate(ctx->args, s, 0, n, 0, ctx->stream));
-    rc = device_flags(ctx);
-    if (rc) { ctx->loaded[s] = 0; refresh_args(ctx); return rc; }
 
     SpeciesParams& P = ctx->run.sp[s];
     P.active = 1;
@@ -453,8 +494,6 @@ extern "C" int pic_load_species(pic_ctx* ctx, int s, const pic_species* sp, int6
     }
     rc = upload_run(ctx);
     if (rc) return rc;
-    // bin by tile, then the drag moments of the load
-    CK(launch_sort(ctx->args, s, ctx->geo.tx, ctx->geo.ty, ctx->geo.tz, ctx->stream));
     if (P.drag) {
         CK(launch_moments_init(ctx->args, s, ctx->stream));
         CK(launch_moments_finalize(ctx->args, &ctx->run, 1, ctx->stream));
@@ -523,24 +562,30 @@ extern "C" int pic_get_particles(pic_ctx* ctx, int s, int32_t* cell, float* offs
     if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
     if (s < 0 || s >= ctx->cfg.nspecies) return fail(ctx, PIC_EINVAL, "bad species index");
     if (n != ctx->loaded[s]) return fail(ctx, PIC_EINVAL, "n must equal the loaded count (%lld)", ctx->loaded[s]);
+    if (id && !ctx->cfg.track_ids) return fail(ctx, PIC_ESTATE, "ids need track_ids");
     int rc = pic_sync(ctx);
     if (rc) return rc;
     int par = 0;
     rc = current_parity(ctx, s, &par);
     if (rc) return rc;
-    const SpeciesBuf& B = ctx->args.buf[s][par];
+    // compaction into the staging area (cell order, then the spill list)
+    CK(launch_compact(ctx->args, s, nullptr, ctx->stream));
+    ctx->launches += 4;
+    Ctl h;
+    CK(cudaMemcpyAsync(&h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (h.staged[s] != n) return fail(ctx, PIC_ESTATE, "device holds %d particles of species %d, expected %lld",
+                                      h.staged[s], s, (long long)n);
+    const Stage T = stage_of(ctx->args, s, par);
     if (n > 0) {
-        if (cell) CK(cudaMemcpyAsync(cell, B.cell, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+        if (cell) CK(cudaMemcpyAsync(cell, T.cell, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
         if (offset)
             for (int d = 0; d < ctx->cfg.ndim; ++d)
-                CK(cudaMemcpyAsync(offset + (size_t)d * n, B.o[d], 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+                CK(cudaMemcpyAsync(offset + (size_t)d * n, T.o[d], 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
         if (u)
             for (int d = 0; d < 3; ++d)
-                CK(cudaMemcpyAsync(u + (size_t)d * n, B.u[d], 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
-        if (id) {
-            if (!B.id) return fail(ctx, PIC_ESTATE, "ids need track_ids");
-            CK(cudaMemcpyAsync(id, B.id, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
-        }
+                CK(cudaMemcpyAsync(u + (size_t)d * n, T.u[d], 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+        if (id) CK(cudaMemcpyAsync(id, T.id, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return PIC_OK;
@@ -623,6 +668,32 @@ extern "C" int pic_kernel_times(pic_ctx* ctx, pic_kernel_time* out, int max, int
         ++n;
     }
     *n_out = n;
+    return PIC_OK;
+}
+
+extern "C" int pic_get_stats(pic_ctx* ctx, pic_stats* out) {
+    if (!ctx || !out) return fail(ctx, PIC_EINVAL, "null argument");
+    CK(cudaStreamSynchronize(ctx->stream));
+    Ctl h;
+    CK(cudaMemcpyAsync(&h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::memset(out, 0, sizeof(*out));
+    std::vector<int> cnt((size_t)ctx->geo.ncell);
+    for (int s = 0; s < ctx->cfg.nspecies; ++s) {
+        const Slots& S = ctx->args.slot[s][h.parity];
+        CK(cudaMemcpyAsync(cnt.data(), S.count, 4 * cnt.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        int sn = 0;
+        CK(cudaMemcpyAsync(&sn, S.sn, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        long long tot = 0;
+        int mx = 0;
+        for (int c : cnt) { tot += c < ctx->geo.cap[s] ? c : ctx->geo.cap[s]; mx = c > mx ? c : mx; }
+        out->particles[s] = tot + sn;
+        out->max_cell[s] = mx;
+        out->spilled[s] = sn;
+        out->cell_capacity[s] = ctx->geo.cap[s];
+    }
+    out->flags = h.err;
     return PIC_OK;
 }
 

@@ -154,39 +154,29 @@ __global__ void moments_finalize_kernel(const RunDev* __restrict__ runs, int run
     }
 }
 
-// Drag moments of the loaded particles (NGP cell of the current position).
+// Drag moments of the loaded particles of species s (NGP cell = the slot's cell), current buffer.
 __global__ void moments_init_kernel(Args a, int s) {
-    const SpeciesBuf B = a.buf[s][a.ctl->parity[s]];
-    const long long n = a.npart[s];
     const RunDev& R = a.runs[0];
     if (!R.sp[s].drag || !R.msum[0]) return;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x) {
-        const long long c = B.cell[p] - R.cell_off;
-        const float ms = 1048576.0f;
-        atomicAdd((unsigned long long*)&R.msum[0][c], (unsigned long long)__float2ll_rn(B.u[0][p] * ms));
-        atomicAdd((unsigned long long*)&R.msum[1][c], (unsigned long long)__float2ll_rn(B.u[1][p] * ms));
-        atomicAdd((unsigned long long*)&R.msum[2][c], (unsigned long long)__float2ll_rn(B.u[2][p] * ms));
-        atomicAdd(&R.mcnt[c], 1);
+    const Slots S = a.slot[s][a.ctl->parity];
+    const int cap = a.cap[s];
+    const float ms = 1048576.0f;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int n = min(S.count[c], cap);
+        long long m[3] = {0, 0, 0};
+        for (int i = 0; i < n; ++i)
+            for (int d = 0; d < 3; ++d) m[d] += __float2ll_rn(S.u[d][(size_t)c * cap + i] * ms);
+        const long long lc = c - R.cell_off;
+        for (int d = 0; d < 3; ++d) atomicAdd((unsigned long long*)&R.msum[d][lc], (unsigned long long)m[d]);
+        atomicAdd(&R.mcnt[lc], n);
     }
-}
-
-// Validation of loaded particles: cell in range, offsets in [0,1), finite momenta.
-__global__ void validate_kernel(Args a, int s, long long first, long long n, int run) {
-    const SpeciesBuf B = a.buf[s][a.ctl->parity[s]];
-    const RunDev& R = a.runs[run];
-    const long long ncell = (long long)R.nx * R.ny * R.nz;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
-         q += (long long)gridDim.x * blockDim.x) {
-        const long long p = first + q;
-        const long long c = (long long)B.cell[p] - R.cell_off;
-        bool ok = c >= 0 && c < ncell;
-        for (int d = 0; d < a.ndim; ++d) {
-            const float o = B.o[d][p];
-            ok = ok && o >= 0.f && o < 1.f;
-        }
-        for (int d = 0; d < 3; ++d) ok = ok && isfinite(B.u[d][p]) && fabsf(B.u[d][p]) < 1e6f;
-        if (!ok) atomicOr(&a.ctl->err, ERR_BADPART);
+    const int ns = min(*S.sn, a.spill_cap[s]);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ns; k += gridDim.x * blockDim.x) {
+        const long long lc = S.scell[k] - R.cell_off;
+        for (int d = 0; d < 3; ++d)
+            atomicAdd((unsigned long long*)&R.msum[d][lc], (unsigned long long)__float2ll_rn(S.su[d][k] * ms));
+        atomicAdd(&R.mcnt[lc], 1);
     }
 }
 
@@ -231,7 +221,10 @@ __global__ void __launch_bounds__(NT) finalize_kernel(Args a) {
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) a.ctl->step = step + 1;
+    if (threadIdx.x == 0) {
+        a.ctl->step = step + 1;
+        a.ctl->parity ^= 1;          // the particles now live in the other buffer
+    }
 }
 
 // ------------------------------------------------------------------ growth fit (FP64)
@@ -323,6 +316,19 @@ int grid_for(long long n) {
 
 }  // namespace
 
+cudaError_t preload_fields() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, yee_b_half_2d);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, yee_e_2d);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, yee_b_half_3d);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, yee_e_3d);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, moments_finalize_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, moments_init_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, finalize_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fit_kernel);
+    return e;
+}
+
 cudaError_t launch_yee2d(const Args& a, const RunDev* host_runs, int nruns, cudaStream_t s) {
     for (int r = 0; r < nruns; ++r) {
         const long long n = (long long)host_runs[r].nx * host_runs[r].ny;
@@ -351,7 +357,7 @@ cudaError_t launch_finalize(const Args& a, cudaStream_t s) {
 }
 
 cudaError_t launch_moments_init(const Args& a, int species, cudaStream_t s) {
-    moments_init_kernel<<<grid_for(a.npart[species]), NT, 0, s>>>(a, species);
+    moments_init_kernel<<<grid_for(a.ncell), NT, 0, s>>>(a, species);
     return cudaGetLastError();
 }
 
@@ -361,13 +367,6 @@ cudaError_t launch_moments_finalize(const Args& a, const RunDev* host_runs, int 
         const long long n = (long long)host_runs[r].nx * host_runs[r].ny * host_runs[r].nz;
         moments_finalize_kernel<<<grid_for(n), NT, 0, s>>>(a.runs, r);
     }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_validate(const Args& a, int species, long long first, long long n, int run,
-                            cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    validate_kernel<<<grid_for(n), NT, 0, s>>>(a, species, first, n, run);
     return cudaGetLastError();
 }
 

@@ -1,27 +1,29 @@
 // pic_internal.cuh -- device-side data structures shared by the libpic kernels.
 //
 // Layout in HBM (all carved from the caller's arena):
-//   particles  per species, two buffers (sort ping-pong), SoA: cell int32, offset float x ndim,
-//              u float x 3, optional id int32.  The cell index is the run-global index
-//              (run cell offset + local index, x fastest).
+//   particles  cell-binned: species s keeps, per cell, a slot range of fixed capacity cap[s]
+//              holding that cell's particles contiguously (SoA: offsets float x ndim,
+//              momenta float x 3, optional id int32) plus a per-cell count.  The cell index is
+//              implied by the slot, so it is not stored.  Two buffers: every step reads buffer
+//              `parity` and writes each particle into its new cell's slots of the other buffer
+//              (a counting sort fused into the push).  Particles that find their new cell full
+//              go to a per-species spill list (cell index stored), processed by its own kernel.
 //   fields     E[3], B[3] float per cell; J[3] int64 fixed point per cell.
 //   drag       per cell: sum u (3 x int64, fixed point 2^20), count int32, and the cell-mean
 //              momentum <u> (3 x float) of the previous step used by the Krook drag.
-//   sort       count / start / cursor int32 per key; keys are tile-major cell indices so a
-//              tile's particles are contiguous after a sort.
 //   diag       FP64 per-CTA field-energy partials, int64 kinetic/momentum accumulators, history.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #define PIC_NS 2                 // species slots
-#define PIC_MOM_SHIFT 20         // fixed-point shift of the drag moments (u * 2^20 as int32)
+#define PIC_MOM_SHIFT 20         // fixed-point shift of the drag moments
 #define PIC_KIN_SHIFT 32         // fixed-point shift of the kinetic/momentum diagnostics
 
 namespace pic {
 
 // Error flags (device word, sticky)
-enum : int { ERR_BADPART = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4 };
+enum : int { ERR_BADPART = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_SPILL_FULL = 8 };
 
 struct SpeciesParams {
     float qmdt2;        // q dt / (2 m)
@@ -35,7 +37,7 @@ struct SpeciesParams {
 struct RunDev {
     int nx, ny, nz;
     int ntx, nty, ntz;      // tiles per axis
-    int cell_off;           // offset of this run's cells/keys in the global key space
+    int cell_off;           // offset of this run's cells in the global cell space
     int shift;              // fixed-point shift S of J
     float dtdx, dtdy, dtdz; // dt / dx: displacement in cells per unit velocity per step
     float cx, cy, cz;       // dt / dx for the Yee curls
@@ -50,20 +52,28 @@ struct RunDev {
     SpeciesParams sp[PIC_NS];
 };
 
-struct SpeciesBuf {
-    int* cell;
-    float* o[3];
-    float* u[3];
-    int* id;
+// One species in one buffer.
+struct Slots {
+    float* o[3];     // [ncell * cap] offsets (x, y[, z])
+    float* u[3];     // [ncell * cap] momenta
+    int* id;         // [ncell * cap] or null
+    int* count;      // [ncell]
+    // spill list (particles whose cell was full)
+    int* scell;      // global cell index
+    float* so[3];
+    float* su[3];
+    int* sid;
+    int* sn;         // number of spilled particles
 };
 
 // Device control block (lives in the arena, updated by kernels)
 struct Ctl {
     long long step;              // steps completed
-    int parity[PIC_NS];          // which particle buffer is current
+    int parity;                  // particle buffer read by the next step
     int err;                     // sticky error flags
-    int pad;
     long long kin[PIC_NS][4];    // kinetic energy + momentum accumulators (diag steps)
+    int spill_max[PIC_NS];       // largest spill count seen
+    int staged[PIC_NS];          // particles in the staging area after the last compaction
 };
 
 struct DiagRec {                 // mirrors pic_diag_rec
@@ -82,12 +92,12 @@ struct Args {
     const int2* work;            // (run, tile) per CTA of the tiled kernels
     int nwork;
     int nspecies;
-    SpeciesBuf buf[PIC_NS][2];
-    int* start[PIC_NS];          // exclusive scan of per-key counts (tile ranges)
-    int* count[PIC_NS];
-    int* cursor[PIC_NS];
-    long long nkeys;             // total keys (= total cells)
-    long long npart[PIC_NS];     // loaded particles per species (all runs)
+    int nruns;
+    int ndim;
+    Slots slot[PIC_NS][2];
+    int cap[PIC_NS];             // slots per cell
+    int spill_cap[PIC_NS];
+    long long ncell;             // total cells (all runs)
     double* partials;            // [nwork][8] field-energy partials of a diag step
     DiagRec* hist;
     int hist_cap;
@@ -95,17 +105,39 @@ struct Args {
     double dt;
     double dV;
     int* scan_tmp;               // block sums of the scan
-    int ndim;
-    int nruns;
+    int* start;                  // [ncell + 1] exclusive scan of clamped counts (compaction)
+    int* gate;                   // device flag of the conditional re-sort
+    // Staging area of species s when buffer b is the current one: the slot memory of the OTHER
+    // buffer viewed as flat arrays of stage_n[s] entries: cell, o[ndim], u[3], id.
+    char* stage[PIC_NS][2];
+    long long stage_n[PIC_NS];
 };
+
+// Flat staging arrays (see Args::stage).
+struct Stage {
+    int* cell;
+    float* o[3];
+    float* u[3];
+    int* id;
+};
+__host__ __device__ inline Stage stage_of(const Args& a, int s, int par) {
+    Stage t;
+    char* b = a.stage[s][par];
+    const long long n = a.stage_n[s];
+    t.cell = reinterpret_cast<int*>(b);
+    for (int d = 0; d < 3; ++d) t.o[d] = d < a.ndim ? reinterpret_cast<float*>(b + 4 * n * (1 + d)) : nullptr;
+    for (int d = 0; d < 3; ++d) t.u[d] = reinterpret_cast<float*>(b + 4 * n * (1 + a.ndim + d));
+    t.id = reinterpret_cast<int*>(b + 4 * n * (4 + a.ndim));
+    return t;
+}
 
 __device__ __forceinline__ int wrapi(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;
 }
 
-// Round x to the nearest integer (ties to even) for |x| < 2^22 with one FFMA: adding 1.5*2^23
-// leaves the integer in the low mantissa bits.
+// Round a*b to the nearest integer (ties to even) for |a*b| < 2^22 with one FFMA: adding
+// 1.5*2^23 leaves the integer in the low mantissa bits.
 __device__ __forceinline__ int round_small(float a, float b) {
     float t = __fmaf_rn(a, b, 12582912.0f);
     return __float_as_int(t) - 0x4B400000;
@@ -115,20 +147,34 @@ __device__ __forceinline__ int round_small(float a, float b) {
 
 // Host-side launchers (defined in the .cu files)
 namespace pic {
+// Load every kernel of the module now (lazy loading would otherwise add the first launch's
+// load time to whatever step first uses a kernel).
+cudaError_t preload_push2d();
+cudaError_t preload_bins();
+cudaError_t preload_fields();
 cudaError_t launch_push2d(const Args& a, cudaStream_t s);
 cudaError_t launch_push3d(const Args& a, cudaStream_t s);
 bool has_push3d();
+cudaError_t launch_spill2d(const Args& a, cudaStream_t s);
 cudaError_t launch_yee2d(const Args& a, const RunDev* host_runs, int nruns, cudaStream_t s);
 cudaError_t launch_yee3d(const Args& a, const RunDev* host_runs, int nruns, cudaStream_t s);
 cudaError_t launch_finalize(const Args& a, cudaStream_t s);
-cudaError_t launch_sort(const Args& a, int species, int tile_x, int tile_y, int tile_z,
-                        cudaStream_t s);
-int sort_launches(long long n);
+cudaError_t launch_clear_next(const Args& a, cudaStream_t s);
+// Counting sort into the per-cell slots and its inverse.  All use the device parity: the
+// current buffer's slots and the staging area in the other buffer's memory.  `gate` (device int,
+// may be null) makes the kernels return at once when it holds 0.
+//   launch_bin:     staging (n particles) -> slots of the current buffer (ids kept if with_ids)
+//   launch_compact: slots + spill list of the current buffer -> staging, cell order
+cudaError_t launch_bin(const Args& a, int species, long long n, bool with_ids, const int* gate,
+                       cudaStream_t s);
+cudaError_t launch_compact(const Args& a, int species, const int* gate, cudaStream_t s);
+cudaError_t launch_spill_gate(const Args& a, cudaStream_t s);
+cudaError_t launch_clear_current(const Args& a, int species, const int* gate, cudaStream_t s);
+// Full re-sort of every species (compact, clear, bin) when any particle is in a spill list.
+cudaError_t launch_resort(const Args& a, cudaStream_t s, int* launches);
 cudaError_t launch_moments_init(const Args& a, int species, cudaStream_t s);
 cudaError_t launch_moments_finalize(const Args& a, const RunDev* host_runs, int nruns,
                                     cudaStream_t s);
-cudaError_t launch_validate(const Args& a, int species, long long first, long long n,
-                            int run, cudaStream_t s);
 cudaError_t launch_fit(const Args& a, long long first, int nrec, int width, double t_noise,
                        double start_factor, double end_factor, double* out3, cudaStream_t s);
 }  // namespace pic

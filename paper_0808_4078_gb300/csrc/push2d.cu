@@ -1,19 +1,17 @@
 // push2d.cu -- fused 2D3V particle step: CIC field gather, relativistic Boris push, Krook drag
 // of the return-current electrons (Eq. (3) friction, per-cell mean-momentum relaxation), move
-// with cell carry, and charge-conserving Esirkepov current deposition (CIC), accumulated in
-// int64 fixed point.
+// with cell carry, charge-conserving Esirkepov current deposition (CIC) accumulated in int64
+// fixed point, and rebinning of every particle into its new cell's slots of the other buffer.
 //
-// One CTA per (run, tile) of 16 x 16 cells, 8 warps.  The counting sort leaves each cell's
-// particles contiguous, so a warp walks whole cells: for cell c it caches the 37 field values
-// any particle of c can touch in registers, and particles still in c that do not leave it this
-// step ("stay" particles, the large majority) are pushed from that cache and accumulate their 8
-// current terms and 4 drag moments in int32 registers; a warp transpose-reduce adds the sums
-// to the shared tile once per cell.  Particles that drifted out of c since the sort, or cross a
-// cell edge in this step, go to a per-warp queue and are processed 32 at a time with per-lane
-// atomics over their 3 x 3 node window (shared tile, or global memory beyond the tile's drift
-// margin).  Every path evaluates the same explicitly-rounded formulas and every current term
-// is an integer before it is summed, so results are bitwise independent of the particle order
-// and of the sort interval.
+// One CTA per (run, tile) of 16 x 16 cells, 8 warps, a warp per cell.  The warp caches the 37
+// field values any particle of its cell can touch in registers.  Particles that stay in the
+// cell this step (the large majority) are pushed from that cache, add their 8 current terms and
+// 4 drag moments to int32 registers (one warp transpose-reduce per cell puts them in the shared
+// tile) and are appended to the cell's new slots with one atomic per warp.  Particles that cross
+// a cell edge go to a per-warp queue and are processed 32 at a time: per-lane atomics over their
+// 3 x 3 node window, and an atomic slot claim in the destination cell.  All paths evaluate the
+// same explicitly-rounded formulas and every current term is an integer before it is summed, so
+// results do not depend on particle order.
 //
 // Shared accumulators are pairs of 32-bit words (value = hi * 4096 + lo) so that all shared
 // atomics are native 32-bit adds; 64-bit shared atomics are several times slower on this GPU.
@@ -23,26 +21,53 @@
 namespace pic {
 namespace {
 
-constexpr int TX = 16, TY = 16, DR = 2;
-constexpr int RX = TX + 2 * DR + 3, RY = TY + 2 * DR + 3, RN = RX * RY;
+constexpr int TX = 16, TY = 16;
+constexpr int RX = TX + 3, RY = TY + 3, RN = RX * RY;   // tile + CIC/Esirkepov stencil halo
 constexpr int NT = 256, NW = NT / 32, QCAP = 64;
 constexpr int CELLS = TX * TY;
-constexpr int FLUSH_CHUNKS = 8;        // register sums stay below 2^31 (8 x 32 particles)
+constexpr int FLUSH_CHUNKS = 8;          // register sums stay below 2^31 (8 x 32 particles)
+constexpr int STAGES = 4;                // per-warp cp.async pipeline depth (chunks in flight)
 constexpr float MOM_SCALE = 1048576.0f;  // 2^20
 constexpr unsigned FULL = 0xffffffffu;
 
 struct Smem {
-    float F[6][RN];                  // Ex Ey Ez Bx By Bz of the region
+    float F[6][RN];                  // Ex Ey Ez Bx By Bz of the region (origin: tile - 1 cell)
     float ub[3][RN];                 // previous cell-mean momentum (drag)
     unsigned Jlo[3][RN];             // current accumulator, value = Jhi * 4096 + Jlo
     int Jhi[3][RN];
     unsigned Mlo[3][RN];             // drag moments (fixed point 2^20), same split
     int Mhi[3][RN];
     int MC[RN];                      // drag counts
-    int q[NW][QCAP];                 // per-warp queue of deferred particle indices
+    unsigned q[NW][QCAP];            // per-warp queue: species << 24 | tile cell << 16 | slot
+    float stg[NW][STAGES][6][32];    // per-warp staged chunks: o0 o1 u0 u1 u2 id (by lane)
+    int cnt[PIC_NS][CELLS];          // particle counts of the tile's cells (current buffer)
     double red[NW][6];
-    unsigned long long kin[4];
+    unsigned long long kin[5];
+    SpeciesParams sp[PIC_NS];
 };
+
+// ------------------------------------------------------------------ async staging
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Position in a warp's work list: its cells ci = warp, warp + NW, ...; per cell the species in
+// order; per species chunks of 32 slots.
+struct Cursor {
+    int ci, s, j;
+};
+__device__ __forceinline__ void advance(Cursor& c, const int (*cnt)[CELLS], int nsp) {
+    c.j += 32;
+    while (c.ci < CELLS) {
+        if (c.j < cnt[c.s][c.ci]) return;
+        c.j = 0;
+        if (++c.s >= nsp) { c.s = 0; c.ci += NW; }
+    }
+}
 
 // ------------------------------------------------------------------ shared accumulators
 __device__ __forceinline__ void add_split(unsigned* lo, int* hi, long long v) {
@@ -271,15 +296,19 @@ __device__ __forceinline__ Pushed push_one(const A& F, const SpeciesParams& P, c
     return r;
 }
 
-__device__ __forceinline__ void kin_add(long long kacc[4], float w, float u0x, float u0y, float u0z,
-                                        float ux, float uy, float uz) {
+// Kinetic energy per species and total momentum at time n, int64 fixed point 2^32:
+// kacc = {Ekin_0, Ekin_1, Px, Py, Pz}.
+__device__ __forceinline__ void kin_add(long long kacc[5], int s, float w, float u0x, float u0y,
+                                        float u0z, float ux, float uy, float uz) {
     const float mx = 0.5f * (u0x + ux), my = 0.5f * (u0y + uy), mz = 0.5f * (u0z + uz);
     const float gmid = sqrtf(1.f + mx * mx + my * my + mz * mz);
     const float sc = 4294967296.0f;   // 2^32
-    kacc[0] += __float2ll_rn(w * (gmid - 1.f) * sc);
-    kacc[1] += __float2ll_rn(w * mx * sc);
-    kacc[2] += __float2ll_rn(w * my * sc);
-    kacc[3] += __float2ll_rn(w * mz * sc);
+    const long long e = __float2ll_rn(w * (gmid - 1.f) * sc);
+    kacc[0] += s ? 0 : e;
+    kacc[1] += s ? e : 0;
+    kacc[2] += __float2ll_rn(w * mx * sc);
+    kacc[3] += __float2ll_rn(w * my * sc);
+    kacc[4] += __float2ll_rn(w * mz * sc);
 }
 
 // The up-to-21 current terms of one particle, applied with `add(comp, i, j, value)`.
@@ -306,72 +335,79 @@ __device__ __forceinline__ void deposit_terms(const Add& add, const SpeciesParam
     }
 }
 
-// ------------------------------------------------------------------ deferred particles
-// Full step of up to 32 queued particles of species P (one per lane), region or global path.
-__device__ __forceinline__ void drain(Smem& sm, const RunDev* Rp, const SpeciesParams& P,
-                                      const SpeciesBuf& B, int k, int lane, int warp, int x0,
-                                      int y0, bool diag, long long kacc[4], int* err) {
-    if (lane >= k) return;
-    const int nx = Rp->nx, ny = Rp->ny;
-    const int p = sm.q[warp][lane];
-    const int lc = B.cell[p] - Rp->cell_off;
-    const float ox = B.o[0][p], oy = B.o[1][p];
-    const float u0x = B.u[0][p], u0y = B.u[1][p], u0z = B.u[2][p];
-    const int cy = lc / nx, cx = lc - cy * nx;
-    int rxi = cx - x0, ryi = cy - y0;
-    if (rxi < -DR) rxi += nx; else if (rxi >= nx - DR) rxi -= nx;
-    if (ryi < -DR) ryi += ny; else if (ryi >= ny - DR) ryi -= ny;
-    const bool inreg = rxi >= -DR && rxi < TX + DR && ryi >= -DR && ryi < TY + DR;
-    const int ix = rxi + DR + 1, iy = ryi + DR + 1;
-    const int n0 = iy * RX + ix;
-    float b0 = 0.f, b1 = 0.f, b2 = 0.f;
-    if (P.drag) {
-        if (inreg) { b0 = sm.ub[0][n0]; b1 = sm.ub[1][n0]; b2 = sm.ub[2][n0]; }
-        else {
-            const size_t g = (size_t)cy * nx + cx;
-            b0 = Rp->ubar[0][g]; b1 = Rp->ubar[1][g]; b2 = Rp->ubar[2][g];
+// ------------------------------------------------------------------ rebinning
+// Claim a slot of cell g in buffer D (or a spill entry) and store the particle there.
+__device__ __forceinline__ void put(const Slots& D, int cap, int spill_cap, int g, int pos, float ox,
+                                    float oy, float ux, float uy, float uz, int id, int* err) {
+    if (pos < cap) {
+        const size_t q = (size_t)g * cap + pos;
+        D.o[0][q] = ox; D.o[1][q] = oy;
+        D.u[0][q] = ux; D.u[1][q] = uy; D.u[2][q] = uz;
+        if (D.id) D.id[q] = id;
+    } else {
+        const int sp = atomicAdd(D.sn, 1);
+        if (sp < spill_cap) {
+            D.scell[sp] = g;
+            D.so[0][sp] = ox; D.so[1][sp] = oy;
+            D.su[0][sp] = ux; D.su[1][sp] = uy; D.su[2][sp] = uz;
+            if (D.sid) D.sid[sp] = id;
+        } else {
+            atomicOr(err, ERR_SPILL_FULL);
         }
     }
-    Pushed r;
-    if (inreg) r = push_one(SharedFields{&sm, n0}, P, Rp, ox, oy, u0x, u0y, u0z, b0, b1, b2);
-    else r = push_one(GlobalFields{Rp, cx, cy}, P, Rp, ox, oy, u0x, u0y, u0z, b0, b1, b2);
-    if (r.bad) { atomicOr(err, ERR_BADPART); return; }
-    if (diag) kin_add(kacc, P.w, u0x, u0y, u0z, r.ux, r.uy, r.uz);
+}
+
+// ------------------------------------------------------------------ crossing particles
+// Full step of up to 32 queued particles (one per lane) of the tile: shared-memory gather and
+// deposit, then rebinning into the destination cell of the other buffer.
+__device__ __forceinline__ void drain(Smem& sm, const Args& a, const RunDev* Rp, int par, int k,
+                                      int lane, int warp, int x0, int y0, bool diag,
+                                      long long kacc[5]) {
+    if (lane >= k) return;
+    const int nx = Rp->nx, ny = Rp->ny;
+    const unsigned e = sm.q[warp][lane];
+    const int s = e >> 24, ci = (e >> 16) & 255, i = e & 65535;
+    const SpeciesParams& P = sm.sp[s];
+    const int lx = ci % TX, ly = ci / TX;
+    const int cx = x0 + lx, cy = y0 + ly;
+    const int g = Rp->cell_off + cy * nx + cx;
+    const int cap = a.cap[s];
+    const Slots S = a.slot[s][par], D = a.slot[s][par ^ 1];
+    const size_t p = (size_t)g * cap + i;
+    const float ox = S.o[0][p], oy = S.o[1][p];
+    const float u0x = S.u[0][p], u0y = S.u[1][p], u0z = S.u[2][p];
+    const int id = S.id ? S.id[p] : 0;
+    const int ix = lx + 1, iy = ly + 1;
+    const int n0 = iy * RX + ix;
+    float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+    if (P.drag) { b0 = sm.ub[0][n0]; b1 = sm.ub[1][n0]; b2 = sm.ub[2][n0]; }
+    const Pushed r = push_one(SharedFields{&sm, n0}, P, Rp, ox, oy, u0x, u0y, u0z, b0, b1, b2);
+    if (r.bad) {
+        // keep the particle where it was, unmoved; the sticky flag fails the run
+        atomicOr(&a.ctl->err, ERR_BADPART);
+        put(D, cap, a.spill_cap[s], g, atomicAdd(&D.count[g], 1), ox, oy, u0x, u0y, u0z, id, &a.ctl->err);
+        return;
+    }
+    if (diag) kin_add(kacc, s, P.w, u0x, u0y, u0z, r.ux, r.uy, r.uz);
     const Win wx = window(ox, r.sx, r.nox), wy = window(oy, r.sy, r.noy);
     const float zf = __fmul_rn(P.jz, r.vz);
-    if (inreg) {
-        auto add = [&](int c, int i, int j, int v) {
-            if (v != 0) add_split(&sm.Jlo[c][j * RX + i], &sm.Jhi[c][j * RX + i], v);
-        };
-        deposit_terms(add, P, ix + wx.off, iy + wy.off, wx, wy, zf);
-        if (P.drag) {
-            const int n1 = (iy + r.sy) * RX + (ix + r.sx);
-            add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], __float2ll_rn(r.ux * MOM_SCALE));
-            add_split(&sm.Mlo[1][n1], &sm.Mhi[1][n1], __float2ll_rn(r.uy * MOM_SCALE));
-            add_split(&sm.Mlo[2][n1], &sm.Mhi[2][n1], __float2ll_rn(r.uz * MOM_SCALE));
-            atomicAdd(&sm.MC[n1], 1);
-        }
-    } else {
-        auto add = [&](int c, int i, int j, int v) {
-            if (v != 0)
-                atomicAdd((unsigned long long*)&Rp->J[c][(size_t)wrapi(j, ny) * nx + wrapi(i, nx)],
-                          (unsigned long long)(long long)v);
-        };
-        deposit_terms(add, P, cx + wx.off, cy + wy.off, wx, wy, zf);
-        if (P.drag) {
-            const size_t g1 = (size_t)wrapi(cy + r.sy, ny) * nx + wrapi(cx + r.sx, nx);
-            atomicAdd((unsigned long long*)&Rp->msum[0][g1], (unsigned long long)__float2ll_rn(r.ux * MOM_SCALE));
-            atomicAdd((unsigned long long*)&Rp->msum[1][g1], (unsigned long long)__float2ll_rn(r.uy * MOM_SCALE));
-            atomicAdd((unsigned long long*)&Rp->msum[2][g1], (unsigned long long)__float2ll_rn(r.uz * MOM_SCALE));
-            atomicAdd(&Rp->mcnt[g1], 1);
-        }
+    auto add = [&](int c, int ii, int jj, int v) {
+        if (v != 0) add_split(&sm.Jlo[c][jj * RX + ii], &sm.Jhi[c][jj * RX + ii], v);
+    };
+    deposit_terms(add, P, ix + wx.off, iy + wy.off, wx, wy, zf);
+    if (P.drag) {
+        const int n1 = (iy + r.sy) * RX + (ix + r.sx);
+        add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], __float2ll_rn(r.ux * MOM_SCALE));
+        add_split(&sm.Mlo[1][n1], &sm.Mhi[1][n1], __float2ll_rn(r.uy * MOM_SCALE));
+        add_split(&sm.Mlo[2][n1], &sm.Mhi[2][n1], __float2ll_rn(r.uz * MOM_SCALE));
+        atomicAdd(&sm.MC[n1], 1);
     }
     int ncx = cx + r.sx, ncy = cy + r.sy;
     ncx = ncx < 0 ? ncx + nx : (ncx >= nx ? ncx - nx : ncx);
     ncy = ncy < 0 ? ncy + ny : (ncy >= ny ? ncy - ny : ncy);
-    B.cell[p] = Rp->cell_off + ncy * nx + ncx;
-    B.o[0][p] = r.nox; B.o[1][p] = r.noy;
-    B.u[0][p] = r.ux; B.u[1][p] = r.uy; B.u[2][p] = r.uz;
+    const int g1 = Rp->cell_off + ncy * nx + ncx;
+    put(D, cap, a.spill_cap[s], g1, atomicAdd(&D.count[g1], 1), r.nox, r.noy, r.ux, r.uy, r.uz, id,
+        &a.ctl->err);
 }
 
 // Register sums of "stay" particles of the cell at region node n0 -> shared tile.
@@ -407,8 +443,9 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
     const int nx = Rp->nx, ny = Rp->ny;
     const int tile = wk.y;
     const int x0 = (tile % Rp->ntx) * TX, y0 = (tile / Rp->ntx) * TY;
-    const int gx0 = x0 - DR - 1, gy0 = y0 - DR - 1;
+    const int gx0 = x0 - 1, gy0 = y0 - 1;
     const long long step = a.ctl->step;
+    const int par = a.ctl->parity;
     const bool diag = a.diag_interval > 0 && (step % a.diag_interval) == 0;
     const bool anydrag = Rp->msum[0] != nullptr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -434,12 +471,18 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
             sm.MC[i] = 0;
         }
     }
-    if (tid < 4) sm.kin[tid] = 0ull;
+    if (tid < 5) sm.kin[tid] = 0ull;
+    if (tid < PIC_NS) sm.sp[tid] = Rp->sp[tid];
+    for (int i = tid; i < PIC_NS * CELLS; i += NT) {
+        const int s = i / CELLS, ci = i - s * CELLS;
+        const int g = Rp->cell_off + (y0 + ci / TX) * nx + (x0 + ci % TX);
+        sm.cnt[s][ci] = (s < a.nspecies && Rp->sp[s].active) ? min(a.slot[s][par].count[g], a.cap[s]) : 0;
+    }
     __syncthreads();
 
     if (diag) {
         // field energy of the tile's own cells (each cell counted by exactly one CTA)
-        const int i = (tid % TX) + DR + 1, j = (tid / TX) + DR + 1;
+        const int i = (tid % TX) + 1, j = (tid / TX) + 1;
         double e[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -461,23 +504,52 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
         }
     }
 
-    for (int s = 0; s < a.nspecies; ++s) {
-        const SpeciesParams P = Rp->sp[s];
-        if (!P.active) continue;
-        const SpeciesBuf B = a.buf[s][a.ctl->parity[s]];
-        const int key0 = Rp->cell_off + tile * CELLS;
-        const int* __restrict__ start = a.start[s];
-        long long kacc[4] = {0, 0, 0, 0};
-        int qn = 0;
-
-        for (int ci = warp; ci < CELLS; ci += NW) {
-            const int cs = start[key0 + ci], ce = start[key0 + ci + 1];
-            if (cs == ce) continue;
-            const int lx = ci % TX, ly = ci / TX;
-            const int gcell = Rp->cell_off + (y0 + ly) * nx + (x0 + lx);
-            const int ix = lx + DR + 1, iy = ly + DR + 1;
-            const int n0 = iy * RX + ix;
-            CellCache cc;
+    long long kacc[5] = {0, 0, 0, 0, 0};
+    int qn = 0;
+    const int nsp = a.nspecies;
+    // issue the asynchronous copies of one chunk into stage st
+    auto issue = [&](const Cursor& c, int st) {
+        if (c.ci < CELLS) {
+            const int i = c.j + lane;
+            if (i < sm.cnt[c.s][c.ci]) {
+                const int lx = c.ci % TX, ly = c.ci / TX;
+                const int g = Rp->cell_off + (y0 + ly) * nx + (x0 + lx);
+                const Slots S = a.slot[c.s][par];
+                const size_t q = (size_t)g * a.cap[c.s] + i;
+                cp_async4(&sm.stg[warp][st][0][lane], S.o[0] + q);
+                cp_async4(&sm.stg[warp][st][1][lane], S.o[1] + q);
+                cp_async4(&sm.stg[warp][st][2][lane], S.u[0] + q);
+                cp_async4(&sm.stg[warp][st][3][lane], S.u[1] + q);
+                cp_async4(&sm.stg[warp][st][4][lane], S.u[2] + q);
+                if (S.id) cp_async4(&sm.stg[warp][st][5][lane], S.id + q);
+            }
+        }
+        cp_async_commit();
+    };
+    Cursor fc{warp, 0, -32};
+    advance(fc, sm.cnt, nsp);
+    Cursor pc = fc;
+#pragma unroll
+    for (int k = 0; k < STAGES - 1; ++k) {
+        issue(fc, k);
+        advance(fc, sm.cnt, nsp);
+    }
+    int st = 0;
+    int cur_ci = -1, n0 = 0, g = 0, nchunk = 0;
+    CellCache cc;
+    int acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = 0;
+    float ub0 = 0.f, ub1 = 0.f, ub2 = 0.f;
+    while (pc.ci < CELLS) {
+        issue(fc, (st + STAGES - 1) % STAGES);
+        advance(fc, sm.cnt, nsp);
+        if (pc.ci != cur_ci) {
+            if (nchunk) { flush_acc(sm, acc, n0, lane); nchunk = 0; }
+            cur_ci = pc.ci;
+            const int lx = cur_ci % TX, ly = cur_ci / TX;
+            g = Rp->cell_off + (y0 + ly) * nx + (x0 + lx);
+            n0 = (ly + 1) * RX + (lx + 1);
 #pragma unroll
             for (int b = 0; b < 2; ++b)
 #pragma unroll
@@ -500,90 +572,95 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
             for (int b = 0; b < 3; ++b)
 #pragma unroll
                 for (int d = 0; d < 3; ++d) cc.bz[b][d] = sm.F[5][n0 + (b - 1) * RX + d - 1];
-            float ub0 = 0.f, ub1 = 0.f, ub2 = 0.f;
-            if (P.drag) { ub0 = sm.ub[0][n0]; ub1 = sm.ub[1][n0]; ub2 = sm.ub[2][n0]; }
-
-            int acc[12];
-#pragma unroll
-            for (int i = 0; i < 12; ++i) acc[i] = 0;
-            int nchunk = 0;
-            for (int base = cs; base < ce; base += 32) {
-                const int p = base + lane;
-                const bool act = p < ce;
-                int cell = -1;
-                float ox = 0.f, oy = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
-                if (act) {
-                    cell = B.cell[p];
-                    ox = B.o[0][p]; oy = B.o[1][p];
-                    ux = B.u[0][p]; uy = B.u[1][p]; uz = B.u[2][p];
-                }
-                const bool here = act && cell == gcell;
-                const Pushed r = push_one(cc, P, Rp, ox, oy, ux, uy, uz, ub0, ub1, ub2);
-                const bool small_u = !P.drag || (fabsf(r.ux) < 4.f && fabsf(r.uy) < 4.f && fabsf(r.uz) < 4.f);
-                const bool stay = here && !r.bad && r.sx == 0 && r.sy == 0 && small_u;
-                if (stay) {
-                    const Win wx = window(ox, 0, r.nox), wy = window(oy, 0, r.noy);
-                    const float zf = __fmul_rn(P.jz, r.vz);
-                    const float jxa = __fmul_rn(P.jx, wx.C[0]), jya = __fmul_rn(P.jy, wy.C[0]);
-                    const float p0 = zp(wy.S0[0], wy.S1[0]), q0 = zq(wy.S0[0], wy.S1[0]);
-                    const float p1 = zp(wy.S0[1], wy.S1[1]), q1 = zq(wy.S0[1], wy.S1[1]);
-                    acc[0] += round_small(jxa, wy.A[0]);                          // Jx (c+1/2, c)
-                    acc[1] += round_small(jxa, wy.A[1]);                          // Jx (c+1/2, c+1)
-                    acc[2] += round_small(jya, wx.A[0]);                          // Jy (c, c+1/2)
-                    acc[3] += round_small(jya, wx.A[1]);                          // Jy (c+1, c+1/2)
-                    acc[4] += round_small(zf, zw(wx.S0[0], wx.S1[0], p0, q0));    // Jz (c, c)
-                    acc[5] += round_small(zf, zw(wx.S0[1], wx.S1[1], p0, q0));    // Jz (c+1, c)
-                    acc[6] += round_small(zf, zw(wx.S0[0], wx.S1[0], p1, q1));    // Jz (c, c+1)
-                    acc[7] += round_small(zf, zw(wx.S0[1], wx.S1[1], p1, q1));    // Jz (c+1, c+1)
-                    if (P.drag) {
-                        acc[8] += __float2int_rn(r.ux * MOM_SCALE);
-                        acc[9] += __float2int_rn(r.uy * MOM_SCALE);
-                        acc[10] += __float2int_rn(r.uz * MOM_SCALE);
-                        acc[11] += 1;
-                    }
-                    if (diag) kin_add(kacc, P.w, ux, uy, uz, r.ux, r.uy, r.uz);
-                    B.o[0][p] = r.nox; B.o[1][p] = r.noy;
-                    B.u[0][p] = r.ux; B.u[1][p] = r.uy; B.u[2][p] = r.uz;
-                }
-                if (here && r.bad) atomicOr(&a.ctl->err, ERR_BADPART);
-                const bool defer = act && !stay && !(here && r.bad);
-                const unsigned dm = __ballot_sync(FULL, defer);
-                if (defer) sm.q[warp][qn + __popc(dm & lt)] = p;
-                qn += __popc(dm);
-                __syncwarp();
-                if (qn >= 32) {
-                    drain(sm, Rp, P, B, 32, lane, warp, x0, y0, diag, kacc, &a.ctl->err);
-                    __syncwarp();
-                    const int rest = qn - 32;
-                    const int moved = lane < rest ? sm.q[warp][32 + lane] : 0;
-                    __syncwarp();
-                    if (lane < rest) sm.q[warp][lane] = moved;
-                    __syncwarp();
-                    qn = rest;
-                }
-                if (++nchunk == FLUSH_CHUNKS) {
-                    flush_acc(sm, acc, n0, lane);
-                    nchunk = 0;
-                }
-            }
-            if (nchunk) flush_acc(sm, acc, n0, lane);
+            if (anydrag) { ub0 = sm.ub[0][n0]; ub1 = sm.ub[1][n0]; ub2 = sm.ub[2][n0]; }
         }
-        if (qn > 0) drain(sm, Rp, P, B, qn, lane, warp, x0, y0, diag, kacc, &a.ctl->err);
+        const int s = pc.s;
+        const SpeciesParams& P = sm.sp[s];
+        const int cap = a.cap[s];
+        const Slots D = a.slot[s][par ^ 1];
+        const int i = pc.j + lane;
+        const bool act = i < sm.cnt[s][pc.ci];
+        cp_async_wait<STAGES - 1>();
+        float ox = 0.f, oy = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
+        int id = 0;
+        if (act) {
+            ox = sm.stg[warp][st][0][lane]; oy = sm.stg[warp][st][1][lane];
+            ux = sm.stg[warp][st][2][lane]; uy = sm.stg[warp][st][3][lane]; uz = sm.stg[warp][st][4][lane];
+            id = __float_as_int(sm.stg[warp][st][5][lane]);
+        }
+        const Pushed r = push_one(cc, P, Rp, ox, oy, ux, uy, uz, ub0, ub1, ub2);
+        const bool small_u = !P.drag || (fabsf(r.ux) < 4.f && fabsf(r.uy) < 4.f && fabsf(r.uz) < 4.f);
+        const bool stay = act && !r.bad && r.sx == 0 && r.sy == 0 && small_u;
+        if (stay) {
+            const Win wx = window(ox, 0, r.nox), wy = window(oy, 0, r.noy);
+            const float zf = __fmul_rn(P.jz, r.vz);
+            const float jxa = __fmul_rn(P.jx, wx.C[0]), jya = __fmul_rn(P.jy, wy.C[0]);
+            const float p0 = zp(wy.S0[0], wy.S1[0]), q0 = zq(wy.S0[0], wy.S1[0]);
+            const float p1 = zp(wy.S0[1], wy.S1[1]), q1 = zq(wy.S0[1], wy.S1[1]);
+            acc[0] += round_small(jxa, wy.A[0]);                          // Jx (c+1/2, c)
+            acc[1] += round_small(jxa, wy.A[1]);                          // Jx (c+1/2, c+1)
+            acc[2] += round_small(jya, wx.A[0]);                          // Jy (c, c+1/2)
+            acc[3] += round_small(jya, wx.A[1]);                          // Jy (c+1, c+1/2)
+            acc[4] += round_small(zf, zw(wx.S0[0], wx.S1[0], p0, q0));    // Jz (c, c)
+            acc[5] += round_small(zf, zw(wx.S0[1], wx.S1[1], p0, q0));    // Jz (c+1, c)
+            acc[6] += round_small(zf, zw(wx.S0[0], wx.S1[0], p1, q1));    // Jz (c, c+1)
+            acc[7] += round_small(zf, zw(wx.S0[1], wx.S1[1], p1, q1));    // Jz (c+1, c+1)
+            if (P.drag) {
+                acc[8] += __float2int_rn(r.ux * MOM_SCALE);
+                acc[9] += __float2int_rn(r.uy * MOM_SCALE);
+                acc[10] += __float2int_rn(r.uz * MOM_SCALE);
+                acc[11] += 1;
+            }
+            if (diag) kin_add(kacc, s, P.w, ux, uy, uz, r.ux, r.uy, r.uz);
+        }
+        // stayers keep their cell: append them to its slots in the other buffer
+        const unsigned sm_ = __ballot_sync(FULL, stay);
+        int pos0 = 0;
+        if (lane == 0 && sm_) pos0 = atomicAdd(&D.count[g], __popc(sm_));
+        pos0 = __shfl_sync(FULL, pos0, 0);
+        if (stay)
+            put(D, cap, a.spill_cap[s], g, pos0 + __popc(sm_ & lt), r.nox, r.noy, r.ux, r.uy, r.uz,
+                id, &a.ctl->err);
+        const bool defer = act && !stay;
+        const unsigned dm = __ballot_sync(FULL, defer);
+        if (defer) sm.q[warp][qn + __popc(dm & lt)] = ((unsigned)s << 24) | ((unsigned)pc.ci << 16) | (unsigned)i;
+        qn += __popc(dm);
         __syncwarp();
+        if (qn >= 32) {
+            drain(sm, a, Rp, par, 32, lane, warp, x0, y0, diag, kacc);
+            __syncwarp();
+            const int rest = qn - 32;
+            const unsigned moved = lane < rest ? sm.q[warp][32 + lane] : 0u;
+            __syncwarp();
+            if (lane < rest) sm.q[warp][lane] = moved;
+            __syncwarp();
+            qn = rest;
+        }
+        if (++nchunk == FLUSH_CHUNKS) {
+            flush_acc(sm, acc, n0, lane);
+            nchunk = 0;
+        }
+        advance(pc, sm.cnt, nsp);
+        st = (st + 1) % STAGES;
+    }
+    if (nchunk) flush_acc(sm, acc, n0, lane);
+    cp_async_wait<0>();
+    if (qn > 0) drain(sm, a, Rp, par, qn, lane, warp, x0, y0, diag, kacc);
+    __syncwarp();
 
-        if (diag) {
+    if (diag) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                long long v = kacc[k];
+        for (int k = 0; k < 5; ++k) {
+            long long v = kacc[k];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-                if (lane == 0 && v != 0) atomicAdd(&sm.kin[k], (unsigned long long)v);
-            }
-            __syncthreads();
-            if (tid < 4 && sm.kin[tid] != 0ull) {
-                atomicAdd((unsigned long long*)&a.ctl->kin[s][tid], sm.kin[tid]);
-                sm.kin[tid] = 0ull;
-            }
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+            if (lane == 0 && v != 0) atomicAdd(&sm.kin[k], (unsigned long long)v);
+        }
+        __syncthreads();
+        if (tid < 5 && sm.kin[tid] != 0ull) {
+            // Ekin per species, momentum summed into species 0's slots
+            if (tid < 2) atomicAdd((unsigned long long*)&a.ctl->kin[tid][0], sm.kin[tid]);
+            else atomicAdd((unsigned long long*)&a.ctl->kin[0][tid - 1], sm.kin[tid]);
         }
     }
     __syncthreads();
@@ -608,6 +685,67 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
     }
 }
 
+// ------------------------------------------------------------------ spilled particles
+// Particles that found their cell full: one thread each, global-memory gather and atomics (the
+// same formulas as the tile paths), rebinned into the other buffer.
+__global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
+    const int par = a.ctl->parity;
+    const long long step = a.ctl->step;
+    const bool diag = a.diag_interval > 0 && (step % a.diag_interval) == 0;
+    const RunDev* Rp = &a.runs[0];
+    const int nx = Rp->nx, ny = Rp->ny;
+    for (int s = 0; s < a.nspecies; ++s) {
+        const Slots S = a.slot[s][par], D = a.slot[s][par ^ 1];
+        const int ns = min(*S.sn, a.spill_cap[s]);
+        const SpeciesParams P = Rp->sp[s];
+        const int cap = a.cap[s];
+        for (int k = blockIdx.x * NT + threadIdx.x; k < ns; k += gridDim.x * NT) {
+            const int g = S.scell[k];
+            const int lc = g - Rp->cell_off;
+            const int cy = lc / nx, cx = lc - cy * nx;
+            const float ox = S.so[0][k], oy = S.so[1][k];
+            const float u0x = S.su[0][k], u0y = S.su[1][k], u0z = S.su[2][k];
+            const int id = S.sid ? S.sid[k] : 0;
+            float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+            if (P.drag) { b0 = Rp->ubar[0][lc]; b1 = Rp->ubar[1][lc]; b2 = Rp->ubar[2][lc]; }
+            const Pushed r = push_one(GlobalFields{Rp, cx, cy}, P, Rp, ox, oy, u0x, u0y, u0z, b0, b1, b2);
+            if (r.bad) {
+                atomicOr(&a.ctl->err, ERR_BADPART);
+                put(D, cap, a.spill_cap[s], g, atomicAdd(&D.count[g], 1), ox, oy, u0x, u0y, u0z, id, &a.ctl->err);
+                continue;
+            }
+            if (diag) {
+                long long kacc[5] = {0, 0, 0, 0, 0};
+                kin_add(kacc, s, P.w, u0x, u0y, u0z, r.ux, r.uy, r.uz);
+                atomicAdd((unsigned long long*)&a.ctl->kin[s][0], (unsigned long long)(kacc[0] + kacc[1]));
+                for (int c = 0; c < 3; ++c)
+                    atomicAdd((unsigned long long*)&a.ctl->kin[0][1 + c], (unsigned long long)kacc[2 + c]);
+            }
+            const Win wx = window(ox, r.sx, r.nox), wy = window(oy, r.sy, r.noy);
+            const float zf = __fmul_rn(P.jz, r.vz);
+            auto add = [&](int c, int i, int j, int v) {
+                if (v != 0)
+                    atomicAdd((unsigned long long*)&Rp->J[c][(size_t)wrapi(j, ny) * nx + wrapi(i, nx)],
+                              (unsigned long long)(long long)v);
+            };
+            deposit_terms(add, P, cx + wx.off, cy + wy.off, wx, wy, zf);
+            int ncx = cx + r.sx, ncy = cy + r.sy;
+            ncx = ncx < 0 ? ncx + nx : (ncx >= nx ? ncx - nx : ncx);
+            ncy = ncy < 0 ? ncy + ny : (ncy >= ny ? ncy - ny : ncy);
+            const int l1 = ncy * nx + ncx;
+            if (P.drag) {
+                atomicAdd((unsigned long long*)&Rp->msum[0][l1], (unsigned long long)__float2ll_rn(r.ux * MOM_SCALE));
+                atomicAdd((unsigned long long*)&Rp->msum[1][l1], (unsigned long long)__float2ll_rn(r.uy * MOM_SCALE));
+                atomicAdd((unsigned long long*)&Rp->msum[2][l1], (unsigned long long)__float2ll_rn(r.uz * MOM_SCALE));
+                atomicAdd(&Rp->mcnt[l1], 1);
+            }
+            const int g1 = Rp->cell_off + l1;
+            put(D, cap, a.spill_cap[s], g1, atomicAdd(&D.count[g1], 1), r.nox, r.noy, r.ux, r.uy, r.uz,
+                id, &a.ctl->err);
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_push2d(const Args& a, cudaStream_t s) {
@@ -620,6 +758,18 @@ cudaError_t launch_push2d(const Args& a, cudaStream_t s) {
         attr = true;
     }
     push2d_kernel<<<a.nwork, NT, sizeof(Smem), s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t preload_push2d() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, push2d_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, spill2d_kernel);
+    return e;
+}
+
+cudaError_t launch_spill2d(const Args& a, cudaStream_t s) {
+    spill2d_kernel<<<152, NT, 0, s>>>(a);
     return cudaGetLastError();
 }
 

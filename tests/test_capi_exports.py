@@ -35,20 +35,26 @@ def test_every_declared_symbol_is_exported(libpic):
 
 def test_required_bytes_and_config_errors_without_gpu(libpic):
     import paper_0808_4078_gb300 as pic
-    cfg = pic.Config(2, 64, 64, 1, 0.1, 0.1, 0.1, 0.05, 2,
-                     (ctypes.c_int64 * 2)(65536, 65536), 8, 1, 100, 0, 0, 0, 0, 0)
+    cap = lambda a, b: (ctypes.c_int64 * 2)(a, b)
+    ccap = lambda a=0, b=0: (ctypes.c_int32 * 2)(a, b)
+    cfg = pic.Config(2, 64, 64, 1, 0.1, 0.1, 0.1, 0.05, 2, cap(65536, 65536), ccap(), 8, 1, 100,
+                     0, 0, 0, 0, 0)
     n = pic.required_bytes(cfg)
-    # two particle buffers x 2 species x 65536 x 24 B, plus per-cell state
-    assert n >= 2 * 2 * 65536 * 24 + 64 * 64 * (24 + 24)
-    bad = pic.Config(2, 60, 64, 1, 0.1, 0.1, 0.1, 0.05, 2, (ctypes.c_int64 * 2)(1, 1),
-                     8, 1, 100, 0, 0, 0, 0, 0)
+    # automatic cell capacity 4 x 16 = 64 slots; 2 buffers x 2 species x 4096 cells x 64 x 20 B
+    assert n >= 2 * 2 * 4096 * 64 * 20 + 64 * 64 * (24 + 24)
+    bad = pic.Config(2, 60, 64, 1, 0.1, 0.1, 0.1, 0.05, 2, cap(1, 1), ccap(), 8, 1, 100,
+                     0, 0, 0, 0, 0)
     with pytest.raises(pic.PicError) as e:
         pic.required_bytes(bad)
     assert e.value.code == -1
-    courant = pic.Config(2, 64, 64, 1, 0.1, 0.1, 0.1, 0.08, 2, (ctypes.c_int64 * 2)(1, 1),
-                         8, 1, 100, 0, 0, 0, 0, 0)
+    courant = pic.Config(2, 64, 64, 1, 0.1, 0.1, 0.1, 0.08, 2, cap(1, 1), ccap(), 8, 1, 100,
+                         0, 0, 0, 0, 0)
     with pytest.raises(pic.PicError):
         pic.required_bytes(courant)
+    tight = pic.Config(2, 64, 64, 1, 0.1, 0.1, 0.1, 0.05, 2, cap(65536, 65536), ccap(16, 16), 8, 1,
+                       100, 0, 0, 0, 0, 0)
+    with pytest.raises(pic.PicError):     # slots must hold 2 x the mean per cell
+        pic.required_bytes(tight)
 
 
 def test_package_fails_loudly_without_library(tmp_path, monkeypatch):
