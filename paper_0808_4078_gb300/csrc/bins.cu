@@ -41,7 +41,12 @@ __global__ void __launch_bounds__(NT) bin_kernel(Args a, int s, long long n, boo
         for (int d = 0; d < 3; ++d) ok = ok && isfinite(uv[d]) && fabsf(uv[d]) < 1e6f;
         if (!ok) { atomicOr(&a.ctl->err, ERR_BADPART); continue; }
         const int id = with_ids ? T.id[p] : (int)p;
-        const int pos = atomicAdd(&S.count[c], 1);
+        const int cs = a.cap_stay[s];
+        int pos = atomicAdd(&S.count[c], 1);
+        if (pos >= cs) {
+            const int pi = atomicAdd(&S.icount[c], 1);
+            pos = pi < cap - cs ? cs + pi : cap;
+        }
         if (pos < cap) {
             const size_t q = (size_t)c * cap + pos;
             for (int d = 0; d < a.ndim; ++d) S.o[d][q] = ov[d];
@@ -61,19 +66,19 @@ __global__ void __launch_bounds__(NT) bin_kernel(Args a, int s, long long n, boo
     }
 }
 
-// Exclusive scan of min(count, cap) over n entries into start, block sums into tmp.
+// Exclusive scan of the particles per cell (both slot areas) into start, block sums into tmp.
 __global__ void __launch_bounds__(NT) scan_blocks(Args a, int s, int* __restrict__ start,
                                                   int* __restrict__ tmp, long long n, const int* gate) {
     if (gate && *gate == 0) return;
-    const int* __restrict__ count = a.slot[s][a.ctl->parity].count;
-    const int cap = a.cap[s];
+    const Slots S = a.slot[s][a.ctl->parity];
+    const int cap = a.cap[s], cs = a.cap_stay[s];
     __shared__ int warp_sums[NT / 32];
     const long long off = (long long)blockIdx.x * CHUNK + (long long)threadIdx.x * ITEMS;
     int v[ITEMS];
     int sum = 0;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        v[i] = off + i < n ? min(count[off + i], cap) : 0;
+        v[i] = off + i < n ? cell_range(S, cap, cs, off + i).n : 0;
         sum += v[i];
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -163,11 +168,12 @@ __global__ void __launch_bounds__(NT) compact_kernel(Args a, int s, const int* g
     const Stage T = stage_of(a, s, par);
     const int cap = a.cap[s];
     const int* __restrict__ start = a.start;
+    const int cs = a.cap_stay[s];
     for (long long c = blockIdx.x * (long long)NT + threadIdx.x; c < a.ncell; c += (long long)gridDim.x * NT) {
-        const int n = min(S.count[c], cap);
+        const CellRange cr = cell_range(S, cap, cs, c);
         const int b = start[c];
-        for (int i = 0; i < n; ++i) {
-            const size_t q = (size_t)c * cap + i;
+        for (int i = 0; i < cr.n; ++i) {
+            const size_t q = slot_of(c, cap, cs, cr.ns, i);
             T.cell[b + i] = (int)c;
             for (int d = 0; d < a.ndim; ++d) T.o[d][b + i] = S.o[d][q];
             for (int d = 0; d < 3; ++d) T.u[d][b + i] = S.u[d][q];
@@ -197,8 +203,10 @@ __global__ void clear_current_kernel(Args a, int s, const int* gate) {
     if (gate && *gate == 0) return;
     const Slots S = a.slot[s][a.ctl->parity];
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
-         c += (long long)gridDim.x * blockDim.x)
+         c += (long long)gridDim.x * blockDim.x) {
         S.count[c] = 0;
+        S.icount[c] = 0;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) *S.sn = 0;
 }
 
@@ -207,7 +215,10 @@ __global__ void clear_next_kernel(Args a) {
     const int nb = a.ctl->parity ^ 1;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
          c += (long long)gridDim.x * blockDim.x)
-        for (int s = 0; s < a.nspecies; ++s) a.slot[s][nb].count[c] = 0;
+        for (int s = 0; s < a.nspecies; ++s) {
+            a.slot[s][nb].count[c] = 0;
+            a.slot[s][nb].icount[c] = 0;
+        }
     if (blockIdx.x == 0 && threadIdx.x < a.nspecies) *a.slot[threadIdx.x][nb].sn = 0;
 }
 

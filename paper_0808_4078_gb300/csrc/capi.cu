@@ -27,7 +27,7 @@ struct Layout {
     size_t total = 0;
     size_t ctl, runs, work;
     // per species, per buffer: slot arrays o[0..2], u[0..2], id; count; spill arrays
-    size_t so[PIC_NS][2][3], su[PIC_NS][2][3], sid[PIC_NS][2], scount[PIC_NS][2];
+    size_t so[PIC_NS][2][3], su[PIC_NS][2][3], sid[PIC_NS][2], scount[PIC_NS][2], sicount[PIC_NS][2];
     size_t sp_cell[PIC_NS][2], sp_o[PIC_NS][2][3], sp_u[PIC_NS][2][3], sp_id[PIC_NS][2], sp_n[PIC_NS][2];
     size_t slot_region[PIC_NS][2];   // start of the contiguous slot arrays (staging view)
     size_t E[3], B[3], J[3], Jlast[3];
@@ -48,6 +48,7 @@ struct Geometry {
     int ntx, nty, ntz;
     long long ncell, ntiles;
     int cap[PIC_NS];          // slots per cell per species
+    int cap_stay[PIC_NS];     // of which the stay area
     int spill_cap[PIC_NS];
 };
 
@@ -75,15 +76,21 @@ int geometry(const pic_config* c, Geometry* g, std::string* err) {
     if (c->sort_interval < 0) { *err = "sort_interval must be >= 0"; return PIC_EINVAL; }
     for (int s = 0; s < PIC_NS; ++s) {
         g->cap[s] = 0;
+        g->cap_stay[s] = 0;
         g->spill_cap[s] = 0;
         if (s >= c->nspecies) continue;
         const long long mean = (c->capacity[s] + g->ncell - 1) / g->ncell;
         long long cap = c->cell_capacity[s] > 0 ? c->cell_capacity[s] : ((4 * mean + 31) / 32) * 32;
         if (cap < 32 && c->cell_capacity[s] <= 0) cap = 32;
-        if (cap < 1 || cap > 65535) { *err = "cell_capacity must be in [1, 65535]"; return PIC_EINVAL; }
+        if (cap < 2 || cap > 65535) { *err = "cell_capacity must be in [2, 65535]"; return PIC_EINVAL; }
         if (cap * g->ncell < 2 * c->capacity[s]) { *err = "cell_capacity must be >= 2 x capacity / cells"; return PIC_EINVAL; }
         if (cap * g->ncell >= (1ll << 31)) { *err = "cells x cell_capacity must be < 2^31"; return PIC_EINVAL; }
         g->cap[s] = (int)cap;
+        // immigrant area: a quarter of the slots (>= 1); the rest keeps the cell's stayers
+        long long ci = (cap + 3) / 4;
+        if (ci < 1) ci = 1;
+        if (ci >= cap) ci = cap > 1 ? cap - 1 : 0;
+        g->cap_stay[s] = (int)(cap - ci);
         long long sc = c->capacity[s] / 16;
         if (sc < 65536) sc = 65536;
         if (sc > c->capacity[s] + 1) sc = c->capacity[s] + 1;
@@ -108,6 +115,7 @@ Layout make_layout(const pic_config* c, const Geometry& g) {
             for (int d = 0; d < 3; ++d) L.su[s][b][d] = take(off, 4 * ns);
             L.sid[s][b] = c->track_ids ? take(off, 4 * ns) : 0;
             L.scount[s][b] = take(off, 4 * nc);
+            L.sicount[s][b] = take(off, 4 * nc);
             const long long sp = g.spill_cap[s];
             L.sp_cell[s][b] = take(off, 4 * sp);
             for (int d = 0; d < 3; ++d) L.sp_o[s][b][d] = d < c->ndim ? take(off, 4 * sp) : 0;
@@ -398,6 +406,7 @@ extern "C" int pic_init(const pic_config* cfg, void* device_arena, size_t arena_
     a.ndim = c.ndim;
     for (int s = 0; s < c.nspecies; ++s) {
         a.cap[s] = g.cap[s];
+        a.cap_stay[s] = g.cap_stay[s];
         a.spill_cap[s] = g.spill_cap[s];
         a.stage_n[s] = c.capacity[s];
         for (int b = 0; b < 2; ++b) {
@@ -410,6 +419,7 @@ extern "C" int pic_init(const pic_config* cfg, void* device_arena, size_t arena_
             }
             S.id = L.sid[s][b] ? at<int>(ctx, L.sid[s][b]) : nullptr;
             S.count = at<int>(ctx, L.scount[s][b]);
+            S.icount = at<int>(ctx, L.sicount[s][b]);
             S.scell = at<int>(ctx, L.sp_cell[s][b]);
             S.sid = L.sp_id[s][b] ? at<int>(ctx, L.sp_id[s][b]) : nullptr;
             S.sn = at<int>(ctx, L.sp_n[s][b]);
@@ -465,6 +475,7 @@ extern "C" int pic_load_species(pic_ctx* ctx, int s, const pic_species* sp, int6
     if (rc) {
         // undo: empty the species' slots
         CK(cudaMemsetAsync(ctx->args.slot[s][par].count, 0, 4 * ctx->geo.ncell, ctx->stream));
+        CK(cudaMemsetAsync(ctx->args.slot[s][par].icount, 0, 4 * ctx->geo.ncell, ctx->stream));
         CK(cudaMemsetAsync(ctx->args.slot[s][par].sn, 0, 4, ctx->stream));
         Ctl h;
         CK(cudaMemcpyAsync(&h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
@@ -678,17 +689,24 @@ extern "C" int pic_get_stats(pic_ctx* ctx, pic_stats* out) {
     CK(cudaMemcpyAsync(&h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     std::memset(out, 0, sizeof(*out));
-    std::vector<int> cnt((size_t)ctx->geo.ncell);
+    std::vector<int> cnt((size_t)ctx->geo.ncell), icnt((size_t)ctx->geo.ncell);
     for (int s = 0; s < ctx->cfg.nspecies; ++s) {
         const Slots& S = ctx->args.slot[s][h.parity];
         CK(cudaMemcpyAsync(cnt.data(), S.count, 4 * cnt.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(icnt.data(), S.icount, 4 * icnt.size(), cudaMemcpyDeviceToHost, ctx->stream));
         int sn = 0;
         CK(cudaMemcpyAsync(&sn, S.sn, 4, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
+        const int cs = ctx->geo.cap_stay[s], ci = ctx->geo.cap[s] - cs;
         long long tot = 0;
         int mx = 0;
-        for (int c : cnt) { tot += c < ctx->geo.cap[s] ? c : ctx->geo.cap[s]; mx = c > mx ? c : mx; }
-        out->particles[s] = tot + sn;
+        for (size_t c = 0; c < cnt.size(); ++c) {
+            const int a = cnt[c] < cs ? cnt[c] : cs, b = icnt[c] < ci ? icnt[c] : ci;
+            tot += a + b;
+            const int raw = cnt[c] + icnt[c];
+            mx = raw > mx ? raw : mx;
+        }
+        out->particles[s] = tot + (sn < ctx->geo.spill_cap[s] ? sn : ctx->geo.spill_cap[s]);
         out->max_cell[s] = mx;
         out->spilled[s] = sn;
         out->cell_capacity[s] = ctx->geo.cap[s];

@@ -159,14 +159,15 @@ __global__ void moments_init_kernel(Args a, int s) {
     const RunDev& R = a.runs[0];
     if (!R.sp[s].drag || !R.msum[0]) return;
     const Slots S = a.slot[s][a.ctl->parity];
-    const int cap = a.cap[s];
+    const int cap = a.cap[s], cs = a.cap_stay[s];
     const float ms = 1048576.0f;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
          c += (long long)gridDim.x * blockDim.x) {
-        const int n = min(S.count[c], cap);
+        const CellRange cr = cell_range(S, cap, cs, c);
+        const int n = cr.n;
         long long m[3] = {0, 0, 0};
         for (int i = 0; i < n; ++i)
-            for (int d = 0; d < 3; ++d) m[d] += __float2ll_rn(S.u[d][(size_t)c * cap + i] * ms);
+            for (int d = 0; d < 3; ++d) m[d] += __float2ll_rn(S.u[d][slot_of(c, cap, cs, cr.ns, i)] * ms);
         const long long lc = c - R.cell_off;
         for (int d = 0; d < 3; ++d) atomicAdd((unsigned long long*)&R.msum[d][lc], (unsigned long long)m[d]);
         atomicAdd(&R.mcnt[lc], n);

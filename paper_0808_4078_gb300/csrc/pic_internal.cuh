@@ -52,12 +52,16 @@ struct RunDev {
     SpeciesParams sp[PIC_NS];
 };
 
-// One species in one buffer.
+// One species in one buffer.  A cell's cap slots are a stay area [0, cap_stay), filled in order
+// by the warp that owns the cell (count = its fill), and an immigrant area [cap_stay, cap) that
+// particles arriving from other cells claim with an atomic counter (icount).  Counters may exceed
+// their area; readers clamp them (the excess went to the spill list).
 struct Slots {
     float* o[3];     // [ncell * cap] offsets (x, y[, z])
     float* u[3];     // [ncell * cap] momenta
     int* id;         // [ncell * cap] or null
-    int* count;      // [ncell]
+    int* count;      // [ncell] stay-area fill
+    int* icount;     // [ncell] immigrant-area fill
     // spill list (particles whose cell was full)
     int* scell;      // global cell index
     float* so[3];
@@ -96,6 +100,7 @@ struct Args {
     int ndim;
     Slots slot[PIC_NS][2];
     int cap[PIC_NS];             // slots per cell
+    int cap_stay[PIC_NS];        // of which the stay area
     int spill_cap[PIC_NS];
     long long ncell;             // total cells (all runs)
     double* partials;            // [nwork][8] field-energy partials of a diag step
@@ -129,6 +134,20 @@ __host__ __device__ inline Stage stage_of(const Args& a, int s, int par) {
     for (int d = 0; d < 3; ++d) t.u[d] = reinterpret_cast<float*>(b + 4 * n * (1 + a.ndim + d));
     t.id = reinterpret_cast<int*>(b + 4 * n * (4 + a.ndim));
     return t;
+}
+
+// Particles of cell c: n = stay part + immigrant part; element k lives in slot slot_of(k).
+struct CellRange {
+    int ns, n;
+};
+__device__ __forceinline__ CellRange cell_range(const Slots& S, int cap, int cap_stay, long long c) {
+    CellRange r;
+    r.ns = min(S.count[c], cap_stay);
+    r.n = r.ns + min(S.icount[c], cap - cap_stay);
+    return r;
+}
+__device__ __forceinline__ size_t slot_of(long long c, int cap, int cap_stay, int ns, int k) {
+    return (size_t)c * cap + (k < ns ? k : cap_stay + (k - ns));
 }
 
 __device__ __forceinline__ int wrapi(int i, int n) {

@@ -40,7 +40,8 @@ struct Smem {
     int MC[RN];                      // drag counts
     unsigned q[NW][QCAP];            // per-warp queue: species << 24 | tile cell << 16 | slot
     float stg[NW][STAGES][6][32];    // per-warp staged chunks: o0 o1 u0 u1 u2 id (by lane)
-    int cnt[PIC_NS][CELLS];          // particle counts of the tile's cells (current buffer)
+    int cnt[PIC_NS][CELLS];          // particles of the tile's cells (current buffer)
+    int cns[PIC_NS][CELLS];          // of which in the stay area
     double red[NW][6];
     unsigned long long kin[5];
     SpeciesParams sp[PIC_NS];
@@ -336,14 +337,19 @@ __device__ __forceinline__ void deposit_terms(const Add& add, const SpeciesParam
 }
 
 // ------------------------------------------------------------------ rebinning
-// Claim a slot of cell g in buffer D (or a spill entry) and store the particle there.
-__device__ __forceinline__ void put(const Slots& D, int cap, int spill_cap, int g, int pos, float ox,
-                                    float oy, float ux, float uy, float uz, int id, int* err) {
-    if (pos < cap) {
-        const size_t q = (size_t)g * cap + pos;
-        D.o[0][q] = ox; D.o[1][q] = oy;
-        D.u[0][q] = ux; D.u[1][q] = uy; D.u[2][q] = uz;
-        if (D.id) D.id[q] = id;
+__device__ __forceinline__ void store_slot(const Slots& D, size_t q, float ox, float oy, float ux,
+                                           float uy, float uz, int id) {
+    D.o[0][q] = ox; D.o[1][q] = oy;
+    D.u[0][q] = ux; D.u[1][q] = uy; D.u[2][q] = uz;
+    if (D.id) D.id[q] = id;
+}
+
+// Particle arriving in cell g of buffer D from elsewhere: claim an immigrant slot, else spill.
+__device__ __forceinline__ void put_imm(const Slots& D, int cap, int cap_stay, int spill_cap, int g,
+                                        float ox, float oy, float ux, float uy, float uz, int id, int* err) {
+    const int pi = atomicAdd(&D.icount[g], 1);
+    if (pi < cap - cap_stay) {
+        store_slot(D, (size_t)g * cap + cap_stay + pi, ox, oy, ux, uy, uz, id);
     } else {
         const int sp = atomicAdd(D.sn, 1);
         if (sp < spill_cap) {
@@ -371,9 +377,9 @@ __device__ __forceinline__ void drain(Smem& sm, const Args& a, const RunDev* Rp,
     const int lx = ci % TX, ly = ci / TX;
     const int cx = x0 + lx, cy = y0 + ly;
     const int g = Rp->cell_off + cy * nx + cx;
-    const int cap = a.cap[s];
+    const int cap = a.cap[s], cst = a.cap_stay[s];
     const Slots S = a.slot[s][par], D = a.slot[s][par ^ 1];
-    const size_t p = (size_t)g * cap + i;
+    const size_t p = slot_of(g, cap, cst, sm.cns[s][ci], i);
     const float ox = S.o[0][p], oy = S.o[1][p];
     const float u0x = S.u[0][p], u0y = S.u[1][p], u0z = S.u[2][p];
     const int id = S.id ? S.id[p] : 0;
@@ -385,7 +391,7 @@ __device__ __forceinline__ void drain(Smem& sm, const Args& a, const RunDev* Rp,
     if (r.bad) {
         // keep the particle where it was, unmoved; the sticky flag fails the run
         atomicOr(&a.ctl->err, ERR_BADPART);
-        put(D, cap, a.spill_cap[s], g, atomicAdd(&D.count[g], 1), ox, oy, u0x, u0y, u0z, id, &a.ctl->err);
+        put_imm(D, cap, cst, a.spill_cap[s], g, ox, oy, u0x, u0y, u0z, id, &a.ctl->err);
         return;
     }
     if (diag) kin_add(kacc, s, P.w, u0x, u0y, u0z, r.ux, r.uy, r.uz);
@@ -406,8 +412,7 @@ __device__ __forceinline__ void drain(Smem& sm, const Args& a, const RunDev* Rp,
     ncx = ncx < 0 ? ncx + nx : (ncx >= nx ? ncx - nx : ncx);
     ncy = ncy < 0 ? ncy + ny : (ncy >= ny ? ncy - ny : ncy);
     const int g1 = Rp->cell_off + ncy * nx + ncx;
-    put(D, cap, a.spill_cap[s], g1, atomicAdd(&D.count[g1], 1), r.nox, r.noy, r.ux, r.uy, r.uz, id,
-        &a.ctl->err);
+    put_imm(D, cap, cst, a.spill_cap[s], g1, r.nox, r.noy, r.ux, r.uy, r.uz, id, &a.ctl->err);
 }
 
 // Register sums of "stay" particles of the cell at region node n0 -> shared tile.
@@ -476,7 +481,10 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
     for (int i = tid; i < PIC_NS * CELLS; i += NT) {
         const int s = i / CELLS, ci = i - s * CELLS;
         const int g = Rp->cell_off + (y0 + ci / TX) * nx + (x0 + ci % TX);
-        sm.cnt[s][ci] = (s < a.nspecies && Rp->sp[s].active) ? min(a.slot[s][par].count[g], a.cap[s]) : 0;
+        CellRange cr{0, 0};
+        if (s < a.nspecies && Rp->sp[s].active) cr = cell_range(a.slot[s][par], a.cap[s], a.cap_stay[s], g);
+        sm.cnt[s][ci] = cr.n;
+        sm.cns[s][ci] = cr.ns;
     }
     __syncthreads();
 
@@ -515,7 +523,7 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
                 const int lx = c.ci % TX, ly = c.ci / TX;
                 const int g = Rp->cell_off + (y0 + ly) * nx + (x0 + lx);
                 const Slots S = a.slot[c.s][par];
-                const size_t q = (size_t)g * a.cap[c.s] + i;
+                const size_t q = slot_of(g, a.cap[c.s], a.cap_stay[c.s], sm.cns[c.s][c.ci], i);
                 cp_async4(&sm.stg[warp][st][0][lane], S.o[0] + q);
                 cp_async4(&sm.stg[warp][st][1][lane], S.o[1] + q);
                 cp_async4(&sm.stg[warp][st][2][lane], S.u[0] + q);
@@ -536,6 +544,7 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
     }
     int st = 0;
     int cur_ci = -1, n0 = 0, g = 0, nchunk = 0;
+    int seg_s = -1, seg_g = 0, wpos = 0;     // stay-area fill of the current (cell, species)
     CellCache cc;
     int acc[12];
 #pragma unroll
@@ -576,8 +585,15 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
         }
         const int s = pc.s;
         const SpeciesParams& P = sm.sp[s];
-        const int cap = a.cap[s];
+        const int cap = a.cap[s], cst = a.cap_stay[s];
         const Slots D = a.slot[s][par ^ 1];
+        if (pc.j == 0) {
+            // new (cell, species): record the previous one's stay count
+            if (seg_s >= 0 && lane == 0) a.slot[seg_s][par ^ 1].count[seg_g] = wpos;
+            seg_s = s;
+            seg_g = g;
+            wpos = 0;
+        }
         const int i = pc.j + lane;
         const bool act = i < sm.cnt[s][pc.ci];
         cp_async_wait<STAGES - 1>();
@@ -613,14 +629,14 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
             }
             if (diag) kin_add(kacc, s, P.w, ux, uy, uz, r.ux, r.uy, r.uz);
         }
-        // stayers keep their cell: append them to its slots in the other buffer
+        // stayers keep their cell: the next free places of its stay area in the other buffer
         const unsigned sm_ = __ballot_sync(FULL, stay);
-        int pos0 = 0;
-        if (lane == 0 && sm_) pos0 = atomicAdd(&D.count[g], __popc(sm_));
-        pos0 = __shfl_sync(FULL, pos0, 0);
-        if (stay)
-            put(D, cap, a.spill_cap[s], g, pos0 + __popc(sm_ & lt), r.nox, r.noy, r.ux, r.uy, r.uz,
-                id, &a.ctl->err);
+        if (stay) {
+            const int pos = wpos + __popc(sm_ & lt);
+            if (pos < cst) store_slot(D, (size_t)g * cap + pos, r.nox, r.noy, r.ux, r.uy, r.uz, id);
+            else put_imm(D, cap, cst, a.spill_cap[s], g, r.nox, r.noy, r.ux, r.uy, r.uz, id, &a.ctl->err);
+        }
+        wpos += __popc(sm_);
         const bool defer = act && !stay;
         const unsigned dm = __ballot_sync(FULL, defer);
         if (defer) sm.q[warp][qn + __popc(dm & lt)] = ((unsigned)s << 24) | ((unsigned)pc.ci << 16) | (unsigned)i;
@@ -644,6 +660,7 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
         st = (st + 1) % STAGES;
     }
     if (nchunk) flush_acc(sm, acc, n0, lane);
+    if (seg_s >= 0 && lane == 0) a.slot[seg_s][par ^ 1].count[seg_g] = wpos;
     cp_async_wait<0>();
     if (qn > 0) drain(sm, a, Rp, par, qn, lane, warp, x0, y0, diag, kacc);
     __syncwarp();
@@ -698,7 +715,7 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
         const Slots S = a.slot[s][par], D = a.slot[s][par ^ 1];
         const int ns = min(*S.sn, a.spill_cap[s]);
         const SpeciesParams P = Rp->sp[s];
-        const int cap = a.cap[s];
+        const int cap = a.cap[s], cst = a.cap_stay[s];
         for (int k = blockIdx.x * NT + threadIdx.x; k < ns; k += gridDim.x * NT) {
             const int g = S.scell[k];
             const int lc = g - Rp->cell_off;
@@ -711,7 +728,7 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
             const Pushed r = push_one(GlobalFields{Rp, cx, cy}, P, Rp, ox, oy, u0x, u0y, u0z, b0, b1, b2);
             if (r.bad) {
                 atomicOr(&a.ctl->err, ERR_BADPART);
-                put(D, cap, a.spill_cap[s], g, atomicAdd(&D.count[g], 1), ox, oy, u0x, u0y, u0z, id, &a.ctl->err);
+                put_imm(D, cap, cst, a.spill_cap[s], g, ox, oy, u0x, u0y, u0z, id, &a.ctl->err);
                 continue;
             }
             if (diag) {
@@ -740,8 +757,7 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
                 atomicAdd(&Rp->mcnt[l1], 1);
             }
             const int g1 = Rp->cell_off + l1;
-            put(D, cap, a.spill_cap[s], g1, atomicAdd(&D.count[g1], 1), r.nox, r.noy, r.ux, r.uy, r.uz,
-                id, &a.ctl->err);
+            put_imm(D, cap, cst, a.spill_cap[s], g1, r.nox, r.noy, r.ux, r.uy, r.uz, id, &a.ctl->err);
         }
     }
 }

@@ -220,3 +220,29 @@ def test_uniform_field_drift_and_gyration(pic):
     wrapped = (drift_cells - disp) / ny
     assert np.all(np.abs(wrapped - np.round(wrapped)) * ny < 2.5)
     eng.close()
+
+
+def test_bins_conserve_particles_and_overflow_is_exact(pic):
+    """Rebinning conserves every particle; with cell capacity just above the mean (4 slots of
+    immigrant area) particles overflow into the spill list and the run stays bitwise equal to
+    one with ample capacity."""
+    wl = _warm_crop(32, 8, seed=12)
+    out = []
+    for ccap in ((0, 0), (16, 16)):
+        eng = pic.Engine.from_workload(wl, track_ids=True, cell_capacity=ccap, sort_interval=4)
+        eng.step(24)
+        st = eng.stats()
+        assert st["particles"] == [s.n for s in wl.species], st
+        assert st["flags"] == 0
+        E, B, _ = eng.fields()
+        parts = []
+        for s in range(2):
+            cell, off, u, ids = eng.particles(s)
+            o = np.argsort(ids)
+            parts.append((cell[o], off[:, o], u[:, o]))
+        out.append((E, B, parts, st))
+        eng.close()
+    assert out[1][3]["max_cell"][1] > 12      # the tight run did use its immigrant area
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for (c, o, u), (c0, o0, u0) in zip(out[1][2], out[0][2]):
+        assert np.array_equal(c, c0) and np.array_equal(o, o0) and np.array_equal(u, u0)
