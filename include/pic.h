@@ -176,6 +176,18 @@ typedef struct pic_stats {
 /* Occupancy of the particle bins of the current buffer.  Synchronises. */
 int pic_get_stats(pic_ctx* ctx, pic_stats* out);
 
+/* Counting sort by cell, the binning primitive of the re-binning step, on caller device memory:
+ * cell[n] (device) holds each particle's cell in [0, ncell); writes start[ncell + 1] (device;
+ * start[c] = number of particles in cells below c) and order[n] (device; order[start[c] ..
+ * start[c+1]) are the indices of the particles of cell c, in no fixed order within a cell).
+ * Particles whose cell lies outside [0, ncell) are left out (start[ncell] counts the others).
+ * scratch: caller device memory of at least pic_bin_cells_scratch_bytes(ncell) bytes, 256-byte
+ * aligned, owned by the caller, not needed after the stream reaches the end of the call.
+ * Asynchronous on `stream` (a cudaStream_t); PIC_EINVAL on bad sizes or null pointers. */
+int pic_bin_cells_scratch_bytes(int32_t ncell, size_t* bytes_out);
+int pic_bin_cells(const int32_t* cell, int64_t n, int32_t ncell, int32_t* start, int32_t* order,
+                  void* scratch, size_t scratch_bytes, void* stream);
+
 /* Kernel launches issued so far by this context (graph replays count their kernel nodes). */
 int64_t pic_launch_count(const pic_ctx* ctx);
 

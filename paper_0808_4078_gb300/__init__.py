@@ -83,6 +83,8 @@ _SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "pic_kernel_times": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "pic_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(Stats)]),
+    "pic_bin_cells_scratch_bytes": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    "pic_bin_cells": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "pic_launch_count": (ctypes.c_int64, [_VP]),
     "pic_step_count": (ctypes.c_int64, [_VP]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
@@ -260,6 +262,24 @@ class Engine:
         for i, s in enumerate(wl.species):
             eng.load_species(i, s.q, s.m, s.w, s.nu, s.cell, s.offset, s.u)
         return eng
+
+
+def bin_cells(cell, ncell, stream=None):
+    """Counting sort by cell on the GPU (pic_bin_cells): cell is an int32 CUDA tensor; returns
+    (start[ncell + 1], order[n]) int32 CUDA tensors.  Scratch is a torch allocation."""
+    import torch
+    n = cell.numel()
+    nb = ctypes.c_size_t(0)
+    _check(lib().pic_bin_cells_scratch_bytes(ncell, ctypes.byref(nb)))
+    scratch = torch.empty(nb.value, dtype=torch.uint8, device=cell.device)
+    start = torch.empty(ncell + 1, dtype=torch.int32, device=cell.device)
+    order = torch.empty(max(n, 1), dtype=torch.int32, device=cell.device)
+    st = stream if stream is not None else torch.cuda.current_stream(cell.device)
+    _check(lib().pic_bin_cells(_VP(cell.data_ptr()), n, ncell, _VP(start.data_ptr()),
+                               _VP(order.data_ptr()), _VP(scratch.data_ptr()), nb.value,
+                               _VP(st.cuda_stream)))
+    st.synchronize()
+    return start, order[:n]
 
 
 def history_array(recs, key, comp=None):

@@ -222,7 +222,123 @@ __global__ void clear_next_kernel(Args a) {
     if (blockIdx.x == 0 && threadIdx.x < a.nspecies) *a.slot[threadIdx.x][nb].sn = 0;
 }
 
+// ------------------------------------------------------------------ standalone counting sort
+__global__ void __launch_bounds__(NT) zero_kernel(int* __restrict__ p, long long n) {
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) p[i] = 0;
+}
+
+// Histogram of cells with warp-aggregated atomics (lanes of equal cell add once).
+__global__ void __launch_bounds__(NT) cell_hist_kernel(const int* __restrict__ cell, long long n, int ncell,
+                                                       int* __restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    for (long long base = blockIdx.x * (long long)NT + (threadIdx.x & ~31); base < n; base += (long long)gridDim.x * NT) {
+        const long long p = base + lane;
+        int key = -1 - lane;
+        if (p < n) {
+            const int c = cell[p];
+            if (c >= 0 && c < ncell) key = c;
+        }
+        const unsigned peers = __match_any_sync(FULL, key);
+        if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&count[key], __popc(peers));
+    }
+}
+
+// Plain exclusive scan of count[0..n) into start (block sums into tmp).
+__global__ void __launch_bounds__(NT) plain_scan_blocks(const int* __restrict__ count, int* __restrict__ start,
+                                                        int* __restrict__ tmp, long long n) {
+    __shared__ int warp_sums[NT / 32];
+    const long long off = (long long)blockIdx.x * CHUNK + (long long)threadIdx.x * ITEMS;
+    int v[ITEMS];
+    int sum = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        v[i] = off + i < n ? count[off + i] : 0;
+        sum += v[i];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < NT / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane < NT / 32) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    int run = incl - sum + (warp > 0 ? warp_sums[warp - 1] : 0);
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        if (off + i < n) start[off + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == NT - 1) tmp[blockIdx.x] = warp_sums[NT / 32 - 1];
+}
+
+// start += block offsets; the cursors (count array reused) start at the cell starts.
+__global__ void __launch_bounds__(NT) scan_add_cursor(int* __restrict__ start, int* __restrict__ cursor,
+                                                      const int* __restrict__ tmp, long long n) {
+    const long long off = (long long)blockIdx.x * CHUNK;
+    const int add = tmp[blockIdx.x];
+    for (int i = threadIdx.x; i < CHUNK; i += NT) {
+        const long long k = off + i;
+        if (k < n) {
+            const int v = start[k] + add;
+            start[k] = v;
+            cursor[k] = v;
+        }
+    }
+}
+
+// Scatter particle indices to their cell's range (warp-aggregated cursor claims).
+__global__ void __launch_bounds__(NT) cell_scatter_kernel(const int* __restrict__ cell, long long n, int ncell,
+                                                          int* __restrict__ cursor, int* __restrict__ order) {
+    const int lane = threadIdx.x & 31;
+    for (long long base = blockIdx.x * (long long)NT + (threadIdx.x & ~31); base < n; base += (long long)gridDim.x * NT) {
+        const long long p = base + lane;
+        int key = -1 - lane;
+        if (p < n) {
+            const int c = cell[p];
+            if (c >= 0 && c < ncell) key = c;
+        }
+        const unsigned peers = __match_any_sync(FULL, key);
+        const int leader = __ffs(peers) - 1;
+        int pos = 0;
+        if (key >= 0 && lane == leader) pos = atomicAdd(&cursor[key], __popc(peers));
+        pos = __shfl_sync(FULL, pos, leader) + __popc(peers & ((1u << lane) - 1u));
+        if (key >= 0) order[pos] = (int)p;
+    }
+}
+
 }  // namespace
+
+// Scratch layout of the standalone counting sort: count/cursor [ncell] then block sums.
+size_t bin_cells_scratch_bytes(long long ncell) {
+    const long long nb = (ncell + CHUNK - 1) / CHUNK + 1;
+    return (size_t)((4 * (ncell + nb) + 255) / 256 * 256);
+}
+
+cudaError_t launch_bin_cells(const int* cell, long long n, int ncell, int* start, int* order, int* scratch,
+                             cudaStream_t st) {
+    int* count = scratch;
+    int* tmp = scratch + ncell;
+    const int nb = (int)((ncell + CHUNK - 1) / CHUNK);
+    zero_kernel<<<grid_for(ncell), NT, 0, st>>>(count, ncell);
+    if (n > 0) cell_hist_kernel<<<grid_for(n), NT, 0, st>>>(cell, n, ncell, count);
+    plain_scan_blocks<<<nb, NT, 0, st>>>(count, start, tmp, ncell);
+    scan_tmp<<<1, NT, 0, st>>>(tmp, nb, start + ncell, nullptr);
+    scan_add_cursor<<<nb, NT, 0, st>>>(start, count, tmp, ncell);
+    if (n > 0) cell_scatter_kernel<<<grid_for(n), NT, 0, st>>>(cell, n, ncell, count, order);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_bin(const Args& a, int s, long long n, bool with_ids, const int* gate, cudaStream_t st) {
     if (n == 0) return cudaSuccess;

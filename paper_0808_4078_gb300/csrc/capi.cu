@@ -715,6 +715,23 @@ extern "C" int pic_get_stats(pic_ctx* ctx, pic_stats* out) {
     return PIC_OK;
 }
 
+extern "C" int pic_bin_cells_scratch_bytes(int32_t ncell, size_t* bytes_out) {
+    if (ncell <= 0 || !bytes_out) return fail(nullptr, PIC_EINVAL, "ncell must be > 0 and bytes_out non-null");
+    *bytes_out = bin_cells_scratch_bytes(ncell);
+    return PIC_OK;
+}
+
+extern "C" int pic_bin_cells(const int32_t* cell, int64_t n, int32_t ncell, int32_t* start, int32_t* order,
+                             void* scratch, size_t scratch_bytes, void* stream) {
+    if (n < 0 || n >= (1ll << 31) || ncell <= 0) return fail(nullptr, PIC_EINVAL, "bad n or ncell");
+    if (!start || !scratch || (n > 0 && (!cell || !order))) return fail(nullptr, PIC_EINVAL, "null pointer");
+    if (scratch_bytes < bin_cells_scratch_bytes(ncell)) return fail(nullptr, PIC_ENOMEM, "scratch too small");
+    if (reinterpret_cast<uintptr_t>(scratch) & 255) return fail(nullptr, PIC_EINVAL, "scratch must be 256-byte aligned");
+    const cudaError_t e = launch_bin_cells(cell, n, ncell, start, order, (int*)scratch, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, "pic_bin_cells: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
 extern "C" int64_t pic_launch_count(const pic_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
 extern "C" int64_t pic_step_count(const pic_ctx* ctx) { return ctx ? ctx->host_step : -1; }

@@ -189,6 +189,10 @@ cudaError_t launch_bin(const Args& a, int species, long long n, bool with_ids, c
 cudaError_t launch_compact(const Args& a, int species, const int* gate, cudaStream_t s);
 cudaError_t launch_spill_gate(const Args& a, cudaStream_t s);
 cudaError_t launch_clear_current(const Args& a, int species, const int* gate, cudaStream_t s);
+// Standalone counting sort by cell (pic_bin_cells): scratch = count/cursor[ncell] + block sums.
+size_t bin_cells_scratch_bytes(long long ncell);
+cudaError_t launch_bin_cells(const int* cell, long long n, int ncell, int* start, int* order, int* scratch,
+                             cudaStream_t s);
 // Full re-sort of every species (compact, clear, bin) when any particle is in a spill list.
 cudaError_t launch_resort(const Args& a, cudaStream_t s, int* launches);
 cudaError_t launch_moments_init(const Args& a, int species, cudaStream_t s);
