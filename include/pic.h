@@ -188,6 +188,22 @@ int pic_bin_cells_scratch_bytes(int32_t ncell, size_t* bytes_out);
 int pic_bin_cells(const int32_t* cell, int64_t n, int32_t ncell, int32_t* start, int32_t* order,
                   void* scratch, size_t scratch_bytes, void* stream);
 
+/* Allocation-free variant of pic_bin_cells, for callers that cannot allocate device memory
+ * themselves: for example code embedded in a host application whose GPU memory belongs to
+ * another allocator it cannot reach, or a timing-critical loop where a cudaMalloc (which can
+ * synchronise the device) is not allowed.  The paper has no counterpart; this is a library
+ * convenience.  Inputs and outputs are the caller's, exactly as for pic_bin_cells; the scratch
+ * is a fixed array compiled into the library (PIC_BIN_NOALLOC_MAX_CELLS cells, about 4.2 MB),
+ * which every GPU that loads the library holds until the process exits.  ncell above the
+ * maximum returns PIC_EINVAL.  The first call on a device looks up that device's copy of the
+ * array (make it before any stream capture); later calls reuse it.  All calls share the one
+ * array: calls that may run at the same time on the GPU (different streams) race and must be
+ * ordered by the caller.  Each call clears the part of the array that must start at zero.
+ * Calls no cudaMalloc, cudaFree or other allocating routine.  Asynchronous on `stream`. */
+#define PIC_BIN_NOALLOC_MAX_CELLS (1 << 20)
+int pic_bin_cells_noalloc(const int32_t* cell, int64_t n, int32_t ncell, int32_t* start,
+                          int32_t* order, void* stream);
+
 /* Kernel launches issued so far by this context (graph replays count their kernel nodes). */
 int64_t pic_launch_count(const pic_ctx* ctx);
 

@@ -6,6 +6,9 @@
 // rebin every particle into the other buffer the same way, fused into the push.
 // Compaction (read-back): exclusive scan of the clamped counts, then each cell's particles are
 // copied to a dense array in cell order, followed by the spill list.
+#include <mutex>
+
+#include "../../include/pic.h"
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -338,6 +341,30 @@ cudaError_t launch_bin_cells(const int* cell, long long n, int ncell, int* start
     scan_add_cursor<<<nb, NT, 0, st>>>(start, count, tmp, ncell);
     if (n > 0) cell_scatter_kernel<<<grid_for(n), NT, 0, st>>>(cell, n, ncell, count, order);
     return cudaGetLastError();
+}
+
+// Scratch of the allocation-free counting sort: count/cursor for up to the maximum number of
+// cells, then the scan's block sums.  Device code could name it directly; host code only holds a
+// stand-in for it, so the entry point passes the device address found below.
+static __device__ __align__(256) int g_bin_scratch[PIC_BIN_NOALLOC_MAX_CELLS + PIC_BIN_NOALLOC_MAX_CELLS / 2048 + 64];
+
+// Device address of g_bin_scratch on the current device, looked up once per device.
+cudaError_t noalloc_bin_scratch(int** out) {
+    static std::mutex mu;
+    static int* addr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_bin_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = static_cast<int*>(p);
+    }
+    *out = addr[dev];
+    return cudaSuccess;
 }
 
 cudaError_t launch_bin(const Args& a, int s, long long n, bool with_ids, const int* gate, cudaStream_t st) {

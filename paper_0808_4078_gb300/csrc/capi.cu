@@ -732,6 +732,21 @@ extern "C" int pic_bin_cells(const int32_t* cell, int64_t n, int32_t ncell, int3
     return PIC_OK;
 }
 
+extern "C" int pic_bin_cells_noalloc(const int32_t* cell, int64_t n, int32_t ncell, int32_t* start,
+                                     int32_t* order, void* stream) {
+    if (n < 0 || n >= (1ll << 31) || ncell <= 0) return fail(nullptr, PIC_EINVAL, "bad n or ncell");
+    if (ncell > PIC_BIN_NOALLOC_MAX_CELLS)
+        return fail(nullptr, PIC_EINVAL, "ncell = %d exceeds PIC_BIN_NOALLOC_MAX_CELLS = %d", (int)ncell,
+                    (int)PIC_BIN_NOALLOC_MAX_CELLS);
+    if (!start || (n > 0 && (!cell || !order))) return fail(nullptr, PIC_EINVAL, "null pointer");
+    int* scratch = nullptr;
+    cudaError_t e = noalloc_bin_scratch(&scratch);
+    if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, "scratch lookup: %s", cudaGetErrorString(e));
+    e = launch_bin_cells(cell, n, ncell, start, order, scratch, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, "pic_bin_cells_noalloc: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
 extern "C" int64_t pic_launch_count(const pic_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
 extern "C" int64_t pic_step_count(const pic_ctx* ctx) { return ctx ? ctx->host_step : -1; }

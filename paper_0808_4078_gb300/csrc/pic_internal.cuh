@@ -193,6 +193,8 @@ cudaError_t launch_clear_current(const Args& a, int species, const int* gate, cu
 size_t bin_cells_scratch_bytes(long long ncell);
 cudaError_t launch_bin_cells(const int* cell, long long n, int ncell, int* start, int* order, int* scratch,
                              cudaStream_t s);
+// Device address of the fixed scratch array of pic_bin_cells_noalloc (current device).
+cudaError_t noalloc_bin_scratch(int** out);
 // Full re-sort of every species (compact, clear, bin) when any particle is in a spill list.
 cudaError_t launch_resort(const Args& a, cudaStream_t s, int* launches);
 cudaError_t launch_moments_init(const Args& a, int species, cudaStream_t s);
