@@ -115,6 +115,20 @@ int pic_required_bytes(const pic_config* cfg, size_t* bytes_out);
 int pic_init(const pic_config* cfg, void* device_arena, size_t arena_bytes, void* cuda_stream,
              pic_ctx** out);
 
+/* Batched scan: one context holding nruns independent 2D runs of different sizes that step
+ * together (one set of launches, one CUDA graph, for all runs).  run_dims[3*r .. 3*r+2] = nx, ny,
+ * nz of run r (nz ignored in 2D); run_capacity[PIC_MAX_SPECIES*r + s] = particle capacity of
+ * species s in run r.  cfg supplies everything else (ndim, dx, dy, dz, dt, nspecies,
+ * cell_capacity, sort_interval, diag_*, track_ids, flags, tiles); cfg->nx/ny/nz/capacity are
+ * not used.  Each run keeps its own fields, species parameters (q must agree across runs) and
+ * diagnostic history.  Same ownership and error rules as pic_required_bytes / pic_init. */
+int pic_required_bytes_batch(const pic_config* cfg, int nruns, const int32_t* run_dims,
+                             const int64_t* run_capacity, size_t* bytes_out);
+int pic_init_batch(const pic_config* cfg, int nruns, const int32_t* run_dims,
+                   const int64_t* run_capacity, void* device_arena, size_t arena_bytes,
+                   void* cuda_stream, pic_ctx** out);
+int pic_num_runs(const pic_ctx* ctx);
+
 /* Load n particles of species index s (0-based) from HOST arrays: cell[n] (linear index,
  * x fastest), offset[ndim*n] (component-major: all x offsets, then y, then z; each in [0,1)),
  * u[3*n] (component-major u_x, u_y, u_z).  Copies, validates (PIC_EBADPART on a bad value),
@@ -123,6 +137,9 @@ int pic_init(const pic_config* cfg, void* device_arena, size_t arena_bytes, void
  * the first step.  Synchronises the stream. */
 int pic_load_species(pic_ctx* ctx, int s, const pic_species* sp, int64_t n, const int32_t* cell,
                      const float* offset, const float* u);
+/* The same for run `run` of a batch (cell indices local to the run); pic_load_species = run 0. */
+int pic_load_species_run(pic_ctx* ctx, int run, int s, const pic_species* sp, int64_t n,
+                         const int32_t* cell, const float* offset, const float* u);
 
 /* Advance nsteps steps: gather + Boris + drag + move + Esirkepov deposit + re-binning of every
  * particle into its new cell, Yee update, a full counting sort every sort_interval steps when
@@ -134,17 +151,21 @@ int pic_sync(pic_ctx* ctx);
 
 /* Copy up to max_recs diagnostic records (oldest first) to out.  Synchronises. */
 int pic_diag(pic_ctx* ctx, pic_diag_rec* out, int max_recs, int* n_out);
+int pic_diag_run(pic_ctx* ctx, int run, pic_diag_rec* out, int max_recs, int* n_out);
 
 /* Copy species s to HOST arrays (any may be NULL): cell[n], offset[ndim*n], u[3*n], id[n]
  * (id requires track_ids).  Particles come in cell order (the order within a cell is not
  * fixed), then the spill list; n must equal the loaded count.  Synchronises. */
 int pic_get_particles(pic_ctx* ctx, int s, int32_t* cell, float* offset, float* u, int32_t* id,
                       int64_t n);
+int pic_get_particles_run(pic_ctx* ctx, int run, int s, int32_t* cell, float* offset, float* u,
+                          int32_t* id, int64_t n);
 
 /* Copy fields to HOST arrays (any may be NULL): E[3*ncell], B[3*ncell] component-major FP32;
  * J[3*ncell] int64 fixed point of the last step's current (J = value * 2^-shift, shift from
  * pic_fixed_point_shift); J needs PIC_FLAG_KEEP_J (PIC_ESTATE otherwise).  Synchronises. */
 int pic_get_fields(pic_ctx* ctx, float* E, float* B, int64_t* J);
+int pic_get_fields_run(pic_ctx* ctx, int run, float* E, float* B, int64_t* J);
 
 /* Overwrite E and B from HOST arrays (component-major FP32, 3*ncell each).  Test and restart
  * use.  Synchronises. */
@@ -160,6 +181,8 @@ int pic_fixed_point_shift(const pic_ctx* ctx, int* shift_out);
  * no window qualifies.  Synchronises. */
 int pic_fit_growth(pic_ctx* ctx, int width, double t_noise, double start_factor,
                    double end_factor, double* gamma_out, double* t0_out, double* t1_out);
+int pic_fit_growth_run(pic_ctx* ctx, int run, int width, double t_noise, double start_factor,
+                       double end_factor, double* gamma_out, double* t0_out, double* t1_out);
 
 /* Per-phase CUDA-event timings (PIC_FLAG_PROFILE).  Synchronises. */
 int pic_kernel_times(pic_ctx* ctx, pic_kernel_time* out, int max, int* n_out);

@@ -71,6 +71,20 @@ _SIGNATURES = {
     "pic_init": (ctypes.c_int, [ctypes.POINTER(Config), _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
     "pic_load_species": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(Species), ctypes.c_int64,
                                         _VP, _VP, _VP]),
+    "pic_required_bytes_batch": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, _VP, _VP,
+                                                ctypes.POINTER(ctypes.c_size_t)]),
+    "pic_init_batch": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, _VP, _VP, _VP, ctypes.c_size_t,
+                                      _VP, ctypes.POINTER(_VP)]),
+    "pic_num_runs": (ctypes.c_int, [_VP]),
+    "pic_load_species_run": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Species),
+                                            ctypes.c_int64, _VP, _VP, _VP]),
+    "pic_diag_run": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "pic_get_particles_run": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP,
+                                             ctypes.c_int64]),
+    "pic_get_fields_run": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+    "pic_fit_growth_run": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "pic_step": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pic_sync": (ctypes.c_int, [_VP]),
     "pic_diag": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
@@ -124,11 +138,13 @@ def required_bytes(cfg: Config) -> int:
 
 
 class Engine:
-    """One PIC run on one GPU.  Arena and stream come from PyTorch."""
+    """One PIC run, or a batch of independent runs (``runs=``), on one GPU.  Arena and stream
+    come from PyTorch.  runs: list of (nx, ny, nz, (capacity_species0, capacity_species1))."""
 
-    def __init__(self, ndim, nx, ny, nz=1, dx=0.1, dy=None, dz=None, dt=0.05, capacity=(0, 0),
+    def __init__(self, ndim, nx=16, ny=16, nz=1, dx=0.1, dy=None, dz=None, dt=0.05, capacity=(0, 0),
                  nspecies=2, sort_interval=8, diag_interval=1, diag_capacity=4096,
-                 track_ids=False, flags=0, device="cuda", stream=None, cell_capacity=(0, 0)):
+                 track_ids=False, flags=0, device="cuda", stream=None, cell_capacity=(0, 0),
+                 runs=None):
         import torch
         self._torch = torch
         if not torch.cuda.is_available():
@@ -138,16 +154,31 @@ class Engine:
         self.cfg = Config(ndim, nx, ny, nz if ndim == 3 else 1, dx, dx if dy is None else dy,
                           dx if dz is None else dz, dt, nspecies, cap, ccap, sort_interval,
                           diag_interval, diag_capacity, int(bool(track_ids)), flags, 0, 0, 0)
-        self.nbytes = required_bytes(self.cfg)
+        if runs is None:
+            runs = [(nx, ny, nz if ndim == 3 else 1, tuple(capacity))]
+        self.runs = [(int(a), int(b), int(c) if ndim == 3 else 1, tuple(int(x) for x in k))
+                     for a, b, c, k in runs]
+        nr = len(self.runs)
+        self._dims = np.array([[a, b, c] for a, b, c, _ in self.runs], dtype=np.int32).reshape(-1)
+        capa = np.zeros((nr, PIC_MAX_SPECIES), dtype=np.int64)
+        for r, (_, _, _, k) in enumerate(self.runs):
+            capa[r, :len(k)] = k[:PIC_MAX_SPECIES]
+        self._caps = capa.reshape(-1)
+        n = ctypes.c_size_t(0)
+        _check(lib().pic_required_bytes_batch(ctypes.byref(self.cfg), nr, _ptr(self._dims),
+                                              _ptr(self._caps), ctypes.byref(n)))
+        self.nbytes = n.value
         self.device = torch.device(device)
         self.arena = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
         self._ctx = _VP()
         with torch.cuda.device(self.device):
-            _check(lib().pic_init(ctypes.byref(self.cfg), _VP(self.arena.data_ptr()), self.nbytes,
-                                  _VP(self.stream.cuda_stream), ctypes.byref(self._ctx)))
-        self.loaded = [0] * PIC_MAX_SPECIES
-        self.ncell = nx * ny * (nz if ndim == 3 else 1)
+            _check(lib().pic_init_batch(ctypes.byref(self.cfg), nr, _ptr(self._dims), _ptr(self._caps),
+                                        _VP(self.arena.data_ptr()), self.nbytes,
+                                        _VP(self.stream.cuda_stream), ctypes.byref(self._ctx)))
+        self.loaded = [[0] * PIC_MAX_SPECIES for _ in range(nr)]
+        self.ncells = [a * b * c for a, b, c, _ in self.runs]
+        self.ncell = self.ncells[0]
 
     # -------------------------------------------------------------- lifecycle
     def close(self):
@@ -168,16 +199,16 @@ class Engine:
         self.close()
 
     # -------------------------------------------------------------- calls
-    def load_species(self, s, q, m, w, nu, cell, offset, u):
+    def load_species(self, s, q, m, w, nu, cell, offset, u, run=0):
         cell = np.ascontiguousarray(cell, dtype=np.int32)
         offset = np.ascontiguousarray(offset, dtype=np.float32)
         u = np.ascontiguousarray(u, dtype=np.float32)
         n = cell.shape[0]
         assert offset.shape == (self.cfg.ndim, n) and u.shape == (3, n)
         sp = Species(q, m, w, nu)
-        _check(lib().pic_load_species(self._ctx, s, ctypes.byref(sp), n, _ptr(cell), _ptr(offset),
-                                      _ptr(u)), self._ctx)
-        self.loaded[s] = n
+        _check(lib().pic_load_species_run(self._ctx, run, s, ctypes.byref(sp), n, _ptr(cell),
+                                          _ptr(offset), _ptr(u)), self._ctx)
+        self.loaded[run][s] = n
 
     def step(self, n=1):
         _check(lib().pic_step(self._ctx, int(n)), self._ctx)
@@ -185,33 +216,34 @@ class Engine:
     def sync(self):
         _check(lib().pic_sync(self._ctx), self._ctx)
 
-    def diag(self, max_recs=None):
+    def diag(self, max_recs=None, run=0):
         cap = self.cfg.diag_capacity if max_recs is None else max_recs
         buf = (DiagRec * cap)()
         n = ctypes.c_int(0)
-        _check(lib().pic_diag(self._ctx, ctypes.cast(buf, _VP), cap, ctypes.byref(n)), self._ctx)
+        _check(lib().pic_diag_run(self._ctx, run, ctypes.cast(buf, _VP), cap, ctypes.byref(n)),
+               self._ctx)
         out = []
         for r in buf[:n.value]:
             out.append(dict(step=r.step, t=r.t, WE=list(r.WE), WB=list(r.WB), Ekin=list(r.Ekin),
                             P=list(r.P), flags=r.flags))
         return out
 
-    def particles(self, s):
-        n = self.loaded[s]
+    def particles(self, s, run=0):
+        n = self.loaded[run][s]
         cell = np.empty(n, np.int32)
         off = np.empty((self.cfg.ndim, n), np.float32)
         u = np.empty((3, n), np.float32)
         ids = np.empty(n, np.int32) if self.cfg.track_ids else None
-        _check(lib().pic_get_particles(self._ctx, s, _ptr(cell), _ptr(off), _ptr(u), _ptr(ids), n),
-               self._ctx)
+        _check(lib().pic_get_particles_run(self._ctx, run, s, _ptr(cell), _ptr(off), _ptr(u),
+                                           _ptr(ids), n), self._ctx)
         return cell, off, u, ids
 
-    def fields(self, with_J=False):
-        shape = (3, self.ncell)
+    def fields(self, with_J=False, run=0):
+        shape = (3, self.ncells[run])
         E = np.empty(shape, np.float32)
         B = np.empty(shape, np.float32)
         J = np.empty(shape, np.int64) if with_J else None
-        _check(lib().pic_get_fields(self._ctx, _ptr(E), _ptr(B), _ptr(J)), self._ctx)
+        _check(lib().pic_get_fields_run(self._ctx, run, _ptr(E), _ptr(B), _ptr(J)), self._ctx)
         return E, B, J
 
     def set_fields(self, E=None, B=None):
@@ -224,11 +256,12 @@ class Engine:
         _check(lib().pic_fixed_point_shift(self._ctx, ctypes.byref(s)), self._ctx)
         return s.value
 
-    def fit_growth(self, width=60, t_noise=2.0, start_factor=10.0, end_factor=1.0 / 30.0):
+    def fit_growth(self, width=60, t_noise=2.0, start_factor=10.0, end_factor=1.0 / 30.0, run=0):
         g, t0, t1 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         ef = -1.0 if end_factor is None else end_factor
-        _check(lib().pic_fit_growth(self._ctx, width, t_noise, start_factor, ef, ctypes.byref(g),
-                                    ctypes.byref(t0), ctypes.byref(t1)), self._ctx)
+        _check(lib().pic_fit_growth_run(self._ctx, run, width, t_noise, start_factor, ef,
+                                        ctypes.byref(g), ctypes.byref(t0), ctypes.byref(t1)),
+               self._ctx)
         return g.value, t0.value, t1.value
 
     def kernel_times(self):
@@ -256,11 +289,22 @@ class Engine:
     @classmethod
     def from_workload(cls, wl, **kw):
         """Engine sized for a pic_inputs.Workload, with its species loaded."""
-        cap = [s.n for s in wl.species] + [0] * (PIC_MAX_SPECIES - len(wl.species))
-        eng = cls(wl.ndim, wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, wl.dz, wl.dt, capacity=cap,
-                  nspecies=len(wl.species), **kw)
-        for i, s in enumerate(wl.species):
-            eng.load_species(i, s.q, s.m, s.w, s.nu, s.cell, s.offset, s.u)
+        return cls.from_workloads([wl], **kw)
+
+    @classmethod
+    def from_workloads(cls, wls, **kw):
+        """One batched engine holding every workload as a run (same ndim, dx, dt, species)."""
+        w0 = wls[0]
+        runs = []
+        for wl in wls:
+            assert (wl.ndim, wl.dx, wl.dt, len(wl.species)) == (w0.ndim, w0.dx, w0.dt, len(w0.species))
+            cap = [s.n for s in wl.species] + [0] * (PIC_MAX_SPECIES - len(wl.species))
+            runs.append((wl.nx, wl.ny, wl.nz, tuple(cap)))
+        eng = cls(w0.ndim, dx=w0.dx, dy=w0.dy, dz=w0.dz, dt=w0.dt, nspecies=len(w0.species),
+                  runs=runs, **kw)
+        for r, wl in enumerate(wls):
+            for i, s in enumerate(wl.species):
+                eng.load_species(i, s.q, s.m, s.w, s.nu, s.cell, s.offset, s.u, run=r)
         return eng
 
 

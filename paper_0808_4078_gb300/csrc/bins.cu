@@ -25,7 +25,8 @@ int grid_for(long long n) {
     return (int)(g < 1 ? 1 : g);
 }
 
-__global__ void __launch_bounds__(NT) bin_kernel(Args a, int s, long long n, bool with_ids, const int* gate) {
+__global__ void __launch_bounds__(NT) bin_kernel(Args a, int s, long long n, bool with_ids, long long cell_base,
+                                                 long long ncell_lim, const int* gate) {
     if (gate && *gate == 0) return;
     const int par = a.ctl->parity;
     const Slots S = a.slot[s][par];
@@ -33,8 +34,9 @@ __global__ void __launch_bounds__(NT) bin_kernel(Args a, int s, long long n, boo
     const int cap = a.cap[s];
     if (n < 0) n = a.ctl->staged[s];   // after a compaction
     for (long long p = blockIdx.x * (long long)NT + threadIdx.x; p < n; p += (long long)gridDim.x * NT) {
-        const int c = T.cell[p];
-        bool ok = c >= 0 && c < a.ncell;
+        const int cl = T.cell[p];
+        bool ok = cl >= 0 && cl < ncell_lim;
+        const long long c = cell_base + cl;
         float ov[3] = {0.f, 0.f, 0.f};
         for (int d = 0; d < a.ndim; ++d) {
             ov[d] = T.o[d][p];
@@ -58,7 +60,7 @@ __global__ void __launch_bounds__(NT) bin_kernel(Args a, int s, long long n, boo
         } else {
             const int sp = atomicAdd(S.sn, 1);
             if (sp < a.spill_cap[s]) {
-                S.scell[sp] = c;
+                S.scell[sp] = (int)c;
                 for (int d = 0; d < a.ndim; ++d) S.so[d][sp] = ov[d];
                 for (int d = 0; d < 3; ++d) S.su[d][sp] = uv[d];
                 if (S.sid) S.sid[sp] = id;
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(NT) bin_kernel(Args a, int s, long long n, boo
 }
 
 // Exclusive scan of the particles per cell (both slot areas) into start, block sums into tmp.
-__global__ void __launch_bounds__(NT) scan_blocks(Args a, int s, int* __restrict__ start,
+__global__ void __launch_bounds__(NT) scan_blocks(Args a, int s, long long c0, int* __restrict__ start,
                                                   int* __restrict__ tmp, long long n, const int* gate) {
     if (gate && *gate == 0) return;
     const Slots S = a.slot[s][a.ctl->parity];
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(NT) scan_blocks(Args a, int s, int* __restrict
     int sum = 0;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        v[i] = off + i < n ? cell_range(S, cap, cs, off + i).n : 0;
+        v[i] = off + i < n ? cell_range(S, cap, cs, c0 + off + i).n : 0;
         sum += v[i];
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -162,9 +164,11 @@ __global__ void __launch_bounds__(NT) scan_add(int* __restrict__ start, const in
     }
 }
 
-// One thread per cell: copy its slots to the staging arrays at start[c] ... in cell order, with
-// the cell index; the spill list follows at start[ncell].
-__global__ void __launch_bounds__(NT) compact_kernel(Args a, int s, const int* gate) {
+// One thread per cell of [c0, c0 + nc): copy its slots to the staging arrays at start[c - c0] ...
+// in cell order, with the cell index minus cell_base; the spill entries of those cells follow
+// at start[nc] (their order is not fixed).
+__global__ void __launch_bounds__(NT) compact_kernel(Args a, int s, long long c0, long long nc,
+                                                     long long cell_base, const int* gate) {
     if (gate && *gate == 0) return;
     const int par = a.ctl->parity;
     const Slots S = a.slot[s][par];
@@ -172,26 +176,38 @@ __global__ void __launch_bounds__(NT) compact_kernel(Args a, int s, const int* g
     const int cap = a.cap[s];
     const int* __restrict__ start = a.start;
     const int cs = a.cap_stay[s];
-    for (long long c = blockIdx.x * (long long)NT + threadIdx.x; c < a.ncell; c += (long long)gridDim.x * NT) {
+    for (long long k = blockIdx.x * (long long)NT + threadIdx.x; k < nc; k += (long long)gridDim.x * NT) {
+        const long long c = c0 + k;
         const CellRange cr = cell_range(S, cap, cs, c);
-        const int b = start[c];
+        const int b = start[k];
         for (int i = 0; i < cr.n; ++i) {
             const size_t q = slot_of(c, cap, cs, cr.ns, i);
-            T.cell[b + i] = (int)c;
+            T.cell[b + i] = (int)(c - cell_base);
             for (int d = 0; d < a.ndim; ++d) T.o[d][b + i] = S.o[d][q];
             for (int d = 0; d < 3; ++d) T.u[d][b + i] = S.u[d][q];
             T.id[b + i] = S.id ? S.id[q] : 0;
         }
     }
     const int ns = min(*S.sn, a.spill_cap[s]);
-    const int b = start[a.ncell];
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->staged[s] = b + ns;
     for (int k = blockIdx.x * NT + threadIdx.x; k < ns; k += gridDim.x * NT) {
-        T.cell[b + k] = S.scell[k];
-        for (int d = 0; d < a.ndim; ++d) T.o[d][b + k] = S.so[d][k];
-        for (int d = 0; d < 3; ++d) T.u[d][b + k] = S.su[d][k];
-        T.id[b + k] = S.sid ? S.sid[k] : 0;
+        const long long c = S.scell[k];
+        if (c < c0 || c >= c0 + nc) continue;
+        const int b = start[nc] + atomicAdd(&a.ctl->staged[s], 1);
+        T.cell[b] = (int)(c - cell_base);
+        for (int d = 0; d < a.ndim; ++d) T.o[d][b] = S.so[d][k];
+        for (int d = 0; d < 3; ++d) T.u[d][b] = S.su[d][k];
+        T.id[b] = S.sid ? S.sid[k] : 0;
     }
+}
+
+// After a compaction: staged count = slot particles + the spill entries appended.
+__global__ void staged_total_kernel(Args a, int s, long long nc, const int* gate) {
+    if (gate && *gate == 0) return;
+    a.ctl->staged[s] += a.start[nc];
+}
+__global__ void staged_zero_kernel(Args a, int s, const int* gate) {
+    if (gate && *gate == 0) return;
+    a.ctl->staged[s] = 0;
 }
 
 // Gate of the periodic re-sort: 1 if any species has spilled particles in the current buffer.
@@ -367,20 +383,23 @@ cudaError_t noalloc_bin_scratch(int** out) {
     return cudaSuccess;
 }
 
-cudaError_t launch_bin(const Args& a, int s, long long n, bool with_ids, const int* gate, cudaStream_t st) {
+cudaError_t launch_bin(const Args& a, int s, long long n, bool with_ids, long long cell_base,
+                       long long ncell_lim, const int* gate, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     const int g = n > 0 ? grid_for(n) : 152 * 16;
-    bin_kernel<<<g, NT, 0, st>>>(a, s, n, with_ids, gate);
+    bin_kernel<<<g, NT, 0, st>>>(a, s, n, with_ids, cell_base, ncell_lim, gate);
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact(const Args& a, int s, const int* gate, cudaStream_t st) {
-    const long long n = a.ncell;
-    const int nb = (int)((n + CHUNK - 1) / CHUNK);
-    scan_blocks<<<nb, NT, 0, st>>>(a, s, a.start, a.scan_tmp, n, gate);
-    scan_tmp<<<1, NT, 0, st>>>(a.scan_tmp, nb, a.start + n, gate);
-    scan_add<<<nb, NT, 0, st>>>(a.start, a.scan_tmp, n, gate);
-    compact_kernel<<<grid_for(n), NT, 0, st>>>(a, s, gate);
+cudaError_t launch_compact(const Args& a, int s, long long c0, long long nc, long long cell_base,
+                           const int* gate, cudaStream_t st) {
+    const int nb = (int)((nc + CHUNK - 1) / CHUNK);
+    scan_blocks<<<nb, NT, 0, st>>>(a, s, c0, a.start, a.scan_tmp, nc, gate);
+    scan_tmp<<<1, NT, 0, st>>>(a.scan_tmp, nb, a.start + nc, gate);
+    scan_add<<<nb, NT, 0, st>>>(a.start, a.scan_tmp, nc, gate);
+    staged_zero_kernel<<<1, 1, 0, st>>>(a, s, gate);
+    compact_kernel<<<grid_for(nc), NT, 0, st>>>(a, s, c0, nc, cell_base, gate);
+    staged_total_kernel<<<1, 1, 0, st>>>(a, s, nc, gate);
     return cudaGetLastError();
 }
 
@@ -409,6 +428,8 @@ cudaError_t preload_bins() {
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, spill_gate_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, clear_current_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, clear_next_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, staged_total_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, staged_zero_kernel);
     return e;
 }
 
@@ -416,12 +437,12 @@ cudaError_t launch_resort(const Args& a, cudaStream_t st, int* launches) {
     spill_gate_kernel<<<1, 1, 0, st>>>(a);
     int l = 1;
     for (int s = 0; s < a.nspecies; ++s) {
-        cudaError_t e = launch_compact(a, s, a.gate, st);
+        cudaError_t e = launch_compact(a, s, 0, a.ncell, 0, a.gate, st);
         if (e != cudaSuccess) return e;
         clear_current_kernel<<<grid_for(a.ncell), NT, 0, st>>>(a, s, a.gate);
         // n < 0: the bin kernel takes the staged count recorded by the compaction
-        bin_kernel<<<152 * 16, NT, 0, st>>>(a, s, -1, true, a.gate);
-        l += 6;
+        bin_kernel<<<152 * 16, NT, 0, st>>>(a, s, -1, true, 0, a.ncell, a.gate);
+        l += 8;
     }
     *launches += l;
     return cudaGetLastError();

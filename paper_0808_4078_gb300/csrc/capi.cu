@@ -1,5 +1,11 @@
 // capi.cu -- the C ABI of libpic (include/pic.h): context, arena carving, particle loading,
-// step scheduling (CUDA graph of one sort period), diagnostics, growth fit, profiling.
+// step scheduling (a CUDA graph of sort_interval steps), diagnostics, growth fit, profiling.
+//
+// A context holds one or more independent runs (a batch): each run has its own grid, fields,
+// species parameters and diagnostic history; particles of all runs share the binned slot
+// arrays (global cell index = run cell offset + local cell), and every kernel covers all runs
+// through the (run, tile) work list, so a batch steps with the same launches as a single run.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -23,15 +29,31 @@ thread_local std::string g_init_error;
 enum Phase { PH_PUSH = 0, PH_YEE, PH_FINAL, PH_SORT, PH_N };
 const char* kPhaseName[PH_N] = {"push_deposit", "yee", "finalize", "sort"};
 
+struct RunGeo {
+    int nx, ny, nz;
+    int ntx, nty, ntz;
+    long long ncell, ntiles;
+    long long cell_off, work_off;
+    long long capacity[PIC_NS];
+};
+
+struct Geometry {
+    int tx, ty, tz;
+    long long ncell, nwork;
+    int cap[PIC_NS];          // slots per cell per species
+    int cap_stay[PIC_NS];     // of which the stay area
+    int spill_cap[PIC_NS];
+    long long capacity[PIC_NS];   // particles per species, all runs
+    std::vector<RunGeo> runs;
+};
+
 struct Layout {
     size_t total = 0;
-    size_t ctl, runs, work;
-    // per species, per buffer: slot arrays o[0..2], u[0..2], id; count; spill arrays
+    size_t ctl, runs, work, work_off, kin;
     size_t so[PIC_NS][2][3], su[PIC_NS][2][3], sid[PIC_NS][2], scount[PIC_NS][2], sicount[PIC_NS][2];
     size_t sp_cell[PIC_NS][2], sp_o[PIC_NS][2][3], sp_u[PIC_NS][2][3], sp_id[PIC_NS][2], sp_n[PIC_NS][2];
     size_t slot_region[PIC_NS][2];   // start of the contiguous slot arrays (staging view)
-    size_t E[3], B[3], J[3], Jlast[3];
-    size_t msum[3], mcnt, ubar[3];
+    std::vector<size_t> E[3], B[3], J[3], Jlast[3], msum[3], mcnt, ubar[3];   // per run
     size_t start, scan_tmp, gate;
     size_t partials, hist, fit;
 };
@@ -43,47 +65,57 @@ size_t take(size_t& off, size_t bytes) {
     return at;
 }
 
-struct Geometry {
-    int tx, ty, tz;
-    int ntx, nty, ntz;
-    long long ncell, ntiles;
-    int cap[PIC_NS];          // slots per cell per species
-    int cap_stay[PIC_NS];     // of which the stay area
-    int spill_cap[PIC_NS];
-};
-
-int geometry(const pic_config* c, Geometry* g, std::string* err) {
+int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t* caps, Geometry* g,
+             std::string* err) {
     if (c->ndim != 2 && c->ndim != 3) { *err = "ndim must be 2 or 3"; return PIC_EINVAL; }
     if (c->ndim == 3 && !pic::has_push3d()) { *err = "3D push not available in this build"; return PIC_EINVAL; }
-    const int nz = c->ndim == 3 ? c->nz : 1;
+    if (nruns < 1 || nruns > 65536) { *err = "nruns must be in [1, 65536]"; return PIC_EINVAL; }
     g->tx = c->tile_x > 0 ? c->tile_x : 16;
     g->ty = c->tile_y > 0 ? c->tile_y : 16;
     g->tz = c->ndim == 3 ? (c->tile_z > 0 ? c->tile_z : 4) : 1;
     if (c->ndim == 2 && (g->tx != 16 || g->ty != 16)) { *err = "2D tiles are 16 x 16"; return PIC_EINVAL; }
-    if (c->nx <= 0 || c->ny <= 0 || nz <= 0) { *err = "grid sizes must be positive"; return PIC_EINVAL; }
-    if (c->nx % g->tx || c->ny % g->ty || nz % g->tz) { *err = "grid sizes must be multiples of the tile"; return PIC_EINVAL; }
-    g->ntx = c->nx / g->tx; g->nty = c->ny / g->ty; g->ntz = nz / g->tz;
-    g->ncell = (long long)c->nx * c->ny * nz;
-    g->ntiles = (long long)g->ntx * g->nty * g->ntz;
-    if (g->ncell >= (1ll << 31) - 1) { *err = "too many cells for int32 cell indices"; return PIC_EINVAL; }
     if (!(c->dx > 0 && c->dy > 0 && c->dt > 0) || (c->ndim == 3 && !(c->dz > 0))) { *err = "dx, dy, dz, dt must be > 0"; return PIC_EINVAL; }
-    double inv2 = 1.0 / (c->dx * c->dx) + 1.0 / (c->dy * c->dy) + (c->ndim == 3 ? 1.0 / (c->dz * c->dz) : 0.0);
+    const double inv2 = 1.0 / (c->dx * c->dx) + 1.0 / (c->dy * c->dy) + (c->ndim == 3 ? 1.0 / (c->dz * c->dz) : 0.0);
     if (c->dt * std::sqrt(inv2) >= 1.0) { *err = "dt violates the Yee Courant condition"; return PIC_EINVAL; }
     if (c->nspecies < 1 || c->nspecies > PIC_NS) { *err = "nspecies must be 1..2"; return PIC_EINVAL; }
-    for (int s = 0; s < c->nspecies; ++s)
-        if (c->capacity[s] < 0 || c->capacity[s] >= (1ll << 31)) { *err = "capacity must be in [0, 2^31)"; return PIC_EINVAL; }
     if (c->diag_interval < 0 || (c->diag_interval > 0 && c->diag_capacity < 1)) { *err = "diag_capacity must be >= 1"; return PIC_EINVAL; }
     if (c->sort_interval < 0) { *err = "sort_interval must be >= 0"; return PIC_EINVAL; }
+    g->runs.assign(nruns, RunGeo{});
+    g->ncell = 0;
+    g->nwork = 0;
+    for (int s = 0; s < PIC_NS; ++s) g->capacity[s] = 0;
+    for (int r = 0; r < nruns; ++r) {
+        RunGeo& R = g->runs[r];
+        R.nx = dims[3 * r];
+        R.ny = dims[3 * r + 1];
+        R.nz = c->ndim == 3 ? dims[3 * r + 2] : 1;
+        if (R.nx <= 0 || R.ny <= 0 || R.nz <= 0) { *err = "grid sizes must be positive"; return PIC_EINVAL; }
+        if (R.nx % g->tx || R.ny % g->ty || R.nz % g->tz) { *err = "grid sizes must be multiples of the tile"; return PIC_EINVAL; }
+        R.ntx = R.nx / g->tx; R.nty = R.ny / g->ty; R.ntz = R.nz / g->tz;
+        R.ncell = (long long)R.nx * R.ny * R.nz;
+        R.ntiles = (long long)R.ntx * R.nty * R.ntz;
+        R.cell_off = g->ncell;
+        R.work_off = g->nwork;
+        g->ncell += R.ncell;
+        g->nwork += R.ntiles;
+        for (int s = 0; s < PIC_NS; ++s) {
+            R.capacity[s] = s < c->nspecies ? caps[PIC_NS * r + s] : 0;
+            if (R.capacity[s] < 0) { *err = "capacity must be >= 0"; return PIC_EINVAL; }
+            g->capacity[s] += R.capacity[s];
+        }
+    }
+    if (g->ncell >= (1ll << 31) - 1) { *err = "too many cells for int32 cell indices"; return PIC_EINVAL; }
     for (int s = 0; s < PIC_NS; ++s) {
         g->cap[s] = 0;
         g->cap_stay[s] = 0;
         g->spill_cap[s] = 0;
         if (s >= c->nspecies) continue;
-        const long long mean = (c->capacity[s] + g->ncell - 1) / g->ncell;
+        if (g->capacity[s] >= (1ll << 31)) { *err = "capacity must be < 2^31 per species"; return PIC_EINVAL; }
+        const long long mean = (g->capacity[s] + g->ncell - 1) / g->ncell;
         long long cap = c->cell_capacity[s] > 0 ? c->cell_capacity[s] : ((4 * mean + 31) / 32) * 32;
         if (cap < 32 && c->cell_capacity[s] <= 0) cap = 32;
         if (cap < 2 || cap > 65535) { *err = "cell_capacity must be in [2, 65535]"; return PIC_EINVAL; }
-        if (cap * g->ncell < 2 * c->capacity[s]) { *err = "cell_capacity must be >= 2 x capacity / cells"; return PIC_EINVAL; }
+        if (cap * g->ncell < 2 * g->capacity[s]) { *err = "cell_capacity must be >= 2 x capacity / cells"; return PIC_EINVAL; }
         if (cap * g->ncell >= (1ll << 31)) { *err = "cells x cell_capacity must be < 2^31"; return PIC_EINVAL; }
         g->cap[s] = (int)cap;
         // immigrant area: a quarter of the slots (>= 1); the rest keeps the cell's stayers
@@ -91,9 +123,9 @@ int geometry(const pic_config* c, Geometry* g, std::string* err) {
         if (ci < 1) ci = 1;
         if (ci >= cap) ci = cap > 1 ? cap - 1 : 0;
         g->cap_stay[s] = (int)(cap - ci);
-        long long sc = c->capacity[s] / 16;
+        long long sc = g->capacity[s] / 16;
         if (sc < 65536) sc = 65536;
-        if (sc > c->capacity[s] + 1) sc = c->capacity[s] + 1;
+        if (sc > g->capacity[s] + 1) sc = g->capacity[s] + 1;
         g->spill_cap[s] = (int)sc;
     }
     return PIC_OK;
@@ -102,10 +134,13 @@ int geometry(const pic_config* c, Geometry* g, std::string* err) {
 Layout make_layout(const pic_config* c, const Geometry& g) {
     Layout L{};
     size_t off = 0;
+    const int nruns = (int)g.runs.size();
     const long long nc = g.ncell;
     L.ctl = take(off, sizeof(Ctl));
-    L.runs = take(off, sizeof(RunDev));
-    L.work = take(off, sizeof(int2) * g.ntiles);
+    L.runs = take(off, sizeof(RunDev) * nruns);
+    L.work = take(off, sizeof(int2) * g.nwork);
+    L.work_off = take(off, sizeof(int) * (nruns + 1));
+    L.kin = take(off, sizeof(long long) * nruns * PIC_NS * 4);
     for (int s = 0; s < c->nspecies; ++s)
         for (int b = 0; b < 2; ++b) {
             const long long ns = nc * g.cap[s];
@@ -123,18 +158,26 @@ Layout make_layout(const pic_config* c, const Geometry& g) {
             L.sp_id[s][b] = c->track_ids ? take(off, 4 * sp) : 0;
             L.sp_n[s][b] = take(off, 4);
         }
-    for (int d = 0; d < 3; ++d) L.E[d] = take(off, 4 * nc);
-    for (int d = 0; d < 3; ++d) L.B[d] = take(off, 4 * nc);
-    for (int d = 0; d < 3; ++d) L.J[d] = take(off, 8 * nc);
-    for (int d = 0; d < 3; ++d) L.Jlast[d] = (c->flags & PIC_FLAG_KEEP_J) ? take(off, 8 * nc) : 0;
-    for (int d = 0; d < 3; ++d) L.msum[d] = take(off, 8 * nc);
-    L.mcnt = take(off, 4 * nc);
-    for (int d = 0; d < 3; ++d) L.ubar[d] = take(off, 4 * nc);
+    for (int d = 0; d < 3; ++d) {
+        L.E[d].resize(nruns); L.B[d].resize(nruns); L.J[d].resize(nruns); L.Jlast[d].resize(nruns);
+        L.msum[d].resize(nruns); L.ubar[d].resize(nruns);
+    }
+    L.mcnt.resize(nruns);
+    for (int r = 0; r < nruns; ++r) {
+        const long long n = g.runs[r].ncell;
+        for (int d = 0; d < 3; ++d) L.E[d][r] = take(off, 4 * n);
+        for (int d = 0; d < 3; ++d) L.B[d][r] = take(off, 4 * n);
+        for (int d = 0; d < 3; ++d) L.J[d][r] = take(off, 8 * n);
+        for (int d = 0; d < 3; ++d) L.Jlast[d][r] = (c->flags & PIC_FLAG_KEEP_J) ? take(off, 8 * n) : 0;
+        for (int d = 0; d < 3; ++d) L.msum[d][r] = take(off, 8 * n);
+        L.mcnt[r] = take(off, 4 * n);
+        for (int d = 0; d < 3; ++d) L.ubar[d][r] = take(off, 4 * n);
+    }
     L.start = take(off, 4 * (nc + 1));
     L.scan_tmp = take(off, 4 * (nc / 2048 + 2));
     L.gate = take(off, 4);
-    L.partials = take(off, sizeof(double) * 8 * g.ntiles);
-    L.hist = take(off, sizeof(DiagRec) * (c->diag_interval > 0 ? c->diag_capacity : 1));
+    L.partials = take(off, sizeof(double) * 8 * g.nwork);
+    L.hist = take(off, sizeof(DiagRec) * nruns * (c->diag_interval > 0 ? c->diag_capacity : 1));
     L.fit = take(off, sizeof(double) * 4);
     L.total = (off + 255) & ~size_t(255);
     return L;
@@ -148,11 +191,13 @@ struct pic_ctx {
     Layout lay{};
     cudaStream_t stream = nullptr;
     char* arena = nullptr;
+    int nruns = 1;
     int sort_interval = 8;
-    RunDev run{};
+    std::vector<RunDev> runs;
     Args args{};
-    long long loaded[PIC_NS] = {0, 0};
+    std::vector<long long> loaded;      // [nruns][PIC_NS]
     double q[PIC_NS] = {0, 0};
+    bool q_set[PIC_NS] = {false, false};
     long long host_step = 0;
     long long launches = 0;
     std::string err;
@@ -189,8 +234,8 @@ int fail(pic_ctx* c, int code, const char* fmt, ...) {
 
 template <class T> T* at(pic_ctx* c, size_t off) { return reinterpret_cast<T*>(c->arena + off); }
 
-int upload_run(pic_ctx* ctx) {
-    CK(cudaMemcpyAsync(at<RunDev>(ctx, ctx->lay.runs), &ctx->run, sizeof(RunDev),
+int upload_runs(pic_ctx* ctx) {
+    CK(cudaMemcpyAsync(at<RunDev>(ctx, ctx->lay.runs), ctx->runs.data(), sizeof(RunDev) * ctx->nruns,
                        cudaMemcpyHostToDevice, ctx->stream));
     ctx->graph_dirty = true;
     return PIC_OK;
@@ -236,14 +281,14 @@ int launch_one_step(pic_ctx* ctx, long long step_index) {
     }
     {
         PhaseScope ps(ctx, PH_YEE);
-        CK(ctx->cfg.ndim == 2 ? launch_yee2d(a, &ctx->run, 1, ctx->stream)
-                              : launch_yee3d(a, &ctx->run, 1, ctx->stream));
-        ctx->launches += 3;
+        CK(ctx->cfg.ndim == 2 ? launch_yee2d(a, ctx->runs.data(), ctx->nruns, ctx->stream)
+                              : launch_yee3d(a, ctx->runs.data(), ctx->nruns, ctx->stream));
+        ctx->launches += ctx->cfg.ndim == 2 ? 3 : 3 * ctx->nruns;
     }
     {
         PhaseScope ps(ctx, PH_FINAL);
         CK(launch_finalize(a, ctx->stream));
-        ctx->launches += 1;
+        ctx->launches += 2;
     }
     if ((step_index + 1) % ctx->sort_interval == 0) {
         PhaseScope ps(ctx, PH_SORT);
@@ -276,10 +321,16 @@ int build_graph(pic_ctx* ctx) {
     return PIC_OK;
 }
 
+int read_ctl(pic_ctx* ctx, Ctl* h) {
+    CK(cudaMemcpyAsync(h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PIC_OK;
+}
+
 int device_flags(pic_ctx* ctx) {
     Ctl h;
-    CK(cudaMemcpyAsync(&h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    int rc = read_ctl(ctx, &h);
+    if (rc) return rc;
     if (h.err & ERR_BADPART) return fail(ctx, PIC_EBADPART, "device: non-finite or out-of-range particle");
     if (h.err & ERR_OVERFLOW) return fail(ctx, PIC_EOVERFLOW, "device: fixed-point headroom exceeded");
     if (h.err & ERR_TIMEOUT) return fail(ctx, PIC_ETIMEOUT, "device: bounded wait gave up");
@@ -287,26 +338,17 @@ int device_flags(pic_ctx* ctx) {
     return PIC_OK;
 }
 
-int current_parity(pic_ctx* ctx, int s, int* par) {
-    Ctl h;
-    CK(cudaMemcpyAsync(&h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    (void)s;
-    *par = h.parity;
-    return PIC_OK;
-}
-
-// Fixed-point shift S: every per-particle current term satisfies |term| * 2^S <= 2^21, so
-// 32 warp lanes sum without int32 overflow and one FFMA rounds it exactly.  A term is bounded
+// Fixed-point shift S of a run: every per-particle current term satisfies |term| * 2^S <= 2^21,
+// so 32 warp lanes sum without int32 overflow and one FFMA rounds it exactly.  A term is bounded
 // by |q| w max(dx/dt, dy/dt, dz/dt, 1) (|v| < c, CIC weights in [0, 1]).
-int choose_shift(const pic_ctx* ctx) {
+int choose_shift(const pic_ctx* ctx, const RunDev& R) {
     const pic_config& c = ctx->cfg;
     double vmax = std::fmax(c.dx / c.dt, c.dy / c.dt);
     if (c.ndim == 3) vmax = std::fmax(vmax, c.dz / c.dt);
     vmax = std::fmax(vmax, 1.0);
     double bound = 0.0;
     for (int s = 0; s < c.nspecies; ++s)
-        if (ctx->run.sp[s].active) bound = std::fmax(bound, std::fabs(ctx->q[s]) * ctx->run.sp[s].w * vmax);
+        if (R.sp[s].active) bound = std::fmax(bound, std::fabs(ctx->q[s]) * R.sp[s].w * vmax);
     if (bound <= 0) return 30;
     int S = (int)std::floor(std::log2(2097152.0 / bound));
     if (S > 40) S = 40;
@@ -314,42 +356,33 @@ int choose_shift(const pic_ctx* ctx) {
     return S;
 }
 
-void set_species_scales(pic_ctx* ctx) {
+void set_species_scales(pic_ctx* ctx, RunDev& R) {
     const pic_config& c = ctx->cfg;
-    const int S = ctx->run.shift;
-    const double two = std::ldexp(1.0, S);
+    R.shift = choose_shift(ctx, R);
+    const double two = std::ldexp(1.0, R.shift);
     for (int s = 0; s < c.nspecies; ++s) {
-        SpeciesParams& P = ctx->run.sp[s];
+        SpeciesParams& P = R.sp[s];
         if (!P.active) continue;
         const double qw = ctx->q[s] * (double)P.w;
         P.jx = (float)(-qw * (c.dx / c.dt) * two);
         P.jy = (float)(-qw * (c.dy / c.dt) * two);
         P.jz = c.ndim == 2 ? (float)(qw * two) : (float)(-qw * (c.dz / c.dt) * two);
     }
-    ctx->run.jscale = (float)std::ldexp(1.0, -S);
+    R.jscale = (float)std::ldexp(1.0, -R.shift);
 }
 
-}  // namespace
-
-// =============================================================================== C ABI
-
-extern "C" int pic_required_bytes(const pic_config* cfg, size_t* bytes_out) {
-    if (!cfg || !bytes_out) return fail(nullptr, PIC_EINVAL, "null argument");
-    Geometry g;
-    std::string err;
-    int rc = geometry(cfg, &g, &err);
-    if (rc != PIC_OK) return fail(nullptr, rc, "%s", err.c_str());
-    *bytes_out = make_layout(cfg, g).total;
+int check_run(pic_ctx* ctx, int run) {
+    if (run < 0 || run >= ctx->nruns) return fail(ctx, PIC_EINVAL, "run %d out of range [0, %d)", run, ctx->nruns);
     return PIC_OK;
 }
 
-extern "C" int pic_init(const pic_config* cfg, void* device_arena, size_t arena_bytes,
-                        void* cuda_stream, pic_ctx** out) {
-    if (!cfg || !out) return fail(nullptr, PIC_EINVAL, "null argument");
+int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int64_t* caps,
+                void* device_arena, size_t arena_bytes, void* cuda_stream, pic_ctx** out) {
+    if (!cfg || !out || !dims || !caps) return fail(nullptr, PIC_EINVAL, "null argument");
     *out = nullptr;
     Geometry g;
     std::string err;
-    int rc = geometry(cfg, &g, &err);
+    int rc = geometry(cfg, nruns, dims, caps, &g, &err);
     if (rc != PIC_OK) return fail(nullptr, rc, "%s", err.c_str());
     Layout L = make_layout(cfg, g);
     if (!device_arena) return fail(nullptr, PIC_EINVAL, "null arena");
@@ -358,57 +391,67 @@ extern "C" int pic_init(const pic_config* cfg, void* device_arena, size_t arena_
     pic_ctx* ctx = new (std::nothrow) pic_ctx;
     if (!ctx) return fail(nullptr, PIC_ENOMEM, "host allocation failed");
     ctx->cfg = *cfg;
-    if (ctx->cfg.ndim == 2) { ctx->cfg.nz = 1; ctx->cfg.dz = ctx->cfg.dx; }
+    if (ctx->cfg.ndim == 2) ctx->cfg.dz = ctx->cfg.dx;
     ctx->geo = g;
     ctx->lay = L;
+    ctx->nruns = nruns;
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->arena = (char*)device_arena;
     ctx->sort_interval = cfg->sort_interval > 0 ? cfg->sort_interval : 8;
+    ctx->loaded.assign((size_t)nruns * PIC_NS, 0);
 
     auto bail = [&](int code) { g_init_error = ctx->err; delete ctx; return code; };
 #define CKI(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { fail(ctx, PIC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); return bail(PIC_ECUDA); } } while (0)
     CKI(preload_push2d());
     CKI(preload_bins());
     CKI(preload_fields());
-    // zero the whole state
     CKI(cudaMemsetAsync(ctx->arena, 0, L.total, ctx->stream));
 
-    RunDev& R = ctx->run;
     const pic_config& c = ctx->cfg;
-    R.nx = c.nx; R.ny = c.ny; R.nz = c.nz;
-    R.ntx = g.ntx; R.nty = g.nty; R.ntz = g.ntz;
-    R.cell_off = 0;
-    R.dtdx = (float)(c.dt / c.dx); R.dtdy = (float)(c.dt / c.dy); R.dtdz = (float)(c.dt / c.dz);
-    R.cx = R.dtdx; R.cy = R.dtdy; R.cz = R.dtdz;
-    for (int d = 0; d < 3; ++d) {
-        R.E[d] = at<float>(ctx, L.E[d]);
-        R.B[d] = at<float>(ctx, L.B[d]);
-        R.J[d] = at<long long>(ctx, L.J[d]);
-        R.Jlast[d] = L.Jlast[d] ? at<long long>(ctx, L.Jlast[d]) : nullptr;
-        R.msum[d] = nullptr;   // published when a drag species is loaded
-        R.ubar[d] = nullptr;
+    ctx->runs.assign(nruns, RunDev{});
+    std::vector<int2> work(g.nwork);
+    std::vector<int> work_off(nruns + 1);
+    for (int r = 0; r < nruns; ++r) {
+        const RunGeo& G = g.runs[r];
+        RunDev& R = ctx->runs[r];
+        R.nx = G.nx; R.ny = G.ny; R.nz = G.nz;
+        R.ntx = G.ntx; R.nty = G.nty; R.ntz = G.ntz;
+        R.cell_off = (int)G.cell_off;
+        R.dtdx = (float)(c.dt / c.dx); R.dtdy = (float)(c.dt / c.dy); R.dtdz = (float)(c.dt / c.dz);
+        R.cx = R.dtdx; R.cy = R.dtdy; R.cz = R.dtdz;
+        for (int d = 0; d < 3; ++d) {
+            R.E[d] = at<float>(ctx, L.E[d][r]);
+            R.B[d] = at<float>(ctx, L.B[d][r]);
+            R.J[d] = at<long long>(ctx, L.J[d][r]);
+            R.Jlast[d] = L.Jlast[d][r] ? at<long long>(ctx, L.Jlast[d][r]) : nullptr;
+            R.msum[d] = nullptr;   // published when a drag species is loaded
+            R.ubar[d] = nullptr;
+        }
+        R.mcnt = nullptr;
+        R.shift = 30;
+        R.jscale = (float)std::ldexp(1.0, -30);
+        for (long long t = 0; t < G.ntiles; ++t) work[G.work_off + t] = make_int2(r, (int)t);
+        work_off[r] = (int)G.work_off;
     }
-    R.mcnt = nullptr;
-    R.shift = 30;
-    R.jscale = (float)std::ldexp(1.0, -30);
-
-    std::vector<int2> work(g.ntiles);
-    for (long long t = 0; t < g.ntiles; ++t) work[t] = make_int2(0, (int)t);
-    CKI(cudaMemcpyAsync(at<int2>(ctx, L.work), work.data(), sizeof(int2) * g.ntiles, cudaMemcpyHostToDevice, ctx->stream));
+    work_off[nruns] = (int)g.nwork;
+    CKI(cudaMemcpyAsync(at<int2>(ctx, L.work), work.data(), sizeof(int2) * g.nwork, cudaMemcpyHostToDevice, ctx->stream));
+    CKI(cudaMemcpyAsync(at<int>(ctx, L.work_off), work_off.data(), sizeof(int) * (nruns + 1), cudaMemcpyHostToDevice, ctx->stream));
 
     Args& a = ctx->args;
     a.ctl = at<Ctl>(ctx, L.ctl);
     a.runs = at<RunDev>(ctx, L.runs);
     a.work = at<int2>(ctx, L.work);
-    a.nwork = (int)g.ntiles;
+    a.work_off = at<int>(ctx, L.work_off);
+    a.kin = at<long long>(ctx, L.kin);
+    a.nwork = (int)g.nwork;
     a.nspecies = c.nspecies;
-    a.nruns = 1;
+    a.nruns = nruns;
     a.ndim = c.ndim;
     for (int s = 0; s < c.nspecies; ++s) {
         a.cap[s] = g.cap[s];
         a.cap_stay[s] = g.cap_stay[s];
         a.spill_cap[s] = g.spill_cap[s];
-        a.stage_n[s] = c.capacity[s];
+        a.stage_n[s] = g.capacity[s];
         for (int b = 0; b < 2; ++b) {
             Slots& S = a.slot[s][b];
             for (int d = 0; d < 3; ++d) {
@@ -438,31 +481,35 @@ extern "C" int pic_init(const pic_config* cfg, void* device_arena, size_t arena_
     a.start = at<int>(ctx, L.start);
     a.gate = at<int>(ctx, L.gate);
 
-    if (upload_run(ctx) != PIC_OK) return bail(PIC_ECUDA);
+    if (upload_runs(ctx) != PIC_OK) return bail(PIC_ECUDA);
     CKI(cudaStreamSynchronize(ctx->stream));
 #undef CKI
     *out = ctx;
     return PIC_OK;
 }
 
-
-extern "C" int pic_load_species(pic_ctx* ctx, int s, const pic_species* sp, int64_t n,
-                                const int32_t* cell, const float* offset, const float* u) {
+int load_run(pic_ctx* ctx, int run, int s, const pic_species* sp, int64_t n, const int32_t* cell,
+             const float* offset, const float* u) {
     if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    int rc = check_run(ctx, run);
+    if (rc) return rc;
+    const RunGeo& G = ctx->geo.runs[run];
     if (!sp || s < 0 || s >= ctx->cfg.nspecies) return fail(ctx, PIC_EINVAL, "bad species index");
-    if (n < 0 || n > ctx->cfg.capacity[s]) return fail(ctx, PIC_ENOMEM, "n = %lld exceeds capacity", (long long)n);
+    if (n < 0 || n > G.capacity[s]) return fail(ctx, PIC_ENOMEM, "n = %lld exceeds the run's capacity", (long long)n);
     if (n > 0 && (!cell || !offset || !u)) return fail(ctx, PIC_EINVAL, "null particle array");
     if (ctx->host_step != 0) return fail(ctx, PIC_ESTATE, "species are loaded before the first step");
-    if (ctx->run.sp[s].active) return fail(ctx, PIC_ESTATE, "species %d is already loaded", s);
+    RunDev& R = ctx->runs[run];
+    if (R.sp[s].active) return fail(ctx, PIC_ESTATE, "species %d of run %d is already loaded", s, run);
     if (!(std::isfinite(sp->q) && std::isfinite(sp->m) && sp->m > 0 && std::isfinite(sp->w) && sp->w >= 0 &&
           std::isfinite(sp->nu) && sp->nu >= 0 && std::fabs(sp->q) <= 1.0))
         return fail(ctx, PIC_EINVAL, "bad species parameters (|q| <= 1, m > 0, w >= 0, nu >= 0)");
+    if (ctx->q_set[s] && ctx->q[s] != sp->q) return fail(ctx, PIC_EINVAL, "species %d has one charge in every run", s);
     const pic_config& c = ctx->cfg;
-    int par = 0;
-    int rc = current_parity(ctx, s, &par);
+    Ctl h;
+    rc = read_ctl(ctx, &h);
     if (rc) return rc;
     // host -> staging (the other buffer's slot memory), then counting-sort into the slots
-    const Stage T = stage_of(ctx->args, s, par);
+    const Stage T = stage_of(ctx->args, s, h.parity);
     if (n > 0) {
         CK(cudaMemcpyAsync(T.cell, cell, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
         for (int d = 0; d < c.ndim; ++d)
@@ -470,47 +517,99 @@ extern "C" int pic_load_species(pic_ctx* ctx, int s, const pic_species* sp, int6
         for (int d = 0; d < 3; ++d)
             CK(cudaMemcpyAsync(T.u[d], u + (size_t)d * n, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
     }
-    CK(launch_bin(ctx->args, s, n, false, nullptr, ctx->stream));
+    CK(launch_bin(ctx->args, s, n, false, G.cell_off, G.ncell, nullptr, ctx->stream));
     rc = device_flags(ctx);
     if (rc) {
-        // undo: empty the species' slots
-        CK(cudaMemsetAsync(ctx->args.slot[s][par].count, 0, 4 * ctx->geo.ncell, ctx->stream));
-        CK(cudaMemsetAsync(ctx->args.slot[s][par].icount, 0, 4 * ctx->geo.ncell, ctx->stream));
-        CK(cudaMemsetAsync(ctx->args.slot[s][par].sn, 0, 4, ctx->stream));
-        Ctl h;
-        CK(cudaMemcpyAsync(&h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
-        h.err = 0;
-        CK(cudaMemcpyAsync(at<Ctl>(ctx, ctx->lay.ctl), &h, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+        // undo: empty the run's cells of this species and clear the flag
+        const Slots& S = ctx->args.slot[s][h.parity];
+        CK(cudaMemsetAsync(S.count + G.cell_off, 0, 4 * G.ncell, ctx->stream));
+        CK(cudaMemsetAsync(S.icount + G.cell_off, 0, 4 * G.ncell, ctx->stream));
+        Ctl z;
+        int rc2 = read_ctl(ctx, &z);
+        if (rc2) return rc2;
+        z.err = 0;
+        CK(cudaMemcpyAsync(at<Ctl>(ctx, ctx->lay.ctl), &z, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         return rc;
     }
-    ctx->loaded[s] = n;
+    ctx->loaded[(size_t)run * PIC_NS + s] = n;
+    ctx->q[s] = sp->q;
+    ctx->q_set[s] = true;
 
-    SpeciesParams& P = ctx->run.sp[s];
+    SpeciesParams& P = R.sp[s];
     P.active = 1;
     P.qmdt2 = (float)(sp->q * c.dt / (2.0 * sp->m));
     P.w = (float)sp->w;
     P.dragf = (float)(-std::expm1(-sp->nu * c.dt));
     P.drag = sp->nu > 0 ? 1 : 0;
-    ctx->q[s] = sp->q;
-    ctx->run.shift = choose_shift(ctx);
-    set_species_scales(ctx);
-    if (P.drag && !ctx->run.msum[0]) {
+    set_species_scales(ctx, R);
+    if (P.drag && !R.msum[0]) {
         for (int d = 0; d < 3; ++d) {
-            ctx->run.msum[d] = at<long long>(ctx, ctx->lay.msum[d]);
-            ctx->run.ubar[d] = at<float>(ctx, ctx->lay.ubar[d]);
+            R.msum[d] = at<long long>(ctx, ctx->lay.msum[d][run]);
+            R.ubar[d] = at<float>(ctx, ctx->lay.ubar[d][run]);
         }
-        ctx->run.mcnt = at<int>(ctx, ctx->lay.mcnt);
+        R.mcnt = at<int>(ctx, ctx->lay.mcnt[run]);
     }
-    rc = upload_run(ctx);
+    rc = upload_runs(ctx);
     if (rc) return rc;
     if (P.drag) {
-        CK(launch_moments_init(ctx->args, s, ctx->stream));
-        CK(launch_moments_finalize(ctx->args, &ctx->run, 1, ctx->stream));
+        CK(launch_moments_init(ctx->args, s, run, G.cell_off, G.ncell, ctx->stream));
+        CK(launch_moments_finalize(ctx->args, run, G.ncell, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return device_flags(ctx);
+}
+
+long long records_written(const pic_ctx* ctx) {
+    const int M = ctx->cfg.diag_interval;
+    if (M <= 0 || ctx->host_step <= 0) return 0;
+    return (ctx->host_step - 1) / M + 1;
+}
+
+}  // namespace
+
+// =============================================================================== C ABI
+
+extern "C" int pic_required_bytes_batch(const pic_config* cfg, int nruns, const int32_t* run_dims,
+                                        const int64_t* run_capacity, size_t* bytes_out) {
+    if (!cfg || !bytes_out || !run_dims || !run_capacity) return fail(nullptr, PIC_EINVAL, "null argument");
+    Geometry g;
+    std::string err;
+    int rc = geometry(cfg, nruns, run_dims, run_capacity, &g, &err);
+    if (rc != PIC_OK) return fail(nullptr, rc, "%s", err.c_str());
+    *bytes_out = make_layout(cfg, g).total;
+    return PIC_OK;
+}
+
+extern "C" int pic_required_bytes(const pic_config* cfg, size_t* bytes_out) {
+    if (!cfg || !bytes_out) return fail(nullptr, PIC_EINVAL, "null argument");
+    const int32_t dims[3] = {cfg->nx, cfg->ny, cfg->nz};
+    const int64_t caps[PIC_NS] = {cfg->capacity[0], cfg->capacity[1]};
+    return pic_required_bytes_batch(cfg, 1, dims, caps, bytes_out);
+}
+
+extern "C" int pic_init(const pic_config* cfg, void* device_arena, size_t arena_bytes,
+                        void* cuda_stream, pic_ctx** out) {
+    if (!cfg) return fail(nullptr, PIC_EINVAL, "null argument");
+    const int32_t dims[3] = {cfg->nx, cfg->ny, cfg->nz};
+    const int64_t caps[PIC_NS] = {cfg->capacity[0], cfg->capacity[1]};
+    return init_common(cfg, 1, dims, caps, device_arena, arena_bytes, cuda_stream, out);
+}
+
+extern "C" int pic_init_batch(const pic_config* cfg, int nruns, const int32_t* run_dims,
+                              const int64_t* run_capacity, void* device_arena, size_t arena_bytes,
+                              void* cuda_stream, pic_ctx** out) {
+    return init_common(cfg, nruns, run_dims, run_capacity, device_arena, arena_bytes, cuda_stream, out);
+}
+
+extern "C" int pic_load_species(pic_ctx* ctx, int s, const pic_species* sp, int64_t n,
+                                const int32_t* cell, const float* offset, const float* u) {
+    return load_run(ctx, 0, s, sp, n, cell, offset, u);
+}
+
+extern "C" int pic_load_species_run(pic_ctx* ctx, int run, int s, const pic_species* sp, int64_t n,
+                                    const int32_t* cell, const float* offset, const float* u) {
+    return load_run(ctx, run, s, sp, n, cell, offset, u);
 }
 
 extern "C" int pic_step(pic_ctx* ctx, int nsteps) {
@@ -544,50 +643,52 @@ extern "C" int pic_sync(pic_ctx* ctx) {
     return device_flags(ctx);
 }
 
-static long long records_written(const pic_ctx* ctx) {
-    const int M = ctx->cfg.diag_interval;
-    if (M <= 0 || ctx->host_step <= 0) return 0;
-    return (ctx->host_step - 1) / M + 1;
-}
-
-extern "C" int pic_diag(pic_ctx* ctx, pic_diag_rec* out, int max_recs, int* n_out) {
+extern "C" int pic_diag_run(pic_ctx* ctx, int run, pic_diag_rec* out, int max_recs, int* n_out) {
     if (!ctx || !n_out || (max_recs > 0 && !out)) return fail(ctx, PIC_EINVAL, "null argument");
-    int rc = pic_sync(ctx);
+    int rc = check_run(ctx, run);
+    if (rc) return rc;
+    rc = pic_sync(ctx);
     if (rc) return rc;
     const long long nrec = records_written(ctx);
     const int cap = ctx->args.hist_cap;
     const long long first = nrec > cap ? nrec - cap : 0;
     long long n = nrec - first;
     if (n > max_recs) n = max_recs;
+    const DiagRec* base = ctx->args.hist + (size_t)run * cap;
     for (long long r = 0; r < n; ++r) {
         const long long slot = (first + r) % cap;
-        CK(cudaMemcpyAsync(out + r, ctx->args.hist + slot, sizeof(DiagRec), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(out + r, base + slot, sizeof(DiagRec), cudaMemcpyDeviceToHost, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
     *n_out = (int)n;
     return PIC_OK;
 }
 
-extern "C" int pic_get_particles(pic_ctx* ctx, int s, int32_t* cell, float* offset, float* u,
-                                 int32_t* id, int64_t n) {
+extern "C" int pic_diag(pic_ctx* ctx, pic_diag_rec* out, int max_recs, int* n_out) {
+    return pic_diag_run(ctx, 0, out, max_recs, n_out);
+}
+
+extern "C" int pic_get_particles_run(pic_ctx* ctx, int run, int s, int32_t* cell, float* offset,
+                                     float* u, int32_t* id, int64_t n) {
     if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    int rc = check_run(ctx, run);
+    if (rc) return rc;
     if (s < 0 || s >= ctx->cfg.nspecies) return fail(ctx, PIC_EINVAL, "bad species index");
-    if (n != ctx->loaded[s]) return fail(ctx, PIC_EINVAL, "n must equal the loaded count (%lld)", ctx->loaded[s]);
+    const long long want = ctx->loaded[(size_t)run * PIC_NS + s];
+    if (n != want) return fail(ctx, PIC_EINVAL, "n must equal the loaded count (%lld)", want);
     if (id && !ctx->cfg.track_ids) return fail(ctx, PIC_ESTATE, "ids need track_ids");
-    int rc = pic_sync(ctx);
+    rc = pic_sync(ctx);
     if (rc) return rc;
-    int par = 0;
-    rc = current_parity(ctx, s, &par);
-    if (rc) return rc;
-    // compaction into the staging area (cell order, then the spill list)
-    CK(launch_compact(ctx->args, s, nullptr, ctx->stream));
-    ctx->launches += 4;
+    const RunGeo& G = ctx->geo.runs[run];
+    // compaction of the run's cells into the staging area (cell order, then its spill entries)
+    CK(launch_compact(ctx->args, s, G.cell_off, G.ncell, G.cell_off, nullptr, ctx->stream));
+    ctx->launches += 6;
     Ctl h;
-    CK(cudaMemcpyAsync(&h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    if (h.staged[s] != n) return fail(ctx, PIC_ESTATE, "device holds %d particles of species %d, expected %lld",
-                                      h.staged[s], s, (long long)n);
-    const Stage T = stage_of(ctx->args, s, par);
+    rc = read_ctl(ctx, &h);
+    if (rc) return rc;
+    if (h.staged[s] != n) return fail(ctx, PIC_ESTATE, "device holds %d particles of species %d in run %d, expected %lld",
+                                      h.staged[s], s, run, (long long)n);
+    const Stage T = stage_of(ctx->args, s, h.parity);
     if (n > 0) {
         if (cell) CK(cudaMemcpyAsync(cell, T.cell, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
         if (offset)
@@ -602,29 +703,42 @@ extern "C" int pic_get_particles(pic_ctx* ctx, int s, int32_t* cell, float* offs
     return PIC_OK;
 }
 
-extern "C" int pic_get_fields(pic_ctx* ctx, float* E, float* B, int64_t* J) {
+extern "C" int pic_get_particles(pic_ctx* ctx, int s, int32_t* cell, float* offset, float* u,
+                                 int32_t* id, int64_t n) {
+    return pic_get_particles_run(ctx, 0, s, cell, offset, u, id, n);
+}
+
+extern "C" int pic_get_fields_run(pic_ctx* ctx, int run, float* E, float* B, int64_t* J) {
     if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
-    int rc = pic_sync(ctx);
+    int rc = check_run(ctx, run);
     if (rc) return rc;
-    const size_t nc = (size_t)ctx->geo.ncell;
+    rc = pic_sync(ctx);
+    if (rc) return rc;
+    const RunDev& R = ctx->runs[run];
+    const size_t nc = (size_t)ctx->geo.runs[run].ncell;
     for (int d = 0; d < 3; ++d) {
-        if (E) CK(cudaMemcpyAsync(E + d * nc, ctx->run.E[d], 4 * nc, cudaMemcpyDeviceToHost, ctx->stream));
-        if (B) CK(cudaMemcpyAsync(B + d * nc, ctx->run.B[d], 4 * nc, cudaMemcpyDeviceToHost, ctx->stream));
+        if (E) CK(cudaMemcpyAsync(E + d * nc, R.E[d], 4 * nc, cudaMemcpyDeviceToHost, ctx->stream));
+        if (B) CK(cudaMemcpyAsync(B + d * nc, R.B[d], 4 * nc, cudaMemcpyDeviceToHost, ctx->stream));
         if (J) {
-            if (!ctx->run.Jlast[0]) return fail(ctx, PIC_ESTATE, "J needs PIC_FLAG_KEEP_J");
-            CK(cudaMemcpyAsync(J + d * nc, ctx->run.Jlast[d], 8 * nc, cudaMemcpyDeviceToHost, ctx->stream));
+            if (!R.Jlast[0]) return fail(ctx, PIC_ESTATE, "J needs PIC_FLAG_KEEP_J");
+            CK(cudaMemcpyAsync(J + d * nc, R.Jlast[d], 8 * nc, cudaMemcpyDeviceToHost, ctx->stream));
         }
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return PIC_OK;
 }
 
+extern "C" int pic_get_fields(pic_ctx* ctx, float* E, float* B, int64_t* J) {
+    return pic_get_fields_run(ctx, 0, E, B, J);
+}
+
 extern "C" int pic_set_fields(pic_ctx* ctx, const float* E, const float* B) {
     if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
-    const size_t nc = (size_t)ctx->geo.ncell;
+    const RunDev& R = ctx->runs[0];
+    const size_t nc = (size_t)ctx->geo.runs[0].ncell;
     for (int d = 0; d < 3; ++d) {
-        if (E) CK(cudaMemcpyAsync(ctx->run.E[d], E + d * nc, 4 * nc, cudaMemcpyHostToDevice, ctx->stream));
-        if (B) CK(cudaMemcpyAsync(ctx->run.B[d], B + d * nc, 4 * nc, cudaMemcpyHostToDevice, ctx->stream));
+        if (E) CK(cudaMemcpyAsync(R.E[d], E + d * nc, 4 * nc, cudaMemcpyHostToDevice, ctx->stream));
+        if (B) CK(cudaMemcpyAsync(R.B[d], B + d * nc, 4 * nc, cudaMemcpyHostToDevice, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return PIC_OK;
@@ -632,22 +746,24 @@ extern "C" int pic_set_fields(pic_ctx* ctx, const float* E, const float* B) {
 
 extern "C" int pic_fixed_point_shift(const pic_ctx* ctx, int* shift_out) {
     if (!ctx || !shift_out) return PIC_EINVAL;
-    *shift_out = ctx->run.shift;
+    *shift_out = ctx->runs[0].shift;
     return PIC_OK;
 }
 
-extern "C" int pic_fit_growth(pic_ctx* ctx, int width, double t_noise, double start_factor,
-                              double end_factor, double* gamma_out, double* t0_out, double* t1_out) {
+extern "C" int pic_fit_growth_run(pic_ctx* ctx, int run, int width, double t_noise, double start_factor,
+                                  double end_factor, double* gamma_out, double* t0_out, double* t1_out) {
     if (!ctx || !gamma_out) return fail(ctx, PIC_EINVAL, "null argument");
+    int rc = check_run(ctx, run);
+    if (rc) return rc;
     if (width < 2) return fail(ctx, PIC_EINVAL, "width must be >= 2");
-    int rc = pic_sync(ctx);
+    rc = pic_sync(ctx);
     if (rc) return rc;
     const long long nrec = records_written(ctx);
     const int cap = ctx->args.hist_cap;
     const long long first = nrec > cap ? nrec - cap : 0;
     const int n = (int)(nrec - first);
     double* d_out = at<double>(ctx, ctx->lay.fit);
-    CK(launch_fit(ctx->args, first, n, width, t_noise, start_factor, end_factor, d_out, ctx->stream));
+    CK(launch_fit(ctx->args, run, first, n, width, t_noise, start_factor, end_factor, d_out, ctx->stream));
     ctx->launches += 1;
     double h[3];
     CK(cudaMemcpyAsync(h, d_out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
@@ -656,6 +772,11 @@ extern "C" int pic_fit_growth(pic_ctx* ctx, int width, double t_noise, double st
     if (t0_out) *t0_out = h[1];
     if (t1_out) *t1_out = h[2];
     return PIC_OK;
+}
+
+extern "C" int pic_fit_growth(pic_ctx* ctx, int width, double t_noise, double start_factor,
+                              double end_factor, double* gamma_out, double* t0_out, double* t1_out) {
+    return pic_fit_growth_run(ctx, 0, width, t_noise, start_factor, end_factor, gamma_out, t0_out, t1_out);
 }
 
 extern "C" int pic_kernel_times(pic_ctx* ctx, pic_kernel_time* out, int max, int* n_out) {
@@ -686,8 +807,8 @@ extern "C" int pic_get_stats(pic_ctx* ctx, pic_stats* out) {
     if (!ctx || !out) return fail(ctx, PIC_EINVAL, "null argument");
     CK(cudaStreamSynchronize(ctx->stream));
     Ctl h;
-    CK(cudaMemcpyAsync(&h, at<Ctl>(ctx, ctx->lay.ctl), sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    int rc = read_ctl(ctx, &h);
+    if (rc) return rc;
     std::memset(out, 0, sizeof(*out));
     std::vector<int> cnt((size_t)ctx->geo.ncell), icnt((size_t)ctx->geo.ncell);
     for (int s = 0; s < ctx->cfg.nspecies; ++s) {
@@ -701,12 +822,11 @@ extern "C" int pic_get_stats(pic_ctx* ctx, pic_stats* out) {
         long long tot = 0;
         int mx = 0;
         for (size_t c = 0; c < cnt.size(); ++c) {
-            const int a = cnt[c] < cs ? cnt[c] : cs, b = icnt[c] < ci ? icnt[c] : ci;
+            const int a = std::min(cnt[c], cs), b = std::min(icnt[c], ci);
             tot += a + b;
-            const int raw = cnt[c] + icnt[c];
-            mx = raw > mx ? raw : mx;
+            mx = std::max(mx, cnt[c] + icnt[c]);
         }
-        out->particles[s] = tot + (sn < ctx->geo.spill_cap[s] ? sn : ctx->geo.spill_cap[s]);
+        out->particles[s] = tot + std::min(sn, ctx->geo.spill_cap[s]);
         out->max_cell[s] = mx;
         out->spilled[s] = sn;
         out->cell_capacity[s] = ctx->geo.cap[s];
@@ -750,6 +870,8 @@ extern "C" int pic_bin_cells_noalloc(const int32_t* cell, int64_t n, int32_t nce
 extern "C" int64_t pic_launch_count(const pic_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
 extern "C" int64_t pic_step_count(const pic_ctx* ctx) { return ctx ? ctx->host_step : -1; }
+
+extern "C" int pic_num_runs(const pic_ctx* ctx) { return ctx ? ctx->nruns : -1; }
 
 extern "C" const char* pic_last_error(const pic_ctx* ctx) {
     return ctx ? ctx->err.c_str() : g_init_error.c_str();

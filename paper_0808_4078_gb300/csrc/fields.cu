@@ -74,6 +74,65 @@ __global__ void yee_e_2d(const RunDev* __restrict__ runs, int run, float dt) {
     }
 }
 
+// Tile-batched 2D Yee over the (run, tile) work list: one CTA per 16 x 16 tile, a thread per
+// cell, every run of a batch in one launch.
+constexpr int YTX = 16, YTY = 16;
+
+__global__ void __launch_bounds__(NT) yee_b_half_2d_tiles(Args a) {
+    const int2 wk = a.work[blockIdx.x];
+    const RunDev& R = a.runs[wk.x];
+    const int nx = R.nx, ny = R.ny;
+    const int i = (wk.y % R.ntx) * YTX + threadIdx.x % YTX;
+    const int j = (wk.y / R.ntx) * YTY + threadIdx.x / YTX;
+    const float hx = 0.5f * R.cx, hy = 0.5f * R.cy;
+    const float* __restrict__ Ex = R.E[0];
+    const float* __restrict__ Ey = R.E[1];
+    const float* __restrict__ Ez = R.E[2];
+    const long long c = (long long)j * nx + i;
+    const int ip = i + 1 == nx ? 0 : i + 1;
+    const int jp = j + 1 == ny ? 0 : j + 1;
+    const long long cxp = (long long)j * nx + ip, cyp = (long long)jp * nx + i;
+    const float ez = Ez[c];
+    R.B[0][c] -= hy * (Ez[cyp] - ez);
+    R.B[1][c] += hx * (Ez[cxp] - ez);
+    R.B[2][c] -= hx * (Ey[cxp] - Ey[c]) - hy * (Ex[cyp] - Ex[c]);
+}
+
+__global__ void __launch_bounds__(NT) yee_e_2d_tiles(Args a, float dt) {
+    const int2 wk = a.work[blockIdx.x];
+    const RunDev& R = a.runs[wk.x];
+    const int nx = R.nx, ny = R.ny;
+    const int i = (wk.y % R.ntx) * YTX + threadIdx.x % YTX;
+    const int j = (wk.y / R.ntx) * YTY + threadIdx.x / YTX;
+    const float cx = R.cx, cy = R.cy, js = R.jscale * dt;
+    const float* __restrict__ Bx = R.B[0];
+    const float* __restrict__ By = R.B[1];
+    const float* __restrict__ Bz = R.B[2];
+    const long long c = (long long)j * nx + i;
+    const int im = i == 0 ? nx - 1 : i - 1;
+    const int jm = j == 0 ? ny - 1 : j - 1;
+    const long long cxm = (long long)j * nx + im, cym = (long long)jm * nx + i;
+    const long long j0 = R.J[0][c], j1 = R.J[1][c], j2 = R.J[2][c];
+    const float jx = (float)j0 * js, jy = (float)j1 * js, jz = (float)j2 * js;
+    R.J[0][c] = 0; R.J[1][c] = 0; R.J[2][c] = 0;
+    if (R.Jlast[0]) { R.Jlast[0][c] = j0; R.Jlast[1][c] = j1; R.Jlast[2][c] = j2; }
+    const float bz = Bz[c];
+    R.E[0][c] += cy * (bz - Bz[cym]) - jx;
+    R.E[1][c] += -cx * (bz - Bz[cxm]) - jy;
+    R.E[2][c] += cx * (By[c] - By[cxm]) - cy * (Bx[c] - Bx[cym]) - jz;
+    if (R.msum[0]) {
+        const int cnt = R.mcnt[c];
+        const float inv = cnt > 0 ? 1.0f / (float)cnt : 0.f;
+        const float sc = inv * (1.0f / 1048576.0f);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            R.ubar[k][c] = (float)R.msum[k][c] * sc;
+            R.msum[k][c] = 0;
+        }
+        R.mcnt[c] = 0;
+    }
+}
+
 // ------------------------------------------------------------------ 3D Yee
 __global__ void yee_b_half_3d(const RunDev* __restrict__ runs, int run) {
     const RunDev& R = runs[run];
@@ -154,27 +213,30 @@ __global__ void moments_finalize_kernel(const RunDev* __restrict__ runs, int run
     }
 }
 
-// Drag moments of the loaded particles of species s (NGP cell = the slot's cell), current buffer.
-__global__ void moments_init_kernel(Args a, int s) {
-    const RunDev& R = a.runs[0];
+// Drag moments of the loaded particles of species s in cells [c0, c0 + nc) of run `run` (NGP
+// cell = the slot's cell), current buffer.
+__global__ void moments_init_kernel(Args a, int s, int run, long long c0, long long nc) {
+    const RunDev& R = a.runs[run];
     if (!R.sp[s].drag || !R.msum[0]) return;
     const Slots S = a.slot[s][a.ctl->parity];
     const int cap = a.cap[s], cs = a.cap_stay[s];
     const float ms = 1048576.0f;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
-         c += (long long)gridDim.x * blockDim.x) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nc;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long c = c0 + k;
         const CellRange cr = cell_range(S, cap, cs, c);
-        const int n = cr.n;
         long long m[3] = {0, 0, 0};
-        for (int i = 0; i < n; ++i)
+        for (int i = 0; i < cr.n; ++i)
             for (int d = 0; d < 3; ++d) m[d] += __float2ll_rn(S.u[d][slot_of(c, cap, cs, cr.ns, i)] * ms);
         const long long lc = c - R.cell_off;
         for (int d = 0; d < 3; ++d) atomicAdd((unsigned long long*)&R.msum[d][lc], (unsigned long long)m[d]);
-        atomicAdd(&R.mcnt[lc], n);
+        atomicAdd(&R.mcnt[lc], cr.n);
     }
     const int ns = min(*S.sn, a.spill_cap[s]);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ns; k += gridDim.x * blockDim.x) {
-        const long long lc = S.scell[k] - R.cell_off;
+        const long long c = S.scell[k];
+        if (c < c0 || c >= c0 + nc) continue;
+        const long long lc = c - R.cell_off;
         for (int d = 0; d < 3; ++d)
             atomicAdd((unsigned long long*)&R.msum[d][lc], (unsigned long long)__float2ll_rn(S.su[d][k] * ms));
         atomicAdd(&R.mcnt[lc], 1);
@@ -182,50 +244,52 @@ __global__ void moments_init_kernel(Args a, int s) {
 }
 
 // ------------------------------------------------------------------ step finalisation
-// Reduces the per-CTA field-energy partials in a fixed order (deterministic FP64), converts the
-// int64 kinetic/momentum sums, writes one history record on diagnostic steps, and advances the
-// device step counter.
+// One block per run: on diagnostic steps reduce the run's per-CTA field-energy partials in a
+// fixed order (deterministic FP64), convert its int64 kinetic/momentum sums and write one
+// history record.  Then `advance_kernel` moves the step counter and flips the particle buffer.
 __global__ void __launch_bounds__(NT) finalize_kernel(Args a) {
     __shared__ double red[NT][6];
+    const int run = blockIdx.x;
     const long long step = a.ctl->step;
     const bool diag = a.diag_interval > 0 && (step % a.diag_interval) == 0;
-    if (diag) {
-        double s[6] = {0, 0, 0, 0, 0, 0};
-        for (int w = threadIdx.x; w < a.nwork; w += NT)
-            for (int c = 0; c < 6; ++c) s[c] += a.partials[(size_t)w * 8 + c];
-        for (int c = 0; c < 6; ++c) red[threadIdx.x][c] = s[c];
-        __syncthreads();
-        for (int o = NT / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o)
-                for (int c = 0; c < 6; ++c) red[threadIdx.x][c] += red[threadIdx.x + o][c];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            const long long r = step / a.diag_interval;
-            DiagRec& d = a.hist[r % a.hist_cap];
-            d.step = step;
-            d.t = (double)step * a.dt;
-            for (int c = 0; c < 3; ++c) {
-                d.WE[c] = red[0][c] * a.dV;
-                d.WB[c] = red[0][3 + c] * a.dV;
-            }
-            const double sc = a.dV / 4294967296.0;
-            double P[3] = {0, 0, 0};
-            for (int sp = 0; sp < PIC_NS; ++sp) {
-                d.Ekin[sp] = (double)a.ctl->kin[sp][0] * sc;
-                for (int c = 0; c < 3; ++c) P[c] += (double)a.ctl->kin[sp][1 + c] * sc;
-                for (int c = 0; c < 4; ++c) a.ctl->kin[sp][c] = 0;
-            }
-            for (int c = 0; c < 3; ++c) d.P[c] = P[c];
-            d.flags = a.ctl->err;
-            d.reserved = 0;
-        }
-    }
+    if (!diag) return;
+    const int w0 = a.work_off[run], w1 = a.work_off[run + 1];
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int w = w0 + threadIdx.x; w < w1; w += NT)
+        for (int c = 0; c < 6; ++c) s[c] += a.partials[(size_t)w * 8 + c];
+    for (int c = 0; c < 6; ++c) red[threadIdx.x][c] = s[c];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        a.ctl->step = step + 1;
-        a.ctl->parity ^= 1;          // the particles now live in the other buffer
+    for (int o = NT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int c = 0; c < 6; ++c) red[threadIdx.x][c] += red[threadIdx.x + o][c];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) {
+        const long long r = step / a.diag_interval;
+        DiagRec& d = a.hist[(size_t)run * a.hist_cap + r % a.hist_cap];
+        d.step = step;
+        d.t = (double)step * a.dt;
+        for (int c = 0; c < 3; ++c) {
+            d.WE[c] = red[0][c] * a.dV;
+            d.WB[c] = red[0][3 + c] * a.dV;
+        }
+        const double sc = a.dV / 4294967296.0;
+        long long* K = a.kin + (size_t)run * PIC_NS * 4;
+        double P[3] = {0, 0, 0};
+        for (int sp = 0; sp < PIC_NS; ++sp) {
+            d.Ekin[sp] = (double)K[sp * 4 + 0] * sc;
+            for (int c = 0; c < 3; ++c) P[c] += (double)K[sp * 4 + 1 + c] * sc;
+            for (int c = 0; c < 4; ++c) K[sp * 4 + c] = 0;
+        }
+        for (int c = 0; c < 3; ++c) d.P[c] = P[c];
+        d.flags = a.ctl->err;
+        d.reserved = 0;
+    }
+}
+
+__global__ void advance_kernel(Ctl* ctl) {
+    ctl->step += 1;
+    ctl->parity ^= 1;          // the particles now live in the other buffer
 }
 
 // ------------------------------------------------------------------ growth fit (FP64)
@@ -327,17 +391,16 @@ cudaError_t preload_fields() {
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, moments_init_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, finalize_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fit_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, yee_b_half_2d_tiles);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, yee_e_2d_tiles);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, advance_kernel);
     return e;
 }
 
-cudaError_t launch_yee2d(const Args& a, const RunDev* host_runs, int nruns, cudaStream_t s) {
-    for (int r = 0; r < nruns; ++r) {
-        const long long n = (long long)host_runs[r].nx * host_runs[r].ny;
-        const int g = grid_for(n);
-        yee_b_half_2d<<<g, NT, 0, s>>>(a.runs, r);
-        yee_e_2d<<<g, NT, 0, s>>>(a.runs, r, (float)a.dt);
-        yee_b_half_2d<<<g, NT, 0, s>>>(a.runs, r);
-    }
+cudaError_t launch_yee2d(const Args& a, const RunDev*, int, cudaStream_t s) {
+    yee_b_half_2d_tiles<<<a.nwork, NT, 0, s>>>(a);
+    yee_e_2d_tiles<<<a.nwork, NT, 0, s>>>(a, (float)a.dt);
+    yee_b_half_2d_tiles<<<a.nwork, NT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -353,28 +416,26 @@ cudaError_t launch_yee3d(const Args& a, const RunDev* host_runs, int nruns, cuda
 }
 
 cudaError_t launch_finalize(const Args& a, cudaStream_t s) {
-    finalize_kernel<<<1, NT, 0, s>>>(a);
+    finalize_kernel<<<a.nruns, NT, 0, s>>>(a);
+    advance_kernel<<<1, 1, 0, s>>>(a.ctl);
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments_init(const Args& a, int species, cudaStream_t s) {
-    moments_init_kernel<<<grid_for(a.ncell), NT, 0, s>>>(a, species);
+cudaError_t launch_moments_init(const Args& a, int species, int run, long long c0, long long nc,
+                                cudaStream_t s) {
+    moments_init_kernel<<<grid_for(nc), NT, 0, s>>>(a, species, run, c0, nc);
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments_finalize(const Args& a, const RunDev* host_runs, int nruns,
-                                    cudaStream_t s) {
-    for (int r = 0; r < nruns; ++r) {
-        const long long n = (long long)host_runs[r].nx * host_runs[r].ny * host_runs[r].nz;
-        moments_finalize_kernel<<<grid_for(n), NT, 0, s>>>(a.runs, r);
-    }
+cudaError_t launch_moments_finalize(const Args& a, int run, long long ncell, cudaStream_t s) {
+    moments_finalize_kernel<<<grid_for(ncell), NT, 0, s>>>(a.runs, run);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fit(const Args& a, long long first, int nrec, int width, double t_noise,
+cudaError_t launch_fit(const Args& a, int run, long long first, int nrec, int width, double t_noise,
                        double start_factor, double end_factor, double* out3, cudaStream_t s) {
-    fit_kernel<<<1, NT, 0, s>>>(a.hist, a.hist_cap, first, nrec, width, t_noise, start_factor,
-                                end_factor, out3);
+    fit_kernel<<<1, NT, 0, s>>>(a.hist + (size_t)run * a.hist_cap, a.hist_cap, first, nrec, width,
+                                t_noise, start_factor, end_factor, out3);
     return cudaGetLastError();
 }
 

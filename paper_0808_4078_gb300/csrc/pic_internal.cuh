@@ -75,9 +75,8 @@ struct Ctl {
     long long step;              // steps completed
     int parity;                  // particle buffer read by the next step
     int err;                     // sticky error flags
-    long long kin[PIC_NS][4];    // kinetic energy + momentum accumulators (diag steps)
-    int spill_max[PIC_NS];       // largest spill count seen
     int staged[PIC_NS];          // particles in the staging area after the last compaction
+    int pad[2];
 };
 
 struct DiagRec {                 // mirrors pic_diag_rec
@@ -93,7 +92,9 @@ struct DiagRec {                 // mirrors pic_diag_rec
 struct Args {
     Ctl* ctl;
     const RunDev* runs;
-    const int2* work;            // (run, tile) per CTA of the tiled kernels
+    const int2* work;            // (run, tile) per CTA of the tiled kernels, runs in order
+    const int* work_off;         // [nruns + 1] first work item of each run
+    long long* kin;              // [nruns][PIC_NS][4] kinetic energy + momentum (diag steps)
     int nwork;
     int nspecies;
     int nruns;
@@ -104,7 +105,7 @@ struct Args {
     int spill_cap[PIC_NS];
     long long ncell;             // total cells (all runs)
     double* partials;            // [nwork][8] field-energy partials of a diag step
-    DiagRec* hist;
+    DiagRec* hist;               // [nruns][hist_cap]
     int hist_cap;
     int diag_interval;
     double dt;
@@ -177,16 +178,20 @@ bool has_push3d();
 cudaError_t launch_spill2d(const Args& a, cudaStream_t s);
 cudaError_t launch_yee2d(const Args& a, const RunDev* host_runs, int nruns, cudaStream_t s);
 cudaError_t launch_yee3d(const Args& a, const RunDev* host_runs, int nruns, cudaStream_t s);
-cudaError_t launch_finalize(const Args& a, cudaStream_t s);
+cudaError_t launch_finalize(const Args& a, cudaStream_t s);   // per-run records, then step++, flip
 cudaError_t launch_clear_next(const Args& a, cudaStream_t s);
 // Counting sort into the per-cell slots and its inverse.  All use the device parity: the
 // current buffer's slots and the staging area in the other buffer's memory.  `gate` (device int,
 // may be null) makes the kernels return at once when it holds 0.
-//   launch_bin:     staging (n particles) -> slots of the current buffer (ids kept if with_ids)
-//   launch_compact: slots + spill list of the current buffer -> staging, cell order
-cudaError_t launch_bin(const Args& a, int species, long long n, bool with_ids, const int* gate,
-                       cudaStream_t s);
-cudaError_t launch_compact(const Args& a, int species, const int* gate, cudaStream_t s);
+//   launch_bin:     staging (n particles; n < 0: the count of the last compaction) -> slots of
+//                   the current buffer; staged cells are cell_base + value, valid if value is in
+//                   [0, ncell_lim); ids kept if with_ids, else the staging index
+//   launch_compact: the slots (and spill entries) of cells [c0, c0 + nc) of the current buffer
+//                   -> staging in cell order, cell values written minus cell_base
+cudaError_t launch_bin(const Args& a, int species, long long n, bool with_ids, long long cell_base,
+                       long long ncell_lim, const int* gate, cudaStream_t s);
+cudaError_t launch_compact(const Args& a, int species, long long c0, long long nc, long long cell_base,
+                           const int* gate, cudaStream_t s);
 cudaError_t launch_spill_gate(const Args& a, cudaStream_t s);
 cudaError_t launch_clear_current(const Args& a, int species, const int* gate, cudaStream_t s);
 // Standalone counting sort by cell (pic_bin_cells): scratch = count/cursor[ncell] + block sums.
@@ -197,9 +202,9 @@ cudaError_t launch_bin_cells(const int* cell, long long n, int ncell, int* start
 cudaError_t noalloc_bin_scratch(int** out);
 // Full re-sort of every species (compact, clear, bin) when any particle is in a spill list.
 cudaError_t launch_resort(const Args& a, cudaStream_t s, int* launches);
-cudaError_t launch_moments_init(const Args& a, int species, cudaStream_t s);
-cudaError_t launch_moments_finalize(const Args& a, const RunDev* host_runs, int nruns,
-                                    cudaStream_t s);
-cudaError_t launch_fit(const Args& a, long long first, int nrec, int width, double t_noise,
+cudaError_t launch_moments_init(const Args& a, int species, int run, long long c0, long long nc,
+                                cudaStream_t s);
+cudaError_t launch_moments_finalize(const Args& a, int run, long long ncell, cudaStream_t s);
+cudaError_t launch_fit(const Args& a, int run, long long first, int nrec, int width, double t_noise,
                        double start_factor, double end_factor, double* out3, cudaStream_t s);
 }  // namespace pic

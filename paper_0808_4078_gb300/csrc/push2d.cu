@@ -676,8 +676,9 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
         __syncthreads();
         if (tid < 5 && sm.kin[tid] != 0ull) {
             // Ekin per species, momentum summed into species 0's slots
-            if (tid < 2) atomicAdd((unsigned long long*)&a.ctl->kin[tid][0], sm.kin[tid]);
-            else atomicAdd((unsigned long long*)&a.ctl->kin[0][tid - 1], sm.kin[tid]);
+            long long* K = a.kin + (size_t)wk.x * PIC_NS * 4;
+            if (tid < 2) atomicAdd((unsigned long long*)&K[tid * 4], sm.kin[tid]);
+            else atomicAdd((unsigned long long*)&K[tid - 1], sm.kin[tid]);
         }
     }
     __syncthreads();
@@ -709,15 +710,21 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
     const int par = a.ctl->parity;
     const long long step = a.ctl->step;
     const bool diag = a.diag_interval > 0 && (step % a.diag_interval) == 0;
-    const RunDev* Rp = &a.runs[0];
-    const int nx = Rp->nx, ny = Rp->ny;
     for (int s = 0; s < a.nspecies; ++s) {
         const Slots S = a.slot[s][par], D = a.slot[s][par ^ 1];
         const int ns = min(*S.sn, a.spill_cap[s]);
-        const SpeciesParams P = Rp->sp[s];
         const int cap = a.cap[s], cst = a.cap_stay[s];
         for (int k = blockIdx.x * NT + threadIdx.x; k < ns; k += gridDim.x * NT) {
             const int g = S.scell[k];
+            int lo = 0, hi = a.nruns - 1;       // run holding cell g
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.runs[mid].cell_off <= g) lo = mid; else hi = mid - 1;
+            }
+            const int run = lo;
+            const RunDev* Rp = &a.runs[run];
+            const int nx = Rp->nx, ny = Rp->ny;
+            const SpeciesParams P = Rp->sp[s];
             const int lc = g - Rp->cell_off;
             const int cy = lc / nx, cx = lc - cy * nx;
             const float ox = S.so[0][k], oy = S.so[1][k];
@@ -734,9 +741,9 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
             if (diag) {
                 long long kacc[5] = {0, 0, 0, 0, 0};
                 kin_add(kacc, s, P.w, u0x, u0y, u0z, r.ux, r.uy, r.uz);
-                atomicAdd((unsigned long long*)&a.ctl->kin[s][0], (unsigned long long)(kacc[0] + kacc[1]));
-                for (int c = 0; c < 3; ++c)
-                    atomicAdd((unsigned long long*)&a.ctl->kin[0][1 + c], (unsigned long long)kacc[2 + c]);
+                long long* K = a.kin + (size_t)run * PIC_NS * 4;
+                atomicAdd((unsigned long long*)&K[s * 4], (unsigned long long)(kacc[0] + kacc[1]));
+                for (int c = 0; c < 3; ++c) atomicAdd((unsigned long long*)&K[1 + c], (unsigned long long)kacc[2 + c]);
             }
             const Win wx = window(ox, r.sx, r.nox), wy = window(oy, r.sy, r.noy);
             const float zf = __fmul_rn(P.jz, r.vz);
