@@ -70,10 +70,12 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
     if (c->ndim != 2 && c->ndim != 3) { *err = "ndim must be 2 or 3"; return PIC_EINVAL; }
     if (c->ndim == 3 && !pic::has_push3d()) { *err = "3D push not available in this build"; return PIC_EINVAL; }
     if (nruns < 1 || nruns > 65536) { *err = "nruns must be in [1, 65536]"; return PIC_EINVAL; }
-    g->tx = c->tile_x > 0 ? c->tile_x : 16;
-    g->ty = c->tile_y > 0 ? c->tile_y : 16;
-    g->tz = c->ndim == 3 ? (c->tile_z > 0 ? c->tile_z : 4) : 1;
+    const int dtx = c->ndim == 3 ? 8 : 16, dty = c->ndim == 3 ? 8 : 16, dtz = c->ndim == 3 ? 4 : 1;
+    g->tx = c->tile_x > 0 ? c->tile_x : dtx;
+    g->ty = c->tile_y > 0 ? c->tile_y : dty;
+    g->tz = c->ndim == 3 ? (c->tile_z > 0 ? c->tile_z : dtz) : 1;
     if (c->ndim == 2 && (g->tx != 16 || g->ty != 16)) { *err = "2D tiles are 16 x 16"; return PIC_EINVAL; }
+    if (c->ndim == 3 && (g->tx != 8 || g->ty != 8 || g->tz != 4)) { *err = "3D tiles are 8 x 8 x 4"; return PIC_EINVAL; }
     if (!(c->dx > 0 && c->dy > 0 && c->dt > 0) || (c->ndim == 3 && !(c->dz > 0))) { *err = "dx, dy, dz, dt must be > 0"; return PIC_EINVAL; }
     const double inv2 = 1.0 / (c->dx * c->dx) + 1.0 / (c->dy * c->dy) + (c->ndim == 3 ? 1.0 / (c->dz * c->dz) : 0.0);
     if (c->dt * std::sqrt(inv2) >= 1.0) { *err = "dt violates the Yee Courant condition"; return PIC_EINVAL; }
@@ -276,7 +278,7 @@ int launch_one_step(pic_ctx* ctx, long long step_index) {
         PhaseScope ps(ctx, PH_PUSH);
         CK(launch_clear_next(a, ctx->stream));
         CK(ctx->cfg.ndim == 2 ? launch_push2d(a, ctx->stream) : launch_push3d(a, ctx->stream));
-        CK(launch_spill2d(a, ctx->stream));
+        CK(ctx->cfg.ndim == 2 ? launch_spill2d(a, ctx->stream) : launch_spill3d(a, ctx->stream));
         ctx->launches += 3;
     }
     {
@@ -403,6 +405,7 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
     auto bail = [&](int code) { g_init_error = ctx->err; delete ctx; return code; };
 #define CKI(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { fail(ctx, PIC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); return bail(PIC_ECUDA); } } while (0)
     CKI(preload_push2d());
+    CKI(preload_push3d());
     CKI(preload_bins());
     CKI(preload_fields());
     CKI(cudaMemsetAsync(ctx->arena, 0, L.total, ctx->stream));

@@ -1,0 +1,117 @@
+// particle_math.cuh -- per-particle arithmetic shared by the 2D and 3D particle kernels:
+// relativistic Boris rotation, the cell carry of a move, the 3-node CIC/Esirkepov window of one
+// axis, the path-averaged transverse shape factor, fixed-point helpers and the kinetic
+// diagnostic.  Every rounding is explicit so that all code paths (tile fast path, queued
+// crossers, spill list) produce the same bits for the same particle.
+#pragma once
+#include "pic_internal.cuh"
+
+namespace pic {
+
+constexpr float MOM_SCALE = 1048576.0f;  // 2^20, fixed point of the drag moments
+
+// ------------------------------------------------------------------ shared accumulators
+__device__ __forceinline__ void add_split(unsigned* lo, int* hi, long long v) {
+    if (v != 0) {
+        atomicAdd(lo, (unsigned)(v & 4095));
+        const int h = (int)(v >> 12);
+        if (h != 0) atomicAdd(hi, h);
+    }
+}
+
+// ------------------------------------------------------------------ Boris
+// Relativistic Boris rotation u^{n-1/2} -> u^{n+1/2}; h = q dt / (2 m).  Explicit roundings
+// keep every particle's update independent of which code path the compiler emits.
+__device__ __forceinline__ void boris(float h, const float EB[6], float& ux, float& uy, float& uz) {
+    const float umx = __fmaf_rn(h, EB[0], ux), umy = __fmaf_rn(h, EB[1], uy), umz = __fmaf_rn(h, EB[2], uz);
+    const float g2 = __fmaf_rn(umz, umz, __fmaf_rn(umy, umy, __fmaf_rn(umx, umx, 1.f)));
+    const float ig = rsqrtf(g2);
+    const float hg = __fmul_rn(h, ig);
+    const float tx = __fmul_rn(hg, EB[3]), ty = __fmul_rn(hg, EB[4]), tz = __fmul_rn(hg, EB[5]);
+    const float t2 = __fmaf_rn(tz, tz, __fmaf_rn(ty, ty, __fmaf_rn(tx, tx, 1.f)));
+    const float sf = __fdividef(2.f, t2);
+    const float upx = __fadd_rn(umx, __fmaf_rn(umy, tz, -__fmul_rn(umz, ty)));
+    const float upy = __fadd_rn(umy, __fmaf_rn(umz, tx, -__fmul_rn(umx, tz)));
+    const float upz = __fadd_rn(umz, __fmaf_rn(umx, ty, -__fmul_rn(umy, tx)));
+    const float sx = __fmul_rn(sf, tx), sy = __fmul_rn(sf, ty), sz = __fmul_rn(sf, tz);
+    ux = __fmaf_rn(h, EB[0], __fadd_rn(umx, __fmaf_rn(upy, sz, -__fmul_rn(upz, sy))));
+    uy = __fmaf_rn(h, EB[1], __fadd_rn(umy, __fmaf_rn(upz, sx, -__fmul_rn(upx, sz))));
+    uz = __fmaf_rn(h, EB[2], __fadd_rn(umz, __fmaf_rn(upx, sy, -__fmul_rn(upy, sx))));
+}
+
+// ------------------------------------------------------------------ Esirkepov window
+// CIC weights of the 3-node window [b, b+1, b+2] with b = min(old cell, new cell), for the old
+// offset o in [0,1) and the carry c in {-1,0,1} with new offset no in [0,1).
+struct Win {
+    float S0[3], S1[3];
+    float C[2];      // running sum of S1 - S0 along the axis (edges b+1/2, b+3/2)
+    float A[3];      // (S0 + S1) / 2
+    int off;         // b - old cell (-1 or 0)
+};
+
+__device__ __forceinline__ Win window(float o, int c, float no) {
+    Win w;
+    const float mo = __fsub_rn(1.f, o), mno = __fsub_rn(1.f, no);
+    if (c < 0) {
+        w.S0[0] = 0.f; w.S0[1] = mo; w.S0[2] = o;
+        w.S1[0] = mno; w.S1[1] = no; w.S1[2] = 0.f;
+        w.C[0] = mno; w.C[1] = o;
+        w.off = -1;
+    } else if (c == 0) {
+        w.S0[0] = mo; w.S0[1] = o; w.S0[2] = 0.f;
+        w.S1[0] = mno; w.S1[1] = no; w.S1[2] = 0.f;
+        w.C[0] = __fsub_rn(o, no); w.C[1] = 0.f;
+        w.off = 0;
+    } else {
+        w.S0[0] = mo; w.S0[1] = o; w.S0[2] = 0.f;
+        w.S1[0] = 0.f; w.S1[1] = mno; w.S1[2] = no;
+        w.C[0] = __fsub_rn(o, 1.f); w.C[1] = -no;
+        w.off = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) w.A[k] = __fmul_rn(0.5f, __fadd_rn(w.S0[k], w.S1[k]));
+    return w;
+}
+
+// Path-averaged shape product of the out-of-plane current,
+// S0x (S0y/3 + S1y/6) + S1x (S0y/6 + S1y/3), with every rounding fixed.
+__device__ __forceinline__ float zp(float s0, float s1) {
+    return __fmaf_rn(s1, 1.f / 6.f, __fmul_rn(s0, 1.f / 3.f));
+}
+__device__ __forceinline__ float zq(float s0, float s1) {
+    return __fmaf_rn(s1, 1.f / 3.f, __fmul_rn(s0, 1.f / 6.f));
+}
+__device__ __forceinline__ float zw(float s0x, float s1x, float p, float q) {
+    return __fmaf_rn(s1x, q, __fmul_rn(s0x, p));
+}
+
+// Carry a new offset r (relative to the old cell, in (-1, 2)) into [0,1) and the cell step.
+__device__ __forceinline__ void carry(float r, float& no, int& c) {
+    c = 0;
+    no = r;
+    if (r < 0.f) {
+        no = __fadd_rn(r, 1.f);
+        c = -1;
+        if (no >= 1.f) { no = 0.f; c = 0; }
+    } else if (r >= 1.f) {
+        no = __fsub_rn(r, 1.f);
+        c = 1;
+    }
+}
+
+// Kinetic energy per species and total momentum at time n, int64 fixed point 2^32:
+// kacc = {Ekin_0, Ekin_1, Px, Py, Pz}.
+__device__ __forceinline__ void kin_add(long long kacc[5], int s, float w, float u0x, float u0y,
+                                        float u0z, float ux, float uy, float uz) {
+    const float mx = 0.5f * (u0x + ux), my = 0.5f * (u0y + uy), mz = 0.5f * (u0z + uz);
+    const float gmid = sqrtf(1.f + mx * mx + my * my + mz * mz);
+    const float sc = 4294967296.0f;   // 2^32
+    const long long e = __float2ll_rn(w * (gmid - 1.f) * sc);
+    kacc[0] += s ? 0 : e;
+    kacc[1] += s ? e : 0;
+    kacc[2] += __float2ll_rn(w * mx * sc);
+    kacc[3] += __float2ll_rn(w * my * sc);
+    kacc[4] += __float2ll_rn(w * mz * sc);
+}
+
+}  // namespace pic

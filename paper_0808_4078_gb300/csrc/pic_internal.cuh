@@ -170,12 +170,14 @@ namespace pic {
 // Load every kernel of the module now (lazy loading would otherwise add the first launch's
 // load time to whatever step first uses a kernel).
 cudaError_t preload_push2d();
+cudaError_t preload_push3d();
 cudaError_t preload_bins();
 cudaError_t preload_fields();
 cudaError_t launch_push2d(const Args& a, cudaStream_t s);
 cudaError_t launch_push3d(const Args& a, cudaStream_t s);
 bool has_push3d();
 cudaError_t launch_spill2d(const Args& a, cudaStream_t s);
+cudaError_t launch_spill3d(const Args& a, cudaStream_t s);
 cudaError_t launch_yee2d(const Args& a, const RunDev* host_runs, int nruns, cudaStream_t s);
 cudaError_t launch_yee3d(const Args& a, const RunDev* host_runs, int nruns, cudaStream_t s);
 cudaError_t launch_finalize(const Args& a, cudaStream_t s);   // per-run records, then step++, flip

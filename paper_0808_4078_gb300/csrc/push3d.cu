@@ -1,10 +1,590 @@
-// push3d.cu -- fused 3D3V particle step (gather, Boris, drag, move, Esirkepov deposit).
+// push3d.cu -- fused 3D3V particle step: CIC field gather on the Yee lattice, relativistic Boris
+// push, Krook drag, move with cell carry, charge-conserving Esirkepov current deposition (CIC,
+// int64 fixed point) and rebinning of every particle into its new cell's slots of the other
+// buffer.
+//
+// One CTA of 256 threads per (run, tile) of 8 x 8 x 4 cells.  The tile's particles (both
+// species, all cells) form one flat list; the CTA walks it in batches of 512, one particle per
+// thread per half batch.  In three dimensions a large share of the beam crosses a cell edge
+// every step (v_z dt / dz ~ 0.47), so there is no per-cell fast path: every particle deposits
+// its (up to) 3 x 18 current terms with 32-bit shared atomics.  A batch adds at most 512 terms
+// of magnitude <= 2^21 to any node, so the int32 accumulators cannot overflow; after each batch
+// they are moved into an int64 shared bank (each thread owns fixed nodes, no atomics).  Particles
+// that stay inside the tile claim their new slot through a shared per-cell counter; only those
+// leaving the tile use global atomics (the destination cell's immigrant area).
+#include "particle_math.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
+namespace {
 
-bool has_push3d() { return false; }
+constexpr int TX = 8, TY = 8, TZ = 4;
+constexpr int RX = TX + 3, RY = TY + 3, RZ = TZ + 3;   // tile + CIC/Esirkepov stencil halo
+constexpr int RXY = RX * RY, RN = RXY * RZ;
+constexpr int CELLS = TX * TY * TZ;
+constexpr int NT = 256, NW = NT / 32;
+constexpr int PER_THREAD = 2;
+constexpr int BATCH = NT * PER_THREAD;   // particles per int32 accumulation round
+constexpr unsigned FULL = 0xffffffffu;
 
-cudaError_t launch_push3d(const Args&, cudaStream_t) { return cudaErrorNotSupported; }
+static_assert(CELLS == NT, "one thread per tile cell in the setup loops");
+static_assert(PIC_NS * CELLS <= 65535, "owner entries fit 16 bits");
+
+struct Smem {
+    float F[6][RN];                  // Ex Ey Ez Bx By Bz of the region (origin: tile - 1 cell)
+    int J32[3][RN];                  // current of the running batch
+    long long J64[3][RN];            // current of the finished batches
+    float ub[3][RN];                 // previous cell-mean momentum (drag)
+    unsigned Mlo[3][RN];             // drag moments (fixed point 2^20), value = Mhi * 4096 + Mlo
+    int Mhi[3][RN];
+    int MC[RN];                      // drag counts
+    int pre[PIC_NS * CELLS + 1];     // exclusive prefix of the (species, cell) particle counts
+    int cns[PIC_NS * CELLS];         // of which in the stay area
+    int scnt[PIC_NS * CELLS];        // stay-area fill of the tile's cells in the next buffer
+    unsigned short owner[BATCH];     // (species, cell) entry of each particle of the batch
+    double red[NW][6];
+    unsigned long long kin[5];
+    int wsum[NW];
+    SpeciesParams sp[PIC_NS];
+};
+
+// ------------------------------------------------------------------ gather
+// Per axis: node-lattice weights (points c, c+1) and half-lattice weights with their first point
+// (c-1 for o < 1/2, else c), for an offset o in [0,1).
+struct AxisW {
+    float n0, n1;
+    float h0, h1;
+    int hb;
+};
+__device__ __forceinline__ AxisW axis_weights(float o) {
+    AxisW w;
+    w.n0 = __fsub_rn(1.f, o);
+    w.n1 = o;
+    const float d = __fsub_rn(o, 0.5f);
+    if (d < 0.f) {
+        w.hb = -1;
+        w.h0 = -d;
+        w.h1 = __fsub_rn(1.f, -d);
+    } else {
+        w.hb = 0;
+        w.h0 = __fsub_rn(1.f, d);
+        w.h1 = d;
+    }
+    return w;
+}
+
+// Trilinear interpolation of component c from accessor F(c, i, j, k) (offsets relative to the
+// particle's cell node), half-shifted along the axes flagged in (hx, hy, hz).
+template <class A>
+__device__ __forceinline__ float interp(const A& F, int c, bool hx, bool hy, bool hz, const AxisW& wx,
+                                        const AxisW& wy, const AxisW& wz) {
+    const int i0 = hx ? wx.hb : 0, j0 = hy ? wy.hb : 0, k0 = hz ? wz.hb : 0;
+    const float ax0 = hx ? wx.h0 : wx.n0, ax1 = hx ? wx.h1 : wx.n1;
+    const float ay0 = hy ? wy.h0 : wy.n0, ay1 = hy ? wy.h1 : wy.n1;
+    const float az0 = hz ? wz.h0 : wz.n0, az1 = hz ? wz.h1 : wz.n1;
+    float fz[2];
+#pragma unroll
+    for (int dk = 0; dk < 2; ++dk) {
+        float fy[2];
+#pragma unroll
+        for (int dj = 0; dj < 2; ++dj)
+            fy[dj] = __fmaf_rn(ax1, F(c, i0 + 1, j0 + dj, k0 + dk), __fmul_rn(ax0, F(c, i0, j0 + dj, k0 + dk)));
+        fz[dk] = __fmaf_rn(ay1, fy[1], __fmul_rn(ay0, fy[0]));
+    }
+    return __fmaf_rn(az1, fz[1], __fmul_rn(az0, fz[0]));
+}
+
+// Yee staggering: Ex (1/2,0,0) Ey (0,1/2,0) Ez (0,0,1/2) Bx (0,1/2,1/2) By (1/2,0,1/2) Bz (1/2,1/2,0).
+template <class A>
+__device__ __forceinline__ void gather3(const A& F, const AxisW& wx, const AxisW& wy, const AxisW& wz, float EB[6]) {
+    EB[0] = interp(F, 0, true, false, false, wx, wy, wz);
+    EB[1] = interp(F, 1, false, true, false, wx, wy, wz);
+    EB[2] = interp(F, 2, false, false, true, wx, wy, wz);
+    EB[3] = interp(F, 3, false, true, true, wx, wy, wz);
+    EB[4] = interp(F, 4, true, false, true, wx, wy, wz);
+    EB[5] = interp(F, 5, true, true, false, wx, wy, wz);
+}
+
+struct SharedFields3 {
+    const Smem* s;
+    int n0;   // region index of the particle's cell node
+    __device__ __forceinline__ float operator()(int c, int i, int j, int k) const {
+        return s->F[c][n0 + k * RXY + j * RX + i];
+    }
+};
+struct GlobalFields3 {
+    const RunDev* R;
+    int cx, cy, cz;
+    __device__ __forceinline__ float operator()(int c, int i, int j, int k) const {
+        const int gi = wrapi(cx + i, R->nx), gj = wrapi(cy + j, R->ny), gk = wrapi(cz + k, R->nz);
+        const float* p = c < 3 ? R->E[c] : R->B[c - 3];
+        return __ldg(p + ((size_t)gk * R->ny + gj) * R->nx + gi);
+    }
+};
+
+// ------------------------------------------------------------------ one particle
+struct Pushed3 {
+    float ux, uy, uz;    // u^{n+1/2}
+    float no[3];         // new offsets
+    int st[3];           // cell steps
+    bool bad;
+};
+
+template <class A>
+__device__ __forceinline__ Pushed3 push3_one(const A& F, const SpeciesParams& P, const RunDev* Rp,
+                                             const float o[3], float ux, float uy, float uz,
+                                             float b0, float b1, float b2) {
+    Pushed3 r;
+    const AxisW wx = axis_weights(o[0]), wy = axis_weights(o[1]), wz = axis_weights(o[2]);
+    float EB[6];
+    gather3(F, wx, wy, wz, EB);
+    boris(P.qmdt2, EB, ux, uy, uz);
+    if (P.drag) {
+        ux = __fmaf_rn(-P.dragf, b0, ux);
+        uy = __fmaf_rn(-P.dragf, b1, uy);
+        uz = __fmaf_rn(-P.dragf, b2, uz);
+    }
+    const float ig = rsqrtf(__fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmaf_rn(ux, ux, 1.f))));
+    const float rx = __fmaf_rn(__fmul_rn(ux, ig), Rp->dtdx, o[0]);
+    const float ry = __fmaf_rn(__fmul_rn(uy, ig), Rp->dtdy, o[1]);
+    const float rz = __fmaf_rn(__fmul_rn(uz, ig), Rp->dtdz, o[2]);
+    r.bad = !(rx > -1.f && rx < 2.f && ry > -1.f && ry < 2.f && rz > -1.f && rz < 2.f);
+    carry(rx, r.no[0], r.st[0]);
+    carry(ry, r.no[1], r.st[1]);
+    carry(rz, r.no[2], r.st[2]);
+    r.ux = ux; r.uy = uy; r.uz = uz;
+    return r;
+}
+
+// The current terms of one move (Esirkepov, CIC): for the axis a with the transverse axes b, c,
+// J_a on the two edges k of the window = round(j_a C_a[k] F_bc), F_bc = S0_b p_c + S1_b q_c the
+// path-averaged transverse shape (p = S0/3 + S1/6, q = S0/6 + S1/3).  add(comp, i, j, k, v)
+// receives node offsets relative to the window base (b_x, b_y, b_z).
+template <class Add>
+__device__ __forceinline__ void deposit3(const Add& add, const SpeciesParams& P, const Win& wx, const Win& wy,
+                                         const Win& wz) {
+    float px[3], qx[3], py[3], qy[3], pz[3], qz[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        px[i] = zp(wx.S0[i], wx.S1[i]); qx[i] = zq(wx.S0[i], wx.S1[i]);
+        py[i] = zp(wy.S0[i], wy.S1[i]); qy[i] = zq(wy.S0[i], wy.S1[i]);
+        pz[i] = zp(wz.S0[i], wz.S1[i]); qz[i] = zq(wz.S0[i], wz.S1[i]);
+    }
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            const float f = zw(wy.S0[l], wy.S1[l], pz[m], qz[m]);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) add(0, k, l, m, round_small(__fmul_rn(P.jx, wx.C[k]), f));
+        }
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float f = zw(wz.S0[m], wz.S1[m], px[k], qx[k]);
+#pragma unroll
+            for (int l = 0; l < 2; ++l) add(1, k, l, m, round_small(__fmul_rn(P.jy, wy.C[l]), f));
+        }
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float f = zw(wx.S0[k], wx.S1[k], py[l], qy[l]);
+#pragma unroll
+            for (int m = 0; m < 2; ++m) add(2, k, l, m, round_small(__fmul_rn(P.jz, wz.C[m]), f));
+        }
+}
+
+// ------------------------------------------------------------------ rebinning
+__device__ __forceinline__ void store3(const Slots& D, size_t q, const float o[3], float ux, float uy,
+                                       float uz, int id) {
+    D.o[0][q] = o[0]; D.o[1][q] = o[1]; D.o[2][q] = o[2];
+    D.u[0][q] = ux; D.u[1][q] = uy; D.u[2][q] = uz;
+    if (D.id) D.id[q] = id;
+}
+
+// Particle arriving in cell g of buffer D from elsewhere: claim an immigrant slot, else spill.
+__device__ __forceinline__ void put_imm3(const Slots& D, int cap, int cap_stay, int spill_cap, long long g,
+                                         const float o[3], float ux, float uy, float uz, int id, int* err) {
+    const int pi = atomicAdd(&D.icount[g], 1);
+    if (pi < cap - cap_stay) {
+        store3(D, (size_t)g * cap + cap_stay + pi, o, ux, uy, uz, id);
+    } else {
+        const int sp = atomicAdd(D.sn, 1);
+        if (sp < spill_cap) {
+            D.scell[sp] = (int)g;
+            D.so[0][sp] = o[0]; D.so[1][sp] = o[1]; D.so[2][sp] = o[2];
+            D.su[0][sp] = ux; D.su[1][sp] = uy; D.su[2][sp] = uz;
+            if (D.sid) D.sid[sp] = id;
+        } else {
+            atomicOr(err, ERR_SPILL_FULL);
+        }
+    }
+}
+
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// Exclusive prefix sum of one int per thread over the CTA; *total gets the sum.  wsum: NW ints
+// of shared scratch.  Contains barriers: every thread must call it.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    __syncthreads();                       // wsum free (a previous call may still read it)
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int base = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const int x = wsum[w];
+        base += w < warp ? x : 0;
+        tot += x;
+    }
+    *total = tot;
+    return base + incl - v;
+}
+
+// ------------------------------------------------------------------ tile kernel
+__global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+    const int2 wk = a.work[blockIdx.x];
+    const RunDev* Rp = &a.runs[wk.x];
+    const int nx = Rp->nx, ny = Rp->ny, nz = Rp->nz;
+    const int tile = wk.y;
+    const int tx = tile % Rp->ntx, tyz = tile / Rp->ntx;
+    const int x0 = tx * TX, y0 = (tyz % Rp->nty) * TY, z0 = (tyz / Rp->nty) * TZ;
+    const int gx0 = x0 - 1, gy0 = y0 - 1, gz0 = z0 - 1;
+    const long long step = a.ctl->step;
+    const int par = a.ctl->parity;
+    const bool diag = a.diag_interval > 0 && (step % a.diag_interval) == 0;
+    const bool anydrag = Rp->msum[0] != nullptr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long cbase = Rp->cell_off;
+
+    for (int i = tid; i < RN; i += NT) {
+        const int rz = i / RXY, rr = i - rz * RXY, ry = rr / RX, rx = rr - ry * RX;
+        const size_t g = ((size_t)wrapi(gz0 + rz, nz) * ny + wrapi(gy0 + ry, ny)) * nx + wrapi(gx0 + rx, nx);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            sm.F[c][i] = Rp->E[c][g];
+            sm.F[3 + c][i] = Rp->B[c][g];
+            sm.J32[c][i] = 0;
+            sm.J64[c][i] = 0;
+        }
+        if (anydrag) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                sm.ub[c][i] = Rp->ubar[c][g];
+                sm.Mlo[c][i] = 0u;
+                sm.Mhi[c][i] = 0;
+            }
+            sm.MC[i] = 0;
+        }
+    }
+    if (tid < 5) sm.kin[tid] = 0ull;
+    if (tid < PIC_NS) sm.sp[tid] = Rp->sp[tid];
+    // particle counts of the tile's cells: thread tid owns cell tid of each species
+    int cnt_own[PIC_NS];
+    {
+        const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
+        const long long g = cbase + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
+#pragma unroll
+        for (int s = 0; s < PIC_NS; ++s) {
+            CellRange cr{0, 0};
+            if (s < a.nspecies && Rp->sp[s].active) cr = cell_range(a.slot[s][par], a.cap[s], a.cap_stay[s], g);
+            cnt_own[s] = cr.n;
+            sm.cns[s * CELLS + tid] = cr.ns;
+            sm.scnt[s * CELLS + tid] = 0;
+        }
+    }
+    // exclusive prefix over entries e = s * CELLS + cell (species-major)
+    {
+        int tot0;
+        const int ex0 = block_exclusive_scan(cnt_own[0], sm.wsum, &tot0);
+        int tot1;
+        const int ex1 = block_exclusive_scan(cnt_own[1], sm.wsum, &tot1);
+        sm.pre[tid] = ex0;
+        sm.pre[CELLS + tid] = tot0 + ex1;
+        if (tid == 0) sm.pre[PIC_NS * CELLS] = tot0 + tot1;
+    }
+    __syncthreads();
+
+    if (diag) {
+        // field energy of the tile's own cells (each cell counted by exactly one CTA)
+        const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
+        const int n = ((lz + 1) * RY + (ly + 1)) * RX + (lx + 1);
+        double e[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const double f = sm.F[c][n];
+            e[c] = f * f;
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) e[c] += __shfl_down_sync(FULL, e[c], o);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) sm.red[warp][c] = e[c];
+        __syncthreads();
+        if (tid < 6) {
+            double s = 0.0;
+            for (int w = 0; w < NW; ++w) s += sm.red[w][tid];
+            a.partials[(size_t)blockIdx.x * 8 + tid] = s;
+        }
+    }
+
+    long long kacc[5] = {0, 0, 0, 0, 0};
+    const int ptot = sm.pre[PIC_NS * CELLS];
+    for (int b0 = 0; b0 < ptot; b0 += BATCH) {
+        // owner of each particle of the batch
+#pragma unroll
+        for (int r = 0; r < PIC_NS; ++r) {
+            const int e = r * CELLS + tid;
+            const int lo = max(sm.pre[e], b0), hi = min(sm.pre[e] + cnt_own[r], b0 + BATCH);
+            for (int p = lo; p < hi; ++p) sm.owner[p - b0] = (unsigned short)e;
+        }
+        __syncthreads();
+        // load the thread's particles of the batch
+        float po[PER_THREAD][3], pu[PER_THREAD][3];
+        int pid[PER_THREAD], pe[PER_THREAD];
+        bool pact[PER_THREAD];
+#pragma unroll
+        for (int r = 0; r < PER_THREAD; ++r) {
+            const int p = b0 + r * NT + tid;
+            pact[r] = p < ptot;
+            pe[r] = 0;
+            pid[r] = 0;
+            po[r][0] = po[r][1] = po[r][2] = 0.f;
+            pu[r][0] = pu[r][1] = pu[r][2] = 0.f;
+            if (pact[r]) {
+                const int e = sm.owner[p - b0];
+                pe[r] = e;
+                const int s = e / CELLS, ci = e - s * CELLS;
+                const int lx = ci % TX, ly = (ci / TX) % TY, lz = ci / (TX * TY);
+                const long long g = cbase + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
+                const Slots& S = a.slot[s][par];
+                const size_t q = slot_of(g, a.cap[s], a.cap_stay[s], sm.cns[e], p - sm.pre[e]);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    po[r][d] = S.o[d][q];
+                    pu[r][d] = S.u[d][q];
+                }
+                if (S.id) pid[r] = S.id[q];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < PER_THREAD; ++r) {
+            if (!pact[r]) continue;
+            const int e = pe[r];
+            const int s = e / CELLS, ci = e - s * CELLS;
+            const int lx = ci % TX, ly = (ci / TX) % TY, lz = ci / (TX * TY);
+            const int ix = lx + 1, iy = ly + 1, iz = lz + 1;
+            const int n0 = (iz * RY + iy) * RX + ix;
+            const SpeciesParams& P = sm.sp[s];
+            const int cap = a.cap[s], cst = a.cap_stay[s];
+            const Slots& D = a.slot[s][par ^ 1];
+            float b0v = 0.f, b1v = 0.f, b2v = 0.f;
+            if (P.drag) { b0v = sm.ub[0][n0]; b1v = sm.ub[1][n0]; b2v = sm.ub[2][n0]; }
+            const Pushed3 res = push3_one(SharedFields3{&sm, n0}, P, Rp, po[r], pu[r][0], pu[r][1], pu[r][2],
+                                          b0v, b1v, b2v);
+            const long long g = cbase + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
+            if (res.bad) {
+                // keep the particle where it was, unmoved; the sticky flag fails the run
+                atomicOr(&a.ctl->err, ERR_BADPART);
+                put_imm3(D, cap, cst, a.spill_cap[s], g, po[r], pu[r][0], pu[r][1], pu[r][2], pid[r], &a.ctl->err);
+                continue;
+            }
+            if (diag) kin_add(kacc, s, P.w, pu[r][0], pu[r][1], pu[r][2], res.ux, res.uy, res.uz);
+            const Win wx = window(po[r][0], res.st[0], res.no[0]);
+            const Win wy = window(po[r][1], res.st[1], res.no[1]);
+            const Win wz = window(po[r][2], res.st[2], res.no[2]);
+            const int nb = n0 + wz.off * RXY + wy.off * RX + wx.off;
+            auto add = [&](int c, int i, int j, int k, int v) {
+                if (v != 0) atomicAdd(&sm.J32[c][nb + k * RXY + j * RX + i], v);
+            };
+            deposit3(add, P, wx, wy, wz);
+            const int n1 = n0 + res.st[2] * RXY + res.st[1] * RX + res.st[0];
+            if (P.drag) {
+                add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], __float2ll_rn(res.ux * MOM_SCALE));
+                add_split(&sm.Mlo[1][n1], &sm.Mhi[1][n1], __float2ll_rn(res.uy * MOM_SCALE));
+                add_split(&sm.Mlo[2][n1], &sm.Mhi[2][n1], __float2ll_rn(res.uz * MOM_SCALE));
+                atomicAdd(&sm.MC[n1], 1);
+            }
+            const int mx = lx + res.st[0], my = ly + res.st[1], mz = lz + res.st[2];
+            const long long g1 = cbase + ((long long)wrap1(z0 + mz, nz) * ny + wrap1(y0 + my, ny)) * nx +
+                                 wrap1(x0 + mx, nx);
+            if (mx >= 0 && mx < TX && my >= 0 && my < TY && mz >= 0 && mz < TZ) {
+                // new cell inside the tile: this CTA owns its stay area
+                const int e1 = s * CELLS + (mz * TY + my) * TX + mx;
+                const int pos = atomicAdd(&sm.scnt[e1], 1);
+                if (pos < cst) store3(D, (size_t)g1 * cap + pos, res.no, res.ux, res.uy, res.uz, pid[r]);
+                else put_imm3(D, cap, cst, a.spill_cap[s], g1, res.no, res.ux, res.uy, res.uz, pid[r], &a.ctl->err);
+            } else {
+                put_imm3(D, cap, cst, a.spill_cap[s], g1, res.no, res.ux, res.uy, res.uz, pid[r], &a.ctl->err);
+            }
+        }
+        __syncthreads();
+        // batch current -> int64 bank
+        for (int i = tid; i < 3 * RN; i += NT) {
+            int* p32 = &sm.J32[0][0] + i;
+            const int v = *p32;
+            if (v) {
+                (&sm.J64[0][0])[i] += v;
+                *p32 = 0;
+            }
+        }
+        __syncthreads();
+    }
+
+    // stay-area fill of the tile's cells in the next buffer
+#pragma unroll
+    for (int s = 0; s < PIC_NS; ++s) {
+        const int v = sm.scnt[s * CELLS + tid];
+        if (v) {
+            const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
+            const long long g = cbase + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
+            a.slot[s][par ^ 1].count[g] = v;
+        }
+    }
+
+    if (diag) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            long long v = kacc[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+            if (lane == 0 && v != 0) atomicAdd(&sm.kin[k], (unsigned long long)v);
+        }
+        __syncthreads();
+        if (tid < 5 && sm.kin[tid] != 0ull) {
+            long long* K = a.kin + (size_t)wk.x * PIC_NS * 4;
+            if (tid < 2) atomicAdd((unsigned long long*)&K[tid * 4], sm.kin[tid]);
+            else atomicAdd((unsigned long long*)&K[tid - 1], sm.kin[tid]);
+        }
+    }
+
+    // flush the region to global memory (halo nodes overlap neighbouring tiles: atomics)
+    for (int i = tid; i < RN; i += NT) {
+        const int rz = i / RXY, rr = i - rz * RXY, ry = rr / RX, rx = rr - ry * RX;
+        const size_t g = ((size_t)wrapi(gz0 + rz, nz) * ny + wrapi(gy0 + ry, ny)) * nx + wrapi(gx0 + rx, nx);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long v = sm.J64[c][i];
+            if (v) atomicAdd((unsigned long long*)&Rp->J[c][g], (unsigned long long)v);
+        }
+        if (anydrag) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const long long v = (long long)sm.Mhi[c][i] * 4096 + (long long)sm.Mlo[c][i];
+                if (v) atomicAdd((unsigned long long*)&Rp->msum[c][g], (unsigned long long)v);
+            }
+            if (sm.MC[i]) atomicAdd(&Rp->mcnt[g], sm.MC[i]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ spilled particles
+// Particles that found their cell full: one thread each, global-memory gather and atomics (the
+// same formulas as the tile kernel), rebinned into the other buffer.
+__global__ void __launch_bounds__(NT) spill3d_kernel(const Args a) {
+    const int par = a.ctl->parity;
+    const long long step = a.ctl->step;
+    const bool diag = a.diag_interval > 0 && (step % a.diag_interval) == 0;
+    for (int s = 0; s < a.nspecies; ++s) {
+        const Slots S = a.slot[s][par], D = a.slot[s][par ^ 1];
+        const int ns = min(*S.sn, a.spill_cap[s]);
+        const int cap = a.cap[s], cst = a.cap_stay[s];
+        for (int k = blockIdx.x * NT + threadIdx.x; k < ns; k += gridDim.x * NT) {
+            const int g = S.scell[k];
+            int lo = 0, hi = a.nruns - 1;       // run holding cell g
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.runs[mid].cell_off <= g) lo = mid; else hi = mid - 1;
+            }
+            const int run = lo;
+            const RunDev* Rp = &a.runs[run];
+            const int nx = Rp->nx, ny = Rp->ny, nz = Rp->nz;
+            const SpeciesParams P = Rp->sp[s];
+            const long long lc = g - Rp->cell_off;
+            const int cz = (int)(lc / ((long long)nx * ny));
+            const int rem = (int)(lc - (long long)cz * nx * ny);
+            const int cy = rem / nx, cx = rem - cy * nx;
+            const float o[3] = {S.so[0][k], S.so[1][k], S.so[2][k]};
+            const float u0x = S.su[0][k], u0y = S.su[1][k], u0z = S.su[2][k];
+            const int id = S.sid ? S.sid[k] : 0;
+            float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+            if (P.drag) { b0 = Rp->ubar[0][lc]; b1 = Rp->ubar[1][lc]; b2 = Rp->ubar[2][lc]; }
+            const Pushed3 r = push3_one(GlobalFields3{Rp, cx, cy, cz}, P, Rp, o, u0x, u0y, u0z, b0, b1, b2);
+            if (r.bad) {
+                atomicOr(&a.ctl->err, ERR_BADPART);
+                put_imm3(D, cap, cst, a.spill_cap[s], g, o, u0x, u0y, u0z, id, &a.ctl->err);
+                continue;
+            }
+            if (diag) {
+                long long kacc[5] = {0, 0, 0, 0, 0};
+                kin_add(kacc, s, P.w, u0x, u0y, u0z, r.ux, r.uy, r.uz);
+                long long* K = a.kin + (size_t)run * PIC_NS * 4;
+                atomicAdd((unsigned long long*)&K[s * 4], (unsigned long long)(kacc[0] + kacc[1]));
+                for (int c = 0; c < 3; ++c) atomicAdd((unsigned long long*)&K[1 + c], (unsigned long long)kacc[2 + c]);
+            }
+            const Win wx = window(o[0], r.st[0], r.no[0]);
+            const Win wy = window(o[1], r.st[1], r.no[1]);
+            const Win wz = window(o[2], r.st[2], r.no[2]);
+            const int bx = cx + wx.off, by = cy + wy.off, bz = cz + wz.off;
+            auto add = [&](int c, int i, int j, int kk, int v) {
+                if (v != 0) {
+                    const size_t gi = ((size_t)wrapi(bz + kk, nz) * ny + wrapi(by + j, ny)) * nx + wrapi(bx + i, nx);
+                    atomicAdd((unsigned long long*)&Rp->J[c][gi], (unsigned long long)(long long)v);
+                }
+            };
+            deposit3(add, P, wx, wy, wz);
+            const int ncx = wrap1(cx + r.st[0], nx), ncy = wrap1(cy + r.st[1], ny), ncz = wrap1(cz + r.st[2], nz);
+            const long long l1 = ((long long)ncz * ny + ncy) * nx + ncx;
+            if (P.drag) {
+                atomicAdd((unsigned long long*)&Rp->msum[0][l1], (unsigned long long)__float2ll_rn(r.ux * MOM_SCALE));
+                atomicAdd((unsigned long long*)&Rp->msum[1][l1], (unsigned long long)__float2ll_rn(r.uy * MOM_SCALE));
+                atomicAdd((unsigned long long*)&Rp->msum[2][l1], (unsigned long long)__float2ll_rn(r.uz * MOM_SCALE));
+                atomicAdd(&Rp->mcnt[l1], 1);
+            }
+            put_imm3(D, cap, cst, a.spill_cap[s], Rp->cell_off + l1, r.no, r.ux, r.uy, r.uz, id, &a.ctl->err);
+        }
+    }
+}
+
+}  // namespace
+
+bool has_push3d() { return true; }
+
+cudaError_t launch_push3d(const Args& a, cudaStream_t s) {
+    if (a.nwork == 0) return cudaSuccess;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(push3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(Smem));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    push3d_kernel<<<a.nwork, NT, sizeof(Smem), s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spill3d(const Args& a, cudaStream_t s) {
+    spill3d_kernel<<<152, NT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t preload_push3d() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, push3d_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, spill3d_kernel);
+    return e;
+}
 
 }  // namespace pic

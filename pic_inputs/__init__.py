@@ -172,3 +172,30 @@ def hot_beam_3d(nx=256, ny=256, nz=512, ppc=8, seed=3, steps=2000):
     """3D3V, beam along z, T_perp=0.2, cold collisionless background, 8 ppc/species."""
     return weibel_load(ndim=3, nx=nx, ny=ny, nz=nz, ppc=ppc, T_perp_beam=0.2, seed=seed,
                        steps=steps, name=f"hot_beam_3d_{nx}x{ny}x{nz}_ppc{ppc}")
+
+
+SCAN_SIZES = (128, 192, 256, 384, 512)
+SCAN_NU = (0.0, 0.01, 0.1, 1.0)
+
+
+def scan_table(nruns=256, seed=4):
+    """The run table of the temperature / collision-rate scan: per run (nx, ny, T_perp, nu),
+    nx and ny drawn independently from SCAN_SIZES, T_perp ~ U[0, 1], nu from SCAN_NU."""
+    rng = np.random.default_rng(seed)
+    nx = rng.choice(SCAN_SIZES, nruns)
+    ny = rng.choice(SCAN_SIZES, nruns)
+    T = rng.random(nruns)
+    nu = rng.choice(SCAN_NU, nruns)
+    return [(int(nx[r]), int(ny[r]), float(T[r]), float(nu[r])) for r in range(nruns)]
+
+
+def scan_runs(nruns=256, ppc=32, seed=4, steps=2000, scale=1):
+    """Workloads of the scan table: 2D3V runs of 32 ppc/species, beam T_perp from the table,
+    background T = 0.001 with the table's Krook rate; run r is loaded with seed 1000 + r.
+    `scale` divides every grid side (small stand-ins of the same table for tests)."""
+    out = []
+    for r, (nx, ny, T, nu) in enumerate(scan_table(nruns, seed)):
+        out.append(weibel_load(ndim=2, nx=nx // scale, ny=ny // scale, ppc=ppc, T_perp_beam=T,
+                               T_bg=0.001, nu=nu, seed=1000 + r, steps=steps,
+                               name=f"scan_run{r}_{nx // scale}x{ny // scale}"))
+    return out
