@@ -17,6 +17,14 @@ every 8 steps.
 With --gpus N under torchrun each rank runs an independent replica (the single run does not
 shard); value is the sum over ranks of particle-steps over the slowest rank's time.
 --impl reference times the oracle on this machine's host cores instead.
+Other workloads (--workload):
+  hot3d  256 x 256 x 512 cells 3D3V, 8 particles per cell per species (536,870,912 particles),
+         beam T_perp = 0.2, cold collisionless background; roofline basis 56 B/particle + 64 B/cell
+  scan   the batched temperature / collision-rate scan: 256 independent 2D runs, nx and ny each
+         from {128, 192, 256, 384, 512}, 32 particles per cell per species, beam T_perp ~ U[0,1],
+         background Krook nu from {0, 0.01, 0.1, 1}; all runs stepped by one set of launches
+         (one CUDA graph per sort interval).  The line also carries the same runs stepped as
+         separate engines, one after the other ("per_run"), the unbatched baseline.
 """
 from __future__ import annotations
 
@@ -35,6 +43,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s"
 BYTES_PER_PARTICLE_2D = 48
+BYTES_PER_PARTICLE_3D = 56
 BYTES_PER_CELL = 64
 
 
@@ -98,16 +107,46 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def build_workload(args, rank):
-    import pic_inputs
-    return pic_inputs.warm_beam_krook_2d(n=args.n, ppc=args.ppc, seed=2 + 1000 * rank)
+def _workers():
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+def workload_name(args):
+    if args.workload == "warm2d":
+        return f"warm_beam_krook_2d_{args.n}x{args.n}_ppc{args.ppc}"
+    if args.workload == "hot3d":
+        nx, ny, nz = args.grid3
+        return f"hot_beam_3d_{nx}x{ny}x{nz}_ppc{args.ppc}"
+    return f"scan_{args.runs}runs_2d_ppc{args.ppc}"
+
+
+def build_load(args, rank):
+    """Particles of this rank's replica, drawn in parallel into shared memory."""
+    import pic_inputs as pi
+    if args.workload == "warm2d":
+        return pi.weibel_load_parallel(ndim=2, nx=args.n, ny=args.n, ppc=args.ppc, T_perp_beam=0.1,
+                                       T_bg=0.001, nu=0.1, seed=2 + 1000 * rank, workers=_workers(),
+                                       name=workload_name(args))
+    nx, ny, nz = args.grid3
+    return pi.weibel_load_parallel(ndim=3, nx=nx, ny=ny, nz=nz, ppc=args.ppc, T_perp_beam=0.2,
+                                   seed=3 + 1000 * rank, workers=_workers(), name=workload_name(args))
+
+
+def _oracle_sample(args):
+    """The bounded oracle sample of each workload: (workload, description)."""
+    import pic_inputs as pi
+    if args.workload == "warm2d":
+        return pi.warm_beam_krook_2d(n=128, ppc=args.ppc, seed=2), "128x128 crop"
+    if args.workload == "hot3d":
+        return pi.hot_beam_3d(nx=32, ny=32, nz=64, ppc=args.ppc, seed=3), "32x32x64 crop"
+    return (pi.weibel_load(ndim=2, nx=128, ny=128, ppc=args.ppc, T_perp_beam=0.5, T_bg=0.001,
+                           nu=0.1, seed=1000), "one 128x128 run of the scan recipe")
 
 
 def cpu_baseline(args, seconds=15.0):
-    """The oracle as it is, single-threaded, on a 128 x 128 crop of the same physics."""
+    """The oracle as it is, single-threaded, on a bounded crop of the same physics."""
     import oracle
-    import pic_inputs
-    wl = pic_inputs.warm_beam_krook_2d(n=128, ppc=args.ppc, seed=2)
+    wl, what = _oracle_sample(args)
     sim = oracle.Simulation.from_workload(wl)
     sim.step(1, record=False)   # warm-up (page-in)
     t0 = time.perf_counter()
@@ -120,7 +159,7 @@ def cpu_baseline(args, seconds=15.0):
             break
     v = wl.nparticles * steps / el
     return {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"128x128 crop, {args.ppc} ppc/species ({wl.nparticles} particles), "
+            "sample": f"{what}, {args.ppc} ppc/species ({wl.nparticles} particles), "
                       f"{steps} steps in {el:.1f} s, FP64 single-threaded C"}
 
 
@@ -131,8 +170,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": METRIC,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"warm_beam_krook_2d_{args.n}x{args.n}_ppc{args.ppc}",
-                       "oracle_sample": "128x128 crop"},
+            "config": {"workload": workload_name(args), "oracle_sample": cb["sample"]},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": cb["sample"],
                              "value": cb["value"], "unit": METRIC},
             "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0,
@@ -140,33 +178,82 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _init_dist(world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        return dist
+    return None
+
+
+def _max_over_ranks(dist, vals):
+    if dist is None:
+        return vals
+    import torch
+    t = torch.tensor(vals, device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def _roofline(alg_bytes, push_n, push_ms):
+    peak, peak_kind = _peaks()
+    push_avg_s = push_ms / max(1, push_n) / 1e3
+    achieved = alg_bytes / push_avg_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "push_deposit",
+            "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
+            "mean_launch_ms": push_avg_s * 1e3}
+
+
+def _timed_steps(eng, steps, warmup, barrier, local_rank):
+    """Warm up, then K steps between CUDA events on the engine stream, with clock sampling."""
+    import torch
+    eng.step(warmup)
+    eng.sync()
+    eng.kernel_times()            # drain warm-up timings
+    base = eng.kernel_times()
+    l0 = eng.launch_count()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    with Clocks(local_rank) as clk:
+        start.record(eng.stream)
+        eng.step(steps)
+        stop.record(eng.stream)
+        stop.synchronize()
+    barrier()
+    times = eng.kernel_times()
+    delta = {k: (times[k][0] - base[k][0], times[k][1] - base[k][1]) for k in times}
+    return start.elapsed_time(stop), eng.launch_count() - l0, delta, clk.summary()
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_0808_4078_gb300 as pic
 
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dist = _init_dist(world, local_rank)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    wl = build_workload(args, rank)
+    L = build_load(args, rank)
+    wl = L.workload
     npart = wl.nparticles
     ncell = wl.ncell
     cap = [s.n for s in wl.species]
-    eng = pic.Engine(2, wl.nx, wl.ny, dx=wl.dx, dt=wl.dt, capacity=cap, sort_interval=args.sort,
-                     diag_interval=args.diag, diag_capacity=4096, flags=pic.PIC_FLAG_PROFILE,
-                     device=f"cuda:{local_rank}")
-    stream = eng.stream
-    # ---------------- end to end through the public API from host buffers
+    eng = pic.Engine(wl.ndim, wl.nx, wl.ny, wl.nz, dx=wl.dx, dt=wl.dt, capacity=cap,
+                     sort_interval=args.sort, diag_interval=args.diag, diag_capacity=4096,
+                     flags=pic.PIC_FLAG_PROFILE, device=f"cuda:{local_rank}")
+    # ---------------- end to end through the public API from (pinned) host buffers
     host = []
     for s in wl.species:
         host.append((torch.from_numpy(s.cell).pin_memory(), torch.from_numpy(s.offset).pin_memory(),
                      torch.from_numpy(s.u).pin_memory()))
+    L.close()
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
@@ -179,68 +266,157 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     h2d = sum(s.n * (4 + 4 * wl.ndim + 12) for s in wl.species)
     d2h = len(recs) * 128
-    e2e_local = npart * args.steps / e2e_s
+    del host
 
     # ---------------- device-resident timing
-    eng.step(args.warmup)
-    eng.sync()
-    eng.kernel_times()            # drain warm-up timings
-    base_times = eng.kernel_times()
-    l0 = eng.launch_count()
-    start = torch.cuda.Event(enable_timing=True)
-    stop = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    barrier()
-    with Clocks(local_rank) as clk:
-        start.record(stream)
-        eng.step(args.steps)
-        stop.record(stream)
-        stop.synchronize()
-    barrier()
-    ms = start.elapsed_time(stop)
-    launches = eng.launch_count() - l0
-    times = eng.kernel_times()
-    push_n = times["push_deposit"][0] - base_times["push_deposit"][0]
-    push_ms = times["push_deposit"][1] - base_times["push_deposit"][1]
-    phase = {k: (times[k][1] - base_times[k][1]) / max(1, args.steps) for k in times}
-
-    t_max = ms
-    e2e_max = e2e_s
-    if dist is not None:
-        tt = torch.tensor([ms, e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max, e2e_max = float(tt[0]), float(tt[1])
+    ms, launches, delta, clocks = _timed_steps(eng, args.steps, args.warmup, barrier, local_rank)
+    phase = {k: v[1] / max(1, args.steps) for k, v in delta.items()}
+    t_max, e2e_max = _max_over_ranks(dist, [ms, e2e_s])
 
     if rank == 0:
-        peak, peak_kind = _peaks()
-        alg_bytes = npart * BYTES_PER_PARTICLE_2D + ncell * BYTES_PER_CELL
-        push_avg_s = push_ms / max(1, push_n) / 1e3
-        achieved = alg_bytes / push_avg_s / 1e9
+        bpp = BYTES_PER_PARTICLE_2D if wl.ndim == 2 else BYTES_PER_PARTICLE_3D
+        alg_bytes = npart * bpp + ncell * BYTES_PER_CELL
         value = world * npart * args.steps / (t_max / 1e3)
+        grid = [wl.nx, wl.ny] + ([wl.nz] if wl.ndim == 3 else [])
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": wl.name, "grid": [wl.nx, wl.ny], "ppc_per_species": args.ppc,
+            "config": {"workload": wl.name, "grid": grid, "ppc_per_species": args.ppc,
                        "particles_per_gpu": npart, "sort_interval": args.sort,
                        "diag_interval": args.diag, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (particles 3.2 GB/GPU), no flush"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "push_deposit", "peak_kind": peak_kind,
-                         "alg_bytes_per_launch": alg_bytes,
-                         "mean_launch_ms": push_avg_s * 1e3},
+                       "l2": f"inputs larger than L2 (particles {npart * (bpp // 2) / 1e9:.1f} GB/GPU), no flush"},
+            "roofline": _roofline(alg_bytes, *delta["push_deposit"]),
             "phase_ms_per_step": phase,
             "e2e": {"value": world * npart * args.steps / e2e_max, "unit": METRIC,
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
             "gpu_launches": launches,
-            "clocks": clk.summary(),
+            "clocks": clocks,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)
     eng.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- batched scan
+def _scan_run(job):
+    """Worker: the particles of run r of the scan table (spawned process)."""
+    import pic_inputs as pi
+    r, (nx, ny, T, nu), ppc = job
+    return r, pi.weibel_load(ndim=2, nx=nx, ny=ny, ppc=ppc, T_perp_beam=T, T_bg=0.001, nu=nu,
+                             seed=1000 + r, name=f"scan_run{r}_{nx}x{ny}")
+
+
+def _partition(table, world):
+    """Greedy longest-first assignment of runs to ranks by cell count."""
+    order = sorted(range(len(table)), key=lambda r: -table[r][0] * table[r][1])
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for r in order:
+        k = min(range(world), key=lambda i: load[i])
+        out[k].append(r)
+        load[k] += table[r][0] * table[r][1]
+    return [sorted(o) for o in out]
+
+
+def run_scan(args, rank, world, local_rank):
+    import multiprocessing as mp
+    import torch
+    import pic_inputs as pi
+    import paper_0808_4078_gb300 as pic
+
+    dist = _init_dist(world, local_rank)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    table = pi.scan_table(args.runs)
+    mine = _partition(table, world)[rank]
+    ppc = args.ppc
+    cc = 2 * ppc                      # slots per cell: twice the mean (the smallest allowed)
+    runs = [(table[r][0], table[r][1], 1, (table[r][0] * table[r][1] * ppc,) * 2) for r in mine]
+    npart = sum(2 * nx * ny * ppc for nx, ny, _, _ in runs)
+    ncell = sum(nx * ny for nx, ny, _, _ in runs)
+    kw = dict(dx=0.1, dt=0.05, sort_interval=args.sort, diag_interval=args.diag,
+              diag_capacity=1024, flags=pic.PIC_FLAG_PROFILE, cell_capacity=(cc, cc),
+              device=f"cuda:{local_rank}")
+    eng = pic.Engine(2, nspecies=2, runs=runs, **kw)
+    jobs = [(r, table[r], ppc) for r in mine]
+    idx = {r: k for k, r in enumerate(mine)}
+    # end to end: the H2D loads (timed per call, generation excluded), K steps, the D2H reads
+    load_s = 0.0
+    with mp.get_context("spawn").Pool(_workers()) as pool:
+        for r, wl in pool.imap_unordered(_scan_run, jobs):
+            t0 = time.perf_counter()
+            for i, s in enumerate(wl.species):
+                eng.load_species(i, s.q, s.m, s.w, s.nu, s.cell, s.offset, s.u, run=idx[r])
+            load_s += time.perf_counter() - t0
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    eng.step(args.steps)
+    recs = [eng.diag(run=k) for k in range(len(mine))]
+    torch.cuda.synchronize()
+    e2e_s = load_s + time.perf_counter() - t0
+    h2d = npart * 20
+    d2h = sum(len(x) for x in recs) * 128
+
+    ms, launches, delta, clocks = _timed_steps(eng, args.steps, args.warmup, barrier, local_rank)
+    phase = {k: v[1] / max(1, args.steps) for k, v in delta.items()}
+    eng.close()
+    del eng
+    torch.cuda.empty_cache()
+
+    # the same runs as separate engines, stepped one after the other
+    per_run_ms = 0.0
+    per_run_launches = 0
+    if not args.no_per_run:
+        with mp.get_context("spawn").Pool(_workers()) as pool:
+            for r, wl in pool.imap_unordered(_scan_run, jobs):
+                e1 = pic.Engine.from_workload(wl, **{k: v for k, v in kw.items() if k not in ("dx", "dt")})
+                m1, l1, _, _ = _timed_steps(e1, args.steps, args.warmup, lambda: None, local_rank)
+                per_run_ms += m1
+                per_run_launches += l1
+                e1.close()
+    t_max, e2e_max, pr_max = _max_over_ranks(dist, [ms, e2e_s, per_run_ms])
+    if dist is not None:
+        import torch.distributed as tdist
+        t = torch.tensor([float(npart)], device="cuda", dtype=torch.float64)
+        tdist.all_reduce(t)
+        tot_part = float(t[0])
+    else:
+        tot_part = float(npart)
+    if rank == 0:
+        alg_bytes = npart * BYTES_PER_PARTICLE_2D + ncell * BYTES_PER_CELL
+        line = {
+            "metric": METRIC, "value": tot_part * args.steps / (t_max / 1e3), "unit": METRIC,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(args), "runs": args.runs, "ppc_per_species": ppc,
+                       "particles": int(tot_part), "cells_rank0": ncell,
+                       "cell_capacity": cc, "sort_interval": args.sort, "diag_interval": args.diag,
+                       "parallelism": f"runs split over {world} GPU(s), greedy by cells",
+                       "l2": "inputs larger than L2, no flush"},
+            "roofline": _roofline(alg_bytes, *delta["push_deposit"]),
+            "phase_ms_per_step": phase,
+            "e2e": {"value": tot_part * args.steps / e2e_max, "unit": METRIC,
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        if not args.no_per_run:
+            line["per_run"] = {"value": tot_part * args.steps / (pr_max / 1e3), "unit": METRIC,
+                               "ms_per_step": pr_max / args.steps, "gpu_launches": per_run_launches,
+                               "what": "the same runs as separate engines, stepped one after the other"}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -251,21 +427,32 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1024)
-    ap.add_argument("--ppc", type=int, default=64)
+    ap.add_argument("--workload", default="warm2d", choices=["warm2d", "hot3d", "scan"])
+    ap.add_argument("--n", type=int, default=1024, help="2D grid side (warm2d)")
+    ap.add_argument("--grid3", type=lambda t: tuple(int(x) for x in t.split(",")),
+                    default=(256, 256, 512), help="3D grid nx,ny,nz (hot3d)")
+    ap.add_argument("--runs", type=int, default=256, help="runs of the scan")
+    ap.add_argument("--ppc", type=int, default=None,
+                    help="particles per cell per species (default 64 / 8 / 32)")
     ap.add_argument("--sort", type=int, default=8)
     ap.add_argument("--diag", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-per-run", action="store_true", help="scan: skip the per-run baseline")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.ppc is None:
+        args.ppc = {"warm2d": 64, "hot3d": 8, "scan": 32}[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    run_ours(args, rank, world, local_rank)
+    if args.workload == "scan":
+        run_scan(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
 
 
 if __name__ == "__main__":

@@ -72,15 +72,19 @@ typedef struct pic_config {
     int32_t nspecies;          /* 1..PIC_MAX_SPECIES */
     int64_t capacity[PIC_MAX_SPECIES];      /* particle capacity per species (< 2^31) */
     int32_t cell_capacity[PIC_MAX_SPECIES]; /* particle slots per cell per species; 0 = automatic
-                                               (4 x the mean per cell, multiple of 32, >= 32);
+                                               (2D: 4 x the mean per cell, multiple of 32,
+                                               >= 32; 3D: 3 x the mean, multiple of 8, >= 16);
                                                must be >= 2 x capacity / cells */
-    int32_t sort_interval;     /* steps between full counting sorts that repack spilled particles
-                                  (particles whose cell's slots were full); 0 = default (8) */
+    int32_t sort_interval;     /* steps between checks for a full counting sort that repacks
+                                  spilled particles (particles whose cell's slots were full; the
+                                  sort runs when a spill list holds > 1/16 of its capacity);
+                                  0 = default (8) */
     int32_t diag_interval;     /* steps between diagnostic records; 0 = no diagnostics */
     int32_t diag_capacity;     /* records kept in the device history ring (>= 1 if diag) */
     int32_t track_ids;         /* 1: carry an int32 id per particle (its load index) */
     int32_t flags;             /* PIC_FLAG_* */
-    int32_t tile_x, tile_y, tile_z; /* 0 = default (16 x 16 in 2D) */
+    int32_t tile_x, tile_y, tile_z; /* 0 = default; the kernels are built for 16 x 16 (2D) and
+                                       8 x 8 x 4 (3D), other values are rejected */
 } pic_config;
 
 typedef struct pic_species {
@@ -143,7 +147,8 @@ int pic_load_species_run(pic_ctx* ctx, int run, int s, const pic_species* sp, in
 
 /* Advance nsteps steps: gather + Boris + drag + move + Esirkepov deposit + re-binning of every
  * particle into its new cell, Yee update, a full counting sort every sort_interval steps when
- * particles have spilled, diagnostics every diag_interval steps.  Asynchronous. */
+ * the spill lists have grown (see sort_interval), diagnostics every diag_interval steps.
+ * Asynchronous. */
 int pic_step(pic_ctx* ctx, int nsteps);
 
 /* Wait for the stream; report sticky device errors. */

@@ -211,9 +211,11 @@ __global__ void staged_zero_kernel(Args a, int s, const int* gate) {
 }
 
 // Gate of the periodic re-sort: 1 if any species has spilled particles in the current buffer.
+// The spill kernel processes spilled particles every step, so the list only needs repacking
+// before it can fill: re-sort when any species' list holds more than 1/16 of its capacity.
 __global__ void spill_gate_kernel(Args a) {
     int any = 0;
-    for (int s = 0; s < a.nspecies; ++s) any |= *a.slot[s][a.ctl->parity].sn > 0;
+    for (int s = 0; s < a.nspecies; ++s) any |= *a.slot[s][a.ctl->parity].sn > a.spill_cap[s] / 16;
     *a.gate = any;
 }
 

@@ -114,14 +114,21 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
         if (s >= c->nspecies) continue;
         if (g->capacity[s] >= (1ll << 31)) { *err = "capacity must be < 2^31 per species"; return PIC_EINVAL; }
         const long long mean = (g->capacity[s] + g->ncell - 1) / g->ncell;
-        long long cap = c->cell_capacity[s] > 0 ? c->cell_capacity[s] : ((4 * mean + 31) / 32) * 32;
-        if (cap < 32 && c->cell_capacity[s] <= 0) cap = 32;
+        // default slots per cell: 2D 4x the mean in warp multiples (a warp owns a cell), 3D 3x
+        // the mean in multiples of 8 (a thread per particle; 8 floats fill a 32-byte sector)
+        long long cap = c->cell_capacity[s];
+        if (cap <= 0) {
+            cap = c->ndim == 2 ? ((4 * mean + 31) / 32) * 32 : ((3 * mean + 7) / 8) * 8;
+            cap = std::max(cap, c->ndim == 2 ? 32ll : 16ll);
+        }
         if (cap < 2 || cap > 65535) { *err = "cell_capacity must be in [2, 65535]"; return PIC_EINVAL; }
         if (cap * g->ncell < 2 * g->capacity[s]) { *err = "cell_capacity must be >= 2 x capacity / cells"; return PIC_EINVAL; }
         if (cap * g->ncell >= (1ll << 31)) { *err = "cells x cell_capacity must be < 2^31"; return PIC_EINVAL; }
         g->cap[s] = (int)cap;
-        // immigrant area: a quarter of the slots (>= 1); the rest keeps the cell's stayers
-        long long ci = (cap + 3) / 4;
+        // immigrant area (>= 1 slot): 2D a quarter of the slots (only particles crossing a tile
+        // edge arrive there); 3D half, since the beam's z flux through the bottom layer of a
+        // 4-cell-deep tile is ~half its particles per step.  The rest keeps the cell's stayers.
+        long long ci = c->ndim == 2 ? (cap + 3) / 4 : (cap + 1) / 2;
         if (ci < 1) ci = 1;
         if (ci >= cap) ci = cap > 1 ? cap - 1 : 0;
         g->cap_stay[s] = (int)(cap - ci);

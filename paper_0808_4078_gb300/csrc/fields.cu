@@ -134,64 +134,62 @@ __global__ void __launch_bounds__(NT) yee_e_2d_tiles(Args a, float dt) {
 }
 
 // ------------------------------------------------------------------ 3D Yee
-__global__ void yee_b_half_3d(const RunDev* __restrict__ runs, int run) {
+// Thread per cell on a 3D launch grid (32 x 8 threads per block along x, y; one z plane per
+// block row), so no index division; neighbours come through L1/L2.
+constexpr int Y3X = 32, Y3Y = 8;
+
+__global__ void __launch_bounds__(Y3X * Y3Y) yee_b_half_3d(const RunDev* __restrict__ runs, int run) {
     const RunDev& R = runs[run];
     const int nx = R.nx, ny = R.ny, nz = R.nz;
-    const long long nxy = (long long)nx * ny, n = nxy * nz;
+    const int i = blockIdx.x * Y3X + threadIdx.x, j = blockIdx.y * Y3Y + threadIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const long long nxy = (long long)nx * ny;
+    const long long c = k * nxy + (long long)j * nx + i;
     const float hx = 0.5f * R.cx, hy = 0.5f * R.cy, hz = 0.5f * R.cz;
     const float* __restrict__ Ex = R.E[0];
     const float* __restrict__ Ey = R.E[1];
     const float* __restrict__ Ez = R.E[2];
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-         c += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(c / nxy);
-        const long long r = c - (long long)k * nxy;
-        const int j = (int)(r / nx), i = (int)(r - (long long)j * nx);
-        const long long dxp = (i + 1 == nx ? -(long long)(nx - 1) : 1);
-        const long long dyp = (j + 1 == ny ? -(long long)(ny - 1) * nx : nx);
-        const long long dzp = (k + 1 == nz ? -(long long)(nz - 1) * nxy : nxy);
-        const float ex = Ex[c], ey = Ey[c], ez = Ez[c];
-        R.B[0][c] -= hy * (Ez[c + dyp] - ez) - hz * (Ey[c + dzp] - ey);
-        R.B[1][c] -= hz * (Ex[c + dzp] - ex) - hx * (Ez[c + dxp] - ez);
-        R.B[2][c] -= hx * (Ey[c + dxp] - ey) - hy * (Ex[c + dyp] - ex);
-    }
+    const long long dxp = (i + 1 == nx ? -(long long)(nx - 1) : 1);
+    const long long dyp = (j + 1 == ny ? -(long long)(ny - 1) * nx : nx);
+    const long long dzp = (k + 1 == nz ? -(long long)(nz - 1) * nxy : nxy);
+    const float ex = Ex[c], ey = Ey[c], ez = Ez[c];
+    R.B[0][c] -= hy * (Ez[c + dyp] - ez) - hz * (Ey[c + dzp] - ey);
+    R.B[1][c] -= hz * (Ex[c + dzp] - ex) - hx * (Ez[c + dxp] - ez);
+    R.B[2][c] -= hx * (Ey[c + dxp] - ey) - hy * (Ex[c + dyp] - ex);
 }
 
-__global__ void yee_e_3d(const RunDev* __restrict__ runs, int run, float dt) {
+__global__ void __launch_bounds__(Y3X * Y3Y) yee_e_3d(const RunDev* __restrict__ runs, int run, float dt) {
     const RunDev& R = runs[run];
     const int nx = R.nx, ny = R.ny, nz = R.nz;
-    const long long nxy = (long long)nx * ny, n = nxy * nz;
+    const int i = blockIdx.x * Y3X + threadIdx.x, j = blockIdx.y * Y3Y + threadIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const long long nxy = (long long)nx * ny;
+    const long long c = k * nxy + (long long)j * nx + i;
     const float cx = R.cx, cy = R.cy, cz = R.cz, js = R.jscale * dt;
     const float* __restrict__ Bx = R.B[0];
     const float* __restrict__ By = R.B[1];
     const float* __restrict__ Bz = R.B[2];
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-         c += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(c / nxy);
-        const long long r = c - (long long)k * nxy;
-        const int j = (int)(r / nx), i = (int)(r - (long long)j * nx);
-        const long long dxm = (i == 0 ? -(long long)(nx - 1) : 1);
-        const long long dym = (j == 0 ? -(long long)(ny - 1) * nx : nx);
-        const long long dzm = (k == 0 ? -(long long)(nz - 1) * nxy : nxy);
-        const long long j0 = R.J[0][c], j1 = R.J[1][c], j2 = R.J[2][c];
-        const float jx = (float)j0 * js, jy = (float)j1 * js, jz = (float)j2 * js;
-        R.J[0][c] = 0; R.J[1][c] = 0; R.J[2][c] = 0;
-        if (R.Jlast[0]) { R.Jlast[0][c] = j0; R.Jlast[1][c] = j1; R.Jlast[2][c] = j2; }
-        const float bx = Bx[c], by = By[c], bz = Bz[c];
-        R.E[0][c] += cy * (bz - Bz[c - dym]) - cz * (by - By[c - dzm]) - jx;
-        R.E[1][c] += cz * (bx - Bx[c - dzm]) - cx * (bz - Bz[c - dxm]) - jy;
-        R.E[2][c] += cx * (by - By[c - dxm]) - cy * (bx - Bx[c - dym]) - jz;
-        if (R.msum[0]) {
-            const int cnt = R.mcnt[c];
-            const float inv = cnt > 0 ? 1.0f / (float)cnt : 0.f;
-            const float sc = inv * (1.0f / 1048576.0f);
+    const long long dxm = (i == 0 ? -(long long)(nx - 1) : 1);
+    const long long dym = (j == 0 ? -(long long)(ny - 1) * nx : nx);
+    const long long dzm = (k == 0 ? -(long long)(nz - 1) * nxy : nxy);
+    const long long j0 = R.J[0][c], j1 = R.J[1][c], j2 = R.J[2][c];
+    const float jx = (float)j0 * js, jy = (float)j1 * js, jz = (float)j2 * js;
+    R.J[0][c] = 0; R.J[1][c] = 0; R.J[2][c] = 0;
+    if (R.Jlast[0]) { R.Jlast[0][c] = j0; R.Jlast[1][c] = j1; R.Jlast[2][c] = j2; }
+    const float bx = Bx[c], by = By[c], bz = Bz[c];
+    R.E[0][c] += cy * (bz - Bz[c - dym]) - cz * (by - By[c - dzm]) - jx;
+    R.E[1][c] += cz * (bx - Bx[c - dzm]) - cx * (bz - Bz[c - dxm]) - jy;
+    R.E[2][c] += cx * (by - By[c - dxm]) - cy * (bx - Bx[c - dym]) - jz;
+    if (R.msum[0]) {
+        const int cnt = R.mcnt[c];
+        const float inv = cnt > 0 ? 1.0f / (float)cnt : 0.f;
+        const float sc = inv * (1.0f / 1048576.0f);
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                R.ubar[q][c] = (float)R.msum[q][c] * sc;
-                R.msum[q][c] = 0;
-            }
-            R.mcnt[c] = 0;
+        for (int q = 0; q < 3; ++q) {
+            R.ubar[q][c] = (float)R.msum[q][c] * sc;
+            R.msum[q][c] = 0;
         }
+        R.mcnt[c] = 0;
     }
 }
 
@@ -406,11 +404,11 @@ cudaError_t launch_yee2d(const Args& a, const RunDev*, int, cudaStream_t s) {
 
 cudaError_t launch_yee3d(const Args& a, const RunDev* host_runs, int nruns, cudaStream_t s) {
     for (int r = 0; r < nruns; ++r) {
-        const long long n = (long long)host_runs[r].nx * host_runs[r].ny * host_runs[r].nz;
-        const int g = grid_for(n);
-        yee_b_half_3d<<<g, NT, 0, s>>>(a.runs, r);
-        yee_e_3d<<<g, NT, 0, s>>>(a.runs, r, (float)a.dt);
-        yee_b_half_3d<<<g, NT, 0, s>>>(a.runs, r);
+        const RunDev& R = host_runs[r];
+        const dim3 grid((R.nx + Y3X - 1) / Y3X, R.ny / Y3Y, R.nz), block(Y3X, Y3Y);
+        yee_b_half_3d<<<grid, block, 0, s>>>(a.runs, r);
+        yee_e_3d<<<grid, block, 0, s>>>(a.runs, r, (float)a.dt);
+        yee_b_half_3d<<<grid, block, 0, s>>>(a.runs, r);
     }
     return cudaGetLastError();
 }

@@ -7,7 +7,7 @@
 // species, all cells) form one flat list; the CTA walks it in batches of 512, one particle per
 // thread per half batch.  In three dimensions a large share of the beam crosses a cell edge
 // every step (v_z dt / dz ~ 0.47), so there is no per-cell fast path: every particle deposits
-// its (up to) 3 x 18 current terms with 32-bit shared atomics.  A batch adds at most 512 terms
+// its (up to) 3 x 18 current terms with predicated 32-bit shared reductions.  A batch adds at most 512 terms
 // of magnitude <= 2^21 to any node, so the int32 accumulators cannot overflow; after each batch
 // they are moved into an int64 shared bank (each thread owns fixed nodes, no atomics).  Particles
 // that stay inside the tile claim their new slot through a shared per-cell counter; only those
@@ -194,6 +194,13 @@ __device__ __forceinline__ void deposit3(const Add& add, const SpeciesParams& P,
 #pragma unroll
             for (int m = 0; m < 2; ++m) add(2, k, l, m, round_small(__fmul_rn(P.jz, wz.C[m]), f));
         }
+}
+
+// Shared-memory reduction without a branch: `red` only when v != 0 (predicated).
+__device__ __forceinline__ void red_shared_nz(int* p, int v) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %1, 0;\n\t@q red.shared.add.s32 [%0], %1;\n\t}\n"
+                 ::"r"(a), "r"(v) : "memory");
 }
 
 // ------------------------------------------------------------------ rebinning
@@ -407,7 +414,7 @@ __global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
             const Win wz = window(po[r][2], res.st[2], res.no[2]);
             const int nb = n0 + wz.off * RXY + wy.off * RX + wx.off;
             auto add = [&](int c, int i, int j, int k, int v) {
-                if (v != 0) atomicAdd(&sm.J32[c][nb + k * RXY + j * RX + i], v);
+                red_shared_nz(&sm.J32[c][nb + k * RXY + j * RX + i], v);
             };
             deposit3(add, P, wx, wy, wz);
             const int n1 = n0 + res.st[2] * RXY + res.st[1] * RX + res.st[0];

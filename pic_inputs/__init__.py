@@ -199,3 +199,115 @@ def scan_runs(nruns=256, ppc=32, seed=4, steps=2000, scale=1):
                                T_bg=0.001, nu=nu, seed=1000 + r, steps=steps,
                                name=f"scan_run{r}_{nx // scale}x{ny // scale}"))
     return out
+
+
+# ---------------------------------------------------------------- parallel generation
+# Large loads (hundreds of millions of particles) drawn by a pool of processes into shared
+# memory.  Same distributions as weibel_load; the streams differ (one child seed per chunk of
+# cells), so the particles are not the same as weibel_load's for the same seed.
+
+def _chunk_fill(args):
+    (shm_names, n_total, ndim, nx, ny, nz, ppc, c0, c1, seed, chunk, sb, spar, sp, uz0) = args
+    from multiprocessing import shared_memory
+    bufs = [shared_memory.SharedMemory(name=nm) for nm in shm_names]
+    try:
+        views = _views(bufs, n_total, ndim)
+        rng_b, rng_p = [np.random.default_rng(s) for s in
+                        np.random.SeedSequence([seed, chunk]).spawn(2)]
+        p0, p1 = c0 * ppc, c1 * ppc
+        n = p1 - p0
+        cells = np.repeat(np.arange(c0, c1, dtype=np.int32), ppc)
+        for s, rng in ((0, rng_b), (1, rng_p)):
+            cell, off, u = views[s]
+            cell[p0:p1] = cells
+            off[:, p0:p1] = rng.random((ndim, n), dtype=np.float32)
+        cell, off, u = views[0]
+        u[0, p0:p1] = rng_b.standard_normal(n, dtype=np.float32) * np.float32(sb) if sb > 0 else 0.0
+        u[1, p0:p1] = rng_b.standard_normal(n, dtype=np.float32) * np.float32(sb) if sb > 0 else 0.0
+        u[2, p0:p1] = np.float32(uz0) + (rng_b.standard_normal(n, dtype=np.float32) * np.float32(spar)
+                                         if spar > 0 else np.float32(0.0))
+        cell, off, u = views[1]
+        for a in range(3):       # thermal parts; the drift is added to u_z afterwards
+            u[a, p0:p1] = rng_p.standard_normal(n, dtype=np.float32) * np.float32(sp) if sp > 0 else 0.0
+        # partial sums for the drift solve: beam current and nothing else
+        ub = views[0][2][:, p0:p1].astype(np.float64)
+        beam_v = float(np.sum(ub[2] / np.sqrt(1.0 + (ub * ub).sum(0))))
+        del views, ub
+        return beam_v
+    finally:
+        for b in bufs:
+            b.close()
+
+
+def _views(bufs, n_total, ndim):
+    out = []
+    for s in range(2):
+        cell = np.ndarray((n_total,), np.int32, buffer=bufs[3 * s].buf)
+        off = np.ndarray((ndim, n_total), np.float32, buffer=bufs[3 * s + 1].buf)
+        u = np.ndarray((3, n_total), np.float32, buffer=bufs[3 * s + 2].buf)
+        out.append((cell, off, u))
+    return out
+
+
+class SharedLoad:
+    """A Workload whose particle arrays live in shared memory; close() releases them."""
+
+    def __init__(self, workload, bufs):
+        self.workload = workload
+        self._bufs = bufs
+
+    def close(self):
+        self.workload = None
+        for b in self._bufs:
+            b.close()
+            b.unlink()
+        self._bufs = []
+
+
+def weibel_load_parallel(*, ndim=2, nx, ny, nz=1, ppc, gamma_b=3.0, nb=0.1, T_perp_beam=0.0,
+                         T_par_beam=0.0, T_bg=0.0, nu=0.0, seed=1, dx=0.1, dt=0.05, steps=0,
+                         workers=8, name=None) -> SharedLoad:
+    """weibel_load's distributions drawn by `workers` processes (spawned) into shared memory.
+
+    The background drift that zeroes the sampled current sum_p w v_z is solved in FP64 over all
+    particles after the draw, as in weibel_load."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    if ndim == 2:
+        nz = 1
+    ncell = nx * ny * nz
+    n = ncell * ppc
+    bufs = []
+    for _ in range(2):
+        bufs.append(shared_memory.SharedMemory(create=True, size=max(4 * n, 4)))
+        bufs.append(shared_memory.SharedMemory(create=True, size=max(4 * ndim * n, 4)))
+        bufs.append(shared_memory.SharedMemory(create=True, size=max(12 * n, 4)))
+    try:
+        nchunk = max(1, min(4 * workers, ncell))
+        edges = np.linspace(0, ncell, nchunk + 1).astype(np.int64)
+        uz0 = math.sqrt(gamma_b * gamma_b - 1.0)
+        jobs = [([b.name for b in bufs], n, ndim, nx, ny, nz, ppc, int(edges[k]), int(edges[k + 1]),
+                 seed, k, math.sqrt(T_perp_beam), math.sqrt(T_par_beam), math.sqrt(T_bg), uz0)
+                for k in range(nchunk)]
+        with mp.get_context("spawn").Pool(workers) as pool:
+            beam_v = sum(pool.map(_chunk_fill, jobs))
+        views = _views(bufs, n, ndim)
+        wb, wp = nb / ppc, (1.0 - nb) / ppc
+        ubg = views[1][2]
+        duz = ubg[2].astype(np.float64)
+        uperp2 = ubg[0].astype(np.float64) ** 2 + ubg[1].astype(np.float64) ** 2
+        d = _solve_drift(-wb * beam_v / wp, duz, uperp2)
+        del uperp2
+        ubg[2][:] = (d + duz).astype(np.float32)
+        del duz
+        sp = [SpeciesLoad("beam", ELECTRON_Q, ELECTRON_M, wb, 0.0, *views[0]),
+              SpeciesLoad("background", ELECTRON_Q, ELECTRON_M, wp, nu, *views[1])]
+        if name is None:
+            dims = f"{nx}x{ny}" + (f"x{nz}" if ndim == 3 else "")
+            name = f"weibel_{ndim}d_{dims}_ppc{ppc}"
+        return SharedLoad(Workload(name, ndim, nx, ny, nz, dx, dx, dx, dt, steps, sp), bufs)
+    except BaseException:
+        for b in bufs:
+            b.close()
+            b.unlink()
+        raise
