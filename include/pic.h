@@ -204,6 +204,39 @@ typedef struct pic_stats {
 /* Occupancy of the particle bins of the current buffer.  Synchronises. */
 int pic_get_stats(pic_ctx* ctx, pic_stats* out);
 
+/* ---------------------------------------------------------------- moment recorder
+ * Coarse-grained state of run `run` at the current step: the inputs and the label parts of a
+ * learned collision closure.  The paper's conclusion conjectures that the collisional friction on
+ * the return current could be written through the local plasma state; the closure's inputs and
+ * label are not given there, so these rows are this library's reading of it.
+ *
+ * Coarse cell = bx x by transverse cells x the whole z extent (3D) or bx x by cells (2D); bx, by
+ * must divide nx, ny.  ncoarse = (nx / bx) (ny / by), numbered x fastest.  Particles count in the
+ * coarse cell of the cell that holds them; species 0 is the beam (b), species 1 the background
+ * (p), weights w as loaded.  out[row * ncoarse + c], float, rows:
+ *   0 n_b, 1 n_p        sum w / cells of the coarse cell (density, units n0)
+ *   2 uz_b, 3 uz_p      w-weighted mean u_z
+ *   4 Tperp_b, 5 Tpar_b (Var u_x + Var u_y) / 2 and Var u_z of the beam (w-weighted variances of
+ *   6 Tperp_p, 7 Tpar_p  the momentum u = gamma v / c), the same for the background
+ *   8 W_ES              mean over the coarse cell's cells of sum_c (E_c - <E_c>_z)^2 with <E_c>_z
+ *                       the mean of the stored E_c over the z column (0 in 2D)
+ *   9 Fz_p              w-weighted mean of q (E + v x B)_z over the background particles, E and B
+ *                       interpolated to each particle (CIC on the Yee lattice), v = u / gamma
+ *   10 Fz_mean          q (Ebar_z + vbar_x Bbar_y - vbar_y Bbar_x): Ebar, Bbar means of the stored
+ *                       fields over the coarse cell, vbar the background's mean velocity
+ *   11 nu_eff           nu_p + (Fz_mean - Fz_p) / uz_p (0 where uz_p = 0), nu_p the background's
+ *                       Krook rate; a single snapshot (a time average over 1/w_p averages rows
+ *                       3, 9, 10 over snapshots first)
+ * out: device memory of >= PIC_MOM_ROWS * ncoarse floats (out_cap floats).  scratch: device
+ * memory of >= pic_record_moments_scratch_bytes() bytes, 8-byte aligned; both owned by the caller
+ * and in use until the context's stream passes the call.  Particle sums are int64 fixed point, so
+ * the record is bitwise reproducible.  Asynchronous on the context's stream; *ncoarse_out (may be
+ * NULL) = ncoarse.  PIC_EINVAL on bad blocks, sizes, alignment or fewer than 2 species. */
+#define PIC_MOM_ROWS 12
+int pic_record_moments_scratch_bytes(pic_ctx* ctx, int run, int bx, int by, size_t* bytes_out);
+int pic_record_moments(pic_ctx* ctx, int run, int bx, int by, float* out, int64_t out_cap,
+                       void* scratch, size_t scratch_bytes, int64_t* ncoarse_out);
+
 /* Counting sort by cell, the binning primitive of the re-binning step, on caller device memory:
  * cell[n] (device) holds each particle's cell in [0, ncell); writes start[ncell + 1] (device;
  * start[c] = number of particles in cells below c) and order[n] (device; order[start[c] ..

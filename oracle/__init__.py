@@ -89,6 +89,8 @@ def lib():
         _lib.orc_deposit_move.argtypes = [ctypes.POINTER(_Grid), ctypes.c_double, P, P,
                                           ctypes.c_double]
         _lib.orc_deposit_move.restype = None
+        _lib.orc_gather_many.argtypes = [ctypes.POINTER(_Grid), ctypes.c_int64, P, P, P, P]
+        _lib.orc_gather_many.restype = None
     return _lib
 
 
@@ -207,6 +209,20 @@ class Simulation:
         out = np.zeros(6)
         g = self.cgrid()
         lib().orc_gather(ctypes.byref(g), X, Y, Z, _ptr(out))
+        return out
+
+    def gather_many(self, X, Y, Z=None):
+        """E and B (n x 6) at the positions X, Y(, Z) in cell units, one orc_gather each."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        Y = np.ascontiguousarray(Y, dtype=np.float64)
+        Zp = None
+        if Z is not None and self.ndim == 3:
+            Z = np.ascontiguousarray(Z, dtype=np.float64)
+            Zp = _ptr(Z)
+        out = np.zeros((X.shape[0], 6))
+        g = self.cgrid()
+        lib().orc_gather_many(ctypes.byref(g), ctypes.c_int64(X.shape[0]), _ptr(X), _ptr(Y), Zp,
+                              _ptr(out))
         return out
 
     def deposit_move(self, qw, P0, P1, vz=0.0):

@@ -478,3 +478,10 @@ void orc_deposit_move(orc_grid *g, double qw, const double P0[3], const double P
     if (g->ndim == 2) deposit_2d(g, qw, P0[0], P0[1], P1[0], P1[1], vz);
     else deposit_3d(g, qw, P0, P1);
 }
+
+/* E and B at n positions (cell units), out[6 * p + c]; the same gather as the push. */
+void orc_gather_many(const orc_grid *g, int64_t n, const double *X, const double *Y,
+                     const double *Z, double *out) {
+    for (int64_t p = 0; p < n; p++)
+        orc_gather(g, X[p], Y[p], Z ? Z[p] : 0.0, out + 6 * p);
+}

@@ -99,11 +99,20 @@ _SIGNATURES = {
     "pic_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(Stats)]),
     "pic_bin_cells_scratch_bytes": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
     "pic_bin_cells": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "pic_record_moments_scratch_bytes": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                        ctypes.POINTER(ctypes.c_size_t)]),
+    "pic_record_moments": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int64,
+                                          _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64)]),
     "pic_launch_count": (ctypes.c_int64, [_VP]),
     "pic_step_count": (ctypes.c_int64, [_VP]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
     "pic_free": (None, [_VP]),
 }
+
+
+PIC_MOM_ROWS = 12
+MOMENT_ROWS = ("n_b", "n_p", "uz_b", "uz_p", "Tperp_b", "Tpar_b", "Tperp_p", "Tpar_p", "W_ES",
+               "Fz_p", "Fz_mean", "nu_eff")
 
 
 def lib():
@@ -278,6 +287,24 @@ class Engine:
         return dict(particles=list(st.particles)[:n], max_cell=list(st.max_cell)[:n],
                     spilled=list(st.spilled)[:n], cell_capacity=list(st.cell_capacity)[:n],
                     flags=st.flags)
+
+    def record_moments(self, bx=4, by=4, run=0, out=None):
+        """Coarse-grained closure moments (pic_record_moments): a (PIC_MOM_ROWS, ncoarse) float32
+        tensor on the engine's device (written into `out` if given), rows MOMENT_ROWS."""
+        torch = self._torch
+        nb = ctypes.c_size_t(0)
+        _check(lib().pic_record_moments_scratch_bytes(self._ctx, run, bx, by, ctypes.byref(nb)), self._ctx)
+        nx, ny = self.runs[run][0], self.runs[run][1]
+        nc = (nx // bx) * (ny // by)
+        if out is None:
+            out = torch.empty((PIC_MOM_ROWS, nc), dtype=torch.float32, device=self.device)
+        scratch = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        n = ctypes.c_int64(0)
+        _check(lib().pic_record_moments(self._ctx, run, bx, by, _VP(out.data_ptr()), out.numel(),
+                                        _VP(scratch.data_ptr()), nb.value, ctypes.byref(n)), self._ctx)
+        # the scratch tensor is released when this returns: let the stream finish with it first
+        self.sync()
+        return out
 
     def launch_count(self):
         return int(lib().pic_launch_count(self._ctx))

@@ -205,6 +205,7 @@ struct pic_ctx {
     std::vector<RunDev> runs;
     Args args{};
     std::vector<long long> loaded;      // [nruns][PIC_NS]
+    std::vector<double> nu;             // [nruns][PIC_NS] Krook rates as loaded
     double q[PIC_NS] = {0, 0};
     bool q_set[PIC_NS] = {false, false};
     long long host_step = 0;
@@ -408,11 +409,13 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
     ctx->arena = (char*)device_arena;
     ctx->sort_interval = cfg->sort_interval > 0 ? cfg->sort_interval : 8;
     ctx->loaded.assign((size_t)nruns * PIC_NS, 0);
+    ctx->nu.assign((size_t)nruns * PIC_NS, 0.0);
 
     auto bail = [&](int code) { g_init_error = ctx->err; delete ctx; return code; };
 #define CKI(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { fail(ctx, PIC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); return bail(PIC_ECUDA); } } while (0)
     CKI(preload_push2d());
     CKI(preload_push3d());
+    CKI(preload_moments());
     CKI(preload_bins());
     CKI(preload_fields());
     CKI(cudaMemsetAsync(ctx->arena, 0, L.total, ctx->stream));
@@ -543,6 +546,7 @@ int load_run(pic_ctx* ctx, int run, int s, const pic_species* sp, int64_t n, con
         return rc;
     }
     ctx->loaded[(size_t)run * PIC_NS + s] = n;
+    ctx->nu[(size_t)run * PIC_NS + s] = sp->nu;
     ctx->q[s] = sp->q;
     ctx->q_set[s] = true;
 
@@ -874,6 +878,48 @@ extern "C" int pic_bin_cells_noalloc(const int32_t* cell, int64_t n, int32_t nce
     if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, "scratch lookup: %s", cudaGetErrorString(e));
     e = launch_bin_cells(cell, n, ncell, start, order, scratch, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, "pic_bin_cells_noalloc: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+namespace {
+int moment_geometry(pic_ctx* ctx, int run, int bx, int by, long long* nc, long long* ncol) {
+    if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    int rc = check_run(ctx, run);
+    if (rc) return rc;
+    const RunDev& R = ctx->runs[run];
+    if (bx < 1 || by < 1 || R.nx % bx || R.ny % by)
+        return fail(ctx, PIC_EINVAL, "coarse block %d x %d must divide the grid %d x %d", bx, by, R.nx, R.ny);
+    *nc = (long long)(R.nx / bx) * (R.ny / by);
+    *ncol = (long long)R.nx * R.ny;
+    return PIC_OK;
+}
+}  // namespace
+
+extern "C" int pic_record_moments_scratch_bytes(pic_ctx* ctx, int run, int bx, int by, size_t* bytes_out) {
+    long long nc, ncol;
+    int rc = moment_geometry(ctx, run, bx, by, &nc, &ncol);
+    if (rc) return rc;
+    if (!bytes_out) return fail(ctx, PIC_EINVAL, "null bytes_out");
+    *bytes_out = moments_scratch_bytes(nc, ncol);
+    return PIC_OK;
+}
+
+extern "C" int pic_record_moments(pic_ctx* ctx, int run, int bx, int by, float* out, int64_t out_cap,
+                                  void* scratch, size_t scratch_bytes, int64_t* ncoarse_out) {
+    long long nc, ncol;
+    int rc = moment_geometry(ctx, run, bx, by, &nc, &ncol);
+    if (rc) return rc;
+    if (!out || !scratch) return fail(ctx, PIC_EINVAL, "null out or scratch");
+    if (out_cap < (int64_t)PIC_MOM_ROWS * nc)
+        return fail(ctx, PIC_EINVAL, "out holds %lld floats, needs %lld", (long long)out_cap, (long long)PIC_MOM_ROWS * nc);
+    if (scratch_bytes < moments_scratch_bytes(nc, ncol))
+        return fail(ctx, PIC_EINVAL, "scratch has %zu bytes, needs %zu", scratch_bytes, moments_scratch_bytes(nc, ncol));
+    if (reinterpret_cast<uintptr_t>(scratch) & 7) return fail(ctx, PIC_EINVAL, "scratch must be 8-byte aligned");
+    if (ctx->cfg.nspecies < 2) return fail(ctx, PIC_EINVAL, "the recorder needs beam and background species");
+    const float q_bg = (float)ctx->q[1];
+    const float nu_bg = (float)ctx->nu[(size_t)run * PIC_NS + 1];
+    CK(launch_moments(ctx->args, ctx->runs[run], run, bx, by, q_bg, nu_bg, out, scratch, ctx->stream));
+    if (ncoarse_out) *ncoarse_out = nc;
     return PIC_OK;
 }
 

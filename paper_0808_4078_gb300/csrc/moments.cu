@@ -1,0 +1,319 @@
+// moments.cu -- coarse-grained moment recorder: the inputs and label parts of the learned
+// collision closure, per coarse cell (bx x by transverse cells x the whole z extent).
+//
+// The paper closes by conjecturing that the collisional drag on the return current could be
+// written through the local plasma state; the quantities recorded here are the reading of that
+// closure's inputs and label (rows in pic.h: densities, mean u_z, momentum variances of beam and
+// background, electrostatic fluctuation energy W_ES, and the background's mean particle force
+// against the force of the coarse-grained fields).
+//
+// Two passes over the particles: the first sums w and w u per coarse cell and species, the
+// second the centred second moments w (u - <u>)^2 (variances of a cold beam are ~1e-6 of <u>^2,
+// far below what <u^2> - <u>^2 resolves) and the background's force and velocity sums.  Sums are
+// int64 fixed point (2^36 per unit; a coarse cell's sum of |w u| must stay below 2^27),
+// accumulated per CTA and added with one atomic per quantity, so they do not depend on the order
+// of the particles; the field column sums are FP64 in a fixed order.  The record is bitwise
+// reproducible.
+#include "pic_internal.cuh"
+
+namespace pic {
+
+// psum rows: pass 1 per species w, w ux, w uy, w uz (rows 4 s + 0..3); pass 2 per species
+// w (ux - <ux>)^2, w (uy - <uy>)^2, w (uz - <uz>)^2 (rows 8 + 3 s + 0..2), then the background's
+// w Fz, w vx, w vy, w vz (rows 14..17).
+constexpr int MOM_PSUMS = 18;
+constexpr int MOM_COLS = 4;                 // per column: W_ES mean, mean Ez, mean Bx, mean By
+constexpr double MOM_FIX = 68719476736.0;   // 2^36
+
+namespace {
+
+constexpr int NT = 256;
+
+struct MomArgs {
+    Args a;
+    int run;
+    int bx, by;        // coarse block in cells
+    int zc;            // z layers per CTA
+    int ncx, ncy;      // coarse cells per axis
+    float q_bg;        // background charge
+    float nu_bg;       // background Krook rate
+    long long* psum;   // [MOM_PSUMS][nc]
+    double* col;       // [MOM_COLS][nx * ny]
+    float* out;        // [PIC_MOM_ROWS][nc]
+};
+
+// Component c of E (c < 3) or B at the particle, CIC on its Yee lattice, global memory.
+__device__ float gather_comp(const RunDev& R, int ndim, int c, int cx, int cy, int cz, float ox, float oy, float oz) {
+    // half-shifted axes of each component: Ex x, Ey y, Ez z (3D); Bx y,z; By x,z; Bz x,y
+    // (2D: Ez and the z shifts are absent)
+    // bit c set: component c is half-shifted along the axis (c = Ex Ey Ez Bx By Bz)
+    const bool hx = (0x31 >> c) & 1, hy = (0x2A >> c) & 1, hz = ndim == 3 && ((0x1C >> c) & 1);
+    const float* F = c < 3 ? R.E[c] : R.B[c - 3];
+    const float xs = hx ? ox - 0.5f : ox, ys = hy ? oy - 0.5f : oy, zs = hz ? oz - 0.5f : oz;
+    const int i0 = xs < 0.f ? -1 : 0, j0 = ys < 0.f ? -1 : 0, k0 = zs < 0.f ? -1 : 0;
+    const float ax = xs - (float)i0, ay = ys - (float)j0, az = zs - (float)k0;
+    const int nz = ndim == 3 ? R.nz : 1;
+    float v = 0.f;
+    for (int dk = 0; dk < (ndim == 3 ? 2 : 1); ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                const int gi = wrapi(cx + i0 + di, R.nx), gj = wrapi(cy + j0 + dj, R.ny);
+                const int gk = ndim == 3 ? wrapi(cz + k0 + dk, nz) : 0;
+                const float wgt = (di ? ax : 1.f - ax) * (dj ? ay : 1.f - ay) *
+                                  (ndim == 3 ? (dk ? az : 1.f - az) : 1.f);
+                v += wgt * F[((size_t)gk * R.ny + gj) * R.nx + gi];
+            }
+    return v;
+}
+
+__device__ __forceinline__ long long fx(double v) { return __double2ll_rn(v * MOM_FIX); }
+
+// Add one particle to the thread's sums: pass 1 first moments, pass 2 centred second moments
+// (mean[s][3] of its coarse cell) and the background force and velocity.
+__device__ __forceinline__ void add_particle(const MomArgs& m, const RunDev& R, int pass, int s, float w,
+                                             const double (*mean)[3], int cx, int cy, int cz, float ox,
+                                             float oy, float oz, float ux, float uy, float uz,
+                                             long long acc[MOM_PSUMS]) {
+    const double dw = w, du[3] = {ux, uy, uz};
+    if (pass == 1) {
+        acc[4 * s] += fx(dw);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) acc[4 * s + 1 + d] += fx(dw * du[d]);
+        return;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double e = du[d] - mean[s][d];
+        acc[8 + 3 * s + d] += fx(dw * e * e);
+    }
+    if (s == 1) {
+        const double ig = 1.0 / sqrt(1.0 + du[0] * du[0] + du[1] * du[1] + du[2] * du[2]);
+        const double vx = du[0] * ig, vy = du[1] * ig, vz = du[2] * ig;
+        const int nd = m.a.ndim;
+        const double ez = gather_comp(R, nd, 2, cx, cy, cz, ox, oy, oz);
+        const double bx = gather_comp(R, nd, 3, cx, cy, cz, ox, oy, oz);
+        const double by = gather_comp(R, nd, 4, cx, cy, cz, ox, oy, oz);
+        const double fz = (double)m.q_bg * (ez + vx * by - vy * bx);
+        acc[14] += fx(dw * fz);
+        acc[15] += fx(dw * vx);
+        acc[16] += fx(dw * vy);
+        acc[17] += fx(dw * vz);
+    }
+}
+
+// Means <u> per species of coarse cell cc from the pass-1 sums.
+__device__ __forceinline__ void coarse_means(const MomArgs& m, long long cc, double mean[2][3]) {
+    const long long nc = (long long)m.ncx * m.ncy;
+    for (int s = 0; s < 2; ++s) {
+        const double sw = (double)m.psum[(size_t)(4 * s) * nc + cc];
+        for (int d = 0; d < 3; ++d)
+            mean[s][d] = sw > 0 ? (double)m.psum[(size_t)(4 * s + 1 + d) * nc + cc] / sw : 0.0;
+    }
+}
+
+// One CTA per (coarse cell, z chunk): a thread per fine cell, all its particles.
+__global__ void __launch_bounds__(NT) mom_particles(const MomArgs m, int pass) {
+    __shared__ long long red[NT / 32][MOM_PSUMS];
+    const Args& a = m.a;
+    const RunDev& R = a.runs[m.run];
+    const int cc = blockIdx.x;
+    double mean[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    if (pass == 2) coarse_means(m, cc, mean);
+    const int X0 = (cc % m.ncx) * m.bx, Y0 = (cc / m.ncx) * m.by;
+    const int per = m.bx * m.by;
+    long long acc[MOM_PSUMS];
+#pragma unroll
+    for (int k = 0; k < MOM_PSUMS; ++k) acc[k] = 0;
+    const int par = a.ctl->parity;
+    for (int t = threadIdx.x; t < per * m.zc; t += NT) {
+        const int col = t % per, lz = t / per;
+        const int cx = X0 + col % m.bx, cy = Y0 + col / m.bx;
+        const int cz = blockIdx.y * m.zc + lz;
+        if (cz >= R.nz) continue;
+        const long long g = R.cell_off + ((long long)cz * R.ny + cy) * R.nx + cx;
+        for (int s = 0; s < a.nspecies && s < 2; ++s) {
+            if (!R.sp[s].active) continue;
+            const Slots& S = a.slot[s][par];
+            const CellRange cr = cell_range(S, a.cap[s], a.cap_stay[s], g);
+            const float w = R.sp[s].w;
+            for (int k = 0; k < cr.n; ++k) {
+                const size_t q = slot_of(g, a.cap[s], a.cap_stay[s], cr.ns, k);
+                add_particle(m, R, pass, s, w, mean, cx, cy, cz, S.o[0][q], S.o[1][q],
+                             a.ndim == 3 ? S.o[2][q] : 0.f, S.u[0][q], S.u[1][q], S.u[2][q], acc);
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < MOM_PSUMS; ++k) {
+        long long v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < MOM_PSUMS) {
+        long long v = 0;
+        for (int w = 0; w < NT / 32; ++w) v += red[w][threadIdx.x];
+        if (v) atomicAdd((unsigned long long*)&m.psum[(size_t)threadIdx.x * m.ncx * m.ncy + cc], (unsigned long long)v);
+    }
+}
+
+// Spilled particles of the run (thread each).
+__global__ void __launch_bounds__(NT) mom_spill(const MomArgs m, int pass) {
+    const Args& a = m.a;
+    const RunDev& R = a.runs[m.run];
+    const int par = a.ctl->parity;
+    const long long nc = (long long)m.ncx * m.ncy;
+    for (int s = 0; s < a.nspecies && s < 2; ++s) {
+        const Slots& S = a.slot[s][par];
+        const int ns = min(*S.sn, a.spill_cap[s]);
+        for (int k = blockIdx.x * NT + threadIdx.x; k < ns; k += gridDim.x * NT) {
+            const long long g = S.scell[k];
+            const long long lc = g - R.cell_off;
+            if (lc < 0 || lc >= (long long)R.nx * R.ny * R.nz) continue;
+            const int cz = (int)(lc / ((long long)R.nx * R.ny));
+            const int rem = (int)(lc - (long long)cz * R.nx * R.ny);
+            const int cy = rem / R.nx, cx = rem - cy * R.nx;
+            long long acc[MOM_PSUMS];
+            for (int i = 0; i < MOM_PSUMS; ++i) acc[i] = 0;
+            const long long cc = (long long)(cy / m.by) * m.ncx + cx / m.bx;
+            double mean[2][3] = {{0, 0, 0}, {0, 0, 0}};
+            if (pass == 2) coarse_means(m, cc, mean);
+            add_particle(m, R, pass, s, R.sp[s].w, mean, cx, cy, cz, S.so[0][k], S.so[1][k],
+                         a.ndim == 3 ? S.so[2][k] : 0.f, S.su[0][k], S.su[1][k], S.su[2][k], acc);
+            for (int i = 0; i < MOM_PSUMS; ++i)
+                if (acc[i]) atomicAdd((unsigned long long*)&m.psum[(size_t)i * nc + cc], (unsigned long long)acc[i]);
+        }
+    }
+}
+
+// Per (x, y) column: mean over z of sum_c (E_c - <E_c>_z)^2, and the z means of Ez, Bx, By.
+__global__ void __launch_bounds__(NT) mom_columns(const MomArgs m) {
+    const RunDev& R = m.a.runs[m.run];
+    const long long ncol = (long long)R.nx * R.ny;
+    const int nz = m.a.ndim == 3 ? R.nz : 1;
+    for (long long c = blockIdx.x * (long long)NT + threadIdx.x; c < ncol; c += (long long)gridDim.x * NT) {
+        double mean[3] = {0, 0, 0}, bx = 0, by = 0;
+        for (int k = 0; k < nz; ++k) {
+            const size_t g = (size_t)k * ncol + c;
+            for (int d = 0; d < 3; ++d) mean[d] += R.E[d][g];
+            bx += R.B[0][g];
+            by += R.B[1][g];
+        }
+        for (int d = 0; d < 3; ++d) mean[d] /= nz;
+        double w = 0;
+        for (int k = 0; k < nz; ++k) {
+            const size_t g = (size_t)k * ncol + c;
+            for (int d = 0; d < 3; ++d) {
+                const double e = (double)R.E[d][g] - mean[d];
+                w += e * e;
+            }
+        }
+        m.col[c] = w / nz;
+        m.col[ncol + c] = mean[2];
+        m.col[2 * ncol + c] = bx / nz;
+        m.col[3 * ncol + c] = by / nz;
+    }
+}
+
+__global__ void __launch_bounds__(NT) mom_finalize(const MomArgs m) {
+    const RunDev& R = m.a.runs[m.run];
+    const long long nc = (long long)m.ncx * m.ncy;
+    const long long ncol = (long long)R.nx * R.ny;
+    const int nz = m.a.ndim == 3 ? R.nz : 1;
+    const double cells = (double)m.bx * m.by * nz;
+    for (long long cc = blockIdx.x * (long long)NT + threadIdx.x; cc < nc; cc += (long long)gridDim.x * NT) {
+        double p[MOM_PSUMS];
+        for (int i = 0; i < MOM_PSUMS; ++i) p[i] = (double)m.psum[(size_t)i * nc + cc] / MOM_FIX;
+        float* o = m.out;
+        for (int s = 0; s < 2; ++s) {
+            const double sw = p[4 * s];
+            double mu[3] = {0, 0, 0}, var[3] = {0, 0, 0};
+            if (sw > 0)
+                for (int d = 0; d < 3; ++d) {
+                    mu[d] = p[4 * s + 1 + d] / sw;
+                    var[d] = p[8 + 3 * s + d] / sw;
+                }
+            o[(size_t)s * nc + cc] = (float)(sw / cells);
+            o[(size_t)(2 + s) * nc + cc] = (float)mu[2];
+            o[(size_t)(4 + 2 * s) * nc + cc] = (float)(0.5 * (var[0] + var[1]));
+            o[(size_t)(5 + 2 * s) * nc + cc] = (float)var[2];
+        }
+        // field blocks, fixed order
+        const int X0 = (int)(cc % m.ncx) * m.bx, Y0 = (int)(cc / m.ncx) * m.by;
+        double f[MOM_COLS] = {0, 0, 0, 0};
+        for (int j = 0; j < m.by; ++j)
+            for (int i = 0; i < m.bx; ++i) {
+                const long long c = (long long)(Y0 + j) * R.nx + (X0 + i);
+                for (int k = 0; k < MOM_COLS; ++k) f[k] += m.col[(size_t)k * ncol + c];
+            }
+        for (int k = 0; k < MOM_COLS; ++k) f[k] /= (double)(m.bx * m.by);
+        o[(size_t)8 * nc + cc] = (float)f[0];
+        const double sw = p[4];
+        double fzp = 0, vx = 0, vy = 0, uz = 0;
+        if (sw > 0) {
+            fzp = p[14] / sw;
+            vx = p[15] / sw;
+            vy = p[16] / sw;
+            uz = p[7] / sw;
+        }
+        const double fzm = (double)m.q_bg * (f[1] + vx * f[3] - vy * f[2]);
+        o[(size_t)9 * nc + cc] = (float)fzp;
+        o[(size_t)10 * nc + cc] = (float)fzm;
+        o[(size_t)11 * nc + cc] = uz != 0 ? (float)((double)m.nu_bg + (fzm - fzp) / uz) : 0.f;
+    }
+}
+
+int grid_of(long long n) {
+    long long g = (n + NT - 1) / NT;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+size_t moments_scratch_bytes(long long nc, long long ncol) {
+    return (size_t)nc * MOM_PSUMS * sizeof(long long) + (size_t)ncol * MOM_COLS * sizeof(double);
+}
+
+cudaError_t launch_moments(const Args& a, const RunDev& host_run, int run, int bx, int by, float q_bg,
+                           float nu_bg, float* out, void* scratch, cudaStream_t s) {
+    MomArgs m;
+    m.a = a;
+    m.run = run;
+    m.bx = bx;
+    m.by = by;
+    m.ncx = host_run.nx / bx;
+    m.ncy = host_run.ny / by;
+    const int nz = a.ndim == 3 ? host_run.nz : 1;
+    const int per = bx * by;
+    m.zc = per >= NT ? 1 : (NT / per < nz ? NT / per : nz);
+    m.q_bg = q_bg;
+    m.nu_bg = nu_bg;
+    const long long nc = (long long)m.ncx * m.ncy;
+    m.psum = static_cast<long long*>(scratch);
+    m.col = reinterpret_cast<double*>(m.psum + (size_t)nc * MOM_PSUMS);
+    m.out = out;
+    cudaError_t e = cudaMemsetAsync(m.psum, 0, (size_t)nc * MOM_PSUMS * sizeof(long long), s);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)nc, (unsigned)((nz + m.zc - 1) / m.zc));
+    for (int pass = 1; pass <= 2; ++pass) {
+        mom_particles<<<grid, NT, 0, s>>>(m, pass);
+        mom_spill<<<152, NT, 0, s>>>(m, pass);
+    }
+    mom_columns<<<grid_of((long long)host_run.nx * host_run.ny), NT, 0, s>>>(m);
+    mom_finalize<<<grid_of(nc), NT, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t preload_moments() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, mom_particles);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_spill);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_columns);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_finalize);
+    return e;
+}
+
+}  // namespace pic

@@ -207,6 +207,12 @@ cudaError_t launch_resort(const Args& a, cudaStream_t s, int* launches);
 cudaError_t launch_moments_init(const Args& a, int species, int run, long long c0, long long nc,
                                 cudaStream_t s);
 cudaError_t launch_moments_finalize(const Args& a, int run, long long ncell, cudaStream_t s);
+// Moment recorder (moments.cu): scratch bytes for nc coarse cells and ncol columns, and the
+// launch (psum cleared, particle and spill sums, field columns, finalisation into out).
+size_t moments_scratch_bytes(long long nc, long long ncol);
+cudaError_t launch_moments(const Args& a, const RunDev& host_run, int run, int bx, int by, float q_bg,
+                           float nu_bg, float* out, void* scratch, cudaStream_t s);
+cudaError_t preload_moments();
 cudaError_t launch_fit(const Args& a, int run, long long first, int nrec, int width, double t_noise,
                        double start_factor, double end_factor, double* out3, cudaStream_t s);
 }  // namespace pic
