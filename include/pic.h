@@ -237,6 +237,43 @@ int pic_record_moments_scratch_bytes(pic_ctx* ctx, int run, int bx, int by, size
 int pic_record_moments(pic_ctx* ctx, int run, int bx, int by, float* out, int64_t out_cap,
                        void* scratch, size_t scratch_bytes, int64_t* ncoarse_out);
 
+/* ---------------------------------------------------------------- closure network
+ * The network that maps the coarse moments (rows 0..8 of pic_record_moments, or the first 8
+ * without W_ES) to the friction rate nu_eff -- this library's reading of the closure the paper's
+ * conclusion conjectures:
+ *   xn = (x - mu) / sigma (features >= nin are 0),  h1 = silu(W1 xn + b1),  h2 = silu(W2 h1 + b2),
+ *   y = w3 . h2 + b3,  silu(z) = z / (1 + exp(-z)),
+ * W1 64 x 9, W2 64 x 64.  The two hidden layers run on the tensor cores with bfloat16 weights and
+ * inputs and FP32 accumulation; the rest is FP32.
+ * params: device float[PIC_MLP_NPARAM] in the order W1[64][9], b1[64], W2[64][64], b2[64],
+ * w3[64], b3.  x: device float, feature-major, x[j * ldx + i] for feature j of sample i (the
+ * moment recorder's output with ldx = ncoarse).  All device buffers are owned by the caller. */
+#define PIC_MLP_IN 9
+#define PIC_MLP_HIDDEN 64
+#define PIC_MLP_NPARAM 4865
+typedef struct pic_mlp_norm {
+    float mu[PIC_MLP_IN];      /* per-feature offset */
+    float sigma[PIC_MLP_IN];   /* per-feature scale (> 0) */
+    int32_t nin;               /* inputs used: 9, or 8 for the variant without W_ES */
+} pic_mlp_norm;
+
+/* y[i] (device float[n]) = network(x[:, i]).  Asynchronous on `stream` (a cudaStream_t). */
+int pic_mlp_forward(const float* params, const pic_mlp_norm* norm, const float* x, int64_t ldx,
+                    int64_t n, float* y, void* stream);
+/* One full-batch Adam step (beta1 0.9, beta2 0.999, eps 1e-8; t >= 1 the step number, adam_m and
+ * adam_v device float[PIC_MLP_NPARAM] moment estimates, zero before t = 1) on the mean squared
+ * error of y against target[n] (device); params updated in place; *loss (device float, may be
+ * NULL) = the loss before the update.  scratch: device memory of >= pic_mlp_train_scratch_bytes()
+ * bytes, 4-byte aligned, in use until the stream passes the call.  Deterministic: the gradient is
+ * summed in a fixed order.  Asynchronous on `stream`. */
+int pic_mlp_train_scratch_bytes(size_t* bytes_out);
+int pic_mlp_train_step(float* params, float* adam_m, float* adam_v, int32_t t, float lr,
+                       const pic_mlp_norm* norm, const float* x, int64_t ldx, const float* target,
+                       int64_t n, float* loss, void* scratch, size_t scratch_bytes, void* stream);
+/* PIC_OK, or PIC_ETIMEOUT if a tensor-core completion wait of the network kernels gave up
+ * (sticky until read with clear != 0).  Synchronous. */
+int pic_mlp_status(int clear);
+
 /* Counting sort by cell, the binning primitive of the re-binning step, on caller device memory:
  * cell[n] (device) holds each particle's cell in [0, ncell); writes start[ncell + 1] (device;
  * start[c] = number of particles in cells below c) and order[n] (device; order[start[c] ..

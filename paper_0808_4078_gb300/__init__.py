@@ -65,6 +65,10 @@ class KernelTime(ctypes.Structure):
                 ("total_ms", ctypes.c_double)]
 
 
+class MlpNorm(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_float * 9), ("sigma", ctypes.c_float * 9), ("nin", ctypes.c_int32)]
+
+
 _VP = ctypes.c_void_p
 _SIGNATURES = {
     "pic_required_bytes": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_size_t)]),
@@ -103,6 +107,11 @@ _SIGNATURES = {
                                                         ctypes.POINTER(ctypes.c_size_t)]),
     "pic_record_moments": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int64,
                                           _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64)]),
+    "pic_mlp_forward": (ctypes.c_int, [_VP, ctypes.POINTER(MlpNorm), _VP, ctypes.c_int64, ctypes.c_int64, _VP, _VP]),
+    "pic_mlp_train_scratch_bytes": (ctypes.c_int, [ctypes.POINTER(ctypes.c_size_t)]),
+    "pic_mlp_train_step": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_float, ctypes.POINTER(MlpNorm),
+                                          _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP, _VP, ctypes.c_size_t, _VP]),
+    "pic_mlp_status": (ctypes.c_int, [ctypes.c_int]),
     "pic_launch_count": (ctypes.c_int64, [_VP]),
     "pic_step_count": (ctypes.c_int64, [_VP]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
@@ -357,3 +366,64 @@ def history_array(recs, key, comp=None):
     if comp is None:
         return np.array([r[key] for r in recs])
     return np.array([r[key][comp] for r in recs])
+
+
+# ---------------------------------------------------------------- closure network
+PIC_MLP_NPARAM = 4865
+
+
+class ClosureNet:
+    """The closure network on the GPU (pic_mlp_*): FP32 master parameters and Adam moments as
+    device tensors; forward and full-batch Adam steps through the C ABI on one stream.
+
+    x arguments are feature-major float32 CUDA tensors of shape (>= nin, n) (the moment
+    recorder's rows 0..8 qualify directly)."""
+
+    def __init__(self, params, mu, sigma, nin=9, device="cuda", stream=None):
+        import torch
+        self._torch = torch
+        self.device = torch.device(device)
+        self.params = torch.as_tensor(np.asarray(params, np.float32), device=self.device).contiguous()
+        assert self.params.numel() == PIC_MLP_NPARAM
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.t = 0
+        self.norm = MlpNorm()
+        for j in range(9):
+            self.norm.mu[j] = float(mu[j]) if j < len(mu) else 0.0
+            self.norm.sigma[j] = float(sigma[j]) if j < len(sigma) else 1.0
+        self.norm.nin = int(nin)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        nb = ctypes.c_size_t(0)
+        _check(lib().pic_mlp_train_scratch_bytes(ctypes.byref(nb)))
+        self._scratch = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        self._loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+
+    def _sync_inputs(self):
+        # inputs made by torch on its current stream must be complete before our stream reads them
+        self.stream.wait_stream(self._torch.cuda.current_stream(self.device))
+
+    def forward(self, x, out=None):
+        torch = self._torch
+        n = x.shape[1]
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=self.device)
+        self._sync_inputs()
+        _check(lib().pic_mlp_forward(_VP(self.params.data_ptr()), ctypes.byref(self.norm), _VP(x.data_ptr()),
+                                     x.stride(0), n, _VP(out.data_ptr()), _VP(self.stream.cuda_stream)))
+        self.stream.synchronize()
+        _check(lib().pic_mlp_status(1))
+        return out
+
+    def train_step(self, x, target, lr):
+        """One Adam step on the batch; returns the loss before the update (a float)."""
+        self.t += 1
+        self._sync_inputs()
+        _check(lib().pic_mlp_train_step(_VP(self.params.data_ptr()), _VP(self.m.data_ptr()),
+                                        _VP(self.v.data_ptr()), self.t, float(lr), ctypes.byref(self.norm),
+                                        _VP(x.data_ptr()), x.stride(0), _VP(target.data_ptr()), x.shape[1],
+                                        _VP(self._loss.data_ptr()), _VP(self._scratch.data_ptr()),
+                                        self._scratch.numel(), _VP(self.stream.cuda_stream)))
+        self.stream.synchronize()
+        _check(lib().pic_mlp_status(1))
+        return float(self._loss.cpu()[0])

@@ -416,6 +416,7 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
     CKI(preload_push2d());
     CKI(preload_push3d());
     CKI(preload_moments());
+    CKI(preload_mlp());
     CKI(preload_bins());
     CKI(preload_fields());
     CKI(cudaMemsetAsync(ctx->arena, 0, L.total, ctx->stream));
@@ -920,6 +921,66 @@ extern "C" int pic_record_moments(pic_ctx* ctx, int run, int bx, int by, float* 
     const float nu_bg = (float)ctx->nu[(size_t)run * PIC_NS + 1];
     CK(launch_moments(ctx->args, ctx->runs[run], run, bx, by, q_bg, nu_bg, out, scratch, ctx->stream));
     if (ncoarse_out) *ncoarse_out = nc;
+    return PIC_OK;
+}
+
+// ---------------------------------------------------------------- closure network
+namespace {
+int mlp_norm(const pic_mlp_norm* in, MlpNorm* out) {
+    if (!in) return fail(nullptr, PIC_EINVAL, "null norm");
+    if (in->nin < 1 || in->nin > PIC_MLP_IN) return fail(nullptr, PIC_EINVAL, "nin must be in [1, %d]", PIC_MLP_IN);
+    for (int j = 0; j < PIC_MLP_IN; ++j) {
+        if (j < in->nin && !(std::isfinite(in->sigma[j]) && in->sigma[j] > 0 && std::isfinite(in->mu[j])))
+            return fail(nullptr, PIC_EINVAL, "feature %d: sigma must be finite and > 0", j);
+        out->mu[j] = j < in->nin ? in->mu[j] : 0.f;
+        out->inv_sigma[j] = j < in->nin ? 1.0f / in->sigma[j] : 0.f;
+    }
+    out->nin = in->nin;
+    return PIC_OK;
+}
+}  // namespace
+
+extern "C" int pic_mlp_forward(const float* params, const pic_mlp_norm* norm, const float* x, int64_t ldx,
+                               int64_t n, float* y, void* stream) {
+    MlpNorm nm;
+    int rc = mlp_norm(norm, &nm);
+    if (rc) return rc;
+    if (n < 0 || ldx < n) return fail(nullptr, PIC_EINVAL, "need n >= 0 and ldx >= n");
+    if (n > 0 && (!params || !x || !y)) return fail(nullptr, PIC_EINVAL, "null pointer");
+    cudaError_t e = launch_mlp_forward(params, nm, x, ldx, n, y, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, "pic_mlp_forward: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+extern "C" int pic_mlp_train_scratch_bytes(size_t* bytes_out) {
+    if (!bytes_out) return fail(nullptr, PIC_EINVAL, "null bytes_out");
+    *bytes_out = mlp_train_scratch_bytes();
+    return PIC_OK;
+}
+
+extern "C" int pic_mlp_train_step(float* params, float* adam_m, float* adam_v, int32_t t, float lr,
+                                  const pic_mlp_norm* norm, const float* x, int64_t ldx, const float* target,
+                                  int64_t n, float* loss, void* scratch, size_t scratch_bytes, void* stream) {
+    MlpNorm nm;
+    int rc = mlp_norm(norm, &nm);
+    if (rc) return rc;
+    if (n < 1 || ldx < n) return fail(nullptr, PIC_EINVAL, "need n >= 1 and ldx >= n");
+    if (t < 1) return fail(nullptr, PIC_EINVAL, "Adam step t must be >= 1");
+    if (!params || !adam_m || !adam_v || !x || !target || !scratch)
+        return fail(nullptr, PIC_EINVAL, "null pointer");
+    if (scratch_bytes < mlp_train_scratch_bytes())
+        return fail(nullptr, PIC_EINVAL, "scratch has %zu bytes, needs %zu", scratch_bytes, mlp_train_scratch_bytes());
+    cudaError_t e = launch_mlp_train(params, adam_m, adam_v, t, lr, nm, x, ldx, target, n, loss, scratch,
+                                     (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, "pic_mlp_train_step: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+extern "C" int pic_mlp_status(int clear) {
+    int err = 0;
+    cudaError_t e = mlp_status(&err, clear != 0);
+    if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, "pic_mlp_status: %s", cudaGetErrorString(e));
+    if (err) return fail(nullptr, PIC_ETIMEOUT, "a tensor-core completion wait of the closure network timed out");
     return PIC_OK;
 }
 

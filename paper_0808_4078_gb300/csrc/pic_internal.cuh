@@ -213,6 +213,21 @@ size_t moments_scratch_bytes(long long nc, long long ncol);
 cudaError_t launch_moments(const Args& a, const RunDev& host_run, int run, int bx, int by, float q_bg,
                            float nu_bg, float* out, void* scratch, cudaStream_t s);
 cudaError_t preload_moments();
+// Closure network (mlp.cu): per-feature normalisation x' = (x - mu) * inv_sigma of the first nin
+// inputs (the others are 0).
+struct MlpNorm {
+    float mu[9];
+    float inv_sigma[9];
+    int nin;
+};
+size_t mlp_train_scratch_bytes();
+cudaError_t launch_mlp_forward(const float* params, const MlpNorm& norm, const float* x, long long ldx, long long n,
+                               float* y, cudaStream_t s);
+cudaError_t launch_mlp_train(float* params, float* am, float* av, int t, float lr, const MlpNorm& norm,
+                             const float* x, long long ldx, const float* target, long long n, float* loss,
+                             void* scratch, cudaStream_t s);
+cudaError_t mlp_status(int* err, bool clear);
+cudaError_t preload_mlp();
 cudaError_t launch_fit(const Args& a, int run, long long first, int nrec, int width, double t_noise,
                        double start_factor, double end_factor, double* out3, cudaStream_t s);
 }  // namespace pic

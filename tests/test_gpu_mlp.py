@@ -1,0 +1,122 @@
+"""Closure network on the tensor cores (pic_mlp_*) against the FP64 oracle network
+(oracle.mlp) with the same bfloat16 roundings of weights and matrix inputs.
+
+Tolerances: the two sides differ only in FP32 accumulation order, the fast exponential of SiLU
+and bfloat16 ties at rounding boundaries of the hidden activations, so the outputs agree to
+~1e-3 of their scale (SURVEY's bar is 1e-2); gradients (recovered from the first Adam moment,
+m = (1 - beta1) g at t = 1) to cosine >= 0.999 and 2e-2 relative.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pic():
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_0808_4078_gb300 as pic
+    return pic
+
+
+def _data(n, seed=4, nin=9):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(0, 1, (n, 9)) * np.linspace(0.5, 3, 9) + np.linspace(-1, 1, 9)
+    t = np.tanh(x[:, 0] - 0.5 * x[:, 2]) + 0.2 * x[:, 4] ** 2 / 9
+    x = x.astype(np.float32).astype(np.float64)
+    if nin < 9:
+        x[:, nin:] = 0.0
+    return x, t.astype(np.float32).astype(np.float64)
+
+
+def _net(pic, p, x, nin=9):
+    from oracle import mlp
+    mu, sd = mlp.feature_norm(x[:, :nin])
+    mu = np.concatenate([mu, np.zeros(9 - nin)]).astype(np.float32).astype(np.float64)
+    sd = np.concatenate([sd, np.ones(9 - nin)]).astype(np.float32).astype(np.float64)
+    return pic.ClosureNet(p, mu, sd, nin=nin), mu, sd
+
+
+def _dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 1000, 70_001])
+def test_forward_matches_oracle(pic, n):
+    from oracle import mlp
+    x, _ = _data(n)
+    p = mlp.init_params(1)
+    net, mu, sd = _net(pic, p, x)
+    y = net.forward(_dev(x.T)).cpu().numpy().astype(np.float64)
+    yo, _ = mlp.forward(p, x, mu, sd, bf16_path=True)
+    scale = np.abs(yo).max() + 1e-6
+    assert np.abs(y - yo).max() <= 1e-3 * scale, np.abs(y - yo).max() / scale
+
+
+def test_forward_eight_inputs(pic):
+    from oracle import mlp
+    x, _ = _data(3000, seed=5, nin=8)
+    p = mlp.init_params(2, nin=8)
+    net, mu, sd = _net(pic, p, x, nin=8)
+    xg = x.copy()
+    xg[:, 8] = 123.0              # ignored when nin = 8
+    y = net.forward(_dev(xg.T)).cpu().numpy().astype(np.float64)
+    yo, _ = mlp.forward(p, x, mu, sd, bf16_path=True)
+    assert np.abs(y - yo).max() <= 1e-3 * (np.abs(yo).max() + 1e-6)
+
+
+def test_gradient_and_loss_match_oracle(pic):
+    from oracle import mlp
+    n = 5000
+    x, t = _data(n, seed=6)
+    p = mlp.init_params(3)
+    net, mu, sd = _net(pic, p, x)
+    loss = net.train_step(_dev(x.T), _dev(t), lr=1e-3)
+    g = net.m.cpu().numpy().astype(np.float64) / 0.1          # m = (1 - beta1) g at t = 1
+    Lo, go = mlp.loss_and_grad(p, x, t, mu, sd, bf16_path=True)
+    assert loss == pytest.approx(Lo, rel=2e-3)
+    cos = g @ go / (np.linalg.norm(g) * np.linalg.norm(go))
+    assert cos >= 0.999, cos
+    assert np.linalg.norm(g - go) <= 2e-2 * np.linalg.norm(go)
+    # the Adam update itself: p1 = p - lr m_hat / (sqrt(v_hat) + eps)
+    p1 = net.params.cpu().numpy().astype(np.float64)
+    pe, _, _ = mlp.adam_step(p.astype(np.float32).astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1, 1e-3)
+    assert np.abs(p1 - pe).max() <= 1e-6
+
+
+def test_training_is_deterministic_and_converges(pic):
+    from oracle import mlp
+    n = 20_000
+    x, t = _data(n, seed=8)
+    p = mlp.init_params(4)
+    runs = []
+    for _ in range(2):
+        net, _, _ = _net(pic, p, x)
+        xd, td = _dev(x.T), _dev(t)
+        losses = [net.train_step(xd, td, lr=3e-3) for _ in range(150)]
+        runs.append((losses, net.params.cpu().numpy()))
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1])
+    assert runs[0][0][-1] < 0.2 * runs[0][0][0]
+
+
+def test_forward_on_recorded_moments(pic):
+    """The recorder's feature rows feed the network without a copy (ldx = ncoarse)."""
+    import pic_inputs as pi
+    from oracle import mlp
+    wl = pi.weibel_load(ndim=2, nx=64, ny=64, ppc=8, T_perp_beam=0.2, T_bg=0.01, nu=0.1, seed=71)
+    eng = pic.Engine.from_workload(wl)
+    eng.step(2)
+    rows = eng.record_moments(4, 4)                     # (12, 256)
+    feats = rows[:9]
+    xf = feats.cpu().numpy().T.astype(np.float64)
+    p = mlp.init_params(5)
+    mu, sd = mlp.feature_norm(xf)
+    mu, sd = mu.astype(np.float32).astype(np.float64), sd.astype(np.float32).astype(np.float64)
+    net = pic.ClosureNet(p, mu, sd)
+    y = net.forward(feats).cpu().numpy().astype(np.float64)
+    yo, _ = mlp.forward(p, xf, mu, sd, bf16_path=True)
+    assert np.abs(y - yo).max() <= 1e-3 * (np.abs(yo).max() + 1e-6)
+    eng.close()
