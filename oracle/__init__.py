@@ -54,7 +54,8 @@ class _Grid(ctypes.Structure):
 class _Species(ctypes.Structure):
     _fields_ = [("q", ctypes.c_double), ("m", ctypes.c_double), ("w", ctypes.c_double),
                 ("nu", ctypes.c_double), ("n", ctypes.c_int64),
-                ("X", P), ("Y", P), ("Z", P), ("ux", P), ("uy", P), ("uz", P), ("ubar", P)]
+                ("X", P), ("Y", P), ("Z", P), ("ux", P), ("uy", P), ("uz", P), ("ubar", P),
+                ("nu_cell", P)]
 
 
 MAX_SPECIES = 4
@@ -109,6 +110,7 @@ class Species:
         self.Z = f(Z) if Z is not None else np.zeros(1)
         self.ux, self.uy, self.uz = f(ux), f(uy), f(uz)
         self.ubar = np.zeros(3 * ncell) if nu > 0 else None
+        self.nu_cell = None
 
     @property
     def n(self):
@@ -117,7 +119,7 @@ class Species:
     def cstruct(self):
         return _Species(self.q, self.m, self.w, self.nu, self.n, _ptr(self.X), _ptr(self.Y),
                         _ptr(self.Z), _ptr(self.ux), _ptr(self.uy), _ptr(self.uz),
-                        _ptr(self.ubar))
+                        _ptr(self.ubar), _ptr(self.nu_cell))
 
     @property
     def u(self):
@@ -161,6 +163,22 @@ class Simulation:
             if lib().orc_moments(ctypes.byref(g), ctypes.byref(cs)) != 0:
                 raise MemoryError("orc_moments")
         return s
+
+    def set_nu_cell(self, s, nu_cell):
+        """Per-cell Krook rates for species s (closure-driven drag; None restores the scalar
+        rate).  Starts the cell-mean momentum tracking if the species had none."""
+        sp = self.species[s]
+        if nu_cell is None:
+            sp.nu_cell = None
+            return
+        sp.nu_cell = np.ascontiguousarray(nu_cell, dtype=np.float64).reshape(-1)
+        assert sp.nu_cell.shape[0] == self.ncell
+        if sp.ubar is None:
+            sp.ubar = np.zeros(3 * self.ncell)
+            g = self.cgrid()
+            cs = sp.cstruct()
+            if lib().orc_moments(ctypes.byref(g), ctypes.byref(cs)) != 0:
+                raise MemoryError("orc_moments")
 
     @classmethod
     def from_workload(cls, wl):

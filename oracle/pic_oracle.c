@@ -55,7 +55,9 @@ typedef struct orc_species {
     int64_t n;
     double *X, *Y, *Z;    /* positions in cell units; Z unused in 2D */
     double *ux, *uy, *uz;
-    double *ubar;     /* 3*ncell cell-mean momentum (NGP) used by the drag; NULL if nu == 0 */
+    double *ubar;     /* 3*ncell cell-mean momentum (NGP) used by the drag; NULL if no drag */
+    double *nu_cell;  /* ncell Krook rates replacing nu, looked up at the particle's cell at time
+                         n (the closure-driven drag); negative rates act as 0; NULL = nu */
 } orc_species;
 
 #define ORC_MAX_SPECIES 4
@@ -399,6 +401,7 @@ int orc_step(orc_grid *g, orc_species *sp, int nsp, orc_diag *d) {
         orc_species *s = &sp[si];
         double qm = s->q / s->m, qw = s->q * s->w;
         double dragf = (s->ubar && s->nu > 0.0) ? 1.0 - exp(-s->nu * g->dt) : 0.0;
+        int per_cell = s->ubar && s->nu_cell;
         double *nsum = NULL, *ncnt = NULL;
         if (s->ubar) {
             nsum = calloc(3 * (size_t)nc, sizeof(double));
@@ -410,7 +413,12 @@ int orc_step(orc_grid *g, orc_species *sp, int nsp, orc_diag *d) {
             double u0[3] = {s->ux[p], s->uy[p], s->uz[p]};
             double u[3] = {u0[0], u0[1], u0[2]};
             const double *ub = s->ubar ? &s->ubar[3 * ngp_cell(g, s, p)] : NULL;
-            push_one(g, qm, P0, u, ub, dragf, P1);
+            double df = dragf;
+            if (per_cell) {
+                double r = s->nu_cell[ngp_cell(g, s, p)];
+                df = r > 0.0 ? 1.0 - exp(-r * g->dt) : 0.0;
+            }
+            push_one(g, qm, P0, u, ub, df, P1);
             double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
             if (g->ndim == 2) deposit_2d(g, qw, P0[0], P0[1], P1[0], P1[1], u[2] / gam);
             else deposit_3d(g, qw, P0, P1);
