@@ -204,6 +204,15 @@ typedef struct pic_stats {
 /* Occupancy of the particle bins of the current buffer.  Synchronises. */
 int pic_get_stats(pic_ctx* ctx, pic_stats* out);
 
+/* Closure-driven drag: replace the Krook rate of species s in run `run` by per-coarse-cell rates
+ * nu (device float[(nx / bx) (ny / by)], the layout of pic_record_moments and pic_mlp_forward's
+ * output; a coarse cell spans the whole z extent in 3D).  Each cell's factor 1 - exp(-nu dt) is
+ * taken once at this call (negative or NaN rates act as 0); the drag then uses the factor of the
+ * particle's cell.  Enables the drag for a species loaded with nu = 0.  nu == NULL restores the
+ * species' scalar rate.  At most one species per run carries the drag (PIC_EINVAL otherwise).
+ * Synchronises the context's stream; nu may be freed on return. */
+int pic_set_drag_map(pic_ctx* ctx, int run, int s, const float* nu, int32_t bx, int32_t by);
+
 /* ---------------------------------------------------------------- moment recorder
  * Coarse-grained state of run `run` at the current step: the inputs and the label parts of a
  * learned collision closure.  The paper's conclusion conjectures that the collisional friction on

@@ -112,6 +112,7 @@ _SIGNATURES = {
     "pic_mlp_train_step": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_float, ctypes.POINTER(MlpNorm),
                                           _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP, _VP, ctypes.c_size_t, _VP]),
     "pic_mlp_status": (ctypes.c_int, [ctypes.c_int]),
+    "pic_set_drag_map": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int32, ctypes.c_int32]),
     "pic_launch_count": (ctypes.c_int64, [_VP]),
     "pic_step_count": (ctypes.c_int64, [_VP]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
@@ -314,6 +315,16 @@ class Engine:
         # the scratch tensor is released when this returns: let the stream finish with it first
         self.sync()
         return out
+
+    def set_drag_map(self, s, nu, bx=1, by=1, run=0):
+        """Per-coarse-cell Krook rates (CUDA float tensor of (nx/bx)(ny/by) values) for species s,
+        or None to restore its scalar rate (pic_set_drag_map)."""
+        if nu is None:
+            _check(lib().pic_set_drag_map(self._ctx, run, s, None, bx, by), self._ctx)
+            return
+        nu = nu.contiguous()
+        self._torch.cuda.current_stream(self.device).synchronize()
+        _check(lib().pic_set_drag_map(self._ctx, run, s, _VP(nu.data_ptr()), bx, by), self._ctx)
 
     def launch_count(self):
         return int(lib().pic_launch_count(self._ctx))

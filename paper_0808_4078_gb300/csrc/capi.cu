@@ -54,6 +54,7 @@ struct Layout {
     size_t sp_cell[PIC_NS][2], sp_o[PIC_NS][2][3], sp_u[PIC_NS][2][3], sp_id[PIC_NS][2], sp_n[PIC_NS][2];
     size_t slot_region[PIC_NS][2];   // start of the contiguous slot arrays (staging view)
     std::vector<size_t> E[3], B[3], J[3], Jlast[3], msum[3], mcnt, ubar[3];   // per run
+    std::vector<size_t> dragmap[PIC_NS];                                     // per run
     size_t start, scan_tmp, gate;
     size_t partials, hist, fit;
 };
@@ -172,6 +173,7 @@ Layout make_layout(const pic_config* c, const Geometry& g) {
         L.msum[d].resize(nruns); L.ubar[d].resize(nruns);
     }
     L.mcnt.resize(nruns);
+    for (int sp = 0; sp < PIC_NS; ++sp) L.dragmap[sp].assign(nruns, 0);
     for (int r = 0; r < nruns; ++r) {
         const long long n = g.runs[r].ncell;
         for (int d = 0; d < 3; ++d) L.E[d][r] = take(off, 4 * n);
@@ -181,6 +183,7 @@ Layout make_layout(const pic_config* c, const Geometry& g) {
         for (int d = 0; d < 3; ++d) L.msum[d][r] = take(off, 8 * n);
         L.mcnt[r] = take(off, 4 * n);
         for (int d = 0; d < 3; ++d) L.ubar[d][r] = take(off, 4 * n);
+        for (int sp = 0; sp < c->nspecies; ++sp) L.dragmap[sp][r] = take(off, 4 * n);
     }
     L.start = take(off, 4 * (nc + 1));
     L.scan_tmp = take(off, 4 * (nc / 2048 + 2));
@@ -442,6 +445,7 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
             R.ubar[d] = nullptr;
         }
         R.mcnt = nullptr;
+        for (int sp = 0; sp < PIC_NS; ++sp) R.dragmap[sp] = nullptr;
         R.shift = 30;
         R.jscale = (float)std::ldexp(1.0, -30);
         for (long long t = 0; t < G.ntiles; ++t) work[G.work_off + t] = make_int2(r, (int)t);
@@ -502,6 +506,26 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
     return PIC_OK;
 }
 
+// Publish the drag moment arrays of run `run` and set the cell means <u> of species s from its
+// loaded particles (the drag of the first step uses them).
+int start_drag(pic_ctx* ctx, int run, int s) {
+    RunDev& R = ctx->runs[run];
+    const RunGeo& G = ctx->geo.runs[run];
+    if (!R.msum[0]) {
+        for (int d = 0; d < 3; ++d) {
+            R.msum[d] = at<long long>(ctx, ctx->lay.msum[d][run]);
+            R.ubar[d] = at<float>(ctx, ctx->lay.ubar[d][run]);
+        }
+        R.mcnt = at<int>(ctx, ctx->lay.mcnt[run]);
+    }
+    int rc = upload_runs(ctx);
+    if (rc) return rc;
+    CK(launch_moments_init(ctx->args, s, run, G.cell_off, G.ncell, ctx->stream));
+    CK(launch_moments_finalize(ctx->args, run, G.ncell, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return device_flags(ctx);
+}
+
 int load_run(pic_ctx* ctx, int run, int s, const pic_species* sp, int64_t n, const int32_t* cell,
              const float* offset, const float* u) {
     if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
@@ -518,6 +542,10 @@ int load_run(pic_ctx* ctx, int run, int s, const pic_species* sp, int64_t n, con
           std::isfinite(sp->nu) && sp->nu >= 0 && std::fabs(sp->q) <= 1.0))
         return fail(ctx, PIC_EINVAL, "bad species parameters (|q| <= 1, m > 0, w >= 0, nu >= 0)");
     if (ctx->q_set[s] && ctx->q[s] != sp->q) return fail(ctx, PIC_EINVAL, "species %d has one charge in every run", s);
+    if (sp->nu > 0)
+        for (int o = 0; o < PIC_NS; ++o)
+            if (o != s && R.sp[o].drag)
+                return fail(ctx, PIC_EINVAL, "run %d: the Krook drag acts on one species per run", run);
     const pic_config& c = ctx->cfg;
     Ctl h;
     rc = read_ctl(ctx, &h);
@@ -558,19 +586,9 @@ int load_run(pic_ctx* ctx, int run, int s, const pic_species* sp, int64_t n, con
     P.dragf = (float)(-std::expm1(-sp->nu * c.dt));
     P.drag = sp->nu > 0 ? 1 : 0;
     set_species_scales(ctx, R);
-    if (P.drag && !R.msum[0]) {
-        for (int d = 0; d < 3; ++d) {
-            R.msum[d] = at<long long>(ctx, ctx->lay.msum[d][run]);
-            R.ubar[d] = at<float>(ctx, ctx->lay.ubar[d][run]);
-        }
-        R.mcnt = at<int>(ctx, ctx->lay.mcnt[run]);
-    }
+    if (P.drag) return start_drag(ctx, run, s);
     rc = upload_runs(ctx);
     if (rc) return rc;
-    if (P.drag) {
-        CK(launch_moments_init(ctx->args, s, run, G.cell_off, G.ncell, ctx->stream));
-        CK(launch_moments_finalize(ctx->args, run, G.ncell, ctx->stream));
-    }
     CK(cudaStreamSynchronize(ctx->stream));
     return device_flags(ctx);
 }
@@ -922,6 +940,40 @@ extern "C" int pic_record_moments(pic_ctx* ctx, int run, int bx, int by, float* 
     CK(launch_moments(ctx->args, ctx->runs[run], run, bx, by, q_bg, nu_bg, out, scratch, ctx->stream));
     if (ncoarse_out) *ncoarse_out = nc;
     return PIC_OK;
+}
+
+extern "C" int pic_set_drag_map(pic_ctx* ctx, int run, int s, const float* nu, int32_t bx, int32_t by) {
+    if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    int rc = check_run(ctx, run);
+    if (rc) return rc;
+    if (s < 0 || s >= ctx->cfg.nspecies) return fail(ctx, PIC_EINVAL, "species %d out of range", s);
+    RunDev& R = ctx->runs[run];
+    SpeciesParams& P = R.sp[s];
+    if (!P.active) return fail(ctx, PIC_ESTATE, "species %d of run %d is not loaded", s, run);
+    if (!nu) {
+        R.dragmap[s] = nullptr;
+        rc = upload_runs(ctx);
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(ctx->stream));
+        return PIC_OK;
+    }
+    if (bx < 1 || by < 1 || R.nx % bx || R.ny % by)
+        return fail(ctx, PIC_EINVAL, "coarse block %d x %d must divide the grid %d x %d", bx, by, R.nx, R.ny);
+    for (int o = 0; o < PIC_NS; ++o)
+        if (o != s && R.sp[o].drag)
+            return fail(ctx, PIC_EINVAL, "run %d: the Krook drag acts on one species per run", run);
+    float* map = at<float>(ctx, ctx->lay.dragmap[s][run]);
+    CK(launch_drag_map(R, map, nu, bx, by, ctx->cfg.dt, ctx->stream));
+    R.dragmap[s] = map;
+    if (!P.drag) {
+        P.drag = 1;
+        P.dragf = 0.f;
+        return start_drag(ctx, run, s);
+    }
+    rc = upload_runs(ctx);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return device_flags(ctx);
 }
 
 // ---------------------------------------------------------------- closure network

@@ -430,6 +430,25 @@ cudaError_t launch_moments_finalize(const Args& a, int run, long long ncell, cud
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void drag_map_kernel(float* __restrict__ map, const float* __restrict__ nu, int nx, int ny,
+                                long long n, int bx, int by, double dt) {
+    const int ncx = nx / bx;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const long long col = c % ((long long)nx * ny);
+        const int j = (int)(col / nx), i = (int)(col - (long long)j * nx);
+        const float r = nu[(long long)(j / by) * ncx + i / bx];
+        map[c] = r > 0.f ? (float)(-expm1(-(double)r * dt)) : 0.f;
+    }
+}
+}  // namespace
+
+cudaError_t launch_drag_map(const RunDev& R, float* map, const float* nu, int bx, int by, double dt, cudaStream_t s) {
+    const long long n = (long long)R.nx * R.ny * R.nz;
+    drag_map_kernel<<<grid_for(n), NT, 0, s>>>(map, nu, R.nx, R.ny, n, bx, by, dt);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fit(const Args& a, int run, long long first, int nrec, int width, double t_noise,
                        double start_factor, double end_factor, double* out3, cudaStream_t s) {
     fit_kernel<<<1, NT, 0, s>>>(a.hist + (size_t)run * a.hist_cap, a.hist_cap, first, nrec, width,

@@ -49,8 +49,14 @@ struct RunDev {
     long long* msum[3];     // drag moments being accumulated (this step)
     int* mcnt;
     float* ubar[3];         // previous step's cell-mean momentum
+    float* dragmap[PIC_NS]; // per-cell drag factor 1 - exp(-nu_c dt) replacing sp[s].dragf, or null
     SpeciesParams sp[PIC_NS];
 };
+
+// Drag factor of species s in local cell lc of run R (the per-cell map if one is set).
+__device__ __forceinline__ float drag_factor(const RunDev* R, const SpeciesParams& P, int s, long long lc) {
+    return R->dragmap[s] ? R->dragmap[s][lc] : P.dragf;
+}
 
 // One species in one buffer.  A cell's cap slots are a stay area [0, cap_stay), filled in order
 // by the warp that owns the cell (count = its fill), and an immigrant area [cap_stay, cap) that
@@ -228,6 +234,9 @@ cudaError_t launch_mlp_train(float* params, float* am, float* av, int t, float l
                              void* scratch, cudaStream_t s);
 cudaError_t mlp_status(int* err, bool clear);
 cudaError_t preload_mlp();
+// Per-cell drag factors of run `run` from per-coarse-cell rates nu (bx x by blocks).
+cudaError_t launch_drag_map(const RunDev& host_run, float* map, const float* nu, int bx, int by, double dt,
+                            cudaStream_t s);
 cudaError_t launch_fit(const Args& a, int run, long long first, int nrec, int width, double t_noise,
                        double start_factor, double end_factor, double* out3, cudaStream_t s);
 }  // namespace pic

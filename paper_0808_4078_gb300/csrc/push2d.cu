@@ -186,16 +186,16 @@ struct Pushed {
 template <class A>
 __device__ __forceinline__ Pushed push_one(const A& F, const SpeciesParams& P, const RunDev* Rp,
                                            float ox, float oy, float ux, float uy, float uz,
-                                           float b0, float b1, float b2) {
+                                           float b0, float b1, float b2, float df) {
     Pushed r;
     const W3 wx = weights(ox), wy = weights(oy);
     float EB[6];
     gather(F, wx, wy, EB);
     boris(P.qmdt2, EB, ux, uy, uz);
     if (P.drag) {
-        ux = __fmaf_rn(-P.dragf, b0, ux);
-        uy = __fmaf_rn(-P.dragf, b1, uy);
-        uz = __fmaf_rn(-P.dragf, b2, uz);
+        ux = __fmaf_rn(-df, b0, ux);
+        uy = __fmaf_rn(-df, b1, uy);
+        uz = __fmaf_rn(-df, b2, uz);
     }
     const float ig = rsqrtf(__fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmaf_rn(ux, ux, 1.f))));
     const float rx = __fmaf_rn(__fmul_rn(ux, ig), Rp->dtdx, ox);
@@ -283,7 +283,8 @@ __device__ __forceinline__ void drain(Smem& sm, const Args& a, const RunDev* Rp,
     const int n0 = iy * RX + ix;
     float b0 = 0.f, b1 = 0.f, b2 = 0.f;
     if (P.drag) { b0 = sm.ub[0][n0]; b1 = sm.ub[1][n0]; b2 = sm.ub[2][n0]; }
-    const Pushed r = push_one(SharedFields{&sm, n0}, P, Rp, ox, oy, u0x, u0y, u0z, b0, b1, b2);
+    const float df = P.drag ? drag_factor(Rp, P, s, g - Rp->cell_off) : 0.f;
+    const Pushed r = push_one(SharedFields{&sm, n0}, P, Rp, ox, oy, u0x, u0y, u0z, b0, b1, b2, df);
     if (r.bad) {
         // keep the particle where it was, unmoved; the sticky flag fails the run
         atomicOr(&a.ctl->err, ERR_BADPART);
@@ -500,7 +501,8 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
             ux = sm.stg[warp][st][2][lane]; uy = sm.stg[warp][st][3][lane]; uz = sm.stg[warp][st][4][lane];
             id = __float_as_int(sm.stg[warp][st][5][lane]);
         }
-        const Pushed r = push_one(cc, P, Rp, ox, oy, ux, uy, uz, ub0, ub1, ub2);
+        const float df = P.drag ? drag_factor(Rp, P, s, g - Rp->cell_off) : 0.f;
+        const Pushed r = push_one(cc, P, Rp, ox, oy, ux, uy, uz, ub0, ub1, ub2, df);
         const bool small_u = !P.drag || (fabsf(r.ux) < 4.f && fabsf(r.uy) < 4.f && fabsf(r.uz) < 4.f);
         const bool stay = act && !r.bad && r.sx == 0 && r.sy == 0 && small_u;
         if (stay) {
@@ -628,7 +630,8 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
             const int id = S.sid ? S.sid[k] : 0;
             float b0 = 0.f, b1 = 0.f, b2 = 0.f;
             if (P.drag) { b0 = Rp->ubar[0][lc]; b1 = Rp->ubar[1][lc]; b2 = Rp->ubar[2][lc]; }
-            const Pushed r = push_one(GlobalFields{Rp, cx, cy}, P, Rp, ox, oy, u0x, u0y, u0z, b0, b1, b2);
+            const float df = P.drag ? drag_factor(Rp, P, s, lc) : 0.f;
+            const Pushed r = push_one(GlobalFields{Rp, cx, cy}, P, Rp, ox, oy, u0x, u0y, u0z, b0, b1, b2, df);
             if (r.bad) {
                 atomicOr(&a.ctl->err, ERR_BADPART);
                 put_imm(D, cap, cst, a.spill_cap[s], g, ox, oy, u0x, u0y, u0z, id, &a.ctl->err);

@@ -133,16 +133,16 @@ struct Pushed3 {
 template <class A>
 __device__ __forceinline__ Pushed3 push3_one(const A& F, const SpeciesParams& P, const RunDev* Rp,
                                              const float o[3], float ux, float uy, float uz,
-                                             float b0, float b1, float b2) {
+                                             float b0, float b1, float b2, float df) {
     Pushed3 r;
     const AxisW wx = axis_weights(o[0]), wy = axis_weights(o[1]), wz = axis_weights(o[2]);
     float EB[6];
     gather3(F, wx, wy, wz, EB);
     boris(P.qmdt2, EB, ux, uy, uz);
     if (P.drag) {
-        ux = __fmaf_rn(-P.dragf, b0, ux);
-        uy = __fmaf_rn(-P.dragf, b1, uy);
-        uz = __fmaf_rn(-P.dragf, b2, uz);
+        ux = __fmaf_rn(-df, b0, ux);
+        uy = __fmaf_rn(-df, b1, uy);
+        uz = __fmaf_rn(-df, b2, uz);
     }
     const float ig = rsqrtf(__fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmaf_rn(ux, ux, 1.f))));
     const float rx = __fmaf_rn(__fmul_rn(ux, ig), Rp->dtdx, o[0]);
@@ -399,9 +399,10 @@ __global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
             const Slots& D = a.slot[s][par ^ 1];
             float b0v = 0.f, b1v = 0.f, b2v = 0.f;
             if (P.drag) { b0v = sm.ub[0][n0]; b1v = sm.ub[1][n0]; b2v = sm.ub[2][n0]; }
-            const Pushed3 res = push3_one(SharedFields3{&sm, n0}, P, Rp, po[r], pu[r][0], pu[r][1], pu[r][2],
-                                          b0v, b1v, b2v);
             const long long g = cbase + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
+            const float df = P.drag ? drag_factor(Rp, P, s, g - cbase) : 0.f;
+            const Pushed3 res = push3_one(SharedFields3{&sm, n0}, P, Rp, po[r], pu[r][0], pu[r][1], pu[r][2],
+                                          b0v, b1v, b2v, df);
             if (res.bad) {
                 // keep the particle where it was, unmoved; the sticky flag fails the run
                 atomicOr(&a.ctl->err, ERR_BADPART);
@@ -528,7 +529,8 @@ __global__ void __launch_bounds__(NT) spill3d_kernel(const Args a) {
             const int id = S.sid ? S.sid[k] : 0;
             float b0 = 0.f, b1 = 0.f, b2 = 0.f;
             if (P.drag) { b0 = Rp->ubar[0][lc]; b1 = Rp->ubar[1][lc]; b2 = Rp->ubar[2][lc]; }
-            const Pushed3 r = push3_one(GlobalFields3{Rp, cx, cy, cz}, P, Rp, o, u0x, u0y, u0z, b0, b1, b2);
+            const float df = P.drag ? drag_factor(Rp, P, s, lc) : 0.f;
+            const Pushed3 r = push3_one(GlobalFields3{Rp, cx, cy, cz}, P, Rp, o, u0x, u0y, u0z, b0, b1, b2, df);
             if (r.bad) {
                 atomicOr(&a.ctl->err, ERR_BADPART);
                 put_imm3(D, cap, cst, a.spill_cap[s], g, o, u0x, u0y, u0z, id, &a.ctl->err);
