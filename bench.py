@@ -112,6 +112,8 @@ def _workers():
 
 
 def workload_name(args):
+    if args.workload == "closure":
+        return f"closure_mlp_9x64x64x1_{args.samples}samples"
     if args.workload == "warm2d":
         return f"warm_beam_krook_2d_{args.n}x{args.n}_ppc{args.ppc}"
     if args.workload == "hot3d":
@@ -143,8 +145,31 @@ def _oracle_sample(args):
                            nu=0.1, seed=1000), "one 128x128 run of the scan recipe")
 
 
+def cpu_baseline_closure(args, seconds=15.0):
+    """The FP64 oracle network (numpy) on 65536 samples, repeated for about `seconds`."""
+    from oracle import mlp
+    n = 65536
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(n, 9))
+    p = mlp.init_params(1)
+    mu, sd = np.zeros(9), np.ones(9)
+    mlp.forward(p, x, mu, sd)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        mlp.forward(p, x, mu, sd)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": n * reps / el, "unit": "samples/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"{n} samples x {reps} forward passes in {el:.1f} s, FP64 numpy (BLAS threads)"}
+
+
 def cpu_baseline(args, seconds=15.0):
     """The oracle as it is, single-threaded, on a bounded crop of the same physics."""
+    if args.workload == "closure":
+        return cpu_baseline_closure(args, seconds)
     import oracle
     wl, what = _oracle_sample(args)
     sim = oracle.Simulation.from_workload(wl)
@@ -167,13 +192,14 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     cb = cpu_baseline(args, seconds=max(5.0, 3.0 * args.steps))
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": METRIC,
+    metric = "closure inference samples/s" if args.workload == "closure" else METRIC
+    line = {"impl": "reference", "metric": metric, "value": cb["value"], "unit": cb["unit"],
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args), "oracle_sample": cb["sample"]},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": cb["sample"],
-                             "value": cb["value"], "unit": METRIC},
-            "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0,
+            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"],
+                             "value": cb["value"], "unit": cb["unit"]},
+            "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -421,13 +447,151 @@ def run_scan(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- closure (recorder + network)
+def _closure_params(seed):
+    """Seeded network parameters, uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)), library order."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.uniform(-1, 1, 64 * 9) / 3.0, rng.uniform(-1, 1, 64) / 3.0,
+             rng.uniform(-1, 1, 64 * 64) / 8.0, rng.uniform(-1, 1, 64) / 8.0,
+             rng.uniform(-1, 1, 64) / 8.0, np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+
+def run_closure(args, rank, world, local_rank):
+    """Moment recorder on a 3D hot-beam state, network inference on 2^20 samples per call and a
+    full-batch training step on 2^20 samples.  value = inference samples/s."""
+    import torch
+    import paper_0808_4078_gb300 as pic
+
+    dist = _init_dist(world, local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    def ev_time(fn, stream, reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    # recorder
+    L = build_load(argparse.Namespace(**{**vars(args), "workload": "hot3d", "ppc": args.rec_ppc}), rank)
+    wl = L.workload
+    eng = pic.Engine(3, wl.nx, wl.ny, wl.nz, dx=wl.dx, dt=wl.dt, capacity=[sp.n for sp in wl.species],
+                     sort_interval=args.sort, diag_interval=0, flags=0, device=f"cuda:{local_rank}")
+    for i, sp in enumerate(wl.species):
+        eng.load_species(i, sp.q, sp.m, sp.w, sp.nu, sp.cell, sp.offset, sp.u)
+    npart, ncell = wl.nparticles, wl.ncell
+    L.close()
+    eng.step(4)
+    import ctypes
+    nbytes = ctypes.c_size_t(0)
+    pic._check(pic.lib().pic_record_moments_scratch_bytes(eng._ctx, 0, 4, 4, ctypes.byref(nbytes)), eng._ctx)
+    nc = (wl.nx // 4) * (wl.ny // 4)
+    out = torch.empty((pic.PIC_MOM_ROWS, nc), dtype=torch.float32, device=dev)
+    scratch = torch.empty(nbytes.value, dtype=torch.uint8, device=dev)
+    n64 = ctypes.c_int64(0)
+
+    def record():
+        pic._check(pic.lib().pic_record_moments(eng._ctx, 0, 4, 4, ctypes.c_void_p(out.data_ptr()), out.numel(),
+                                                ctypes.c_void_p(scratch.data_ptr()), nbytes.value,
+                                                ctypes.byref(n64)), eng._ctx)
+    rec_ms = ev_time(record, eng.stream, max(3, args.steps // 4))
+    eng.close()
+    del eng, scratch
+    torch.cuda.empty_cache()
+
+    # network
+    n = args.samples
+    g = torch.Generator(device=dev).manual_seed(5)
+    x = torch.randn((9, n), generator=g, device=dev, dtype=torch.float32)
+    t = torch.randn((n,), generator=g, device=dev, dtype=torch.float32)
+    net = pic.ClosureNet(_closure_params(1), [0.0] * 9, [1.0] * 9, device=dev)
+    y = torch.empty(n, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    lib = pic.lib()
+
+    def infer():
+        pic._check(lib.pic_mlp_forward(ctypes.c_void_p(net.params.data_ptr()), ctypes.byref(net.norm),
+                                       ctypes.c_void_p(x.data_ptr()), n, n, ctypes.c_void_p(y.data_ptr()),
+                                       ctypes.c_void_p(net.stream.cuda_stream)))
+    with Clocks(local_rank) as clk:
+        inf_ms = ev_time(infer, net.stream, args.steps)
+    pic._check(lib.pic_mlp_status(1))
+    step = [0]
+
+    def train():
+        step[0] += 1
+        pic._check(lib.pic_mlp_train_step(ctypes.c_void_p(net.params.data_ptr()), ctypes.c_void_p(net.m.data_ptr()),
+                                          ctypes.c_void_p(net.v.data_ptr()), step[0], 1e-4, ctypes.byref(net.norm),
+                                          ctypes.c_void_p(x.data_ptr()), n, ctypes.c_void_p(t.data_ptr()), n,
+                                          None, ctypes.c_void_p(net._scratch.data_ptr()), net._scratch.numel(),
+                                          ctypes.c_void_p(net.stream.cuda_stream)))
+    train_ms = ev_time(train, net.stream, max(3, args.steps // 4))
+    pic._check(lib.pic_mlp_status(1))
+
+    # end to end: host features -> device, inference, host result
+    xh = x.cpu().pin_memory()
+    yh = torch.empty(n, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(net.stream):
+            x.copy_(xh, non_blocking=True)
+            infer()
+            yh.copy_(y, non_blocking=True)
+    net.stream.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+
+    if rank == 0:
+        peaks = {}
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                peaks = json.load(f)
+        except Exception:
+            pass
+        bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+        flops = 2.0 * n * (16 * 64 + 64 * 64)          # the two tensor-core products (K padded to 16)
+        tflops = flops / (inf_ms / 1e3) / 1e12
+        rec_bytes = npart * 36 + ncell * 32           # pass 1 reads u, pass 2 o + u; field columns
+        line = {
+            "metric": "closure inference samples/s", "value": n / (inf_ms / 1e3), "unit": "samples/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": inf_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": f"closure_mlp_9x64x64x1_{n}samples", "samples_per_call": n,
+                       "recorder_state": f"hot_beam_3d_{wl.nx}x{wl.ny}x{wl.nz}_ppc{args.rec_ppc}",
+                       "l2": "features 37.7 MB < L2: inference inputs may be L2-resident between calls"},
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                         "frac": tflops / bf16_peak, "traffic": None, "kernel": "mlp_forward",
+                         "peak_kind": "measured" if "bf16_tflops" in peaks else "fallback",
+                         "flops_per_launch": flops, "mean_launch_ms": inf_ms},
+            "recorder": {"ms_per_snapshot": rec_ms, "coarse_cells": nc, "particles": npart,
+                         "alg_bytes": rec_bytes, "achieved_gbs": rec_bytes / (rec_ms / 1e3) / 1e9},
+            "train": {"ms_per_step": train_ms, "samples_per_s": n / (train_ms / 1e3)},
+            "e2e": {"value": n / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 36 * n,
+                    "d2h_bytes_per_step": 4 * n},
+            "gpu_launches": 1,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="warm2d", choices=["warm2d", "hot3d", "scan"])
+    ap.add_argument("--workload", default="warm2d", choices=["warm2d", "hot3d", "scan", "closure"])
     ap.add_argument("--n", type=int, default=1024, help="2D grid side (warm2d)")
     ap.add_argument("--grid3", type=lambda t: tuple(int(x) for x in t.split(",")),
                     default=(256, 256, 512), help="3D grid nx,ny,nz (hot3d)")
@@ -438,11 +602,13 @@ def main():
     ap.add_argument("--diag", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-run", action="store_true", help="scan: skip the per-run baseline")
+    ap.add_argument("--samples", type=int, default=1 << 20, help="closure: network samples per call")
+    ap.add_argument("--rec-ppc", type=int, default=8, help="closure: particles per cell of the recorder state")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.ppc is None:
-        args.ppc = {"warm2d": 64, "hot3d": 8, "scan": 32}[args.workload]
+        args.ppc = {"warm2d": 64, "hot3d": 8, "scan": 32, "closure": 8}[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -451,6 +617,8 @@ def main():
         return
     if args.workload == "scan":
         run_scan(args, rank, world, local_rank)
+    elif args.workload == "closure":
+        run_closure(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

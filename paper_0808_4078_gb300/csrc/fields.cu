@@ -16,62 +16,74 @@ namespace {
 
 constexpr int NT = 256;
 
-// ------------------------------------------------------------------ 2D Yee
-__global__ void yee_b_half_2d(const RunDev* __restrict__ runs, int run) {
-    const RunDev& R = runs[run];
-    const int nx = R.nx, ny = R.ny;
-    const long long n = (long long)nx * ny;
-    const float hx = 0.5f * R.cx, hy = 0.5f * R.cy;
+// ------------------------------------------------------------------ Yee cells
+// E update of one cell (2D or 3D): curl B from the backward neighbours (offsets dxm, dym, dzm;
+// dzm = 0 in 2D), the step's current (int64 fixed point, cleared after use, kept in Jlast on
+// request) and the drag-moment finalisation.  Every pointer is read from the run table before
+// the first store: otherwise each store could alias the table and force the pointers to be
+// reloaded from memory in a dependent chain.
+__device__ __forceinline__ void e_cell(const RunDev& R, long long c, long long dxm, long long dym, long long dzm,
+                                       float dt) {
     float* __restrict__ Ex = R.E[0];
     float* __restrict__ Ey = R.E[1];
     float* __restrict__ Ez = R.E[2];
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-         c += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
-        const int ip = i + 1 == nx ? 0 : i + 1;
-        const int jp = j + 1 == ny ? 0 : j + 1;
-        const long long cxp = (long long)j * nx + ip, cyp = (long long)jp * nx + i;
-        const float ez = Ez[c];
-        R.B[0][c] -= hy * (Ez[cyp] - ez);
-        R.B[1][c] += hx * (Ez[cxp] - ez);
-        R.B[2][c] -= hx * (Ey[cxp] - Ey[c]) - hy * (Ex[cyp] - Ex[c]);
-    }
-}
-
-__global__ void yee_e_2d(const RunDev* __restrict__ runs, int run, float dt) {
-    const RunDev& R = runs[run];
-    const int nx = R.nx, ny = R.ny;
-    const long long n = (long long)nx * ny;
-    const float cx = R.cx, cy = R.cy, js = R.jscale * dt;
     const float* __restrict__ Bx = R.B[0];
     const float* __restrict__ By = R.B[1];
     const float* __restrict__ Bz = R.B[2];
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-         c += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
-        const int im = i == 0 ? nx - 1 : i - 1;
-        const int jm = j == 0 ? ny - 1 : j - 1;
-        const long long cxm = (long long)j * nx + im, cym = (long long)jm * nx + i;
-        const long long j0 = R.J[0][c], j1 = R.J[1][c], j2 = R.J[2][c];
-        const float jx = (float)j0 * js, jy = (float)j1 * js, jz = (float)j2 * js;
-        R.J[0][c] = 0; R.J[1][c] = 0; R.J[2][c] = 0;
-        if (R.Jlast[0]) { R.Jlast[0][c] = j0; R.Jlast[1][c] = j1; R.Jlast[2][c] = j2; }
-        const float bz = Bz[c];
-        R.E[0][c] += cy * (bz - Bz[cym]) - jx;
-        R.E[1][c] += -cx * (bz - Bz[cxm]) - jy;
-        R.E[2][c] += cx * (By[c] - By[cxm]) - cy * (Bx[c] - Bx[cym]) - jz;
-        if (R.msum[0]) {
-            const int cnt = R.mcnt[c];
-            const float inv = cnt > 0 ? 1.0f / (float)cnt : 0.f;
-            const float sc = inv * (1.0f / 1048576.0f);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                R.ubar[k][c] = (float)R.msum[k][c] * sc;
-                R.msum[k][c] = 0;
-            }
-            R.mcnt[c] = 0;
-        }
+    long long* __restrict__ J0 = R.J[0];
+    long long* __restrict__ J1 = R.J[1];
+    long long* __restrict__ J2 = R.J[2];
+    long long* __restrict__ L0 = R.Jlast[0];
+    long long* __restrict__ L1 = R.Jlast[1];
+    long long* __restrict__ L2 = R.Jlast[2];
+    long long* __restrict__ M0 = R.msum[0];
+    long long* __restrict__ M1 = R.msum[1];
+    long long* __restrict__ M2 = R.msum[2];
+    int* __restrict__ MC = R.mcnt;
+    float* __restrict__ U0 = R.ubar[0];
+    float* __restrict__ U1 = R.ubar[1];
+    float* __restrict__ U2 = R.ubar[2];
+    const float cx = R.cx, cy = R.cy, cz = R.cz, js = R.jscale * dt;
+    const long long j0 = J0[c], j1 = J1[c], j2 = J2[c];
+    const float bx = Bx[c], by = By[c], bz = Bz[c];
+    const float bz_ym = Bz[c - dym], bz_xm = Bz[c - dxm], by_xm = By[c - dxm], bx_ym = Bx[c - dym];
+    const float by_zm = dzm ? By[c - dzm] : by, bx_zm = dzm ? Bx[c - dzm] : bx;
+    const float ex = Ex[c], ey = Ey[c], ez = Ez[c];
+    const float jx = (float)j0 * js, jy = (float)j1 * js, jz = (float)j2 * js;
+    J0[c] = 0; J1[c] = 0; J2[c] = 0;
+    if (L0) { L0[c] = j0; L1[c] = j1; L2[c] = j2; }
+    Ex[c] = ex + (cy * (bz - bz_ym) - cz * (by - by_zm) - jx);
+    Ey[c] = ey + (cz * (bx - bx_zm) - cx * (bz - bz_xm) - jy);
+    Ez[c] = ez + (cx * (by - by_xm) - cy * (bx - bx_ym) - jz);
+    if (M0) {
+        const int cnt = MC[c];
+        const long long m0 = M0[c], m1 = M1[c], m2 = M2[c];
+        const float inv = cnt > 0 ? 1.0f / (float)cnt : 0.f;
+        const float sc = inv * (1.0f / 1048576.0f);
+        U0[c] = (float)m0 * sc;
+        U1[c] = (float)m1 * sc;
+        U2[c] = (float)m2 * sc;
+        M0[c] = 0; M1[c] = 0; M2[c] = 0;
+        MC[c] = 0;
     }
+}
+
+// B half step of one cell from the forward neighbours (dzp = 0 in 2D), pointers read first.
+__device__ __forceinline__ void b_cell(const RunDev& R, long long c, long long dxp, long long dyp, long long dzp) {
+    const float* __restrict__ Ex = R.E[0];
+    const float* __restrict__ Ey = R.E[1];
+    const float* __restrict__ Ez = R.E[2];
+    float* __restrict__ Bx = R.B[0];
+    float* __restrict__ By = R.B[1];
+    float* __restrict__ Bz = R.B[2];
+    const float hx = 0.5f * R.cx, hy = 0.5f * R.cy, hz = 0.5f * R.cz;
+    const float ex = Ex[c], ey = Ey[c], ez = Ez[c];
+    const float ez_yp = Ez[c + dyp], ez_xp = Ez[c + dxp], ey_xp = Ey[c + dxp], ex_yp = Ex[c + dyp];
+    const float ey_zp = dzp ? Ey[c + dzp] : ey, ex_zp = dzp ? Ex[c + dzp] : ex;
+    const float bx = Bx[c], by = By[c], bz = Bz[c];
+    Bx[c] = bx - (hy * (ez_yp - ez) - hz * (ey_zp - ey));
+    By[c] = by - (hz * (ex_zp - ex) - hx * (ez_xp - ez));
+    Bz[c] = bz - (hx * (ey_xp - ey) - hy * (ex_yp - ex));
 }
 
 // Tile-batched 2D Yee over the (run, tile) work list: one CTA per 16 x 16 tile, a thread per
@@ -84,18 +96,9 @@ __global__ void __launch_bounds__(NT) yee_b_half_2d_tiles(Args a) {
     const int nx = R.nx, ny = R.ny;
     const int i = (wk.y % R.ntx) * YTX + threadIdx.x % YTX;
     const int j = (wk.y / R.ntx) * YTY + threadIdx.x / YTX;
-    const float hx = 0.5f * R.cx, hy = 0.5f * R.cy;
-    const float* __restrict__ Ex = R.E[0];
-    const float* __restrict__ Ey = R.E[1];
-    const float* __restrict__ Ez = R.E[2];
-    const long long c = (long long)j * nx + i;
-    const int ip = i + 1 == nx ? 0 : i + 1;
-    const int jp = j + 1 == ny ? 0 : j + 1;
-    const long long cxp = (long long)j * nx + ip, cyp = (long long)jp * nx + i;
-    const float ez = Ez[c];
-    R.B[0][c] -= hy * (Ez[cyp] - ez);
-    R.B[1][c] += hx * (Ez[cxp] - ez);
-    R.B[2][c] -= hx * (Ey[cxp] - Ey[c]) - hy * (Ex[cyp] - Ex[c]);
+    const long long dxp = i + 1 == nx ? -(long long)(nx - 1) : 1;
+    const long long dyp = j + 1 == ny ? -(long long)(ny - 1) * nx : nx;
+    b_cell(R, (long long)j * nx + i, dxp, dyp, 0);
 }
 
 __global__ void __launch_bounds__(NT) yee_e_2d_tiles(Args a, float dt) {
@@ -104,33 +107,9 @@ __global__ void __launch_bounds__(NT) yee_e_2d_tiles(Args a, float dt) {
     const int nx = R.nx, ny = R.ny;
     const int i = (wk.y % R.ntx) * YTX + threadIdx.x % YTX;
     const int j = (wk.y / R.ntx) * YTY + threadIdx.x / YTX;
-    const float cx = R.cx, cy = R.cy, js = R.jscale * dt;
-    const float* __restrict__ Bx = R.B[0];
-    const float* __restrict__ By = R.B[1];
-    const float* __restrict__ Bz = R.B[2];
-    const long long c = (long long)j * nx + i;
-    const int im = i == 0 ? nx - 1 : i - 1;
-    const int jm = j == 0 ? ny - 1 : j - 1;
-    const long long cxm = (long long)j * nx + im, cym = (long long)jm * nx + i;
-    const long long j0 = R.J[0][c], j1 = R.J[1][c], j2 = R.J[2][c];
-    const float jx = (float)j0 * js, jy = (float)j1 * js, jz = (float)j2 * js;
-    R.J[0][c] = 0; R.J[1][c] = 0; R.J[2][c] = 0;
-    if (R.Jlast[0]) { R.Jlast[0][c] = j0; R.Jlast[1][c] = j1; R.Jlast[2][c] = j2; }
-    const float bz = Bz[c];
-    R.E[0][c] += cy * (bz - Bz[cym]) - jx;
-    R.E[1][c] += -cx * (bz - Bz[cxm]) - jy;
-    R.E[2][c] += cx * (By[c] - By[cxm]) - cy * (Bx[c] - Bx[cym]) - jz;
-    if (R.msum[0]) {
-        const int cnt = R.mcnt[c];
-        const float inv = cnt > 0 ? 1.0f / (float)cnt : 0.f;
-        const float sc = inv * (1.0f / 1048576.0f);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            R.ubar[k][c] = (float)R.msum[k][c] * sc;
-            R.msum[k][c] = 0;
-        }
-        R.mcnt[c] = 0;
-    }
+    const long long dxm = i == 0 ? -(long long)(nx - 1) : 1;
+    const long long dym = j == 0 ? -(long long)(ny - 1) * nx : nx;
+    e_cell(R, (long long)j * nx + i, dxm, dym, 0, dt);
 }
 
 // ------------------------------------------------------------------ 3D Yee
@@ -144,18 +123,10 @@ __global__ void __launch_bounds__(Y3X * Y3Y) yee_b_half_3d(const RunDev* __restr
     const int i = blockIdx.x * Y3X + threadIdx.x, j = blockIdx.y * Y3Y + threadIdx.y, k = blockIdx.z;
     if (i >= nx) return;
     const long long nxy = (long long)nx * ny;
-    const long long c = k * nxy + (long long)j * nx + i;
-    const float hx = 0.5f * R.cx, hy = 0.5f * R.cy, hz = 0.5f * R.cz;
-    const float* __restrict__ Ex = R.E[0];
-    const float* __restrict__ Ey = R.E[1];
-    const float* __restrict__ Ez = R.E[2];
     const long long dxp = (i + 1 == nx ? -(long long)(nx - 1) : 1);
     const long long dyp = (j + 1 == ny ? -(long long)(ny - 1) * nx : nx);
     const long long dzp = (k + 1 == nz ? -(long long)(nz - 1) * nxy : nxy);
-    const float ex = Ex[c], ey = Ey[c], ez = Ez[c];
-    R.B[0][c] -= hy * (Ez[c + dyp] - ez) - hz * (Ey[c + dzp] - ey);
-    R.B[1][c] -= hz * (Ex[c + dzp] - ex) - hx * (Ez[c + dxp] - ez);
-    R.B[2][c] -= hx * (Ey[c + dxp] - ey) - hy * (Ex[c + dyp] - ex);
+    b_cell(R, k * nxy + (long long)j * nx + i, dxp, dyp, dzp);
 }
 
 __global__ void __launch_bounds__(Y3X * Y3Y) yee_e_3d(const RunDev* __restrict__ runs, int run, float dt) {
@@ -164,33 +135,10 @@ __global__ void __launch_bounds__(Y3X * Y3Y) yee_e_3d(const RunDev* __restrict__
     const int i = blockIdx.x * Y3X + threadIdx.x, j = blockIdx.y * Y3Y + threadIdx.y, k = blockIdx.z;
     if (i >= nx) return;
     const long long nxy = (long long)nx * ny;
-    const long long c = k * nxy + (long long)j * nx + i;
-    const float cx = R.cx, cy = R.cy, cz = R.cz, js = R.jscale * dt;
-    const float* __restrict__ Bx = R.B[0];
-    const float* __restrict__ By = R.B[1];
-    const float* __restrict__ Bz = R.B[2];
     const long long dxm = (i == 0 ? -(long long)(nx - 1) : 1);
     const long long dym = (j == 0 ? -(long long)(ny - 1) * nx : nx);
     const long long dzm = (k == 0 ? -(long long)(nz - 1) * nxy : nxy);
-    const long long j0 = R.J[0][c], j1 = R.J[1][c], j2 = R.J[2][c];
-    const float jx = (float)j0 * js, jy = (float)j1 * js, jz = (float)j2 * js;
-    R.J[0][c] = 0; R.J[1][c] = 0; R.J[2][c] = 0;
-    if (R.Jlast[0]) { R.Jlast[0][c] = j0; R.Jlast[1][c] = j1; R.Jlast[2][c] = j2; }
-    const float bx = Bx[c], by = By[c], bz = Bz[c];
-    R.E[0][c] += cy * (bz - Bz[c - dym]) - cz * (by - By[c - dzm]) - jx;
-    R.E[1][c] += cz * (bx - Bx[c - dzm]) - cx * (bz - Bz[c - dxm]) - jy;
-    R.E[2][c] += cx * (by - By[c - dxm]) - cy * (bx - Bx[c - dym]) - jz;
-    if (R.msum[0]) {
-        const int cnt = R.mcnt[c];
-        const float inv = cnt > 0 ? 1.0f / (float)cnt : 0.f;
-        const float sc = inv * (1.0f / 1048576.0f);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            R.ubar[q][c] = (float)R.msum[q][c] * sc;
-            R.msum[q][c] = 0;
-        }
-        R.mcnt[c] = 0;
-    }
+    e_cell(R, k * nxy + (long long)j * nx + i, dxm, dym, dzm, dt);
 }
 
 // Moments -> <u> without a field update (after loading particles).
@@ -381,8 +329,7 @@ int grid_for(long long n) {
 
 cudaError_t preload_fields() {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, yee_b_half_2d);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, yee_e_2d);
+    cudaError_t e = cudaFuncGetAttributes(&fa, yee_b_half_2d_tiles);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, yee_b_half_3d);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, yee_e_3d);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, moments_finalize_kernel);

@@ -10,6 +10,32 @@ namespace pic {
 
 constexpr float MOM_SCALE = 1048576.0f;  // 2^20, fixed point of the drag moments
 
+// Per-run constants of the particle kernels, read from the run table once, before the first
+// store: the kernels store particles through pointers the compiler cannot tell apart from the
+// table, so fields read through it later would be reloaded from memory after every store.
+struct RunConst {
+    float dtdx, dtdy, dtdz;     // cells moved per unit velocity per step
+    int nx, ny, nz;
+    int cell_off;
+    const float* dmap0;         // per-cell drag factors of species 0 and 1 (or null)
+    const float* dmap1;
+};
+__device__ __forceinline__ RunConst run_const(const RunDev* R) {
+    static_assert(PIC_NS == 2, "two species slots");
+    RunConst k;
+    k.dtdx = R->dtdx; k.dtdy = R->dtdy; k.dtdz = R->dtdz;
+    k.nx = R->nx; k.ny = R->ny; k.nz = R->nz;
+    k.cell_off = R->cell_off;
+    k.dmap0 = R->dragmap[0];
+    k.dmap1 = R->dragmap[1];
+    return k;
+}
+// Drag factor of species s in local cell lc: the per-cell map if one is set, else the scalar.
+__device__ __forceinline__ float drag_of(const RunConst& k, const SpeciesParams& P, int s, long long lc) {
+    const float* m = s ? k.dmap1 : k.dmap0;
+    return m ? m[lc] : P.dragf;
+}
+
 // ------------------------------------------------------------------ shared accumulators
 __device__ __forceinline__ void add_split(unsigned* lo, int* hi, long long v) {
     if (v != 0) {

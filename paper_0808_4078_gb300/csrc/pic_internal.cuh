@@ -53,10 +53,6 @@ struct RunDev {
     SpeciesParams sp[PIC_NS];
 };
 
-// Drag factor of species s in local cell lc of run R (the per-cell map if one is set).
-__device__ __forceinline__ float drag_factor(const RunDev* R, const SpeciesParams& P, int s, long long lc) {
-    return R->dragmap[s] ? R->dragmap[s][lc] : P.dragf;
-}
 
 // One species in one buffer.  A cell's cap slots are a stay area [0, cap_stay), filled in order
 // by the warp that owns the cell (count = its fill), and an immigrant area [cap_stay, cap) that

@@ -184,7 +184,7 @@ struct Pushed {
 };
 
 template <class A>
-__device__ __forceinline__ Pushed push_one(const A& F, const SpeciesParams& P, const RunDev* Rp,
+__device__ __forceinline__ Pushed push_one(const A& F, const SpeciesParams& P, const RunConst& K,
                                            float ox, float oy, float ux, float uy, float uz,
                                            float b0, float b1, float b2, float df) {
     Pushed r;
@@ -198,8 +198,8 @@ __device__ __forceinline__ Pushed push_one(const A& F, const SpeciesParams& P, c
         uz = __fmaf_rn(-df, b2, uz);
     }
     const float ig = rsqrtf(__fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmaf_rn(ux, ux, 1.f))));
-    const float rx = __fmaf_rn(__fmul_rn(ux, ig), Rp->dtdx, ox);
-    const float ry = __fmaf_rn(__fmul_rn(uy, ig), Rp->dtdy, oy);
+    const float rx = __fmaf_rn(__fmul_rn(ux, ig), K.dtdx, ox);
+    const float ry = __fmaf_rn(__fmul_rn(uy, ig), K.dtdy, oy);
     r.bad = !(rx > -1.f && rx < 2.f && ry > -1.f && ry < 2.f);
     carry(rx, r.nox, r.sx);
     carry(ry, r.noy, r.sy);
@@ -262,17 +262,17 @@ __device__ __forceinline__ void put_imm(const Slots& D, int cap, int cap_stay, i
 // ------------------------------------------------------------------ crossing particles
 // Full step of up to 32 queued particles (one per lane) of the tile: shared-memory gather and
 // deposit, then rebinning into the destination cell of the other buffer.
-__device__ __forceinline__ void drain(Smem& sm, const Args& a, const RunDev* Rp, int par, int k,
+__device__ __forceinline__ void drain(Smem& sm, const Args& a, const RunConst& K, int par, int k,
                                       int lane, int warp, int x0, int y0, bool diag,
                                       long long kacc[5]) {
     if (lane >= k) return;
-    const int nx = Rp->nx, ny = Rp->ny;
+    const int nx = K.nx, ny = K.ny;
     const unsigned e = sm.q[warp][lane];
     const int s = e >> 24, ci = (e >> 16) & 255, i = e & 65535;
     const SpeciesParams& P = sm.sp[s];
     const int lx = ci % TX, ly = ci / TX;
     const int cx = x0 + lx, cy = y0 + ly;
-    const int g = Rp->cell_off + cy * nx + cx;
+    const int g = K.cell_off + cy * nx + cx;
     const int cap = a.cap[s], cst = a.cap_stay[s];
     const Slots S = a.slot[s][par], D = a.slot[s][par ^ 1];
     const size_t p = slot_of(g, cap, cst, sm.cns[s][ci], i);
@@ -283,8 +283,8 @@ __device__ __forceinline__ void drain(Smem& sm, const Args& a, const RunDev* Rp,
     const int n0 = iy * RX + ix;
     float b0 = 0.f, b1 = 0.f, b2 = 0.f;
     if (P.drag) { b0 = sm.ub[0][n0]; b1 = sm.ub[1][n0]; b2 = sm.ub[2][n0]; }
-    const float df = P.drag ? drag_factor(Rp, P, s, g - Rp->cell_off) : 0.f;
-    const Pushed r = push_one(SharedFields{&sm, n0}, P, Rp, ox, oy, u0x, u0y, u0z, b0, b1, b2, df);
+    const float df = P.drag ? drag_of(K, P, s, g - K.cell_off) : 0.f;
+    const Pushed r = push_one(SharedFields{&sm, n0}, P, K, ox, oy, u0x, u0y, u0z, b0, b1, b2, df);
     if (r.bad) {
         // keep the particle where it was, unmoved; the sticky flag fails the run
         atomicOr(&a.ctl->err, ERR_BADPART);
@@ -308,7 +308,7 @@ __device__ __forceinline__ void drain(Smem& sm, const Args& a, const RunDev* Rp,
     int ncx = cx + r.sx, ncy = cy + r.sy;
     ncx = ncx < 0 ? ncx + nx : (ncx >= nx ? ncx - nx : ncx);
     ncy = ncy < 0 ? ncy + ny : (ncy >= ny ? ncy - ny : ncy);
-    const int g1 = Rp->cell_off + ncy * nx + ncx;
+    const int g1 = K.cell_off + ncy * nx + ncx;
     put_imm(D, cap, cst, a.spill_cap[s], g1, r.nox, r.noy, r.ux, r.uy, r.uz, id, &a.ctl->err);
 }
 
@@ -342,7 +342,8 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const int2 wk = a.work[blockIdx.x];
     const RunDev* Rp = &a.runs[wk.x];
-    const int nx = Rp->nx, ny = Rp->ny;
+    const RunConst K = run_const(Rp);
+    const int nx = K.nx, ny = K.ny;
     const int tile = wk.y;
     const int x0 = (tile % Rp->ntx) * TX, y0 = (tile / Rp->ntx) * TY;
     const int gx0 = x0 - 1, gy0 = y0 - 1;
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
     if (tid < PIC_NS) sm.sp[tid] = Rp->sp[tid];
     for (int i = tid; i < PIC_NS * CELLS; i += NT) {
         const int s = i / CELLS, ci = i - s * CELLS;
-        const int g = Rp->cell_off + (y0 + ci / TX) * nx + (x0 + ci % TX);
+        const int g = K.cell_off + (y0 + ci / TX) * nx + (x0 + ci % TX);
         CellRange cr{0, 0};
         if (s < a.nspecies && Rp->sp[s].active) cr = cell_range(a.slot[s][par], a.cap[s], a.cap_stay[s], g);
         sm.cnt[s][ci] = cr.n;
@@ -418,7 +419,7 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
             const int i = c.j + lane;
             if (i < sm.cnt[c.s][c.ci]) {
                 const int lx = c.ci % TX, ly = c.ci / TX;
-                const int g = Rp->cell_off + (y0 + ly) * nx + (x0 + lx);
+                const int g = K.cell_off + (y0 + ly) * nx + (x0 + lx);
                 const Slots S = a.slot[c.s][par];
                 const size_t q = slot_of(g, a.cap[c.s], a.cap_stay[c.s], sm.cns[c.s][c.ci], i);
                 cp_async4(&sm.stg[warp][st][0][lane], S.o[0] + q);
@@ -454,7 +455,7 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
             if (nchunk) { flush_acc(sm, acc, n0, lane); nchunk = 0; }
             cur_ci = pc.ci;
             const int lx = cur_ci % TX, ly = cur_ci / TX;
-            g = Rp->cell_off + (y0 + ly) * nx + (x0 + lx);
+            g = K.cell_off + (y0 + ly) * nx + (x0 + lx);
             n0 = (ly + 1) * RX + (lx + 1);
 #pragma unroll
             for (int b = 0; b < 2; ++b)
@@ -501,8 +502,8 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
             ux = sm.stg[warp][st][2][lane]; uy = sm.stg[warp][st][3][lane]; uz = sm.stg[warp][st][4][lane];
             id = __float_as_int(sm.stg[warp][st][5][lane]);
         }
-        const float df = P.drag ? drag_factor(Rp, P, s, g - Rp->cell_off) : 0.f;
-        const Pushed r = push_one(cc, P, Rp, ox, oy, ux, uy, uz, ub0, ub1, ub2, df);
+        const float df = P.drag ? drag_of(K, P, s, g - K.cell_off) : 0.f;
+        const Pushed r = push_one(cc, P, K, ox, oy, ux, uy, uz, ub0, ub1, ub2, df);
         const bool small_u = !P.drag || (fabsf(r.ux) < 4.f && fabsf(r.uy) < 4.f && fabsf(r.uz) < 4.f);
         const bool stay = act && !r.bad && r.sx == 0 && r.sy == 0 && small_u;
         if (stay) {
@@ -541,7 +542,7 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
         qn += __popc(dm);
         __syncwarp();
         if (qn >= 32) {
-            drain(sm, a, Rp, par, 32, lane, warp, x0, y0, diag, kacc);
+            drain(sm, a, K, par, 32, lane, warp, x0, y0, diag, kacc);
             __syncwarp();
             const int rest = qn - 32;
             const unsigned moved = lane < rest ? sm.q[warp][32 + lane] : 0u;
@@ -560,7 +561,7 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
     if (nchunk) flush_acc(sm, acc, n0, lane);
     if (seg_s >= 0 && lane == 0) a.slot[seg_s][par ^ 1].count[seg_g] = wpos;
     cp_async_wait<0>();
-    if (qn > 0) drain(sm, a, Rp, par, qn, lane, warp, x0, y0, diag, kacc);
+    if (qn > 0) drain(sm, a, K, par, qn, lane, warp, x0, y0, diag, kacc);
     __syncwarp();
 
     if (diag) {
@@ -630,8 +631,9 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
             const int id = S.sid ? S.sid[k] : 0;
             float b0 = 0.f, b1 = 0.f, b2 = 0.f;
             if (P.drag) { b0 = Rp->ubar[0][lc]; b1 = Rp->ubar[1][lc]; b2 = Rp->ubar[2][lc]; }
-            const float df = P.drag ? drag_factor(Rp, P, s, lc) : 0.f;
-            const Pushed r = push_one(GlobalFields{Rp, cx, cy}, P, Rp, ox, oy, u0x, u0y, u0z, b0, b1, b2, df);
+            const RunConst K = run_const(Rp);
+            const float df = P.drag ? drag_of(K, P, s, lc) : 0.f;
+            const Pushed r = push_one(GlobalFields{Rp, cx, cy}, P, K, ox, oy, u0x, u0y, u0z, b0, b1, b2, df);
             if (r.bad) {
                 atomicOr(&a.ctl->err, ERR_BADPART);
                 put_imm(D, cap, cst, a.spill_cap[s], g, ox, oy, u0x, u0y, u0z, id, &a.ctl->err);

@@ -131,7 +131,7 @@ struct Pushed3 {
 };
 
 template <class A>
-__device__ __forceinline__ Pushed3 push3_one(const A& F, const SpeciesParams& P, const RunDev* Rp,
+__device__ __forceinline__ Pushed3 push3_one(const A& F, const SpeciesParams& P, const RunConst& K,
                                              const float o[3], float ux, float uy, float uz,
                                              float b0, float b1, float b2, float df) {
     Pushed3 r;
@@ -145,9 +145,9 @@ __device__ __forceinline__ Pushed3 push3_one(const A& F, const SpeciesParams& P,
         uz = __fmaf_rn(-df, b2, uz);
     }
     const float ig = rsqrtf(__fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmaf_rn(ux, ux, 1.f))));
-    const float rx = __fmaf_rn(__fmul_rn(ux, ig), Rp->dtdx, o[0]);
-    const float ry = __fmaf_rn(__fmul_rn(uy, ig), Rp->dtdy, o[1]);
-    const float rz = __fmaf_rn(__fmul_rn(uz, ig), Rp->dtdz, o[2]);
+    const float rx = __fmaf_rn(__fmul_rn(ux, ig), K.dtdx, o[0]);
+    const float ry = __fmaf_rn(__fmul_rn(uy, ig), K.dtdy, o[1]);
+    const float rz = __fmaf_rn(__fmul_rn(uz, ig), K.dtdz, o[2]);
     r.bad = !(rx > -1.f && rx < 2.f && ry > -1.f && ry < 2.f && rz > -1.f && rz < 2.f);
     carry(rx, r.no[0], r.st[0]);
     carry(ry, r.no[1], r.st[1]);
@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const int2 wk = a.work[blockIdx.x];
     const RunDev* Rp = &a.runs[wk.x];
-    const int nx = Rp->nx, ny = Rp->ny, nz = Rp->nz;
+    const RunConst K = run_const(Rp);
+    const int nx = K.nx, ny = K.ny, nz = K.nz;
     const int tile = wk.y;
     const int tx = tile % Rp->ntx, tyz = tile / Rp->ntx;
     const int x0 = tx * TX, y0 = (tyz % Rp->nty) * TY, z0 = (tyz / Rp->nty) * TZ;
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
     const bool diag = a.diag_interval > 0 && (step % a.diag_interval) == 0;
     const bool anydrag = Rp->msum[0] != nullptr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long long cbase = Rp->cell_off;
+    const long long cbase = K.cell_off;
 
     for (int i = tid; i < RN; i += NT) {
         const int rz = i / RXY, rr = i - rz * RXY, ry = rr / RX, rx = rr - ry * RX;
@@ -400,8 +401,8 @@ __global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
             float b0v = 0.f, b1v = 0.f, b2v = 0.f;
             if (P.drag) { b0v = sm.ub[0][n0]; b1v = sm.ub[1][n0]; b2v = sm.ub[2][n0]; }
             const long long g = cbase + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
-            const float df = P.drag ? drag_factor(Rp, P, s, g - cbase) : 0.f;
-            const Pushed3 res = push3_one(SharedFields3{&sm, n0}, P, Rp, po[r], pu[r][0], pu[r][1], pu[r][2],
+            const float df = P.drag ? drag_of(K, P, s, g - cbase) : 0.f;
+            const Pushed3 res = push3_one(SharedFields3{&sm, n0}, P, K, po[r], pu[r][0], pu[r][1], pu[r][2],
                                           b0v, b1v, b2v, df);
             if (res.bad) {
                 // keep the particle where it was, unmoved; the sticky flag fails the run
@@ -529,8 +530,9 @@ __global__ void __launch_bounds__(NT) spill3d_kernel(const Args a) {
             const int id = S.sid ? S.sid[k] : 0;
             float b0 = 0.f, b1 = 0.f, b2 = 0.f;
             if (P.drag) { b0 = Rp->ubar[0][lc]; b1 = Rp->ubar[1][lc]; b2 = Rp->ubar[2][lc]; }
-            const float df = P.drag ? drag_factor(Rp, P, s, lc) : 0.f;
-            const Pushed3 r = push3_one(GlobalFields3{Rp, cx, cy, cz}, P, Rp, o, u0x, u0y, u0z, b0, b1, b2, df);
+            const RunConst K = run_const(Rp);
+            const float df = P.drag ? drag_of(K, P, s, lc) : 0.f;
+            const Pushed3 r = push3_one(GlobalFields3{Rp, cx, cy, cz}, P, K, o, u0x, u0y, u0z, b0, b1, b2, df);
             if (r.bad) {
                 atomicOr(&a.ctl->err, ERR_BADPART);
                 put_imm3(D, cap, cst, a.spill_cap[s], g, o, u0x, u0y, u0z, id, &a.ctl->err);
