@@ -107,10 +107,33 @@ __device__ __forceinline__ float get_bf16(const unsigned char* tile, int row, in
     return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tile + kmaj<KB>(row, k)));
 }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
+// Logistic sigmoid through sigma(z) = (1 + tanh(z / 2)) / 2: one special-function operation
+// (tanh.approx, relative error ~2^-11, below the bfloat16 rounding of the hidden activations)
+// instead of an exponential and a reciprocal.  SiLU and its derivative use it in both the
+// forward and the training kernels, so training optimises the function inference evaluates.
+__device__ __forceinline__ float tanh_approx(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sigmoid(float z) { return fmaf(0.5f, tanh_approx(0.5f * z), 0.5f); }
+__device__ __forceinline__ float silu(float z) { return z * sigmoid(z); }
 __device__ __forceinline__ float dsilu(float z) {
-    const float s = 1.f / (1.f + __expf(-z));
+    const float s = sigmoid(z);
     return s * (1.f + z * (1.f - s));
+}
+
+// Eight consecutive values of one row into a K-major tile as one 16-byte store (k0 % 8 == 0).
+template <int KB>
+__device__ __forceinline__ void put8_bf16(unsigned char* tile, int row, int k0, const float* v) {
+    uint4 q;
+    unsigned* w = reinterpret_cast<unsigned*>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        w[i] = *reinterpret_cast<const unsigned*>(&b);
+    }
+    *reinterpret_cast<uint4*>(tile + kmaj<KB>(row, k0)) = q;
 }
 
 struct MlpArgs {
@@ -144,7 +167,9 @@ struct __align__(1024) MlpTrainSmem {
 };
 
 // Parameters -> shared memory (bfloat16 operand tiles and FP32 vectors); zero the padding.
-__device__ void load_params(MlpSmem& s, const float* p, unsigned char* w2t) {
+template <class S>
+__device__ void load_params(S& s, const float* p, unsigned char* w2t) {
+    const int NT = blockDim.x;
     for (int i = threadIdx.x; i < MLP_H * MLP_KIN; i += NT) {
         const int n = i / MLP_KIN, k = i % MLP_KIN;
         put_bf16<2>(s.W1, n, k, k < MLP_IN ? p[OFF_W1 + n * MLP_IN + k] : 0.f);
@@ -163,10 +188,12 @@ __device__ void load_params(MlpSmem& s, const float* p, unsigned char* w2t) {
     if (threadIdx.x == 0) s.b3 = p[OFF_B3];
 }
 
-// TMEM (64 columns) and the completion barrier; every thread gets the TMEM address.
-__device__ void setup(MlpSmem& s) {
+// TMEM (NCOL columns) and the completion barrier; every thread gets the TMEM address.
+template <int NCOL = 64, class S>
+__device__ void setup(S& s) {
     if (threadIdx.x < 32) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;\n" ::"r"(smem_u32(&s.tmem)) : "memory");
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     ::"r"(smem_u32(&s.tmem)), "r"(NCOL) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (threadIdx.x == 0) {
@@ -178,12 +205,13 @@ __device__ void setup(MlpSmem& s) {
     fence_after();
 }
 
-__device__ void teardown(MlpSmem& s) {
+template <int NCOL = 64, class S>
+__device__ void teardown(S& s) {
     fence_before();
     __syncthreads();
     fence_after();
     if (threadIdx.x < 32)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;\n" ::"r"(s.tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(s.tmem), "r"(NCOL) : "memory");
 }
 
 // One product into the accumulator: `ksteps` MMAs of K = 16 over the A and B tiles (KB core
@@ -231,31 +259,98 @@ __device__ __forceinline__ void stage_inputs(MlpSmem& s, const MlpArgs& m, long 
 }
 
 // ------------------------------------------------------------------ inference
-__global__ void __launch_bounds__(NT) mlp_forward_kernel(const MlpArgs m) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    MlpSmem& s = *reinterpret_cast<MlpSmem*>(smem_raw);
-    load_params(s, m.params, nullptr);
-    setup(s);
-    unsigned phase = 0;
-    const int r = threadIdx.x;
-    const long long ntiles = (m.n + ROWS - 1) / ROWS;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const long long i = t * ROWS + r;
-        float xn[MLP_IN];
-        stage_inputs(s, m, i, r, xn);
-        if (!product<2>(s, s.X, s.W1, phase)) break;
-        float z[MLP_H];
-        read_row(s, z);
+// 256 threads: two sub-tiles of 128 rows (thread = sample row; warps 0-3 sub-tile 0, warps 4-7
+// sub-tile 1), so each MMA round trip serves 256 samples.  Sub-tile h accumulates in TMEM
+// columns 64 h .. 64 h + 63 (128 columns allocated).  The next tile's inputs are loaded while
+// the tensor cores work.
+constexpr int FWD_NT = 256, FWD_SUB = 2, FWD_ROWS = FWD_SUB * ROWS;
+
+struct __align__(1024) MlpFwdSmem {
+    unsigned char X[FWD_SUB][ROWS * MLP_KIN * 2];     // stride ROWS * 2 * 16 bytes (KB = 2)
+    unsigned char H[FWD_SUB][ROWS * MLP_H * 2];       // stride ROWS * 8 * 16 bytes (KB = 8)
+    unsigned char W1[MLP_H * MLP_KIN * 2];
+    unsigned char W2[MLP_H * MLP_H * 2];
+    float b1[MLP_H], b2[MLP_H], w3[MLP_H];
+    float b3;
+    unsigned long long bar;
+    unsigned tmem;
+};
+static_assert(sizeof(((MlpFwdSmem*)0)->X[0]) == ROWS * 2 * 16 && sizeof(((MlpFwdSmem*)0)->H[0]) == ROWS * 8 * 16,
+              "sub-tile strides");
+
+// Both sub-tiles' products (KB core matrices per row group; sub-tile h's A tile at
+// A0 + h * ROWS * KB * 16 bytes), one commit; false on timeout.
+template <int KB>
+__device__ bool product2(MlpFwdSmem& s, const unsigned char* A0, const unsigned char* B, unsigned& phase) {
+    constexpr int ASTRIDE = ROWS * KB * 16;
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (threadIdx.x == 0) {
+        constexpr unsigned LBO = 128, SBO = 128 * KB;
 #pragma unroll
-        for (int k = 0; k < MLP_H; ++k) put_bf16<8>(s.H, r, k, silu(z[k] + s.b1[k]));
-        if (!product<8>(s, s.H, s.W2, phase)) break;
-        read_row(s, z);
+        for (int h = 0; h < FWD_SUB; ++h)
+#pragma unroll
+            for (int ks = 0; ks < KB / 2; ++ks)
+                mma_bf16(s.tmem + MLP_H * h, mdesc(A0 + h * ASTRIDE + ks * 256, LBO, SBO),
+                         mdesc(B + ks * 256, LBO, SBO), ks > 0);
+        mma_commit(&s.bar);
+    }
+    const bool ok = bar_wait(&s.bar, phase);
+    phase ^= 1u;
+    fence_after();
+    if (!ok) atomicExch(&g_mlp_err, 1);
+    return __syncthreads_and(ok);
+}
+
+__device__ __forceinline__ void load_x(const MlpArgs& m, long long i, float x[MLP_IN]) {
+#pragma unroll
+    for (int j = 0; j < MLP_IN; ++j) x[j] = (i < m.n && j < m.norm.nin) ? __ldg(m.x + j * m.ldx + i) : 0.f;
+}
+
+__global__ void __launch_bounds__(FWD_NT) mlp_forward_kernel(const MlpArgs m) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    MlpFwdSmem& s = *reinterpret_cast<MlpFwdSmem*>(smem_raw);
+    load_params(s, m.params, nullptr);
+    setup<FWD_SUB * MLP_H>(s);
+    const int h = threadIdx.x >> 7, r = threadIdx.x & (ROWS - 1);
+    const unsigned taddr = s.tmem + ((unsigned)(r & ~31) << 16) + MLP_H * h;
+    unsigned phase = 0;
+    const long long ntiles = (m.n + FWD_ROWS - 1) / FWD_ROWS;
+    float xr[MLP_IN];
+    load_x(m, (long long)blockIdx.x * FWD_ROWS + threadIdx.x, xr);
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long i = t * FWD_ROWS + threadIdx.x;
+        float xs[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            xs[j] = j < MLP_IN && j < m.norm.nin ? (xr[j] - m.norm.mu[j]) * m.norm.inv_sigma[j] : 0.f;
+        put8_bf16<2>(s.X[h], r, 0, xs);
+        put8_bf16<2>(s.X[h], r, 8, xs + 8);
+        load_x(m, i + (long long)gridDim.x * FWD_ROWS, xr);      // next tile, in flight meanwhile
+        if (!product2<2>(s, s.X[0], s.W1, phase)) break;
+        float z[MLP_H];
+#pragma unroll
+        for (int c = 0; c < MLP_H; c += 16) tmem_ld16(taddr + c, z + c);
+        tmem_ld_wait();
+#pragma unroll
+        for (int c = 0; c < MLP_H; c += 8) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = silu(z[c + q] + s.b1[c + q]);
+            put8_bf16<8>(s.H[h], r, c, v);
+        }
+        if (!product2<8>(s, s.H[0], s.W2, phase)) break;
+#pragma unroll
+        for (int c = 0; c < MLP_H; c += 16) tmem_ld16(taddr + c, z + c);
+        tmem_ld_wait();
         float y = s.b3;
 #pragma unroll
         for (int k = 0; k < MLP_H; ++k) y = fmaf(s.w3[k], silu(z[k] + s.b2[k]), y);
         if (i < m.n) m.y[i] = y;
     }
-    teardown(s);
+    teardown<FWD_SUB * MLP_H>(s);
 }
 
 // ------------------------------------------------------------------ training
@@ -382,11 +477,6 @@ __global__ void mlp_adam_kernel(float* params, float* am, float* av, const float
     }
 }
 
-int mlp_grid(long long n, int per_sm) {
-    const long long tiles = (n + ROWS - 1) / ROWS;
-    const long long g = tiles < 152LL * per_sm ? tiles : 152LL * per_sm;
-    return (int)(g < 1 ? 1 : g);
-}
 
 }  // namespace
 
@@ -399,13 +489,15 @@ cudaError_t launch_mlp_forward(const float* params, const MlpNorm& norm, const f
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(MlpSmem));
+                                             (int)sizeof(MlpFwdSmem));
         if (e != cudaSuccess) return e;
         attr = true;
     }
     if (n <= 0) return cudaSuccess;
     MlpArgs m{params, norm, x, ldx, n, nullptr, y, nullptr};
-    mlp_forward_kernel<<<mlp_grid(n, 4), NT, sizeof(MlpSmem), s>>>(m);
+    const long long tiles = (n + FWD_ROWS - 1) / FWD_ROWS;
+    const int grid = (int)(tiles < 152LL * 4 ? tiles : 152LL * 4);
+    mlp_forward_kernel<<<grid, FWD_NT, sizeof(MlpFwdSmem), s>>>(m);
     return cudaGetLastError();
 }
 

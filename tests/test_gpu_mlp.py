@@ -1,10 +1,14 @@
 """Closure network on the tensor cores (pic_mlp_*) against the FP64 oracle network
 (oracle.mlp) with the same bfloat16 roundings of weights and matrix inputs.
 
-Tolerances: the two sides differ only in FP32 accumulation order, the fast exponential of SiLU
-and bfloat16 ties at rounding boundaries of the hidden activations, so the outputs agree to
-~1e-3 of their scale (SURVEY's bar is 1e-2); gradients (recovered from the first Adam moment,
-m = (1 - beta1) g at t = 1) to cosine >= 0.999 and 2e-2 relative.
+Tolerances: the two sides differ in FP32 accumulation order and in the sigmoid, which the
+kernels take from tanh.approx (relative error ~2^-11).  That error can move a hidden activation
+across a bfloat16 rounding boundary; one such flip changes the output by about
+|w3| |W2| 2^-8 h1, ~1e-3 of the output scale, in a few samples.  So, relative to the output
+scale: median error <= 1e-5 and mean <= 2e-4 (without flips the error is ~1e-7; any real error
+in the products or the layout breaks both), maximum <= 5e-3 (the bar for the forward pass is
+1e-2); gradients (recovered from the first Adam moment, m = (1 - beta1) g
+at t = 1) to cosine >= 0.999 and 2e-2 relative.
 """
 import numpy as np
 import pytest
@@ -30,6 +34,14 @@ def _data(n, seed=4, nin=9):
     return x, t.astype(np.float32).astype(np.float64)
 
 
+def _close(y, yo):
+    scale = np.abs(yo).max() + 1e-6
+    err = np.abs(y - yo) / scale
+    assert np.median(err) <= 1e-5, np.median(err)
+    assert err.mean() <= 2e-4, err.mean()
+    assert err.max() <= 5e-3, err.max()
+
+
 def _net(pic, p, x, nin=9):
     from oracle import mlp
     mu, sd = mlp.feature_norm(x[:, :nin])
@@ -51,8 +63,7 @@ def test_forward_matches_oracle(pic, n):
     net, mu, sd = _net(pic, p, x)
     y = net.forward(_dev(x.T)).cpu().numpy().astype(np.float64)
     yo, _ = mlp.forward(p, x, mu, sd, bf16_path=True)
-    scale = np.abs(yo).max() + 1e-6
-    assert np.abs(y - yo).max() <= 1e-3 * scale, np.abs(y - yo).max() / scale
+    _close(y, yo)
 
 
 def test_forward_eight_inputs(pic):
@@ -64,7 +75,7 @@ def test_forward_eight_inputs(pic):
     xg[:, 8] = 123.0              # ignored when nin = 8
     y = net.forward(_dev(xg.T)).cpu().numpy().astype(np.float64)
     yo, _ = mlp.forward(p, x, mu, sd, bf16_path=True)
-    assert np.abs(y - yo).max() <= 1e-3 * (np.abs(yo).max() + 1e-6)
+    _close(y, yo)
 
 
 def test_gradient_and_loss_match_oracle(pic):
@@ -118,5 +129,5 @@ def test_forward_on_recorded_moments(pic):
     net = pic.ClosureNet(p, mu, sd)
     y = net.forward(feats).cpu().numpy().astype(np.float64)
     yo, _ = mlp.forward(p, xf, mu, sd, bf16_path=True)
-    assert np.abs(y - yo).max() <= 1e-3 * (np.abs(yo).max() + 1e-6)
+    _close(y, yo)
     eng.close()
