@@ -45,6 +45,14 @@ METRIC = "particle-steps/s"
 BYTES_PER_PARTICLE_2D = 48
 BYTES_PER_PARTICLE_3D = 56
 BYTES_PER_CELL = 64
+# DRAM bytes per particle of the push kernels (dram__bytes_read.sum + dram__bytes_write.sum of
+# one ncu capture of a small case, divided by its particles; the capture commands are in the
+# profile summaries named here).  They describe the kernels as captured: re-capture after
+# changing a kernel.
+NCU_TRAFFIC_PER_PARTICLE = {
+    2: (58.56, "profiles/push2d_warm_beam_krook_2d.md (256x256, 128 ppc)"),
+    3: (149.78, "profiles/push3d_hot_beam_3d.md (128x128x64, 16 ppc)"),
+}
 
 
 def _peaks():
@@ -223,14 +231,19 @@ def _max_over_ranks(dist, vals):
     return [float(x) for x in t]
 
 
-def _roofline(alg_bytes, push_n, push_ms):
+def _roofline(alg_bytes, push_n, push_ms, ndim=None, npart=None):
     peak, peak_kind = _peaks()
     push_avg_s = push_ms / max(1, push_n) / 1e3
     achieved = alg_bytes / push_avg_s / 1e9
-    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "push_deposit",
-            "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
-            "mean_launch_ms": push_avg_s * 1e3}
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "traffic": None, "kernel": "push_deposit",
+           "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
+           "mean_launch_ms": push_avg_s * 1e3}
+    if ndim in NCU_TRAFFIC_PER_PARTICLE and npart:
+        per, src = NCU_TRAFFIC_PER_PARTICLE[ndim]
+        out["traffic"] = per * npart
+        out["traffic_source"] = f"ncu DRAM bytes of a small case scaled by particles: {src}"
+    return out
 
 
 def _timed_steps(eng, steps, warmup, barrier, local_rank):
@@ -313,7 +326,7 @@ def run_ours(args, rank, world, local_rank):
                        "particles_per_gpu": npart, "sort_interval": args.sort,
                        "diag_interval": args.diag, "parallelism": f"replicas{world}",
                        "l2": f"inputs larger than L2 (particles {npart * (bpp // 2) / 1e9:.1f} GB/GPU), no flush"},
-            "roofline": _roofline(alg_bytes, *delta["push_deposit"]),
+            "roofline": _roofline(alg_bytes, *delta["push_deposit"], ndim=wl.ndim, npart=npart),
             "phase_ms_per_step": phase,
             "e2e": {"value": world * npart * args.steps / e2e_max, "unit": METRIC,
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
@@ -569,7 +582,9 @@ def run_closure(args, rank, world, local_rank):
                        "recorder_state": f"hot_beam_3d_{wl.nx}x{wl.ny}x{wl.nz}_ppc{args.rec_ppc}",
                        "l2": "features 37.7 MB < L2: inference inputs may be L2-resident between calls"},
             "roofline": {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
-                         "frac": tflops / bf16_peak, "traffic": None, "kernel": "mlp_forward",
+                         "frac": tflops / bf16_peak, "traffic": 37.8e6 * n / (1 << 20),
+                         "traffic_source": "ncu DRAM bytes, profiles/mlp_forward_closure.md",
+                         "kernel": "mlp_forward",
                          "peak_kind": "measured" if "bf16_tflops" in peaks else "fallback",
                          "flops_per_launch": flops, "mean_launch_ms": inf_ms},
             "recorder": {"ms_per_snapshot": rec_ms, "coarse_cells": nc, "particles": npart,
