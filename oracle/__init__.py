@@ -48,14 +48,15 @@ class _Grid(ctypes.Structure):
                 ("nz", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
                 ("dz", ctypes.c_double), ("dt", ctypes.c_double),
                 ("Ex", P), ("Ey", P), ("Ez", P), ("Bx", P), ("By", P), ("Bz", P),
-                ("Jx", P), ("Jy", P), ("Jz", P)]
+                ("Jx", P), ("Jy", P), ("Jz", P), ("step", ctypes.c_int64)]
 
 
 class _Species(ctypes.Structure):
     _fields_ = [("q", ctypes.c_double), ("m", ctypes.c_double), ("w", ctypes.c_double),
                 ("nu", ctypes.c_double), ("n", ctypes.c_int64),
                 ("X", P), ("Y", P), ("Z", P), ("ux", P), ("uy", P), ("uz", P), ("ubar", P),
-                ("nu_cell", P)]
+                ("nu_cell", P), ("nu_coll", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("index", ctypes.c_int32)]
 
 
 MAX_SPECIES = 4
@@ -92,6 +93,11 @@ def lib():
         _lib.orc_deposit_move.restype = None
         _lib.orc_gather_many.argtypes = [ctypes.POINTER(_Grid), ctypes.c_int64, P, P, P, P]
         _lib.orc_gather_many.restype = None
+        U32 = ctypes.POINTER(ctypes.c_uint32)
+        _lib.orc_philox4x32_10.argtypes = [U32, U32, U32]
+        _lib.orc_philox4x32_10.restype = None
+        _lib.orc_collide_ion.argtypes = [P, ctypes.c_double, U32]
+        _lib.orc_collide_ion.restype = None
     return _lib
 
 
@@ -111,6 +117,9 @@ class Species:
         self.ux, self.uy, self.uz = f(ux), f(uy), f(uz)
         self.ubar = np.zeros(3 * ncell) if nu > 0 else None
         self.nu_cell = None
+        self.nu_coll = 0.0
+        self.seed = 0
+        self.index = 0
 
     @property
     def n(self):
@@ -119,7 +128,7 @@ class Species:
     def cstruct(self):
         return _Species(self.q, self.m, self.w, self.nu, self.n, _ptr(self.X), _ptr(self.Y),
                         _ptr(self.Z), _ptr(self.ux), _ptr(self.uy), _ptr(self.uz),
-                        _ptr(self.ubar), _ptr(self.nu_cell))
+                        _ptr(self.ubar), _ptr(self.nu_cell), self.nu_coll, self.seed, self.index)
 
     @property
     def u(self):
@@ -152,7 +161,7 @@ class Simulation:
         E, B, J = self.E, self.B, self.J
         return _Grid(self.ndim, self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.dt,
                      _ptr(E[0]), _ptr(E[1]), _ptr(E[2]), _ptr(B[0]), _ptr(B[1]), _ptr(B[2]),
-                     _ptr(J[0]), _ptr(J[1]), _ptr(J[2]))
+                     _ptr(J[0]), _ptr(J[1]), _ptr(J[2]), self.step_index)
 
     def add_species(self, q, m, w, nu, X, Y, Z, ux, uy, uz, name=""):
         s = Species(q, m, w, nu, X, Y, Z if self.ndim == 3 else None, ux, uy, uz, self.ncell, name)
@@ -163,6 +172,14 @@ class Simulation:
             if lib().orc_moments(ctypes.byref(g), ctypes.byref(cs)) != 0:
                 raise MemoryError("orc_moments")
         return s
+
+    def set_collisions(self, s, nu, seed):
+        """Binary electron-ion collisions of species s at momentum-transfer rate nu, draws keyed
+        by `seed` (64-bit), the particle index and the step (Takizuka & Abe, immobile ions)."""
+        sp = self.species[s]
+        sp.nu_coll = float(nu)
+        sp.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        sp.index = s
 
     def set_nu_cell(self, s, nu_cell):
         """Per-cell Krook rates for species s (closure-driven drag; None restores the scalar
@@ -203,6 +220,7 @@ class Simulation:
         arr = (_Species * len(self.species))(*[s.cstruct() for s in self.species])
         for _ in range(n):
             d = _Diag()
+            g.step = self.step_index          # keys this step's collision draws
             rc = L.orc_step(ctypes.byref(g), arr, len(self.species), ctypes.byref(d) if record else None)
             if rc != 0:
                 raise RuntimeError(f"orc_step failed ({rc})")
@@ -272,4 +290,21 @@ def boris(qm, dt, EB, u):
     e = np.ascontiguousarray(EB, dtype=np.float64)
     uu = np.ascontiguousarray(u, dtype=np.float64).copy()
     lib().orc_boris(qm, dt, _ptr(e), _ptr(uu))
+    return uu
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of four 32-bit counter words and two key words (oracle C)."""
+    c = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return list(o)
+
+
+def collide_ion(u, sigma, r):
+    """One binary electron-ion collision of momentum u (3,) with draws r (4 uint32)."""
+    uu = np.ascontiguousarray(u, dtype=np.float64).copy()
+    rr = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in r])
+    lib().orc_collide_ion(_ptr(uu), float(sigma), rr)
     return uu

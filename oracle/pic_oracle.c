@@ -47,6 +47,7 @@ typedef struct orc_grid {
     double *Ex, *Ey, *Ez; /* nx*ny*nz each */
     double *Bx, *By, *Bz;
     double *Jx, *Jy, *Jz; /* current density of the last step, J^{n+1/2} */
+    int64_t step;         /* steps completed: keys the binary-collision draws of the next step */
 } orc_grid;
 
 typedef struct orc_species {
@@ -58,6 +59,9 @@ typedef struct orc_species {
     double *ubar;     /* 3*ncell cell-mean momentum (NGP) used by the drag; NULL if no drag */
     double *nu_cell;  /* ncell Krook rates replacing nu, looked up at the particle's cell at time
                          n (the closure-driven drag); negative rates act as 0; NULL = nu */
+    double nu_coll;   /* binary electron-ion collision rate (momentum transfer); 0 = none */
+    uint64_t seed;    /* key of the collision draws */
+    int32_t index;    /* species index in the draws' counter */
 } orc_species;
 
 #define ORC_MAX_SPECIES 4
@@ -355,18 +359,82 @@ static void field_energy(const orc_grid *g, orc_diag *d) {
     }
 }
 
+/* ---------------------------------------------------------------- binary collisions */
+
+/* Philox4x32-10, the counter-based generator of Salmon, Moraes, Dror & Shaw ("Parallel random
+ * numbers: as easy as 1, 2, 3", SC'11): ten rounds of
+ *   (hi0, lo0) = M0 * c0,  (hi1, lo1) = M1 * c2,  c = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0)
+ * with M0 = 0xD2511F53, M1 = 0xCD9E8D57 and the key raised by the Weyl constants
+ * (0x9E3779B9, 0xBB67AE85) between rounds. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c0 = hi1 ^ c1 ^ k0; c1 = lo1; c2 = hi0 ^ c3 ^ k1; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* The draws of particle `id` of species `sp` at step `step`: counter (id, step lo, step hi, sp),
+ * key = the seed's two halves. */
+static void collision_draws(uint64_t seed, int64_t id, int64_t step, int32_t sp, uint32_t r[4]) {
+    const uint32_t ctr[4] = {(uint32_t)id, (uint32_t)((uint64_t)step & 0xffffffffu),
+                             (uint32_t)((uint64_t)step >> 32), (uint32_t)sp};
+    const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    orc_philox4x32_10(ctr, key, r);
+}
+
+static double unit_open(uint32_t x) { return ((double)x + 0.5) / 4294967296.0; }
+
+/* Binary collision of an electron with an immobile ion over one step (Takizuka & Abe, J. Comput.
+ * Phys. 25, 205 (1977), with an infinitely heavy partner so that the relative velocity is the
+ * electron's own): u is turned by the scattering angle theta, tan(theta / 2) = delta ~
+ * N(0, sigma^2), about a random azimuth phi ~ U[0, 2 pi); |u| is unchanged.  The mean momentum
+ * then relaxes at <1 - cos theta> / dt = 2 sigma^2 / dt per step for small sigma, so
+ * sigma^2 = nu dt / 2 gives the momentum-transfer rate nu (the reading of the collision rate).
+ * r: four 32-bit draws (r0, r1 -> delta by Box-Muller, r2 -> phi). */
+void orc_collide_ion(double u[3], double sigma, const uint32_t r[4]) {
+    const double pi = 3.14159265358979323846;
+    double delta = sigma * sqrt(-2.0 * log(unit_open(r[0]))) * cos(2.0 * pi * unit_open(r[1]));
+    double phi = 2.0 * pi * unit_open(r[2]);
+    double sn = 2.0 * delta / (1.0 + delta * delta), omc = 2.0 * delta * delta / (1.0 + delta * delta);
+    double cp = cos(phi), sp = sin(phi);
+    double uperp = sqrt(u[0] * u[0] + u[1] * u[1]);
+    double umag = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    double d[3];
+    if (uperp > 0.0) {
+        d[0] = (u[0] * u[2] / uperp) * sn * cp - (u[1] * umag / uperp) * sn * sp - u[0] * omc;
+        d[1] = (u[1] * u[2] / uperp) * sn * cp + (u[0] * umag / uperp) * sn * sp - u[1] * omc;
+        d[2] = -uperp * sn * cp - u[2] * omc;
+    } else {
+        d[0] = umag * sn * cp;
+        d[1] = umag * sn * sp;
+        d[2] = -u[2] * omc;
+    }
+    for (int a = 0; a < 3; a++) u[a] += d[a];
+}
+
 /* ---------------------------------------------------------------- one particle */
 
 /* Advance one particle by one step: gather, Boris, drag, move.  Returns the unwrapped new
  * position in P1 and writes u.  ubar_c is the mean momentum of the particle's cell (NULL
  * for no drag), dragf = 1 - exp(-nu dt). */
 static void push_one(const orc_grid *g, double qm, const double P0[3], double u[3],
-                     const double *ubar_c, double dragf, double P1[3]) {
+                     const double *ubar_c, double dragf, const orc_species *coll, int64_t id,
+                     double P1[3]) {
     double EB[6];
     orc_gather(g, P0[0], P0[1], P0[2], EB);
     orc_boris(qm, g->dt, EB, u);
     if (ubar_c && dragf != 0.0)
         for (int a = 0; a < 3; a++) u[a] -= dragf * ubar_c[a];
+    if (coll && coll->nu_coll > 0.0) {
+        uint32_t r[4];
+        collision_draws(coll->seed, id, g->step, coll->index, r);
+        orc_collide_ion(u, sqrt(0.5 * coll->nu_coll * g->dt), r);
+    }
     double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     P1[0] = P0[0] + g->dt * u[0] / gam / g->dx;
     P1[1] = P0[1] + g->dt * u[1] / gam / g->dy;
@@ -377,7 +445,7 @@ static void push_one(const orc_grid *g, double qm, const double P0[3], double u[
 void orc_push_particle(const orc_grid *g, double qm, double nu, double *X, double *Y, double *Z,
                        double u[3], const double ubar_c[3]) {
     double P0[3] = {*X, *Y, Z ? *Z : 0.0}, P1[3];
-    push_one(g, qm, P0, u, ubar_c, ubar_c ? 1.0 - exp(-nu * g->dt) : 0.0, P1);
+    push_one(g, qm, P0, u, ubar_c, ubar_c ? 1.0 - exp(-nu * g->dt) : 0.0, NULL, 0, P1);
     *X = wrap_pos(P1[0], g->nx);
     *Y = wrap_pos(P1[1], g->ny);
     if (Z && g->ndim == 3) *Z = wrap_pos(P1[2], g->nz);
@@ -418,7 +486,7 @@ int orc_step(orc_grid *g, orc_species *sp, int nsp, orc_diag *d) {
                 double r = s->nu_cell[ngp_cell(g, s, p)];
                 df = r > 0.0 ? 1.0 - exp(-r * g->dt) : 0.0;
             }
-            push_one(g, qm, P0, u, ub, df, P1);
+            push_one(g, qm, P0, u, ub, df, s, p, P1);
             double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
             if (g->ndim == 2) deposit_2d(g, qw, P0[0], P0[1], P1[0], P1[1], u[2] / gam);
             else deposit_3d(g, qw, P0, P1);
