@@ -213,6 +213,16 @@ int pic_get_stats(pic_ctx* ctx, pic_stats* out);
  * Synchronises the context's stream; nu may be freed on return. */
 int pic_set_drag_map(pic_ctx* ctx, int run, int s, const float* nu, int32_t bx, int32_t by);
 
+/* Binary electron-ion collisions of species s in run `run` (the paper's collision model; its
+ * scheme is not given there): every step, after the Boris push and any Krook drag, each particle's
+ * momentum turns by a scattering angle theta with tan(theta / 2) ~ N(0, nu dt / 2) about a
+ * uniform azimuth (Takizuka & Abe, J. Comput. Phys. 25, 205 (1977), with an immobile ion as the
+ * partner), which keeps |u| and relaxes the mean momentum at the rate nu to first order in
+ * nu dt.  The draws of particle p at step n are Philox4x32-10 (Salmon et al., SC'11) of the
+ * counter (id_p, n, s) under the 64-bit key `seed`, so the context must carry particle ids
+ * (track_ids); PIC_EINVAL otherwise.  nu = 0 switches the collisions off.  Synchronises. */
+int pic_set_collisions(pic_ctx* ctx, int run, int s, double nu, uint64_t seed);
+
 /* ---------------------------------------------------------------- moment recorder
  * Coarse-grained state of run `run` at the current step: the inputs and the label parts of a
  * learned collision closure.  The paper's conclusion conjectures that the collisional friction on

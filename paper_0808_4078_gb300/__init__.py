@@ -113,6 +113,7 @@ _SIGNATURES = {
                                           _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP, _VP, ctypes.c_size_t, _VP]),
     "pic_mlp_status": (ctypes.c_int, [ctypes.c_int]),
     "pic_set_drag_map": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int32, ctypes.c_int32]),
+    "pic_set_collisions": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64]),
     "pic_launch_count": (ctypes.c_int64, [_VP]),
     "pic_step_count": (ctypes.c_int64, [_VP]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
@@ -315,6 +316,10 @@ class Engine:
         # the scratch tensor is released when this returns: let the stream finish with it first
         self.sync()
         return out
+
+    def set_collisions(self, s, nu, seed, run=0):
+        """Binary electron-ion collisions of species s at rate nu (pic_set_collisions)."""
+        _check(lib().pic_set_collisions(self._ctx, run, s, float(nu), int(seed) & 0xFFFFFFFFFFFFFFFF), self._ctx)
 
     def set_drag_map(self, s, nu, bx=1, by=1, run=0):
         """Per-coarse-cell Krook rates (CUDA float tensor of (nx/bx)(ny/by) values) for species s,

@@ -976,6 +976,26 @@ extern "C" int pic_set_drag_map(pic_ctx* ctx, int run, int s, const float* nu, i
     return device_flags(ctx);
 }
 
+extern "C" int pic_set_collisions(pic_ctx* ctx, int run, int s, double nu, uint64_t seed) {
+    if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    int rc = check_run(ctx, run);
+    if (rc) return rc;
+    if (s < 0 || s >= ctx->cfg.nspecies) return fail(ctx, PIC_EINVAL, "species %d out of range", s);
+    if (!(std::isfinite(nu) && nu >= 0)) return fail(ctx, PIC_EINVAL, "collision rate must be finite and >= 0");
+    if (nu > 0 && !ctx->cfg.track_ids)
+        return fail(ctx, PIC_EINVAL, "binary collisions key their draws by particle id: set track_ids");
+    SpeciesParams& P = ctx->runs[run].sp[s];
+    if (!P.active) return fail(ctx, PIC_ESTATE, "species %d of run %d is not loaded", s, run);
+    P.coll = nu > 0 ? 1 : 0;
+    P.coll_sigma = (float)std::sqrt(0.5 * nu * ctx->cfg.dt);
+    P.seed_lo = (unsigned)(seed & 0xffffffffu);
+    P.seed_hi = (unsigned)(seed >> 32);
+    rc = upload_runs(ctx);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PIC_OK;
+}
+
 // ---------------------------------------------------------------- closure network
 namespace {
 int mlp_norm(const pic_mlp_norm* in, MlpNorm* out) {

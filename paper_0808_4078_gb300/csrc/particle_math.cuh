@@ -140,4 +140,67 @@ __device__ __forceinline__ void kin_add(long long kacc[5], int s, float w, float
     kacc[4] += __float2ll_rn(w * mz * sc);
 }
 
+// ------------------------------------------------------------------ binary collisions
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of
+// (hi0, lo0) = M0 c0, (hi1, lo1) = M1 c2, c = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0), the key
+// raised by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// (x + 1/2) 2^-32 in FP32: a uniform draw in (0, 1].
+__device__ __forceinline__ float unit_open(unsigned x) {
+    return __fmaf_rn(__uint2float_rn(x), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+}
+
+// One binary collision of an electron with an immobile ion over the step (Takizuka & Abe 1977
+// with an infinitely heavy partner): u turns by theta, tan(theta / 2) = delta ~ N(0, sigma^2),
+// about a uniform azimuth; |u| is kept.  The draws of particle `id` of species `s` at step
+// `step` are Philox4x32-10 of counter (id, step lo, step hi, s) under the key (seed_lo,
+// seed_hi): r0, r1 give delta (Box-Muller), r2 the azimuth.  Every rounding is explicit.
+__device__ __forceinline__ void collide_ion(float& ux, float& uy, float& uz, const SpeciesParams& P, int s,
+                                            unsigned id, long long step) {
+    const uint4 r = philox4x32_10(make_uint4(id, (unsigned)((unsigned long long)step & 0xffffffffu),
+                                             (unsigned)((unsigned long long)step >> 32), (unsigned)s),
+                                  P.seed_lo, P.seed_hi);
+    const float twopi = 6.283185307179586f;
+    // ln U for U = (r + 1/2) 2^-32: for U >= 1/2 through log1p of the exact complement
+    // (2^32 - r - 1/2) 2^-32, which FP32 holds without the 2^-24 quantisation of U near 1
+    const float lnu = r.x < 0x80000000u ? logf(unit_open(r.x)) : log1pf(-unit_open(~r.x));
+    const float rad = sqrtf(__fmul_rn(-2.f, lnu));
+    // accurate sine and cosine (their large-argument path is never taken for angles in (0, 2 pi])
+    const float delta = __fmul_rn(__fmul_rn(P.coll_sigma, rad), cosf(__fmul_rn(twopi, unit_open(r.y))));
+    const float phi = __fmul_rn(twopi, unit_open(r.z));
+    const float sp = sinf(phi), cp = cosf(phi);
+    const float d2 = __fmul_rn(delta, delta);
+    const float inv = __fdiv_rn(1.f, __fadd_rn(1.f, d2));
+    const float sn = __fmul_rn(__fmul_rn(2.f, delta), inv);
+    const float omc = __fmul_rn(__fmul_rn(2.f, d2), inv);
+    const float up2 = __fmaf_rn(uy, uy, __fmul_rn(ux, ux));
+    const float uperp = sqrtf(up2);
+    const float umag = sqrtf(__fmaf_rn(uz, uz, up2));
+    float dx, dy, dz;
+    if (uperp > 0.f) {
+        const float a = __fdiv_rn(__fmul_rn(sn, cp), uperp);      // sin theta cos phi / u_perp
+        const float b = __fdiv_rn(__fmul_rn(sn, sp), uperp);      // sin theta sin phi / u_perp
+        dx = __fsub_rn(__fsub_rn(__fmul_rn(__fmul_rn(ux, uz), a), __fmul_rn(__fmul_rn(uy, umag), b)), __fmul_rn(ux, omc));
+        dy = __fsub_rn(__fadd_rn(__fmul_rn(__fmul_rn(uy, uz), a), __fmul_rn(__fmul_rn(ux, umag), b)), __fmul_rn(uy, omc));
+        dz = __fsub_rn(__fmul_rn(-uperp, __fmul_rn(sn, cp)), __fmul_rn(uz, omc));
+    } else {
+        dx = __fmul_rn(umag, __fmul_rn(sn, cp));
+        dy = __fmul_rn(umag, __fmul_rn(sn, sp));
+        dz = __fmul_rn(-uz, omc);
+    }
+    ux = __fadd_rn(ux, dx);
+    uy = __fadd_rn(uy, dy);
+    uz = __fadd_rn(uz, dz);
+}
+
 }  // namespace pic

@@ -32,6 +32,9 @@ struct SpeciesParams {
     float w;            // weight (density per macro-particle)
     int drag;           // accumulate cell moments and apply the drag
     int active;         // species loaded
+    int coll;           // binary electron-ion collisions on
+    float coll_sigma;   // sqrt(nu_coll dt / 2): standard deviation of tan(theta / 2)
+    unsigned seed_lo, seed_hi;   // key of the collision draws
 };
 
 struct RunDev {

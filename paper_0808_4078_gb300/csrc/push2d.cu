@@ -186,7 +186,8 @@ struct Pushed {
 template <class A>
 __device__ __forceinline__ Pushed push_one(const A& F, const SpeciesParams& P, const RunConst& K,
                                            float ox, float oy, float ux, float uy, float uz,
-                                           float b0, float b1, float b2, float df) {
+                                           float b0, float b1, float b2, float df,
+                                           int s, unsigned id, long long step) {
     Pushed r;
     const W3 wx = weights(ox), wy = weights(oy);
     float EB[6];
@@ -197,6 +198,7 @@ __device__ __forceinline__ Pushed push_one(const A& F, const SpeciesParams& P, c
         uy = __fmaf_rn(-df, b1, uy);
         uz = __fmaf_rn(-df, b2, uz);
     }
+    if (P.coll) collide_ion(ux, uy, uz, P, s, id, step);
     const float ig = rsqrtf(__fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmaf_rn(ux, ux, 1.f))));
     const float rx = __fmaf_rn(__fmul_rn(ux, ig), K.dtdx, ox);
     const float ry = __fmaf_rn(__fmul_rn(uy, ig), K.dtdy, oy);
@@ -263,7 +265,7 @@ __device__ __forceinline__ void put_imm(const Slots& D, int cap, int cap_stay, i
 // Full step of up to 32 queued particles (one per lane) of the tile: shared-memory gather and
 // deposit, then rebinning into the destination cell of the other buffer.
 __device__ __forceinline__ void drain(Smem& sm, const Args& a, const RunConst& K, int par, int k,
-                                      int lane, int warp, int x0, int y0, bool diag,
+                                      int lane, int warp, int x0, int y0, bool diag, long long step,
                                       long long kacc[5]) {
     if (lane >= k) return;
     const int nx = K.nx, ny = K.ny;
@@ -284,7 +286,7 @@ __device__ __forceinline__ void drain(Smem& sm, const Args& a, const RunConst& K
     float b0 = 0.f, b1 = 0.f, b2 = 0.f;
     if (P.drag) { b0 = sm.ub[0][n0]; b1 = sm.ub[1][n0]; b2 = sm.ub[2][n0]; }
     const float df = P.drag ? drag_of(K, P, s, g - K.cell_off) : 0.f;
-    const Pushed r = push_one(SharedFields{&sm, n0}, P, K, ox, oy, u0x, u0y, u0z, b0, b1, b2, df);
+    const Pushed r = push_one(SharedFields{&sm, n0}, P, K, ox, oy, u0x, u0y, u0z, b0, b1, b2, df, s, id, step);
     if (r.bad) {
         // keep the particle where it was, unmoved; the sticky flag fails the run
         atomicOr(&a.ctl->err, ERR_BADPART);
@@ -503,7 +505,7 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
             id = __float_as_int(sm.stg[warp][st][5][lane]);
         }
         const float df = P.drag ? drag_of(K, P, s, g - K.cell_off) : 0.f;
-        const Pushed r = push_one(cc, P, K, ox, oy, ux, uy, uz, ub0, ub1, ub2, df);
+        const Pushed r = push_one(cc, P, K, ox, oy, ux, uy, uz, ub0, ub1, ub2, df, s, (unsigned)id, step);
         const bool small_u = !P.drag || (fabsf(r.ux) < 4.f && fabsf(r.uy) < 4.f && fabsf(r.uz) < 4.f);
         const bool stay = act && !r.bad && r.sx == 0 && r.sy == 0 && small_u;
         if (stay) {
@@ -542,7 +544,7 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
         qn += __popc(dm);
         __syncwarp();
         if (qn >= 32) {
-            drain(sm, a, K, par, 32, lane, warp, x0, y0, diag, kacc);
+            drain(sm, a, K, par, 32, lane, warp, x0, y0, diag, step, kacc);
             __syncwarp();
             const int rest = qn - 32;
             const unsigned moved = lane < rest ? sm.q[warp][32 + lane] : 0u;
@@ -561,7 +563,7 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
     if (nchunk) flush_acc(sm, acc, n0, lane);
     if (seg_s >= 0 && lane == 0) a.slot[seg_s][par ^ 1].count[seg_g] = wpos;
     cp_async_wait<0>();
-    if (qn > 0) drain(sm, a, K, par, qn, lane, warp, x0, y0, diag, kacc);
+    if (qn > 0) drain(sm, a, K, par, qn, lane, warp, x0, y0, diag, step, kacc);
     __syncwarp();
 
     if (diag) {
@@ -633,7 +635,8 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
             if (P.drag) { b0 = Rp->ubar[0][lc]; b1 = Rp->ubar[1][lc]; b2 = Rp->ubar[2][lc]; }
             const RunConst K = run_const(Rp);
             const float df = P.drag ? drag_of(K, P, s, lc) : 0.f;
-            const Pushed r = push_one(GlobalFields{Rp, cx, cy}, P, K, ox, oy, u0x, u0y, u0z, b0, b1, b2, df);
+            const Pushed r = push_one(GlobalFields{Rp, cx, cy}, P, K, ox, oy, u0x, u0y, u0z, b0, b1, b2, df, s,
+                                      (unsigned)id, step);
             if (r.bad) {
                 atomicOr(&a.ctl->err, ERR_BADPART);
                 put_imm(D, cap, cst, a.spill_cap[s], g, ox, oy, u0x, u0y, u0z, id, &a.ctl->err);

@@ -133,7 +133,8 @@ struct Pushed3 {
 template <class A>
 __device__ __forceinline__ Pushed3 push3_one(const A& F, const SpeciesParams& P, const RunConst& K,
                                              const float o[3], float ux, float uy, float uz,
-                                             float b0, float b1, float b2, float df) {
+                                             float b0, float b1, float b2, float df, int s, unsigned id,
+                                             long long step) {
     Pushed3 r;
     const AxisW wx = axis_weights(o[0]), wy = axis_weights(o[1]), wz = axis_weights(o[2]);
     float EB[6];
@@ -144,6 +145,7 @@ __device__ __forceinline__ Pushed3 push3_one(const A& F, const SpeciesParams& P,
         uy = __fmaf_rn(-df, b1, uy);
         uz = __fmaf_rn(-df, b2, uz);
     }
+    if (P.coll) collide_ion(ux, uy, uz, P, s, id, step);
     const float ig = rsqrtf(__fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmaf_rn(ux, ux, 1.f))));
     const float rx = __fmaf_rn(__fmul_rn(ux, ig), K.dtdx, o[0]);
     const float ry = __fmaf_rn(__fmul_rn(uy, ig), K.dtdy, o[1]);
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
             const long long g = cbase + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
             const float df = P.drag ? drag_of(K, P, s, g - cbase) : 0.f;
             const Pushed3 res = push3_one(SharedFields3{&sm, n0}, P, K, po[r], pu[r][0], pu[r][1], pu[r][2],
-                                          b0v, b1v, b2v, df);
+                                          b0v, b1v, b2v, df, s, (unsigned)pid[r], step);
             if (res.bad) {
                 // keep the particle where it was, unmoved; the sticky flag fails the run
                 atomicOr(&a.ctl->err, ERR_BADPART);
@@ -532,7 +534,8 @@ __global__ void __launch_bounds__(NT) spill3d_kernel(const Args a) {
             if (P.drag) { b0 = Rp->ubar[0][lc]; b1 = Rp->ubar[1][lc]; b2 = Rp->ubar[2][lc]; }
             const RunConst K = run_const(Rp);
             const float df = P.drag ? drag_of(K, P, s, lc) : 0.f;
-            const Pushed3 r = push3_one(GlobalFields3{Rp, cx, cy, cz}, P, K, o, u0x, u0y, u0z, b0, b1, b2, df);
+            const Pushed3 r = push3_one(GlobalFields3{Rp, cx, cy, cz}, P, K, o, u0x, u0y, u0z, b0, b1, b2, df, s,
+                                        (unsigned)id, step);
             if (r.bad) {
                 atomicOr(&a.ctl->err, ERR_BADPART);
                 put_imm3(D, cap, cst, a.spill_cap[s], g, o, u0x, u0y, u0z, id, &a.ctl->err);
