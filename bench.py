@@ -411,6 +411,15 @@ def run_scan(args, rank, world, local_rank):
     del eng
     torch.cuda.empty_cache()
 
+    # theory line: Eq. (12) growth rate per run, c_s^2 = 3 T_perp / gamma_b^2 (transverse velocity
+    # variance of the load), beta0 = sqrt(8) / 3, n_b = 0.1, the run's nu
+    gb = 3.0
+    params = [(3.0 * table[r][2] / gb ** 2, np.sqrt(gb * gb - 1) / gb, 0.1, table[r][3]) for r in mine]
+    pic.dispersion_growth(params, 0.05, 10.0, 2000)              # load the module
+    t0 = time.perf_counter()
+    th_gamma, th_k = pic.dispersion_growth(params, 0.05, 10.0, 2000)
+    theory_ms = (time.perf_counter() - t0) * 1e3
+
     # the same runs as separate engines, stepped one after the other
     per_run_ms = 0.0
     per_run_launches = 0
@@ -449,6 +458,10 @@ def run_scan(args, rank, world, local_rank):
             "gpu_launches": launches,
             "clocks": clocks,
         }
+        line["theory"] = {"what": "Eq. (12) max growth rate over k in [0.05, 10] (2000 points) per run",
+                          "ms_with_copies": theory_ms, "runs": len(mine),
+                          "gamma_range": [float(th_gamma.min()), float(th_gamma.max())],
+                          "unstable_runs": int((th_gamma > 1e-6).sum())}
         if not args.no_per_run:
             line["per_run"] = {"value": tot_part * args.steps / (pr_max / 1e3), "unit": METRIC,
                                "ms_per_step": pr_max / args.steps, "gpu_launches": per_run_launches,

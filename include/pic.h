@@ -223,6 +223,17 @@ int pic_set_drag_map(pic_ctx* ctx, int run, int s, const float* nu, int32_t bx, 
  * (track_ids); PIC_EINVAL otherwise.  nu = 0 switches the collisions off.  Synchronises. */
 int pic_set_collisions(pic_ctx* ctx, int run, int s, double nu, uint64_t seed);
 
+/* Growth rates of the collisional filamentation of a warm beam, Eq. (12) of the paper,
+ *   w^2 = c_s^2 k^2 - w_b^2 beta0^2 k^2 / (k^2 + k_pe^2 / (1 + i nu / w)),
+ * in units k_pe = c / w_p = 1, w_b^2 = n_b (the theory line for the temperature / collision-rate
+ * scan).  params: device double[nsets][4] = (c_s^2, beta0, n_b, nu) per set; k scans nk
+ * uniform points of [kmin, kmax].  gamma_out, kstar_out: device double[nsets], the largest
+ * imaginary part of w over the k grid and the k where it occurs (the lowest such k).  The
+ * relation is non-relativistic (the paper's), so a comparison with the relativistic runs is
+ * qualitative.  Asynchronous on `stream`. */
+int pic_dispersion_growth(const double* params, int32_t nsets, double kmin, double kmax, int32_t nk,
+                          double* gamma_out, double* kstar_out, void* stream);
+
 /* ---------------------------------------------------------------- moment recorder
  * Coarse-grained state of run `run` at the current step: the inputs and the label parts of a
  * learned collision closure.  The paper's conclusion conjectures that the collisional friction on

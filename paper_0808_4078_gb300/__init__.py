@@ -114,6 +114,8 @@ _SIGNATURES = {
     "pic_mlp_status": (ctypes.c_int, [ctypes.c_int]),
     "pic_set_drag_map": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int32, ctypes.c_int32]),
     "pic_set_collisions": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64]),
+    "pic_dispersion_growth": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_int32, _VP, _VP, _VP]),
     "pic_launch_count": (ctypes.c_int64, [_VP]),
     "pic_step_count": (ctypes.c_int64, [_VP]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
@@ -443,3 +445,18 @@ class ClosureNet:
         self.stream.synchronize()
         _check(lib().pic_mlp_status(1))
         return float(self._loss.cpu()[0])
+
+
+def dispersion_growth(params, kmin, kmax, nk, stream=None):
+    """Max over a uniform k grid of Im w of Eq. (12) per parameter set (pic_dispersion_growth).
+    params: (nsets, 4) array-like of (c_s^2, beta0, n_b, nu).  Returns (gamma, kstar) as numpy."""
+    import torch
+    p = torch.as_tensor(np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 4), device="cuda")
+    n = p.shape[0]
+    g = torch.empty(n, dtype=torch.float64, device="cuda")
+    k = torch.empty(n, dtype=torch.float64, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().pic_dispersion_growth(_VP(p.data_ptr()), n, float(kmin), float(kmax), int(nk),
+                                       _VP(g.data_ptr()), _VP(k.data_ptr()), _VP(st.cuda_stream)))
+    st.synchronize()
+    return g.cpu().numpy(), k.cpu().numpy()

@@ -996,6 +996,17 @@ extern "C" int pic_set_collisions(pic_ctx* ctx, int run, int s, double nu, uint6
     return PIC_OK;
 }
 
+extern "C" int pic_dispersion_growth(const double* params, int32_t nsets, double kmin, double kmax, int32_t nk,
+                                     double* gamma_out, double* kstar_out, void* stream) {
+    if (nsets < 0 || nk < 1 || !(kmin >= 0) || !(kmax >= kmin) || !std::isfinite(kmax))
+        return fail(nullptr, PIC_EINVAL, "need nsets >= 0, nk >= 1 and 0 <= kmin <= kmax");
+    if (nsets == 0) return PIC_OK;
+    if (!params || !gamma_out || !kstar_out) return fail(nullptr, PIC_EINVAL, "null pointer");
+    cudaError_t e = launch_dispersion(params, nsets, kmin, kmax, nk, gamma_out, kstar_out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, "pic_dispersion_growth: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
 // ---------------------------------------------------------------- closure network
 namespace {
 int mlp_norm(const pic_mlp_norm* in, MlpNorm* out) {

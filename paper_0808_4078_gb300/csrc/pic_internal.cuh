@@ -236,6 +236,9 @@ cudaError_t preload_mlp();
 // Per-cell drag factors of run `run` from per-coarse-cell rates nu (bx x by blocks).
 cudaError_t launch_drag_map(const RunDev& host_run, float* map, const float* nu, int bx, int by, double dt,
                             cudaStream_t s);
+// Growth rates of the collisional filamentation dispersion relation (dispersion.cu).
+cudaError_t launch_dispersion(const double* params, int nsets, double kmin, double kmax, int nk, double* gamma,
+                              double* kstar, cudaStream_t s);
 cudaError_t launch_fit(const Args& a, int run, long long first, int nrec, int width, double t_noise,
                        double start_factor, double end_factor, double* out3, cudaStream_t s);
 }  // namespace pic
