@@ -3,11 +3,12 @@
 // with cell carry, charge-conserving Esirkepov current deposition (CIC) accumulated in int64
 // fixed point, and rebinning of every particle into its new cell's slots of the other buffer.
 //
-// One CTA per (run, tile) of 16 x 16 cells, 8 warps, a warp per cell.  The warp caches the 37
-// field values any particle of its cell can touch in registers.  Particles that stay in the
-// cell this step (the large majority) are pushed from that cache, add their 8 current terms and
-// 4 drag moments to int32 registers (one warp transpose-reduce per cell puts them in the shared
-// tile) and are appended to the cell's new slots with one atomic per warp.  Particles that cross
+// One CTA per (run, tile) of 16 x 16 cells, 8 warps, a warp per cell, 3 CTAs per SM (80
+// registers: the fields are read from the shared tile, not cached in registers, which buys the
+// third CTA).  Particles that stay in the cell this step (the large majority) add their 8
+// current terms and 4 drag moments to int32 registers (one warp transpose-reduce per cell puts
+// them in the shared tile) and are written to the cell's new stay slots at warp-local offsets
+// (no atomics).  Particles that cross
 // a cell edge go to a per-warp queue and are processed 32 at a time: per-lane atomics over their
 // 3 x 3 node window, and an atomic slot claim in the destination cell.  All paths evaluate the
 // same explicitly-rounded formulas and every current term is an integer before it is summed, so
@@ -107,24 +108,6 @@ __device__ __forceinline__ void gather(const A& F, const W3& wx, const W3& wy, f
     EB[2] = __fmaf_rn(wy.n[1], row_n(F, wx, 2, 1), __fmul_rn(wy.n[0], row_n(F, wx, 2, 0)));
     EB[5] = __fmaf_rn(wy.h[2], row_h(F, wx, 5, 1), __fmaf_rn(wy.h[1], row_h(F, wx, 5, 0), __fmul_rn(wy.h[0], row_h(F, wx, 5, -1))));
 }
-
-// The 37 values of one cell, in registers.
-struct CellCache {
-    float ex[2][3], by[2][3];   // [dy 0..1][dx -1..1]
-    float ey[3][2], bx[3][2];   // [dy -1..1][dx 0..1]
-    float ez[2][2];             // [dy 0..1][dx 0..1]
-    float bz[3][3];             // [dy -1..1][dx -1..1]
-    __device__ __forceinline__ float operator()(int c, int dx, int dy) const {
-        switch (c) {
-            case 0: return ex[dy][dx + 1];
-            case 4: return by[dy][dx + 1];
-            case 1: return ey[dy + 1][dx];
-            case 3: return bx[dy + 1][dx];
-            case 2: return ez[dy][dx];
-            default: return bz[dy + 1][dx + 1];
-        }
-    }
-};
 
 struct SharedFields {
     const Smem* s;
@@ -339,7 +322,7 @@ __device__ __forceinline__ void flush_acc(Smem& sm, int acc[12], int n0, int lan
     add_split(lo, hi, tot);
 }
 
-__global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
+__global__ void __launch_bounds__(NT, 3) push2d_kernel(const Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const int2 wk = a.work[blockIdx.x];
@@ -445,7 +428,6 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
     int st = 0;
     int cur_ci = -1, n0 = 0, g = 0, nchunk = 0;
     int seg_s = -1, seg_g = 0, wpos = 0;     // stay-area fill of the current (cell, species)
-    CellCache cc;
     int acc[12];
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = 0;
@@ -459,28 +441,6 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
             const int lx = cur_ci % TX, ly = cur_ci / TX;
             g = K.cell_off + (y0 + ly) * nx + (x0 + lx);
             n0 = (ly + 1) * RX + (lx + 1);
-#pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    cc.ex[b][d] = sm.F[0][n0 + b * RX + d - 1];
-                    cc.by[b][d] = sm.F[4][n0 + b * RX + d - 1];
-                }
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-#pragma unroll
-                for (int d = 0; d < 2; ++d) {
-                    cc.ey[b][d] = sm.F[1][n0 + (b - 1) * RX + d];
-                    cc.bx[b][d] = sm.F[3][n0 + (b - 1) * RX + d];
-                }
-#pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int d = 0; d < 2; ++d) cc.ez[b][d] = sm.F[2][n0 + b * RX + d];
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-#pragma unroll
-                for (int d = 0; d < 3; ++d) cc.bz[b][d] = sm.F[5][n0 + (b - 1) * RX + d - 1];
             if (anydrag) { ub0 = sm.ub[0][n0]; ub1 = sm.ub[1][n0]; ub2 = sm.ub[2][n0]; }
         }
         const int s = pc.s;
@@ -505,7 +465,7 @@ __global__ void __launch_bounds__(NT, 2) push2d_kernel(const Args a) {
             id = __float_as_int(sm.stg[warp][st][5][lane]);
         }
         const float df = P.drag ? drag_of(K, P, s, g - K.cell_off) : 0.f;
-        const Pushed r = push_one(cc, P, K, ox, oy, ux, uy, uz, ub0, ub1, ub2, df, s, (unsigned)id, step);
+        const Pushed r = push_one(SharedFields{&sm, n0}, P, K, ox, oy, ux, uy, uz, ub0, ub1, ub2, df, s, (unsigned)id, step);
         const bool small_u = !P.drag || (fabsf(r.ux) < 4.f && fabsf(r.uy) < 4.f && fabsf(r.uz) < 4.f);
         const bool stay = act && !r.bad && r.sx == 0 && r.sy == 0 && small_u;
         if (stay) {
