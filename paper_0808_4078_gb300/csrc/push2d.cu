@@ -71,6 +71,11 @@ __device__ __forceinline__ void advance(Cursor& c, const int (*cnt)[CELLS], int 
     }
 }
 
+// Slot of element k of cell g (32-bit: the library keeps cells x cap below 2^31).
+__device__ __forceinline__ int slot32(int g, int cap, int cap_stay, int ns, int k) {
+    return g * cap + (k < ns ? k : cap_stay + (k - ns));
+}
+
 // ------------------------------------------------------------------ gather
 // CIC weights of an axis for an offset o in [0,1): node lattice (nodes c, c+1) and the
 // half-shifted lattice (points c-1/2, c+1/2, c+3/2, stored at c-1, c, c+1).
@@ -218,7 +223,7 @@ __device__ __forceinline__ void deposit_terms(const Add& add, const SpeciesParam
 }
 
 // ------------------------------------------------------------------ rebinning
-__device__ __forceinline__ void store_slot(const Slots& D, size_t q, float ox, float oy, float ux,
+__device__ __forceinline__ void store_slot(const Slots& D, int q, float ox, float oy, float ux,
                                            float uy, float uz, int id) {
     D.o[0][q] = ox; D.o[1][q] = oy;
     D.u[0][q] = ux; D.u[1][q] = uy; D.u[2][q] = uz;
@@ -230,7 +235,7 @@ __device__ __forceinline__ void put_imm(const Slots& D, int cap, int cap_stay, i
                                         float ox, float oy, float ux, float uy, float uz, int id, int* err) {
     const int pi = atomicAdd(&D.icount[g], 1);
     if (pi < cap - cap_stay) {
-        store_slot(D, (size_t)g * cap + cap_stay + pi, ox, oy, ux, uy, uz, id);
+        store_slot(D, g * cap + cap_stay + pi, ox, oy, ux, uy, uz, id);
     } else {
         const int sp = atomicAdd(D.sn, 1);
         if (sp < spill_cap) {
@@ -260,7 +265,7 @@ __device__ __forceinline__ void drain(Smem& sm, const Args& a, const RunConst& K
     const int g = K.cell_off + cy * nx + cx;
     const int cap = a.cap[s], cst = a.cap_stay[s];
     const Slots S = a.slot[s][par], D = a.slot[s][par ^ 1];
-    const size_t p = slot_of(g, cap, cst, sm.cns[s][ci], i);
+    const int p = slot32(g, cap, cst, sm.cns[s][ci], i);
     const float ox = S.o[0][p], oy = S.o[1][p];
     const float u0x = S.u[0][p], u0y = S.u[1][p], u0z = S.u[2][p];
     const int id = S.id ? S.id[p] : 0;
@@ -406,7 +411,7 @@ __global__ void __launch_bounds__(NT, 3) push2d_kernel(const Args a) {
                 const int lx = c.ci % TX, ly = c.ci / TX;
                 const int g = K.cell_off + (y0 + ly) * nx + (x0 + lx);
                 const Slots S = a.slot[c.s][par];
-                const size_t q = slot_of(g, a.cap[c.s], a.cap_stay[c.s], sm.cns[c.s][c.ci], i);
+                const int q = slot32(g, a.cap[c.s], a.cap_stay[c.s], sm.cns[c.s][c.ci], i);
                 cp_async4(&sm.stg[warp][st][0][lane], S.o[0] + q);
                 cp_async4(&sm.stg[warp][st][1][lane], S.o[1] + q);
                 cp_async4(&sm.stg[warp][st][2][lane], S.u[0] + q);
@@ -494,7 +499,7 @@ __global__ void __launch_bounds__(NT, 3) push2d_kernel(const Args a) {
         const unsigned sm_ = __ballot_sync(FULL, stay);
         if (stay) {
             const int pos = wpos + __popc(sm_ & lt);
-            if (pos < cst) store_slot(D, (size_t)g * cap + pos, r.nox, r.noy, r.ux, r.uy, r.uz, id);
+            if (pos < cst) store_slot(D, g * cap + pos, r.nox, r.noy, r.ux, r.uy, r.uz, id);
             else put_imm(D, cap, cst, a.spill_cap[s], g, r.nox, r.noy, r.ux, r.uy, r.uz, id, &a.ctl->err);
         }
         wpos += __popc(sm_);
