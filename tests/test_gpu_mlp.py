@@ -55,7 +55,7 @@ def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
 
 
-@pytest.mark.parametrize("n", [1, 127, 128, 1000, 70_001])
+@pytest.mark.parametrize("n", [1, 127, 128, 1000, 70_001, 1 << 20])
 def test_forward_matches_oracle(pic, n):
     from oracle import mlp
     x, _ = _data(n)
