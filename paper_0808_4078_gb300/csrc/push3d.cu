@@ -161,10 +161,13 @@ __device__ __forceinline__ Pushed3 push3_one(const A& F, const SpeciesParams& P,
 // The current terms of one move (Esirkepov, CIC): for the axis a with the transverse axes b, c,
 // J_a on the two edges k of the window = round(j_a C_a[k] F_bc), F_bc = S0_b p_c + S1_b q_c the
 // path-averaged transverse shape (p = S0/3 + S1/6, q = S0/6 + S1/3).  add(comp, i, j, k, v)
-// receives node offsets relative to the window base (b_x, b_y, b_z).
+// receives node offsets relative to the window base (b_x, b_y, b_z).  A particle that does not
+// cross a cell edge along an axis has a zero third node (S0 = S1 = 0) and a zero second edge
+// (C[1] = 0) on that axis: xa, ya, za (warp-uniform: "some lane of the warp crosses along x, y,
+// z") skip those terms for the whole warp; the remaining terms are unchanged.
 template <class Add>
 __device__ __forceinline__ void deposit3(const Add& add, const SpeciesParams& P, const Win& wx, const Win& wy,
-                                         const Win& wz) {
+                                         const Win& wz, bool xa, bool ya, bool za) {
     float px[3], qx[3], py[3], qy[3], pz[3], qz[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -173,29 +176,38 @@ __device__ __forceinline__ void deposit3(const Add& add, const SpeciesParams& P,
         pz[i] = zp(wz.S0[i], wz.S1[i]); qz[i] = zq(wz.S0[i], wz.S1[i]);
     }
 #pragma unroll
-    for (int m = 0; m < 3; ++m)
+    for (int m = 0; m < 3; ++m) {
+        if (m == 2 && !za) continue;
 #pragma unroll
         for (int l = 0; l < 3; ++l) {
+            if (l == 2 && !ya) continue;
             const float f = zw(wy.S0[l], wy.S1[l], pz[m], qz[m]);
-#pragma unroll
-            for (int k = 0; k < 2; ++k) add(0, k, l, m, round_small(__fmul_rn(P.jx, wx.C[k]), f));
+            add(0, 0, l, m, round_small(__fmul_rn(P.jx, wx.C[0]), f));
+            if (xa) add(0, 1, l, m, round_small(__fmul_rn(P.jx, wx.C[1]), f));
         }
+    }
 #pragma unroll
-    for (int m = 0; m < 3; ++m)
+    for (int m = 0; m < 3; ++m) {
+        if (m == 2 && !za) continue;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
+            if (k == 2 && !xa) continue;
             const float f = zw(wz.S0[m], wz.S1[m], px[k], qx[k]);
-#pragma unroll
-            for (int l = 0; l < 2; ++l) add(1, k, l, m, round_small(__fmul_rn(P.jy, wy.C[l]), f));
+            add(1, k, 0, m, round_small(__fmul_rn(P.jy, wy.C[0]), f));
+            if (ya) add(1, k, 1, m, round_small(__fmul_rn(P.jy, wy.C[1]), f));
         }
+    }
 #pragma unroll
-    for (int l = 0; l < 3; ++l)
+    for (int l = 0; l < 3; ++l) {
+        if (l == 2 && !ya) continue;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
+            if (k == 2 && !xa) continue;
             const float f = zw(wx.S0[k], wx.S1[k], py[l], qy[l]);
-#pragma unroll
-            for (int m = 0; m < 2; ++m) add(2, k, l, m, round_small(__fmul_rn(P.jz, wz.C[m]), f));
+            add(2, k, l, 0, round_small(__fmul_rn(P.jz, wz.C[0]), f));
+            if (za) add(2, k, l, 1, round_small(__fmul_rn(P.jz, wz.C[1]), f));
         }
+    }
 }
 
 // Shared-memory reduction without a branch: `red` only when v != 0 (predicated).
@@ -391,6 +403,7 @@ __global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
         }
 #pragma unroll
         for (int r = 0; r < PER_THREAD; ++r) {
+            const unsigned am = __ballot_sync(FULL, pact[r]);
             if (!pact[r]) continue;
             const int e = pe[r];
             const int s = e / CELLS, ci = e - s * CELLS;
@@ -406,6 +419,8 @@ __global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
             const float df = P.drag ? drag_of(K, P, s, g - cbase) : 0.f;
             const Pushed3 res = push3_one(SharedFields3{&sm, n0}, P, K, po[r], pu[r][0], pu[r][1], pu[r][2],
                                           b0v, b1v, b2v, df, s, (unsigned)pid[r], step);
+            const bool xa = __any_sync(am, res.st[0] != 0), ya = __any_sync(am, res.st[1] != 0),
+                       za = __any_sync(am, res.st[2] != 0);
             if (res.bad) {
                 // keep the particle where it was, unmoved; the sticky flag fails the run
                 atomicOr(&a.ctl->err, ERR_BADPART);
@@ -420,7 +435,7 @@ __global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
             auto add = [&](int c, int i, int j, int k, int v) {
                 red_shared_nz(&sm.J32[c][nb + k * RXY + j * RX + i], v);
             };
-            deposit3(add, P, wx, wy, wz);
+            deposit3(add, P, wx, wy, wz, xa, ya, za);
             const int n1 = n0 + res.st[2] * RXY + res.st[1] * RX + res.st[0];
             if (P.drag) {
                 add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], __float2ll_rn(res.ux * MOM_SCALE));
@@ -558,7 +573,7 @@ __global__ void __launch_bounds__(NT) spill3d_kernel(const Args a) {
                     atomicAdd((unsigned long long*)&Rp->J[c][gi], (unsigned long long)(long long)v);
                 }
             };
-            deposit3(add, P, wx, wy, wz);
+            deposit3(add, P, wx, wy, wz, true, true, true);
             const int ncx = wrap1(cx + r.st[0], nx), ncy = wrap1(cy + r.st[1], ny), ncz = wrap1(cz + r.st[2], nz);
             const long long l1 = ((long long)ncz * ny + ncy) * nx + ncx;
             if (P.drag) {
