@@ -120,6 +120,8 @@ def _workers():
 
 
 def workload_name(args):
+    if args.workload == "hybrid":
+        return f"hybrid_beam_2d_{args.n}x{args.n}_ppc{args.ppc}"
     if args.workload == "closure":
         return f"closure_mlp_9x64x64x1_{args.samples}samples"
     if args.workload == "warm2d":
@@ -178,6 +180,8 @@ def cpu_baseline(args, seconds=15.0):
     """The oracle as it is, single-threaded, on a bounded crop of the same physics."""
     if args.workload == "closure":
         return cpu_baseline_closure(args, seconds)
+    if args.workload == "hybrid":
+        return cpu_baseline_hybrid(args, seconds)
     import oracle
     wl, what = _oracle_sample(args)
     sim = oracle.Simulation.from_workload(wl)
@@ -613,13 +617,141 @@ def run_closure(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- hybrid model
+HYB_BYTES_PER_PARTICLE = 44     # read cell, ox, oy, ux, uy, P (24 B); write cell, ox, oy, ux, uy (20 B)
+HYB_BYTES_PER_NODE = 24         # read the FP32 (a, beta_p) pair once; J and N (int64) written once
+
+
+def _hybrid_load(args, rank=0):
+    import pic_inputs as pi
+    return pi.hybrid_beam_load(nx=args.n, ny=args.n, ppc=args.ppc, seed=6 + 1000 * rank)
+
+
+def cpu_baseline_hybrid(args, seconds=15.0):
+    """The FP64 hybrid oracle (numpy + sparse LU) on a 128 x 128 crop of the same load."""
+    import pic_inputs as pi
+    from oracle import hybrid
+    L = pi.hybrid_beam_load(nx=128, ny=128, ppc=args.ppc, seed=6)
+    sim = hybrid.HybridSim(L.nx, L.ny, L.dx, L.dx, L.dt, n0=1.0, nu=L.nu, w=L.w)
+    sim.load(L.X, L.Y, L.ux, L.uy, L.uz, L.beta_p0)
+    sim.step(1)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        sim.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": L.n * steps / el, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"128x128 crop, {args.ppc} ppc ({L.n} particles), {steps} steps in {el:.1f} s, "
+                      f"FP64 numpy + scipy sparse LU, single-threaded"}
+
+
+def run_hybrid(args, rank, world, local_rank):
+    """The quasi-neutral hybrid model: push/deposit, variable-density field solve, update.
+    value = beam particle-steps/s; the roofline is taken on the push/deposit kernel."""
+    import torch
+    import paper_0808_4078_gb300 as pic
+
+    dist = _init_dist(world, local_rank)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    L = _hybrid_load(args, rank)
+    n, nx, ny = L.n, L.nx, L.ny
+    nc = nx * ny
+
+    def make(flags):
+        return pic.HybridEngine(nx, ny, L.dx, L.dx, L.dt, 1.0, L.nu, L.w, n, max_iter=args.cg_iter,
+                                flags=flags, device=f"cuda:{local_rank}")
+
+    # ---------------- end to end through the public API from host buffers
+    eng = make(0)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    eng.load(L.X, L.Y, L.ux, L.uy, L.uz, L.beta_p0)
+    eng.step(args.steps)
+    en = eng.energies()
+    e2e_s = time.perf_counter() - t0
+    h2d = n * 24 + nc * 16              # FP32 cell/offsets/momenta and the (a, beta_p) pair
+    d2h = 3 * 8
+    assert np.isfinite(en).all()
+
+    # ---------------- device-resident timing of the graph-replayed step
+    eng.step(args.warmup)
+    eng.sync()
+    l0 = eng.launch_count()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    with Clocks(local_rank) as clk:
+        start.record(eng.stream)
+        eng.step(args.steps)
+        stop.record(eng.stream)
+        stop.synchronize()
+    barrier()
+    ms = start.elapsed_time(stop)
+    launches = eng.launch_count() - l0
+    st = eng.stats()
+    eng.close()
+
+    # ---------------- phase split (CUDA events per phase, direct launches)
+    eng = make(pic.PIC_FLAG_PROFILE)
+    eng.load(L.X, L.Y, L.ux, L.uy, L.uz, L.beta_p0)
+    eng.step(args.warmup)
+    base = eng.kernel_times()
+    eng.step(args.steps)
+    times = eng.kernel_times()
+    eng.close()
+    phase = {k: (times[k][1] - base[k][1]) / args.steps for k in times}
+    t_max, e2e_max = _max_over_ranks(dist, [ms, e2e_s])
+
+    if rank == 0:
+        peak, peak_kind = _peaks()
+        alg = n * HYB_BYTES_PER_PARTICLE + nc * HYB_BYTES_PER_NODE
+        push_ms = phase["push_deposit"]
+        achieved = alg / (push_ms / 1e3) / 1e9
+        line = {
+            "metric": METRIC, "value": world * n * args.steps / (t_max / 1e3), "unit": METRIC,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"hybrid_beam_2d_{nx}x{ny}_ppc{args.ppc}", "grid": [nx, ny],
+                       "ppc": args.ppc, "particles_per_gpu": n, "cg_max_iter": args.cg_iter,
+                       "parallelism": f"replicas{world}",
+                       "l2": f"particles {n * 24 / 1e9:.2f} GB > L2, no flush"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "hybrid push_deposit",
+                         "peak_kind": peak_kind, "alg_bytes_per_launch": alg,
+                         "mean_launch_ms": push_ms},
+            "phase_ms_per_step": phase,
+            "solver": {"cg_iterations_per_step": st["cg_iterations"] / max(1, st["steps"]),
+                       "unconverged_steps": st["unconverged_steps"]},
+            "e2e": {"value": world * n * args.steps / e2e_max, "unit": METRIC,
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_hybrid(args)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="warm2d", choices=["warm2d", "hot3d", "scan", "closure"])
+    ap.add_argument("--workload", default="warm2d", choices=["warm2d", "hot3d", "scan", "closure", "hybrid"])
+    ap.add_argument("--cg-iter", type=int, default=16, help="hybrid: conjugate-gradient iterations per step")
     ap.add_argument("--n", type=int, default=1024, help="2D grid side (warm2d)")
     ap.add_argument("--grid3", type=lambda t: tuple(int(x) for x in t.split(",")),
                     default=(256, 256, 512), help="3D grid nx,ny,nz (hot3d)")
@@ -636,7 +768,7 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.ppc is None:
-        args.ppc = {"warm2d": 64, "hot3d": 8, "scan": 32, "closure": 8}[args.workload]
+        args.ppc = {"warm2d": 64, "hot3d": 8, "scan": 32, "closure": 8, "hybrid": 16}[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -647,6 +779,8 @@ def main():
         run_scan(args, rank, world, local_rank)
     elif args.workload == "closure":
         run_closure(args, rank, world, local_rank)
+    elif args.workload == "hybrid":
+        run_hybrid(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

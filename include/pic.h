@@ -234,6 +234,68 @@ int pic_set_collisions(pic_ctx* ctx, int run, int s, double nu, uint64_t seed);
 int pic_dispersion_growth(const double* params, int32_t nsets, double kmin, double kmax, int32_t nk,
                           double* gamma_out, double* kstar_out, void* stream);
 
+/* ---------------------------------------------------------------- hybrid model
+ * The paper's quasi-neutral model (Eqs. 1-6) as a simulation of its own: a kinetic electron beam
+ * in the transverse plane, the plasma return current as a fluid and the axial vector potential
+ * from Ampere's law without the displacement current.  Units as above, a = e A_z / (m c^2):
+ *   lap a = n_b beta_bz + n_p beta_p,  n_p = n0 - n_b   (Eq. 2; quasi-neutral plasma density)
+ *   d beta_p / dt + nu beta_p = d a / dt                (Eq. 3)
+ *   d u_perp / dt = -(beta_z - beta_p) grad a            (Eq. 4)
+ *   u_z = P + a, P conserved per particle               (Eq. 6)
+ * Without collisions the energy of Eq. 7 (beam, magnetic, plasma kinetic with the local n_p) is
+ * an invariant; pic_hybrid_energies returns its three parts.
+ * Periodic nx x ny grid (powers of two in [8, 2048]), a and beta_p at nodes (FP64), 5-point
+ * Laplacian, CIC interpolation and deposit, particles FP32 (cell + offset).  A step pushes the
+ * beam in the old fields, deposits its density and current at the new positions, solves
+ * (lap - n_p) a^{n+1} = n_b beta_b + n_p (beta_p^n - a^n - nu dt beta_p^n) with
+ * n_p = max(n0 - n_b, 0) per node (FP64 residual, FP32 conjugate-gradient correction
+ * preconditioned by the constant-density spectral solve, stopped at a relative residual of tol or
+ * after max_iter iterations) and updates beta_p^{n+1} = beta_p^n + a^{n+1} - a^n - nu dt beta_p^n.
+ * Steps replay a CUDA graph of one step unless a flag asks otherwise.  Host arrays are copied
+ * during the calls; the arena (pic_hybrid_required_bytes, 256-byte aligned) and the stream belong
+ * to the caller.  Deterministic: results do not depend on particle order or scheduling. */
+typedef struct pic_hybrid pic_hybrid;
+typedef struct pic_hybrid_config {
+    int32_t nx, ny;             /* nodes per axis, powers of two in [8, 2048] */
+    double dx, dy, dt;          /* c/w_p, 1/w_p; dt < dx and dt < dy */
+    double n0;                  /* total electron density (1 in these units), > 0 */
+    double nu;                  /* collision rate of the plasma flow, >= 0 */
+    double w;                   /* beam density per macro-particle and cell, >= 0 */
+    int64_t capacity;           /* beam particles, <= 2^31 */
+    double tol;                 /* relative residual of the solve; 0 = 1e-5 */
+    int32_t max_iter;           /* conjugate-gradient iterations per step; 0 = 16, <= 1000 */
+    int32_t flags;              /* PIC_FLAG_PROFILE (phase timing, no graph), PIC_FLAG_NO_GRAPH */
+} pic_hybrid_config;
+int pic_hybrid_required_bytes(const pic_hybrid_config* cfg, size_t* bytes_out);
+int pic_hybrid_init(const pic_hybrid_config* cfg, void* device_arena, size_t arena_bytes,
+                    void* cuda_stream, pic_hybrid** out);
+/* Beam particles (host: X, Y in cell units within the grid, momenta u = gamma beta) and the
+ * plasma velocity beta_p at the nodes (host, ny x nx); a starts at 0, so P = u_z.
+ * PIC_EBADPART for particles outside the grid or non-finite values.  Synchronous. */
+int pic_hybrid_load(pic_hybrid* h, int64_t n, const double* X, const double* Y, const double* ux,
+                    const double* uy, const double* uz, const double* beta_p);
+int pic_hybrid_step(pic_hybrid* h, int nsteps);          /* asynchronous on the stream */
+/* Read back (host arrays, any may be NULL): a and beta_p (ny x nx), particle X, Y, ux, uy in the
+ * load order.  Synchronises. */
+int pic_hybrid_get(pic_hybrid* h, double* a, double* beta_p, double* X, double* Y, double* ux,
+                   double* uy);
+/* Magnetic energy sum |D+ a|^2 / 2 dx dy, beam kinetic energy sum w (gamma - 1) dx dy and plasma
+ * kinetic energy sum n_p beta_p^2 / 2 dx dy; deterministic.  Synchronises. */
+int pic_hybrid_energies(pic_hybrid* h, double out3[3]);
+/* {steps, conjugate-gradient iterations in total, steps that stopped at max_iter above tol,
+ * iterations of the last step}.  Synchronises. */
+int pic_hybrid_stats(pic_hybrid* h, int64_t out4[4]);
+/* With PIC_FLAG_PROFILE: CUDA-event time on the stream per phase ("push_deposit", "field_solve",
+ * "update"), accumulated over the steps so far; same record as pic_kernel_times.  Synchronises. */
+int pic_hybrid_kernel_times(pic_hybrid* h, pic_kernel_time* out, int max, int* n_out);
+/* Kernels launched by pic_hybrid_step so far: per step the push, the solve set-up and the update,
+ * and per conjugate-gradient iteration 7 kernels (8 in a graph, whose while node runs only the
+ * iterations needed; direct launches run max_iter, returning at once after convergence).
+ * Synchronises; -1 on error. */
+int64_t pic_hybrid_launch_count(pic_hybrid* h);
+int64_t pic_hybrid_step_count(const pic_hybrid* h);
+void pic_hybrid_free(pic_hybrid* h);
+
 /* ---------------------------------------------------------------- moment recorder
  * Coarse-grained state of run `run` at the current step: the inputs and the label parts of a
  * learned collision closure.  The paper's conclusion conjectures that the collisional friction on

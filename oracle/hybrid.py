@@ -130,20 +130,26 @@ class HybridSim:
             out += np.bincount(jj * self.nx + ii, weights=q * wgt, minlength=self.nx * self.ny)
         return out.reshape(self.ny, self.nx)
 
+    def push(self, X, Y, ux, uy, P):
+        """Steps 1-3 for the given particles in the current fields: (X, Y, ux, uy) after the move."""
+        a, bp, dt = self.a, self.beta_p, self.dt
+        ua = self._interp(a, X, Y)
+        gx, gy = self._grad(a, X, Y)
+        bpp = self._interp(bp, X, Y)
+        uz = P + ua
+        g = np.sqrt(1.0 + ux ** 2 + uy ** 2 + uz ** 2)
+        f = uz / g - bpp
+        ux = ux - dt * f * gx
+        uy = uy - dt * f * gy
+        g2 = np.sqrt(1.0 + ux ** 2 + uy ** 2 + uz ** 2)
+        X = (X + dt * ux / (g2 * self.dx)) % self.nx
+        Y = (Y + dt * uy / (g2 * self.dy)) % self.ny
+        return X, Y, ux, uy
+
     def step(self, n=1):
         for _ in range(n):
             a, bp, dt = self.a, self.beta_p, self.dt
-            ua = self._interp(a, self.X, self.Y)
-            gx, gy = self._grad(a, self.X, self.Y)
-            bpp = self._interp(bp, self.X, self.Y)
-            uz = self.P + ua
-            g = np.sqrt(1.0 + self.ux ** 2 + self.uy ** 2 + uz ** 2)
-            f = uz / g - bpp
-            self.ux = self.ux - dt * f * gx
-            self.uy = self.uy - dt * f * gy
-            g2 = np.sqrt(1.0 + self.ux ** 2 + self.uy ** 2 + uz ** 2)
-            self.X = (self.X + dt * self.ux / (g2 * self.dx)) % self.nx
-            self.Y = (self.Y + dt * self.uy / (g2 * self.dy)) % self.ny
+            self.X, self.Y, self.ux, self.uy = self.push(self.X, self.Y, self.ux, self.uy, self.P)
             uzs = self.P + self._interp(a, self.X, self.Y)
             gs = np.sqrt(1.0 + self.ux ** 2 + self.uy ** 2 + uzs ** 2)
             jb = self._deposit(self.X, self.Y, self.w * uzs / gs)

@@ -65,6 +65,13 @@ class KernelTime(ctypes.Structure):
                 ("total_ms", ctypes.c_double)]
 
 
+class HybridConfig(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("dx", ctypes.c_double),
+                ("dy", ctypes.c_double), ("dt", ctypes.c_double), ("n0", ctypes.c_double),
+                ("nu", ctypes.c_double), ("w", ctypes.c_double), ("capacity", ctypes.c_int64),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
 class MlpNorm(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_float * 9), ("sigma", ctypes.c_float * 9), ("nin", ctypes.c_int32)]
 
@@ -116,6 +123,17 @@ _SIGNATURES = {
     "pic_set_collisions": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64]),
     "pic_dispersion_growth": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_int32, _VP, _VP, _VP]),
+    "pic_hybrid_required_bytes": (ctypes.c_int, [ctypes.POINTER(HybridConfig), ctypes.POINTER(ctypes.c_size_t)]),
+    "pic_hybrid_init": (ctypes.c_int, [ctypes.POINTER(HybridConfig), _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+    "pic_hybrid_load": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "pic_hybrid_step": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "pic_hybrid_get": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "pic_hybrid_energies": (ctypes.c_int, [_VP, _VP]),
+    "pic_hybrid_stats": (ctypes.c_int, [_VP, _VP]),
+    "pic_hybrid_kernel_times": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "pic_hybrid_launch_count": (ctypes.c_int64, [_VP]),
+    "pic_hybrid_step_count": (ctypes.c_int64, [_VP]),
+    "pic_hybrid_free": (None, [_VP]),
     "pic_launch_count": (ctypes.c_int64, [_VP]),
     "pic_step_count": (ctypes.c_int64, [_VP]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
@@ -460,3 +478,75 @@ def dispersion_growth(params, kmin, kmax, nk, stream=None):
                                        _VP(g.data_ptr()), _VP(k.data_ptr()), _VP(st.cuda_stream)))
     st.synchronize()
     return g.cpu().numpy(), k.cpu().numpy()
+
+
+# ---------------------------------------------------------------- hybrid model
+class HybridEngine:
+    """The quasi-neutral hybrid model (pic_hybrid_*): arena and stream from PyTorch."""
+
+    def __init__(self, nx, ny, dx, dy, dt, n0, nu, w, capacity, tol=0.0, max_iter=0, flags=0,
+                 device="cuda"):
+        import torch
+        self._torch = torch
+        self.cfg = HybridConfig(nx, ny, dx, dy, dt, n0, nu, w, capacity, tol, max_iter, flags)
+        nb = ctypes.c_size_t(0)
+        _check(lib().pic_hybrid_required_bytes(ctypes.byref(self.cfg), ctypes.byref(nb)))
+        self.device = torch.device(device)
+        self.arena = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        self.stream = torch.cuda.Stream(self.device)
+        h = _VP()
+        _check(lib().pic_hybrid_init(ctypes.byref(self.cfg), _VP(self.arena.data_ptr()), nb.value,
+                                     _VP(self.stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+        self.n = 0
+
+    def close(self):
+        if self._h:
+            lib().pic_hybrid_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, X, Y, ux, uy, uz, beta_p):
+        f = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        X, Y, ux, uy, uz = f(X), f(Y), f(ux), f(uy), f(uz)
+        bp = np.broadcast_to(np.asarray(beta_p, np.float64), (self.cfg.ny, self.cfg.nx)).copy()
+        self.n = X.shape[0]
+        _check(lib().pic_hybrid_load(self._h, self.n, _ptr(X), _ptr(Y), _ptr(ux), _ptr(uy), _ptr(uz), _ptr(bp)))
+
+    def step(self, n=1):
+        _check(lib().pic_hybrid_step(self._h, int(n)))
+
+    def sync(self):
+        self.stream.synchronize()
+
+    def state(self):
+        nc = (self.cfg.ny, self.cfg.nx)
+        a, bp = np.empty(nc), np.empty(nc)
+        X, Y, ux, uy = (np.empty(self.n) for _ in range(4))
+        _check(lib().pic_hybrid_get(self._h, _ptr(a), _ptr(bp), _ptr(X), _ptr(Y), _ptr(ux), _ptr(uy)))
+        return dict(a=a, beta_p=bp, X=X, Y=Y, ux=ux, uy=uy)
+
+    def energies(self):
+        out = np.zeros(3)
+        _check(lib().pic_hybrid_energies(self._h, _ptr(out)))
+        return out
+
+    def stats(self):
+        out = np.zeros(4, np.int64)
+        _check(lib().pic_hybrid_stats(self._h, _ptr(out)))
+        return dict(steps=int(out[0]), cg_iterations=int(out[1]), unconverged_steps=int(out[2]),
+                    last_iterations=int(out[3]))
+
+    def kernel_times(self):
+        recs = (KernelTime * 3)()
+        n = ctypes.c_int(0)
+        _check(lib().pic_hybrid_kernel_times(self._h, ctypes.cast(recs, _VP), 3, ctypes.byref(n)))
+        return {recs[i].name.decode(): (int(recs[i].launches), float(recs[i].total_ms)) for i in range(n.value)}
+
+    def launch_count(self):
+        return int(lib().pic_hybrid_launch_count(self._h))

@@ -1073,6 +1073,11 @@ extern "C" int64_t pic_step_count(const pic_ctx* ctx) { return ctx ? ctx->host_s
 
 extern "C" int pic_num_runs(const pic_ctx* ctx) { return ctx ? ctx->nruns : -1; }
 
+namespace pic {
+// Error text of a failed call that has no context (read back with pic_last_error(NULL)).
+void set_call_error(const char* msg) { g_init_error = msg; }
+}  // namespace pic
+
 extern "C" const char* pic_last_error(const pic_ctx* ctx) {
     return ctx ? ctx->err.c_str() : g_init_error.c_str();
 }

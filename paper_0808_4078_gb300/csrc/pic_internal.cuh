@@ -239,6 +239,8 @@ cudaError_t launch_drag_map(const RunDev& host_run, float* map, const float* nu,
 // Growth rates of the collisional filamentation dispersion relation (dispersion.cu).
 cudaError_t launch_dispersion(const double* params, int nsets, double kmin, double kmax, int nk, double* gamma,
                               double* kstar, cudaStream_t s);
+// Error text of a failed context-free call (pic_last_error(NULL)).
+void set_call_error(const char* msg);
 cudaError_t launch_fit(const Args& a, int run, long long first, int nrec, int width, double t_noise,
                        double start_factor, double end_factor, double* out3, cudaStream_t s);
 }  // namespace pic

@@ -311,3 +311,48 @@ def weibel_load_parallel(*, ndim=2, nx, ny, nz=1, ppc, gamma_b=3.0, nb=0.1, T_pe
             b.close()
             b.unlink()
         raise
+
+
+# ---------------------------------------------------------------- hybrid-model loads
+@dataclass
+class HybridLoad:
+    """Initial state of the quasi-neutral hybrid model: beam particles at X, Y (cell units, FP64
+    holding FP32-representable offsets, so an FP32 cell + offset copy is exact), momenta (FP64
+    holding FP32 values), the beam density per particle w, and the initial plasma flow beta_p0
+    that carries the return current (zero net current)."""
+    name: str
+    nx: int
+    ny: int
+    dx: float
+    dt: float
+    nu: float
+    X: np.ndarray
+    Y: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    uz: np.ndarray
+    w: float
+    beta_p0: float
+
+    @property
+    def n(self) -> int:
+        return int(self.X.shape[0])
+
+
+def hybrid_beam_load(*, nx, ny, ppc, gamma_b=3.0, nb=0.1, T_perp_beam=0.1, nu=0.1, dx=0.1,
+                     dt=0.05, seed=6, name=None):
+    """ppc beam particles per cell in cell order (x fastest), uniform in-cell offsets, transverse
+    momenta ~ N(0, sqrt(T_perp_beam)), u_z = sqrt(gamma_b^2 - 1); beta_p0 = -nb <beta_z> / (1 - nb)."""
+    rng = np.random.default_rng(seed)
+    ncell = nx * ny
+    cell = np.repeat(np.arange(ncell, dtype=np.int64), ppc)
+    off = rng.random((2, cell.shape[0]), dtype=np.float32)
+    X = (cell % nx).astype(np.float64) + off[0].astype(np.float64)
+    Y = (cell // nx).astype(np.float64) + off[1].astype(np.float64)
+    s = np.float32(math.sqrt(T_perp_beam))
+    ux = (s * rng.standard_normal(cell.shape[0], dtype=np.float32)).astype(np.float64)
+    uy = (s * rng.standard_normal(cell.shape[0], dtype=np.float32)).astype(np.float64)
+    uz = np.full(cell.shape[0], float(np.float32(math.sqrt(gamma_b ** 2 - 1))))
+    bz = uz / np.sqrt(1.0 + ux ** 2 + uy ** 2 + uz ** 2)
+    return HybridLoad(name or f"hybrid_beam_2d_{nx}x{ny}_ppc{ppc}", nx, ny, dx, dt, nu, X, Y, ux, uy,
+                      uz, nb / ppc, float(-nb * bz.mean() / (1.0 - nb)))

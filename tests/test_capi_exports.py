@@ -57,6 +57,24 @@ def test_required_bytes_and_config_errors_without_gpu(libpic):
         pic.required_bytes(tight)
 
 
+def test_hybrid_required_bytes_and_config_errors_without_gpu(libpic):
+    import paper_0808_4078_gb300 as pic
+    lib = pic.lib()
+    nb = ctypes.c_size_t(0)
+    ok = pic.HybridConfig(256, 128, 0.1, 0.1, 0.05, 1.0, 0.0, 0.01, 1000, 0.0, 0, 0)
+    assert lib.pic_hybrid_required_bytes(ctypes.byref(ok), ctypes.byref(nb)) == 0
+    # particles 24 B, grid 8 x 8 B + 7 x 4 B + 2 x 8 B complex per node
+    assert nb.value >= 1000 * 24 + 256 * 128 * (40 + 28 + 16)
+    for bad in (pic.HybridConfig(96, 128, 0.1, 0.1, 0.05, 1.0, 0.0, 0.01, 10, 0.0, 0, 0),     # not 2^k
+                pic.HybridConfig(4096, 8, 0.1, 0.1, 0.05, 1.0, 0.0, 0.01, 10, 0.0, 0, 0),     # > 2048
+                pic.HybridConfig(64, 64, 0.1, 0.1, 0.1, 1.0, 0.0, 0.01, 10, 0.0, 0, 0),       # dt = dx
+                pic.HybridConfig(64, 64, 0.1, 0.1, 0.05, 0.0, 0.0, 0.01, 10, 0.0, 0, 0),      # n0 = 0
+                pic.HybridConfig(64, 64, 0.1, 0.1, 0.05, 1.0, -1.0, 0.01, 10, 0.0, 0, 0),     # nu < 0
+                pic.HybridConfig(64, 64, 0.1, 0.1, 0.05, 1.0, 0.0, 0.01, -1, 0.0, 0, 0),      # capacity
+                pic.HybridConfig(64, 64, 0.1, 0.1, 0.05, 1.0, 0.0, 0.01, 10, 0.0, 5000)):  # max_iter
+        assert lib.pic_hybrid_required_bytes(ctypes.byref(bad), ctypes.byref(nb)) == -1
+
+
 def test_package_fails_loudly_without_library(tmp_path, monkeypatch):
     import paper_0808_4078_gb300 as pic
     monkeypatch.setattr(pic, "LIB_PATH", str(tmp_path / "missing.so"))
