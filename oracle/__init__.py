@@ -48,7 +48,7 @@ class _Grid(ctypes.Structure):
                 ("nz", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
                 ("dz", ctypes.c_double), ("dt", ctypes.c_double),
                 ("Ex", P), ("Ey", P), ("Ez", P), ("Bx", P), ("By", P), ("Bz", P),
-                ("Jx", P), ("Jy", P), ("Jz", P), ("step", ctypes.c_int64)]
+                ("Jx", P), ("Jy", P), ("Jz", P), ("step", ctypes.c_int64), ("j_filter", ctypes.c_int)]
 
 
 class _Species(ctypes.Structure):
@@ -78,6 +78,8 @@ def lib():
         _lib.orc_moments.restype = ctypes.c_int
         _lib.orc_yee.argtypes = [ctypes.POINTER(_Grid)]
         _lib.orc_yee.restype = None
+        _lib.orc_binomial.argtypes = [ctypes.POINTER(_Grid), P]
+        _lib.orc_binomial.restype = None
         _lib.orc_rho.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Species), ctypes.c_int, P]
         _lib.orc_rho.restype = None
         _lib.orc_gather.argtypes = [ctypes.POINTER(_Grid), ctypes.c_double, ctypes.c_double,
@@ -138,8 +140,9 @@ class Species:
 class Simulation:
     """Grid + species, advanced by the C oracle one step at a time."""
 
-    def __init__(self, ndim, nx, ny, nz=1, dx=0.1, dy=None, dz=None, dt=0.05):
+    def __init__(self, ndim, nx, ny, nz=1, dx=0.1, dy=None, dz=None, dt=0.05, j_filter=0):
         self.ndim, self.nx, self.ny = ndim, nx, ny
+        self.j_filter = int(j_filter)   # 1: binomial pass per axis on J before the field update
         self.nz = nz if ndim == 3 else 1
         self.dx = dx
         self.dy = dx if dy is None else dy
@@ -161,7 +164,7 @@ class Simulation:
         E, B, J = self.E, self.B, self.J
         return _Grid(self.ndim, self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.dt,
                      _ptr(E[0]), _ptr(E[1]), _ptr(E[2]), _ptr(B[0]), _ptr(B[1]), _ptr(B[2]),
-                     _ptr(J[0]), _ptr(J[1]), _ptr(J[2]), self.step_index)
+                     _ptr(J[0]), _ptr(J[1]), _ptr(J[2]), self.step_index, self.j_filter)
 
     def add_species(self, q, m, w, nu, X, Y, Z, ux, uy, uz, name=""):
         s = Species(q, m, w, nu, X, Y, Z if self.ndim == 3 else None, ux, uy, uz, self.ncell, name)
@@ -198,9 +201,9 @@ class Simulation:
                 raise MemoryError("orc_moments")
 
     @classmethod
-    def from_workload(cls, wl):
+    def from_workload(cls, wl, j_filter=0):
         """Build from a pic_inputs.Workload: X = cell index + FP32 offset, exactly, in FP64."""
-        sim = cls(wl.ndim, wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, wl.dz, wl.dt)
+        sim = cls(wl.ndim, wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, wl.dz, wl.dt, j_filter=j_filter)
         for s in wl.species:
             i = (s.cell % wl.nx).astype(np.float64)
             j = ((s.cell // wl.nx) % wl.ny).astype(np.float64)
@@ -240,6 +243,13 @@ class Simulation:
     def yee(self):
         g = self.cgrid()
         lib().orc_yee(ctypes.byref(g))
+
+    def binomial(self, F):
+        """One 1-2-1 pass per axis of a grid array (copy), as applied to J when j_filter is on."""
+        out = np.ascontiguousarray(F, dtype=np.float64).copy()
+        assert out.size == self.ncell
+        lib().orc_binomial(ctypes.byref(self.cgrid()), _ptr(out))
+        return out
 
     def gather(self, X, Y, Z=0.0):
         out = np.zeros(6)

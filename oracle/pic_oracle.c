@@ -48,6 +48,7 @@ typedef struct orc_grid {
     double *Bx, *By, *Bz;
     double *Jx, *Jy, *Jz; /* current density of the last step, J^{n+1/2} */
     int64_t step;         /* steps completed: keys the binary-collision draws of the next step */
+    int j_filter;         /* 1: one binomial pass per axis on J before the field update */
 } orc_grid;
 
 typedef struct orc_species {
@@ -310,6 +311,38 @@ static void yee_full_e(orc_grid *g, double dt) {
     }
 }
 
+/* ---------------------------------------------------------------- current filter */
+
+/* One 1-2-1 binomial pass along each axis of a periodic grid array (x, y, then z in 3D):
+ * F_i <- (F_{i-1} + 2 F_i + F_{i+1}) / 4.  The smoothing that damps grid-scale current
+ * (numerical Cherenkov control); the paper is silent on filtering. */
+void orc_binomial(const orc_grid *g, double *F) {
+    int nx = g->nx, ny = g->ny, nz = g->ndim == 3 ? g->nz : 1;
+    int64_t nc = (int64_t)nx * ny * nz;
+    double *t = malloc(sizeof(double) * (size_t)nc);
+    if (!t) return;
+    for (int axis = 0; axis < g->ndim; axis++) {
+        memcpy(t, F, sizeof(double) * (size_t)nc);
+        for (int k = 0; k < nz; k++)
+            for (int j = 0; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    int64_t c = ((int64_t)k * ny + j) * nx + i, m, p;
+                    if (axis == 0) {
+                        m = ((int64_t)k * ny + j) * nx + (i + nx - 1) % nx;
+                        p = ((int64_t)k * ny + j) * nx + (i + 1) % nx;
+                    } else if (axis == 1) {
+                        m = ((int64_t)k * ny + (j + ny - 1) % ny) * nx + i;
+                        p = ((int64_t)k * ny + (j + 1) % ny) * nx + i;
+                    } else {
+                        m = ((int64_t)((k + nz - 1) % nz) * ny + j) * nx + i;
+                        p = ((int64_t)((k + 1) % nz) * ny + j) * nx + i;
+                    }
+                    F[c] = 0.25 * (t[m] + 2.0 * t[c] + t[p]);
+                }
+    }
+    free(t);
+}
+
 /* Yee step with the grid's current: B^n -> B^{n+1/2}, E^n -> E^{n+1}, B^{n+1/2} -> B^{n+1}. */
 void orc_yee(orc_grid *g) {
     yee_half_b(g, 0.5 * g->dt);
@@ -513,6 +546,11 @@ int orc_step(orc_grid *g, orc_species *sp, int nsp, orc_diag *d) {
                     s->ubar[3 * c + a] = ncnt[c] > 0 ? nsum[3 * c + a] / ncnt[c] : 0.0;
             free(nsum); free(ncnt);
         }
+    }
+    if (g->j_filter) {
+        orc_binomial(g, g->Jx);
+        orc_binomial(g, g->Jy);
+        orc_binomial(g, g->Jz);
     }
     orc_yee(g);
     return 0;
