@@ -290,7 +290,7 @@ def run_ours(args, rank, world, local_rank):
     cap = [s.n for s in wl.species]
     eng = pic.Engine(wl.ndim, wl.nx, wl.ny, wl.nz, dx=wl.dx, dt=wl.dt, capacity=cap,
                      sort_interval=args.sort, diag_interval=args.diag, diag_capacity=4096,
-                     flags=pic.PIC_FLAG_PROFILE, device=f"cuda:{local_rank}")
+                     flags=pic.PIC_FLAG_PROFILE, device=f"cuda:{local_rank}", j_filter=args.j_filter)
     # ---------------- end to end through the public API from (pinned) host buffers
     host = []
     for s in wl.species:
@@ -329,6 +329,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": wl.name, "grid": grid, "ppc_per_species": args.ppc,
                        "particles_per_gpu": npart, "sort_interval": args.sort,
                        "diag_interval": args.diag, "parallelism": f"replicas{world}",
+                       "j_filter": args.j_filter,
                        "l2": f"inputs larger than L2 (particles {npart * (bpp // 2) / 1e9:.1f} GB/GPU), no flush"},
             "roofline": _roofline(alg_bytes, *delta["push_deposit"], ndim=wl.ndim, npart=npart),
             "phase_ms_per_step": phase,
@@ -752,6 +753,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="warm2d", choices=["warm2d", "hot3d", "scan", "closure", "hybrid"])
     ap.add_argument("--cg-iter", type=int, default=16, help="hybrid: conjugate-gradient iterations per step")
+    ap.add_argument("--j-filter", type=int, default=0, choices=[0, 1],
+                    help="warm2d / hot3d: binomial current filter before the E update")
     ap.add_argument("--n", type=int, default=1024, help="2D grid side (warm2d)")
     ap.add_argument("--grid3", type=lambda t: tuple(int(x) for x in t.split(",")),
                     default=(256, 256, 512), help="3D grid nx,ny,nz (hot3d)")

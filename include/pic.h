@@ -85,6 +85,11 @@ typedef struct pic_config {
     int32_t flags;             /* PIC_FLAG_* */
     int32_t tile_x, tile_y, tile_z; /* 0 = default; the kernels are built for 16 x 16 (2D) and
                                        8 x 8 x 4 (3D), other values are rejected */
+    int32_t j_filter;          /* 1: smooth the step's current with one binomial 1-2-1 pass per
+                                  axis (periodic) before the E update, against numerical
+                                  Cherenkov radiation of the relativistic beam on the Yee grid
+                                  (not in the paper); the sum is exact in int64 and scaled by
+                                  4^-ndim; pic_get_fields returns the unfiltered J; 0 = off */
 } pic_config;
 
 typedef struct pic_species {

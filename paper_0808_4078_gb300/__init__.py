@@ -38,7 +38,8 @@ class Config(ctypes.Structure):
                 ("cell_capacity", ctypes.c_int32 * PIC_MAX_SPECIES), ("sort_interval", ctypes.c_int32),
                 ("diag_interval", ctypes.c_int32), ("diag_capacity", ctypes.c_int32),
                 ("track_ids", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32)]
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
+                ("j_filter", ctypes.c_int32)]
 
 
 class Species(ctypes.Structure):
@@ -184,7 +185,7 @@ class Engine:
     def __init__(self, ndim, nx=16, ny=16, nz=1, dx=0.1, dy=None, dz=None, dt=0.05, capacity=(0, 0),
                  nspecies=2, sort_interval=8, diag_interval=1, diag_capacity=4096,
                  track_ids=False, flags=0, device="cuda", stream=None, cell_capacity=(0, 0),
-                 runs=None):
+                 runs=None, j_filter=0):
         import torch
         self._torch = torch
         if not torch.cuda.is_available():
@@ -193,7 +194,8 @@ class Engine:
         ccap = (ctypes.c_int32 * PIC_MAX_SPECIES)(*[int(c) for c in cell_capacity][:PIC_MAX_SPECIES])
         self.cfg = Config(ndim, nx, ny, nz if ndim == 3 else 1, dx, dx if dy is None else dy,
                           dx if dz is None else dz, dt, nspecies, cap, ccap, sort_interval,
-                          diag_interval, diag_capacity, int(bool(track_ids)), flags, 0, 0, 0)
+                          diag_interval, diag_capacity, int(bool(track_ids)), flags, 0, 0, 0,
+                          int(j_filter))
         if runs is None:
             runs = [(nx, ny, nz if ndim == 3 else 1, tuple(capacity))]
         self.runs = [(int(a), int(b), int(c) if ndim == 3 else 1, tuple(int(x) for x in k))

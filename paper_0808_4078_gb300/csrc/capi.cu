@@ -53,7 +53,7 @@ struct Layout {
     size_t so[PIC_NS][2][3], su[PIC_NS][2][3], sid[PIC_NS][2], scount[PIC_NS][2], sicount[PIC_NS][2];
     size_t sp_cell[PIC_NS][2], sp_o[PIC_NS][2][3], sp_u[PIC_NS][2][3], sp_id[PIC_NS][2], sp_n[PIC_NS][2];
     size_t slot_region[PIC_NS][2];   // start of the contiguous slot arrays (staging view)
-    std::vector<size_t> E[3], B[3], J[3], Jlast[3], msum[3], mcnt, ubar[3];   // per run
+    std::vector<size_t> E[3], B[3], J[3], Jlast[3], Jf[3], msum[3], mcnt, ubar[3];   // per run
     std::vector<size_t> dragmap[PIC_NS];                                     // per run
     size_t start, scan_tmp, gate;
     size_t partials, hist, fit;
@@ -83,6 +83,7 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
     if (c->nspecies < 1 || c->nspecies > PIC_NS) { *err = "nspecies must be 1..2"; return PIC_EINVAL; }
     if (c->diag_interval < 0 || (c->diag_interval > 0 && c->diag_capacity < 1)) { *err = "diag_capacity must be >= 1"; return PIC_EINVAL; }
     if (c->sort_interval < 0) { *err = "sort_interval must be >= 0"; return PIC_EINVAL; }
+    if (c->j_filter != 0 && c->j_filter != 1) { *err = "j_filter must be 0 or 1"; return PIC_EINVAL; }
     g->runs.assign(nruns, RunGeo{});
     g->ncell = 0;
     g->nwork = 0;
@@ -170,6 +171,7 @@ Layout make_layout(const pic_config* c, const Geometry& g) {
         }
     for (int d = 0; d < 3; ++d) {
         L.E[d].resize(nruns); L.B[d].resize(nruns); L.J[d].resize(nruns); L.Jlast[d].resize(nruns);
+        L.Jf[d].resize(nruns);
         L.msum[d].resize(nruns); L.ubar[d].resize(nruns);
     }
     L.mcnt.resize(nruns);
@@ -180,6 +182,7 @@ Layout make_layout(const pic_config* c, const Geometry& g) {
         for (int d = 0; d < 3; ++d) L.B[d][r] = take(off, 4 * n);
         for (int d = 0; d < 3; ++d) L.J[d][r] = take(off, 8 * n);
         for (int d = 0; d < 3; ++d) L.Jlast[d][r] = (c->flags & PIC_FLAG_KEEP_J) ? take(off, 8 * n) : 0;
+        for (int d = 0; d < 3; ++d) L.Jf[d][r] = c->j_filter ? take(off, 8 * n) : 0;
         for (int d = 0; d < 3; ++d) L.msum[d][r] = take(off, 8 * n);
         L.mcnt[r] = take(off, 4 * n);
         for (int d = 0; d < 3; ++d) L.ubar[d][r] = take(off, 4 * n);
@@ -296,7 +299,7 @@ int launch_one_step(pic_ctx* ctx, long long step_index) {
         PhaseScope ps(ctx, PH_YEE);
         CK(ctx->cfg.ndim == 2 ? launch_yee2d(a, ctx->runs.data(), ctx->nruns, ctx->stream)
                               : launch_yee3d(a, ctx->runs.data(), ctx->nruns, ctx->stream));
-        ctx->launches += ctx->cfg.ndim == 2 ? 3 : 3 * ctx->nruns;
+        ctx->launches += (ctx->cfg.ndim == 2 ? 1 : ctx->nruns) * (ctx->cfg.j_filter ? 4 : 3);
     }
     {
         PhaseScope ps(ctx, PH_FINAL);
@@ -382,6 +385,7 @@ void set_species_scales(pic_ctx* ctx, RunDev& R) {
         P.jz = c.ndim == 2 ? (float)(qw * two) : (float)(-qw * (c.dz / c.dt) * two);
     }
     R.jscale = (float)std::ldexp(1.0, -R.shift);
+    R.jfscale = (float)std::ldexp(1.0, -R.shift - 2 * c.ndim);
 }
 
 int check_run(pic_ctx* ctx, int run) {
@@ -441,6 +445,7 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
             R.B[d] = at<float>(ctx, L.B[d][r]);
             R.J[d] = at<long long>(ctx, L.J[d][r]);
             R.Jlast[d] = L.Jlast[d][r] ? at<long long>(ctx, L.Jlast[d][r]) : nullptr;
+            R.Jf[d] = L.Jf[d][r] ? at<long long>(ctx, L.Jf[d][r]) : nullptr;
             R.msum[d] = nullptr;   // published when a drag species is loaded
             R.ubar[d] = nullptr;
         }
@@ -448,6 +453,7 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
         for (int sp = 0; sp < PIC_NS; ++sp) R.dragmap[sp] = nullptr;
         R.shift = 30;
         R.jscale = (float)std::ldexp(1.0, -30);
+        R.jfscale = (float)std::ldexp(1.0, -30 - 2 * c.ndim);
         for (long long t = 0; t < G.ntiles; ++t) work[G.work_off + t] = make_int2(r, (int)t);
         work_off[r] = (int)G.work_off;
     }

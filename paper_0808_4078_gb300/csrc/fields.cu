@@ -43,13 +43,18 @@ __device__ __forceinline__ void e_cell(const RunDev& R, long long c, long long d
     float* __restrict__ U0 = R.ubar[0];
     float* __restrict__ U1 = R.ubar[1];
     float* __restrict__ U2 = R.ubar[2];
-    const float cx = R.cx, cy = R.cy, cz = R.cz, js = R.jscale * dt;
+    const long long* __restrict__ F0 = R.Jf[0];
+    const long long* __restrict__ F1 = R.Jf[1];
+    const long long* __restrict__ F2 = R.Jf[2];
+    const float cx = R.cx, cy = R.cy, cz = R.cz;
+    const float js = (F0 ? R.jfscale : R.jscale) * dt;
     const long long j0 = J0[c], j1 = J1[c], j2 = J2[c];
+    const long long u0 = F0 ? F0[c] : j0, u1 = F0 ? F1[c] : j1, u2 = F0 ? F2[c] : j2;
     const float bx = Bx[c], by = By[c], bz = Bz[c];
     const float bz_ym = Bz[c - dym], bz_xm = Bz[c - dxm], by_xm = By[c - dxm], bx_ym = Bx[c - dym];
     const float by_zm = dzm ? By[c - dzm] : by, bx_zm = dzm ? Bx[c - dzm] : bx;
     const float ex = Ex[c], ey = Ey[c], ez = Ez[c];
-    const float jx = (float)j0 * js, jy = (float)j1 * js, jz = (float)j2 * js;
+    const float jx = (float)u0 * js, jy = (float)u1 * js, jz = (float)u2 * js;
     J0[c] = 0; J1[c] = 0; J2[c] = 0;
     if (L0) { L0[c] = j0; L1[c] = j1; L2[c] = j2; }
     Ex[c] = ex + (cy * (bz - bz_ym) - cz * (by - by_zm) - jx);
@@ -112,6 +117,33 @@ __global__ void __launch_bounds__(NT) yee_e_2d_tiles(Args a, float dt) {
     e_cell(R, (long long)j * nx + i, dxm, dym, 0, dt);
 }
 
+// ------------------------------------------------------------------ current filter
+// Binomial 1-2-1 pass per axis (periodic) of the three current components, as one 3^ndim
+// stencil with integer weights (1, 2, 1) x (1, 2, 1) [x (1, 2, 1)]: exact in int64; the E update
+// scales by 4^-ndim.  Reads J at the neighbours, so it runs as its own kernel before the E update
+// (which clears J).
+__device__ __forceinline__ long long row121(const long long* __restrict__ J, long long c, long long dxm, long long dxp) {
+    return J[c - dxm] + 2 * J[c] + J[c + dxp];
+}
+
+__global__ void __launch_bounds__(NT) jfilter_2d_tiles(Args a) {
+    const int2 wk = a.work[blockIdx.x];
+    const RunDev& R = a.runs[wk.x];
+    const int nx = R.nx, ny = R.ny;
+    const int i = (wk.y % R.ntx) * YTX + threadIdx.x % YTX;
+    const int j = (wk.y / R.ntx) * YTY + threadIdx.x / YTX;
+    const long long c = (long long)j * nx + i;
+    const long long dxm = i == 0 ? -(long long)(nx - 1) : 1;
+    const long long dxp = i + 1 == nx ? -(long long)(nx - 1) : 1;
+    const long long dym = j == 0 ? -(long long)(ny - 1) * nx : nx;
+    const long long dyp = j + 1 == ny ? -(long long)(ny - 1) * nx : nx;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const long long* __restrict__ J = R.J[d];
+        R.Jf[d][c] = row121(J, c - dym, dxm, dxp) + 2 * row121(J, c, dxm, dxp) + row121(J, c + dyp, dxm, dxp);
+    }
+}
+
 // ------------------------------------------------------------------ 3D Yee
 // Thread per cell on a 3D launch grid (32 x 8 threads per block along x, y; one z plane per
 // block row), so no index division; neighbours come through L1/L2.
@@ -139,6 +171,28 @@ __global__ void __launch_bounds__(Y3X * Y3Y) yee_e_3d(const RunDev* __restrict__
     const long long dym = (j == 0 ? -(long long)(ny - 1) * nx : nx);
     const long long dzm = (k == 0 ? -(long long)(nz - 1) * nxy : nxy);
     e_cell(R, k * nxy + (long long)j * nx + i, dxm, dym, dzm, dt);
+}
+
+__global__ void __launch_bounds__(Y3X * Y3Y) jfilter_3d(const RunDev* __restrict__ runs, int run) {
+    const RunDev& R = runs[run];
+    const int nx = R.nx, ny = R.ny, nz = R.nz;
+    const int i = blockIdx.x * Y3X + threadIdx.x, j = blockIdx.y * Y3Y + threadIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const long long nxy = (long long)nx * ny;
+    const long long c = k * nxy + (long long)j * nx + i;
+    const long long dxm = i == 0 ? -(long long)(nx - 1) : 1;
+    const long long dxp = i + 1 == nx ? -(long long)(nx - 1) : 1;
+    const long long dym = j == 0 ? -(long long)(ny - 1) * nx : nx;
+    const long long dyp = j + 1 == ny ? -(long long)(ny - 1) * nx : nx;
+    const long long dzm = k == 0 ? -(long long)(nz - 1) * nxy : nxy;
+    const long long dzp = k + 1 == nz ? -(long long)(nz - 1) * nxy : nxy;
+    for (int d = 0; d < 3; ++d) {
+        const long long* __restrict__ J = R.J[d];
+        auto plane = [&](long long cc) {
+            return row121(J, cc - dym, dxm, dxp) + 2 * row121(J, cc, dxm, dxp) + row121(J, cc + dyp, dxm, dxp);
+        };
+        R.Jf[d][c] = plane(c - dzm) + 2 * plane(c) + plane(c + dzp);
+    }
 }
 
 // Moments -> <u> without a field update (after loading particles).
@@ -342,8 +396,9 @@ cudaError_t preload_fields() {
     return e;
 }
 
-cudaError_t launch_yee2d(const Args& a, const RunDev*, int, cudaStream_t s) {
+cudaError_t launch_yee2d(const Args& a, const RunDev* host_runs, int, cudaStream_t s) {
     yee_b_half_2d_tiles<<<a.nwork, NT, 0, s>>>(a);
+    if (host_runs[0].Jf[0]) jfilter_2d_tiles<<<a.nwork, NT, 0, s>>>(a);
     yee_e_2d_tiles<<<a.nwork, NT, 0, s>>>(a, (float)a.dt);
     yee_b_half_2d_tiles<<<a.nwork, NT, 0, s>>>(a);
     return cudaGetLastError();
@@ -354,6 +409,7 @@ cudaError_t launch_yee3d(const Args& a, const RunDev* host_runs, int nruns, cuda
         const RunDev& R = host_runs[r];
         const dim3 grid((R.nx + Y3X - 1) / Y3X, R.ny / Y3Y, R.nz), block(Y3X, Y3Y);
         yee_b_half_3d<<<grid, block, 0, s>>>(a.runs, r);
+        if (R.Jf[0]) jfilter_3d<<<grid, block, 0, s>>>(a.runs, r);
         yee_e_3d<<<grid, block, 0, s>>>(a.runs, r, (float)a.dt);
         yee_b_half_3d<<<grid, block, 0, s>>>(a.runs, r);
     }

@@ -49,6 +49,8 @@ struct RunDev {
     float* B[3];
     long long* J[3];
     long long* Jlast[3];    // copy of the last step's J (test mode), or null
+    long long* Jf[3];       // binomially filtered J (weights summing to 4^ndim), or null
+    float jfscale;          // 2^-S / 4^ndim
     long long* msum[3];     // drag moments being accumulated (this step)
     int* mcnt;
     float* ubar[3];         // previous step's cell-mean momentum

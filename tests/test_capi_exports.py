@@ -51,6 +51,12 @@ def test_required_bytes_and_config_errors_without_gpu(libpic):
                          0, 0, 0, 0, 0)
     with pytest.raises(pic.PicError):
         pic.required_bytes(courant)
+    filt = pic.Config(2, 64, 64, 1, 0.1, 0.1, 0.1, 0.05, 2, cap(65536, 65536), ccap(), 8, 1, 100,
+                      0, 0, 0, 0, 0, 1)
+    assert pic.required_bytes(filt) >= n + 64 * 64 * 24      # the filtered current, int64 x 3
+    filt.j_filter = 2
+    with pytest.raises(pic.PicError):
+        pic.required_bytes(filt)
     tight = pic.Config(2, 64, 64, 1, 0.1, 0.1, 0.1, 0.05, 2, cap(65536, 65536), ccap(16, 16), 8, 1,
                        100, 0, 0, 0, 0, 0)
     with pytest.raises(pic.PicError):     # slots must hold 2 x the mean per cell
