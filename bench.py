@@ -621,6 +621,9 @@ def run_closure(args, rank, world, local_rank):
 # ---------------------------------------------------------------- hybrid model
 HYB_BYTES_PER_PARTICLE = 44     # read cell, ox, oy, ux, uy, P (24 B); write cell, ox, oy, ux, uy (20 B)
 HYB_BYTES_PER_NODE = 24         # read the FP32 (a, beta_p) pair once; J and N (int64) written once
+# DRAM bytes per particle of the hybrid push (ncu, 1024^2 nodes x 8 ppc, scaled by particles):
+# profiles/hybrid_push_deposit_1024x1024.md
+HYB_NCU_TRAFFIC_PER_PARTICLE = (226.725632e6 + 126.075904e6) / 8388608
 
 
 def _hybrid_load(args, rank=0):
@@ -667,7 +670,7 @@ def run_hybrid(args, rank, world, local_rank):
 
     def make(flags):
         return pic.HybridEngine(nx, ny, L.dx, L.dx, L.dt, 1.0, L.nu, L.w, n, max_iter=args.cg_iter,
-                                flags=flags, device=f"cuda:{local_rank}")
+                                flags=flags, sort_interval=args.hybrid_sort, device=f"cuda:{local_rank}")
 
     # ---------------- end to end through the public API from host buffers
     eng = make(0)
@@ -724,10 +727,14 @@ def run_hybrid(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"hybrid_beam_2d_{nx}x{ny}_ppc{args.ppc}", "grid": [nx, ny],
                        "ppc": args.ppc, "particles_per_gpu": n, "cg_max_iter": args.cg_iter,
+                       "sort_interval": args.hybrid_sort or 16,
                        "parallelism": f"replicas{world}",
                        "l2": f"particles {n * 24 / 1e9:.2f} GB > L2, no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "hybrid push_deposit",
+                         "frac": achieved / peak, "traffic": HYB_NCU_TRAFFIC_PER_PARTICLE * n,
+                         "traffic_source": "ncu DRAM bytes of the 8-ppc case scaled by particles: "
+                                           "profiles/hybrid_push_deposit_1024x1024.md",
+                         "kernel": "hybrid push_deposit",
                          "peak_kind": peak_kind, "alg_bytes_per_launch": alg,
                          "mean_launch_ms": push_ms},
             "phase_ms_per_step": phase,
@@ -753,6 +760,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="warm2d", choices=["warm2d", "hot3d", "scan", "closure", "hybrid"])
     ap.add_argument("--cg-iter", type=int, default=16, help="hybrid: conjugate-gradient iterations per step")
+    ap.add_argument("--hybrid-sort", type=int, default=0, help="hybrid: steps between sorts by cell (0 = 16)")
     ap.add_argument("--j-filter", type=int, default=0, choices=[0, 1],
                     help="warm2d / hot3d: binomial current filter before the E update")
     ap.add_argument("--n", type=int, default=1024, help="2D grid side (warm2d)")

@@ -256,6 +256,8 @@ int pic_dispersion_growth(const double* params, int32_t nsets, double kmin, doub
  * n_p = max(n0 - n_b, 0) per node (FP64 residual, FP32 conjugate-gradient correction
  * preconditioned by the constant-density spectral solve, stopped at a relative residual of tol or
  * after max_iter iterations) and updates beta_p^{n+1} = beta_p^n + a^{n+1} - a^n - nu dt beta_p^n.
+ * The beam is kept in cell order by a counting sort every sort_interval steps; deposits are exact
+ * integer sums, so results do not depend on the order.  Particle read-back is in the load order.
  * Steps replay a CUDA graph of one step unless a flag asks otherwise.  Host arrays are copied
  * during the calls; the arena (pic_hybrid_required_bytes, 256-byte aligned) and the stream belong
  * to the caller.  Deterministic: results do not depend on particle order or scheduling. */
@@ -270,6 +272,8 @@ typedef struct pic_hybrid_config {
     double tol;                 /* relative residual of the solve; 0 = 1e-5 */
     int32_t max_iter;           /* conjugate-gradient iterations per step; 0 = 16, <= 1000 */
     int32_t flags;              /* PIC_FLAG_PROFILE (phase timing, no graph), PIC_FLAG_NO_GRAPH */
+    int32_t sort_interval;      /* steps between counting sorts of the beam by cell (keeps the
+                                   deposit's lanes on shared cells); 0 = 16 */
 } pic_hybrid_config;
 int pic_hybrid_required_bytes(const pic_hybrid_config* cfg, size_t* bytes_out);
 int pic_hybrid_init(const pic_hybrid_config* cfg, void* device_arena, size_t arena_bytes,
@@ -291,12 +295,13 @@ int pic_hybrid_energies(pic_hybrid* h, double out3[3]);
  * iterations of the last step}.  Synchronises. */
 int pic_hybrid_stats(pic_hybrid* h, int64_t out4[4]);
 /* With PIC_FLAG_PROFILE: CUDA-event time on the stream per phase ("push_deposit", "field_solve",
- * "update"), accumulated over the steps so far; same record as pic_kernel_times.  Synchronises. */
+ * "update", "sort"), accumulated over the steps so far; same record as pic_kernel_times.
+ * Synchronises. */
 int pic_hybrid_kernel_times(pic_hybrid* h, pic_kernel_time* out, int max, int* n_out);
 /* Kernels launched by pic_hybrid_step so far: per step the push, the solve set-up and the update,
- * and per conjugate-gradient iteration 7 kernels (8 in a graph, whose while node runs only the
- * iterations needed; direct launches run max_iter, returning at once after convergence).
- * Synchronises; -1 on error. */
+ * per conjugate-gradient iteration 7 kernels (8 in a graph, whose while node runs only the
+ * iterations needed; direct launches run max_iter, returning at once after convergence), and 8
+ * per sort.  Synchronises; -1 on error. */
 int64_t pic_hybrid_launch_count(pic_hybrid* h);
 int64_t pic_hybrid_step_count(const pic_hybrid* h);
 void pic_hybrid_free(pic_hybrid* h);

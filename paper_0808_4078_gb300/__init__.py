@@ -70,7 +70,8 @@ class HybridConfig(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("dx", ctypes.c_double),
                 ("dy", ctypes.c_double), ("dt", ctypes.c_double), ("n0", ctypes.c_double),
                 ("nu", ctypes.c_double), ("w", ctypes.c_double), ("capacity", ctypes.c_int64),
-                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("sort_interval", ctypes.c_int32)]
 
 
 class MlpNorm(ctypes.Structure):
@@ -487,10 +488,11 @@ class HybridEngine:
     """The quasi-neutral hybrid model (pic_hybrid_*): arena and stream from PyTorch."""
 
     def __init__(self, nx, ny, dx, dy, dt, n0, nu, w, capacity, tol=0.0, max_iter=0, flags=0,
-                 device="cuda"):
+                 sort_interval=0, device="cuda"):
         import torch
         self._torch = torch
-        self.cfg = HybridConfig(nx, ny, dx, dy, dt, n0, nu, w, capacity, tol, max_iter, flags)
+        self.cfg = HybridConfig(nx, ny, dx, dy, dt, n0, nu, w, capacity, tol, max_iter, flags,
+                                sort_interval)
         nb = ctypes.c_size_t(0)
         _check(lib().pic_hybrid_required_bytes(ctypes.byref(self.cfg), ctypes.byref(nb)))
         self.device = torch.device(device)
@@ -545,9 +547,9 @@ class HybridEngine:
                     last_iterations=int(out[3]))
 
     def kernel_times(self):
-        recs = (KernelTime * 3)()
+        recs = (KernelTime * 4)()
         n = ctypes.c_int(0)
-        _check(lib().pic_hybrid_kernel_times(self._h, ctypes.cast(recs, _VP), 3, ctypes.byref(n)))
+        _check(lib().pic_hybrid_kernel_times(self._h, ctypes.cast(recs, _VP), 4, ctypes.byref(n)))
         return {recs[i].name.decode(): (int(recs[i].launches), float(recs[i].total_ms)) for i in range(n.value)}
 
     def launch_count(self):

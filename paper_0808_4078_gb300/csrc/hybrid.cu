@@ -41,8 +41,8 @@ namespace pic {
 namespace {
 
 constexpr double JFIX = 1099511627776.0;   // 2^40
-constexpr float JFIXF = 1099511627776.0f;
 constexpr int NT = 256;
+constexpr int WIN = 256;                   // nodes per deposit window of the push
 constexpr int RGRID = 8 * 152;             // blocks of the reducing node kernels (full occupancy)
 
 // scalar slots of the solver state (device doubles)
@@ -55,8 +55,13 @@ struct HybDev {
     double dxd, dyd, dtd, n0, nu, tol2;
     double idx1, idy1, idx2, idy2;  // 1/dx, 1/dy, 1/dx^2, 1/dy^2 (FP64): no FP64 division on the device
     long long n;
-    // particles
-    int* cell; float* ox; float* oy; float* ux; float* uy; float* P;
+    // particles (and the second buffer the periodic sort permutes into)
+    int* cell; float* ox; float* oy; float* ux; float* uy; float* P; int* id;
+    int* cell2; float* ox2; float* oy2; float* ux2; float* uy2; float* P2; int* id2;
+    int* order; int* start; int* bscratch;   // counting sort by cell
+    float sfix;                     // 2^S32: per-particle deposit terms as int32 at this scale
+    int sshift;                     // 40 - S32: int32 group sums shifted into the 2^40 grids
+    long long* ebeam;               // fixed-point beam-energy partials
     // grid
     double* a; double* bp;          // [ny][nx]
     float2* f32;                    // (a, beta_p) in FP32 for the gather
@@ -205,39 +210,22 @@ __device__ __forceinline__ void red_add(long long* p, long long v) {
     atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
 }
 
-// x rounded to the nearest int64 (ties to even) through 32-bit conversions only: the 64-bit
-// conversion runs on the FP64 unit, which this part has little of.  With a = |x|,
-// hi = floor(a 2^-32) and a - hi 2^32 are exact in FP32 (either hi = 0, or ulp(a) >= 2^9), so
-// hi 2^32 + rint(a - hi 2^32) = rint(a); valid for |x| < 2^62.
-__device__ __forceinline__ long long to_fixed(float x) {
-    const float a = fabsf(x);
-    const float hi = floorf(a * 2.3283064365386963e-10f);
-    const unsigned lo = __float2uint_rn(a - hi * 4294967296.0f);
-    const long long v = (long long)__float2uint_rz(hi) * 4294967296LL + (long long)lo;
-    return x < 0.0f ? -v : v;
-}
-
-// Sum of v over this lane's run of consecutive lanes with equal keys (seg_end = the run's last
-// lane), valid at the run's first lane: a suffix scan that never crosses a run boundary.
-__device__ __forceinline__ float run_sum(float v, int lane, int seg_end) {
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const float t = __shfl_down_sync(0xffffffffu, v, off);
-        if (lane + off <= seg_end) v += t;
-    }
-    return v;
-}
-
 // Push (move = 1) or only deposit (move = 0): gather, Eq. 4 and Eq. 6, move, and the CIC deposit
-// of density w and current w beta_z at the new position with the old a.  Particles loaded in
-// cell order stay nearly so (they cross a cell in tens of steps), so consecutive lanes mostly
-// share a cell: each run of equal cells in a warp is summed in FP32 by shuffles (fixed lane
-// order, hence reproducible) and its first lane adds the run's eight sums to the int64 grids.
+// of density w and current w beta_z at the new position with the old a.  The particles are kept
+// in cell order by a periodic counting sort (they cross a cell in tens of steps), so a CTA's chunk
+// of NT particles covers a few dozen neighbouring cells: its integer terms are summed with shared
+// atomics in two windows of nodes (from the chunk's lowest cell, and one row up) whose nonzero
+// entries are then added to the int64 grids; nodes outside the windows go straight to the grids.
 __global__ void __launch_bounds__(NT) push_kernel(const HybDev h, int move) {
+    // two node windows x (current, density), int32 at 2^S32
+    __shared__ int win[4][WIN];
+    __shared__ int wmins[NT / 32];
+    for (int e = threadIdx.x; e < 4 * WIN; e += NT) (&win[0][0])[e] = 0;
     const long long stride = (long long)gridDim.x * NT;
     const int lane = threadIdx.x & 31;
-    for (long long base = blockIdx.x * (long long)NT + (threadIdx.x & ~31); base < h.n; base += stride) {
-        const long long p = base + lane;
+    // block-uniform chunks of NT particles (the window passes below synchronise the block)
+    for (long long base = blockIdx.x * (long long)NT; base < h.n; base += stride) {
+        const long long p = base + threadIdx.x;
         const bool act = p < h.n;
         int cell = 0;
         float ox = 0.f, oy = 0.f, ux = 0.f, uy = 0.f, P = 0.f;
@@ -275,50 +263,73 @@ __global__ void __launch_bounds__(NT) push_kernel(const HybDev h, int move) {
         }
         const Node4 c = nodes(h, cell, ox, oy);
         const float gx0 = 1.0f - c.fx, gy0 = 1.0f - c.fy;
-        float w00 = 0.f, w10 = 0.f, w01 = 0.f, w11 = 0.f, q = 0.f;
+        // per-particle terms as int32 at 2^S32 (exact integer sums from here on, so the grids do
+        // not depend on particle order): density w S and current w beta_z S per node
+        int v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (act) {
             const float av = gy0 * (gx0 * h.f32[c.c00].x + c.fx * h.f32[c.c10].x) +
                              c.fy * (gx0 * h.f32[c.c01].x + c.fx * h.f32[c.c11].x);
             const float uzs = P + av;
-            q = uzs / sqrtf(1.0f + ux * ux + uy * uy + uzs * uzs);
-            w00 = gx0 * gy0; w10 = c.fx * gy0; w01 = gx0 * c.fy; w11 = c.fx * c.fy;
-        }
-        // runs of equal cells (inactive lanes get keys of their own)
-        const int key = act ? cell : -1 - lane;
-        const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-        const bool head = lane == 0 || prev != key;
-        const unsigned heads = __ballot_sync(0xffffffffu, head);
-        if (heads == 0xffffffffu) {   // no two neighbours share a cell: deposit per particle
-            if (act) {
-                const float sq = h.w * JFIXF, sw = h.w * JFIXF;   // same rounding as a run of one
-                red_add(&h.J[c.c00], to_fixed(sq * (q * w00)));
-                red_add(&h.J[c.c10], to_fixed(sq * (q * w10)));
-                red_add(&h.J[c.c01], to_fixed(sq * (q * w01)));
-                red_add(&h.J[c.c11], to_fixed(sq * (q * w11)));
-                red_add(&h.N[c.c00], to_fixed(sw * w00));
-                red_add(&h.N[c.c10], to_fixed(sw * w10));
-                red_add(&h.N[c.c01], to_fixed(sw * w01));
-                red_add(&h.N[c.c11], to_fixed(sw * w11));
+            const float q = uzs / sqrtf(1.0f + ux * ux + uy * uy + uzs * uzs);
+            const float sw = h.w * h.sfix, sq = sw * q;
+            const float w4[4] = {gx0 * gy0, c.fx * gy0, gx0 * c.fy, c.fx * c.fy};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v[k] = __float2int_rn(sq * w4[k]);
+                v[4 + k] = __float2int_rn(sw * w4[k]);
             }
-            continue;
         }
-        const unsigned later = lane == 31 ? 0u : (heads & (0xffffffffu << (lane + 1)));
-        const int seg_end = later ? __ffs(later) - 2 : 31;
-        const float s00 = run_sum(w00, lane, seg_end), s10 = run_sum(w10, lane, seg_end);
-        const float s01 = run_sum(w01, lane, seg_end), s11 = run_sum(w11, lane, seg_end);
-        const float j00 = run_sum(q * w00, lane, seg_end), j10 = run_sum(q * w10, lane, seg_end);
-        const float j01 = run_sum(q * w01, lane, seg_end), j11 = run_sum(q * w11, lane, seg_end);
-        if (act && head) {
-            const float sq = h.w * JFIXF, sw = h.w * JFIXF;
-            red_add(&h.J[c.c00], to_fixed(sq * j00));
-            red_add(&h.J[c.c10], to_fixed(sq * j10));
-            red_add(&h.J[c.c01], to_fixed(sq * j01));
-            red_add(&h.J[c.c11], to_fixed(sq * j11));
-            red_add(&h.N[c.c00], to_fixed(sw * s00));
-            red_add(&h.N[c.c10], to_fixed(sw * s10));
-            red_add(&h.N[c.c01], to_fixed(sw * s01));
-            red_add(&h.N[c.c11], to_fixed(sw * s11));
+        // the chunk's lowest cell anchors two windows of nodes: [cmin, cmin + WIN) and the same
+        // columns one row up; particles kept in cell order by the periodic sort land in them
+        const int wmin = __reduce_min_sync(0xffffffffu, act ? cell : 0x7fffffff);
+        if (lane == 0) wmins[threadIdx.x >> 5] = wmin;
+        __syncthreads();
+        int cmin = wmins[0];
+#pragma unroll
+        for (int wi = 1; wi < NT / 32; ++wi) cmin = min(cmin, wmins[wi]);
+        if (act) {
+            const int nd[4] = {c.c00, c.c10, c.c01, c.c11};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int o = nd[k] - cmin;
+                int* slot = nullptr;
+                if (o >= 0 && o < WIN) slot = &win[0][o];
+                else if (o - h.nx >= 0 && o - h.nx < WIN) slot = &win[1][o - h.nx];
+                if (slot) {
+                    if (v[k]) atomicAdd(slot, v[k]);
+                    if (v[4 + k]) atomicAdd(slot + 2 * WIN, v[4 + k]);
+                } else {   // outside the windows: straight to the grids
+                    if (v[k]) red_add(&h.J[nd[k]], (long long)v[k] << h.sshift);
+                    if (v[4 + k]) red_add(&h.N[nd[k]], (long long)v[4 + k] << h.sshift);
+                }
+            }
         }
+        __syncthreads();
+        // flush the windows' nonzero entries and clear them for the next chunk
+        for (int e = threadIdx.x; e < 2 * WIN; e += NT) {
+            const int node = cmin + (e < WIN ? e : h.nx + e - WIN);
+            int* wj = &win[0][0] + e;
+            int* wn = wj + 2 * WIN;
+            const int sj = *wj, sn = *wn;
+            if (sj) { red_add(&h.J[node], (long long)sj << h.sshift); *wj = 0; }
+            if (sn) { red_add(&h.N[node], (long long)sn << h.sshift); *wn = 0; }
+        }
+        __syncthreads();
+    }
+}
+
+// Sort support: gather the particle arrays into the second buffer in cell order, then copy back.
+__global__ void __launch_bounds__(NT) permute_kernel(const HybDev h) {
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < h.n; i += (long long)gridDim.x * NT) {
+        const int q = h.order[i];
+        h.cell2[i] = h.cell[q]; h.ox2[i] = h.ox[q]; h.oy2[i] = h.oy[q];
+        h.ux2[i] = h.ux[q]; h.uy2[i] = h.uy[q]; h.P2[i] = h.P[q]; h.id2[i] = h.id[q];
+    }
+}
+__global__ void __launch_bounds__(NT) copy_back_kernel(const HybDev h) {
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < h.n; i += (long long)gridDim.x * NT) {
+        h.cell[i] = h.cell2[i]; h.ox[i] = h.ox2[i]; h.oy[i] = h.oy2[i];
+        h.ux[i] = h.ux2[i]; h.uy[i] = h.uy2[i]; h.P[i] = h.P2[i]; h.id[i] = h.id2[i];
     }
 }
 
@@ -372,7 +383,7 @@ __global__ void fft_rows_inv_z_kernel(const HybDev h) {
     extern __shared__ float2 fsh[];
     __shared__ double rzs[1024];
     __shared__ double rz32[32];
-    if (threadIdx.x < 32) rz32[threadIdx.x] = 0.0;   // rows shorter than 64 run fewer than 32 threads
+    const int nw = blockDim.x < 32 ? (int)blockDim.x : 32;   // rows shorter than 64 run fewer threads
     const int N = h.nx;
     const float2* row = h.ws0 + (size_t)blockIdx.x * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) fsh[i] = row[i];
@@ -397,7 +408,7 @@ __global__ void fft_rows_inv_z_kernel(const HybDev h) {
     __shared__ bool last;
     if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int t = 0; t < 32; ++t) s += rz32[t];
+        for (int t = 0; t < nw; ++t) s += rz32[t];
         h.part[blockIdx.x] = s;
         __threadfence();
         last = atomicAdd(h.ticket, 1u) == gridDim.x - 1;
@@ -418,7 +429,7 @@ __global__ void fft_rows_inv_z_kernel(const HybDev h) {
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot = 0.0;
-        for (int t = 0; t < 32; ++t) tot += rz32[t];
+        for (int t = 0; t < nw; ++t) tot += rz32[t];
         *h.ticket = 0u;
         const double it = h.S[S_ITER];
         h.S[S_BETA] = it == 0.0 ? 0.0 : tot / h.S[S_RZ];
@@ -515,7 +526,9 @@ __global__ void __launch_bounds__(NT) energy_kernel(const HybDev h) {
         e[0] += 0.5 * (ax * ax + ay * ay);
         e[2] += 0.5 * (double)h.np[c] * h.bp[c] * h.bp[c];
     }
-    // beam: gamma - 1 in FP32 per particle (the FP64 unit is scarce), summed in FP64
+    // beam: gamma - 1 in FP32 per particle (the FP64 unit is scarce), summed exactly in fixed
+    // point (integer part and 30 fraction bits), so the sum does not depend on particle order
+    long long eb = 0;
     for (long long p = blockIdx.x * (long long)NT + threadIdx.x; p < h.n; p += (long long)gridDim.x * NT) {
         const Node4 c = nodes(h, h.cell[p], h.ox[p], h.oy[p]);
         const float gx0 = 1.0f - c.fx, gy0 = 1.0f - c.fy;
@@ -523,17 +536,23 @@ __global__ void __launch_bounds__(NT) energy_kernel(const HybDev h) {
                          c.fy * (gx0 * h.f32[c.c01].x + c.fx * h.f32[c.c11].x);
         const float uz = h.P[p] + av, ux = h.ux[p], uy = h.uy[p];
         const float u2 = ux * ux + uy * uy + uz * uz;
-        e[1] += (double)(u2 / (1.0f + sqrtf(1.0f + u2)));   // gamma - 1 without cancellation
+        const float gm1 = u2 / (1.0f + sqrtf(1.0f + u2));   // gamma - 1 without cancellation
+        const float ip = floorf(gm1);
+        eb += (long long)(int)ip * 1073741824LL + (long long)__float2int_rn((gm1 - ip) * 1073741824.0f);
     }
-    e[1] *= (double)h.w;
+    __shared__ long long redb[NT];
+    redb[threadIdx.x] = eb;
     for (int k = 0; k < 3; ++k) red[threadIdx.x][k] = e[k];
     __syncthreads();
     for (int o = NT / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o)
+        if (threadIdx.x < o) {
             for (int k = 0; k < 3; ++k) red[threadIdx.x][k] += red[threadIdx.x + o][k];
+            redb[threadIdx.x] += redb[threadIdx.x + o];
+        }
         __syncthreads();
     }
     if (threadIdx.x < 3) h.part[blockIdx.x * 3 + threadIdx.x] = red[0][threadIdx.x];
+    if (threadIdx.x == 0) h.ebeam[blockIdx.x] = redb[0];
 }
 
 int gridn(long long n) {
@@ -564,17 +583,20 @@ struct pic_hybrid {
     long long steps = 0;
     long long direct_launches = 0;   // kernels of directly launched steps
     long long graph_steps = 0;       // steps replayed as a graph (their CG loops vary in length)
+    long long sorts = 0;
     int max_iter = 0;
-    // one step captured as a CUDA graph (rebuilt after a load changes the kernel arguments)
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
+    int sort_interval = 16;          // steps between counting sorts of the particles by cell
+    // one step captured as a CUDA graph, plain and with the sort in front (rebuilt after a load
+    // changes the kernel arguments)
+    cudaGraph_t graph = nullptr, graph_s = nullptr;
+    cudaGraphExec_t graph_exec = nullptr, graph_exec_s = nullptr;
     bool graph_dirty = true;
     // phase timing (flag PIC_FLAG_PROFILE): event pairs resolved by pic_hybrid_kernel_times
     struct Ev { int phase; cudaEvent_t a, b; };
     std::vector<Ev> pending;
     std::vector<cudaEvent_t> pool;
-    double phase_ms[3] = {0, 0, 0};
-    long long phase_n[3] = {0, 0, 0};
+    double phase_ms[4] = {0, 0, 0, 0};
+    long long phase_n[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -600,7 +622,7 @@ int hfail(int code, const char* fmt, ...) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct HLayout {
-    size_t cell, ox, oy, ux, uy, P;
+    size_t cell, ox, oy, ux, uy, P, id, cell2, ox2, oy2, ux2, uy2, P2, id2, order, start, bscratch, ebeam;
     size_t a, bp, f32, J, N, np, d, r, z, q, p0, p1, ws0, ws1, twx, twy, lamx, lamy, S, part, ticket, total;
 };
 HLayout hlayout(const pic_hybrid_config* c) {
@@ -609,7 +631,11 @@ HLayout hlayout(const pic_hybrid_config* c) {
     const size_t nc = (size_t)c->nx * c->ny, np = (size_t)c->capacity;
     auto take = [&](size_t bytes) { off = align256(off); size_t at = off; off += bytes; return at; };
     L.cell = take(4 * np); L.ox = take(4 * np); L.oy = take(4 * np);
-    L.ux = take(4 * np); L.uy = take(4 * np); L.P = take(4 * np);
+    L.ux = take(4 * np); L.uy = take(4 * np); L.P = take(4 * np); L.id = take(4 * np);
+    L.cell2 = take(4 * np); L.ox2 = take(4 * np); L.oy2 = take(4 * np);
+    L.ux2 = take(4 * np); L.uy2 = take(4 * np); L.P2 = take(4 * np); L.id2 = take(4 * np);
+    L.order = take(4 * np); L.start = take(4 * (nc + 1)); L.bscratch = take(pic::bin_cells_scratch_bytes((long long)nc));
+    L.ebeam = take(8 * (size_t)RGRID);
     L.a = take(8 * nc); L.bp = take(8 * nc); L.f32 = take(8 * nc); L.J = take(8 * nc); L.N = take(8 * nc);
     L.np = take(4 * nc); L.d = take(4 * nc); L.r = take(4 * nc); L.z = take(4 * nc); L.q = take(4 * nc);
     L.p0 = take(4 * nc); L.p1 = take(4 * nc); L.ws0 = take(8 * nc); L.ws1 = take(8 * nc);
@@ -629,10 +655,12 @@ int check_cfg(const pic_hybrid_config* c) {
     if (c->capacity < 0 || c->capacity > (int64_t)1 << 31) return hfail(PIC_EINVAL, "capacity must be in [0, 2^31]");
     if (c->tol < 0 || c->max_iter < 0 || c->max_iter > 1000) return hfail(PIC_EINVAL, "need tol >= 0, max_iter in [0, 1000]");
     if (c->flags & ~(PIC_FLAG_PROFILE | PIC_FLAG_NO_GRAPH)) return hfail(PIC_EINVAL, "unknown flags");
+    if (c->sort_interval < 0) return hfail(PIC_EINVAL, "sort_interval must be >= 0");
+    if (!(c->w <= 1e6)) return hfail(PIC_EINVAL, "w must be <= 1e6");
     return PIC_OK;
 }
 
-const char* const kHybPhase[3] = {"push_deposit", "field_solve", "update"};
+const char* const kHybPhase[4] = {"push_deposit", "field_solve", "update", "sort"};
 
 cudaEvent_t get_event(pic_hybrid* h) {
     if (!h->pool.empty()) {
@@ -674,6 +702,17 @@ void launch_pre(pic_hybrid* h) {
     if (d.n > 0) push_kernel<<<gridn(d.n), NT, 0, h->stream>>>(d, 1);
 }
 
+// Counting sort of the particles by cell (the library's binning: histogram, scan, scatter of
+// indices), then a gather into the second buffer and a copy back: 6 launches.
+void launch_sort(pic_hybrid* h) {
+    HybDev& d = h->d;
+    if (d.n == 0) return;
+    pic::launch_bin_cells(d.cell, d.n, d.nx * d.ny, d.start, d.order, d.bscratch, h->stream);
+    permute_kernel<<<gridn(d.n), NT, 0, h->stream>>>(d);
+    copy_back_kernel<<<gridn(d.n), NT, 0, h->stream>>>(d);
+}
+constexpr int SORT_LAUNCHES = 8;   // 6 of the binning (zero, histogram, 3 scan passes, scatter) + 2
+
 void launch_rhs(pic_hybrid* h) {
     HybDev& d = h->d;
     rhs_kernel<<<gridr((long long)d.nx * d.ny), NT, 0, h->stream>>>(d);
@@ -700,8 +739,12 @@ void launch_post(pic_hybrid* h) {
     update_kernel<<<gridr((long long)d.nx * d.ny), NT, 0, h->stream>>>(d);
 }
 
-// Push and deposit, the solve (max_iter CG iterations, early-exiting kernels), the update.
-int launch_step(pic_hybrid* h) {
+// (Sort,) push and deposit, the solve (max_iter CG iterations, early-exiting kernels), the update.
+int launch_step(pic_hybrid* h, bool sort) {
+    if (sort) {
+        HPhase ps(h, 3);
+        launch_sort(h);
+    }
     {
         HPhase ph(h, 0);
         launch_pre(h);
@@ -722,19 +765,20 @@ int launch_step(pic_hybrid* h) {
 void drop_graph(pic_hybrid* h) {
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->graph) cudaGraphDestroy(h->graph);
-    h->graph_exec = nullptr;
-    h->graph = nullptr;
+    if (h->graph_exec_s) cudaGraphExecDestroy(h->graph_exec_s);
+    if (h->graph_s) cudaGraphDestroy(h->graph_s);
+    h->graph_exec = h->graph_exec_s = nullptr;
+    h->graph = h->graph_s = nullptr;
     h->graph_dirty = true;
 }
 
 // One step as a graph: push and solve set-up, a while node whose body is one CG iteration plus
 // the loop control (the loop runs only the iterations the solve needs, at most max_iter), then
 // the update.  Each part is captured from the stream into the graph.
-int build_graph(pic_hybrid* h) {
-    drop_graph(h);
+int build_one_graph(pic_hybrid* h, bool sort, cudaGraph_t* gout, cudaGraphExec_t* xout) {
     cudaGraph_t g = nullptr;
     HCK(cudaGraphCreate(&g, 0));
-    h->graph = g;
+    *gout = g;
     cudaGraphConditionalHandle cond{};
     HCK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
     const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
@@ -757,7 +801,11 @@ int build_graph(pic_hybrid* h) {
         return cudaGetLastError();
     };
     std::vector<cudaGraphNode_t> pre;
-    cudaError_t e = capture(g, nullptr, 0, [&] { launch_pre(h); launch_rhs(h); }, &pre);
+    cudaError_t e = capture(g, nullptr, 0, [&] {
+        if (sort) launch_sort(h);
+        launch_pre(h);
+        launch_rhs(h);
+    }, &pre);
     if (e != cudaSuccess) { drop_graph(h); return hfail(PIC_ECUDA, "graph capture (push): %s", cudaGetErrorString(e)); }
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
@@ -776,10 +824,17 @@ int build_graph(pic_hybrid* h) {
     if (e != cudaSuccess) { drop_graph(h); return hfail(PIC_ECUDA, "graph capture (solve): %s", cudaGetErrorString(e)); }
     e = capture(g, &loop, 1, [&] { launch_post(h); }, nullptr);
     if (e != cudaSuccess) { drop_graph(h); return hfail(PIC_ECUDA, "graph capture (update): %s", cudaGetErrorString(e)); }
-    e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+    e = cudaGraphInstantiate(xout, g, 0);
     if (e != cudaSuccess) { drop_graph(h); return hfail(PIC_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
-    h->graph_dirty = false;
     return PIC_OK;
+}
+
+int build_graph(pic_hybrid* h) {
+    drop_graph(h);
+    int rc = build_one_graph(h, false, &h->graph, &h->graph_exec);
+    if (rc == PIC_OK) rc = build_one_graph(h, true, &h->graph_s, &h->graph_exec_s);
+    if (rc == PIC_OK) h->graph_dirty = false;
+    return rc;
 }
 
 }  // namespace
@@ -822,6 +877,24 @@ extern "C" int pic_hybrid_init(const pic_hybrid_config* cfg, void* arena, size_t
     auto F = [&](size_t o) { return reinterpret_cast<float*>(base + o); };
     d.cell = reinterpret_cast<int*>(base + L.cell);
     d.ox = F(L.ox); d.oy = F(L.oy); d.ux = F(L.ux); d.uy = F(L.uy); d.P = F(L.P);
+    d.id = reinterpret_cast<int*>(base + L.id);
+    d.cell2 = reinterpret_cast<int*>(base + L.cell2);
+    d.ox2 = F(L.ox2); d.oy2 = F(L.oy2); d.ux2 = F(L.ux2); d.uy2 = F(L.uy2); d.P2 = F(L.P2);
+    d.id2 = reinterpret_cast<int*>(base + L.id2);
+    d.order = reinterpret_cast<int*>(base + L.order);
+    d.start = reinterpret_cast<int*>(base + L.start);
+    d.bscratch = reinterpret_cast<int*>(base + L.bscratch);
+    d.ebeam = reinterpret_cast<long long*>(base + L.ebeam);
+    h->sort_interval = cfg->sort_interval > 0 ? cfg->sort_interval : 16;
+    // deposit terms: |term| <= w, and a window entry sums at most NT of them below 2^31:
+    // 2^S32 <= 2^31 / (NT w); S32 <= 40 (the grids' scale) so the sums enter the grids by a shift
+    {
+        int s32 = 40;
+        const double lim = 2147483647.0 / (double)NT;
+        while (s32 > 0 && cfg->w * std::ldexp(1.0, s32) >= lim) --s32;
+        d.sfix = (float)std::ldexp(1.0, s32);
+        d.sshift = 40 - s32;
+    }
     d.a = reinterpret_cast<double*>(base + L.a);
     d.bp = reinterpret_cast<double*>(base + L.bp);
     d.f32 = reinterpret_cast<float2*>(base + L.f32);
@@ -899,12 +972,17 @@ extern "C" int pic_hybrid_load(pic_hybrid* h, int64_t n, const double* X, const 
     HCK(cudaMemcpyAsync(d.ux, fux.data(), 4 * n, cudaMemcpyHostToDevice, h->stream));
     HCK(cudaMemcpyAsync(d.uy, fuy.data(), 4 * n, cudaMemcpyHostToDevice, h->stream));
     HCK(cudaMemcpyAsync(d.P, fP.data(), 4 * n, cudaMemcpyHostToDevice, h->stream));
+    std::vector<int> ids(n);
+    for (int64_t p = 0; p < n; ++p) ids[p] = (int)p;
+    HCK(cudaMemcpyAsync(d.id, ids.data(), 4 * n, cudaMemcpyHostToDevice, h->stream));
     HCK(cudaMemcpyAsync(d.bp, beta_p, 8 * nc, cudaMemcpyHostToDevice, h->stream));
     HCK(cudaMemcpyAsync(d.f32, f32.data(), 8 * nc, cudaMemcpyHostToDevice, h->stream));
     HCK(cudaMemsetAsync(d.a, 0, 8 * nc, h->stream));
     HCK(cudaMemsetAsync(d.J, 0, 8 * nc, h->stream));
     HCK(cudaMemsetAsync(d.N, 0, 8 * nc, h->stream));
     HCK(cudaMemsetAsync(d.S, 0, 8 * S_NSLOT, h->stream));
+    launch_sort(h);   // cell order from the start, whatever the caller's order
+    HCK(cudaGetLastError());
     if (n > 0) push_kernel<<<gridn(n), NT, 0, h->stream>>>(d, 0);
     density_kernel<<<gridn((long long)nc), NT, 0, h->stream>>>(d);
     HCK(cudaGetLastError());
@@ -919,18 +997,20 @@ extern "C" int pic_hybrid_step(pic_hybrid* h, int nsteps) {
     if (nsteps < 0) return hfail(PIC_EINVAL, "nsteps must be >= 0");
     const bool use_graph = !(h->cfg.flags & (PIC_FLAG_PROFILE | PIC_FLAG_NO_GRAPH));
     for (int s = 0; s < nsteps; ++s) {
+        const bool sort = h->sort_interval > 0 && h->d.n > 0 && h->steps > 0 && h->steps % h->sort_interval == 0;
         if (use_graph) {
             if (h->graph_dirty) {
                 int rc = build_graph(h);
                 if (rc) return rc;
             }
-            HCK(cudaGraphLaunch(h->graph_exec, h->stream));
+            HCK(cudaGraphLaunch(sort ? h->graph_exec_s : h->graph_exec, h->stream));
             ++h->graph_steps;
         } else {
-            int rc = launch_step(h);
+            int rc = launch_step(h, sort);
             if (rc) return rc;
             h->direct_launches += step_launches(h, h->max_iter, false);
         }
+        if (sort) { h->direct_launches += SORT_LAUNCHES; ++h->sorts; }
         ++h->steps;
     }
     return PIC_OK;
@@ -949,7 +1029,7 @@ extern "C" int pic_hybrid_kernel_times(pic_hybrid* h, pic_kernel_time* out, int 
     }
     h->pending.clear();
     int n = 0;
-    for (int p = 0; p < 3 && n < max && out; ++p, ++n) {
+    for (int p = 0; p < 4 && n < max && out; ++p, ++n) {
         std::snprintf(out[n].name, sizeof out[n].name, "%s", kHybPhase[p]);
         out[n].launches = h->phase_n[p];
         out[n].total_ms = h->phase_ms[p];
@@ -977,19 +1057,22 @@ extern "C" int pic_hybrid_get(pic_hybrid* h, double* a, double* beta_p, double* 
     const long long n = d.n;
     if (a) HCK(cudaMemcpyAsync(a, d.a, 8 * nc, cudaMemcpyDeviceToHost, h->stream));
     if (beta_p) HCK(cudaMemcpyAsync(beta_p, d.bp, 8 * nc, cudaMemcpyDeviceToHost, h->stream));
-    std::vector<int> cell(X || Y ? n : 0);
+    std::vector<int> cell(X || Y ? n : 0), ids(n);
     std::vector<float> ox(X ? n : 0), oy(Y ? n : 0), fux(ux ? n : 0), fuy(uy ? n : 0);
+    HCK(cudaMemcpyAsync(ids.data(), d.id, 4 * n, cudaMemcpyDeviceToHost, h->stream));
     if (X || Y) HCK(cudaMemcpyAsync(cell.data(), d.cell, 4 * n, cudaMemcpyDeviceToHost, h->stream));
     if (X) HCK(cudaMemcpyAsync(ox.data(), d.ox, 4 * n, cudaMemcpyDeviceToHost, h->stream));
     if (Y) HCK(cudaMemcpyAsync(oy.data(), d.oy, 4 * n, cudaMemcpyDeviceToHost, h->stream));
     if (ux) HCK(cudaMemcpyAsync(fux.data(), d.ux, 4 * n, cudaMemcpyDeviceToHost, h->stream));
     if (uy) HCK(cudaMemcpyAsync(fuy.data(), d.uy, 4 * n, cudaMemcpyDeviceToHost, h->stream));
     HCK(cudaStreamSynchronize(h->stream));
-    for (long long p = 0; p < n; ++p) {
-        if (X) X[p] = (double)(cell[p] & (d.nx - 1)) + (double)ox[p];
-        if (Y) Y[p] = (double)(cell[p] >> d.lx) + (double)oy[p];
-        if (ux) ux[p] = fux[p];
-        if (uy) uy[p] = fuy[p];
+    for (long long p = 0; p < n; ++p) {   // back to the load order
+        const int q = ids[p];
+        if (q < 0 || q >= n) return hfail(PIC_ESTATE, "particle ids corrupted");
+        if (X) X[q] = (double)(cell[p] & (d.nx - 1)) + (double)ox[p];
+        if (Y) Y[q] = (double)(cell[p] >> d.lx) + (double)oy[p];
+        if (ux) ux[q] = fux[p];
+        if (uy) uy[q] = fuy[p];
     }
     return PIC_OK;
 }
@@ -1000,14 +1083,19 @@ extern "C" int pic_hybrid_energies(pic_hybrid* h, double out3[3]) {
     energy_kernel<<<RGRID, NT, 0, h->stream>>>(d);
     HCK(cudaGetLastError());
     std::vector<double> part(3 * RGRID);
+    std::vector<long long> eb(RGRID);
     HCK(cudaMemcpyAsync(part.data(), d.part, 8 * part.size(), cudaMemcpyDeviceToHost, h->stream));
+    HCK(cudaMemcpyAsync(eb.data(), d.ebeam, 8 * eb.size(), cudaMemcpyDeviceToHost, h->stream));
     HCK(cudaStreamSynchronize(h->stream));
     const double dA = d.dxd * d.dyd;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 3; k += 2) {
         double s = 0.0;
         for (int b = 0; b < RGRID; ++b) s += part[3 * b + k];
         out3[k] = s * dA;
     }
+    long long sb = 0;
+    for (int b = 0; b < RGRID; ++b) sb += eb[b];
+    out3[1] = (double)sb * 0x1p-30 * h->cfg.w * dA;
     return PIC_OK;
 }
 
