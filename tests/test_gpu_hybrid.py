@@ -13,7 +13,8 @@ few 1e-5 -- the tests allow 2e-4 (relative to the largest value of each array) a
   * a seeded single mode grows at the model's linear rate within 2%;
   * Eq. 7: the collisionless total energy drift stays below 1% of the peak magnetic energy and
     falls with dt, as in the oracle;
-  * bitwise reproducibility, solver convergence, and argument errors.
+  * bitwise reproducibility, independence of the periodic sort, graph = direct launches,
+    solver convergence, and argument errors.
 """
 import numpy as np
 import pytest
@@ -130,6 +131,23 @@ def test_bitwise_reproducible(pic):
         eng.close()
     for k in out[0]:
         assert np.array_equal(out[0][k], out[1][k]), k
+
+
+def test_sort_does_not_change_results(pic):
+    """Deposits are exact integer sums, so sorting the beam by cell every step and never
+    sorting (after the load) give bitwise the same state, in the load order."""
+    nx, ny, n = 32, 16, 32 * 16 * 8 + 11
+    X, Y, ux, uy, uz = _warm(nx, ny, n, 12)
+    out = []
+    for si in (1, 1000000):
+        eng = pic.HybridEngine(nx, ny, 0.2, 0.2, 0.05, 1.0, 0.05, 0.1 / 8, n, sort_interval=si)
+        eng.load(X, Y, ux, uy, uz, BP0)
+        eng.step(12)
+        out.append((eng.state(), eng.energies()))
+        eng.close()
+    for k in out[0][0]:
+        assert np.array_equal(out[0][0][k], out[1][0][k]), k
+    assert np.array_equal(out[0][1], out[1][1])
 
 
 def test_graph_matches_direct_launches(pic):
