@@ -43,7 +43,7 @@ struct MomArgs {
 };
 
 // Component c of E (c < 3) or B at the particle, CIC on its Yee lattice, global memory.
-__device__ float gather_comp(const RunDev& R, int ndim, int c, int cx, int cy, int cz, float ox, float oy, float oz) {
+__device__ __forceinline__ float gather_comp(const RunDev& R, int ndim, int c, int cx, int cy, int cz, float ox, float oy, float oz) {
     // half-shifted axes of each component: Ex x, Ey y, Ez z (3D); Bx y,z; By x,z; Bz x,y
     // (2D: Ez and the z shifts are absent)
     // bit c set: component c is half-shifted along the axis (c = Ex Ey Ez Bx By Bz)
@@ -66,64 +66,94 @@ __device__ float gather_comp(const RunDev& R, int ndim, int c, int cx, int cy, i
     return v;
 }
 
-__device__ __forceinline__ long long fx(double v) { return __double2ll_rn(v * MOM_FIX); }
+// v 2^36 rounded to the nearest int64 (ties to even) through 32-bit conversions only: the 64-bit
+// ones run on the FP64 unit, which this part has little of.  With a = |v| 2^36 (an exact
+// scaling), hi = floor(a 2^-32) and a - hi 2^32 are exact in FP32 (either hi = 0 or
+// ulp(a) >= 2^9), so hi 2^32 + rint(a - hi 2^32) = rint(a); valid for |v| 2^36 < 2^62.
+__device__ __forceinline__ long long fx(float v) {
+    const float a = fabsf(v) * 68719476736.0f;
+    const float hi = floorf(a * 2.3283064365386963e-10f);
+    const unsigned lo = __float2uint_rn(a - hi * 4294967296.0f);
+    const long long r = (long long)__float2uint_rz(hi) * 4294967296LL + (long long)lo;
+    return v < 0.0f ? -r : r;
+}
 
-// Add one particle to the thread's sums: pass 1 first moments, pass 2 centred second moments
-// (mean[s][3] of its coarse cell) and the background force and velocity.
-__device__ __forceinline__ void add_particle(const MomArgs& m, const RunDev& R, int pass, int s, float w,
-                                             const double (*mean)[3], int cx, int cy, int cz, float ox,
+// Mean of a coarse cell as an unevaluated FP32 sum hi + lo, so that u - mean keeps FP32
+// relative accuracy for the small deviations of a cold beam: u - hi is exact when u is within a
+// factor 2 of hi (Sterbenz), then lo is subtracted.
+struct Mean2 { float hi[2][3], lo[2][3]; };
+
+// Add one particle to the thread's sums (FP32 arithmetic, exact fixed-point sums): pass 1 first
+// moments, pass 2 centred second moments about its coarse cell's mean and the background force
+// and velocity.
+// Rows of each pass: pass 1 rows [0, 8), pass 2 rows [8, 18); acc holds the pass's rows only.
+template <int PASS> struct PassRows;
+template <> struct PassRows<1> { static constexpr int base = 0, n = 8; };
+template <> struct PassRows<2> { static constexpr int base = 8, n = 10; };
+
+template <int PASS>
+__device__ __forceinline__ void add_particle(const MomArgs& m, const RunDev& R, int s, float w,
+                                             const Mean2& mean, int cx, int cy, int cz, float ox,
                                              float oy, float oz, float ux, float uy, float uz,
-                                             long long acc[MOM_PSUMS]) {
-    const double dw = w, du[3] = {ux, uy, uz};
-    if (pass == 1) {
-        acc[4 * s] += fx(dw);
+                                             long long* acc) {
+    const float du[3] = {ux, uy, uz};
+    if (PASS == 1) {
+        acc[4 * s] += fx(w);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) acc[4 * s + 1 + d] += fx(dw * du[d]);
+        for (int d = 0; d < 3; ++d) acc[4 * s + 1 + d] += fx(__fmul_rn(w, du[d]));
         return;
     }
+    acc -= 8;   // pass-2 rows are numbered from 8
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const double e = du[d] - mean[s][d];
-        acc[8 + 3 * s + d] += fx(dw * e * e);
+        const float e = __fsub_rn(__fsub_rn(du[d], mean.hi[s][d]), mean.lo[s][d]);
+        acc[8 + 3 * s + d] += fx(__fmul_rn(w, __fmul_rn(e, e)));
     }
     if (s == 1) {
-        const double ig = 1.0 / sqrt(1.0 + du[0] * du[0] + du[1] * du[1] + du[2] * du[2]);
-        const double vx = du[0] * ig, vy = du[1] * ig, vz = du[2] * ig;
+        const float ig = 1.0f / sqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+        const float vx = ux * ig, vy = uy * ig, vz = uz * ig;
         const int nd = m.a.ndim;
-        const double ez = gather_comp(R, nd, 2, cx, cy, cz, ox, oy, oz);
-        const double bx = gather_comp(R, nd, 3, cx, cy, cz, ox, oy, oz);
-        const double by = gather_comp(R, nd, 4, cx, cy, cz, ox, oy, oz);
-        const double fz = (double)m.q_bg * (ez + vx * by - vy * bx);
-        acc[14] += fx(dw * fz);
-        acc[15] += fx(dw * vx);
-        acc[16] += fx(dw * vy);
-        acc[17] += fx(dw * vz);
+        const float ez = gather_comp(R, nd, 2, cx, cy, cz, ox, oy, oz);
+        const float bx = gather_comp(R, nd, 3, cx, cy, cz, ox, oy, oz);
+        const float by = gather_comp(R, nd, 4, cx, cy, cz, ox, oy, oz);
+        const float fz = m.q_bg * (ez + vx * by - vy * bx);
+        acc[14] += fx(w * fz);
+        acc[15] += fx(w * vx);
+        acc[16] += fx(w * vy);
+        acc[17] += fx(w * vz);
     }
 }
 
-// Means <u> per species of coarse cell cc from the pass-1 sums.
-__device__ __forceinline__ void coarse_means(const MomArgs& m, long long cc, double mean[2][3]) {
+// Means <u> per species of coarse cell cc from the pass-1 sums (FP64 once per CTA, then split
+// into an FP32 pair).
+__device__ __forceinline__ void coarse_means(const MomArgs& m, long long cc, Mean2& mean) {
     const long long nc = (long long)m.ncx * m.ncy;
     for (int s = 0; s < 2; ++s) {
         const double sw = (double)m.psum[(size_t)(4 * s) * nc + cc];
-        for (int d = 0; d < 3; ++d)
-            mean[s][d] = sw > 0 ? (double)m.psum[(size_t)(4 * s + 1 + d) * nc + cc] / sw : 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const double mu = sw > 0 ? (double)m.psum[(size_t)(4 * s + 1 + d) * nc + cc] / sw : 0.0;
+            mean.hi[s][d] = (float)mu;
+            mean.lo[s][d] = (float)(mu - (double)mean.hi[s][d]);
+        }
     }
 }
 
-// One CTA per (coarse cell, z chunk): a thread per fine cell, all its particles.
-__global__ void __launch_bounds__(NT) mom_particles(const MomArgs m, int pass) {
-    __shared__ long long red[NT / 32][MOM_PSUMS];
+// One CTA per (coarse cell, z chunk): a thread per fine cell, all its particles; one kernel per
+// pass, each holding only its own sums (registers decide the occupancy here).
+template <int PASS>
+__global__ void __launch_bounds__(NT, 3) mom_particles(const MomArgs m) {
+    constexpr int B = PassRows<PASS>::base, NR = PassRows<PASS>::n;
+    __shared__ long long red[NT / 32][NR];
     const Args& a = m.a;
     const RunDev& R = a.runs[m.run];
     const int cc = blockIdx.x;
-    double mean[2][3] = {{0, 0, 0}, {0, 0, 0}};
-    if (pass == 2) coarse_means(m, cc, mean);
+    Mean2 mean{};
+    if (PASS == 2) coarse_means(m, cc, mean);
     const int X0 = (cc % m.ncx) * m.bx, Y0 = (cc / m.ncx) * m.by;
     const int per = m.bx * m.by;
-    long long acc[MOM_PSUMS];
+    long long acc[NR];
 #pragma unroll
-    for (int k = 0; k < MOM_PSUMS; ++k) acc[k] = 0;
+    for (int k = 0; k < NR; ++k) acc[k] = 0;
     const int par = a.ctl->parity;
     for (int t = threadIdx.x; t < per * m.zc; t += NT) {
         const int col = t % per, lz = t / per;
@@ -138,29 +168,31 @@ __global__ void __launch_bounds__(NT) mom_particles(const MomArgs m, int pass) {
             const float w = R.sp[s].w;
             for (int k = 0; k < cr.n; ++k) {
                 const size_t q = slot_of(g, a.cap[s], a.cap_stay[s], cr.ns, k);
-                add_particle(m, R, pass, s, w, mean, cx, cy, cz, S.o[0][q], S.o[1][q],
-                             a.ndim == 3 ? S.o[2][q] : 0.f, S.u[0][q], S.u[1][q], S.u[2][q], acc);
+                add_particle<PASS>(m, R, s, w, mean, cx, cy, cz, S.o[0][q], S.o[1][q],
+                                   a.ndim == 3 ? S.o[2][q] : 0.f, S.u[0][q], S.u[1][q], S.u[2][q], acc);
             }
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < MOM_PSUMS; ++k) {
+    for (int k = 0; k < NR; ++k) {
         long long v = acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) red[warp][k] = v;
     }
     __syncthreads();
-    if (threadIdx.x < MOM_PSUMS) {
+    if (threadIdx.x < NR) {
         long long v = 0;
         for (int w = 0; w < NT / 32; ++w) v += red[w][threadIdx.x];
-        if (v) atomicAdd((unsigned long long*)&m.psum[(size_t)threadIdx.x * m.ncx * m.ncy + cc], (unsigned long long)v);
+        if (v) atomicAdd((unsigned long long*)&m.psum[(size_t)(B + threadIdx.x) * m.ncx * m.ncy + cc], (unsigned long long)v);
     }
 }
 
 // Spilled particles of the run (thread each).
-__global__ void __launch_bounds__(NT) mom_spill(const MomArgs m, int pass) {
+template <int PASS>
+__global__ void __launch_bounds__(NT) mom_spill(const MomArgs m) {
+    constexpr int B = PassRows<PASS>::base, NR = PassRows<PASS>::n;
     const Args& a = m.a;
     const RunDev& R = a.runs[m.run];
     const int par = a.ctl->parity;
@@ -175,15 +207,15 @@ __global__ void __launch_bounds__(NT) mom_spill(const MomArgs m, int pass) {
             const int cz = (int)(lc / ((long long)R.nx * R.ny));
             const int rem = (int)(lc - (long long)cz * R.nx * R.ny);
             const int cy = rem / R.nx, cx = rem - cy * R.nx;
-            long long acc[MOM_PSUMS];
-            for (int i = 0; i < MOM_PSUMS; ++i) acc[i] = 0;
+            long long acc[NR];
+            for (int i = 0; i < NR; ++i) acc[i] = 0;
             const long long cc = (long long)(cy / m.by) * m.ncx + cx / m.bx;
-            double mean[2][3] = {{0, 0, 0}, {0, 0, 0}};
-            if (pass == 2) coarse_means(m, cc, mean);
-            add_particle(m, R, pass, s, R.sp[s].w, mean, cx, cy, cz, S.so[0][k], S.so[1][k],
-                         a.ndim == 3 ? S.so[2][k] : 0.f, S.su[0][k], S.su[1][k], S.su[2][k], acc);
-            for (int i = 0; i < MOM_PSUMS; ++i)
-                if (acc[i]) atomicAdd((unsigned long long*)&m.psum[(size_t)i * nc + cc], (unsigned long long)acc[i]);
+            Mean2 mean{};
+            if (PASS == 2) coarse_means(m, cc, mean);
+            add_particle<PASS>(m, R, s, R.sp[s].w, mean, cx, cy, cz, S.so[0][k], S.so[1][k],
+                               a.ndim == 3 ? S.so[2][k] : 0.f, S.su[0][k], S.su[1][k], S.su[2][k], acc);
+            for (int i = 0; i < NR; ++i)
+                if (acc[i]) atomicAdd((unsigned long long*)&m.psum[(size_t)(B + i) * nc + cc], (unsigned long long)acc[i]);
         }
     }
 }
@@ -298,10 +330,10 @@ cudaError_t launch_moments(const Args& a, const RunDev& host_run, int run, int b
     cudaError_t e = cudaMemsetAsync(m.psum, 0, (size_t)nc * MOM_PSUMS * sizeof(long long), s);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)nc, (unsigned)((nz + m.zc - 1) / m.zc));
-    for (int pass = 1; pass <= 2; ++pass) {
-        mom_particles<<<grid, NT, 0, s>>>(m, pass);
-        mom_spill<<<152, NT, 0, s>>>(m, pass);
-    }
+    mom_particles<1><<<grid, NT, 0, s>>>(m);
+    mom_spill<1><<<152, NT, 0, s>>>(m);
+    mom_particles<2><<<grid, NT, 0, s>>>(m);
+    mom_spill<2><<<152, NT, 0, s>>>(m);
     mom_columns<<<grid_of((long long)host_run.nx * host_run.ny), NT, 0, s>>>(m);
     mom_finalize<<<grid_of(nc), NT, 0, s>>>(m);
     return cudaGetLastError();
@@ -309,8 +341,10 @@ cudaError_t launch_moments(const Args& a, const RunDev& host_run, int run, int b
 
 cudaError_t preload_moments() {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, mom_particles);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_spill);
+    cudaError_t e = cudaFuncGetAttributes(&fa, mom_particles<1>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_particles<2>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_spill<1>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_spill<2>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_columns);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_finalize);
     return e;
