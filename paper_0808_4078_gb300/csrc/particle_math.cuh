@@ -127,17 +127,29 @@ __device__ __forceinline__ void carry(float r, float& no, int& c) {
 
 // Kinetic energy per species and total momentum at time n, int64 fixed point 2^32:
 // kacc = {Ekin_0, Ekin_1, Px, Py, Pz}.
+// x rounded to the nearest int64, ties to even (the value of __float2ll_rn), through 32-bit
+// conversions only: the 64-bit conversion executes on the FP64 unit, which this part has little
+// of.  With a = |x|, hi = floor(a 2^-32) and a - hi 2^32 are exact in FP32 (either hi = 0, or
+// ulp(a) >= 2^9), so hi 2^32 + rint(a - hi 2^32) = rint(a); valid for |x| < 2^62.
+__device__ __forceinline__ long long f2ll_rn(float x) {
+    const float a = fabsf(x);
+    const float hi = floorf(a * 2.3283064365386963e-10f);
+    const unsigned lo = __float2uint_rn(a - hi * 4294967296.0f);
+    const long long v = (long long)__float2uint_rz(hi) * 4294967296LL + (long long)lo;
+    return x < 0.0f ? -v : v;
+}
+
 __device__ __forceinline__ void kin_add(long long kacc[5], int s, float w, float u0x, float u0y,
                                         float u0z, float ux, float uy, float uz) {
     const float mx = 0.5f * (u0x + ux), my = 0.5f * (u0y + uy), mz = 0.5f * (u0z + uz);
     const float gmid = sqrtf(1.f + mx * mx + my * my + mz * mz);
     const float sc = 4294967296.0f;   // 2^32
-    const long long e = __float2ll_rn(w * (gmid - 1.f) * sc);
+    const long long e = f2ll_rn(w * (gmid - 1.f) * sc);
     kacc[0] += s ? 0 : e;
     kacc[1] += s ? e : 0;
-    kacc[2] += __float2ll_rn(w * mx * sc);
-    kacc[3] += __float2ll_rn(w * my * sc);
-    kacc[4] += __float2ll_rn(w * mz * sc);
+    kacc[2] += f2ll_rn(w * mx * sc);
+    kacc[3] += f2ll_rn(w * my * sc);
+    kacc[4] += f2ll_rn(w * mz * sc);
 }
 
 // ------------------------------------------------------------------ binary collisions

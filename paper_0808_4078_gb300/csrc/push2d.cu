@@ -290,9 +290,9 @@ __device__ __forceinline__ void drain(Smem& sm, const Args& a, const RunConst& K
     deposit_terms(add, P, ix + wx.off, iy + wy.off, wx, wy, zf);
     if (P.drag) {
         const int n1 = (iy + r.sy) * RX + (ix + r.sx);
-        add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], __float2ll_rn(r.ux * MOM_SCALE));
-        add_split(&sm.Mlo[1][n1], &sm.Mhi[1][n1], __float2ll_rn(r.uy * MOM_SCALE));
-        add_split(&sm.Mlo[2][n1], &sm.Mhi[2][n1], __float2ll_rn(r.uz * MOM_SCALE));
+        add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], f2ll_rn(r.ux * MOM_SCALE));
+        add_split(&sm.Mlo[1][n1], &sm.Mhi[1][n1], f2ll_rn(r.uy * MOM_SCALE));
+        add_split(&sm.Mlo[2][n1], &sm.Mhi[2][n1], f2ll_rn(r.uz * MOM_SCALE));
         atomicAdd(&sm.MC[n1], 1);
     }
     int ncx = cx + r.sx, ncy = cy + r.sy;
@@ -627,9 +627,9 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
             ncy = ncy < 0 ? ncy + ny : (ncy >= ny ? ncy - ny : ncy);
             const int l1 = ncy * nx + ncx;
             if (P.drag) {
-                atomicAdd((unsigned long long*)&Rp->msum[0][l1], (unsigned long long)__float2ll_rn(r.ux * MOM_SCALE));
-                atomicAdd((unsigned long long*)&Rp->msum[1][l1], (unsigned long long)__float2ll_rn(r.uy * MOM_SCALE));
-                atomicAdd((unsigned long long*)&Rp->msum[2][l1], (unsigned long long)__float2ll_rn(r.uz * MOM_SCALE));
+                atomicAdd((unsigned long long*)&Rp->msum[0][l1], (unsigned long long)f2ll_rn(r.ux * MOM_SCALE));
+                atomicAdd((unsigned long long*)&Rp->msum[1][l1], (unsigned long long)f2ll_rn(r.uy * MOM_SCALE));
+                atomicAdd((unsigned long long*)&Rp->msum[2][l1], (unsigned long long)f2ll_rn(r.uz * MOM_SCALE));
                 atomicAdd(&Rp->mcnt[l1], 1);
             }
             const int g1 = Rp->cell_off + l1;

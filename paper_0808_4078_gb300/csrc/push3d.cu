@@ -438,9 +438,9 @@ __global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
             deposit3(add, P, wx, wy, wz, xa, ya, za);
             const int n1 = n0 + res.st[2] * RXY + res.st[1] * RX + res.st[0];
             if (P.drag) {
-                add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], __float2ll_rn(res.ux * MOM_SCALE));
-                add_split(&sm.Mlo[1][n1], &sm.Mhi[1][n1], __float2ll_rn(res.uy * MOM_SCALE));
-                add_split(&sm.Mlo[2][n1], &sm.Mhi[2][n1], __float2ll_rn(res.uz * MOM_SCALE));
+                add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], f2ll_rn(res.ux * MOM_SCALE));
+                add_split(&sm.Mlo[1][n1], &sm.Mhi[1][n1], f2ll_rn(res.uy * MOM_SCALE));
+                add_split(&sm.Mlo[2][n1], &sm.Mhi[2][n1], f2ll_rn(res.uz * MOM_SCALE));
                 atomicAdd(&sm.MC[n1], 1);
             }
             const int mx = lx + res.st[0], my = ly + res.st[1], mz = lz + res.st[2];
@@ -577,9 +577,9 @@ __global__ void __launch_bounds__(NT) spill3d_kernel(const Args a) {
             const int ncx = wrap1(cx + r.st[0], nx), ncy = wrap1(cy + r.st[1], ny), ncz = wrap1(cz + r.st[2], nz);
             const long long l1 = ((long long)ncz * ny + ncy) * nx + ncx;
             if (P.drag) {
-                atomicAdd((unsigned long long*)&Rp->msum[0][l1], (unsigned long long)__float2ll_rn(r.ux * MOM_SCALE));
-                atomicAdd((unsigned long long*)&Rp->msum[1][l1], (unsigned long long)__float2ll_rn(r.uy * MOM_SCALE));
-                atomicAdd((unsigned long long*)&Rp->msum[2][l1], (unsigned long long)__float2ll_rn(r.uz * MOM_SCALE));
+                atomicAdd((unsigned long long*)&Rp->msum[0][l1], (unsigned long long)f2ll_rn(r.ux * MOM_SCALE));
+                atomicAdd((unsigned long long*)&Rp->msum[1][l1], (unsigned long long)f2ll_rn(r.uy * MOM_SCALE));
+                atomicAdd((unsigned long long*)&Rp->msum[2][l1], (unsigned long long)f2ll_rn(r.uz * MOM_SCALE));
                 atomicAdd(&Rp->mcnt[l1], 1);
             }
             put_imm3(D, cap, cst, a.spill_cap[s], Rp->cell_off + l1, r.no, r.ux, r.uy, r.uz, id, &a.ctl->err);
