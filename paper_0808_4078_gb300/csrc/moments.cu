@@ -38,6 +38,7 @@ struct MomArgs {
     float q_bg;        // background charge
     float nu_bg;       // background Krook rate
     long long* psum;   // [MOM_PSUMS][nc]
+    float* meanbuf;    // [nc][12]: coarse means of pass 1 as FP32 pairs
     double* col;       // [MOM_COLS][nx * ny]
     float* out;        // [PIC_MOM_ROWS][nc]
 };
@@ -124,24 +125,38 @@ __device__ __forceinline__ void add_particle(const MomArgs& m, const RunDev& R, 
     }
 }
 
-// Means <u> per species of coarse cell cc from the pass-1 sums (FP64 once per CTA, then split
-// into an FP32 pair).
-__device__ __forceinline__ void coarse_means(const MomArgs& m, long long cc, Mean2& mean) {
+// Means <u> per species of each coarse cell from the pass-1 sums, computed once (FP64 divisions
+// are costly on this part) and stored as FP32 pairs for pass 2: meanbuf[cc] = hi[6], lo[6].
+__global__ void __launch_bounds__(NT) mom_means(const MomArgs m) {
     const long long nc = (long long)m.ncx * m.ncy;
-    for (int s = 0; s < 2; ++s) {
-        const double sw = (double)m.psum[(size_t)(4 * s) * nc + cc];
-        for (int d = 0; d < 3; ++d) {
-            const double mu = sw > 0 ? (double)m.psum[(size_t)(4 * s + 1 + d) * nc + cc] / sw : 0.0;
-            mean.hi[s][d] = (float)mu;
-            mean.lo[s][d] = (float)(mu - (double)mean.hi[s][d]);
+    for (long long cc = blockIdx.x * (long long)NT + threadIdx.x; cc < nc; cc += (long long)gridDim.x * NT) {
+        float* o = m.meanbuf + (size_t)cc * 12;
+        for (int s = 0; s < 2; ++s) {
+            const double sw = (double)m.psum[(size_t)(4 * s) * nc + cc];
+            for (int d = 0; d < 3; ++d) {
+                const double mu = sw > 0 ? (double)m.psum[(size_t)(4 * s + 1 + d) * nc + cc] / sw : 0.0;
+                const float hi = (float)mu;
+                o[3 * s + d] = hi;
+                o[6 + 3 * s + d] = (float)(mu - (double)hi);
+            }
         }
     }
 }
 
+__device__ __forceinline__ void coarse_means(const MomArgs& m, long long cc, Mean2& mean) {
+    const float* o = m.meanbuf + (size_t)cc * 12;
+    for (int s = 0; s < 2; ++s)
+        for (int d = 0; d < 3; ++d) {
+            mean.hi[s][d] = o[3 * s + d];
+            mean.lo[s][d] = o[6 + 3 * s + d];
+        }
+}
+
 // One CTA per (coarse cell, z chunk): a thread per fine cell, all its particles; one kernel per
-// pass, each holding only its own sums (registers decide the occupancy here).
+// pass, each holding only its own sums (pass 2 with its field gathers runs 2 CTAs per SM without
+// spilling, measured faster than 3 with spills).
 template <int PASS>
-__global__ void __launch_bounds__(NT, 3) mom_particles(const MomArgs m) {
+__global__ void __launch_bounds__(NT, PASS == 1 ? 3 : 2) mom_particles(const MomArgs m) {
     constexpr int B = PassRows<PASS>::base, NR = PassRows<PASS>::n;
     __shared__ long long red[NT / 32][NR];
     const Args& a = m.a;
@@ -306,7 +321,8 @@ int grid_of(long long n) {
 }  // namespace
 
 size_t moments_scratch_bytes(long long nc, long long ncol) {
-    return (size_t)nc * MOM_PSUMS * sizeof(long long) + (size_t)ncol * MOM_COLS * sizeof(double);
+    return (size_t)nc * MOM_PSUMS * sizeof(long long) + (size_t)ncol * MOM_COLS * sizeof(double) +
+           (size_t)nc * 12 * sizeof(float);
 }
 
 cudaError_t launch_moments(const Args& a, const RunDev& host_run, int run, int bx, int by, float q_bg,
@@ -326,12 +342,14 @@ cudaError_t launch_moments(const Args& a, const RunDev& host_run, int run, int b
     const long long nc = (long long)m.ncx * m.ncy;
     m.psum = static_cast<long long*>(scratch);
     m.col = reinterpret_cast<double*>(m.psum + (size_t)nc * MOM_PSUMS);
+    m.meanbuf = reinterpret_cast<float*>(m.col + (size_t)host_run.nx * host_run.ny * MOM_COLS);
     m.out = out;
     cudaError_t e = cudaMemsetAsync(m.psum, 0, (size_t)nc * MOM_PSUMS * sizeof(long long), s);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)nc, (unsigned)((nz + m.zc - 1) / m.zc));
     mom_particles<1><<<grid, NT, 0, s>>>(m);
     mom_spill<1><<<152, NT, 0, s>>>(m);
+    mom_means<<<grid_of(nc), NT, 0, s>>>(m);
     mom_particles<2><<<grid, NT, 0, s>>>(m);
     mom_spill<2><<<152, NT, 0, s>>>(m);
     mom_columns<<<grid_of((long long)host_run.nx * host_run.ny), NT, 0, s>>>(m);
@@ -345,6 +363,7 @@ cudaError_t preload_moments() {
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_particles<2>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_spill<1>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_spill<2>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_means);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_columns);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_finalize);
     return e;
