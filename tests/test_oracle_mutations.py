@@ -2,7 +2,8 @@
 
 Each case compiles a copy of oracle/pic_oracle.c with one plausible error (a dropped factor,
 a flipped sign, a wrong stagger or index) in a temporary directory, runs the pin suite against
-that copy on the CPU, and requires it to fail.  The repository's oracle is never modified.
+that copy on the CPU, and requires it to fail.  The hybrid model's oracle (oracle/hybrid.py)
+gets the same treatment against its own pins.  The repository's oracle is never modified.
 """
 import os
 import shutil
@@ -59,6 +60,45 @@ def test_planted_mistake_is_caught(name, tmp_path):
         shutil.copy(os.path.join(ROOT, "tests", f), d / "tests" / f)
     (d / "oracle" / "pic_oracle.c").write_text(src.replace(old, new, 1))
     r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
+                        "-p", "no:cacheprovider"], cwd=d, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 1, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
+
+
+HYBRID_MUTATIONS = {
+    "uniform_plasma_density": ("return np.maximum(self.n0 - nb, 0.0)",
+                               "return np.maximum(self.n0 - nb.mean() + 0.0 * nb, 0.0)"),
+    "force_plasma_sign": ("f = uz / g - bpp", "f = uz / g + bpp"),
+    "ohmic_term_dropped": ("rhs = jb + n_p * (bp - a - self.nu * dt * bp)", "rhs = jb + n_p * (bp - a)"),
+    "plasma_update_without_friction": ("self.beta_p = bp + a_new - a - self.nu * dt * bp",
+                                       "self.beta_p = bp + a_new - a"),
+    "canonical_momentum_without_a": ("uz = P + ua", "uz = P"),
+    "move_without_gamma": ("X = (X + dt * ux / (g2 * self.dx)) % self.nx", "X = (X + dt * ux / self.dx) % self.nx"),
+    "current_without_gamma": ("jb = self._deposit(self.X, self.Y, self.w * uzs / gs)",
+                              "jb = self._deposit(self.X, self.Y, self.w * uzs)"),
+    "gradient_x_weights": ("gx = ((1 - fy) * (F[j0, i1] - F[j0, i0]) + fy * (F[j1, i1] - F[j1, i0])) / self.dx",
+                           "gx = ((1 - fx) * (F[j0, i1] - F[j0, i0]) + fx * (F[j1, i1] - F[j1, i0])) / self.dx"),
+    "laplacian_wrong_spacing": ("return (sp.kron(sp.identity(ny), ring(nx, dx)) + sp.kron(ring(ny, dy), sp.identity(nx))).tocsc()",
+                                "return (sp.kron(sp.identity(ny), ring(nx, dx)) + sp.kron(ring(ny, dx), sp.identity(nx))).tocsc()"),
+    "energy_uniform_density": ("0.5 * np.sum(self.plasma_density() * self.beta_p ** 2) * dA",
+                               "0.5 * self.n0 * np.sum(self.beta_p ** 2) * dA"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(HYBRID_MUTATIONS))
+def test_planted_hybrid_mistake_is_caught(name, tmp_path):
+    old, new = HYBRID_MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", "hybrid.py")).read()
+    assert old in src, f"mutation anchor for {name} no longer in the hybrid oracle"
+    d = tmp_path / "copy"
+    shutil.copytree(os.path.join(ROOT, "oracle"), d / "oracle",
+                    ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    (d / "tests").mkdir()
+    for f in ("conftest.py", "test_oracle_hybrid.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), d / "tests" / f)
+    (d / "oracle" / "hybrid.py").write_text(src.replace(old, new, 1))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_hybrid.py", "-q", "-x",
                         "-p", "no:cacheprovider"], cwd=d, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 1, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
