@@ -20,13 +20,14 @@
 // is mixed-precision refinement: the residual of a^n is formed in FP64, the correction
 // d = a^{n+1} - a^n is solved in FP32 by conjugate gradients preconditioned with the exact inverse
 // of the constant-density operator (lap - n_bar) -- a spectral solve by this file's own FP32
-// radix-2 Stockham FFT (one CTA per row in shared memory: rows, transpose, columns with the
-// division and the inverse in one kernel, transpose, rows).  Beam density and current are summed
-// in int64 fixed point (2^40) so that they do not depend on particle order; every inner product is
-// a fixed-order two-level sum (per-block partials, then the last block to finish adds them in
-// block order), so a run is bitwise reproducible.  Every kernel of a CG iteration returns at once
-// when the previous one found the residual below the tolerance, so the host launches a fixed
-// number of iterations without reading anything back.
+// radix-2 Stockham FFT in shared memory: forward transforms of the rows (fused into the kernels
+// that produce the residual), a column pass on strips of 4 columns (forward, division, inverse),
+// inverse transforms of the rows.  Beam density and current are exact integer sums, so they do
+// not depend on particle order; every inner product is a fixed-order two-level sum (per-block
+// partials, then the last block to finish adds them in block order), so a run is bitwise
+// reproducible.  Every kernel of a CG iteration returns at once when the previous one found the
+// residual below the tolerance; in a CUDA graph the iterations are the body of a while node that
+// stops after convergence.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -54,6 +55,7 @@ struct HybDev {
     float idx, idy;                 // 1/dx, 1/dy (FP32)
     double dxd, dyd, dtd, n0, nu, tol2;
     double idx1, idy1, idx2, idy2;  // 1/dx, 1/dy, 1/dx^2, 1/dy^2 (FP64): no FP64 division on the device
+    double keep;                    // 1 - nu dt
     long long n;
     // particles (and the second buffer the periodic sort permutes into)
     int* cell; float* ox; float* oy; float* ux; float* uy; float* P; int* id;
@@ -68,7 +70,7 @@ struct HybDev {
     long long* J; long long* N;     // beam current and density, fixed point
     float* np;                      // plasma density of the current positions
     float* d; float* r; float* z; float* q; float* p0; float* p1;
-    float2* ws0; float2* ws1;       // FFT work, [ny][nx] and [nx][ny]
+    float2* ws0;                    // FFT work, [ny][nx]
     const float2* twx; const float2* twy;   // exp(-2 pi i m / N), m < N/2
     const float* lamx; const float* lamy;   // 5-point eigenvalues per axis
     float nbar;                     // preconditioner density
@@ -108,53 +110,66 @@ __device__ float2* fft_smem(float2* b0, float2* b1, int N, int logn, const float
 
 __device__ __forceinline__ bool solver_done(const HybDev& h) { return h.S[S_DONE] != 0.0; }
 
-// forward transform of each row of ws0 (ny rows of nx)
-__global__ void fft_rows_fwd_kernel(const HybDev h) {
-    if (solver_done(h)) return;
-    extern __shared__ float2 fsh[];
-    const int N = h.nx;
-    float2* row = h.ws0 + (size_t)blockIdx.x * N;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) fsh[i] = row[i];
-    __syncthreads();
-    const float2* out = fft_smem(fsh, fsh + N, N, h.lx, h.twx, false);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) row[i] = out[i];
+// The same passes over ncol columns at once, column c at b + c ld (ld = N + 1 against bank
+// conflicts of the strided loads); all threads of the block take part.
+__device__ float2* fft_multi(float2* b0, float2* b1, int ncol, int ld, int N, int logn,
+                             const float2* __restrict__ tw, bool inverse) {
+    const int half = N >> 1;
+    int ls = 0;
+    for (int Ns = 1; Ns < N; Ns <<= 1, ++ls) {
+        for (int t = threadIdx.x; t < ncol * half; t += blockDim.x) {
+            const int c = t >> (logn - 1), j = t & (half - 1);
+            const float2* x = b0 + c * ld;
+            float2* y = b1 + c * ld;
+            const float2 v0 = x[j];
+            float2 v1 = x[j + half];
+            const int k = j & (Ns - 1);
+            float2 w = tw[k << (logn - 1 - ls)];
+            if (inverse) w.y = -w.y;
+            v1 = cmulf(v1, w);
+            const int idx = ((j - k) << 1) + k;
+            y[idx] = make_float2(v0.x + v1.x, v0.y + v1.y);
+            y[idx + Ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
+        }
+        __syncthreads();
+        float2* t = b0; b0 = b1; b1 = t;
+    }
+    return b0;
 }
 
-// out[c][r] = in[r][c] for an R x C complex array (32 x 32 tiles through shared memory)
-__global__ void transpose_kernel(const HybDev h, const float2* __restrict__ in, float2* __restrict__ out, int R, int C) {
-    if (solver_done(h)) return;
-    __shared__ float2 t[32][33];
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int r = r0 + k, c = c0 + threadIdx.x;
-        if (r < R && c < C) t[k][threadIdx.x] = in[(size_t)r * C + c];
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int c = c0 + k, r = r0 + threadIdx.x;
-        if (r < R && c < C) out[(size_t)c * R + r] = t[threadIdx.x][k];
-    }
-}
-
-// Column pass on the transposed spectrum (row kx of ny values): forward transform, division by
-// the eigenvalue of (lap - n_bar) with the 1/(nx ny) of the inverse, inverse transform.
-__global__ void fft_cols_solve_kernel(const HybDev h, int logny) {
+// Column pass of the spectral solve on a strip of CW columns of the row-major spectrum (ws0
+// holds the rows' forward transforms): forward transforms along y, division by the eigenvalue of
+// (lap - n_bar) with the 1/(nx ny) of the inverse, inverse transforms; in place.  A strip row of
+// CW complex values is one 32-byte sector, so the strided access wastes no DRAM bandwidth and no
+// transpose is needed.
+constexpr int CW = 4;
+constexpr int NTC = 512;   // threads of the column-strip kernel
+__global__ void __launch_bounds__(NTC) fft_cols_strip_kernel(const HybDev h, int logny) {
     if (solver_done(h)) return;
     extern __shared__ float2 fsh[];
-    const int N = h.ny, kx = blockIdx.x;
-    float2* row = h.ws1 + (size_t)kx * N;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) fsh[i] = row[i];
+    const int N = h.ny, ld = N + 1, kx0 = blockIdx.x * CW;
+    float2* b0 = fsh;
+    float2* b1 = fsh + CW * ld;
+    for (int e = threadIdx.x; e < CW * N; e += blockDim.x) {
+        const int row = e / CW, c = e - row * CW;
+        b0[c * ld + row] = h.ws0[((size_t)row << h.lx) + kx0 + c];
+    }
     __syncthreads();
-    float2* b = fft_smem(fsh, fsh + N, N, logny, h.twy, false);
-    float2* o = b == fsh ? fsh + N : fsh;
+    float2* res = fft_multi(b0, b1, CW, ld, N, logny, h.twy, false);
+    float2* oth = res == b0 ? b1 : b0;
     const float scale = 1.0f / ((float)h.nx * (float)h.ny);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const float inv = scale / (h.lamx[kx] + h.lamy[i] - h.nbar);
-        b[i] = make_float2(b[i].x * inv, b[i].y * inv);
+    for (int e = threadIdx.x; e < CW * N; e += blockDim.x) {
+        const int c = e >> logny, ky = e & (N - 1);
+        const float inv = scale / (h.lamx[kx0 + c] + h.lamy[ky] - h.nbar);
+        float2* v = res + c * ld + ky;
+        *v = make_float2(v->x * inv, v->y * inv);
     }
     __syncthreads();
-    const float2* out = fft_smem(b, o, N, logny, h.twy, true);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) row[i] = out[i];
+    const float2* out = fft_multi(res, oth, CW, ld, N, logny, h.twy, true);
+    for (int e = threadIdx.x; e < CW * N; e += blockDim.x) {
+        const int row = e / CW, c = e - row * CW;
+        h.ws0[((size_t)row << h.lx) + kx0 + c] = out[c * ld + row];
+    }
 }
 
 // ---------------------------------------------------------------- reductions
@@ -190,6 +205,59 @@ __device__ __forceinline__ void grid_sum(const HybDev& h, double v, Fin fin) {
         *h.ticket = 0u;
         fin(red[0]);
     }
+}
+
+// The same for kernels with one CTA per grid row (blockDim up to 1024): block sums by 32
+// strided partial sums then thread 0, row partials in part[], the last CTA adds them.
+template <class Fin>
+__device__ __forceinline__ void rows_sum(const HybDev& h, double v, Fin fin) {
+    __shared__ double rs[1024];
+    __shared__ double r32[32];
+    __shared__ bool last;
+    const int nw = blockDim.x < 32 ? (int)blockDim.x : 32;
+    rs[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (int t = threadIdx.x; t < (int)blockDim.x; t += 32) s += rs[t];
+        r32[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int t = 0; t < nw; ++t) s += r32[t];
+        h.part[blockIdx.x] = s;
+        __threadfence();
+        last = atomicAdd(h.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += ((volatile double*)h.part)[b];
+    rs[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t2 = 0.0;
+        for (int t = threadIdx.x; t < (int)blockDim.x; t += 32) t2 += rs[t];
+        r32[threadIdx.x] = t2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int t = 0; t < nw; ++t) tot += r32[t];
+        *h.ticket = 0u;
+        fin(tot);
+    }
+}
+
+// Forward transform of a row held in shared memory (nx complex values), stored to its ws0 row.
+__device__ __forceinline__ void row_fft_store(const HybDev& h, float2* fsh, int j) {
+    __syncthreads();
+    const int N = h.nx;
+    const float2* out = fft_smem(fsh, fsh + N, N, h.lx, h.twx, false);
+    float2* row = h.ws0 + ((size_t)j << h.lx);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) row[i] = out[i];
 }
 
 // ---------------------------------------------------------------- particles
@@ -351,26 +419,30 @@ __device__ __forceinline__ double lap64(const HybDev& h, const double* F, int i,
 }
 
 // n_p of the new positions; FP64 residual r0 = b - (lap - n_p) a^n of the initial guess; d = 0;
-// ws0 = r0; <r0, r0> opens the solve.
-__global__ void __launch_bounds__(NT) rhs_kernel(const HybDev h) {
-    const int nc = h.nx * h.ny;
-    float rr = 0.0f;   // a dozen nodes per thread in FP32, the rest of the sum in FP64
-    for (int c = blockIdx.x * NT + threadIdx.x; c < nc; c += gridDim.x * NT) {
+// <r0, r0> opens the solve; one CTA per row, which also applies the preconditioner's forward
+// transform along x to its row of r0 (into ws0).
+__global__ void rhs_rows_kernel(const HybDev h) {
+    extern __shared__ float2 fsh[];
+    const int j = blockIdx.x;
+    float rr = 0.0f;   // a few nodes per thread in FP32, the rest of the sum in FP64
+    for (int i = threadIdx.x; i < h.nx; i += blockDim.x) {
+        const int c = (j << h.lx) + i;
         const double jb = (double)h.J[c] / JFIX, nb = (double)h.N[c] / JFIX;
         h.J[c] = 0; h.N[c] = 0;
         const float npf = (float)fmax(h.n0 - nb, 0.0);
         const double npd = (double)npf;
         h.np[c] = npf;
-        const double a = h.a[c], bp = h.bp[c];
-        const double b = jb + npd * (bp - a - h.nu * h.dtd * bp);
-        const double r0 = b - (lap64(h, h.a, c & (h.nx - 1), c >> h.lx) - npd * a);
+        // b - (lap - n_p) a^n with b = n_b beta_b + n_p (beta_p - a^n - nu dt beta_p): the n_p a^n
+        // terms cancel
+        const double r0 = jb + npd * (h.keep * h.bp[c]) - lap64(h, h.a, i, j);
         const float rf = (float)r0;
         h.r[c] = rf;
         h.d[c] = 0.0f;
-        h.ws0[c] = make_float2(rf, 0.0f);
+        fsh[i] = make_float2(rf, 0.0f);
         rr = fmaf(rf, rf, rr);
     }
-    grid_sum(h, (double)rr, [&](double t) {
+    row_fft_store(h, fsh, j);
+    rows_sum(h, (double)rr, [&](double t) {
         h.S[S_RR0] = t; h.S[S_RR] = t; h.S[S_ITER] = 0.0; h.S[S_RZ] = 0.0; h.S[S_BETA] = 0.0;
         h.S[S_LOOP] = 0.0;
         h.S[S_DONE] = t == 0.0 ? 1.0 : 0.0;
@@ -381,9 +453,6 @@ __global__ void __launch_bounds__(NT) rhs_kernel(const HybDev h) {
 __global__ void fft_rows_inv_z_kernel(const HybDev h) {
     if (solver_done(h)) return;
     extern __shared__ float2 fsh[];
-    __shared__ double rzs[1024];
-    __shared__ double rz32[32];
-    const int nw = blockDim.x < 32 ? (int)blockDim.x : 32;   // rows shorter than 64 run fewer threads
     const int N = h.nx;
     const float2* row = h.ws0 + (size_t)blockIdx.x * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) fsh[i] = row[i];
@@ -396,45 +465,11 @@ __global__ void fft_rows_inv_z_kernel(const HybDev h) {
         h.z[c] = zv;
         rz = fmaf(h.r[c], zv, rz);
     }
-    // fixed-order block sum for any blockDim up to 1024: 32 strided partial sums, then thread 0
-    rzs[threadIdx.x] = (double)rz;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double s = 0.0;
-        for (int t = threadIdx.x; t < (int)blockDim.x; t += 32) s += rzs[t];
-        rz32[threadIdx.x] = s;
-    }
-    __syncthreads();
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int t = 0; t < nw; ++t) s += rz32[t];
-        h.part[blockIdx.x] = s;
-        __threadfence();
-        last = atomicAdd(h.ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    // the last block adds the row partials: strided per thread, then 32 lanes, then thread 0
-    __threadfence();
-    double s = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += ((volatile double*)h.part)[b];
-    rzs[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double t2 = 0.0;
-        for (int t = threadIdx.x; t < (int)blockDim.x; t += 32) t2 += rzs[t];
-        rz32[threadIdx.x] = t2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot = 0.0;
-        for (int t = 0; t < nw; ++t) tot += rz32[t];
-        *h.ticket = 0u;
+    rows_sum(h, (double)rz, [&](double tot) {
         const double it = h.S[S_ITER];
         h.S[S_BETA] = it == 0.0 ? 0.0 : tot / h.S[S_RZ];
         h.S[S_RZ] = tot;
-    }
+    });
 }
 
 // p_new = z + beta p_old; q = (lap - n_p) p_new in FP32; <p_new, q>; alpha.  The two direction
@@ -465,21 +500,25 @@ __global__ void __launch_bounds__(NT) apply_kernel(const HybDev h) {
     grid_sum(h, (double)pq, [&](double t) { h.S[S_ALPHA] = h.S[S_RZ] / t; });
 }
 
-// d += alpha p; r -= alpha q; ws0 = r; <r, r>; stop test.
-__global__ void __launch_bounds__(NT) axpy_kernel(const HybDev h) {
+// d += alpha p; r -= alpha q; <r, r>; stop test; one CTA per row, which also applies the next
+// iteration's forward transform along x to its row of r (into ws0).
+__global__ void axpy_rows_kernel(const HybDev h) {
     if (solver_done(h)) return;
-    const int nc = h.nx * h.ny;
+    extern __shared__ float2 fsh[];
+    const int j = blockIdx.x;
     const float* __restrict__ p = ((int)h.S[S_ITER] & 1) ? h.p0 : h.p1;
     const float alpha = (float)h.S[S_ALPHA];
     float rr = 0.0f;
-    for (int c = blockIdx.x * NT + threadIdx.x; c < nc; c += gridDim.x * NT) {
+    for (int i = threadIdx.x; i < h.nx; i += blockDim.x) {
+        const int c = (j << h.lx) + i;
         h.d[c] = fmaf(alpha, p[c], h.d[c]);
         const float rv = fmaf(-alpha, h.q[c], h.r[c]);
         h.r[c] = rv;
-        h.ws0[c] = make_float2(rv, 0.0f);
+        fsh[i] = make_float2(rv, 0.0f);
         rr = fmaf(rv, rv, rr);
     }
-    grid_sum(h, (double)rr, [&](double t) {
+    row_fft_store(h, fsh, j);
+    rows_sum(h, (double)rr, [&](double t) {
         h.S[S_RR] = t;
         h.S[S_ITER] += 1.0;
         h.S[S_ITERS_TOTAL] += 1.0;
@@ -623,7 +662,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct HLayout {
     size_t cell, ox, oy, ux, uy, P, id, cell2, ox2, oy2, ux2, uy2, P2, id2, order, start, bscratch, ebeam;
-    size_t a, bp, f32, J, N, np, d, r, z, q, p0, p1, ws0, ws1, twx, twy, lamx, lamy, S, part, ticket, total;
+    size_t a, bp, f32, J, N, np, d, r, z, q, p0, p1, ws0, twx, twy, lamx, lamy, S, part, ticket, total;
 };
 HLayout hlayout(const pic_hybrid_config* c) {
     HLayout L{};
@@ -638,7 +677,7 @@ HLayout hlayout(const pic_hybrid_config* c) {
     L.ebeam = take(8 * (size_t)RGRID);
     L.a = take(8 * nc); L.bp = take(8 * nc); L.f32 = take(8 * nc); L.J = take(8 * nc); L.N = take(8 * nc);
     L.np = take(4 * nc); L.d = take(4 * nc); L.r = take(4 * nc); L.z = take(4 * nc); L.q = take(4 * nc);
-    L.p0 = take(4 * nc); L.p1 = take(4 * nc); L.ws0 = take(8 * nc); L.ws1 = take(8 * nc);
+    L.p0 = take(4 * nc); L.p1 = take(4 * nc); L.ws0 = take(8 * nc);
     L.twx = take(8 * (size_t)c->nx / 2); L.twy = take(8 * (size_t)c->ny / 2);
     L.lamx = take(4 * (size_t)c->nx); L.lamy = take(4 * (size_t)c->ny);
     L.S = take(8 * S_NSLOT); L.part = take(8 * 3 * (size_t)(RGRID > 2048 ? RGRID : 2048)); L.ticket = take(4);
@@ -694,7 +733,7 @@ struct HPhase {
 // launches of one step: push, solve set-up, 7 per CG iteration run (+1 loop control in a graph),
 // update; counted from the iterations the solver reports when the step is a graph
 int step_launches(const pic_hybrid* h, int iters, bool graph) {
-    return (h->d.n > 0 ? 1 : 0) + 2 + (graph ? 8 : 7) * iters;
+    return (h->d.n > 0 ? 1 : 0) + 2 + (graph ? 5 : 4) * iters;
 }
 
 void launch_pre(pic_hybrid* h) {
@@ -713,25 +752,24 @@ void launch_sort(pic_hybrid* h) {
 }
 constexpr int SORT_LAUNCHES = 8;   // 6 of the binning (zero, histogram, 3 scan passes, scatter) + 2
 
+int row_threads(int n) { return n / 2 < 1024 ? n / 2 : 1024; }
+
 void launch_rhs(pic_hybrid* h) {
     HybDev& d = h->d;
-    rhs_kernel<<<gridr((long long)d.nx * d.ny), NT, 0, h->stream>>>(d);
+    rhs_rows_kernel<<<d.ny, row_threads(d.nx), 2 * (size_t)d.nx * sizeof(float2), h->stream>>>(d);
 }
 
-// one preconditioned CG iteration (every kernel returns at once after convergence)
+// one preconditioned CG iteration (every kernel returns at once after convergence): the column
+// pass and the inverse row transforms of the preconditioner, the direction update, the residual
+// update with the next forward row transforms
 void launch_iteration(pic_hybrid* h) {
     HybDev& d = h->d;
     const int nx = d.nx, ny = d.ny, nc = nx * ny;
-    const int lny = ilog2(ny);
-    const size_t shx = 2 * (size_t)nx * sizeof(float2), shy = 2 * (size_t)ny * sizeof(float2);
-    const dim3 tb(32, 8);
-    fft_rows_fwd_kernel<<<ny, nx / 2 < 1024 ? nx / 2 : 1024, shx, h->stream>>>(d);
-    transpose_kernel<<<dim3((nx + 31) / 32, (ny + 31) / 32), tb, 0, h->stream>>>(d, d.ws0, d.ws1, ny, nx);
-    fft_cols_solve_kernel<<<nx, ny / 2 < 1024 ? ny / 2 : 1024, shy, h->stream>>>(d, lny);
-    transpose_kernel<<<dim3((ny + 31) / 32, (nx + 31) / 32), tb, 0, h->stream>>>(d, d.ws1, d.ws0, nx, ny);
-    fft_rows_inv_z_kernel<<<ny, nx / 2 < 1024 ? nx / 2 : 1024, shx, h->stream>>>(d);
+    const size_t shx = 2 * (size_t)nx * sizeof(float2), shc = 2 * (size_t)CW * (ny + 1) * sizeof(float2);
+    fft_cols_strip_kernel<<<nx / CW, NTC, shc, h->stream>>>(d, ilog2(ny));
+    fft_rows_inv_z_kernel<<<ny, row_threads(nx), shx, h->stream>>>(d);
     apply_kernel<<<gridr(nc), NT, 0, h->stream>>>(d);
-    axpy_kernel<<<gridr(nc), NT, 0, h->stream>>>(d);
+    axpy_rows_kernel<<<ny, row_threads(nx), shx, h->stream>>>(d);
 }
 
 void launch_post(pic_hybrid* h) {
@@ -856,8 +894,10 @@ extern "C" int pic_hybrid_init(const pic_hybrid_config* cfg, void* arena, size_t
     if (arena_bytes < L.total) return hfail(PIC_ENOMEM, "arena has %zu bytes, needs %zu", arena_bytes, L.total);
     if (reinterpret_cast<uintptr_t>(arena) & 255) return hfail(PIC_EINVAL, "arena must be 256-byte aligned");
     const int shmax = 2 * 2048 * (int)sizeof(float2);
-    HCK(cudaFuncSetAttribute(fft_rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, shmax));
-    HCK(cudaFuncSetAttribute(fft_cols_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, shmax));
+    const int shcol = 2 * CW * (2048 + 1) * (int)sizeof(float2);
+    HCK(cudaFuncSetAttribute(rhs_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, shmax));
+    HCK(cudaFuncSetAttribute(axpy_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, shmax));
+    HCK(cudaFuncSetAttribute(fft_cols_strip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, shcol));
     HCK(cudaFuncSetAttribute(fft_rows_inv_z_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, shmax));
     pic_hybrid* h = new pic_hybrid;
     h->cfg = *cfg;
@@ -871,6 +911,7 @@ extern "C" int pic_hybrid_init(const pic_hybrid_config* cfg, void* arena, size_t
     d.idx = (float)(1.0 / cfg->dx); d.idy = (float)(1.0 / cfg->dy);
     d.idx1 = 1.0 / cfg->dx; d.idy1 = 1.0 / cfg->dy;
     d.idx2 = 1.0 / (cfg->dx * cfg->dx); d.idy2 = 1.0 / (cfg->dy * cfg->dy);
+    d.keep = 1.0 - cfg->nu * cfg->dt;
     const double tol = cfg->tol > 0 ? cfg->tol : 1e-5;
     d.tol2 = tol * tol;
     d.n = 0;
@@ -902,7 +943,6 @@ extern "C" int pic_hybrid_init(const pic_hybrid_config* cfg, void* arena, size_t
     d.N = reinterpret_cast<long long*>(base + L.N);
     d.np = F(L.np); d.d = F(L.d); d.r = F(L.r); d.z = F(L.z); d.q = F(L.q); d.p0 = F(L.p0); d.p1 = F(L.p1);
     d.ws0 = reinterpret_cast<float2*>(base + L.ws0);
-    d.ws1 = reinterpret_cast<float2*>(base + L.ws1);
     d.twx = reinterpret_cast<const float2*>(base + L.twx);
     d.twy = reinterpret_cast<const float2*>(base + L.twy);
     d.lamx = reinterpret_cast<const float*>(base + L.lamx);
@@ -1040,13 +1080,13 @@ extern "C" int pic_hybrid_kernel_times(pic_hybrid* h, pic_kernel_time* out, int 
 
 extern "C" int64_t pic_hybrid_launch_count(pic_hybrid* h) {
     if (!h) return -1;
-    // graph steps: push, set-up and update per step and 8 kernels per run of the loop body (the
+    // graph steps: push, set-up and update per step and 5 kernels per run of the loop body (the
     // loop control counts the runs on the device)
     double S[S_NSLOT];
     if (cudaMemcpyAsync(S, h->d.S, sizeof S, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess)
         return -1;
-    return h->direct_launches + h->graph_steps * ((h->d.n > 0 ? 1 : 0) + 2) + 8 * (long long)S[S_LOOPS_TOTAL];
+    return h->direct_launches + h->graph_steps * ((h->d.n > 0 ? 1 : 0) + 2) + 5 * (long long)S[S_LOOPS_TOTAL];
 }
 
 extern "C" int pic_hybrid_get(pic_hybrid* h, double* a, double* beta_p, double* X, double* Y, double* ux,

@@ -69,8 +69,8 @@ def test_hybrid_required_bytes_and_config_errors_without_gpu(libpic):
     nb = ctypes.c_size_t(0)
     ok = pic.HybridConfig(256, 128, 0.1, 0.1, 0.05, 1.0, 0.0, 0.01, 1000, 0.0, 0, 0)
     assert lib.pic_hybrid_required_bytes(ctypes.byref(ok), ctypes.byref(nb)) == 0
-    # particles 24 B, grid 8 x 8 B + 7 x 4 B + 2 x 8 B complex per node
-    assert nb.value >= 1000 * 24 + 256 * 128 * (40 + 28 + 16)
+    # particles 24 B + id + sort buffer and index (60 B), grid 5 x 8 B + 7 x 4 B + one 8 B complex
+    assert nb.value >= 1000 * 60 + 256 * 128 * (40 + 28 + 8)
     for bad in (pic.HybridConfig(96, 128, 0.1, 0.1, 0.05, 1.0, 0.0, 0.01, 10, 0.0, 0, 0),     # not 2^k
                 pic.HybridConfig(4096, 8, 0.1, 0.1, 0.05, 1.0, 0.0, 0.01, 10, 0.0, 0, 0),     # > 2048
                 pic.HybridConfig(64, 64, 0.1, 0.1, 0.1, 1.0, 0.0, 0.01, 10, 0.0, 0, 0),       # dt = dx

@@ -167,8 +167,8 @@ def test_graph_matches_direct_launches(pic):
         eng.close()
     for k in out[0]:
         assert np.array_equal(out[0][k], out[1][k]), k
-    assert launches[1] == 6 * (3 + 7 * 16)
-    assert launches[0] == 6 * 3 + 8 * iters and launches[0] < launches[1]
+    assert launches[1] == 6 * (3 + 4 * 16)
+    assert launches[0] == 6 * 3 + 5 * iters and launches[0] < launches[1]
 
 
 def test_growth_rate(pic):
