@@ -14,7 +14,9 @@ few 1e-5 -- the tests allow 2e-4 (relative to the largest value of each array) a
   * Eq. 7: the collisionless total energy drift stays below 1% of the peak magnetic energy and
     falls with dt, as in the oracle;
   * bitwise reproducibility, independence of the periodic sort, graph = direct launches,
-    solver convergence, and argument errors.
+    solver convergence, and argument errors;
+  * edge cases: no beam at all (the plasma current switches off in one step, closed form) and
+    the largest grid sides (2048 x 16 and 16 x 2048 nodes) against the oracle.
 """
 import numpy as np
 import pytest
@@ -220,6 +222,34 @@ def test_eq7_energy_conservation(pic):
     assert m2 > 1e-2
     assert d2 < 0.01 * m2, (d2, m2)
     assert d1 / d2 > 1.5, (d1, d2)
+
+
+def test_empty_beam(pic):
+    nu, dt, bp0 = 0.3, 0.05, -0.04
+    eng = pic.HybridEngine(16, 8, 0.1, 0.1, dt, 1.0, nu, 0.0, 0)
+    eng.load(np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0), bp0)
+    eng.step(3)
+    st = eng.state()
+    assert np.allclose(st["a"], -bp0 * (1 - nu * dt), rtol=1e-6, atol=0)
+    assert np.abs(st["beta_p"]).max() < 1e-9
+    assert eng.stats()["unconverged_steps"] == 0
+    eng.close()
+
+
+@pytest.mark.parametrize("nx,ny", [(2048, 16), (16, 2048)])
+def test_largest_grid_sides(pic, nx, ny):
+    from oracle import hybrid
+    n = nx * ny * 2 + 3
+    X, Y, ux, uy, uz = _warm(nx, ny, n, 13)
+    w = 0.1 * nx * ny / n
+    eng, sim = _pair(pic, nx, ny, 0.2, 0.05, 0.05, w, X, Y, ux, uy, uz, BP0)
+    eng.step(3)
+    sim.step(3)
+    st = eng.state()
+    assert _rel(st["a"], sim.a) < 2e-4 and _rel(st["beta_p"], sim.beta_p) < 2e-4
+    assert np.abs((st["X"] - sim.X + nx / 2) % nx - nx / 2).max() < 1e-4
+    assert np.abs((st["Y"] - sim.Y + ny / 2) % ny - ny / 2).max() < 1e-4
+    eng.close()
 
 
 def test_argument_errors(pic):

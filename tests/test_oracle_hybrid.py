@@ -14,6 +14,9 @@
     plasma density) is conserved through the nonlinear filamentation stage up to the time
     discretisation: the drift stays below 1% of the peak magnetic energy and halves with dt
     (a uniform plasma density breaks the invariant: 7% of the peak magnetic energy);
+  * without a beam the plasma current switches off in one step: the axial field that stops it
+    raises a uniformly by beta_p0 (1 - nu dt) (Eqs. 2 and 3 with n_b = 0: a^1 = a^0 - beta_p0
+    (1 - nu dt), beta_p^1 = 0);
   * the beam push in a static vector potential without plasma flow (a purely magnetic field,
     Eq. 1) does no work: gamma = sqrt(1 + u_perp^2 + (P + a)^2) (Eq. 6) stays constant to the
     time discretisation (0.36% over t = 30 at dt = 0.01, halving with dt; dropping a from u_z
@@ -168,3 +171,12 @@ def test_magnetic_push_does_no_work():
     d1, d2 = _static_push_drift(0.01), _static_push_drift(0.005)
     assert d1 < 0.01, d1
     assert d1 / d2 > 1.7, (d1, d2)
+
+
+def test_empty_beam_current_switches_off():
+    nu, dt, bp0 = 0.3, 0.05, -0.04
+    sim = hybrid.HybridSim(16, 8, 0.1, 0.1, dt, n0=1.0, nu=nu, w=0.0)
+    sim.load(np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0), bp0)
+    sim.step(1)
+    assert np.allclose(sim.a, -bp0 * (1 - nu * dt), rtol=1e-13, atol=0)
+    assert np.abs(sim.beta_p).max() < 1e-14
