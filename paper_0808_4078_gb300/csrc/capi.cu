@@ -251,6 +251,8 @@ int fail(pic_ctx* c, int code, const char* fmt, ...) {
 template <class T> T* at(pic_ctx* c, size_t off) { return reinterpret_cast<T*>(c->arena + off); }
 
 int upload_runs(pic_ctx* ctx) {
+    ctx->args.anydrag = 0;
+    for (int r = 0; r < ctx->nruns; ++r) ctx->args.anydrag |= ctx->runs[r].msum[0] != nullptr;
     CK(cudaMemcpyAsync(at<RunDev>(ctx, ctx->lay.runs), ctx->runs.data(), sizeof(RunDev) * ctx->nruns,
                        cudaMemcpyHostToDevice, ctx->stream));
     ctx->graph_dirty = true;

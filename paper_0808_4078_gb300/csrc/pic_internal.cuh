@@ -103,6 +103,7 @@ struct Args {
     const int* work_off;         // [nruns + 1] first work item of each run
     long long* kin;              // [nruns][PIC_NS][4] kinetic energy + momentum (diag steps)
     int nwork;
+    int anydrag;                 // some run has a Krook-drag species (host copy of the run table)
     int nspecies;
     int nruns;
     int ndim;

@@ -34,10 +34,6 @@ struct Smem {
     float F[6][RN];                  // Ex Ey Ez Bx By Bz of the region (origin: tile - 1 cell)
     int J32[3][RN];                  // current of the running batch
     long long J64[3][RN];            // current of the finished batches
-    float ub[3][RN];                 // previous cell-mean momentum (drag)
-    unsigned Mlo[3][RN];             // drag moments (fixed point 2^20), value = Mhi * 4096 + Mlo
-    int Mhi[3][RN];
-    int MC[RN];                      // drag counts
     int pre[PIC_NS * CELLS + 1];     // exclusive prefix of the (species, cell) particle counts
     int cns[PIC_NS * CELLS];         // of which in the stay area
     int scnt[PIC_NS * CELLS];        // stay-area fill of the tile's cells in the next buffer
@@ -46,6 +42,11 @@ struct Smem {
     unsigned long long kin[5];
     int wsum[NW];
     SpeciesParams sp[PIC_NS];
+    // drag arrays last: a launch without drag allocates the shared memory up to `ub` only
+    float ub[3][RN];                 // previous cell-mean momentum (drag)
+    unsigned Mlo[3][RN];             // drag moments (fixed point 2^20), value = Mhi * 4096 + Mlo
+    int Mhi[3][RN];
+    int MC[RN];                      // drag counts
 };
 
 // ------------------------------------------------------------------ gather
@@ -130,7 +131,7 @@ struct Pushed3 {
     bool bad;
 };
 
-template <class A>
+template <bool DRAG, class A>
 __device__ __forceinline__ Pushed3 push3_one(const A& F, const SpeciesParams& P, const RunConst& K,
                                              const float o[3], float ux, float uy, float uz,
                                              float b0, float b1, float b2, float df, int s, unsigned id,
@@ -140,7 +141,7 @@ __device__ __forceinline__ Pushed3 push3_one(const A& F, const SpeciesParams& P,
     float EB[6];
     gather3(F, wx, wy, wz, EB);
     boris(P.qmdt2, EB, ux, uy, uz);
-    if (P.drag) {
+    if (DRAG && P.drag) {
         ux = __fmaf_rn(-df, b0, ux);
         uy = __fmaf_rn(-df, b1, uy);
         uz = __fmaf_rn(-df, b2, uz);
@@ -271,7 +272,8 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total
 }
 
 // ------------------------------------------------------------------ tile kernel
-__global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
+template <bool DRAG>
+__global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const int2 wk = a.work[blockIdx.x];
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
     const long long step = a.ctl->step;
     const int par = a.ctl->parity;
     const bool diag = a.diag_interval > 0 && (step % a.diag_interval) == 0;
-    const bool anydrag = Rp->msum[0] != nullptr;
+    const bool anydrag = DRAG && Rp->msum[0] != nullptr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long cbase = K.cell_off;
 
@@ -414,10 +416,10 @@ __global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
             const int cap = a.cap[s], cst = a.cap_stay[s];
             const Slots& D = a.slot[s][par ^ 1];
             float b0v = 0.f, b1v = 0.f, b2v = 0.f;
-            if (P.drag) { b0v = sm.ub[0][n0]; b1v = sm.ub[1][n0]; b2v = sm.ub[2][n0]; }
+            if (DRAG && P.drag) { b0v = sm.ub[0][n0]; b1v = sm.ub[1][n0]; b2v = sm.ub[2][n0]; }
             const long long g = cbase + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
-            const float df = P.drag ? drag_of(K, P, s, g - cbase) : 0.f;
-            const Pushed3 res = push3_one(SharedFields3{&sm, n0}, P, K, po[r], pu[r][0], pu[r][1], pu[r][2],
+            const float df = DRAG && P.drag ? drag_of(K, P, s, g - cbase) : 0.f;
+            const Pushed3 res = push3_one<DRAG>(SharedFields3{&sm, n0}, P, K, po[r], pu[r][0], pu[r][1], pu[r][2],
                                           b0v, b1v, b2v, df, s, (unsigned)pid[r], step);
             const bool xa = __any_sync(am, res.st[0] != 0), ya = __any_sync(am, res.st[1] != 0),
                        za = __any_sync(am, res.st[2] != 0);
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(NT, 2) push3d_kernel(const Args a) {
             };
             deposit3(add, P, wx, wy, wz, xa, ya, za);
             const int n1 = n0 + res.st[2] * RXY + res.st[1] * RX + res.st[0];
-            if (P.drag) {
+            if (DRAG && P.drag) {
                 add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], f2ll_rn(res.ux * MOM_SCALE));
                 add_split(&sm.Mlo[1][n1], &sm.Mhi[1][n1], f2ll_rn(res.uy * MOM_SCALE));
                 add_split(&sm.Mlo[2][n1], &sm.Mhi[2][n1], f2ll_rn(res.uz * MOM_SCALE));
@@ -549,7 +551,7 @@ __global__ void __launch_bounds__(NT) spill3d_kernel(const Args a) {
             if (P.drag) { b0 = Rp->ubar[0][lc]; b1 = Rp->ubar[1][lc]; b2 = Rp->ubar[2][lc]; }
             const RunConst K = run_const(Rp);
             const float df = P.drag ? drag_of(K, P, s, lc) : 0.f;
-            const Pushed3 r = push3_one(GlobalFields3{Rp, cx, cy, cz}, P, K, o, u0x, u0y, u0z, b0, b1, b2, df, s,
+            const Pushed3 r = push3_one<true>(GlobalFields3{Rp, cx, cy, cz}, P, K, o, u0x, u0y, u0z, b0, b1, b2, df, s,
                                         (unsigned)id, step);
             if (r.bad) {
                 atomicOr(&a.ctl->err, ERR_BADPART);
@@ -595,12 +597,16 @@ cudaError_t launch_push3d(const Args& a, cudaStream_t s) {
     if (a.nwork == 0) return cudaSuccess;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(push3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(push3d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sizeof(Smem));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(push3d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)offsetof(Smem, ub));
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    push3d_kernel<<<a.nwork, NT, sizeof(Smem), s>>>(a);
+    if (a.anydrag) push3d_kernel<true><<<a.nwork, NT, sizeof(Smem), s>>>(a);
+    else push3d_kernel<false><<<a.nwork, NT, offsetof(Smem, ub), s>>>(a);
     return cudaGetLastError();
 }
 
@@ -611,7 +617,8 @@ cudaError_t launch_spill3d(const Args& a, cudaStream_t s) {
 
 cudaError_t preload_push3d() {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, push3d_kernel);
+    cudaError_t e = cudaFuncGetAttributes(&fa, push3d_kernel<true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, push3d_kernel<false>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, spill3d_kernel);
     return e;
 }
