@@ -226,11 +226,12 @@ def _init_dist(world, local_rank):
     return None
 
 
-def _max_over_ranks(dist, vals):
+def _max_over_ranks(dist, vals, device="cuda"):
+    """Element-wise maximum over ranks (the slowest rank's times); identity without a group."""
     if dist is None:
         return vals
     import torch
-    t = torch.tensor(vals, device="cuda", dtype=torch.float64)
+    t = torch.tensor(vals, device=device, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return [float(x) for x in t]
 
