@@ -20,7 +20,7 @@
 // is mixed-precision refinement: the residual of a^n is formed in FP64, the correction
 // d = a^{n+1} - a^n is solved in FP32 by conjugate gradients preconditioned with the exact inverse
 // of the constant-density operator (lap - n_bar) -- a spectral solve by this file's own FP32
-// radix-2 Stockham FFT in shared memory: forward transforms of the rows (fused into the kernels
+// radix-4 Stockham FFT in shared memory: forward transforms of the rows (fused into the kernels
 // that produce the residual), a column pass on strips of 4 columns (forward, division, inverse),
 // inverse transforms of the rows.  Beam density and current are exact integer sums, so they do
 // not depend on particle order; every inner product is a fixed-order two-level sum (per-block
@@ -71,7 +71,7 @@ struct HybDev {
     float* np;                      // plasma density of the current positions
     float* d; float* r; float* z; float* q; float* p0; float* p1;
     float2* ws0;                    // FFT work, [ny][nx]
-    const float2* twx; const float2* twy;   // exp(-2 pi i m / N), m < N/2
+    const float2* twx; const float2* twy;   // exp(-2 pi i m / N), m < N
     const float* lamx; const float* lamy;   // 5-point eigenvalues per axis
     float nbar;                     // preconditioner density
     double* S;                      // solver scalars
@@ -84,49 +84,55 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 }
 
 // ---------------------------------------------------------------- FFT
-// Radix-2 Stockham pass over one row held in shared memory: at span Ns, input j and j + N/2 feed
-// outputs (j / Ns) 2 Ns + (j % Ns) and that + Ns with the twiddle exp(sign i pi (j % Ns) / Ns) =
-// tw[(j % Ns) N / (2 Ns)] (conjugated for the inverse).  Returns the buffer holding the result.
-__device__ float2* fft_smem(float2* b0, float2* b1, int N, int logn, const float2* __restrict__ tw, bool inverse) {
-    const int half = N >> 1;
-    int ls = 0;
-    for (int Ns = 1; Ns < N; Ns <<= 1, ++ls) {
-        for (int j = threadIdx.x; j < half; j += blockDim.x) {
-            const float2 v0 = b0[j];
-            float2 v1 = b0[j + half];
+// Stockham autosort passes over ncol columns held in shared memory (column c at b0 + c ld), all
+// threads of the block taking part.  Radix-4 stages at span Ns: inputs j + r N/4 (r < 4) are
+// twiddled by exp(sign 2 pi i r (j % Ns) / (4 Ns)) = tw[r (j % Ns) N / (4 Ns)] (conjugated for the
+// inverse), combined by the 4-point DFT and written to (j / Ns) 4 Ns + (j % Ns) + r Ns; when
+// log2 N is odd a last radix-2 stage (inputs j, j + N/2, outputs (j / Ns) 2 Ns + (j % Ns) + r Ns)
+// completes the transform.  tw holds exp(-2 pi i m / N) for m < N.  Returns the buffer with the
+// result.
+__device__ __forceinline__ float2 twid(const float2* __restrict__ tw, int m, bool inverse) {
+    const float2 t = tw[m];
+    return inverse ? make_float2(t.x, -t.y) : t;
+}
+__device__ float2* fft_multi(float2* b0, float2* b1, int ncol, int ld, int N, int logn,
+                             const float2* __restrict__ tw, bool inverse) {
+    int Ns = 1, ls = 0;
+    for (; ls + 2 <= logn; Ns <<= 2, ls += 2) {
+        const int q = N >> 2, lq = logn - 2, sh = logn - 2 - ls;
+        for (int t = threadIdx.x; t < ncol * q; t += blockDim.x) {
+            const int c = t >> lq, j = t & (q - 1);
+            const float2* x = b0 + c * ld;
+            float2* y = b1 + c * ld;
             const int k = j & (Ns - 1);
-            float2 t = tw[k << (logn - 1 - ls)];
-            if (inverse) t.y = -t.y;
-            v1 = cmulf(v1, t);
-            const int idx = ((j - k) << 1) + k;
-            b1[idx] = make_float2(v0.x + v1.x, v0.y + v1.y);
-            b1[idx + Ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
+            float2 v0 = x[j], v1 = x[j + q], v2 = x[j + 2 * q], v3 = x[j + 3 * q];
+            if (k) {
+                v1 = cmulf(v1, twid(tw, k << sh, inverse));
+                v2 = cmulf(v2, twid(tw, (2 * k) << sh, inverse));
+                v3 = cmulf(v3, twid(tw, (3 * k) << sh, inverse));
+            }
+            const float2 a0 = make_float2(v0.x + v2.x, v0.y + v2.y), a1 = make_float2(v0.x - v2.x, v0.y - v2.y);
+            const float2 a2 = make_float2(v1.x + v3.x, v1.y + v3.y), a3 = make_float2(v1.x - v3.x, v1.y - v3.y);
+            // -i a3 for the forward transform, +i a3 for the inverse
+            const float2 ia3 = inverse ? make_float2(-a3.y, a3.x) : make_float2(a3.y, -a3.x);
+            const int idx = ((j - k) << 2) + k;
+            y[idx] = make_float2(a0.x + a2.x, a0.y + a2.y);
+            y[idx + Ns] = make_float2(a1.x + ia3.x, a1.y + ia3.y);
+            y[idx + 2 * Ns] = make_float2(a0.x - a2.x, a0.y - a2.y);
+            y[idx + 3 * Ns] = make_float2(a1.x - ia3.x, a1.y - ia3.y);
         }
         __syncthreads();
         float2* t = b0; b0 = b1; b1 = t;
     }
-    return b0;
-}
-
-__device__ __forceinline__ bool solver_done(const HybDev& h) { return h.S[S_DONE] != 0.0; }
-
-// The same passes over ncol columns at once, column c at b + c ld (ld = N + 1 against bank
-// conflicts of the strided loads); all threads of the block take part.
-__device__ float2* fft_multi(float2* b0, float2* b1, int ncol, int ld, int N, int logn,
-                             const float2* __restrict__ tw, bool inverse) {
-    const int half = N >> 1;
-    int ls = 0;
-    for (int Ns = 1; Ns < N; Ns <<= 1, ++ls) {
+    if (ls < logn) {
+        const int half = N >> 1, lh = logn - 1;
         for (int t = threadIdx.x; t < ncol * half; t += blockDim.x) {
-            const int c = t >> (logn - 1), j = t & (half - 1);
+            const int c = t >> lh, j = t & (half - 1);
             const float2* x = b0 + c * ld;
             float2* y = b1 + c * ld;
-            const float2 v0 = x[j];
-            float2 v1 = x[j + half];
             const int k = j & (Ns - 1);
-            float2 w = tw[k << (logn - 1 - ls)];
-            if (inverse) w.y = -w.y;
-            v1 = cmulf(v1, w);
+            const float2 v0 = x[j];
+            const float2 v1 = cmulf(x[j + half], twid(tw, k << (logn - 1 - ls), inverse));
             const int idx = ((j - k) << 1) + k;
             y[idx] = make_float2(v0.x + v1.x, v0.y + v1.y);
             y[idx + Ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
@@ -136,6 +142,14 @@ __device__ float2* fft_multi(float2* b0, float2* b1, int ncol, int ld, int N, in
     }
     return b0;
 }
+
+// One row (N complex values) held in shared memory.
+__device__ __forceinline__ float2* fft_smem(float2* b0, float2* b1, int N, int logn, const float2* __restrict__ tw,
+                                            bool inverse) {
+    return fft_multi(b0, b1, 1, N, N, logn, tw, inverse);
+}
+
+__device__ __forceinline__ bool solver_done(const HybDev& h) { return h.S[S_DONE] != 0.0; }
 
 // Column pass of the spectral solve on a strip of CW columns of the row-major spectrum (ws0
 // holds the rows' forward transforms): forward transforms along y, division by the eigenvalue of
@@ -678,7 +692,7 @@ HLayout hlayout(const pic_hybrid_config* c) {
     L.a = take(8 * nc); L.bp = take(8 * nc); L.f32 = take(8 * nc); L.J = take(8 * nc); L.N = take(8 * nc);
     L.np = take(4 * nc); L.d = take(4 * nc); L.r = take(4 * nc); L.z = take(4 * nc); L.q = take(4 * nc);
     L.p0 = take(4 * nc); L.p1 = take(4 * nc); L.ws0 = take(8 * nc);
-    L.twx = take(8 * (size_t)c->nx / 2); L.twy = take(8 * (size_t)c->ny / 2);
+    L.twx = take(8 * (size_t)c->nx); L.twy = take(8 * (size_t)c->ny);
     L.lamx = take(4 * (size_t)c->nx); L.lamy = take(4 * (size_t)c->ny);
     L.S = take(8 * S_NSLOT); L.part = take(8 * 3 * (size_t)(RGRID > 2048 ? RGRID : 2048)); L.ticket = take(4);
     L.total = align256(off);
@@ -952,11 +966,11 @@ extern "C" int pic_hybrid_init(const pic_hybrid_config* cfg, void* arena, size_t
     d.ticket = reinterpret_cast<unsigned*>(base + L.ticket);
     d.nbar = (float)cfg->n0;   // until a load fixes the mean beam density
     // twiddles and eigenvalues from the host's double-precision sin/cos
-    std::vector<float2> twx(cfg->nx / 2), twy(cfg->ny / 2);
+    std::vector<float2> twx(cfg->nx), twy(cfg->ny);
     std::vector<float> lamx(cfg->nx), lamy(cfg->ny);
     const double pi = 3.14159265358979323846;
-    for (int m = 0; m < cfg->nx / 2; ++m) twx[m] = make_float2((float)std::cos(2 * pi * m / cfg->nx), (float)-std::sin(2 * pi * m / cfg->nx));
-    for (int m = 0; m < cfg->ny / 2; ++m) twy[m] = make_float2((float)std::cos(2 * pi * m / cfg->ny), (float)-std::sin(2 * pi * m / cfg->ny));
+    for (int m = 0; m < cfg->nx; ++m) twx[m] = make_float2((float)std::cos(2 * pi * m / cfg->nx), (float)-std::sin(2 * pi * m / cfg->nx));
+    for (int m = 0; m < cfg->ny; ++m) twy[m] = make_float2((float)std::cos(2 * pi * m / cfg->ny), (float)-std::sin(2 * pi * m / cfg->ny));
     for (int m = 0; m < cfg->nx; ++m) { const double s = std::sin(pi * m / cfg->nx); lamx[m] = (float)(-4.0 / (cfg->dx * cfg->dx) * s * s); }
     for (int m = 0; m < cfg->ny; ++m) { const double s = std::sin(pi * m / cfg->ny); lamy[m] = (float)(-4.0 / (cfg->dy * cfg->dy) * s * s); }
     const size_t nc = (size_t)cfg->nx * cfg->ny;
