@@ -766,7 +766,7 @@ void launch_sort(pic_hybrid* h) {
 }
 constexpr int SORT_LAUNCHES = 8;   // 6 of the binning (zero, histogram, 3 scan passes, scatter) + 2
 
-int row_threads(int n) { return n / 2 < 1024 ? n / 2 : 1024; }
+int row_threads(int n) { return n / 4 < 1024 ? n / 4 : 1024; }   // one radix-4 butterfly per thread
 
 void launch_rhs(pic_hybrid* h) {
     HybDev& d = h->d;
