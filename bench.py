@@ -25,6 +25,14 @@ Other workloads (--workload):
          background Krook nu from {0, 0.01, 0.1, 1}; all runs stepped by one set of launches
          (one CUDA graph per sort interval).  The line also carries the same runs stepped as
          separate engines, one after the other ("per_run"), the unbatched baseline.
+  closure  the learned-closure path: moment recorder on the 3D hot-beam state, network inference
+         on 2^20 samples per call (value = samples/s, roofline on the tensor-core forward
+         kernel) and a full-batch training step
+  hybrid the quasi-neutral hybrid model: 1024 x 1024 nodes, 16 beam particles per cell
+         (16,777,216), T_perp = 0.1, nu = 0.1; a step is the beam push/deposit, the variable-
+         density field solve (CG in a CUDA graph while node) and the update, with a counting
+         sort every 16 steps; roofline basis 44 B/particle + 24 B/node on the push
+--j-filter 1 adds the binomial current filter before the E update (warm2d, hot3d).
 """
 from __future__ import annotations
 

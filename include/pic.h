@@ -299,7 +299,7 @@ int pic_hybrid_stats(pic_hybrid* h, int64_t out4[4]);
  * Synchronises. */
 int pic_hybrid_kernel_times(pic_hybrid* h, pic_kernel_time* out, int max, int* n_out);
 /* Kernels launched by pic_hybrid_step so far: per step the push, the solve set-up and the update,
- * per conjugate-gradient iteration 7 kernels (8 in a graph, whose while node runs only the
+ * per conjugate-gradient iteration 4 kernels (5 in a graph, whose while node runs only the
  * iterations needed; direct launches run max_iter, returning at once after convergence), and 8
  * per sort.  Synchronises; -1 on error. */
 int64_t pic_hybrid_launch_count(pic_hybrid* h);
