@@ -359,9 +359,7 @@ def run_ours(args, rank, world, local_rank):
 def _scan_run(job):
     """Worker: the particles of run r of the scan table (spawned process)."""
     import pic_inputs as pi
-    r, (nx, ny, T, nu), ppc = job
-    return r, pi.weibel_load(ndim=2, nx=nx, ny=ny, ppc=ppc, T_perp_beam=T, T_bg=0.001, nu=nu,
-                             seed=1000 + r, name=f"scan_run{r}_{nx}x{ny}")
+    return pi.scan_run(job)
 
 
 def _partition(table, world):

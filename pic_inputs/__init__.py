@@ -201,6 +201,14 @@ def scan_runs(nruns=256, ppc=32, seed=4, steps=2000, scale=1):
     return out
 
 
+def scan_run(job):
+    """Run r of the scan table at full size: job = (r, (nx, ny, T_perp, nu), ppc) -> (r, workload).
+    A top-level function, so spawned process pools can generate runs in parallel."""
+    r, (nx, ny, T, nu), ppc = job
+    return r, weibel_load(ndim=2, nx=nx, ny=ny, ppc=ppc, T_perp_beam=T, T_bg=0.001, nu=nu,
+                          seed=1000 + r, name=f"scan_run{r}_{nx}x{ny}")
+
+
 # ---------------------------------------------------------------- parallel generation
 # Large loads (hundreds of millions of particles) drawn by a pool of processes into shared
 # memory.  Same distributions as weibel_load; the streams differ (one child seed per chunk of
