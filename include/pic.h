@@ -72,12 +72,14 @@ typedef struct pic_config {
     int32_t nspecies;          /* 1..PIC_MAX_SPECIES */
     int64_t capacity[PIC_MAX_SPECIES];      /* particle capacity per species (< 2^31) */
     int32_t cell_capacity[PIC_MAX_SPECIES]; /* particle slots per cell per species; 0 = automatic
-                                               (2D: 4 x the mean per cell, multiple of 32,
+                                               (2D: 8 x the mean per cell, multiple of 32,
                                                >= 32; 3D: 3 x the mean, multiple of 8, >= 16);
                                                must be >= 2 x capacity / cells */
     int32_t sort_interval;     /* steps between checks for a full counting sort that repacks
-                                  spilled particles (particles whose cell's slots were full; the
-                                  sort runs when a spill list holds > 1/16 of its capacity);
+                                  spilled particles (particles whose cell's slots were full,
+                                  held in a list of a quarter of the species' capacity; the sort
+                                  runs when a list has grown by > 1/16 of its size since the last
+                                  sort);
                                   0 = default (8) */
     int32_t diag_interval;     /* steps between diagnostic records; 0 = no diagnostics */
     int32_t diag_capacity;     /* records kept in the device history ring (>= 1 if diag) */

@@ -210,13 +210,22 @@ __global__ void staged_zero_kernel(Args a, int s, const int* gate) {
     a.ctl->staged[s] = 0;
 }
 
-// Gate of the periodic re-sort: 1 if any species has spilled particles in the current buffer.
-// The spill kernel processes spilled particles every step, so the list only needs repacking
-// before it can fill: re-sort when any species' list holds more than 1/16 of its capacity.
+// Gate of the periodic re-sort.  The spill kernel processes spilled particles every step, so the
+// list only needs repacking before it can fill: re-sort when any species' list has grown by more
+// than 1/16 of its capacity since the last re-sort.  (Particles of cells denser than their slots,
+// as in pinched filaments, stay in the list after a re-sort; counting from the last fill keeps
+// them from triggering a full sort every interval.)
 __global__ void spill_gate_kernel(Args a) {
     int any = 0;
-    for (int s = 0; s < a.nspecies; ++s) any |= *a.slot[s][a.ctl->parity].sn > a.spill_cap[s] / 16;
+    for (int s = 0; s < a.nspecies; ++s)
+        any |= *a.slot[s][a.ctl->parity].sn > a.ctl->spill_base[s] + a.spill_cap[s] / 16;
     *a.gate = any;
+}
+
+// After a gated re-sort: the new fill of every spill list is the base of the next gate.
+__global__ void spill_base_kernel(Args a) {
+    if (*a.gate == 0) return;
+    for (int s = 0; s < a.nspecies; ++s) a.ctl->spill_base[s] = min(*a.slot[s][a.ctl->parity].sn, a.spill_cap[s]);
 }
 
 // Zero the counts and spill counter of species s in the current buffer (before re-binning).
@@ -428,6 +437,7 @@ cudaError_t preload_bins() {
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, scan_add);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, compact_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, spill_gate_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, spill_base_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, clear_current_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, clear_next_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, staged_total_kernel);
@@ -446,7 +456,8 @@ cudaError_t launch_resort(const Args& a, cudaStream_t st, int* launches) {
         bin_kernel<<<152 * 16, NT, 0, st>>>(a, s, -1, true, 0, a.ncell, a.gate);
         l += 8;
     }
-    *launches += l;
+    spill_base_kernel<<<1, 1, 0, st>>>(a);
+    *launches += l + 1;
     return cudaGetLastError();
 }
 

@@ -116,11 +116,13 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
         if (s >= c->nspecies) continue;
         if (g->capacity[s] >= (1ll << 31)) { *err = "capacity must be < 2^31 per species"; return PIC_EINVAL; }
         const long long mean = (g->capacity[s] + g->ncell - 1) / g->ncell;
-        // default slots per cell: 2D 4x the mean in warp multiples (a warp owns a cell), 3D 3x
-        // the mean in multiples of 8 (a thread per particle; 8 floats fill a 32-byte sector)
+        // default slots per cell: 2D 8x the mean in warp multiples (a warp owns a cell; the
+        // beam pinches to ~9x its mean density in the nonlinear filamentation stage), 3D 3x the
+        // mean in multiples of 8 (a thread per particle; 8 floats fill a 32-byte sector; the
+        // spill list takes the filaments' excess)
         long long cap = c->cell_capacity[s];
         if (cap <= 0) {
-            cap = c->ndim == 2 ? ((4 * mean + 31) / 32) * 32 : ((3 * mean + 7) / 8) * 8;
+            cap = c->ndim == 2 ? ((8 * mean + 31) / 32) * 32 : ((3 * mean + 7) / 8) * 8;
             cap = std::max(cap, c->ndim == 2 ? 32ll : 16ll);
         }
         if (cap < 2 || cap > 65535) { *err = "cell_capacity must be in [2, 65535]"; return PIC_EINVAL; }
@@ -134,7 +136,7 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
         if (ci < 1) ci = 1;
         if (ci >= cap) ci = cap > 1 ? cap - 1 : 0;
         g->cap_stay[s] = (int)(cap - ci);
-        long long sc = g->capacity[s] / 16;
+        long long sc = g->capacity[s] / 4;   // room for the excess of dense filaments
         if (sc < 65536) sc = 65536;
         if (sc > g->capacity[s] + 1) sc = g->capacity[s] + 1;
         g->spill_cap[s] = (int)sc;

@@ -83,7 +83,7 @@ struct Ctl {
     int parity;                  // particle buffer read by the next step
     int err;                     // sticky error flags
     int staged[PIC_NS];          // particles in the staging area after the last compaction
-    int pad[2];
+    int spill_base[PIC_NS];      // spill-list fill right after the last re-sort
 };
 
 struct DiagRec {                 // mirrors pic_diag_rec

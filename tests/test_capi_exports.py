@@ -40,8 +40,8 @@ def test_required_bytes_and_config_errors_without_gpu(libpic):
     cfg = pic.Config(2, 64, 64, 1, 0.1, 0.1, 0.1, 0.05, 2, cap(65536, 65536), ccap(), 8, 1, 100,
                      0, 0, 0, 0, 0)
     n = pic.required_bytes(cfg)
-    # automatic cell capacity 4 x 16 = 64 slots; 2 buffers x 2 species x 4096 cells x 64 x 20 B
-    assert n >= 2 * 2 * 4096 * 64 * 20 + 64 * 64 * (24 + 24)
+    # automatic cell capacity 8 x 16 = 128 slots; 2 buffers x 2 species x 4096 cells x 128 x 20 B
+    assert n >= 2 * 2 * 4096 * 128 * 20 + 64 * 64 * (24 + 24)
     bad = pic.Config(2, 60, 64, 1, 0.1, 0.1, 0.1, 0.05, 2, cap(1, 1), ccap(), 8, 1, 100,
                      0, 0, 0, 0, 0)
     with pytest.raises(pic.PicError) as e:
