@@ -569,6 +569,38 @@ __global__ void __launch_bounds__(NT, 3) push2d_kernel(const Args a) {
     }
 }
 
+// Kinetic and momentum sums of spilled particles, kept per thread for its current run and
+// added to the run's totals when the run changes and once at the end: per-particle atomics on
+// the same five words serialised completely when filaments overflowed their cells and tens of
+// millions of particles took this path.  At the end a warp whose lanes all hold the same run
+// reduces in registers and adds once.
+struct KinCache {
+    long long v[5] = {0, 0, 0, 0, 0};
+    int run = -1;
+    __device__ void flush(const Args& a) {
+        if (run < 0) return;
+        long long* K = a.kin + (size_t)run * PIC_NS * 4;
+        if (v[0]) atomicAdd((unsigned long long*)&K[0], (unsigned long long)v[0]);
+        if (v[1]) atomicAdd((unsigned long long*)&K[4], (unsigned long long)v[1]);
+        for (int c = 0; c < 3; ++c)
+            if (v[2 + c]) atomicAdd((unsigned long long*)&K[1 + c], (unsigned long long)v[2 + c]);
+        for (int c = 0; c < 5; ++c) v[c] = 0;
+    }
+    __device__ void use(const Args& a, int r) {
+        if (r != run) { flush(a); run = r; }
+    }
+    // all threads of the warp call this once, after their loops
+    __device__ void finish(const Args& a) {
+        const int m = __reduce_max_sync(0xffffffffu, run);
+        if (__all_sync(0xffffffffu, run < 0 || run == m) && m >= 0) {
+            for (int c = 0; c < 5; ++c)
+                for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+            run = (threadIdx.x & 31) == 0 ? m : -1;
+        }
+        flush(a);
+    }
+};
+
 // ------------------------------------------------------------------ spilled particles
 // Particles that found their cell full: one thread each, global-memory gather and atomics (the
 // same formulas as the tile paths), rebinned into the other buffer.
@@ -576,6 +608,7 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
     const int par = a.ctl->parity;
     const long long step = a.ctl->step;
     const bool diag = a.diag_interval > 0 && (step % a.diag_interval) == 0;
+    KinCache kc;
     for (int s = 0; s < a.nspecies; ++s) {
         const Slots S = a.slot[s][par], D = a.slot[s][par ^ 1];
         const int ns = min(*S.sn, a.spill_cap[s]);
@@ -608,11 +641,8 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
                 continue;
             }
             if (diag) {
-                long long kacc[5] = {0, 0, 0, 0, 0};
-                kin_add(kacc, s, P.w, u0x, u0y, u0z, r.ux, r.uy, r.uz);
-                long long* K = a.kin + (size_t)run * PIC_NS * 4;
-                atomicAdd((unsigned long long*)&K[s * 4], (unsigned long long)(kacc[0] + kacc[1]));
-                for (int c = 0; c < 3; ++c) atomicAdd((unsigned long long*)&K[1 + c], (unsigned long long)kacc[2 + c]);
+                kc.use(a, run);
+                kin_add(kc.v, s, P.w, u0x, u0y, u0z, r.ux, r.uy, r.uz);
             }
             const Win wx = window(ox, r.sx, r.nox), wy = window(oy, r.sy, r.noy);
             const float zf = __fmul_rn(P.jz, r.vz);
@@ -636,6 +666,7 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
             put_imm(D, cap, cst, a.spill_cap[s], g1, r.nox, r.noy, r.ux, r.uy, r.uz, id, &a.ctl->err);
         }
     }
+    kc.finish(a);
 }
 
 }  // namespace
@@ -661,7 +692,7 @@ cudaError_t preload_push2d() {
 }
 
 cudaError_t launch_spill2d(const Args& a, cudaStream_t s) {
-    spill2d_kernel<<<152, NT, 0, s>>>(a);
+    spill2d_kernel<<<152 * 8, NT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
