@@ -102,3 +102,43 @@ def test_planted_hybrid_mistake_is_caught(name, tmp_path):
                         "-p", "no:cacheprovider"], cwd=d, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 1, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
+
+
+# Mistakes in the closed forms (oracle/theory.py: the cold two-fluid relation, Eqs. 11, 12
+# and 14) and in the growth fit (oracle/fit.py), caught by the pins that use them.
+THEORY_MUTATIONS = {
+    "theory.py": {
+        "eq12_collision_term_dropped": ("coeffs = [k2 + 1.0, 1j * k2 * nu,", "coeffs = [k2 + 1.0, 0.0 * nu,"),
+        "eq12_constant_term_sign": ("1j * nu * (b - a * k2)]", "1j * nu * (b + a * k2)]"),
+        "eq11_threshold_sign": ("return cs2 - beta0 * beta0 * nb / n0", "return cs2 + beta0 * beta0 * nb / n0"),
+        "cold_coupling_sign": ("A * k2 * C - k2 * D * D]", "A * k2 * C + k2 * D * D]"),
+        "cold_B_gamma_power": ("B += n / g ** 3", "B += n / g"),
+    },
+    "fit.py": {
+        "fit_energy_not_amplitude": ("best = (0.5 * slope,", "best = (slope,"),
+        "fit_noise_level_ignored": ("ok = (W > lo) & (W < hi)", "ok = (W > 0) & (W < hi)"),
+    },
+}
+_THEORY_CASES = [(f, n) for f in sorted(THEORY_MUTATIONS) for n in sorted(THEORY_MUTATIONS[f])]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("fname,name", _THEORY_CASES)
+def test_planted_theory_mistake_is_caught(fname, name, tmp_path):
+    old, new = THEORY_MUTATIONS[fname][name]
+    src = open(os.path.join(ROOT, "oracle", fname)).read()
+    assert old in src, f"mutation anchor for {name} no longer in oracle/{fname}"
+    d = tmp_path / "copy"
+    shutil.copytree(os.path.join(ROOT, "oracle"), d / "oracle",
+                    ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    shutil.copytree(os.path.join(ROOT, "pic_inputs"), d / "pic_inputs",
+                    ignore=shutil.ignore_patterns("__pycache__"))
+    (d / "tests").mkdir()
+    for f in ("conftest.py", "test_oracle_pins.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), d / "tests" / f)
+    (d / "oracle" / fname).write_text(src.replace(old, new, 1))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
+                        "-k", "dispersion or fit or cold_weibel or below_cold",
+                        "-p", "no:cacheprovider"], cwd=d, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 1, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"

@@ -441,6 +441,14 @@ def test_cold_dispersion_limits():
     assert abs(math.sqrt(-0.5 * ((A - C) - math.sqrt(disc))) - math.sqrt(C)) < 1e-12
     # current neutrality of the load
     assert abs(sum(n * v for n, v in sp)) < 1e-15
+    # k = 0: a uniform E_x drives motion across the drift (transverse mass gamma m), a uniform
+    # E_z motion along it (longitudinal mass gamma^3 m), so w^2 in {0, sum n/gamma,
+    # sum n/gamma^3}
+    gam = [1.0 / math.sqrt(1.0 - v * v) for _, v in sp]
+    want = sorted([0.0, sum(n / g for (n, _), g in zip(sp, gam)),
+                   sum(n / g ** 3 for (n, _), g in zip(sp, gam))])
+    got = sorted(np.roots(theory.cold_dispersion_coeffs(0.0, sp)).real)
+    assert np.allclose(got, want, rtol=0, atol=1e-13), (got, want)
 
 
 def test_resistive_dispersion_small_nu_limit():
@@ -457,6 +465,27 @@ def test_resistive_dispersion_small_nu_limit():
     # collisionless: no growing root
     r = theory.resistive_roots(0.3, cs2, beta0, nb, 0.0)
     assert max(z.imag for z in r) < 1e-9
+
+
+def test_resistive_dispersion_cubic_and_strong_collision_limit():
+    """Every root of the cubic satisfies Eq. (12) in its unexpanded rational form (the cubic is
+    Eq. (12) multiplied by (k^2 (w + i nu) + w), which is nonzero at the roots); and for
+    nu >> |w| the return current no longer screens (k_pe^2 / (1 + i nu/w) -> 0), so Eq. (12)
+    reduces to w^2 = c_s^2 k^2 - w_b^2 beta0^2 (the beam current's field unscreened), approached
+    as 1/nu."""
+    from oracle import theory
+    beta0, nb = 0.9, 0.1
+    for k, cs2, nu in [(0.05, 0.18, 1e-3), (0.3, 0.01, 0.5), (2.0, 0.05, 3.0), (1.0, 0.0, 0.1)]:
+        for w in theory.resistive_roots(k, cs2, beta0, nb, nu):
+            eq12 = cs2 * k * k - nb * beta0 ** 2 * k * k / (k * k + 1.0 / (1.0 + 1j * nu / w))
+            assert abs(w * w - eq12) < 1e-11 * abs(w * w)
+    k, cs2 = 0.5, 0.18
+    g_inf = np.sqrt(nb * beta0 ** 2 - cs2 * k * k)
+    err = []
+    for nu in (1e3, 1e4):
+        g = max(z.imag for z in theory.resistive_roots(k, cs2, beta0, nb, nu))
+        err.append(abs(g / g_inf - 1))
+    assert err[1] < 2e-4 and 8 < err[0] / err[1] < 12, err
 
 
 def test_single_mode_cold_weibel_growth(oracle_lib):
