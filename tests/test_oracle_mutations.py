@@ -1,9 +1,12 @@
 """Planted mistakes in the oracle must fail a pin.
 
-Each case compiles a copy of oracle/pic_oracle.c with one plausible error (a dropped factor,
-a flipped sign, a wrong stagger or index) in a temporary directory, runs the pin suite against
-that copy on the CPU, and requires it to fail.  The hybrid model's oracle (oracle/hybrid.py)
-gets the same treatment against its own pins.  The repository's oracle is never modified.
+Each case copies the oracle to a temporary directory with one plausible error (a dropped
+factor, a flipped sign, a wrong stagger, index or operand) in one of its files, runs the pins of
+that part against the copy on the CPU (the C library is rebuilt there), and requires a pin to
+fail.  Covered: the PIC step (oracle/pic_oracle.c against the main pins), the hybrid model, the
+closed forms and the growth fit, the collision operator and its generator, the current filter,
+the per-cell drag, the closure moments and the network.  The repository's oracle is never
+modified.
 """
 import os
 import shutil
@@ -44,25 +47,33 @@ MUTATIONS = {
 }
 
 
-@pytest.mark.slow
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_planted_mistake_is_caught(name, tmp_path):
-    old, new = MUTATIONS[name]
-    src = open(os.path.join(ROOT, "oracle", "pic_oracle.c")).read()
-    assert old in src, f"mutation anchor for {name} no longer in the oracle"
+def _pins_fail_on_copy(fname, old, new, pin_file, tmp_path, select=None):
+    """Copy the oracle (and the seeded-input module) to tmp_path with one replacement in
+    oracle/<fname>, run the pin file against the copy, and report whether a pin failed."""
+    src = open(os.path.join(ROOT, "oracle", fname)).read()
+    assert old in src, f"mutation anchor no longer in oracle/{fname}: {old!r}"
     d = tmp_path / "copy"
     shutil.copytree(os.path.join(ROOT, "oracle"), d / "oracle",
                     ignore=shutil.ignore_patterns("*.so", "__pycache__"))
     shutil.copytree(os.path.join(ROOT, "pic_inputs"), d / "pic_inputs",
                     ignore=shutil.ignore_patterns("__pycache__"))
     (d / "tests").mkdir()
-    for f in ("conftest.py", "test_oracle_pins.py"):
+    for f in ("conftest.py", pin_file):
         shutil.copy(os.path.join(ROOT, "tests", f), d / "tests" / f)
-    (d / "oracle" / "pic_oracle.c").write_text(src.replace(old, new, 1))
-    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
-                        "-p", "no:cacheprovider"], cwd=d, capture_output=True, text=True,
-                       timeout=600)
-    assert r.returncode == 1, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
+    (d / "oracle" / fname).write_text(src.replace(old, new, 1))
+    cmd = [sys.executable, "-m", "pytest", "tests/" + pin_file, "-q", "-x", "-p", "no:cacheprovider"]
+    if select:
+        cmd += ["-k", select]
+    r = subprocess.run(cmd, cwd=d, capture_output=True, text=True, timeout=600)
+    return r.returncode == 1, r.stdout[-2000:]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    failed, out = _pins_fail_on_copy("pic_oracle.c", old, new, "test_oracle_pins.py", tmp_path)
+    assert failed, f"planted mistake {name} passed every pin:\n{out}"
 
 
 HYBRID_MUTATIONS = {
@@ -89,19 +100,8 @@ HYBRID_MUTATIONS = {
 @pytest.mark.parametrize("name", sorted(HYBRID_MUTATIONS))
 def test_planted_hybrid_mistake_is_caught(name, tmp_path):
     old, new = HYBRID_MUTATIONS[name]
-    src = open(os.path.join(ROOT, "oracle", "hybrid.py")).read()
-    assert old in src, f"mutation anchor for {name} no longer in the hybrid oracle"
-    d = tmp_path / "copy"
-    shutil.copytree(os.path.join(ROOT, "oracle"), d / "oracle",
-                    ignore=shutil.ignore_patterns("*.so", "__pycache__"))
-    (d / "tests").mkdir()
-    for f in ("conftest.py", "test_oracle_hybrid.py"):
-        shutil.copy(os.path.join(ROOT, "tests", f), d / "tests" / f)
-    (d / "oracle" / "hybrid.py").write_text(src.replace(old, new, 1))
-    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_hybrid.py", "-q", "-x",
-                        "-p", "no:cacheprovider"], cwd=d, capture_output=True, text=True,
-                       timeout=600)
-    assert r.returncode == 1, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
+    failed, out = _pins_fail_on_copy("hybrid.py", old, new, "test_oracle_hybrid.py", tmp_path)
+    assert failed, f"planted mistake {name} passed every pin:\n{out}"
 
 
 # Mistakes in the closed forms (oracle/theory.py: the cold two-fluid relation, Eqs. 11, 12
@@ -126,19 +126,57 @@ _THEORY_CASES = [(f, n) for f in sorted(THEORY_MUTATIONS) for n in sorted(THEORY
 @pytest.mark.parametrize("fname,name", _THEORY_CASES)
 def test_planted_theory_mistake_is_caught(fname, name, tmp_path):
     old, new = THEORY_MUTATIONS[fname][name]
-    src = open(os.path.join(ROOT, "oracle", fname)).read()
-    assert old in src, f"mutation anchor for {name} no longer in oracle/{fname}"
-    d = tmp_path / "copy"
-    shutil.copytree(os.path.join(ROOT, "oracle"), d / "oracle",
-                    ignore=shutil.ignore_patterns("*.so", "__pycache__"))
-    shutil.copytree(os.path.join(ROOT, "pic_inputs"), d / "pic_inputs",
-                    ignore=shutil.ignore_patterns("__pycache__"))
-    (d / "tests").mkdir()
-    for f in ("conftest.py", "test_oracle_pins.py"):
-        shutil.copy(os.path.join(ROOT, "tests", f), d / "tests" / f)
-    (d / "oracle" / fname).write_text(src.replace(old, new, 1))
-    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
-                        "-k", "dispersion or fit or cold_weibel or below_cold",
-                        "-p", "no:cacheprovider"], cwd=d, capture_output=True, text=True,
-                       timeout=600)
-    assert r.returncode == 1, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
+    failed, out = _pins_fail_on_copy(fname, old, new, "test_oracle_pins.py", tmp_path,
+                                     select="dispersion or fit or cold_weibel or below_cold")
+    assert failed, f"planted mistake {name} passed every pin:\n{out}"
+
+
+# Mistakes in the collision operator, the current filter and the per-cell drag (oracle C
+# library), in the closure moments (oracle/closure.py) and in the network (oracle/mlp.py),
+# each against its own pin file.
+COMPONENT_MUTATIONS = {
+    "collision_variance": ("pic_oracle.c", "test_oracle_collisions.py",
+                           "orc_collide_ion(u, sqrt(0.5 * coll->nu_coll * g->dt), r);",
+                           "orc_collide_ion(u, sqrt(coll->nu_coll * g->dt), r);"),
+    "collision_cos_term": ("pic_oracle.c", "test_oracle_collisions.py",
+                           "omc = 2.0 * delta * delta / (1.0 + delta * delta);",
+                           "omc = delta * delta / (1.0 + delta * delta);"),
+    "collision_azimuth_sign": ("pic_oracle.c", "test_oracle_collisions.py",
+                               "d[1] = (u[1] * u[2] / uperp) * sn * cp + (u[0] * umag / uperp) * sn * sp",
+                               "d[1] = (u[1] * u[2] / uperp) * sn * cp - (u[0] * umag / uperp) * sn * sp"),
+    "philox_multiplier": ("pic_oracle.c", "test_oracle_collisions.py",
+                          "p0 = (uint64_t)0xD2511F53u * c0", "p0 = (uint64_t)0xD2511F55u * c0"),
+    "filter_neighbour": ("pic_oracle.c", "test_oracle_filter.py",
+                         "F[c] = 0.25 * (t[m] + 2.0 * t[c] + t[p]);", "F[c] = 0.25 * (t[m] + 2.0 * t[c] + t[c]);"),
+    "filter_one_axis": ("pic_oracle.c", "test_oracle_filter.py",
+                        "for (int axis = 0; axis < g->ndim; axis++) {", "for (int axis = 0; axis < 1; axis++) {"),
+    "drag_map_negative_rate": ("pic_oracle.c", "test_oracle_closure_drag.py",
+                               "df = r > 0.0 ? 1.0 - exp(-r * g->dt) : 0.0;", "df = 1.0 - exp(-r * g->dt);"),
+    "closure_tperp_half": ("closure.py", "test_oracle_closure.py",
+                           'out[4 + 2 * si] = 0.5 * (var["x"] + var["y"])', 'out[4 + 2 * si] = (var["x"] + var["y"])'),
+    "closure_vxb_sign": ("closure.py", "test_oracle_closure.py",
+                         "fz = s.q * (EB[:, 2] + vx * EB[:, 4] - vy * EB[:, 3])",
+                         "fz = s.q * (EB[:, 2] + vx * EB[:, 4] + vy * EB[:, 3])"),
+    "closure_label_sign": ("closure.py", "test_oracle_closure.py",
+                           "nu + (np.asarray(fz_mean) - np.asarray(fz_p)) / uz_p",
+                           "nu + (np.asarray(fz_p) - np.asarray(fz_mean)) / uz_p"),
+    "closure_w_es_no_zmean": ("closure.py", "test_oracle_closure.py",
+                              "zmean = Ec.mean(axis=0, keepdims=True) if sim.ndim == 3 else Ec",
+                              "zmean = 0.0 * Ec"),
+    "mlp_dsilu": ("mlp.py", "test_oracle_mlp.py",
+                  "return s * (1.0 + z * (1.0 - s))", "return s * (1.0 + z * s)"),
+    "mlp_w2_gradient_operand": ("mlp.py", "test_oracle_mlp.py",
+                                'g["W2"] = d2.T @ c["h1"]', 'g["W2"] = d2.T @ c["h2"]'),
+    "mlp_adam_bias_correction": ("mlp.py", "test_oracle_mlp.py",
+                                 "vh = v / (1 - beta2 ** t)", "vh = v"),
+    "mlp_bf16_ties_up": ("mlp.py", "test_oracle_mlp.py",
+                         "r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16", "r = ((b + 0x8000) >> 16) << 16"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(COMPONENT_MUTATIONS))
+def test_planted_component_mistake_is_caught(name, tmp_path):
+    fname, pin_file, old, new = COMPONENT_MUTATIONS[name]
+    failed, out = _pins_fail_on_copy(fname, old, new, pin_file, tmp_path)
+    assert failed, f"planted mistake {name} passed every pin:\n{out}"
