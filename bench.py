@@ -208,14 +208,33 @@ def cpu_baseline(args, seconds=15.0):
                       f"{steps} steps in {el:.1f} s, FP64 single-threaded C"}
 
 
+def units_per_step(args):
+    """Units of the metric one step of the workload processes (particles, or samples per call)."""
+    if args.workload == "closure":
+        return args.samples
+    if args.workload == "hybrid":
+        return args.n * args.n * args.ppc
+    if args.workload == "warm2d":
+        return 2 * args.n * args.n * args.ppc
+    if args.workload == "hot3d":
+        nx, ny, nz = args.grid3
+        return 2 * nx * ny * nz * args.ppc
+    import pic_inputs as pi
+    return sum(2 * nx * ny * args.ppc for nx, ny, _, _ in pi.scan_table(args.runs))
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     cb = cpu_baseline(args, seconds=max(5.0, 3.0 * args.steps))
     metric = "closure inference samples/s" if args.workload == "closure" else METRIC
+    units = units_per_step(args)
     line = {"impl": "reference", "metric": metric, "value": cb["value"], "unit": cb["unit"],
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            # the oracle runs a bounded sample; a full step of the workload at its rate takes:
+            "ms_per_step": units / cb["value"] * 1e3, "units_per_step": units,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args), "oracle_sample": cb["sample"]},
             "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"],
                              "value": cb["value"], "unit": cb["unit"]},
