@@ -220,6 +220,29 @@ int pic_get_stats(pic_ctx* ctx, pic_stats* out);
  * Synchronises the context's stream; nu may be freed on return. */
 int pic_set_drag_map(pic_ctx* ctx, int run, int s, const float* nu, int32_t bx, int32_t by);
 
+/* Checkpoint and resume.  pic_checkpoint synchronises the context's stream and writes its whole
+ * state to the file `path`: the device arena (particles in both buffers, spill lists, fields, J,
+ * drag moments and maps, diagnostic history, control block with the step counter) and the host
+ * state (species parameters, particle counts, Krook and collision settings, step count).  It
+ * writes `path`.tmp first and renames it, so an existing checkpoint is replaced only by a
+ * complete one.  A context with a sticky device error is not written (that error is returned).
+ * pic_restore loads such a file into a context created by pic_init / pic_init_batch with the
+ * same configuration (grids, capacities, species count, cell_capacity, dx..dt, sort_interval,
+ * diag_interval / diag_capacity, track_ids, j_filter, PIC_FLAG_KEEP_J; PIC_FLAG_PROFILE and
+ * PIC_FLAG_NO_GRAPH may differ), with or without species loaded; it replaces the context's whole
+ * state and the run continues bit for bit as if it had not been interrupted (integer current
+ * deposits, counter-based collision draws keyed by particle id and step).  A file of another
+ * configuration, another library version, or of the wrong size returns PIC_EINVAL and leaves
+ * the context unchanged (every check precedes the first copy; a read or CUDA error during the
+ * copy leaves a partial state).  Launch counters and profiling timers are not part of the state.
+ * Both synchronise; the file is read/written through a 64 MB host buffer. */
+int pic_checkpoint(pic_ctx* ctx, const char* path);
+int pic_restore(pic_ctx* ctx, const char* path);
+
+/* Particles of species s loaded in run `run` (after a restore: those of the checkpoint); -1 on a
+ * bad argument. */
+int64_t pic_loaded_count(const pic_ctx* ctx, int run, int s);
+
 /* Binary electron-ion collisions of species s in run `run` (the paper's collision model; its
  * scheme is not given there): every step, after the Boris push and any Krook drag, each particle's
  * momentum turns by a scattering angle theta with tan(theta / 2) ~ N(0, nu dt / 2) about a

@@ -136,6 +136,9 @@ _SIGNATURES = {
     "pic_hybrid_launch_count": (ctypes.c_int64, [_VP]),
     "pic_hybrid_step_count": (ctypes.c_int64, [_VP]),
     "pic_hybrid_free": (None, [_VP]),
+    "pic_checkpoint": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "pic_restore": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "pic_loaded_count": (ctypes.c_int64, [_VP, ctypes.c_int, ctypes.c_int]),
     "pic_launch_count": (ctypes.c_int64, [_VP]),
     "pic_step_count": (ctypes.c_int64, [_VP]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
@@ -353,6 +356,17 @@ class Engine:
         nu = nu.contiguous()
         self._torch.cuda.current_stream(self.device).synchronize()
         _check(lib().pic_set_drag_map(self._ctx, run, s, _VP(nu.data_ptr()), bx, by), self._ctx)
+
+    def checkpoint(self, path):
+        """Write the whole run state to `path` (pic_checkpoint)."""
+        _check(lib().pic_checkpoint(self._ctx, os.fsencode(path)), self._ctx)
+
+    def restore(self, path):
+        """Replace this engine's state by a checkpoint of the same configuration (pic_restore)."""
+        _check(lib().pic_restore(self._ctx, os.fsencode(path)), self._ctx)
+        for r in range(len(self.runs)):
+            for s in range(PIC_MAX_SPECIES):
+                self.loaded[r][s] = int(lib().pic_loaded_count(self._ctx, r, s))
 
     def launch_count(self):
         return int(lib().pic_launch_count(self._ctx))

@@ -1077,6 +1077,238 @@ extern "C" int pic_mlp_status(int clear) {
     return PIC_OK;
 }
 
+// ============================================================== checkpoint / restore
+//
+// File layout (little-endian, this library's struct layouts, checked by size fields):
+//   CkptHeader; per run a CkptRunGeo (checked against the restoring context) and a CkptRunState
+//   (host-side run state); then the context's arena bytes [0, layout total).
+// Device pointers are never read back from a file: a restore rebuilds every pointer of the run
+// table from the restoring context's own layout, so a file can only change values, not addresses.
+namespace {
+
+constexpr char kCkptMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
+constexpr uint32_t kCkptVersion = 1;
+constexpr size_t kCkptChunk = size_t(64) << 20;
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, header_bytes, rungeo_bytes, runstate_bytes, species_bytes, ctl_bytes;
+    int32_t ndim, nspecies, nruns, track_ids, keep_j, j_filter;
+    int32_t diag_interval, diag_capacity, sort_interval, reserved;
+    int32_t cap[PIC_NS], cap_stay[PIC_NS], spill_cap[PIC_NS];
+    double dx, dy, dz, dt;
+    uint64_t layout_total;
+    int64_t host_step;
+    double q[PIC_NS];
+    int32_t q_set[PIC_NS];
+};
+
+struct CkptRunGeo {
+    int64_t nx, ny, nz;
+    int64_t capacity[PIC_NS];
+};
+
+struct CkptRunState {
+    SpeciesParams sp[PIC_NS];
+    int32_t shift;
+    float jscale, jfscale;
+    int32_t drag_moments;          // msum / mcnt / ubar published (a Krook species was loaded)
+    int32_t dragmap[PIC_NS];       // per-cell drag map set for species s
+    int32_t reserved;
+    int64_t loaded[PIC_NS];
+    double nu[PIC_NS];
+};
+
+CkptHeader ckpt_header(const pic_ctx* ctx) {
+    CkptHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, kCkptMagic, sizeof h.magic);
+    h.version = kCkptVersion;
+    h.header_bytes = sizeof(CkptHeader);
+    h.rungeo_bytes = sizeof(CkptRunGeo);
+    h.runstate_bytes = sizeof(CkptRunState);
+    h.species_bytes = sizeof(SpeciesParams);
+    h.ctl_bytes = sizeof(Ctl);
+    const pic_config& c = ctx->cfg;
+    h.ndim = c.ndim;
+    h.nspecies = c.nspecies;
+    h.nruns = ctx->nruns;
+    h.track_ids = c.track_ids ? 1 : 0;
+    h.keep_j = (c.flags & PIC_FLAG_KEEP_J) ? 1 : 0;
+    h.j_filter = c.j_filter;
+    h.diag_interval = c.diag_interval;
+    h.diag_capacity = c.diag_interval > 0 ? c.diag_capacity : 0;
+    h.sort_interval = ctx->sort_interval;
+    for (int s = 0; s < PIC_NS; ++s) {
+        h.cap[s] = ctx->geo.cap[s];
+        h.cap_stay[s] = ctx->geo.cap_stay[s];
+        h.spill_cap[s] = ctx->geo.spill_cap[s];
+        h.q[s] = ctx->q[s];
+        h.q_set[s] = ctx->q_set[s] ? 1 : 0;
+    }
+    h.dx = c.dx; h.dy = c.dy; h.dz = c.dz; h.dt = c.dt;
+    h.layout_total = ctx->lay.total;
+    h.host_step = ctx->host_step;
+    return h;
+}
+
+CkptRunGeo ckpt_rungeo(const pic_ctx* ctx, int r) {
+    CkptRunGeo g;
+    std::memset(&g, 0, sizeof g);
+    const RunGeo& G = ctx->geo.runs[r];
+    g.nx = G.nx; g.ny = G.ny; g.nz = G.nz;
+    for (int s = 0; s < PIC_NS; ++s) g.capacity[s] = G.capacity[s];
+    return g;
+}
+
+// Everything of the header that fixes the arena layout or the step schedule; host_step, q and
+// q_set are state, not geometry.
+bool ckpt_same_geometry(const CkptHeader& a, const CkptHeader& b) {
+    CkptHeader x = a, y = b;
+    x.host_step = y.host_step = 0;
+    for (int s = 0; s < PIC_NS; ++s) { x.q[s] = y.q[s] = 0; x.q_set[s] = y.q_set[s] = 0; }
+    return std::memcmp(&x, &y, sizeof x) == 0;
+}
+
+struct File {
+    FILE* f = nullptr;
+    ~File() { if (f) std::fclose(f); }
+};
+
+}  // namespace
+
+extern "C" int pic_checkpoint(pic_ctx* ctx, const char* path) {
+    if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    if (!path || !*path) return fail(ctx, PIC_EINVAL, "null or empty path");
+    int rc = pic_sync(ctx);              // the state of the last queued step, and its sticky flags
+    if (rc) return rc;
+    const std::string tmp = std::string(path) + ".tmp";
+    {
+        File out;
+        out.f = std::fopen(tmp.c_str(), "wb");
+        if (!out.f) return fail(ctx, PIC_EINVAL, "cannot open %s for writing", tmp.c_str());
+        const CkptHeader h = ckpt_header(ctx);
+        bool ok = std::fwrite(&h, sizeof h, 1, out.f) == 1;
+        for (int r = 0; ok && r < ctx->nruns; ++r) {
+            const CkptRunGeo g = ckpt_rungeo(ctx, r);
+            const RunDev& R = ctx->runs[r];
+            CkptRunState st;
+            std::memset(&st, 0, sizeof st);
+            for (int s = 0; s < PIC_NS; ++s) {
+                st.sp[s] = R.sp[s];
+                st.dragmap[s] = R.dragmap[s] ? 1 : 0;
+                st.loaded[s] = ctx->loaded[(size_t)r * PIC_NS + s];
+                st.nu[s] = ctx->nu[(size_t)r * PIC_NS + s];
+            }
+            st.shift = R.shift;
+            st.jscale = R.jscale;
+            st.jfscale = R.jfscale;
+            st.drag_moments = R.msum[0] ? 1 : 0;
+            ok = std::fwrite(&g, sizeof g, 1, out.f) == 1 && std::fwrite(&st, sizeof st, 1, out.f) == 1;
+        }
+        std::vector<char> buf(std::min(kCkptChunk, ctx->lay.total));
+        cudaError_t ce = cudaSuccess;
+        for (size_t off = 0; ok && off < ctx->lay.total; off += buf.size()) {
+            const size_t n = std::min(buf.size(), ctx->lay.total - off);
+            ce = cudaMemcpyAsync(buf.data(), ctx->arena + off, n, cudaMemcpyDeviceToHost, ctx->stream);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+            ok = ce == cudaSuccess && std::fwrite(buf.data(), 1, n, out.f) == n;
+        }
+        ok = ok && std::fflush(out.f) == 0;
+        const int cl = std::fclose(out.f);
+        out.f = nullptr;
+        if (!ok || cl != 0) {
+            std::remove(tmp.c_str());
+            if (ce != cudaSuccess) return fail(ctx, PIC_ECUDA, "pic_checkpoint: %s", cudaGetErrorString(ce));
+            return fail(ctx, PIC_EINVAL, "writing %s failed", tmp.c_str());
+        }
+    }
+    if (std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return fail(ctx, PIC_EINVAL, "cannot rename %s to %s", tmp.c_str(), path);
+    }
+    return PIC_OK;
+}
+
+extern "C" int pic_restore(pic_ctx* ctx, const char* path) {
+    if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    if (!path || !*path) return fail(ctx, PIC_EINVAL, "null or empty path");
+    File in;
+    in.f = std::fopen(path, "rb");
+    if (!in.f) return fail(ctx, PIC_EINVAL, "cannot open %s", path);
+    CkptHeader h;
+    if (std::fread(&h, sizeof h, 1, in.f) != 1) return fail(ctx, PIC_EINVAL, "%s: short header", path);
+    if (std::memcmp(h.magic, kCkptMagic, sizeof h.magic) != 0) return fail(ctx, PIC_EINVAL, "%s: not a checkpoint", path);
+    if (h.version != kCkptVersion || h.header_bytes != sizeof(CkptHeader) || h.rungeo_bytes != sizeof(CkptRunGeo) ||
+        h.runstate_bytes != sizeof(CkptRunState) || h.species_bytes != sizeof(SpeciesParams) || h.ctl_bytes != sizeof(Ctl))
+        return fail(ctx, PIC_EINVAL, "%s: written by an incompatible library version", path);
+    if (!ckpt_same_geometry(h, ckpt_header(ctx)))
+        return fail(ctx, PIC_EINVAL, "%s: configuration differs from this context's (grid, species, slots, "
+                                     "dx, dt, intervals, ids, filter or KEEP_J)", path);
+    if (h.host_step < 0) return fail(ctx, PIC_EINVAL, "%s: bad step count", path);
+    std::vector<CkptRunState> st(ctx->nruns);
+    for (int r = 0; r < ctx->nruns; ++r) {
+        CkptRunGeo g;
+        if (std::fread(&g, sizeof g, 1, in.f) != 1 || std::fread(&st[r], sizeof st[r], 1, in.f) != 1)
+            return fail(ctx, PIC_EINVAL, "%s: short run table", path);
+        const CkptRunGeo mine = ckpt_rungeo(ctx, r);
+        if (std::memcmp(&g, &mine, sizeof g) != 0)
+            return fail(ctx, PIC_EINVAL, "%s: run %d has another grid or capacity than this context's", path, r);
+        for (int s = 0; s < PIC_NS; ++s)
+            if (st[r].loaded[s] < 0 || st[r].loaded[s] > mine.capacity[s] || !(st[r].nu[s] >= 0))
+                return fail(ctx, PIC_EINVAL, "%s: run %d: bad species state", path, r);
+    }
+    // the arena image must be exactly what is left of the file
+    const long here = std::ftell(in.f);
+    if (here < 0 || std::fseek(in.f, 0, SEEK_END) != 0) return fail(ctx, PIC_EINVAL, "%s: cannot seek", path);
+    const long end = std::ftell(in.f);
+    if (end < here || (unsigned long long)(end - here) != (unsigned long long)ctx->lay.total)
+        return fail(ctx, PIC_EINVAL, "%s: arena image has %lld bytes, this context needs %zu", path,
+                    (long long)(end - here), ctx->lay.total);
+    if (std::fseek(in.f, here, SEEK_SET) != 0) return fail(ctx, PIC_EINVAL, "%s: cannot seek", path);
+
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::vector<char> buf(std::min(kCkptChunk, ctx->lay.total));
+    for (size_t off = 0; off < ctx->lay.total; off += buf.size()) {
+        const size_t n = std::min(buf.size(), ctx->lay.total - off);
+        if (std::fread(buf.data(), 1, n, in.f) != n) return fail(ctx, PIC_EINVAL, "%s: short arena image", path);
+        CK(cudaMemcpyAsync(ctx->arena + off, buf.data(), n, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    // host state; pointers from this context's layout
+    const Layout& L = ctx->lay;
+    for (int r = 0; r < ctx->nruns; ++r) {
+        RunDev& R = ctx->runs[r];
+        for (int s = 0; s < PIC_NS; ++s) {
+            R.sp[s] = st[r].sp[s];
+            R.dragmap[s] = (st[r].dragmap[s] && s < ctx->cfg.nspecies) ? at<float>(ctx, L.dragmap[s][r]) : nullptr;
+            ctx->loaded[(size_t)r * PIC_NS + s] = st[r].loaded[s];
+            ctx->nu[(size_t)r * PIC_NS + s] = st[r].nu[s];
+        }
+        R.shift = st[r].shift;
+        R.jscale = st[r].jscale;
+        R.jfscale = st[r].jfscale;
+        for (int d = 0; d < 3; ++d) {
+            R.msum[d] = st[r].drag_moments ? at<long long>(ctx, L.msum[d][r]) : nullptr;
+            R.ubar[d] = st[r].drag_moments ? at<float>(ctx, L.ubar[d][r]) : nullptr;
+        }
+        R.mcnt = st[r].drag_moments ? at<int>(ctx, L.mcnt[r]) : nullptr;
+    }
+    for (int s = 0; s < PIC_NS; ++s) {
+        ctx->q[s] = h.q[s];
+        ctx->q_set[s] = h.q_set[s] != 0;
+    }
+    ctx->host_step = h.host_step;
+    int rc = upload_runs(ctx);           // overwrites the run table of the image
+    if (rc) return rc;
+    return pic_sync(ctx);
+}
+
+extern "C" int64_t pic_loaded_count(const pic_ctx* ctx, int run, int s) {
+    if (!ctx || run < 0 || run >= ctx->nruns || s < 0 || s >= PIC_NS) return -1;
+    return ctx->loaded[(size_t)run * PIC_NS + s];
+}
+
 extern "C" int64_t pic_launch_count(const pic_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
 extern "C" int64_t pic_step_count(const pic_ctx* ctx) { return ctx ? ctx->host_step : -1; }

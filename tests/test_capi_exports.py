@@ -63,6 +63,14 @@ def test_required_bytes_and_config_errors_without_gpu(libpic):
         pic.required_bytes(tight)
 
 
+def test_checkpoint_argument_errors_without_gpu(libpic):
+    import paper_0808_4078_gb300 as pic
+    lib = pic.lib()
+    assert lib.pic_checkpoint(None, b"/nonexistent/x.ckpt") == -1
+    assert lib.pic_restore(None, b"/nonexistent/x.ckpt") == -1
+    assert lib.pic_loaded_count(None, 0, 0) == -1
+
+
 def test_hybrid_required_bytes_and_config_errors_without_gpu(libpic):
     import paper_0808_4078_gb300 as pic
     lib = pic.lib()
