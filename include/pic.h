@@ -49,10 +49,18 @@ extern "C" {
 
 #define PIC_OK 0
 #define PIC_EINVAL (-1)     /* bad argument or configuration */
-#define PIC_ENOMEM (-2)     /* arena smaller than pic_required_bytes(), or capacity exceeded */
+#define PIC_ENOMEM (-2)     /* arena smaller than pic_required_bytes(), capacity exceeded, or (device,
+                               sticky) a species' spill list full: raise cell_capacity */
 #define PIC_ECUDA (-3)      /* a CUDA runtime call failed */
-#define PIC_EOVERFLOW (-4)  /* fixed-point headroom exceeded or a particle moved >= 1 cell */
-#define PIC_EBADPART (-5)   /* non-finite or out-of-range particle data */
+#define PIC_EOVERFLOW (-4)  /* fixed-point headroom exceeded.  Reserved: the per-run shift S bounds
+                               every current term by 2^21 (|v| < c), so no int32 warp sum or int64
+                               node sum can overflow and this version never returns it */
+#define PIC_EBADPART (-5)   /* non-finite or out-of-range particle data at load (nothing is
+                               loaded), or on the device a particle whose new position would lie
+                               a cell or more away (a non-finite momentum, e.g. from non-finite
+                               fields; the Courant check at init excludes it otherwise): the
+                               particle stays where it was, unmoved and not deposited, and the
+                               sticky flag fails the next synchronising call */
 #define PIC_ETIMEOUT (-6)   /* a bounded device wait gave up */
 #define PIC_ESTATE (-7)     /* call not valid in the current state */
 
