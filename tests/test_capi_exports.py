@@ -63,6 +63,46 @@ def test_required_bytes_and_config_errors_without_gpu(libpic):
         pic.required_bytes(tight)
 
 
+def _batch_bytes(cfg, dims, caps):
+    import numpy as np
+    import paper_0808_4078_gb300 as pic
+    d = np.ascontiguousarray(dims, dtype=np.int32).reshape(-1)
+    c = np.ascontiguousarray(caps, dtype=np.int64).reshape(-1)
+    n = ctypes.c_size_t(0)
+    rc = pic.lib().pic_required_bytes_batch(ctypes.byref(cfg), len(d) // 3, d.ctypes.data_as(ctypes.c_void_p),
+                                            c.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n))
+    return rc, n.value
+
+
+def test_batch_geometry_without_gpu(libpic):
+    """Host-side geometry of batches and 3D grids: sizes add up, bad entries are refused."""
+    import paper_0808_4078_gb300 as pic
+    z2 = lambda: (ctypes.c_int64 * 2)(0, 0)
+    cfg = pic.Config(2, 0, 0, 1, 0.1, 0.1, 0.1, 0.05, 2, z2(), (ctypes.c_int32 * 2)(32, 32), 8, 1,
+                     16, 0, 0, 0, 0, 0, 0)
+    rc1, a = _batch_bytes(cfg, [64, 64, 1], [64 * 64 * 4] * 2)
+    rc2, b = _batch_bytes(cfg, [32, 48, 1], [32 * 48 * 4] * 2)
+    rc3, ab = _batch_bytes(cfg, [64, 64, 1, 32, 48, 1], [64 * 64 * 4] * 2 + [32 * 48 * 4] * 2)
+    assert rc1 == rc2 == rc3 == 0
+    assert max(a, b) < ab <= a + b + (1 << 20)                   # one arena holds both runs
+    assert _batch_bytes(cfg, [64, 64, 1, 30, 48, 1], [1] * 4)[0] == -1       # not a tile multiple
+    assert _batch_bytes(cfg, [64, 64, 1, 0, 48, 1], [1] * 4)[0] == -1        # empty grid
+    assert _batch_bytes(cfg, [64, 64, 1], [1, -1])[0] == -1                  # negative capacity
+    assert _batch_bytes(cfg, [64, 64, 1], [1 << 31, 0])[0] == -1             # >= 2^31 particles
+    cfg.cell_capacity[0] = cfg.cell_capacity[1] = 65535
+    assert _batch_bytes(cfg, [4096, 4096, 1], [1, 1])[0] == -1               # slots >= 2^31
+    cfg.cell_capacity[0] = cfg.cell_capacity[1] = 0
+    cfg.tile_x = 8
+    assert _batch_bytes(cfg, [64, 64, 1], [1, 1])[0] == -1                   # 2D tiles are 16 x 16
+    c3 = pic.Config(3, 16, 16, 8, 0.1, 0.1, 0.1, 0.05, 2, z2(), (ctypes.c_int32 * 2)(0, 0), 8, 1,
+                    16, 0, 0, 0, 0, 0, 0)
+    rc, n3 = _batch_bytes(c3, [16, 16, 8], [16 * 16 * 8 * 8] * 2)
+    assert rc == 0 and n3 > 2 * 2 * 2048 * 24 * 24       # species x buffers x cells x 3*8 slots x 24 B
+    assert _batch_bytes(c3, [16, 16, 6], [1, 1])[0] == -1                     # z not a multiple of 4
+    c3.dt = 0.06                                                              # Courant: 0.06 sqrt(300) > 1
+    assert _batch_bytes(c3, [16, 16, 8], [1, 1])[0] == -1
+
+
 def test_checkpoint_argument_errors_without_gpu(libpic):
     import paper_0808_4078_gb300 as pic
     lib = pic.lib()
