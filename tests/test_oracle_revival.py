@@ -1,4 +1,8 @@
-"""The paper's cases (c) and (d) on the oracle: a hot beam (T_perp ~ 70 keV = 0.137 m c^2,
+"""The paper's four simulation cases on the oracle.  Cases (a) and (b): a cold beam filaments
+with and without collisions of the background (W_B grows by more than 30x in a 24^2 box within
+t = 25; measured ~200x, ~200x with the Krook reading, ~700x with binary collisions).
+
+Cases (c) and (d): a hot beam (T_perp ~ 70 keV = 0.137 m c^2,
 v_b = 0.9 c, n_p / n_b = 9) in a collisionless background shows no filamentation growth, and the
 same beam in a collisional background grows again (the simulation section: collisions of the
 return-current electrons revive the instability).  Collision rate nu = 0.15 w_p as in the paper.
@@ -67,3 +71,16 @@ def test_hybrid_model_collisions_revive_the_instability():
     g0, g1 = _hybrid(0.0), _hybrid(NU)
     assert g0 < 20.0, (g0, g1)
     assert g1 > 60.0, (g0, g1)
+
+
+@pytest.mark.parametrize("kind", ["none", "krook", "binary"])
+def test_cold_beam_filaments_with_and_without_collisions(oracle_lib, kind):
+    wl = pi.weibel_load(ndim=2, nx=24, ny=24, ppc=16, gamma_b=GB, T_perp_beam=0.0, seed=9,
+                        nu=NU if kind == "krook" else 0.0)
+    sim = oracle_lib.Simulation.from_workload(wl)
+    if kind == "binary":
+        sim.set_collisions(1, NU, 12345)
+    sim.step(500)
+    WB = sim.history_array("WB")
+    W, t = WB[:, 0] + WB[:, 1], sim.history_array("t")
+    assert W[-50:].mean() / W[(t > 0.5) & (t <= 2.5)].mean() > 30.0
