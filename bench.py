@@ -58,7 +58,7 @@ BYTES_PER_CELL = 64
 # profile summaries named here).  They describe the kernels as captured: re-capture after
 # changing a kernel.
 NCU_TRAFFIC_PER_PARTICLE = {
-    2: (58.95, "profiles/push2d_warm_beam_krook_2d.md (256x256, 64 ppc per species)"),
+    2: (47.54, "profiles/push2d_warm_beam_krook_2d.md (256x256, 64 ppc per species)"),
     3: (154.58, "profiles/push3d_hot_beam_3d.md (128x128x64, 8 ppc per species)"),
 }
 
@@ -318,7 +318,8 @@ def run_ours(args, rank, world, local_rank):
     cap = [s.n for s in wl.species]
     eng = pic.Engine(wl.ndim, wl.nx, wl.ny, wl.nz, dx=wl.dx, dt=wl.dt, capacity=cap,
                      sort_interval=args.sort, diag_interval=args.diag, diag_capacity=4096,
-                     flags=pic.PIC_FLAG_PROFILE, device=f"cuda:{local_rank}", j_filter=args.j_filter)
+                     flags=pic.PIC_FLAG_PROFILE, device=f"cuda:{local_rank}", j_filter=args.j_filter,
+                     tile=args.tile if wl.ndim == 2 else (0, 0), ctas_per_sm=args.ctas)
     # ---------------- end to end through the public API from (pinned) host buffers
     host = []
     for s in wl.species:
@@ -796,6 +797,9 @@ def main():
     ap.add_argument("--ppc", type=int, default=None,
                     help="particles per cell per species (default 64 / 8 / 32)")
     ap.add_argument("--sort", type=int, default=8)
+    ap.add_argument("--tile", type=lambda t: tuple(int(x) for x in t.split("x")), default=(0, 0),
+                    help="2D particle-kernel tile, e.g. 32x8 (0x0 = default)")
+    ap.add_argument("--ctas", type=int, default=0, help="2D particle kernel: CTAs per SM (2 or 3; 0 = default)")
     ap.add_argument("--diag", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-run", action="store_true", help="scan: skip the per-run baseline")

@@ -93,13 +93,16 @@ typedef struct pic_config {
     int32_t diag_capacity;     /* records kept in the device history ring (>= 1 if diag) */
     int32_t track_ids;         /* 1: carry an int32 id per particle (its load index) */
     int32_t flags;             /* PIC_FLAG_* */
-    int32_t tile_x, tile_y, tile_z; /* 0 = default; the kernels are built for 16 x 16 (2D) and
-                                       8 x 8 x 4 (3D), other values are rejected */
+    int32_t tile_x, tile_y, tile_z; /* cells per tile of the particle kernels: 2D 16 x 16,
+                                       32 x 8 or 8 x 32 (tile_z ignored); 3D 8 x 8 x 4; other
+                                       values are rejected; 0 = default (16 x 16 in 2D) */
     int32_t j_filter;          /* 1: smooth the step's current with one binomial 1-2-1 pass per
                                   axis (periodic) before the E update, against numerical
                                   Cherenkov radiation of the relativistic beam on the Yee grid
                                   (not in the paper); the sum is exact in int64 and scaled by
                                   4^-ndim; pic_get_fields returns the unfiltered J; 0 = off */
+    int32_t ctas_per_sm;       /* 2D particle kernel: CTAs per SM its registers are budgeted
+                                  for (2 or 3); 0 = default (2); ignored in 3D */
 } pic_config;
 
 typedef struct pic_species {

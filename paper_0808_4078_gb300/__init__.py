@@ -39,7 +39,7 @@ class Config(ctypes.Structure):
                 ("diag_interval", ctypes.c_int32), ("diag_capacity", ctypes.c_int32),
                 ("track_ids", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
-                ("j_filter", ctypes.c_int32)]
+                ("j_filter", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
 class Species(ctypes.Structure):
@@ -189,7 +189,7 @@ class Engine:
     def __init__(self, ndim, nx=16, ny=16, nz=1, dx=0.1, dy=None, dz=None, dt=0.05, capacity=(0, 0),
                  nspecies=2, sort_interval=8, diag_interval=1, diag_capacity=4096,
                  track_ids=False, flags=0, device="cuda", stream=None, cell_capacity=(0, 0),
-                 runs=None, j_filter=0):
+                 runs=None, j_filter=0, tile=(0, 0), ctas_per_sm=0):
         import torch
         self._torch = torch
         if not torch.cuda.is_available():
@@ -198,8 +198,8 @@ class Engine:
         ccap = (ctypes.c_int32 * PIC_MAX_SPECIES)(*[int(c) for c in cell_capacity][:PIC_MAX_SPECIES])
         self.cfg = Config(ndim, nx, ny, nz if ndim == 3 else 1, dx, dx if dy is None else dy,
                           dx if dz is None else dz, dt, nspecies, cap, ccap, sort_interval,
-                          diag_interval, diag_capacity, int(bool(track_ids)), flags, 0, 0, 0,
-                          int(j_filter))
+                          diag_interval, diag_capacity, int(bool(track_ids)), flags,
+                          int(tile[0]), int(tile[1]), 0, int(j_filter), int(ctas_per_sm))
         if runs is None:
             runs = [(nx, ny, nz if ndim == 3 else 1, tuple(capacity))]
         self.runs = [(int(a), int(b), int(c) if ndim == 3 else 1, tuple(int(x) for x in k))

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(NT) bin_kernel(Args a, int s, long long n, boo
             pos = pi < cap - cs ? cs + pi : cap;
         }
         if (pos < cap) {
-            const size_t q = (size_t)c * cap + pos;
+            const size_t q = slot_elt(S, (long long)c * cap + pos);
             for (int d = 0; d < a.ndim; ++d) S.o[d][q] = ov[d];
             for (int d = 0; d < 3; ++d) S.u[d][q] = uv[d];
             if (S.id) S.id[q] = id;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(NT) compact_kernel(Args a, int s, long long c0
         const CellRange cr = cell_range(S, cap, cs, c);
         const int b = start[k];
         for (int i = 0; i < cr.n; ++i) {
-            const size_t q = slot_of(c, cap, cs, cr.ns, i);
+            const size_t q = slot_elt(S, (long long)slot_of(c, cap, cs, cr.ns, i));
             T.cell[b + i] = (int)(c - cell_base);
             for (int d = 0; d < a.ndim; ++d) T.o[d][b + i] = S.o[d][q];
             for (int d = 0; d < 3; ++d) T.u[d][b + i] = S.u[d][q];

@@ -39,6 +39,7 @@ struct RunGeo {
 
 struct Geometry {
     int tx, ty, tz;
+    int push_variant;         // compiled variant of the 2D particle kernel (tile shape, CTAs/SM)
     long long ncell, nwork;
     int cap[PIC_NS];          // slots per cell per species
     int cap_stay[PIC_NS];     // of which the stay area
@@ -75,7 +76,12 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
     g->tx = c->tile_x > 0 ? c->tile_x : dtx;
     g->ty = c->tile_y > 0 ? c->tile_y : dty;
     g->tz = c->ndim == 3 ? (c->tile_z > 0 ? c->tile_z : dtz) : 1;
-    if (c->ndim == 2 && (g->tx != 16 || g->ty != 16)) { *err = "2D tiles are 16 x 16"; return PIC_EINVAL; }
+    g->push_variant = 0;
+    if (c->ndim == 2) {
+        if (c->ctas_per_sm != 0 && c->ctas_per_sm != 2 && c->ctas_per_sm != 3) { *err = "ctas_per_sm must be 0, 2 or 3"; return PIC_EINVAL; }
+        g->push_variant = pic::push2d_variant(g->tx, g->ty, c->ctas_per_sm);
+        if (g->push_variant < 0) { *err = "2D tiles are 16 x 16, 32 x 8 or 8 x 32"; return PIC_EINVAL; }
+    }
     if (c->ndim == 3 && (g->tx != 8 || g->ty != 8 || g->tz != 4)) { *err = "3D tiles are 8 x 8 x 4"; return PIC_EINVAL; }
     if (!(c->dx > 0 && c->dy > 0 && c->dt > 0) || (c->ndim == 3 && !(c->dz > 0))) { *err = "dx, dy, dz, dt must be > 0"; return PIC_EINVAL; }
     const double inv2 = 1.0 / (c->dx * c->dx) + 1.0 / (c->dy * c->dy) + (c->ndim == 3 ? 1.0 / (c->dz * c->dz) : 0.0);
@@ -144,6 +150,9 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
     return PIC_OK;
 }
 
+// Arrays per particle slot: offsets, momenta and the optional id.
+int slot_arrays(const pic_config* c) { return c->ndim + 3 + (c->track_ids ? 1 : 0); }
+
 Layout make_layout(const pic_config* c, const Geometry& g) {
     Layout L{};
     size_t off = 0;
@@ -156,12 +165,15 @@ Layout make_layout(const pic_config* c, const Geometry& g) {
     L.kin = take(off, sizeof(long long) * nruns * PIC_NS * 4);
     for (int s = 0; s < c->nspecies; ++s)
         for (int b = 0; b < 2; ++b) {
-            const long long ns = nc * g.cap[s];
-            off = (off + 255) & ~size_t(255);
-            L.slot_region[s][b] = off;
-            for (int d = 0; d < 3; ++d) L.so[s][b][d] = d < c->ndim ? take(off, 4 * ns) : 0;
-            for (int d = 0; d < 3; ++d) L.su[s][b][d] = take(off, 4 * ns);
-            L.sid[s][b] = c->track_ids ? take(off, 4 * ns) : 0;
+            // slot arrays in blocks of PIC_BLK slots (see Slots): array d of block k at
+            // region + (k * na + d) * PIC_BLK floats
+            const long long nblk = (nc * g.cap[s] + PIC_BLK - 1) / PIC_BLK;
+            const int na = slot_arrays(c);
+            const size_t r0 = take(off, (size_t)4 * nblk * na * PIC_BLK);
+            L.slot_region[s][b] = r0;
+            for (int d = 0; d < 3; ++d) L.so[s][b][d] = d < c->ndim ? r0 + (size_t)4 * PIC_BLK * d : 0;
+            for (int d = 0; d < 3; ++d) L.su[s][b][d] = r0 + (size_t)4 * PIC_BLK * (c->ndim + d);
+            L.sid[s][b] = c->track_ids ? r0 + (size_t)4 * PIC_BLK * (c->ndim + 3) : 0;
             L.scount[s][b] = take(off, 4 * nc);
             L.sicount[s][b] = take(off, 4 * nc);
             const long long sp = g.spill_cap[s];
@@ -472,6 +484,8 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
     a.work_off = at<int>(ctx, L.work_off);
     a.kin = at<long long>(ctx, L.kin);
     a.nwork = (int)g.nwork;
+    a.tx = g.tx; a.ty = g.ty; a.tz = g.tz;
+    a.push_variant = g.push_variant;
     a.nspecies = c.nspecies;
     a.nruns = nruns;
     a.ndim = c.ndim;
@@ -489,6 +503,7 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
                 S.su[d] = at<float>(ctx, L.sp_u[s][b][d]);
             }
             S.id = L.sid[s][b] ? at<int>(ctx, L.sid[s][b]) : nullptr;
+            S.bstride = (long long)slot_arrays(&c) * PIC_BLK;
             S.count = at<int>(ctx, L.scount[s][b]);
             S.icount = at<int>(ctx, L.sicount[s][b]);
             S.scell = at<int>(ctx, L.sp_cell[s][b]);
@@ -1094,7 +1109,7 @@ struct CkptHeader {
     char magic[8];
     uint32_t version, header_bytes, rungeo_bytes, runstate_bytes, species_bytes, ctl_bytes;
     int32_t ndim, nspecies, nruns, track_ids, keep_j, j_filter;
-    int32_t diag_interval, diag_capacity, sort_interval, reserved;
+    int32_t diag_interval, diag_capacity, sort_interval, tiles;   // tiles: tx | ty << 8 | tz << 16
     int32_t cap[PIC_NS], cap_stay[PIC_NS], spill_cap[PIC_NS];
     double dx, dy, dz, dt;
     uint64_t layout_total;
@@ -1139,6 +1154,7 @@ CkptHeader ckpt_header(const pic_ctx* ctx) {
     h.diag_interval = c.diag_interval;
     h.diag_capacity = c.diag_interval > 0 ? c.diag_capacity : 0;
     h.sort_interval = ctx->sort_interval;
+    h.tiles = ctx->geo.tx | (ctx->geo.ty << 8) | (ctx->geo.tz << 16);
     for (int s = 0; s < PIC_NS; ++s) {
         h.cap[s] = ctx->geo.cap[s];
         h.cap_stay[s] = ctx->geo.cap_stay[s];

@@ -91,16 +91,15 @@ __device__ __forceinline__ void b_cell(const RunDev& R, long long c, long long d
     Bz[c] = bz - (hx * (ey_xp - ey) - hy * (ex_yp - ex));
 }
 
-// Tile-batched 2D Yee over the (run, tile) work list: one CTA per 16 x 16 tile, a thread per
-// cell, every run of a batch in one launch.
-constexpr int YTX = 16, YTY = 16;
+// Tile-batched 2D Yee over the (run, tile) work list: one CTA per tile of a.tx x a.ty = 256
+// cells (the particle kernel's tile shape), a thread per cell, every run of a batch in one launch.
 
 __global__ void __launch_bounds__(NT) yee_b_half_2d_tiles(Args a) {
     const int2 wk = a.work[blockIdx.x];
     const RunDev& R = a.runs[wk.x];
     const int nx = R.nx, ny = R.ny;
-    const int i = (wk.y % R.ntx) * YTX + threadIdx.x % YTX;
-    const int j = (wk.y / R.ntx) * YTY + threadIdx.x / YTX;
+    const int i = (wk.y % R.ntx) * a.tx + threadIdx.x % a.tx;
+    const int j = (wk.y / R.ntx) * a.ty + threadIdx.x / a.tx;
     const long long dxp = i + 1 == nx ? -(long long)(nx - 1) : 1;
     const long long dyp = j + 1 == ny ? -(long long)(ny - 1) * nx : nx;
     b_cell(R, (long long)j * nx + i, dxp, dyp, 0);
@@ -110,8 +109,8 @@ __global__ void __launch_bounds__(NT) yee_e_2d_tiles(Args a, float dt) {
     const int2 wk = a.work[blockIdx.x];
     const RunDev& R = a.runs[wk.x];
     const int nx = R.nx, ny = R.ny;
-    const int i = (wk.y % R.ntx) * YTX + threadIdx.x % YTX;
-    const int j = (wk.y / R.ntx) * YTY + threadIdx.x / YTX;
+    const int i = (wk.y % R.ntx) * a.tx + threadIdx.x % a.tx;
+    const int j = (wk.y / R.ntx) * a.ty + threadIdx.x / a.tx;
     const long long dxm = i == 0 ? -(long long)(nx - 1) : 1;
     const long long dym = j == 0 ? -(long long)(ny - 1) * nx : nx;
     e_cell(R, (long long)j * nx + i, dxm, dym, 0, dt);
@@ -130,8 +129,8 @@ __global__ void __launch_bounds__(NT) jfilter_2d_tiles(Args a) {
     const int2 wk = a.work[blockIdx.x];
     const RunDev& R = a.runs[wk.x];
     const int nx = R.nx, ny = R.ny;
-    const int i = (wk.y % R.ntx) * YTX + threadIdx.x % YTX;
-    const int j = (wk.y / R.ntx) * YTY + threadIdx.x / YTX;
+    const int i = (wk.y % R.ntx) * a.tx + threadIdx.x % a.tx;
+    const int j = (wk.y / R.ntx) * a.ty + threadIdx.x / a.tx;
     const long long c = (long long)j * nx + i;
     const long long dxm = i == 0 ? -(long long)(nx - 1) : 1;
     const long long dxp = i + 1 == nx ? -(long long)(nx - 1) : 1;
@@ -227,7 +226,7 @@ __global__ void moments_init_kernel(Args a, int s, int run, long long c0, long l
         const CellRange cr = cell_range(S, cap, cs, c);
         long long m[3] = {0, 0, 0};
         for (int i = 0; i < cr.n; ++i)
-            for (int d = 0; d < 3; ++d) m[d] += __float2ll_rn(S.u[d][slot_of(c, cap, cs, cr.ns, i)] * ms);
+            for (int d = 0; d < 3; ++d) m[d] += __float2ll_rn(S.u[d][slot_elt(S, (long long)slot_of(c, cap, cs, cr.ns, i))] * ms);
         const long long lc = c - R.cell_off;
         for (int d = 0; d < 3; ++d) atomicAdd((unsigned long long*)&R.msum[d][lc], (unsigned long long)m[d]);
         atomicAdd(&R.mcnt[lc], cr.n);

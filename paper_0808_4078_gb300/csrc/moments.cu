@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(NT, PASS == 1 ? 3 : 2) mom_particles(const Mom
             const CellRange cr = cell_range(S, a.cap[s], a.cap_stay[s], g);
             const float w = R.sp[s].w;
             for (int k = 0; k < cr.n; ++k) {
-                const size_t q = slot_of(g, a.cap[s], a.cap_stay[s], cr.ns, k);
+                const size_t q = slot_elt(S, (long long)slot_of(g, a.cap[s], a.cap_stay[s], cr.ns, k));
                 add_particle<PASS>(m, R, s, w, mean, cx, cy, cz, S.o[0][q], S.o[1][q],
                                    a.ndim == 3 ? S.o[2][q] : 0.f, S.u[0][q], S.u[1][q], S.u[2][q], acc);
             }

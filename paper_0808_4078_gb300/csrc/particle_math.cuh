@@ -44,6 +44,18 @@ __device__ __forceinline__ void add_split(unsigned* lo, int* hi, long long v) {
         if (h != 0) atomicAdd(hi, h);
     }
 }
+// Shared-memory add of v unless it is 0, as a predicated reduction (no branch, so lanes with
+// different values do not diverge).
+__device__ __forceinline__ void red_nz(void* p, int v) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %1, 0;\n\t@q red.shared.add.s32 [%0], %1;\n\t}\n"
+                 ::"r"(a), "r"(v) : "memory");
+}
+// add_split without branches: value = hi * 4096 + lo.
+__device__ __forceinline__ void add_split_pred(unsigned* lo, int* hi, long long v) {
+    red_nz(lo, (int)(v & 4095));
+    red_nz(hi, (int)(v >> 12));
+}
 
 // ------------------------------------------------------------------ Boris
 // Relativistic Boris rotation u^{n-1/2} -> u^{n+1/2}; h = q dt / (2 m).  Explicit roundings
@@ -75,25 +87,23 @@ struct Win {
     int off;         // b - old cell (-1 or 0)
 };
 
+// (Selects rather than branches: lanes of one warp with different carries do not diverge.)
+//   c < 0:  S0 = (0, 1-o, o),  S1 = (1-no, no, 0),  C = (1-no, o)
+//   c = 0:  S0 = (1-o, o, 0),  S1 = (1-no, no, 0),  C = (o-no, 0)
+//   c > 0:  S0 = (1-o, o, 0),  S1 = (0, 1-no, no),  C = (o-1, -no)
 __device__ __forceinline__ Win window(float o, int c, float no) {
     Win w;
     const float mo = __fsub_rn(1.f, o), mno = __fsub_rn(1.f, no);
-    if (c < 0) {
-        w.S0[0] = 0.f; w.S0[1] = mo; w.S0[2] = o;
-        w.S1[0] = mno; w.S1[1] = no; w.S1[2] = 0.f;
-        w.C[0] = mno; w.C[1] = o;
-        w.off = -1;
-    } else if (c == 0) {
-        w.S0[0] = mo; w.S0[1] = o; w.S0[2] = 0.f;
-        w.S1[0] = mno; w.S1[1] = no; w.S1[2] = 0.f;
-        w.C[0] = __fsub_rn(o, no); w.C[1] = 0.f;
-        w.off = 0;
-    } else {
-        w.S0[0] = mo; w.S0[1] = o; w.S0[2] = 0.f;
-        w.S1[0] = 0.f; w.S1[1] = mno; w.S1[2] = no;
-        w.C[0] = __fsub_rn(o, 1.f); w.C[1] = -no;
-        w.off = 0;
-    }
+    const bool neg = c < 0, pos = c > 0;
+    w.S0[0] = neg ? 0.f : mo;
+    w.S0[1] = neg ? mo : o;
+    w.S0[2] = neg ? o : 0.f;
+    w.S1[0] = pos ? 0.f : mno;
+    w.S1[1] = pos ? mno : no;
+    w.S1[2] = pos ? no : 0.f;
+    w.C[0] = neg ? mno : (pos ? __fsub_rn(o, 1.f) : __fsub_rn(o, no));
+    w.C[1] = neg ? o : (pos ? -no : 0.f);
+    w.off = neg ? -1 : 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) w.A[k] = __fmul_rn(0.5f, __fadd_rn(w.S0[k], w.S1[k]));
     return w;
@@ -112,17 +122,13 @@ __device__ __forceinline__ float zw(float s0x, float s1x, float p, float q) {
 }
 
 // Carry a new offset r (relative to the old cell, in (-1, 2)) into [0,1) and the cell step.
+// A negative r whose r + 1 rounds to 1 stays in the cell at offset 0.  Written with selects so
+// that divergent lanes take no branches.
 __device__ __forceinline__ void carry(float r, float& no, int& c) {
-    c = 0;
-    no = r;
-    if (r < 0.f) {
-        no = __fadd_rn(r, 1.f);
-        c = -1;
-        if (no >= 1.f) { no = 0.f; c = 0; }
-    } else if (r >= 1.f) {
-        no = __fsub_rn(r, 1.f);
-        c = 1;
-    }
+    const float up = __fadd_rn(r, 1.f), down = __fsub_rn(r, 1.f);
+    const bool neg = r < 0.f, tie = up >= 1.f, big = r >= 1.f;
+    no = neg ? (tie ? 0.f : up) : (big ? down : r);
+    c = neg ? (tie ? 0 : -1) : (big ? 1 : 0);
 }
 
 // Kinetic energy per species and total momentum at time n, int64 fixed point 2^32:

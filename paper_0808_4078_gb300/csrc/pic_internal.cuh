@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #define PIC_NS 2                 // species slots
+#define PIC_BLK 32               // slots per block of the particle arrays
 #define PIC_MOM_SHIFT 20         // fixed-point shift of the drag moments
 #define PIC_KIN_SHIFT 32         // fixed-point shift of the kinetic/momentum diagnostics
 
@@ -59,14 +60,20 @@ struct RunDev {
 };
 
 
-// One species in one buffer.  A cell's cap slots are a stay area [0, cap_stay), filled in order
-// by the warp that owns the cell (count = its fill), and an immigrant area [cap_stay, cap) that
-// particles arriving from other cells claim with an atomic counter (icount).  Counters may exceed
-// their area; readers clamp them (the excess went to the spill list).
+// One species in one buffer.  A cell's cap slots are a stay area [0, cap_stay), filled by the CTA
+// that owns the cell's tile (count = its fill: the cell's stayers and, in 2D, the particles that
+// reach it from other cells of the same tile), and an immigrant area [cap_stay, cap) that the
+// other particles arriving in the cell claim with an atomic counter (icount).  Counters may
+// exceed their area; readers clamp them (the excess went to the spill list).
+// Slot arrays are stored in blocks of PIC_BLK consecutive slots: a block holds PIC_BLK values of
+// each array in turn (o_x, o_y[, o_z], u_x, u_y, u_z[, id]), so that one address per particle
+// reaches all its values and a warp reading 32 consecutive slots reads whole 128-byte lines.  Slot
+// q of array X is X[slot_elt(S, q)]; o[d], u[d] and id point at their array in block 0.
 struct Slots {
-    float* o[3];     // [ncell * cap] offsets (x, y[, z])
-    float* u[3];     // [ncell * cap] momenta
-    int* id;         // [ncell * cap] or null
+    float* o[3];     // offsets (x, y[, z])
+    float* u[3];     // momenta
+    int* id;         // or null
+    long long bstride;   // floats per block (PIC_BLK x arrays)
     int* count;      // [ncell] stay-area fill
     int* icount;     // [ncell] immigrant-area fill
     // spill list (particles whose cell was full)
@@ -103,6 +110,8 @@ struct Args {
     const int* work_off;         // [nruns + 1] first work item of each run
     long long* kin;              // [nruns][PIC_NS][4] kinetic energy + momentum (diag steps)
     int nwork;
+    int tx, ty, tz;              // tile shape of the tiled kernels (cells per axis)
+    int push_variant;            // which compiled variant of the particle kernel runs (0 = default)
     int anydrag;                 // some run has a Krook-drag species (host copy of the run table)
     int nspecies;
     int nruns;
@@ -158,6 +167,10 @@ __device__ __forceinline__ CellRange cell_range(const Slots& S, int cap, int cap
 __device__ __forceinline__ size_t slot_of(long long c, int cap, int cap_stay, int ns, int k) {
     return (size_t)c * cap + (k < ns ? k : cap_stay + (k - ns));
 }
+// Element of slot q in the slot arrays (see Slots).
+__host__ __device__ __forceinline__ size_t slot_elt(const Slots& S, long long q) {
+    return (size_t)(q / PIC_BLK) * (size_t)S.bstride + (size_t)(q % PIC_BLK);
+}
 
 __device__ __forceinline__ int wrapi(int i, int n) {
     i %= n;
@@ -182,6 +195,11 @@ cudaError_t preload_push3d();
 cudaError_t preload_bins();
 cudaError_t preload_fields();
 cudaError_t launch_push2d(const Args& a, cudaStream_t s);
+// Compiled variants of the 2D particle kernel: index for a tile shape and CTAs per SM (minb 0:
+// the default, 2), or -1; count; shape of variant v.
+int push2d_variant(int tx, int ty, int minb);
+int push2d_num_variants();
+void push2d_variant_info(int v, int* tx, int* ty, int* minb);
 cudaError_t launch_push3d(const Args& a, cudaStream_t s);
 bool has_push3d();
 cudaError_t launch_spill2d(const Args& a, cudaStream_t s);

@@ -3,123 +3,162 @@
 // with cell carry, charge-conserving Esirkepov current deposition (CIC) accumulated in int64
 // fixed point, and rebinning of every particle into its new cell's slots of the other buffer.
 //
-// One CTA per (run, tile) of 16 x 16 cells, 8 warps, a warp per cell, 3 CTAs per SM (80
-// registers: the fields are read from the shared tile, not cached in registers, which buys the
-// third CTA).  Particles that stay in the cell this step (the large majority) add their 8
-// current terms and 4 drag moments to int32 registers (one warp transpose-reduce per cell puts
-// them in the shared tile) and are written to the cell's new stay slots at warp-local offsets
-// (no atomics).  Particles that cross
-// a cell edge go to a per-warp queue and are processed 32 at a time: per-lane atomics over their
-// 3 x 3 node window, and an atomic slot claim in the destination cell.  All paths evaluate the
-// same explicitly-rounded formulas and every current term is an integer before it is summed, so
+// One CTA per (run, tile) of TX x TY = 256 cells (16 x 16, 32 x 8 or 8 x 32), 8 warps, 2 or 3
+// CTAs per SM (the autotuner picks the variant); a warp walks its cells one at a time, each cell's species in order, 32
+// particles per chunk, with the next chunk's particles loaded into registers while the current
+// one is pushed.
+//
+// Gather: on entering a cell the warp writes a 14-entry table to shared memory: for each of the
+// 13 (component, quadrant) combinations of the staggered CIC stencils, the bilinear form
+// f = c0 + c1 t + c2 s + c3 t s of the component over the 2 x 2 points that bracket the quadrant
+// (t, s the particle's coordinates relative to the patch), and the cell's drag mean.  A particle
+// then reads 6 float4 (broadcast: the whole warp is in one cell) and evaluates each component
+// with 3 FMAs instead of weighting 37 shared values.  Every path (this one, the queued crossers,
+// the spill list) builds the same patches with the same roundings, so results do not depend on
+// which path a particle took.
+//
+// Particles that stay in their cell (the large majority) add their 8 current terms and 4 drag
+// moments to int32 registers (one warp transpose-reduce per cell puts them in the shared tile)
+// and claim slots of the cell's stay area in the other buffer with one shared-memory atomic per
+// chunk.  Particles that cross a cell edge are queued per warp with their pushed state and
+// deposited 32 at a time with per-lane shared atomics over their 3 x 3 node window; a crosser
+// that stays inside the tile claims a slot in its new cell's stay area through the same shared
+// counter, and only particles leaving the tile (or finding the stay area full) take the
+// destination cell's immigrant area through a global atomic.  The CTA writes its cells' stay
+// counts when all its warps are done.  Every current term is an integer before it is summed, so
 // results do not depend on particle order.
 //
 // Shared accumulators are pairs of 32-bit words (value = hi * 4096 + lo) so that all shared
 // atomics are native 32-bit adds; 64-bit shared atomics are several times slower on this GPU.
 // The tile is added to global int64 J with atomics at the end (halos overlap neighbours).
+#include <mutex>
+
 #include "pic_internal.cuh"
 #include "particle_math.cuh"
 
 namespace pic {
 namespace {
 
-constexpr int TX = 16, TY = 16;
-constexpr int RX = TX + 3, RY = TY + 3, RN = RX * RY;   // tile + CIC/Esirkepov stencil halo
-constexpr int NT = 256, NW = NT / 32, QCAP = 64;
-constexpr int CELLS = TX * TY;
+constexpr int NT = 256, NW = NT / 32;
+constexpr int QCAP = 32;                 // queued crossers per warp (a drain empties the queue)
 constexpr int FLUSH_CHUNKS = 8;          // register sums stay below 2^31 (8 x 32 particles)
-constexpr int STAGES = 4;                // per-warp cp.async pipeline depth (chunks in flight)
+constexpr int NTAB = 14;                 // 13 field patches + the drag mean of the warp's cell
 constexpr unsigned FULL = 0xffffffffu;
+static_assert(PIC_BLK == 32, "a chunk of 32 slots is one block of the slot arrays");
 
+template <int TX, int TY>
+struct Geo {
+    static constexpr int RX = TX + 3, RY = TY + 3, RN = RX * RY, CELLS = TX * TY;
+    static_assert(CELLS == 256, "a tile holds 256 cells (32 per warp)");
+};
+
+template <int TX, int TY>
 struct Smem {
+    static constexpr int RN = Geo<TX, TY>::RN, CELLS = Geo<TX, TY>::CELLS;
+    float4 T[NW][NTAB];              // per-warp table of the cell being pushed
+    float4 qa[NW][QCAP];             // queued crossers: ox oy nox noy
+    float4 qb[NW][QCAP];             //   ux uy uz vz
+    int2 qc[NW][QCAP];               //   meta (species, cell, carries, bad), id
+    double red[NW][6];
+    unsigned long long kin[5];
+    long long kl[5][NT];             // per-thread kinetic/momentum sums of a diagnostic step
+    float* src[PIC_NS];              // block 0 of the slot arrays of the current buffer
+    float* dst[PIC_NS];              // and of the other buffer
     float F[6][RN];                  // Ex Ey Ez Bx By Bz of the region (origin: tile - 1 cell)
-    float ub[3][RN];                 // previous cell-mean momentum (drag)
     unsigned Jlo[3][RN];             // current accumulator, value = Jhi * 4096 + Jlo
     int Jhi[3][RN];
     unsigned Mlo[3][RN];             // drag moments (fixed point 2^20), same split
     int Mhi[3][RN];
     int MC[RN];                      // drag counts
-    unsigned q[NW][QCAP];            // per-warp queue: species << 24 | tile cell << 16 | slot
-    float stg[NW][STAGES][6][32];    // per-warp staged chunks: o0 o1 u0 u1 u2 id (by lane)
-    int cnt[PIC_NS][CELLS];          // particles of the tile's cells (current buffer)
-    int cns[PIC_NS][CELLS];          // of which in the stay area
-    double red[NW][6];
-    unsigned long long kin[5];
+    float ub[3][CELLS];              // previous cell-mean momentum of the tile's cells (drag)
+    float df[PIC_NS][CELLS];         // drag factor 1 - exp(-nu dt) per species and cell
+    int ns[PIC_NS][CELLS];           // stay part of the tile's cells (current buffer)
+    int nn[PIC_NS][CELLS];           // all particles of the tile's cells (current buffer)
+    int oc[PIC_NS][CELLS];           // stay-area claims in the other buffer
+    int toff[16];                    // region offset of each table patch's first point
     SpeciesParams sp[PIC_NS];
+    Slots dslot[PIC_NS];             // slot descriptors of the other buffer
+    int cap[PIC_NS], cst[PIC_NS], spc[PIC_NS];   // slots per cell, stay area, spill capacity
 };
 
-// ------------------------------------------------------------------ async staging
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// Position in a warp's work list: its cells ci = warp, warp + NW, ...; per cell the species in
-// order; per species chunks of 32 slots.
-struct Cursor {
-    int ci, s, j;
-};
-__device__ __forceinline__ void advance(Cursor& c, const int (*cnt)[CELLS], int nsp) {
-    c.j += 32;
-    while (c.ci < CELLS) {
-        if (c.j < cnt[c.s][c.ci]) return;
-        c.j = 0;
-        if (++c.s >= nsp) { c.s = 0; c.ci += NW; }
-    }
-}
-
-// Slot of element k of cell g (32-bit: the library keeps cells x cap below 2^31).
-__device__ __forceinline__ int slot32(int g, int cap, int cap_stay, int ns, int k) {
-    return g * cap + (k < ns ? k : cap_stay + (k - ns));
-}
 
 // ------------------------------------------------------------------ gather
-// CIC weights of an axis for an offset o in [0,1): node lattice (nodes c, c+1) and the
-// half-shifted lattice (points c-1/2, c+1/2, c+3/2, stored at c-1, c, c+1).
-struct W3 {
-    float n[2];
-    float h[3];
-};
-__device__ __forceinline__ W3 weights(float o) {
-    W3 w;
-    const float d = __fsub_rn(o, 0.5f);
-    w.n[0] = __fsub_rn(1.f, o);
-    w.n[1] = o;
-    w.h[0] = fmaxf(-d, 0.f);
-    w.h[1] = __fsub_rn(1.f, fabsf(d));
-    w.h[2] = fmaxf(d, 0.f);
-    return w;
+// Bilinear patch of a component over the points (0,0), (1,0), (0,1), (1,1) of its own lattice:
+// f(t, s) = c0 + c1 t + c2 s + c3 t s (x, y, z, w = c0, c1, c2, c3).
+__device__ __forceinline__ float4 patch(float f00, float f10, float f01, float f11) {
+    const float c1 = __fsub_rn(f10, f00), c2 = __fsub_rn(f01, f00);
+    return make_float4(f00, c1, c2, __fsub_rn(__fsub_rn(f11, f10), c2));
+}
+__device__ __forceinline__ float peval(const float4 c, float t, float s) {
+    return __fmaf_rn(t, __fmaf_rn(c.w, s, c.y), __fmaf_rn(c.z, s, c.x));
 }
 
-// F(c, dx, dy): component c at offset (dx, dy) from the particle's cell node.
-template <class A>
-__device__ __forceinline__ float row_h(const A& F, const W3& wx, int c, int dy) {
-    return __fmaf_rn(wx.h[2], F(c, 1, dy), __fmaf_rn(wx.h[1], F(c, 0, dy), __fmul_rn(wx.h[0], F(c, -1, dy))));
-}
-template <class A>
-__device__ __forceinline__ float row_n(const A& F, const W3& wx, int c, int dy) {
-    return __fmaf_rn(wx.n[1], F(c, 1, dy), __fmul_rn(wx.n[0], F(c, 0, dy)));
-}
-// Staggering: Ex, By (1/2, 0); Ey, Bx (0, 1/2); Ez (0, 0); Bz (1/2, 1/2).
-template <class A>
-__device__ __forceinline__ void gather(const A& F, const W3& wx, const W3& wy, float EB[6]) {
-    EB[0] = __fmaf_rn(wy.n[1], row_h(F, wx, 0, 1), __fmul_rn(wy.n[0], row_h(F, wx, 0, 0)));
-    EB[4] = __fmaf_rn(wy.n[1], row_h(F, wx, 4, 1), __fmul_rn(wy.n[0], row_h(F, wx, 4, 0)));
-    EB[1] = __fmaf_rn(wy.h[2], row_n(F, wx, 1, 1), __fmaf_rn(wy.h[1], row_n(F, wx, 1, 0), __fmul_rn(wy.h[0], row_n(F, wx, 1, -1))));
-    EB[3] = __fmaf_rn(wy.h[2], row_n(F, wx, 3, 1), __fmaf_rn(wy.h[1], row_n(F, wx, 3, 0), __fmul_rn(wy.h[0], row_n(F, wx, 3, -1))));
-    EB[2] = __fmaf_rn(wy.n[1], row_n(F, wx, 2, 1), __fmul_rn(wy.n[0], row_n(F, wx, 2, 0)));
-    EB[5] = __fmaf_rn(wy.h[2], row_h(F, wx, 5, 1), __fmaf_rn(wy.h[1], row_h(F, wx, 5, 0), __fmul_rn(wy.h[0], row_h(F, wx, 5, -1))));
-}
-
-struct SharedFields {
-    const Smem* s;
-    int n0;   // region index of the particle's cell node
-    __device__ __forceinline__ float operator()(int c, int dx, int dy) const {
-        return s->F[c][n0 + dy * RX + dx];
+// Table entry e (0..12): component and the origin of its patch relative to the cell's node.
+// Staggering: Ex, By at (1/2, 0); Ey, Bx at (0, 1/2); Ez at (0, 0); Bz at (1/2, 1/2).  A half-
+// shifted axis has two patches, for offsets below and above 1/2 (origin -1 and 0 on that
+// lattice, coordinate o + 1/2 and o - 1/2); a node axis one (origin 0, coordinate o).
+//   0, 1 Ex (x half)    2, 3 By (x half)    4, 5 Ey (y half)    6, 7 Bx (y half)    8 Ez
+//   9..12 Bz: 9 + [ox >= 1/2] + 2 [oy >= 1/2]
+__device__ __forceinline__ void patch_origin(int e, int& c, int& dx, int& dy) {
+    if (e < 4) {
+        c = e < 2 ? 0 : 4; dx = (e & 1) - 1; dy = 0;
+    } else if (e < 8) {
+        c = e < 6 ? 1 : 3; dx = 0; dy = (e & 1) - 1;
+    } else if (e == 8) {
+        c = 2; dx = 0; dy = 0;
+    } else {
+        c = 5; dx = ((e - 9) & 1) - 1; dy = ((e - 9) >> 1) - 1;
     }
+}
+template <class A>
+__device__ __forceinline__ float4 patch_at(const A& F, int e) {
+    int c, dx, dy;
+    patch_origin(e, c, dx, dy);
+    return patch(F(c, dx, dy), F(c, dx + 1, dy), F(c, dx, dy + 1), F(c, dx + 1, dy + 1));
+}
+
+struct Quad {
+    int qx, qy;
+    float hx, hy;    // coordinates on the half-shifted lattices
+};
+__device__ __forceinline__ Quad quad(float ox, float oy) {
+    Quad q;
+    q.qx = ox >= 0.5f;
+    q.qy = oy >= 0.5f;
+    q.hx = __fadd_rn(ox, q.qx ? -0.5f : 0.5f);
+    q.hy = __fadd_rn(oy, q.qy ? -0.5f : 0.5f);
+    return q;
+}
+// E and B at the particle from the cell's table.
+__device__ __forceinline__ void gather_tab(const float4* T, float ox, float oy, float EB[6]) {
+    const Quad q = quad(ox, oy);
+    const float4* ta = T + q.qx;
+    const float4* tb = T + q.qy;
+    EB[0] = peval(ta[0], q.hx, oy);
+    EB[4] = peval(ta[2], q.hx, oy);
+    EB[1] = peval(tb[4], ox, q.hy);
+    EB[3] = peval(tb[6], ox, q.hy);
+    EB[2] = peval(T[8], ox, oy);
+    EB[5] = peval(ta[9 + 2 * q.qy], q.hx, q.hy);
+}
+// The same from a field accessor F(c, dx, dy) (component c at node offset (dx, dy)).
+template <class A>
+__device__ __forceinline__ void gather_fetch(const A& F, float ox, float oy, float EB[6]) {
+    const Quad q = quad(ox, oy);
+    EB[0] = peval(patch_at(F, q.qx), q.hx, oy);
+    EB[4] = peval(patch_at(F, 2 + q.qx), q.hx, oy);
+    EB[1] = peval(patch_at(F, 4 + q.qy), ox, q.hy);
+    EB[3] = peval(patch_at(F, 6 + q.qy), ox, q.hy);
+    EB[2] = peval(patch_at(F, 8), ox, oy);
+    EB[5] = peval(patch_at(F, 9 + q.qx + 2 * q.qy), q.hx, q.hy);
+}
+
+template <int RX>
+struct SharedFields {
+    const float* F;   // region fields, component stride rn
+    int rn;
+    int n0;           // region index of the cell's node
+    __device__ __forceinline__ float operator()(int c, int dx, int dy) const { return F[c * rn + n0 + dy * RX + dx]; }
 };
 struct GlobalFields {
     const RunDev* R;
@@ -131,38 +170,7 @@ struct GlobalFields {
     }
 };
 
-// Warp sum of 16 int values; lane l returns the total of value index l >> 1.
-__device__ __forceinline__ int transpose_reduce16(int v[16], int lane) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const bool hi = lane & 16;
-        const int send = hi ? v[i] : v[i + 8];
-        const int keep = hi ? v[i + 8] : v[i];
-        v[i] = keep + __shfl_xor_sync(FULL, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const bool hi = lane & 8;
-        const int send = hi ? v[i] : v[i + 4];
-        const int keep = hi ? v[i + 4] : v[i];
-        v[i] = keep + __shfl_xor_sync(FULL, send, 8);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const bool hi = lane & 4;
-        const int send = hi ? v[i] : v[i + 2];
-        const int keep = hi ? v[i + 2] : v[i];
-        v[i] = keep + __shfl_xor_sync(FULL, send, 4);
-    }
-    {
-        const bool hi = lane & 2;
-        const int send = hi ? v[0] : v[1];
-        const int keep = hi ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(FULL, send, 2);
-    }
-    return v[0] + __shfl_xor_sync(FULL, v[0], 1);
-}
-
+// Boris push, drag, collisions and move of one particle (shared by all paths).
 struct Pushed {
     float ux, uy, uz;     // u^{n+1/2}
     float nox, noy;       // new offsets
@@ -170,16 +178,11 @@ struct Pushed {
     float vz;
     bool bad;
 };
-
-template <class A>
-__device__ __forceinline__ Pushed push_one(const A& F, const SpeciesParams& P, const RunConst& K,
-                                           float ox, float oy, float ux, float uy, float uz,
-                                           float b0, float b1, float b2, float df,
-                                           int s, unsigned id, long long step) {
+__device__ __forceinline__ Pushed push_rest(const float EB[6], const SpeciesParams& P, const RunConst& K,
+                                            float ox, float oy, float ux, float uy, float uz,
+                                            float b0, float b1, float b2, float df,
+                                            int s, unsigned id, long long step) {
     Pushed r;
-    const W3 wx = weights(ox), wy = weights(oy);
-    float EB[6];
-    gather(F, wx, wy, EB);
     boris(P.qmdt2, EB, ux, uy, uz);
     if (P.drag) {
         ux = __fmaf_rn(-df, b0, ux);
@@ -223,14 +226,25 @@ __device__ __forceinline__ void deposit_terms(const Add& add, const SpeciesParam
 }
 
 // ------------------------------------------------------------------ rebinning
+// Slot q of the 2D slot arrays starting at block 0 = base: o_x, o_y, u_x, u_y, u_z[, id] are
+// PIC_BLK floats apart within a block.
+__device__ __forceinline__ void store2(float* base, long long bstride, bool ids, int q, float ox, float oy,
+                                       float ux, float uy, float uz, int id) {
+    float* p = base + (size_t)(q / PIC_BLK) * bstride + (q % PIC_BLK);
+    p[0] = ox;
+    p[PIC_BLK] = oy;
+    p[2 * PIC_BLK] = ux;
+    p[3 * PIC_BLK] = uy;
+    p[4 * PIC_BLK] = uz;
+    if (ids) reinterpret_cast<int*>(p)[5 * PIC_BLK] = id;
+}
 __device__ __forceinline__ void store_slot(const Slots& D, int q, float ox, float oy, float ux,
                                            float uy, float uz, int id) {
-    D.o[0][q] = ox; D.o[1][q] = oy;
-    D.u[0][q] = ux; D.u[1][q] = uy; D.u[2][q] = uz;
-    if (D.id) D.id[q] = id;
+    store2(D.o[0], D.bstride, D.id != nullptr, q, ox, oy, ux, uy, uz, id);
 }
 
-// Particle arriving in cell g of buffer D from elsewhere: claim an immigrant slot, else spill.
+// Particle arriving in cell g of buffer D from another tile (or finding the stay area full):
+// claim an immigrant slot, else spill.
 __device__ __forceinline__ void put_imm(const Slots& D, int cap, int cap_stay, int spill_cap, int g,
                                         float ox, float oy, float ux, float uy, float uz, int id, int* err) {
     const int pi = atomicAdd(&D.icount[g], 1);
@@ -250,99 +264,176 @@ __device__ __forceinline__ void put_imm(const Slots& D, int cap, int cap_stay, i
 }
 
 // ------------------------------------------------------------------ crossing particles
-// Full step of up to 32 queued particles (one per lane) of the tile: shared-memory gather and
-// deposit, then rebinning into the destination cell of the other buffer.
-__device__ __forceinline__ void drain(Smem& sm, const Args& a, const RunConst& K, int par, int k,
-                                      int lane, int warp, int x0, int y0, bool diag, long long step,
-                                      long long kacc[5]) {
-    if (lane >= k) return;
-    const int nx = K.nx, ny = K.ny;
-    const unsigned e = sm.q[warp][lane];
-    const int s = e >> 24, ci = (e >> 16) & 255, i = e & 65535;
-    const SpeciesParams& P = sm.sp[s];
-    const int lx = ci % TX, ly = ci / TX;
-    const int cx = x0 + lx, cy = y0 + ly;
-    const int g = K.cell_off + cy * nx + cx;
-    const int cap = a.cap[s], cst = a.cap_stay[s];
-    const Slots S = a.slot[s][par], D = a.slot[s][par ^ 1];
-    const int p = slot32(g, cap, cst, sm.cns[s][ci], i);
-    const float ox = S.o[0][p], oy = S.o[1][p];
-    const float u0x = S.u[0][p], u0y = S.u[1][p], u0z = S.u[2][p];
-    const int id = S.id ? S.id[p] : 0;
-    const int ix = lx + 1, iy = ly + 1;
-    const int n0 = iy * RX + ix;
-    float b0 = 0.f, b1 = 0.f, b2 = 0.f;
-    if (P.drag) { b0 = sm.ub[0][n0]; b1 = sm.ub[1][n0]; b2 = sm.ub[2][n0]; }
-    const float df = P.drag ? drag_of(K, P, s, g - K.cell_off) : 0.f;
-    const Pushed r = push_one(SharedFields{&sm, n0}, P, K, ox, oy, u0x, u0y, u0z, b0, b1, b2, df, s, id, step);
-    if (r.bad) {
-        // keep the particle where it was, unmoved; the sticky flag fails the run
-        atomicOr(&a.ctl->err, ERR_BADPART);
-        put_imm(D, cap, cst, a.spill_cap[s], g, ox, oy, u0x, u0y, u0z, id, &a.ctl->err);
-        return;
-    }
-    if (diag) kin_add(kacc, s, P.w, u0x, u0y, u0z, r.ux, r.uy, r.uz);
-    const Win wx = window(ox, r.sx, r.nox), wy = window(oy, r.sy, r.noy);
-    const float zf = __fmul_rn(P.jz, r.vz);
-    auto add = [&](int c, int ii, int jj, int v) {
-        if (v != 0) add_split(&sm.Jlo[c][jj * RX + ii], &sm.Jhi[c][jj * RX + ii], v);
-    };
-    deposit_terms(add, P, ix + wx.off, iy + wy.off, wx, wy, zf);
-    if (P.drag) {
-        const int n1 = (iy + r.sy) * RX + (ix + r.sx);
-        add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], f2ll_rn(r.ux * MOM_SCALE));
-        add_split(&sm.Mlo[1][n1], &sm.Mhi[1][n1], f2ll_rn(r.uy * MOM_SCALE));
-        add_split(&sm.Mlo[2][n1], &sm.Mhi[2][n1], f2ll_rn(r.uz * MOM_SCALE));
-        atomicAdd(&sm.MC[n1], 1);
-    }
-    int ncx = cx + r.sx, ncy = cy + r.sy;
-    ncx = ncx < 0 ? ncx + nx : (ncx >= nx ? ncx - nx : ncx);
-    ncy = ncy < 0 ? ncy + ny : (ncy >= ny ? ncy - ny : ncy);
-    const int g1 = K.cell_off + ncy * nx + ncx;
-    put_imm(D, cap, cst, a.spill_cap[s], g1, r.nox, r.noy, r.ux, r.uy, r.uz, id, &a.ctl->err);
+
+// ------------------------------------------------------------------ crossing particles
+// Queue entry meta word: species (bit 0), tile cell (bits 1-10), x and y cell steps + 1 (bits
+// 11-12, 13-14), bad (bit 15).  A bad particle is queued with its old state.
+__device__ __forceinline__ int qmeta(int s, int ci, int sx, int sy, bool bad) {
+    return s | (ci << 1) | ((sx + 1) << 11) | ((sy + 1) << 13) | ((int)bad << 15);
 }
 
-// Register sums of "stay" particles of the cell at region node n0 -> shared tile.
-__device__ __forceinline__ void flush_acc(Smem& sm, int acc[12], int n0, int lane) {
-    int v[16];
+// Deposit and rebin the k queued particles of this warp (one per lane).
+template <int TX, int TY>
+__device__ __noinline__ void drain(Smem<TX, TY>& sm, const Args& a, const RunConst& K, int k, int lane,
+                                   int warp, int x0, int y0) {
+    constexpr int RX = Geo<TX, TY>::RX;
+    if (lane < k) {
+        const float4 qa = sm.qa[warp][lane], qb = sm.qb[warp][lane];
+        const int2 qc = sm.qc[warp][lane];
+        const float ox = qa.x, oy = qa.y, nox = qa.z, noy = qa.w;
+        const float ux = qb.x, uy = qb.y, uz = qb.z, vz = qb.w;
+        const int m = qc.x, id = qc.y;
+        const int s = m & 1, ci = (m >> 1) & 1023, sx = ((m >> 11) & 3) - 1, sy = ((m >> 13) & 3) - 1;
+        const SpeciesParams& P = sm.sp[s];
+        const int lx = ci % TX, ly = ci / TX;
+        const int cx = x0 + lx, cy = y0 + ly;
+        const int nx = K.nx, ny = K.ny;
+        const int g = K.cell_off + cy * nx + cx;
+        const int cap = sm.cap[s], cst = sm.cst[s], spc = sm.spc[s];
+        const Slots& D = sm.dslot[s];
+        if (m & (1 << 15)) {
+            // keep the particle where it was, unmoved; the sticky flag fails the run
+            atomicOr(&a.ctl->err, ERR_BADPART);
+            put_imm(D, cap, cst, spc, g, nox, noy, ux, uy, uz, id, &a.ctl->err);
+        } else {
+            const int ix = lx + 1, iy = ly + 1;
+            const Win wx = window(ox, sx, nox), wy = window(oy, sy, noy);
+            const float zf = __fmul_rn(P.jz, vz);
+            auto add = [&](int c, int ii, int jj, int v) {
+                add_split_pred(&sm.Jlo[c][jj * RX + ii], &sm.Jhi[c][jj * RX + ii], v);
+            };
+            deposit_terms(add, P, ix + wx.off, iy + wy.off, wx, wy, zf);
+            if (P.drag) {
+                const int n1 = (iy + sy) * RX + (ix + sx);
+                add_split_pred(&sm.Mlo[0][n1], &sm.Mhi[0][n1], f2ll_rn(ux * MOM_SCALE));
+                add_split_pred(&sm.Mlo[1][n1], &sm.Mhi[1][n1], f2ll_rn(uy * MOM_SCALE));
+                add_split_pred(&sm.Mlo[2][n1], &sm.Mhi[2][n1], f2ll_rn(uz * MOM_SCALE));
+                atomicAdd(&sm.MC[n1], 1);
+            }
+            const int dlx = lx + sx, dly = ly + sy;
+            if (dlx >= 0 && dlx < TX && dly >= 0 && dly < TY) {
+                const int g1 = g + sy * nx + sx;
+                const int pos = atomicAdd(&sm.oc[s][dly * TX + dlx], 1);
+                if (pos < cst) store_slot(D, g1 * cap + pos, nox, noy, ux, uy, uz, id);
+                else put_imm(D, cap, cst, spc, g1, nox, noy, ux, uy, uz, id, &a.ctl->err);
+            } else {
+                int ncx = cx + sx, ncy = cy + sy;
+                ncx = ncx < 0 ? ncx + nx : (ncx >= nx ? ncx - nx : ncx);
+                ncy = ncy < 0 ? ncy + ny : (ncy >= ny ? ncy - ny : ncy);
+                put_imm(D, cap, cst, spc, K.cell_off + ncy * nx + ncx, nox, noy, ux, uy, uz, id, &a.ctl->err);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Register sums of "stay" particles of the cell at region node n0 -> shared tile: warp sums
+// of the 12 accumulators (8 current terms, 4 drag moments when the cell has a drag species);
+// lane i adds sum i.  At most 8 chunks are summed between flushes, so a warp sum of terms of at
+// most 2^21 stays below 2^29.
+template <int TX, int TY>
+__device__ __forceinline__ void flush_acc(Smem<TX, TY>& sm, int acc[12], int n0, int lane, bool moments) {
+    constexpr int RX = Geo<TX, TY>::RX;
+    int tot = 0;
 #pragma unroll
-    for (int i = 0; i < 12; ++i) { v[i] = acc[i]; acc[i] = 0; }
-    v[12] = v[13] = v[14] = v[15] = 0;
-    const int tot = transpose_reduce16(v, lane);
-    const int idx = lane >> 1;
-    if ((lane & 1) || tot == 0 || idx > 11) return;
-    if (idx == 11) { atomicAdd(&sm.MC[n0], tot); return; }
-    // node offsets: Jx (0,0),(0,1); Jy (0,0),(1,0); Jz (0,0),(1,0),(0,1),(1,1); moments (0,0)
-    const int off = (idx == 1 || idx == 6) ? RX : (idx == 3 || idx == 5) ? 1 : (idx == 7) ? RX + 1 : 0;
-    unsigned* lo;
-    int* hi;
-    if (idx < 8) {
-        const int c = idx < 2 ? 0 : (idx < 4 ? 1 : 2);
-        lo = &sm.Jlo[c][n0 + off];
-        hi = &sm.Jhi[c][n0 + off];
-    } else {
-        lo = &sm.Mlo[idx - 8][n0];
-        hi = &sm.Mhi[idx - 8][n0];
+    for (int i = 0; i < 8; ++i) {
+        const int t = __reduce_add_sync(FULL, acc[i]);
+        tot = lane == i ? t : tot;
+        acc[i] = 0;
     }
-    add_split(lo, hi, tot);
+    if (moments) {
+#pragma unroll
+        for (int i = 8; i < 12; ++i) {
+            const int t = __reduce_add_sync(FULL, acc[i]);
+            tot = lane == i ? t : tot;
+            acc[i] = 0;
+        }
+    }
+    if (lane < 11) {
+        // node offsets: Jx (0,0),(0,1); Jy (0,0),(1,0); Jz (0,0),(1,0),(0,1),(1,1); moments (0,0)
+        const int off = (lane == 1 || lane == 6) ? RX : (lane == 3 || lane == 5) ? 1 : (lane == 7) ? RX + 1 : 0;
+        const int c = lane < 2 ? 0 : (lane < 4 ? 1 : 2);
+        unsigned* lo = lane < 8 ? &sm.Jlo[c][n0 + off] : &sm.Mlo[lane - 8][n0];
+        int* hi = lane < 8 ? &sm.Jhi[c][n0 + off] : &sm.Mhi[lane - 8][n0];
+        add_split_pred(lo, hi, tot);
+    } else if (lane == 11) {
+        red_nz(&sm.MC[n0], tot);
+    }
 }
 
-__global__ void __launch_bounds__(NT, 3) push2d_kernel(const Args a) {
+// A warp's work is a sequence of segments, one per (cell, species) with particles: cells
+// ci = warp, warp + NW, ...; per cell the species in order.  A segment's particles are
+// elements k = 0 .. n-1: slots q0 + k for k < ns (stay area), qi + k beyond (immigrant area).
+struct Seg {
+    int ci, s, n, ns, q0, qi;
+};
+template <int TX, int TY>
+__device__ __forceinline__ Seg seg_find(const Smem<TX, TY>& sm, int ci, int s, int nsp, int cell_off, int nx,
+                                        int x0, int y0) {
+    constexpr int CELLS = Geo<TX, TY>::CELLS;
+    while (ci < CELLS && sm.nn[s][ci] == 0) {
+        if (++s >= nsp) { s = 0; ci += NW; }
+    }
+    Seg r;
+    r.ci = ci;
+    r.s = s;
+    r.n = r.ns = r.q0 = r.qi = 0;
+    if (ci < CELLS) {
+        r.n = sm.nn[s][ci];
+        r.ns = sm.ns[s][ci];
+        const int g = cell_off + (y0 + ci / TX) * nx + (x0 + ci % TX);
+        r.q0 = g * sm.cap[s];
+        r.qi = r.q0 + sm.cst[s] - r.ns;
+    }
+    return r;
+}
+
+struct Part {
+    float ox, oy, ux, uy, uz;
+    int id;
+};
+// The lane's particle of the chunk starting at element j of segment L (zeros past its end).
+__device__ __forceinline__ Part load_part(const Seg& L, int j, int lane, const float* src, long long bstride,
+                                          bool ids) {
+    Part p;
+    p.ox = p.oy = p.ux = p.uy = p.uz = 0.f;
+    p.id = 0;
+    const int k = j + lane;
+    if (k < L.n) {
+        const int q = (k < L.ns ? L.q0 : L.qi) + k;
+        const float* b = src + (size_t)(q / PIC_BLK) * bstride + (q % PIC_BLK);
+        p.ox = __ldg(b);
+        p.oy = __ldg(b + PIC_BLK);
+        p.ux = __ldg(b + 2 * PIC_BLK);
+        p.uy = __ldg(b + 3 * PIC_BLK);
+        p.uz = __ldg(b + 4 * PIC_BLK);
+        if (ids) p.id = __ldg(reinterpret_cast<const int*>(b) + 5 * PIC_BLK);
+    }
+    return p;
+}
+
+template <int TX, int TY, int MINB>
+__global__ void __launch_bounds__(NT, MINB) push2d_kernel(const Args a) {
+    using G = Geo<TX, TY>;
+    constexpr int RX = G::RX, RN = G::RN, CELLS = G::CELLS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+    Smem<TX, TY>& sm = *reinterpret_cast<Smem<TX, TY>*>(smem_raw);
     const int2 wk = a.work[blockIdx.x];
     const RunDev* Rp = &a.runs[wk.x];
     const RunConst K = run_const(Rp);
     const int nx = K.nx, ny = K.ny;
     const int tile = wk.y;
-    const int x0 = (tile % Rp->ntx) * TX, y0 = (tile / Rp->ntx) * TY;
+    const int ntx = Rp->ntx;
+    const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
     const int gx0 = x0 - 1, gy0 = y0 - 1;
     const long long step = a.ctl->step;
     const int par = a.ctl->parity;
     const bool diag = a.diag_interval > 0 && (step % a.diag_interval) == 0;
     const bool anydrag = Rp->msum[0] != nullptr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned lt = (1u << lane) - 1u;
+    const int nsp = a.nspecies;
+    const long long bstride = a.slot[0][0].bstride;
+    const bool ids = a.slot[0][0].id != nullptr;
 
     for (int i = tid; i < RN; i += NT) {
         const int ry = i / RX, rx = i - ry * RX;
@@ -357,7 +448,6 @@ __global__ void __launch_bounds__(NT, 3) push2d_kernel(const Args a) {
         if (anydrag) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                sm.ub[c][i] = Rp->ubar[c][g];
                 sm.Mlo[c][i] = 0u;
                 sm.Mhi[c][i] = 0;
             }
@@ -365,14 +455,42 @@ __global__ void __launch_bounds__(NT, 3) push2d_kernel(const Args a) {
         }
     }
     if (tid < 5) sm.kin[tid] = 0ull;
-    if (tid < PIC_NS) sm.sp[tid] = Rp->sp[tid];
-    for (int i = tid; i < PIC_NS * CELLS; i += NT) {
-        const int s = i / CELLS, ci = i - s * CELLS;
-        const int g = K.cell_off + (y0 + ci / TX) * nx + (x0 + ci % TX);
-        CellRange cr{0, 0};
-        if (s < a.nspecies && Rp->sp[s].active) cr = cell_range(a.slot[s][par], a.cap[s], a.cap_stay[s], g);
-        sm.cnt[s][ci] = cr.n;
-        sm.cns[s][ci] = cr.ns;
+    if (diag)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) sm.kl[k][tid] = 0;
+    if (tid < PIC_NS) {
+        sm.sp[tid] = Rp->sp[tid];
+        sm.src[tid] = a.slot[tid][par].o[0];
+        sm.dst[tid] = a.slot[tid][par ^ 1].o[0];
+        sm.dslot[tid] = a.slot[tid][par ^ 1];
+        sm.cap[tid] = a.cap[tid];
+        sm.cst[tid] = a.cap_stay[tid];
+        sm.spc[tid] = a.spill_cap[tid];
+    }
+    if (tid >= 32 && tid < 32 + 13) {
+        int c, dx, dy;
+        patch_origin(tid - 32, c, dx, dy);
+        sm.toff[tid - 32] = c * RN + dy * RX + dx;
+    }
+    for (int ci = tid; ci < CELLS; ci += NT) {
+        const int lc = (y0 + ci / TX) * nx + (x0 + ci % TX);
+        const int g = K.cell_off + lc;
+#pragma unroll
+        for (int s = 0; s < PIC_NS; ++s) {
+            CellRange cr{0, 0};
+            if (s < nsp && Rp->sp[s].active) cr = cell_range(a.slot[s][par], a.cap[s], a.cap_stay[s], g);
+            sm.nn[s][ci] = cr.n;
+            sm.ns[s][ci] = cr.ns;
+            sm.oc[s][ci] = 0;
+            float f = 0.f;
+            if (Rp->sp[s].drag) {
+                const float* m = s ? K.dmap1 : K.dmap0;
+                f = m ? m[lc] : Rp->sp[s].dragf;
+            }
+            sm.df[s][ci] = f;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sm.ub[c][ci] = anydrag ? Rp->ubar[c][lc] : 0.f;
     }
     __syncthreads();
 
@@ -400,171 +518,169 @@ __global__ void __launch_bounds__(NT, 3) push2d_kernel(const Args a) {
         }
     }
 
-    long long kacc[5] = {0, 0, 0, 0, 0};
-    int qn = 0;
-    const int nsp = a.nspecies;
-    // issue the asynchronous copies of one chunk into stage st
-    auto issue = [&](const Cursor& c, int st) {
-        if (c.ci < CELLS) {
-            const int i = c.j + lane;
-            if (i < sm.cnt[c.s][c.ci]) {
-                const int lx = c.ci % TX, ly = c.ci / TX;
-                const int g = K.cell_off + (y0 + ly) * nx + (x0 + lx);
-                const Slots S = a.slot[c.s][par];
-                const int q = slot32(g, a.cap[c.s], a.cap_stay[c.s], sm.cns[c.s][c.ci], i);
-                cp_async4(&sm.stg[warp][st][0][lane], S.o[0] + q);
-                cp_async4(&sm.stg[warp][st][1][lane], S.o[1] + q);
-                cp_async4(&sm.stg[warp][st][2][lane], S.u[0] + q);
-                cp_async4(&sm.stg[warp][st][3][lane], S.u[1] + q);
-                cp_async4(&sm.stg[warp][st][4][lane], S.u[2] + q);
-                if (S.id) cp_async4(&sm.stg[warp][st][5][lane], S.id + q);
-            }
-        }
-        cp_async_commit();
-    };
-    Cursor fc{warp, 0, -32};
-    advance(fc, sm.cnt, nsp);
-    Cursor pc = fc;
-#pragma unroll
-    for (int k = 0; k < STAGES - 1; ++k) {
-        issue(fc, k);
-        advance(fc, sm.cnt, nsp);
-    }
-    int st = 0;
-    int cur_ci = -1, n0 = 0, g = 0, nchunk = 0;
-    int seg_s = -1, seg_g = 0, wpos = 0;     // stay-area fill of the current (cell, species)
+    // L: the segment the next chunk is loaded from (lj its first element); the chunk in
+    // registers (nxt) is pushed in the following iteration.
+    Seg L = seg_find(sm, warp, 0, nsp, K.cell_off, nx, x0, y0);
+    int lj = 0;
+    Part nxt = load_part(L, 0, lane, sm.src[L.s], bstride, ids);
+    int cur_ci = -1, n0 = 0, nchunk = 0, qn = 0;
+    const bool cell_drag = anydrag;   // the tile's cells carry drag moments
     int acc[12];
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = 0;
-    float ub0 = 0.f, ub1 = 0.f, ub2 = 0.f;
-    while (pc.ci < CELLS) {
-        issue(fc, (st + STAGES - 1) % STAGES);
-        advance(fc, sm.cnt, nsp);
-        if (pc.ci != cur_ci) {
-            if (nchunk) { flush_acc(sm, acc, n0, lane); nchunk = 0; }
-            cur_ci = pc.ci;
-            const int lx = cur_ci % TX, ly = cur_ci / TX;
-            g = K.cell_off + (y0 + ly) * nx + (x0 + lx);
-            n0 = (ly + 1) * RX + (lx + 1);
-            if (anydrag) { ub0 = sm.ub[0][n0]; ub1 = sm.ub[1][n0]; ub2 = sm.ub[2][n0]; }
+    const float4* Tw = sm.T[warp];
+    const unsigned lt = (1u << lane) - 1u;
+    while (L.ci < CELLS) {
+        const int ci = L.ci, s = L.s, n = L.n, q0 = L.q0, j = lj;
+        const Part p = nxt;
+        lj += 32;
+        if (lj >= L.n) {
+            L = seg_find(sm, s + 1 < nsp ? ci : ci + NW, s + 1 < nsp ? s + 1 : 0, nsp, K.cell_off, nx, x0, y0);
+            lj = 0;
         }
-        const int s = pc.s;
+        if (L.ci < CELLS) nxt = load_part(L, lj, lane, sm.src[L.s], bstride, ids);
+        if (ci != cur_ci) {
+            if (nchunk) { flush_acc(sm, acc, n0, lane, cell_drag); nchunk = 0; }
+            cur_ci = ci;
+            n0 = (ci / TX + 1) * RX + (ci % TX + 1);
+            __syncwarp();
+            if (lane < 13) {
+                const float* f = &sm.F[0][0] + n0 + sm.toff[lane];
+                sm.T[warp][lane] = patch(f[0], f[1], f[RX], f[RX + 1]);
+            } else if (lane == 13) {
+                sm.T[warp][13] = make_float4(sm.ub[0][ci], sm.ub[1][ci], sm.ub[2][ci], 0.f);
+            }
+            __syncwarp();
+        }
         const SpeciesParams& P = sm.sp[s];
-        const int cap = a.cap[s], cst = a.cap_stay[s];
-        const Slots D = a.slot[s][par ^ 1];
-        if (pc.j == 0) {
-            // new (cell, species): record the previous one's stay count
-            if (seg_s >= 0 && lane == 0) a.slot[seg_s][par ^ 1].count[seg_g] = wpos;
-            seg_s = s;
-            seg_g = g;
-            wpos = 0;
+        const bool act = j + lane < n;
+        float EB[6];
+        gather_tab(Tw, p.ox, p.oy, EB);
+        const bool drag = P.drag;
+        float b0 = 0.f, b1 = 0.f, b2 = 0.f, df = 0.f;
+        if (drag) {
+            const float4 d = Tw[13];
+            b0 = d.x; b1 = d.y; b2 = d.z;
+            df = sm.df[s][ci];
         }
-        const int i = pc.j + lane;
-        const bool act = i < sm.cnt[s][pc.ci];
-        cp_async_wait<STAGES - 1>();
-        float ox = 0.f, oy = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
-        int id = 0;
-        if (act) {
-            ox = sm.stg[warp][st][0][lane]; oy = sm.stg[warp][st][1][lane];
-            ux = sm.stg[warp][st][2][lane]; uy = sm.stg[warp][st][3][lane]; uz = sm.stg[warp][st][4][lane];
-            id = __float_as_int(sm.stg[warp][st][5][lane]);
+        const Pushed r = push_rest(EB, P, K, p.ox, p.oy, p.ux, p.uy, p.uz, b0, b1, b2, df, s, (unsigned)p.id, step);
+        if (diag && act && !r.bad) {
+            long long kv[5] = {0, 0, 0, 0, 0};
+            kin_add(kv, s, P.w, p.ux, p.uy, p.uz, r.ux, r.uy, r.uz);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) sm.kl[k][tid] += kv[k];
         }
-        const float df = P.drag ? drag_of(K, P, s, g - K.cell_off) : 0.f;
-        const Pushed r = push_one(SharedFields{&sm, n0}, P, K, ox, oy, ux, uy, uz, ub0, ub1, ub2, df, s, (unsigned)id, step);
-        const bool small_u = !P.drag || (fabsf(r.ux) < 4.f && fabsf(r.uy) < 4.f && fabsf(r.uz) < 4.f);
+        const bool small_u = !drag || fmaxf(fabsf(r.ux), fmaxf(fabsf(r.uy), fabsf(r.uz))) < 4.f;
         const bool stay = act && !r.bad && r.sx == 0 && r.sy == 0 && small_u;
         if (stay) {
-            const Win wx = window(ox, 0, r.nox), wy = window(oy, 0, r.noy);
+            const Win wx = window(p.ox, 0, r.nox), wy = window(p.oy, 0, r.noy);
             const float zf = __fmul_rn(P.jz, r.vz);
             const float jxa = __fmul_rn(P.jx, wx.C[0]), jya = __fmul_rn(P.jy, wy.C[0]);
-            const float p0 = zp(wy.S0[0], wy.S1[0]), q0 = zq(wy.S0[0], wy.S1[0]);
-            const float p1 = zp(wy.S0[1], wy.S1[1]), q1 = zq(wy.S0[1], wy.S1[1]);
+            const float zp0 = zp(wy.S0[0], wy.S1[0]), zq0 = zq(wy.S0[0], wy.S1[0]);
+            const float zp1 = zp(wy.S0[1], wy.S1[1]), zq1 = zq(wy.S0[1], wy.S1[1]);
             acc[0] += round_small(jxa, wy.A[0]);                          // Jx (c+1/2, c)
             acc[1] += round_small(jxa, wy.A[1]);                          // Jx (c+1/2, c+1)
             acc[2] += round_small(jya, wx.A[0]);                          // Jy (c, c+1/2)
             acc[3] += round_small(jya, wx.A[1]);                          // Jy (c+1, c+1/2)
-            acc[4] += round_small(zf, zw(wx.S0[0], wx.S1[0], p0, q0));    // Jz (c, c)
-            acc[5] += round_small(zf, zw(wx.S0[1], wx.S1[1], p0, q0));    // Jz (c+1, c)
-            acc[6] += round_small(zf, zw(wx.S0[0], wx.S1[0], p1, q1));    // Jz (c, c+1)
-            acc[7] += round_small(zf, zw(wx.S0[1], wx.S1[1], p1, q1));    // Jz (c+1, c+1)
-            if (P.drag) {
-                acc[8] += __float2int_rn(r.ux * MOM_SCALE);
-                acc[9] += __float2int_rn(r.uy * MOM_SCALE);
-                acc[10] += __float2int_rn(r.uz * MOM_SCALE);
+            acc[4] += round_small(zf, zw(wx.S0[0], wx.S1[0], zp0, zq0));  // Jz (c, c)
+            acc[5] += round_small(zf, zw(wx.S0[1], wx.S1[1], zp0, zq0));  // Jz (c+1, c)
+            acc[6] += round_small(zf, zw(wx.S0[0], wx.S1[0], zp1, zq1));  // Jz (c, c+1)
+            acc[7] += round_small(zf, zw(wx.S0[1], wx.S1[1], zp1, zq1));  // Jz (c+1, c+1)
+            if (drag) {
+                // |u| < 4: round_small gives rint(u 2^20), the value f2ll_rn gives on the other paths
+                acc[8] += round_small(r.ux, MOM_SCALE);
+                acc[9] += round_small(r.uy, MOM_SCALE);
+                acc[10] += round_small(r.uz, MOM_SCALE);
                 acc[11] += 1;
             }
-            if (diag) kin_add(kacc, s, P.w, ux, uy, uz, r.ux, r.uy, r.uz);
         }
-        // stayers keep their cell: the next free places of its stay area in the other buffer
-        const unsigned sm_ = __ballot_sync(FULL, stay);
-        if (stay) {
-            const int pos = wpos + __popc(sm_ & lt);
-            if (pos < cst) store_slot(D, g * cap + pos, r.nox, r.noy, r.ux, r.uy, r.uz, id);
-            else put_imm(D, cap, cst, a.spill_cap[s], g, r.nox, r.noy, r.ux, r.uy, r.uz, id, &a.ctl->err);
+        // stayers take the next places of their cell's stay area in the other buffer
+        const unsigned smask = __ballot_sync(FULL, stay);
+        if (smask) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&sm.oc[s][ci], __popc(smask));
+            base = __shfl_sync(FULL, base, 0);
+            if (stay) {
+                const int pos = base + __popc(smask & lt);
+                if (pos < sm.cst[s]) store2(sm.dst[s], bstride, ids, q0 + pos, r.nox, r.noy, r.ux, r.uy, r.uz, p.id);
+                else put_imm(sm.dslot[s], sm.cap[s], sm.cst[s], sm.spc[s], q0 / sm.cap[s], r.nox, r.noy, r.ux, r.uy,
+                             r.uz, p.id, &a.ctl->err);
+            }
         }
-        wpos += __popc(sm_);
+        // the others are queued with their pushed state (bad ones with their old state)
         const bool defer = act && !stay;
         const unsigned dm = __ballot_sync(FULL, defer);
-        if (defer) sm.q[warp][qn + __popc(dm & lt)] = ((unsigned)s << 24) | ((unsigned)pc.ci << 16) | (unsigned)i;
-        qn += __popc(dm);
-        __syncwarp();
-        if (qn >= 32) {
-            drain(sm, a, K, par, 32, lane, warp, x0, y0, diag, step, kacc);
+        if (dm) {
+            if (qn + __popc(dm) > QCAP) {
+                drain(sm, a, K, qn, lane, warp, x0, y0);
+                qn = 0;
+            }
+            if (defer) {
+                const int k = qn + __popc(dm & lt);
+                sm.qa[warp][k] = make_float4(p.ox, p.oy, r.nox, r.noy);
+                sm.qb[warp][k] = make_float4(r.ux, r.uy, r.uz, r.vz);
+                sm.qc[warp][k] = make_int2(qmeta(s, ci, r.sx, r.sy, false), p.id);
+                if (r.bad) {
+                    // rare: kept unmoved with its old state
+                    sm.qa[warp][k] = make_float4(p.ox, p.oy, p.ox, p.oy);
+                    sm.qb[warp][k] = make_float4(p.ux, p.uy, p.uz, r.vz);
+                    sm.qc[warp][k] = make_int2(qmeta(s, ci, 0, 0, true), p.id);
+                }
+            }
+            qn += __popc(dm);
             __syncwarp();
-            const int rest = qn - 32;
-            const unsigned moved = lane < rest ? sm.q[warp][32 + lane] : 0u;
-            __syncwarp();
-            if (lane < rest) sm.q[warp][lane] = moved;
-            __syncwarp();
-            qn = rest;
         }
         if (++nchunk == FLUSH_CHUNKS) {
-            flush_acc(sm, acc, n0, lane);
+            flush_acc(sm, acc, n0, lane, cell_drag);
             nchunk = 0;
         }
-        advance(pc, sm.cnt, nsp);
-        st = (st + 1) % STAGES;
     }
-    if (nchunk) flush_acc(sm, acc, n0, lane);
-    if (seg_s >= 0 && lane == 0) a.slot[seg_s][par ^ 1].count[seg_g] = wpos;
-    cp_async_wait<0>();
-    if (qn > 0) drain(sm, a, K, par, qn, lane, warp, x0, y0, diag, step, kacc);
-    __syncwarp();
+    if (nchunk) flush_acc(sm, acc, n0, lane, cell_drag);
+    if (qn > 0) drain(sm, a, K, qn, lane, warp, x0, y0);
 
     if (diag) {
+        // the threads' kinetic and momentum sums: warp sums, then the CTA's
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            long long v = kacc[k];
+            long long v = sm.kl[k][tid];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
             if (lane == 0 && v != 0) atomicAdd(&sm.kin[k], (unsigned long long)v);
         }
         __syncthreads();
         if (tid < 5 && sm.kin[tid] != 0ull) {
             // Ekin per species, momentum summed into species 0's slots
-            long long* K = a.kin + (size_t)wk.x * PIC_NS * 4;
-            if (tid < 2) atomicAdd((unsigned long long*)&K[tid * 4], sm.kin[tid]);
-            else atomicAdd((unsigned long long*)&K[tid - 1], sm.kin[tid]);
+            long long* Kk = a.kin + (size_t)wk.x * PIC_NS * 4;
+            if (tid < 2) atomicAdd((unsigned long long*)&Kk[tid * 4], sm.kin[tid]);
+            else atomicAdd((unsigned long long*)&Kk[tid - 1], sm.kin[tid]);
         }
     }
     __syncthreads();
 
+    // stay counts of the tile's cells in the other buffer (readers clamp them to the stay area)
+    for (int i = tid; i < PIC_NS * CELLS; i += NT) {
+        const int s = i / CELLS, ci = i - s * CELLS;
+        if (s < nsp && Rp->sp[s].active) {
+            const int gg = K.cell_off + (y0 + ci / TX) * nx + (x0 + ci % TX);
+            sm.dslot[s].count[gg] = sm.oc[s][ci];
+        }
+    }
     // flush the region to global memory (halo nodes overlap neighbouring tiles: atomics)
     for (int i = tid; i < RN; i += NT) {
         const int ry = i / RX, rx = i - ry * RX;
-        const size_t g = (size_t)wrapi(gy0 + ry, ny) * nx + wrapi(gx0 + rx, nx);
+        const size_t gi = (size_t)wrapi(gy0 + ry, ny) * nx + wrapi(gx0 + rx, nx);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long v = (long long)sm.Jhi[c][i] * 4096 + (long long)sm.Jlo[c][i];
-            if (v) atomicAdd((unsigned long long*)&Rp->J[c][g], (unsigned long long)v);
+            if (v) atomicAdd((unsigned long long*)&Rp->J[c][gi], (unsigned long long)v);
         }
         if (anydrag) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const long long v = (long long)sm.Mhi[c][i] * 4096 + (long long)sm.Mlo[c][i];
-                if (v) atomicAdd((unsigned long long*)&Rp->msum[c][g], (unsigned long long)v);
+                if (v) atomicAdd((unsigned long long*)&Rp->msum[c][gi], (unsigned long long)v);
             }
-            if (sm.MC[i]) atomicAdd(&Rp->mcnt[g], sm.MC[i]);
+            if (sm.MC[i]) atomicAdd(&Rp->mcnt[gi], sm.MC[i]);
         }
     }
 }
@@ -579,11 +695,11 @@ struct KinCache {
     int run = -1;
     __device__ void flush(const Args& a) {
         if (run < 0) return;
-        long long* K = a.kin + (size_t)run * PIC_NS * 4;
-        if (v[0]) atomicAdd((unsigned long long*)&K[0], (unsigned long long)v[0]);
-        if (v[1]) atomicAdd((unsigned long long*)&K[4], (unsigned long long)v[1]);
+        long long* Kk = a.kin + (size_t)run * PIC_NS * 4;
+        if (v[0]) atomicAdd((unsigned long long*)&Kk[0], (unsigned long long)v[0]);
+        if (v[1]) atomicAdd((unsigned long long*)&Kk[4], (unsigned long long)v[1]);
         for (int c = 0; c < 3; ++c)
-            if (v[2 + c]) atomicAdd((unsigned long long*)&K[1 + c], (unsigned long long)v[2 + c]);
+            if (v[2 + c]) atomicAdd((unsigned long long*)&Kk[1 + c], (unsigned long long)v[2 + c]);
         for (int c = 0; c < 5; ++c) v[c] = 0;
     }
     __device__ void use(const Args& a, int r) {
@@ -633,8 +749,9 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
             if (P.drag) { b0 = Rp->ubar[0][lc]; b1 = Rp->ubar[1][lc]; b2 = Rp->ubar[2][lc]; }
             const RunConst K = run_const(Rp);
             const float df = P.drag ? drag_of(K, P, s, lc) : 0.f;
-            const Pushed r = push_one(GlobalFields{Rp, cx, cy}, P, K, ox, oy, u0x, u0y, u0z, b0, b1, b2, df, s,
-                                      (unsigned)id, step);
+            float EB[6];
+            gather_fetch(GlobalFields{Rp, cx, cy}, ox, oy, EB);
+            const Pushed r = push_rest(EB, P, K, ox, oy, u0x, u0y, u0z, b0, b1, b2, df, s, (unsigned)id, step);
             if (r.bad) {
                 atomicOr(&a.ctl->err, ERR_BADPART);
                 put_imm(D, cap, cst, a.spill_cap[s], g, ox, oy, u0x, u0y, u0z, id, &a.ctl->err);
@@ -669,25 +786,73 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
     kc.finish(a);
 }
 
+// ------------------------------------------------------------------ variants and launch
+// Compiled variants of the particle kernel: tile shape and CTAs per SM (the register budget).
+struct Variant {
+    void (*fn)(Args);
+    int tx, ty, minb;
+    size_t smem;
+};
+template <int TX, int TY, int MINB>
+constexpr Variant make_variant() {
+    return Variant{push2d_kernel<TX, TY, MINB>, TX, TY, MINB, sizeof(Smem<TX, TY>)};
+}
+const Variant kVariants[] = {
+    make_variant<16, 16, 3>(), make_variant<16, 16, 2>(),
+    make_variant<32, 8, 3>(),  make_variant<32, 8, 2>(),
+    make_variant<8, 32, 3>(),  make_variant<8, 32, 2>(),
+};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+// The dynamic shared-memory limit is a per-device attribute of each kernel: set it once per
+// (device, variant).
+std::mutex g_attr_mu;
+unsigned long long g_attr_done[64];   // bit v of entry d: variant v configured on device d
+
+cudaError_t ensure_attr(int v) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (g_attr_done[dev] & (1ull << v)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kVariants[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVariants[v].smem);
+    if (e != cudaSuccess) return e;
+    g_attr_done[dev] |= 1ull << v;
+    return cudaSuccess;
+}
+
 }  // namespace
+
+// Index of the compiled variant for a tile shape and CTAs per SM (minb 0: the default, 2 CTAs
+// per SM with 128 registers: the 3-CTA budget of 80 registers spills), or -1.
+int push2d_variant(int tx, int ty, int minb) {
+    for (int v = 0; v < kNumVariants; ++v)
+        if (kVariants[v].tx == tx && kVariants[v].ty == ty && kVariants[v].minb == (minb == 0 ? 2 : minb))
+            return v;
+    return -1;
+}
+int push2d_num_variants() { return kNumVariants; }
+void push2d_variant_info(int v, int* tx, int* ty, int* minb) {
+    *tx = kVariants[v].tx;
+    *ty = kVariants[v].ty;
+    *minb = kVariants[v].minb;
+}
 
 cudaError_t launch_push2d(const Args& a, cudaStream_t s) {
     if (a.nwork == 0) return cudaSuccess;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(push2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(Smem));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    push2d_kernel<<<a.nwork, NT, sizeof(Smem), s>>>(a);
+    const int v = a.push_variant;
+    if (v < 0 || v >= kNumVariants || kVariants[v].tx != a.tx || kVariants[v].ty != a.ty) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_attr(v);
+    if (e != cudaSuccess) return e;
+    kVariants[v].fn<<<a.nwork, NT, kVariants[v].smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t preload_push2d() {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, push2d_kernel);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, spill2d_kernel);
+    cudaError_t e = cudaFuncGetAttributes(&fa, spill2d_kernel);
+    for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) e = cudaFuncGetAttributes(&fa, kVariants[v].fn);
     return e;
 }
 

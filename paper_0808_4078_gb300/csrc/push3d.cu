@@ -219,8 +219,9 @@ __device__ __forceinline__ void red_shared_nz(int* p, int v) {
 }
 
 // ------------------------------------------------------------------ rebinning
-__device__ __forceinline__ void store3(const Slots& D, size_t q, const float o[3], float ux, float uy,
+__device__ __forceinline__ void store3(const Slots& D, size_t slot, const float o[3], float ux, float uy,
                                        float uz, int id) {
+    const size_t q = slot_elt(D, (long long)slot);
     D.o[0][q] = o[0]; D.o[1][q] = o[1]; D.o[2][q] = o[2];
     D.u[0][q] = ux; D.u[1][q] = uy; D.u[2][q] = uz;
     if (D.id) D.id[q] = id;
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
                 const int lx = ci % TX, ly = (ci / TX) % TY, lz = ci / (TX * TY);
                 const long long g = cbase + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
                 const Slots& S = a.slot[s][par];
-                const size_t q = slot_of(g, a.cap[s], a.cap_stay[s], sm.cns[e], p - sm.pre[e]);
+                const size_t q = slot_elt(S, (long long)slot_of(g, a.cap[s], a.cap_stay[s], sm.cns[e], p - sm.pre[e]));
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     po[r][d] = S.o[d][q];

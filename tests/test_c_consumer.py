@@ -50,7 +50,7 @@ def test_host_calls_from_c(consumer):
     import paper_0808_4078_gb300 as pic
     cap = (ctypes.c_int64 * 2)(65536, 65536)
     cfg = pic.Config(2, 64, 64, 1, 0.1, 0.1, 0.1, 0.05, 2, cap, (ctypes.c_int32 * 2)(0, 0), 8, 1, 100,
-                     0, 0, 0, 0, 0, 0)
+                     0, 0, 0, 0, 0, 0, 0)
     assert consumer["required_rc"] == "0"
     assert int(consumer["required_bytes"]) == pic.required_bytes(cfg)
     assert consumer["bad_rc"] == "-1" and consumer["bad_has_text"] == "1"

@@ -93,7 +93,18 @@ def test_batch_geometry_without_gpu(libpic):
     assert _batch_bytes(cfg, [4096, 4096, 1], [1, 1])[0] == -1               # slots >= 2^31
     cfg.cell_capacity[0] = cfg.cell_capacity[1] = 0
     cfg.tile_x = 8
-    assert _batch_bytes(cfg, [64, 64, 1], [1, 1])[0] == -1                   # 2D tiles are 16 x 16
+    assert _batch_bytes(cfg, [64, 64, 1], [1, 1])[0] == -1                   # 8 x 16 is not a 2D tile
+    for tx, ty in ((32, 8), (8, 32), (16, 16)):
+        cfg.tile_x, cfg.tile_y = tx, ty
+        for ctas in (0, 2, 3):
+            cfg.ctas_per_sm = ctas
+            assert _batch_bytes(cfg, [64, 64, 1], [1, 1])[0] == 0, (tx, ty, ctas)
+        cfg.ctas_per_sm = 4
+        assert _batch_bytes(cfg, [64, 64, 1], [1, 1])[0] == -1               # no 4-CTA variant
+    cfg.ctas_per_sm = 0
+    cfg.tile_x, cfg.tile_y = 32, 8
+    assert _batch_bytes(cfg, [48, 64, 1], [1, 1])[0] == -1                   # 48 not a multiple of 32
+    cfg.tile_x = cfg.tile_y = 0
     c3 = pic.Config(3, 16, 16, 8, 0.1, 0.1, 0.1, 0.05, 2, z2(), (ctypes.c_int32 * 2)(0, 0), 8, 1,
                     16, 0, 0, 0, 0, 0, 0)
     rc, n3 = _batch_bytes(c3, [16, 16, 8], [16 * 16 * 8 * 8] * 2)
