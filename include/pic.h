@@ -172,6 +172,13 @@ int pic_step(pic_ctx* ctx, int nsteps);
 /* Wait for the stream; report sticky device errors. */
 int pic_sync(pic_ctx* ctx);
 
+/* Wait for the stream, write the sticky device error bits to *flags_out (may be NULL; bit 1:
+ * a non-finite or out-of-range particle, which the step kept unmoved and left out of the
+ * current; 2: fixed-point headroom; 4: a bounded wait gave up; 8: a spill list was full) and
+ * clear them, so that a caller can read back the state that produced the error.  The state
+ * after an error is the step's result for every particle that did not raise it.  PIC_OK. */
+int pic_clear_flags(pic_ctx* ctx, int32_t* flags_out);
+
 /* Copy up to max_recs diagnostic records (oldest first) to out.  Synchronises. */
 int pic_diag(pic_ctx* ctx, pic_diag_rec* out, int max_recs, int* n_out);
 int pic_diag_run(pic_ctx* ctx, int run, pic_diag_rec* out, int max_recs, int* n_out);
@@ -409,8 +416,16 @@ int pic_mlp_train_step(float* params, float* adam_m, float* adam_v, int32_t t, f
                        const pic_mlp_norm* norm, const float* x, int64_t ldx, const float* target,
                        int64_t n, float* loss, void* scratch, size_t scratch_bytes, void* stream);
 /* PIC_OK, or PIC_ETIMEOUT if a tensor-core completion wait of the network kernels gave up
- * (sticky until read with clear != 0).  Synchronous. */
+ * (sticky until read with clear != 0).  The outputs of a call during which a wait gave up are
+ * undefined: a kernel that times out waits once more (also bounded) for the tensor cores before
+ * it frees its tensor memory and returns, and the network's results of that call are not
+ * written in full.  Synchronous. */
 int pic_mlp_status(int clear);
+
+/* Test hook of the bounded wait above: one CTA on `stream` waits on a completion barrier that
+ * nothing arrives on, with no tensor-core work issued, giving up after `polls` polls
+ * (1 <= polls <= 2^20); the give-up sets the flag pic_mlp_status reports.  Asynchronous. */
+int pic_mlp_wait_test(int64_t polls, void* stream);
 
 /* Counting sort by cell, the binning primitive of the re-binning step, on caller device memory:
  * cell[n] (device) holds each particle's cell in [0, ncell); writes start[ncell + 1] (device;

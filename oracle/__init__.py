@@ -28,19 +28,36 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pic_oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
+_SO_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 
 P = ctypes.POINTER(ctypes.c_double)
 
 
 def build(force: bool = False) -> str:
-    """Compile pic_oracle.c into oracle/liboracle.so with the host gcc (no -march flags)."""
+    """Compile pic_oracle.c into oracle/liboracle.so with the host gcc (no -march flags), and
+    the all-core variant (build_threads)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC",
                                "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
+    build_threads(force)
     return _SO
+
+
+def build_threads(force: bool = False) -> str:
+    """The same C with OpenMP (-O3 -fopenmp; no -march flags, so that it gives the same results
+    on every host): the particle loop on all threads, each depositing into its own current and
+    moment arrays.  Used to time the oracle on every host core; the tests' oracle is the
+    single-threaded build."""
+    if force or not os.path.exists(_SO_OMP) or os.path.getmtime(_SO_OMP) < os.path.getmtime(_SRC):
+        tmp = _SO_OMP + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O3", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO_OMP)
+    return _SO_OMP
 
 
 class _Grid(ctypes.Structure):
@@ -70,37 +87,51 @@ class _Diag(ctypes.Structure):
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        _lib.orc_step.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Species), ctypes.c_int,
-                                  ctypes.POINTER(_Diag)]
-        _lib.orc_step.restype = ctypes.c_int
-        _lib.orc_moments.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Species)]
-        _lib.orc_moments.restype = ctypes.c_int
-        _lib.orc_yee.argtypes = [ctypes.POINTER(_Grid)]
-        _lib.orc_yee.restype = None
-        _lib.orc_binomial.argtypes = [ctypes.POINTER(_Grid), P]
-        _lib.orc_binomial.restype = None
-        _lib.orc_rho.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Species), ctypes.c_int, P]
-        _lib.orc_rho.restype = None
-        _lib.orc_gather.argtypes = [ctypes.POINTER(_Grid), ctypes.c_double, ctypes.c_double,
-                                    ctypes.c_double, P]
-        _lib.orc_gather.restype = None
-        _lib.orc_boris.argtypes = [ctypes.c_double, ctypes.c_double, P, P]
-        _lib.orc_boris.restype = None
-        _lib.orc_push_particle.argtypes = [ctypes.POINTER(_Grid), ctypes.c_double, ctypes.c_double,
-                                           P, P, P, P, P]
-        _lib.orc_push_particle.restype = None
-        _lib.orc_deposit_move.argtypes = [ctypes.POINTER(_Grid), ctypes.c_double, P, P,
-                                          ctypes.c_double]
-        _lib.orc_deposit_move.restype = None
-        _lib.orc_gather_many.argtypes = [ctypes.POINTER(_Grid), ctypes.c_int64, P, P, P, P]
-        _lib.orc_gather_many.restype = None
-        U32 = ctypes.POINTER(ctypes.c_uint32)
-        _lib.orc_philox4x32_10.argtypes = [U32, U32, U32]
-        _lib.orc_philox4x32_10.restype = None
-        _lib.orc_collide_ion.argtypes = [P, ctypes.c_double, U32]
-        _lib.orc_collide_ion.restype = None
+        _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+def lib_threads():
+    """The all-core build (see build_threads)."""
+    global _lib_omp
+    if _lib_omp is None:
+        build()
+        _lib_omp = _bind(ctypes.CDLL(build_threads()))
+    return _lib_omp
+
+
+def _bind(L):
+    """Argument types of the oracle library's entry points."""
+    L.orc_step.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Species), ctypes.c_int,
+                           ctypes.POINTER(_Diag)]
+    L.orc_step.restype = ctypes.c_int
+    L.orc_moments.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Species)]
+    L.orc_moments.restype = ctypes.c_int
+    L.orc_yee.argtypes = [ctypes.POINTER(_Grid)]
+    L.orc_yee.restype = None
+    L.orc_binomial.argtypes = [ctypes.POINTER(_Grid), P]
+    L.orc_binomial.restype = None
+    L.orc_rho.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Species), ctypes.c_int, P]
+    L.orc_rho.restype = None
+    L.orc_gather.argtypes = [ctypes.POINTER(_Grid), ctypes.c_double, ctypes.c_double,
+                             ctypes.c_double, P]
+    L.orc_gather.restype = None
+    L.orc_boris.argtypes = [ctypes.c_double, ctypes.c_double, P, P]
+    L.orc_boris.restype = None
+    L.orc_push_particle.argtypes = [ctypes.POINTER(_Grid), ctypes.c_double, ctypes.c_double,
+                                       P, P, P, P, P]
+    L.orc_push_particle.restype = None
+    L.orc_deposit_move.argtypes = [ctypes.POINTER(_Grid), ctypes.c_double, P, P,
+                                   ctypes.c_double]
+    L.orc_deposit_move.restype = None
+    L.orc_gather_many.argtypes = [ctypes.POINTER(_Grid), ctypes.c_int64, P, P, P, P]
+    L.orc_gather_many.restype = None
+    U32 = ctypes.POINTER(ctypes.c_uint32)
+    L.orc_philox4x32_10.argtypes = [U32, U32, U32]
+    L.orc_philox4x32_10.restype = None
+    L.orc_collide_ion.argtypes = [P, ctypes.c_double, U32]
+    L.orc_collide_ion.restype = None
+    return L
 
 
 def _ptr(a):
@@ -140,8 +171,9 @@ class Species:
 class Simulation:
     """Grid + species, advanced by the C oracle one step at a time."""
 
-    def __init__(self, ndim, nx, ny, nz=1, dx=0.1, dy=None, dz=None, dt=0.05, j_filter=0):
+    def __init__(self, ndim, nx, ny, nz=1, dx=0.1, dy=None, dz=None, dt=0.05, j_filter=0, threads=False):
         self.ndim, self.nx, self.ny = ndim, nx, ny
+        self.threads = bool(threads)    # step with the all-core build (timing only)
         self.j_filter = int(j_filter)   # 1: binomial pass per axis on J before the field update
         self.nz = nz if ndim == 3 else 1
         self.dx = dx
@@ -201,9 +233,10 @@ class Simulation:
                 raise MemoryError("orc_moments")
 
     @classmethod
-    def from_workload(cls, wl, j_filter=0):
+    def from_workload(cls, wl, j_filter=0, threads=False):
         """Build from a pic_inputs.Workload: X = cell index + FP32 offset, exactly, in FP64."""
-        sim = cls(wl.ndim, wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, wl.dz, wl.dt, j_filter=j_filter)
+        sim = cls(wl.ndim, wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, wl.dz, wl.dt, j_filter=j_filter,
+                  threads=threads)
         for s in wl.species:
             i = (s.cell % wl.nx).astype(np.float64)
             j = ((s.cell // wl.nx) % wl.ny).astype(np.float64)
@@ -218,7 +251,7 @@ class Simulation:
         return sim
 
     def step(self, n=1, record=True):
-        L = lib()
+        L = lib_threads() if self.threads else lib()
         g = self.cgrid()
         arr = (_Species * len(self.species))(*[s.cstruct() for s in self.species])
         for _ in range(n):

@@ -36,6 +36,9 @@
  *   Bx(i,j+1/2,k+1/2) By(i+1/2,j,k+1/2) Bz(i+1/2,j+1/2,k).
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -486,6 +489,90 @@ void orc_push_particle(const orc_grid *g, double qm, double nu, double *X, doubl
 
 /* ---------------------------------------------------------------- full step */
 
+/* Particle p of species s (index si): push, deposit into g's current, diagnostics into d (may
+ * be NULL), cell-mean momentum sums into nsum/ncnt (NULL without drag). */
+static void step_particle(const orc_grid *g, orc_species *s, int si, int64_t p, double qm, double qw,
+                          double dragf, double dV, orc_diag *d, double *nsum, double *ncnt) {
+    double P0[3] = {s->X[p], s->Y[p], g->ndim == 3 ? s->Z[p] : 0.0}, P1[3];
+    double u0[3] = {s->ux[p], s->uy[p], s->uz[p]};
+    double u[3] = {u0[0], u0[1], u0[2]};
+    const double *ub = s->ubar ? &s->ubar[3 * ngp_cell(g, s, p)] : NULL;
+    double df = dragf;
+    if (s->ubar && s->nu_cell) {
+        double r = s->nu_cell[ngp_cell(g, s, p)];
+        df = r > 0.0 ? 1.0 - exp(-r * g->dt) : 0.0;
+    }
+    push_one(g, qm, P0, u, ub, df, s, p, P1);
+    double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (g->ndim == 2) deposit_2d((orc_grid *)g, qw, P0[0], P0[1], P1[0], P1[1], u[2] / gam);
+    else deposit_3d((orc_grid *)g, qw, P0, P1);
+    if (d) {
+        /* time-n momentum: mean of u^{n-1/2} and u^{n+1/2} */
+        double um[3] = {0.5 * (u0[0] + u[0]), 0.5 * (u0[1] + u[1]), 0.5 * (u0[2] + u[2])};
+        double gmid = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+        d->Ekin[si] += s->w * (gmid - 1.0) * dV;
+        for (int a = 0; a < 3; a++) d->P[a] += s->w * um[a] * dV;
+    }
+    s->X[p] = wrap_pos(P1[0], g->nx);
+    s->Y[p] = wrap_pos(P1[1], g->ny);
+    if (g->ndim == 3) s->Z[p] = wrap_pos(P1[2], g->nz);
+    s->ux[p] = u[0]; s->uy[p] = u[1]; s->uz[p] = u[2];
+    if (nsum) {
+        /* cell of the new position: the next step's drag mean */
+        int64_t c = ngp_cell(g, s, p);
+        for (int a = 0; a < 3; a++) nsum[3 * c + a] += u[a];
+        ncnt[c] += 1.0;
+    }
+}
+
+#ifdef _OPENMP
+/* The particle loop of one species on all threads (build with -fopenmp; used only to time the
+ * oracle on every host core): each thread deposits into its own current and moment arrays,
+ * summed afterwards in thread order.  The same per-particle arithmetic as the serial loop; sums
+ * are taken in a different order. */
+static int step_species_threads(orc_grid *g, orc_species *s, int si, double qm, double qw, double dragf,
+                                double dV, orc_diag *d, double *nsum, double *ncnt) {
+    const int64_t nc = ncell_of(g);
+    const int T = omp_get_max_threads();
+    double *J = calloc((size_t)T * 3 * (size_t)nc, sizeof(double));
+    double *M = nsum ? calloc((size_t)T * 4 * (size_t)nc, sizeof(double)) : NULL;
+    orc_diag *D = calloc((size_t)T, sizeof(orc_diag));
+    if (!J || (nsum && !M) || !D) { free(J); free(M); free(D); return -1; }
+#pragma omp parallel num_threads(T)
+    {
+        const int t = omp_get_thread_num();
+        orc_grid gl = *g;
+        gl.Jx = J + (size_t)t * 3 * nc;
+        gl.Jy = gl.Jx + nc;
+        gl.Jz = gl.Jy + nc;
+        double *ns = M ? M + (size_t)t * 4 * nc : NULL, *nn = ns ? ns + 3 * nc : NULL;
+#pragma omp for schedule(static)
+        for (int64_t p = 0; p < s->n; p++)
+            step_particle(&gl, s, si, p, qm, qw, dragf, dV, d ? &D[t] : NULL, ns, nn);
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < nc; c++)
+        for (int t = 0; t < T; t++) {
+            const double *Jt = J + (size_t)t * 3 * nc;
+            g->Jx[c] += Jt[c];
+            g->Jy[c] += Jt[nc + c];
+            g->Jz[c] += Jt[2 * nc + c];
+            if (M) {
+                const double *Mt = M + (size_t)t * 4 * nc;
+                for (int a = 0; a < 3; a++) nsum[3 * c + a] += Mt[3 * c + a];
+                ncnt[c] += Mt[3 * nc + c];
+            }
+        }
+    if (d)
+        for (int t = 0; t < T; t++) {
+            d->Ekin[si] += D[t].Ekin[si];
+            for (int a = 0; a < 3; a++) d->P[a] += D[t].P[a];
+        }
+    free(J); free(M); free(D);
+    return 0;
+}
+#endif
+
 int orc_step(orc_grid *g, orc_species *sp, int nsp, orc_diag *d) {
     int64_t nc = ncell_of(g);
     double dV = g->dx * g->dy * (g->ndim == 3 ? g->dz : 1.0);
@@ -502,44 +589,21 @@ int orc_step(orc_grid *g, orc_species *sp, int nsp, orc_diag *d) {
         orc_species *s = &sp[si];
         double qm = s->q / s->m, qw = s->q * s->w;
         double dragf = (s->ubar && s->nu > 0.0) ? 1.0 - exp(-s->nu * g->dt) : 0.0;
-        int per_cell = s->ubar && s->nu_cell;
         double *nsum = NULL, *ncnt = NULL;
         if (s->ubar) {
             nsum = calloc(3 * (size_t)nc, sizeof(double));
             ncnt = calloc((size_t)nc, sizeof(double));
             if (!nsum || !ncnt) { free(nsum); free(ncnt); return -1; }
         }
-        for (int64_t p = 0; p < s->n; p++) {
-            double P0[3] = {s->X[p], s->Y[p], g->ndim == 3 ? s->Z[p] : 0.0}, P1[3];
-            double u0[3] = {s->ux[p], s->uy[p], s->uz[p]};
-            double u[3] = {u0[0], u0[1], u0[2]};
-            const double *ub = s->ubar ? &s->ubar[3 * ngp_cell(g, s, p)] : NULL;
-            double df = dragf;
-            if (per_cell) {
-                double r = s->nu_cell[ngp_cell(g, s, p)];
-                df = r > 0.0 ? 1.0 - exp(-r * g->dt) : 0.0;
+#ifdef _OPENMP
+        if (omp_get_max_threads() > 1) {
+            if (step_species_threads(g, s, si, qm, qw, dragf, dV, d, nsum, ncnt) != 0) {
+                free(nsum); free(ncnt); return -1;
             }
-            push_one(g, qm, P0, u, ub, df, s, p, P1);
-            double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-            if (g->ndim == 2) deposit_2d(g, qw, P0[0], P0[1], P1[0], P1[1], u[2] / gam);
-            else deposit_3d(g, qw, P0, P1);
-            if (d) {
-                /* time-n momentum: mean of u^{n-1/2} and u^{n+1/2} */
-                double um[3] = {0.5 * (u0[0] + u[0]), 0.5 * (u0[1] + u[1]), 0.5 * (u0[2] + u[2])};
-                double gmid = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-                d->Ekin[si] += s->w * (gmid - 1.0) * dV;
-                for (int a = 0; a < 3; a++) d->P[a] += s->w * um[a] * dV;
-            }
-            s->X[p] = wrap_pos(P1[0], g->nx);
-            s->Y[p] = wrap_pos(P1[1], g->ny);
-            if (g->ndim == 3) s->Z[p] = wrap_pos(P1[2], g->nz);
-            s->ux[p] = u[0]; s->uy[p] = u[1]; s->uz[p] = u[2];
-            if (nsum) {
-                int64_t c = ngp_cell(g, s, p);
-                for (int a = 0; a < 3; a++) nsum[3 * c + a] += u[a];
-                ncnt[c] += 1.0;
-            }
-        }
+        } else
+#endif
+        for (int64_t p = 0; p < s->n; p++)
+            step_particle(g, s, si, p, qm, qw, dragf, dV, d, nsum, ncnt);
         if (nsum) {
             for (int64_t c = 0; c < nc; c++)
                 for (int a = 0; a < 3; a++)

@@ -100,6 +100,7 @@ _SIGNATURES = {
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "pic_step": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pic_sync": (ctypes.c_int, [_VP]),
+    "pic_clear_flags": (ctypes.c_int, [_VP, _VP]),
     "pic_diag": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "pic_get_particles": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.c_int64]),
     "pic_get_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -121,6 +122,7 @@ _SIGNATURES = {
     "pic_mlp_train_step": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_float, ctypes.POINTER(MlpNorm),
                                           _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP, _VP, ctypes.c_size_t, _VP]),
     "pic_mlp_status": (ctypes.c_int, [ctypes.c_int]),
+    "pic_mlp_wait_test": (ctypes.c_int, [ctypes.c_int64, _VP]),
     "pic_set_drag_map": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int32, ctypes.c_int32]),
     "pic_set_collisions": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64]),
     "pic_dispersion_growth": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
@@ -261,6 +263,12 @@ class Engine:
 
     def sync(self):
         _check(lib().pic_sync(self._ctx), self._ctx)
+
+    def clear_flags(self):
+        """Sticky device error bits (PIC_FLAG_BIT_*), cleared."""
+        f = ctypes.c_int32(0)
+        _check(lib().pic_clear_flags(self._ctx, ctypes.byref(f)), self._ctx)
+        return f.value
 
     def diag(self, max_recs=None, run=0):
         cap = self.cfg.diag_capacity if max_recs is None else max_recs

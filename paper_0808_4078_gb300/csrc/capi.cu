@@ -9,8 +9,11 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -701,6 +704,37 @@ extern "C" int pic_sync(pic_ctx* ctx) {
     return device_flags(ctx);
 }
 
+namespace pic {
+// Kernels whose shared-memory limit is set, per device (the attribute is per device: a process
+// that drives several GPUs sets it on each).
+cudaError_t smem_attr_once(const void* fn, int bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void*>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, fn})) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.insert({dev, fn});
+    return e;
+}
+}  // namespace pic
+
+extern "C" int pic_clear_flags(pic_ctx* ctx, int32_t* flags_out) {
+    if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    CK(cudaStreamSynchronize(ctx->stream));
+    Ctl h;
+    int rc = read_ctl(ctx, &h);
+    if (rc) return rc;
+    if (flags_out) *flags_out = h.err;
+    const int zero = 0;
+    CK(cudaMemcpyAsync(reinterpret_cast<char*>(at<Ctl>(ctx, ctx->lay.ctl)) + offsetof(Ctl, err), &zero, sizeof zero,
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PIC_OK;
+}
+
 extern "C" int pic_diag_run(pic_ctx* ctx, int run, pic_diag_rec* out, int max_recs, int* n_out) {
     if (!ctx || !n_out || (max_recs > 0 && !out)) return fail(ctx, PIC_EINVAL, "null argument");
     int rc = check_run(ctx, run);
@@ -1081,6 +1115,13 @@ extern "C" int pic_mlp_train_step(float* params, float* adam_m, float* adam_v, i
     cudaError_t e = launch_mlp_train(params, adam_m, adam_v, t, lr, nm, x, ldx, target, n, loss, scratch,
                                      (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, "pic_mlp_train_step: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+extern "C" int pic_mlp_wait_test(int64_t polls, void* stream) {
+    if (polls < 1 || polls > (1 << 20)) return fail(nullptr, PIC_EINVAL, "polls must be in [1, 2^20]");
+    const cudaError_t e = launch_mlp_wait_test(polls, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, "pic_mlp_wait_test: %s", cudaGetErrorString(e));
     return PIC_OK;
 }
 

@@ -18,7 +18,8 @@
 // partials in a fixed order and applies Adam, so a training step is deterministic.
 //
 // Every wait on the MMA completion barrier is bounded: on timeout the kernel records an error
-// flag (read by pic_mlp_status), frees its TMEM and returns.
+// flag (read by pic_mlp_status), waits once more (bounded) so that a late MMA does not write into
+// TMEM that has been freed, frees its TMEM and returns; that call's outputs are undefined.
 #include <cuda_bf16.h>
 
 #include "pic_internal.cuh"
@@ -70,11 +71,17 @@ __device__ __forceinline__ bool bar_try_wait(unsigned long long* bar, unsigned p
         : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase `parity` of the barrier; false on timeout.
-__device__ __forceinline__ bool bar_wait(unsigned long long* bar, unsigned parity) {
-    for (long long i = 0; i < WAIT_LIMIT; ++i)
+// Bounded wait for the phase `parity` of the barrier; false after `limit` polls.
+__device__ __forceinline__ bool bar_wait(unsigned long long* bar, unsigned parity, long long limit = WAIT_LIMIT) {
+    for (long long i = 0; i < limit; ++i)
         if (bar_try_wait(bar, parity)) return true;
     return false;
+}
+// After a wait gave up: flag it, then wait once more (bounded) so that no committed MMA is
+// still writing when the kernel frees its TMEM; if that wait gives up too the flag says so (2).
+__device__ __forceinline__ void timed_out(unsigned long long* bar, unsigned parity) {
+    const bool late = bar_wait(bar, parity);
+    atomicMax(&g_mlp_err, late ? 1 : 2);
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
@@ -231,9 +238,9 @@ __device__ bool product(MlpSmem& s, const unsigned char* A, const unsigned char*
         mma_commit(&s.bar);
     }
     const bool ok = bar_wait(&s.bar, phase);
+    if (!ok) timed_out(&s.bar, phase);
     phase ^= 1u;
     fence_after();
-    if (!ok) atomicExch(&g_mlp_err, 1);
     return __syncthreads_and(ok);
 }
 
@@ -298,9 +305,9 @@ __device__ bool product2(MlpFwdSmem& s, const unsigned char* A0, const unsigned 
         mma_commit(&s.bar);
     }
     const bool ok = bar_wait(&s.bar, phase);
+    if (!ok) timed_out(&s.bar, phase);
     phase ^= 1u;
     fence_after();
-    if (!ok) atomicExch(&g_mlp_err, 1);
     return __syncthreads_and(ok);
 }
 
@@ -486,13 +493,8 @@ size_t mlp_train_scratch_bytes() { return (size_t)MLP_TRAIN_GRID * (MLP_NPARAM +
 
 cudaError_t launch_mlp_forward(const float* params, const MlpNorm& norm, const float* x, long long ldx, long long n,
                                float* y, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(MlpFwdSmem));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = smem_attr_once((const void*)mlp_forward_kernel, (int)sizeof(MlpFwdSmem));
+    if (e != cudaSuccess) return e;
     if (n <= 0) return cudaSuccess;
     MlpArgs m{params, norm, x, ldx, n, nullptr, y, nullptr};
     const long long tiles = (n + FWD_ROWS - 1) / FWD_ROWS;
@@ -504,18 +506,30 @@ cudaError_t launch_mlp_forward(const float* params, const MlpNorm& norm, const f
 cudaError_t launch_mlp_train(float* params, float* am, float* av, int t, float lr, const MlpNorm& norm,
                              const float* x, long long ldx, const float* target, long long n, float* loss,
                              void* scratch, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(MlpTrainSmem));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = smem_attr_once((const void*)mlp_train_kernel, (int)sizeof(MlpTrainSmem));
+    if (e != cudaSuccess) return e;
     float* part = static_cast<float*>(scratch);
     MlpArgs m{params, norm, x, ldx, n, target, nullptr, part};
     // a fixed grid: CTA c takes tiles c, c + grid, ... so the partials and their sum are fixed
     mlp_train_kernel<<<MLP_TRAIN_GRID, NT, sizeof(MlpTrainSmem), s>>>(m);
     mlp_adam_kernel<<<20, 256, 0, s>>>(params, am, av, part, MLP_TRAIN_GRID, t, lr, 0.9f, 0.999f, 1e-8f, n, loss);
+    return cudaGetLastError();
+}
+
+// Test hook: one CTA waits on a barrier that nothing arrives on (no MMA is issued), gives up
+// after `polls` polls and sets the flag as a timed-out network kernel does.
+__global__ void mlp_wait_test_kernel(long long polls) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !bar_wait(&bar, 0, polls)) atomicMax(&g_mlp_err, 1);
+}
+
+cudaError_t launch_mlp_wait_test(long long polls, cudaStream_t s) {
+    mlp_wait_test_kernel<<<1, 32, 0, s>>>(polls);
     return cudaGetLastError();
 }
 

@@ -253,6 +253,11 @@ cudaError_t launch_mlp_train(float* params, float* am, float* av, int t, float l
                              const float* x, long long ldx, const float* target, long long n, float* loss,
                              void* scratch, cudaStream_t s);
 cudaError_t mlp_status(int* err, bool clear);
+// One CTA waiting on a barrier nothing arrives on, giving up after `polls` polls (test hook).
+cudaError_t launch_mlp_wait_test(long long polls, cudaStream_t s);
+// cudaFuncAttributeMaxDynamicSharedMemorySize of kernel fn, set once per device (the attribute
+// is per device).
+cudaError_t smem_attr_once(const void* fn, int bytes);
 cudaError_t preload_mlp();
 // Per-cell drag factors of run `run` from per-coarse-cell rates nu (bx x by blocks).
 cudaError_t launch_drag_map(const RunDev& host_run, float* map, const float* nu, int bx, int by, double dt,

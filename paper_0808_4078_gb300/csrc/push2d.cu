@@ -31,8 +31,6 @@
 // Shared accumulators are pairs of 32-bit words (value = hi * 4096 + lo) so that all shared
 // atomics are native 32-bit adds; 64-bit shared atomics are several times slower on this GPU.
 // The tile is added to global int64 J with atomics at the end (halos overlap neighbours).
-#include <mutex>
-
 #include "pic_internal.cuh"
 #include "particle_math.cuh"
 
@@ -804,23 +802,6 @@ const Variant kVariants[] = {
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
-// The dynamic shared-memory limit is a per-device attribute of each kernel: set it once per
-// (device, variant).
-std::mutex g_attr_mu;
-unsigned long long g_attr_done[64];   // bit v of entry d: variant v configured on device d
-
-cudaError_t ensure_attr(int v) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_attr_mu);
-    if (g_attr_done[dev] & (1ull << v)) return cudaSuccess;
-    e = cudaFuncSetAttribute(kVariants[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVariants[v].smem);
-    if (e != cudaSuccess) return e;
-    g_attr_done[dev] |= 1ull << v;
-    return cudaSuccess;
-}
 
 }  // namespace
 
@@ -843,7 +824,7 @@ cudaError_t launch_push2d(const Args& a, cudaStream_t s) {
     if (a.nwork == 0) return cudaSuccess;
     const int v = a.push_variant;
     if (v < 0 || v >= kNumVariants || kVariants[v].tx != a.tx || kVariants[v].ty != a.ty) return cudaErrorInvalidValue;
-    cudaError_t e = ensure_attr(v);
+    cudaError_t e = smem_attr_once((const void*)kVariants[v].fn, (int)kVariants[v].smem);
     if (e != cudaSuccess) return e;
     kVariants[v].fn<<<a.nwork, NT, kVariants[v].smem, s>>>(a);
     return cudaGetLastError();

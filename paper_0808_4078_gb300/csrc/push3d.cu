@@ -627,16 +627,9 @@ bool has_push3d() { return true; }
 
 cudaError_t launch_push3d(const Args& a, cudaStream_t s) {
     if (a.nwork == 0) return cudaSuccess;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(push3d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(Smem));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(push3d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)offsetof(Smem, ub));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = smem_attr_once((const void*)push3d_kernel<true>, (int)sizeof(Smem));
+    if (e == cudaSuccess) e = smem_attr_once((const void*)push3d_kernel<false>, (int)offsetof(Smem, ub));
+    if (e != cudaSuccess) return e;
     if (a.anydrag) push3d_kernel<true><<<a.nwork, NT, sizeof(Smem), s>>>(a);
     else push3d_kernel<false><<<a.nwork, NT, offsetof(Smem, ub), s>>>(a);
     return cudaGetLastError();

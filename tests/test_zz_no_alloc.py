@@ -92,3 +92,28 @@ def test_noalloc_rejects_too_many_cells(lib):
     rc = L.pic_bin_cells_noalloc(p, 4, (1 << 20) + 1, p, p, None)
     assert rc == -1
     assert b"PIC_BIN_NOALLOC_MAX_CELLS" in L.pic_last_error(None)
+
+
+def test_noalloc_calls_allocate_nothing(lib):
+    """After a first call (which looks up this device's scratch array), further calls leave the
+    device's free memory unchanged: nothing is allocated on the caller's behalf."""
+    import torch
+    _, L = lib
+    stream = torch.cuda.Stream()
+    rng = np.random.default_rng(12)
+    ncell, n = 1 << 16, 400_000
+    cell = torch.from_numpy(rng.integers(0, ncell, n).astype(np.int32)).cuda()
+    start = torch.empty(ncell + 1, dtype=torch.int32, device="cuda")
+    order = torch.empty(n, dtype=torch.int32, device="cuda")
+    args = (ctypes.c_void_p(cell.data_ptr()), n, ncell, ctypes.c_void_p(start.data_ptr()),
+            ctypes.c_void_p(order.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    torch.cuda.synchronize()
+    assert L.pic_bin_cells_noalloc(*args) == 0
+    stream.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        assert L.pic_bin_cells_noalloc(*args) == 0
+    stream.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert int(start[-1].item()) == n
