@@ -415,6 +415,30 @@ int pic_mlp_train_scratch_bytes(size_t* bytes_out);
 int pic_mlp_train_step(float* params, float* adam_m, float* adam_v, int32_t t, float lr,
                        const pic_mlp_norm* norm, const float* x, int64_t ldx, const float* target,
                        int64_t n, float* loss, void* scratch, size_t scratch_bytes, void* stream);
+/* Input normalisation of the network from its training set: per feature j < nin the mean and
+ * the population standard deviation (FP64 sums in a fixed order) of x[j * ldx + i], i < n,
+ * written to mu_sigma (device float[2 * PIC_MLP_IN]: the 9 means, then the 9 deviations;
+ * features >= nin get 0 and 1, a constant feature a deviation of 1).  Asynchronous on `stream`. */
+int pic_mlp_fit_norm(const float* x, int64_t ldx, int64_t n, int32_t nin, float* mu_sigma, void* stream);
+
+/* Training samples of the closure from a series of moment snapshots -- this library's reading
+ * of the conclusion's conjecture that the two-stream turbulence of a 3D run acts on the return
+ * current like a collision rate, averaged over a time of order 1/w_p.  rows: device
+ * float[nsnap][PIC_MOM_ROWS][nc], consecutive pic_record_moments outputs of one run.  Windows of
+ * `window` consecutive snapshots (nsnap / window of them; a remainder is ignored) are averaged;
+ * for window w and coarse cell c the sample's features are the window means of rows 0..8 and its
+ * label is nu_p + (<Fz_mean> - <Fz_p>) / <uz_p> (nu_p: the background's Krook rate of the run).
+ * A sample is kept where |<uz_p>| >= uz_min (below it the return current has stopped and the
+ * ratio is ill-conditioned) and the label is finite.  Kept samples are written in (window, cell)
+ * order: feat (device float, feature-major, feat[j * cap + i], j < 9), label (device float[cap]);
+ * *n_out (device int64) = the number kept (only the first cap are written).  scratch: device
+ * memory of >= pic_closure_samples_scratch_bytes(nsnap / window * nc) bytes, 16-byte aligned.
+ * PIC_EINVAL on bad sizes or null pointers.  Asynchronous on `stream`. */
+int pic_closure_samples_scratch_bytes(int64_t nsamples, size_t* bytes_out);
+int pic_closure_samples(const float* rows, int32_t nsnap, int64_t nc, int32_t window, float nu_p, float uz_min,
+                        float* feat, float* label, int64_t cap, int64_t* n_out, void* scratch,
+                        size_t scratch_bytes, void* stream);
+
 /* PIC_OK, or PIC_ETIMEOUT if a tensor-core completion wait of the network kernels gave up
  * (sticky until read with clear != 0).  The outputs of a call during which a wait gave up are
  * undefined: a kernel that times out waits once more (also bounded) for the tensor cores before

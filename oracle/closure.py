@@ -106,3 +106,26 @@ def label_from_rows(uz_p, fz_p, fz_mean, nu):
     uz_p = np.asarray(uz_p, dtype=np.float64)
     with np.errstate(invalid="ignore", divide="ignore"):
         return np.where(uz_p != 0, nu + (np.asarray(fz_mean) - np.asarray(fz_p)) / uz_p, 0.0)
+
+
+def samples(rows, window, nu_p, uz_min):
+    """Training samples of the closure from consecutive snapshots rows[nsnap, 12, nc] (FP64):
+    windows of `window` snapshots are averaged; per (window, coarse cell), in that order, the
+    features are the window means of rows 0..8 and the label is
+    nu_p + (<Fz_mean> - <Fz_p>) / <uz_p> (label_from_rows of the window means: the ratio of the
+    time means, not the mean of snapshot ratios); samples with |<uz_p>| < uz_min or a non-finite
+    label are dropped.  Returns (features[9, n], labels[n])."""
+    rows = np.asarray(rows, dtype=np.float64)
+    nsnap, nrow, nc = rows.shape
+    nw = nsnap // window
+    feats, labs = [], []
+    for w in range(nw):
+        m = rows[w * window:(w + 1) * window].mean(axis=0)         # (12, nc)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            lab = nu_p + (m[10] - m[9]) / m[3]
+        keep = (np.abs(m[3]) >= uz_min) & np.isfinite(lab)
+        feats.append(m[:9, keep])
+        labs.append(lab[keep])
+    if not feats:
+        return np.zeros((9, 0)), np.zeros(0)
+    return np.concatenate(feats, axis=1), np.concatenate(labs)

@@ -123,6 +123,11 @@ _SIGNATURES = {
                                           _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP, _VP, ctypes.c_size_t, _VP]),
     "pic_mlp_status": (ctypes.c_int, [ctypes.c_int]),
     "pic_mlp_wait_test": (ctypes.c_int, [ctypes.c_int64, _VP]),
+    "pic_mlp_fit_norm": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _VP, _VP]),
+    "pic_closure_samples_scratch_bytes": (ctypes.c_int, [ctypes.c_int64, _VP]),
+    "pic_closure_samples": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_float,
+                                           ctypes.c_float, _VP, _VP, ctypes.c_int64, _VP, _VP, ctypes.c_size_t,
+                                           _VP]),
     "pic_set_drag_map": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int32, ctypes.c_int32]),
     "pic_set_collisions": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64]),
     "pic_dispersion_growth": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_double,

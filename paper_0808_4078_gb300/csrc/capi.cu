@@ -1118,6 +1118,37 @@ extern "C" int pic_mlp_train_step(float* params, float* adam_m, float* adam_v, i
     return PIC_OK;
 }
 
+extern "C" int pic_mlp_fit_norm(const float* x, int64_t ldx, int64_t n, int32_t nin, float* mu_sigma, void* stream) {
+    if (!x || !mu_sigma) return fail(nullptr, PIC_EINVAL, "pic_mlp_fit_norm: null pointer");
+    if (nin < 1 || nin > PIC_MLP_IN || n < 1 || ldx < n) return fail(nullptr, PIC_EINVAL, "pic_mlp_fit_norm: bad sizes");
+    const cudaError_t e = launch_fit_norm(x, ldx, n, nin, mu_sigma, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, "pic_mlp_fit_norm: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+extern "C" int pic_closure_samples_scratch_bytes(int64_t nsamples, size_t* bytes_out) {
+    if (!bytes_out || nsamples < 0) return fail(nullptr, PIC_EINVAL, "pic_closure_samples_scratch_bytes: bad argument");
+    *bytes_out = closure_samples_scratch_bytes(nsamples);
+    return PIC_OK;
+}
+
+extern "C" int pic_closure_samples(const float* rows, int32_t nsnap, int64_t nc, int32_t window, float nu_p,
+                                   float uz_min, float* feat, float* label, int64_t cap, int64_t* n_out,
+                                   void* scratch, size_t scratch_bytes, void* stream) {
+    if (!rows || !feat || !label || !n_out || !scratch) return fail(nullptr, PIC_EINVAL, "pic_closure_samples: null pointer");
+    if (nsnap < 1 || nc < 1 || window < 1 || window > nsnap || cap < 0)
+        return fail(nullptr, PIC_EINVAL, "pic_closure_samples: bad sizes");
+    if (!(uz_min >= 0.f) || !std::isfinite(nu_p)) return fail(nullptr, PIC_EINVAL, "pic_closure_samples: bad uz_min or nu_p");
+    const long long M = (long long)(nsnap / window) * nc;
+    if (scratch_bytes < closure_samples_scratch_bytes(M) || (reinterpret_cast<uintptr_t>(scratch) & 15))
+        return fail(nullptr, PIC_EINVAL, "pic_closure_samples: scratch too small or misaligned");
+    const cudaError_t e = launch_closure_samples(rows, nsnap, nc, window, nu_p, uz_min, feat, label, cap,
+                                                 reinterpret_cast<long long*>(n_out), scratch,
+                                                 static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, "pic_closure_samples: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
 extern "C" int pic_mlp_wait_test(int64_t polls, void* stream) {
     if (polls < 1 || polls > (1 << 20)) return fail(nullptr, PIC_EINVAL, "polls must be in [1, 2^20]");
     const cudaError_t e = launch_mlp_wait_test(polls, static_cast<cudaStream_t>(stream));

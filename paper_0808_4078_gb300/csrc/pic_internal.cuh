@@ -253,6 +253,12 @@ cudaError_t launch_mlp_train(float* params, float* am, float* av, int t, float l
                              const float* x, long long ldx, const float* target, long long n, float* loss,
                              void* scratch, cudaStream_t s);
 cudaError_t mlp_status(int* err, bool clear);
+// Closure training samples and the network's input normalisation (closure.cu).
+size_t closure_samples_scratch_bytes(long long m);
+cudaError_t launch_closure_samples(const float* rows, int nsnap, long long nc, int window, float nu_p, float uz_min,
+                                   float* feat, float* label, long long cap, long long* n_out, void* scratch,
+                                   cudaStream_t s);
+cudaError_t launch_fit_norm(const float* x, long long ldx, long long n, int nin, float* mu_sigma, cudaStream_t s);
 // One CTA waiting on a barrier nothing arrives on, giving up after `polls` polls (test hook).
 cudaError_t launch_mlp_wait_test(long long polls, cudaStream_t s);
 // cudaFuncAttributeMaxDynamicSharedMemorySize of kernel fn, set once per device (the attribute

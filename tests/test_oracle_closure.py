@@ -125,3 +125,36 @@ def test_label_from_time_means():
     uz = np.array([0.1, 0.1, 0.0])
     lab = closure.label_from_rows(uz, np.array([0.02, 0.0, 1.0]), np.array([0.0, 0.01, 2.0]), 0.5)
     assert np.allclose(lab, [0.5 - 0.2, 0.5 + 0.1, 0.0])
+
+
+def test_samples_average_windows_then_form_the_ratio():
+    """Windows of 2 snapshots; the label is the ratio of the window means (here 0.1 + (2 - 1) / 0.5
+    = 2.1 for window 0, not the mean of the per-snapshot ratios, 2.6); the cell whose mean drift
+    is below uz_min is dropped; order is (window, cell)."""
+    nc = 3
+    rows = np.zeros((5, 12, nc))        # 5 snapshots: 2 windows, the last snapshot unused
+    rows[:, 0] = np.arange(5)[:, None] + np.array([0.0, 10.0, 20.0])   # n_b: window means 0.5, 2.5
+    rows[0, 3], rows[1, 3] = 0.25, 0.75                                 # uz_p: mean 0.5 in window 0
+    rows[2, 3], rows[3, 3] = 1.0, 1.0
+    rows[:, 3, 2] = 1e-4                                                # cell 2: drift stopped
+    rows[:, 9] = 1.0                                                    # Fz_p
+    rows[:, 10] = 2.0                                                   # Fz_mean
+    rows[4] = 99.0                                                      # ignored remainder
+    f, lab = closure.samples(rows, 2, 0.1, 1e-3)
+    assert f.shape == (9, 4) and lab.shape == (4,)
+    assert np.allclose(f[0], [0.5, 10.5, 2.5, 12.5])
+    assert np.allclose(lab[:2], 0.1 + 1.0 / 0.5)
+    assert np.allclose(lab[2:], 0.1 + 1.0 / 1.0)
+    per_snapshot = np.mean([0.1 + 1.0 / 0.25, 0.1 + 1.0 / 0.75])
+    assert abs(per_snapshot - lab[0]) > 0.4
+
+
+def test_samples_of_uniform_krook_rows_recover_the_rate():
+    """Without field fluctuations (Fz_p = Fz_mean) every kept label is the Krook rate itself."""
+    rng = np.random.default_rng(2)
+    rows = rng.normal(size=(8, 12, 16))
+    rows[:, 3] = -0.1 + 0.01 * rng.normal(size=(8, 16))
+    rows[:, 10] = rows[:, 9]
+    f, lab = closure.samples(rows, 4, 0.37, 0.05)
+    assert lab.shape == (32,) and np.allclose(lab, 0.37)
+    assert np.allclose(f[8], rows[:4, 8].mean(0).tolist() + rows[4:, 8].mean(0).tolist())

@@ -163,6 +163,12 @@ COMPONENT_MUTATIONS = {
     "closure_w_es_no_zmean": ("closure.py", "test_oracle_closure.py",
                               "zmean = Ec.mean(axis=0, keepdims=True) if sim.ndim == 3 else Ec",
                               "zmean = 0.0 * Ec"),
+    "closure_samples_mean_of_ratios": ("closure.py", "test_oracle_closure.py",
+                                       "lab = nu_p + (m[10] - m[9]) / m[3]",
+                                       "lab = nu_p + ((rows[w * window:(w + 1) * window, 10] - "
+                                       "rows[w * window:(w + 1) * window, 9]) / rows[w * window:(w + 1) * window, 3]).mean(0)"),
+    "closure_samples_uz_mask": ("closure.py", "test_oracle_closure.py",
+                                "keep = (np.abs(m[3]) >= uz_min) & np.isfinite(lab)", "keep = np.isfinite(lab)"),
     "mlp_dsilu": ("mlp.py", "test_oracle_mlp.py",
                   "return s * (1.0 + z * (1.0 - s))", "return s * (1.0 + z * s)"),
     "mlp_w2_gradient_operand": ("mlp.py", "test_oracle_mlp.py",
