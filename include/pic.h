@@ -102,7 +102,7 @@ typedef struct pic_config {
                                   (not in the paper); the sum is exact in int64 and scaled by
                                   4^-ndim; pic_get_fields returns the unfiltered J; 0 = off */
     int32_t ctas_per_sm;       /* 2D particle kernel: CTAs per SM its registers are budgeted
-                                  for (2 or 3); 0 = default (2); ignored in 3D */
+                                  for (2, 3 or 4); 0 = default (3); ignored in 3D */
 } pic_config;
 
 typedef struct pic_species {

@@ -250,6 +250,7 @@ __global__ void clear_next_kernel(Args a) {
             a.slot[s][nb].icount[c] = 0;
         }
     if (blockIdx.x == 0 && threadIdx.x < a.nspecies) *a.slot[threadIdx.x][nb].sn = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.xo_n) *a.xo_n = 0;
 }
 
 // ------------------------------------------------------------------ standalone counting sort

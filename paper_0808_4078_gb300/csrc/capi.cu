@@ -60,6 +60,8 @@ struct Layout {
     std::vector<size_t> E[3], B[3], J[3], Jlast[3], Jf[3], msum[3], mcnt, ubar[3];   // per run
     std::vector<size_t> dragmap[PIC_NS];                                     // per run
     size_t start, scan_tmp, gate;
+    size_t xq, xo, xo_n;             // 2D crosser queues and their overflow list
+    int xq_cap = 0, xo_cap = 0;
     size_t partials, hist, fit;
 };
 
@@ -81,7 +83,7 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
     g->tz = c->ndim == 3 ? (c->tile_z > 0 ? c->tile_z : dtz) : 1;
     g->push_variant = 0;
     if (c->ndim == 2) {
-        if (c->ctas_per_sm != 0 && c->ctas_per_sm != 2 && c->ctas_per_sm != 3) { *err = "ctas_per_sm must be 0, 2 or 3"; return PIC_EINVAL; }
+        if (c->ctas_per_sm < 0 || c->ctas_per_sm == 1 || c->ctas_per_sm > 4) { *err = "ctas_per_sm must be 0, 2, 3 or 4"; return PIC_EINVAL; }
         g->push_variant = pic::push2d_variant(g->tx, g->ty, c->ctas_per_sm);
         if (g->push_variant < 0) { *err = "2D tiles are 16 x 16, 32 x 8 or 8 x 32"; return PIC_EINVAL; }
     }
@@ -208,6 +210,24 @@ Layout make_layout(const pic_config* c, const Geometry& g) {
     L.start = take(off, 4 * (nc + 1));
     L.scan_tmp = take(off, 4 * (nc / 2048 + 2));
     L.gate = take(off, 4);
+    if (c->ndim == 2) {
+        // crosser queue per tile: an eighth of the densest run's mean particles per tile (a step
+        // moves at most half a cell, so only a fraction of a tile's particles cross an edge);
+        // the excess of denser tiles goes to the overflow list
+        long long per_tile = 0;
+        for (const RunGeo& R : g.runs) {
+            long long np = 0;
+            for (int s = 0; s < PIC_NS; ++s) np += R.capacity[s];
+            if (R.ntiles > 0) per_tile = std::max(per_tile, (np + R.ntiles - 1) / R.ntiles);
+        }
+        L.xq_cap = (int)std::max(256ll, ((per_tile / 8 + 31) / 32) * 32);
+        L.xq = take(off, sizeof(Crosser) * (size_t)L.xq_cap * (size_t)g.nwork);
+        long long tot = 0;
+        for (int s = 0; s < PIC_NS; ++s) tot += g.capacity[s];
+        L.xo_cap = (int)std::min<long long>(std::max(65536ll, tot / 16), (1ll << 31) - 1);
+        L.xo = take(off, sizeof(CrosserX) * (size_t)L.xo_cap);
+        L.xo_n = take(off, 4);
+    }
     L.partials = take(off, sizeof(double) * 8 * g.nwork);
     L.hist = take(off, sizeof(DiagRec) * nruns * (c->diag_interval > 0 ? c->diag_capacity : 1));
     L.fit = take(off, sizeof(double) * 4);
@@ -526,6 +546,11 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
     a.scan_tmp = at<int>(ctx, L.scan_tmp);
     a.start = at<int>(ctx, L.start);
     a.gate = at<int>(ctx, L.gate);
+    a.xq = L.xq_cap ? at<Crosser>(ctx, L.xq) : nullptr;
+    a.xq_cap = L.xq_cap;
+    a.xo = L.xo_cap ? at<CrosserX>(ctx, L.xo) : nullptr;
+    a.xo_n = L.xo_cap ? at<int>(ctx, L.xo_n) : nullptr;
+    a.xo_cap = L.xo_cap;
 
     if (upload_runs(ctx) != PIC_OK) return bail(PIC_ECUDA);
     CKI(cudaStreamSynchronize(ctx->stream));

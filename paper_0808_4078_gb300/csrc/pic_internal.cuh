@@ -134,6 +134,30 @@ struct Args {
     // buffer viewed as flat arrays of stage_n[s] entries: cell, o[ndim], u[3], id.
     char* stage[PIC_NS][2];
     long long stage_n[PIC_NS];
+    // 2D particle kernel: crossers of a cell edge are deposited after a CTA's main loop.  CTA b
+    // queues them in xq + b * xq_cap entries (Crosser); past xq_cap they go to the overflow list
+    // xo (xo_cap entries, fill *xo_n, cleared every step), deposited by the spill kernel.
+    struct Crosser* xq;
+    int xq_cap;
+    struct CrosserX* xo;
+    int* xo_n;
+    int xo_cap;
+};
+
+// A particle that crossed a cell edge, pushed: old and new offsets, u^{n+1/2}, v_z, and a meta
+// word (species bit 0, tile cell bits 1-10, x and y cell steps + 1 bits 11-12 and 13-14, bad
+// bit 15), id.  A bad particle (non-finite push) carries its old state and no steps.
+struct __align__(16) Crosser {
+    float4 o;      // ox, oy, nox, noy
+    float4 u;      // ux, uy, uz, vz
+    int2 m;        // meta, id
+    int2 pad;
+};
+// Overflow entry: the crosser and its old cell (global index).
+struct __align__(16) CrosserX {
+    Crosser c;
+    int cell;
+    int pad[3];
 };
 
 // Flat staging arrays (see Args::stage).
@@ -196,7 +220,7 @@ cudaError_t preload_bins();
 cudaError_t preload_fields();
 cudaError_t launch_push2d(const Args& a, cudaStream_t s);
 // Compiled variants of the 2D particle kernel: index for a tile shape and CTAs per SM (minb 0:
-// the default, 2), or -1; count; shape of variant v.
+// the default, 3), or -1; count; shape of variant v.
 int push2d_variant(int tx, int ty, int minb);
 int push2d_num_variants();
 void push2d_variant_info(int v, int* tx, int* ty, int* minb);

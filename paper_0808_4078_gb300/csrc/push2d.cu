@@ -3,8 +3,8 @@
 // with cell carry, charge-conserving Esirkepov current deposition (CIC) accumulated in int64
 // fixed point, and rebinning of every particle into its new cell's slots of the other buffer.
 //
-// One CTA per (run, tile) of TX x TY = 256 cells (16 x 16, 32 x 8 or 8 x 32), 8 warps, 2 or 3
-// CTAs per SM (the autotuner picks the variant); a warp walks its cells one at a time, each cell's species in order, 32
+// One CTA per (run, tile) of TX x TY = 256 cells (16 x 16, 32 x 8 or 8 x 32), 8 warps, 2, 3 or
+// 4 CTAs per SM (the autotuner picks the variant); a warp walks its cells one at a time, each cell's species in order, 32
 // particles per chunk, with the next chunk's particles loaded into registers while the current
 // one is pushed.
 //
@@ -18,15 +18,18 @@
 // which path a particle took.
 //
 // Particles that stay in their cell (the large majority) add their 8 current terms and 4 drag
-// moments to int32 registers (one warp transpose-reduce per cell puts them in the shared tile)
-// and claim slots of the cell's stay area in the other buffer with one shared-memory atomic per
-// chunk.  Particles that cross a cell edge are queued per warp with their pushed state and
-// deposited 32 at a time with per-lane shared atomics over their 3 x 3 node window; a crosser
-// that stays inside the tile claims a slot in its new cell's stay area through the same shared
-// counter, and only particles leaving the tile (or finding the stay area full) take the
-// destination cell's immigrant area through a global atomic.  The CTA writes its cells' stay
-// counts when all its warps are done.  Every current term is an integer before it is summed, so
-// results do not depend on particle order.
+// moments to int32 registers (warp sums per cell put them in the shared tile) and claim slots of
+// the cell's stay area in the other buffer with one shared-memory atomic per chunk.  Particles
+// that cross a cell edge are queued with their pushed state in the CTA's crosser queue in global
+// memory (L2-resident while the CTA runs); when the main loop is done, all threads deposit them
+// with per-lane shared reductions over their 3 x 3 node window (keeping the deposit out of the
+// main loop keeps its registers within the budget of 3 CTAs per SM); a crosser that stays inside
+// the tile claims a slot in its new cell's stay area through the same shared counter, and only
+// particles leaving the tile (or finding the stay area full) take the destination cell's
+// immigrant area through a global atomic.  Crossers past the queue's capacity go to an overflow
+// list that the spill kernel deposits.  The CTA writes its cells' stay counts when all this is
+// done.  Every current term is an integer before it is summed, so results do not depend on
+// particle order.
 //
 // Shared accumulators are pairs of 32-bit words (value = hi * 4096 + lo) so that all shared
 // atomics are native 32-bit adds; 64-bit shared atomics are several times slower on this GPU.
@@ -38,7 +41,6 @@ namespace pic {
 namespace {
 
 constexpr int NT = 256, NW = NT / 32;
-constexpr int QCAP = 32;                 // queued crossers per warp (a drain empties the queue)
 constexpr int FLUSH_CHUNKS = 8;          // register sums stay below 2^31 (8 x 32 particles)
 constexpr int NTAB = 14;                 // 13 field patches + the drag mean of the warp's cell
 constexpr unsigned FULL = 0xffffffffu;
@@ -54,9 +56,6 @@ template <int TX, int TY>
 struct Smem {
     static constexpr int RN = Geo<TX, TY>::RN, CELLS = Geo<TX, TY>::CELLS;
     float4 T[NW][NTAB];              // per-warp table of the cell being pushed
-    float4 qa[NW][QCAP];             // queued crossers: ox oy nox noy
-    float4 qb[NW][QCAP];             //   ux uy uz vz
-    int2 qc[NW][QCAP];               //   meta (species, cell, carries, bad), id
     double red[NW][6];
     unsigned long long kin[5];
     long long kl[5][NT];             // per-thread kinetic/momentum sums of a diagnostic step
@@ -74,6 +73,7 @@ struct Smem {
     int nn[PIC_NS][CELLS];           // all particles of the tile's cells (current buffer)
     int oc[PIC_NS][CELLS];           // stay-area claims in the other buffer
     int toff[16];                    // region offset of each table patch's first point
+    int nq;                          // crossers queued by this CTA
     SpeciesParams sp[PIC_NS];
     Slots dslot[PIC_NS];             // slot descriptors of the other buffer
     int cap[PIC_NS], cst[PIC_NS], spc[PIC_NS];   // slots per cell, stay area, spill capacity
@@ -270,59 +270,54 @@ __device__ __forceinline__ int qmeta(int s, int ci, int sx, int sy, bool bad) {
     return s | (ci << 1) | ((sx + 1) << 11) | ((sy + 1) << 13) | ((int)bad << 15);
 }
 
-// Deposit and rebin the k queued particles of this warp (one per lane).
+// Deposit and rebin one queued crosser of the tile (the CTA's closing phase; one per thread).
 template <int TX, int TY>
-__device__ __noinline__ void drain(Smem<TX, TY>& sm, const Args& a, const RunConst& K, int k, int lane,
-                                   int warp, int x0, int y0) {
+__device__ __forceinline__ void cross_one(Smem<TX, TY>& sm, const Args& a, const RunConst& K, const Crosser& e,
+                                          int x0, int y0) {
     constexpr int RX = Geo<TX, TY>::RX;
-    if (lane < k) {
-        const float4 qa = sm.qa[warp][lane], qb = sm.qb[warp][lane];
-        const int2 qc = sm.qc[warp][lane];
-        const float ox = qa.x, oy = qa.y, nox = qa.z, noy = qa.w;
-        const float ux = qb.x, uy = qb.y, uz = qb.z, vz = qb.w;
-        const int m = qc.x, id = qc.y;
-        const int s = m & 1, ci = (m >> 1) & 1023, sx = ((m >> 11) & 3) - 1, sy = ((m >> 13) & 3) - 1;
-        const SpeciesParams& P = sm.sp[s];
-        const int lx = ci % TX, ly = ci / TX;
-        const int cx = x0 + lx, cy = y0 + ly;
-        const int nx = K.nx, ny = K.ny;
-        const int g = K.cell_off + cy * nx + cx;
-        const int cap = sm.cap[s], cst = sm.cst[s], spc = sm.spc[s];
-        const Slots& D = sm.dslot[s];
-        if (m & (1 << 15)) {
-            // keep the particle where it was, unmoved; the sticky flag fails the run
-            atomicOr(&a.ctl->err, ERR_BADPART);
-            put_imm(D, cap, cst, spc, g, nox, noy, ux, uy, uz, id, &a.ctl->err);
-        } else {
-            const int ix = lx + 1, iy = ly + 1;
-            const Win wx = window(ox, sx, nox), wy = window(oy, sy, noy);
-            const float zf = __fmul_rn(P.jz, vz);
-            auto add = [&](int c, int ii, int jj, int v) {
-                add_split_pred(&sm.Jlo[c][jj * RX + ii], &sm.Jhi[c][jj * RX + ii], v);
-            };
-            deposit_terms(add, P, ix + wx.off, iy + wy.off, wx, wy, zf);
-            if (P.drag) {
-                const int n1 = (iy + sy) * RX + (ix + sx);
-                add_split_pred(&sm.Mlo[0][n1], &sm.Mhi[0][n1], f2ll_rn(ux * MOM_SCALE));
-                add_split_pred(&sm.Mlo[1][n1], &sm.Mhi[1][n1], f2ll_rn(uy * MOM_SCALE));
-                add_split_pred(&sm.Mlo[2][n1], &sm.Mhi[2][n1], f2ll_rn(uz * MOM_SCALE));
-                atomicAdd(&sm.MC[n1], 1);
-            }
-            const int dlx = lx + sx, dly = ly + sy;
-            if (dlx >= 0 && dlx < TX && dly >= 0 && dly < TY) {
-                const int g1 = g + sy * nx + sx;
-                const int pos = atomicAdd(&sm.oc[s][dly * TX + dlx], 1);
-                if (pos < cst) store_slot(D, g1 * cap + pos, nox, noy, ux, uy, uz, id);
-                else put_imm(D, cap, cst, spc, g1, nox, noy, ux, uy, uz, id, &a.ctl->err);
-            } else {
-                int ncx = cx + sx, ncy = cy + sy;
-                ncx = ncx < 0 ? ncx + nx : (ncx >= nx ? ncx - nx : ncx);
-                ncy = ncy < 0 ? ncy + ny : (ncy >= ny ? ncy - ny : ncy);
-                put_imm(D, cap, cst, spc, K.cell_off + ncy * nx + ncx, nox, noy, ux, uy, uz, id, &a.ctl->err);
-            }
-        }
+    const float ox = e.o.x, oy = e.o.y, nox = e.o.z, noy = e.o.w;
+    const float ux = e.u.x, uy = e.u.y, uz = e.u.z, vz = e.u.w;
+    const int m = e.m.x, id = e.m.y;
+    const int s = m & 1, ci = (m >> 1) & 1023, sx = ((m >> 11) & 3) - 1, sy = ((m >> 13) & 3) - 1;
+    const SpeciesParams& P = sm.sp[s];
+    const int lx = ci % TX, ly = ci / TX;
+    const int cx = x0 + lx, cy = y0 + ly;
+    const int nx = K.nx, ny = K.ny;
+    const int g = K.cell_off + cy * nx + cx;
+    const int cap = sm.cap[s], cst = sm.cst[s], spc = sm.spc[s];
+    const Slots& D = sm.dslot[s];
+    if (m & (1 << 15)) {
+        // keep the particle where it was, unmoved; the sticky flag fails the run
+        atomicOr(&a.ctl->err, ERR_BADPART);
+        put_imm(D, cap, cst, spc, g, nox, noy, ux, uy, uz, id, &a.ctl->err);
+        return;
     }
-    __syncwarp();
+    const int ix = lx + 1, iy = ly + 1;
+    const Win wx = window(ox, sx, nox), wy = window(oy, sy, noy);
+    const float zf = __fmul_rn(P.jz, vz);
+    auto add = [&](int c, int ii, int jj, int v) {
+        add_split_pred(&sm.Jlo[c][jj * RX + ii], &sm.Jhi[c][jj * RX + ii], v);
+    };
+    deposit_terms(add, P, ix + wx.off, iy + wy.off, wx, wy, zf);
+    if (P.drag) {
+        const int n1 = (iy + sy) * RX + (ix + sx);
+        add_split_pred(&sm.Mlo[0][n1], &sm.Mhi[0][n1], f2ll_rn(ux * MOM_SCALE));
+        add_split_pred(&sm.Mlo[1][n1], &sm.Mhi[1][n1], f2ll_rn(uy * MOM_SCALE));
+        add_split_pred(&sm.Mlo[2][n1], &sm.Mhi[2][n1], f2ll_rn(uz * MOM_SCALE));
+        atomicAdd(&sm.MC[n1], 1);
+    }
+    const int dlx = lx + sx, dly = ly + sy;
+    if (dlx >= 0 && dlx < TX && dly >= 0 && dly < TY) {
+        const int g1 = g + sy * nx + sx;
+        const int pos = atomicAdd(&sm.oc[s][dly * TX + dlx], 1);
+        if (pos < cst) store_slot(D, g1 * cap + pos, nox, noy, ux, uy, uz, id);
+        else put_imm(D, cap, cst, spc, g1, nox, noy, ux, uy, uz, id, &a.ctl->err);
+    } else {
+        int ncx = cx + sx, ncy = cy + sy;
+        ncx = ncx < 0 ? ncx + nx : (ncx >= nx ? ncx - nx : ncx);
+        ncy = ncy < 0 ? ncy + ny : (ncy >= ny ? ncy - ny : ncy);
+        put_imm(D, cap, cst, spc, K.cell_off + ncy * nx + ncx, nox, noy, ux, uy, uz, id, &a.ctl->err);
+    }
 }
 
 // Register sums of "stay" particles of the cell at region node n0 -> shared tile: warp sums
@@ -453,6 +448,7 @@ __global__ void __launch_bounds__(NT, MINB) push2d_kernel(const Args a) {
         }
     }
     if (tid < 5) sm.kin[tid] = 0ull;
+    if (tid == 0) sm.nq = 0;
     if (diag)
 #pragma unroll
         for (int k = 0; k < 5; ++k) sm.kl[k][tid] = 0;
@@ -521,7 +517,7 @@ __global__ void __launch_bounds__(NT, MINB) push2d_kernel(const Args a) {
     Seg L = seg_find(sm, warp, 0, nsp, K.cell_off, nx, x0, y0);
     int lj = 0;
     Part nxt = load_part(L, 0, lane, sm.src[L.s], bstride, ids);
-    int cur_ci = -1, n0 = 0, nchunk = 0, qn = 0;
+    int cur_ci = -1, n0 = 0, nchunk = 0;
     const bool cell_drag = anydrag;   // the tile's cells carry drag moments
     int acc[12];
 #pragma unroll
@@ -605,28 +601,40 @@ __global__ void __launch_bounds__(NT, MINB) push2d_kernel(const Args a) {
                              r.uz, p.id, &a.ctl->err);
             }
         }
-        // the others are queued with their pushed state (bad ones with their old state)
+        // the others are queued with their pushed state (bad ones with their old state) in the
+        // CTA's crosser queue in global memory, deposited after the loop
         const bool defer = act && !stay;
         const unsigned dm = __ballot_sync(FULL, defer);
         if (dm) {
-            if (qn + __popc(dm) > QCAP) {
-                drain(sm, a, K, qn, lane, warp, x0, y0);
-                qn = 0;
-            }
+            int qb = 0;
+            if (lane == 0) qb = atomicAdd(&sm.nq, __popc(dm));
+            qb = __shfl_sync(FULL, qb, 0);
             if (defer) {
-                const int k = qn + __popc(dm & lt);
-                sm.qa[warp][k] = make_float4(p.ox, p.oy, r.nox, r.noy);
-                sm.qb[warp][k] = make_float4(r.ux, r.uy, r.uz, r.vz);
-                sm.qc[warp][k] = make_int2(qmeta(s, ci, r.sx, r.sy, false), p.id);
+                Crosser e;
+                e.o = make_float4(p.ox, p.oy, r.nox, r.noy);
+                e.u = make_float4(r.ux, r.uy, r.uz, r.vz);
+                e.m = make_int2(qmeta(s, ci, r.sx, r.sy, false), p.id);
+                e.pad = make_int2(0, 0);
                 if (r.bad) {
                     // rare: kept unmoved with its old state
-                    sm.qa[warp][k] = make_float4(p.ox, p.oy, p.ox, p.oy);
-                    sm.qb[warp][k] = make_float4(p.ux, p.uy, p.uz, r.vz);
-                    sm.qc[warp][k] = make_int2(qmeta(s, ci, 0, 0, true), p.id);
+                    e.o = make_float4(p.ox, p.oy, p.ox, p.oy);
+                    e.u = make_float4(p.ux, p.uy, p.uz, r.vz);
+                    e.m = make_int2(qmeta(s, ci, 0, 0, true), p.id);
+                }
+                const int k = qb + __popc(dm & lt);
+                if (k < a.xq_cap) {
+                    a.xq[(size_t)blockIdx.x * a.xq_cap + k] = e;
+                } else {
+                    // rare: past the CTA's queue, to the overflow list deposited by the spill kernel
+                    const int o = atomicAdd(a.xo_n, 1);
+                    if (o < a.xo_cap) {
+                        a.xo[o].c = e;
+                        a.xo[o].cell = q0 / sm.cap[s];
+                    } else {
+                        atomicOr(&a.ctl->err, ERR_SPILL_FULL);
+                    }
                 }
             }
-            qn += __popc(dm);
-            __syncwarp();
         }
         if (++nchunk == FLUSH_CHUNKS) {
             flush_acc(sm, acc, n0, lane, cell_drag);
@@ -634,7 +642,13 @@ __global__ void __launch_bounds__(NT, MINB) push2d_kernel(const Args a) {
         }
     }
     if (nchunk) flush_acc(sm, acc, n0, lane, cell_drag);
-    if (qn > 0) drain(sm, a, K, qn, lane, warp, x0, y0);
+    // the tile's crossers, one per thread
+    __syncthreads();
+    {
+        const int nq = min(sm.nq, a.xq_cap);
+        const Crosser* q = a.xq + (size_t)blockIdx.x * a.xq_cap;
+        for (int i = tid; i < nq; i += NT) cross_one(sm, a, K, q[i], x0, y0);
+    }
 
     if (diag) {
         // the threads' kinetic and momentum sums: warp sums, then the CTA's
@@ -718,10 +732,61 @@ struct KinCache {
 // ------------------------------------------------------------------ spilled particles
 // Particles that found their cell full: one thread each, global-memory gather and atomics (the
 // same formulas as the tile paths), rebinned into the other buffer.
+__device__ __forceinline__ int run_of_cell(const Args& a, int g) {
+    int lo = 0, hi = a.nruns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.runs[mid].cell_off <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
     const int par = a.ctl->parity;
     const long long step = a.ctl->step;
     const bool diag = a.diag_interval > 0 && (step % a.diag_interval) == 0;
+    // crossers past their CTA's queue (pushed and counted in the diagnostics by the particle
+    // kernel): deposit with global atomics, rebin into the destination's immigrant area
+    const int nxo = a.xo_n ? min(*a.xo_n, a.xo_cap) : 0;
+    for (int k = blockIdx.x * NT + threadIdx.x; k < nxo; k += gridDim.x * NT) {
+        const CrosserX& x = a.xo[k];
+        const int g = x.cell;
+        const RunDev* Rp = &a.runs[run_of_cell(a, g)];
+        const int nx = Rp->nx, ny = Rp->ny;
+        const int m = x.c.m.x, id = x.c.m.y;
+        const int s = m & 1, sx = ((m >> 11) & 3) - 1, sy = ((m >> 13) & 3) - 1;
+        const SpeciesParams P = Rp->sp[s];
+        const Slots D = a.slot[s][par ^ 1];
+        const int cap = a.cap[s], cst = a.cap_stay[s];
+        const float ox = x.c.o.x, oy = x.c.o.y, nox = x.c.o.z, noy = x.c.o.w;
+        const float ux = x.c.u.x, uy = x.c.u.y, uz = x.c.u.z, vz = x.c.u.w;
+        if (m & (1 << 15)) {
+            atomicOr(&a.ctl->err, ERR_BADPART);
+            put_imm(D, cap, cst, a.spill_cap[s], g, nox, noy, ux, uy, uz, id, &a.ctl->err);
+            continue;
+        }
+        const int lc = g - Rp->cell_off;
+        const int cy = lc / nx, cx = lc - cy * nx;
+        const Win wx = window(ox, sx, nox), wy = window(oy, sy, noy);
+        const float zf = __fmul_rn(P.jz, vz);
+        auto add = [&](int c, int i, int j, int v) {
+            if (v != 0)
+                atomicAdd((unsigned long long*)&Rp->J[c][(size_t)wrapi(j, ny) * nx + wrapi(i, nx)],
+                          (unsigned long long)(long long)v);
+        };
+        deposit_terms(add, P, cx + wx.off, cy + wy.off, wx, wy, zf);
+        int ncx = cx + sx, ncy = cy + sy;
+        ncx = ncx < 0 ? ncx + nx : (ncx >= nx ? ncx - nx : ncx);
+        ncy = ncy < 0 ? ncy + ny : (ncy >= ny ? ncy - ny : ncy);
+        const int l1 = ncy * nx + ncx;
+        if (P.drag) {
+            atomicAdd((unsigned long long*)&Rp->msum[0][l1], (unsigned long long)f2ll_rn(ux * MOM_SCALE));
+            atomicAdd((unsigned long long*)&Rp->msum[1][l1], (unsigned long long)f2ll_rn(uy * MOM_SCALE));
+            atomicAdd((unsigned long long*)&Rp->msum[2][l1], (unsigned long long)f2ll_rn(uz * MOM_SCALE));
+            atomicAdd(&Rp->mcnt[l1], 1);
+        }
+        put_imm(D, cap, cst, a.spill_cap[s], Rp->cell_off + l1, nox, noy, ux, uy, uz, id, &a.ctl->err);
+    }
     KinCache kc;
     for (int s = 0; s < a.nspecies; ++s) {
         const Slots S = a.slot[s][par], D = a.slot[s][par ^ 1];
@@ -729,12 +794,7 @@ __global__ void __launch_bounds__(NT) spill2d_kernel(const Args a) {
         const int cap = a.cap[s], cst = a.cap_stay[s];
         for (int k = blockIdx.x * NT + threadIdx.x; k < ns; k += gridDim.x * NT) {
             const int g = S.scell[k];
-            int lo = 0, hi = a.nruns - 1;       // run holding cell g
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (a.runs[mid].cell_off <= g) lo = mid; else hi = mid - 1;
-            }
-            const int run = lo;
+            const int run = run_of_cell(a, g);
             const RunDev* Rp = &a.runs[run];
             const int nx = Rp->nx, ny = Rp->ny;
             const SpeciesParams P = Rp->sp[s];
@@ -796,20 +856,20 @@ constexpr Variant make_variant() {
     return Variant{push2d_kernel<TX, TY, MINB>, TX, TY, MINB, sizeof(Smem<TX, TY>)};
 }
 const Variant kVariants[] = {
-    make_variant<16, 16, 3>(), make_variant<16, 16, 2>(),
-    make_variant<32, 8, 3>(),  make_variant<32, 8, 2>(),
-    make_variant<8, 32, 3>(),  make_variant<8, 32, 2>(),
+    make_variant<16, 16, 3>(), make_variant<16, 16, 2>(), make_variant<16, 16, 4>(),
+    make_variant<32, 8, 3>(),  make_variant<32, 8, 2>(),  make_variant<32, 8, 4>(),
+    make_variant<8, 32, 3>(),  make_variant<8, 32, 2>(),  make_variant<8, 32, 4>(),
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 
 }  // namespace
 
-// Index of the compiled variant for a tile shape and CTAs per SM (minb 0: the default, 2 CTAs
-// per SM with 128 registers: the 3-CTA budget of 80 registers spills), or -1.
+// Index of the compiled variant for a tile shape and CTAs per SM (minb 0: the default, 3 CTAs
+// per SM with 80 registers), or -1.
 int push2d_variant(int tx, int ty, int minb) {
     for (int v = 0; v < kNumVariants; ++v)
-        if (kVariants[v].tx == tx && kVariants[v].ty == ty && kVariants[v].minb == (minb == 0 ? 2 : minb))
+        if (kVariants[v].tx == tx && kVariants[v].ty == ty && kVariants[v].minb == (minb == 0 ? 3 : minb))
             return v;
     return -1;
 }

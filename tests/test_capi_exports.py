@@ -96,11 +96,12 @@ def test_batch_geometry_without_gpu(libpic):
     assert _batch_bytes(cfg, [64, 64, 1], [1, 1])[0] == -1                   # 8 x 16 is not a 2D tile
     for tx, ty in ((32, 8), (8, 32), (16, 16)):
         cfg.tile_x, cfg.tile_y = tx, ty
-        for ctas in (0, 2, 3):
+        for ctas in (0, 2, 3, 4):
             cfg.ctas_per_sm = ctas
             assert _batch_bytes(cfg, [64, 64, 1], [1, 1])[0] == 0, (tx, ty, ctas)
-        cfg.ctas_per_sm = 4
-        assert _batch_bytes(cfg, [64, 64, 1], [1, 1])[0] == -1               # no 4-CTA variant
+        for ctas in (1, 5):
+            cfg.ctas_per_sm = ctas
+            assert _batch_bytes(cfg, [64, 64, 1], [1, 1])[0] == -1           # no such variant
     cfg.ctas_per_sm = 0
     cfg.tile_x, cfg.tile_y = 32, 8
     assert _batch_bytes(cfg, [48, 64, 1], [1, 1])[0] == -1                   # 48 not a multiple of 32

@@ -1,5 +1,5 @@
-"""Every compiled variant of the 2D particle kernel (tile shape 16 x 16, 32 x 8, 8 x 32; 2 or 3
-CTAs per SM) computes the same step: after 25 steps of a warm-beam Krook run with particles
+"""Every compiled variant of the 2D particle kernel (tile shape 16 x 16, 32 x 8, 8 x 32; 2, 3 or
+4 CTAs per SM) computes the same step: after 25 steps of a warm-beam Krook run with particles
 crossing tile edges, the particles (by id), E, B and the last step's J are bitwise equal to the
 default variant's, and the first of them matches the FP64 oracle."""
 import numpy as np
@@ -9,7 +9,8 @@ import pic_inputs as pi
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [((16, 16), 2), ((16, 16), 3), ((32, 8), 2), ((32, 8), 3), ((8, 32), 2), ((8, 32), 3)]
+VARIANTS = [((16, 16), 3), ((16, 16), 2), ((16, 16), 4), ((32, 8), 2), ((32, 8), 3), ((32, 8), 4),
+            ((8, 32), 2), ((8, 32), 3), ((8, 32), 4)]
 
 
 @pytest.fixture(scope="module")
