@@ -4,7 +4,8 @@ Workload (default): 1024 x 1024 cells, 64 particles per cell per species (134,21
 particles), gamma = 3 beam (nb = 0.1) with T_perp = 0.1, background T = 0.001 with Krook
 nu = 0.1, dx = 0.1, dt = 0.05; synthetic seeded load.  A step is the whole hot path: fused
 gather/Boris/drag/move/Esirkepov deposit, Yee update, step finalisation, and the counting sort
-every 8 steps.
+every 8 steps.  Before the timed region the autotuner times every variant of the 2D particle
+kernel on the run (config.tile reports its pick; --no-autotune or --tile/--ctas skip it).
 
   value     particle-steps/s with the particles resident in HBM (CUDA events on the engine
             stream, after warm-up; particle data >> L2, so no flush is needed)
@@ -376,6 +377,10 @@ def run_ours(args, rank, world, local_rank):
     d2h = len(recs) * 128
     del host
 
+    # ---------------- autotuner (its steps are steps of the run, outside the timed region)
+    tune = None
+    if wl.ndim == 2 and tuple(args.tile) == (0, 0) and args.ctas == 0 and not args.no_autotune:
+        tune = eng.autotune(16)
     # ---------------- device-resident timing
     ms, launches, delta, clocks = _timed_steps(eng, args.steps, args.warmup, barrier, local_rank)
     phase = {k: v[1] / max(1, args.steps) for k, v in delta.items()}
@@ -394,7 +399,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": wl.name, "grid": grid, "ppc_per_species": args.ppc,
                        "particles_per_gpu": npart, "sort_interval": args.sort,
                        "diag_interval": args.diag, "parallelism": f"replicas{world}",
-                       "j_filter": args.j_filter,
+                       "j_filter": args.j_filter, "tile": list(eng.tile_config()),
                        "l2": f"inputs larger than L2 (particles {npart * (bpp // 2) / 1e9:.1f} GB/GPU), no flush"},
             "roofline": _roofline(alg_bytes, *delta["push_deposit"], ndim=wl.ndim, npart=npart),
             "phase_ms_per_step": phase,
@@ -403,6 +408,8 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": launches,
             "clocks": clocks,
         }
+        if tune is not None:
+            line["autotune"] = [{"tile": [t[0], t[1]], "ctas_per_sm": t[2], "ms_per_step": t[3]} for t in tune]
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)
@@ -836,6 +843,8 @@ def main():
     ap.add_argument("--tile", type=lambda t: tuple(int(x) for x in t.split("x")), default=(0, 0),
                     help="2D particle-kernel tile, e.g. 32x8 (0x0 = default)")
     ap.add_argument("--ctas", type=int, default=0, help="2D particle kernel: CTAs per SM (2, 3 or 4; 0 = default)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="2D: keep the default kernel variant instead of timing them all first")
     ap.add_argument("--diag", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-run", action="store_true", help="scan: skip the per-run baseline")

@@ -479,6 +479,31 @@ int pic_bin_cells(const int32_t* cell, int64_t n, int32_t ncell, int32_t* start,
 int pic_bin_cells_noalloc(const int32_t* cell, int64_t n, int32_t ncell, int32_t* start,
                           int32_t* order, void* stream);
 
+/* Autotuner of the 2D particle kernel's compiled variants (tile shape 16 x 16, 32 x 8 or 8 x 32
+ * cells; 2, 3 or 4 CTAs per SM; every one computes the same bits).  The next steps of the run
+ * are taken with each variant whose tile divides every run's grid in turn: sort_interval steps to
+ * warm up (graph capture), then steps_per_variant (rounded up to a multiple of sort_interval)
+ * timed with CUDA events on the context's stream; the run stays exactly what it would have been
+ * with any one variant.  The fastest variant is kept for the rest of the run and recorded in the
+ * tuning cache under the key (dimension, grids, particles per run, GPU name): in memory and, if
+ * a cache file is set (pic_tune_cache_set, or the environment variable PIC_TUNE_CACHE), in that
+ * file (one JSON object per line, rewritten through path.tmp and a rename).  A context
+ * created with tile_x = tile_y = ctas_per_sm = 0 whose key is cached starts with the cached
+ * variant.  out (host, may be NULL when max_entries is 0) receives one entry per variant timed
+ * (up to max_entries; *n_out the number written).  In 3D (one kernel) the step is timed and
+ * nothing is chosen.  Synchronises. */
+typedef struct pic_tune_entry {
+    int32_t tile_x, tile_y, ctas_per_sm;   /* ctas_per_sm: tile_z in 3D */
+    float ms_per_step;
+} pic_tune_entry;
+int pic_autotune(pic_ctx* ctx, int steps_per_variant, pic_tune_entry* out, int max_entries, int* n_out);
+/* Set the tuning-cache file (NULL: memory only) and load its entries; replaces the in-memory
+ * cache.  PIC_OK. */
+int pic_tune_cache_set(const char* path);
+/* The particle kernel's configuration: out3 = {tile_x, tile_y, ctas_per_sm} in 2D,
+ * {tile_x, tile_y, tile_z} in 3D. */
+int pic_tile_config(const pic_ctx* ctx, int32_t* out3);
+
 /* Kernel launches issued so far by this context (graph replays count their kernel nodes). */
 int64_t pic_launch_count(const pic_ctx* ctx);
 

@@ -42,6 +42,16 @@ class Config(ctypes.Structure):
                 ("j_filter", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("ms_per_step", ctypes.c_float)]
+
+
+def set_tune_cache(path):
+    """Tuning-cache file of the autotuner (pic_tune_cache_set); None: memory only."""
+    _check(lib().pic_tune_cache_set(None if path is None else os.fsencode(path)))
+
+
 class Species(ctypes.Structure):
     _fields_ = [("q", ctypes.c_double), ("m", ctypes.c_double), ("w", ctypes.c_double),
                 ("nu", ctypes.c_double)]
@@ -123,6 +133,9 @@ _SIGNATURES = {
                                           _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP, _VP, ctypes.c_size_t, _VP]),
     "pic_mlp_status": (ctypes.c_int, [ctypes.c_int]),
     "pic_mlp_wait_test": (ctypes.c_int, [ctypes.c_int64, _VP]),
+    "pic_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP]),
+    "pic_tune_cache_set": (ctypes.c_int, [ctypes.c_char_p]),
+    "pic_tile_config": (ctypes.c_int, [_VP, _VP]),
     "pic_mlp_fit_norm": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _VP, _VP]),
     "pic_closure_samples_scratch_bytes": (ctypes.c_int, [ctypes.c_int64, _VP]),
     "pic_closure_samples": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_float,
@@ -268,6 +281,21 @@ class Engine:
 
     def sync(self):
         _check(lib().pic_sync(self._ctx), self._ctx)
+
+    def autotune(self, steps_per_variant=16):
+        """Time every compiled variant of the particle kernel on the next steps of this run and
+        keep the fastest (pic_autotune); returns [(tile_x, tile_y, ctas_per_sm, ms_per_step)]."""
+        buf = (TuneEntry * 16)()
+        n = ctypes.c_int(0)
+        _check(lib().pic_autotune(self._ctx, int(steps_per_variant), ctypes.cast(buf, _VP), 16,
+                                  ctypes.byref(n)), self._ctx)
+        return [(e.tile_x, e.tile_y, e.ctas_per_sm, e.ms_per_step) for e in buf[:n.value]]
+
+    def tile_config(self):
+        """(tile_x, tile_y, ctas_per_sm) of the particle kernel ((tile_x, tile_y, tile_z) in 3D)."""
+        out = (ctypes.c_int32 * 3)()
+        _check(lib().pic_tile_config(self._ctx, ctypes.cast(out, _VP)), self._ctx)
+        return tuple(out)
 
     def clear_flags(self):
         """Sticky device error bits (PIC_FLAG_BIT_*), cleared."""

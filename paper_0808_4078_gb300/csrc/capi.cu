@@ -11,6 +11,8 @@
 #include <cstdio>
 #include <cstddef>
 #include <cstring>
+#include <cstdlib>
+#include <map>
 #include <mutex>
 #include <new>
 #include <set>
@@ -264,7 +266,14 @@ struct pic_ctx {
     std::vector<cudaEvent_t> pool;
     double phase_ms[PH_N] = {0, 0, 0, 0};
     long long phase_n[PH_N] = {0, 0, 0, 0};
+    std::string tune_key;               // workload and GPU key of the tuning cache
 };
+
+namespace {
+std::string tune_key(const pic_config& c, int nruns, const int32_t* dims, const int64_t* caps);
+}
+int switch_variant(pic_ctx* ctx, int v);
+void apply_cached_variant(pic_ctx* ctx);
 
 namespace {
 
@@ -553,6 +562,8 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
     a.xo_cap = L.xo_cap;
 
     if (upload_runs(ctx) != PIC_OK) return bail(PIC_ECUDA);
+    ctx->tune_key = tune_key(c, nruns, dims, caps);
+    apply_cached_variant(ctx);
     CKI(cudaStreamSynchronize(ctx->stream));
 #undef CKI
     *out = ctx;
@@ -1189,6 +1200,247 @@ extern "C" int pic_mlp_status(int clear) {
     return PIC_OK;
 }
 
+// ============================================================== autotuner
+//
+// The compiled variants of the 2D particle kernel (tile shape 16 x 16, 32 x 8, 8 x 32; 2, 3 or
+// 4 CTAs per SM) compute the same bits; which is fastest depends on the workload and the GPU.
+// pic_autotune times each on the running context and keeps the fastest; picks are kept per key
+// (dimension, grids, particles, GPU name) in memory and in a JSON file (PIC_TUNE_CACHE or
+// pic_tune_cache_set), one object per line:
+//   {"key": "...", "tile_x": 16, "tile_y": 16, "ctas_per_sm": 4, "ms_per_step": 2.70}
+// A context created with tile_x = tile_y = ctas_per_sm = 0 starts with the cached pick.
+namespace {
+
+struct TunePick {
+    int tx, ty, ctas;
+    double ms;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TunePick> g_tune;
+std::string g_tune_path;
+bool g_tune_loaded = false;
+
+std::string json_str_field(const std::string& line, const char* name) {
+    const std::string k = std::string("\"") + name + "\"";
+    size_t p = line.find(k);
+    if (p == std::string::npos) return "";
+    p = line.find('"', line.find(':', p + k.size()) + 1);
+    if (p == std::string::npos) return "";
+    const size_t q = line.find('"', p + 1);
+    return q == std::string::npos ? "" : line.substr(p + 1, q - p - 1);
+}
+double json_num_field(const std::string& line, const char* name, bool* ok) {
+    const std::string k = std::string("\"") + name + "\"";
+    size_t p = line.find(k);
+    if (p == std::string::npos) { *ok = false; return 0; }
+    p = line.find(':', p + k.size());
+    if (p == std::string::npos) { *ok = false; return 0; }
+    char* end = nullptr;
+    const double v = std::strtod(line.c_str() + p + 1, &end);
+    if (end == line.c_str() + p + 1) *ok = false;
+    return v;
+}
+
+// Caller holds g_tune_mu.
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    if (g_tune_path.empty()) {
+        const char* env = std::getenv("PIC_TUNE_CACHE");
+        if (env) g_tune_path = env;
+    }
+    if (g_tune_path.empty()) return;
+    std::FILE* f = std::fopen(g_tune_path.c_str(), "r");
+    if (!f) return;
+    char buf[1024];
+    while (std::fgets(buf, sizeof buf, f)) {
+        const std::string line(buf);
+        const std::string key = json_str_field(line, "key");
+        bool ok = true;
+        TunePick t;
+        t.tx = (int)json_num_field(line, "tile_x", &ok);
+        t.ty = (int)json_num_field(line, "tile_y", &ok);
+        t.ctas = (int)json_num_field(line, "ctas_per_sm", &ok);
+        t.ms = json_num_field(line, "ms_per_step", &ok);
+        if (ok && !key.empty() && pic::push2d_variant(t.tx, t.ty, t.ctas) >= 0) g_tune[key] = t;
+    }
+    std::fclose(f);
+}
+
+// Caller holds g_tune_mu.  Written to path.tmp and renamed.
+int tune_save_locked() {
+    if (g_tune_path.empty()) return PIC_OK;
+    const std::string tmp = g_tune_path + ".tmp";
+    std::FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return PIC_EINVAL;
+    for (const auto& kv : g_tune)
+        std::fprintf(f, "{\"key\": \"%s\", \"tile_x\": %d, \"tile_y\": %d, \"ctas_per_sm\": %d, \"ms_per_step\": %.6f}\n",
+                     kv.first.c_str(), kv.second.tx, kv.second.ty, kv.second.ctas, kv.second.ms);
+    const bool bad = std::fclose(f) != 0;
+    if (bad || std::rename(tmp.c_str(), g_tune_path.c_str()) != 0) return PIC_EINVAL;
+    return PIC_OK;
+}
+
+// Workload key: dimension, grids and particles per run (an FNV-1a hash of them for more than
+// four runs), and the GPU's name.
+std::string tune_key(const pic_config& c, int nruns, const int32_t* dims, const int64_t* caps) {
+    int dev = 0;
+    cudaDeviceProp prop;
+    std::string gpu = "unknown";
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) gpu = prop.name;
+    std::string k = "ndim=" + std::to_string(c.ndim) + ";runs=" + std::to_string(nruns) + ";";
+    if (nruns <= 4) {
+        for (int r = 0; r < nruns; ++r) {
+            k += std::to_string(dims[3 * r]) + "x" + std::to_string(dims[3 * r + 1]);
+            if (c.ndim == 3) k += "x" + std::to_string(dims[3 * r + 2]);
+            k += ":";
+            for (int s = 0; s < c.nspecies; ++s) k += std::to_string(caps[PIC_NS * r + s]) + (s + 1 < c.nspecies ? "+" : ";");
+        }
+    } else {
+        unsigned long long h = 1469598103934665603ull;
+        auto mix = [&](long long v) {
+            for (int b = 0; b < 8; ++b) { h ^= (unsigned long long)((v >> (8 * b)) & 255); h *= 1099511628211ull; }
+        };
+        for (int r = 0; r < nruns; ++r) {
+            for (int d = 0; d < 3; ++d) mix(dims[3 * r + d]);
+            for (int s = 0; s < c.nspecies; ++s) mix(caps[PIC_NS * r + s]);
+        }
+        char hb[32];
+        std::snprintf(hb, sizeof hb, "%016llx", h);
+        k += std::string("batch=") + hb + ";";
+    }
+    for (char& ch : gpu) if (ch == '"' || ch == '\\') ch = '_';
+    return k + "gpu=" + gpu;
+}
+
+}  // namespace
+
+// Switch the 2D particle kernel (and the tiled field kernels) to variant v; the tile count per
+// run is the same for every shape (256 cells per tile), so only the tile grid changes.
+int switch_variant(pic_ctx* ctx, int v) {
+    int tx, ty, mb;
+    push2d_variant_info(v, &tx, &ty, &mb);
+    for (const RunGeo& G : ctx->geo.runs)
+        if (G.nx % tx || G.ny % ty) return fail(ctx, PIC_EINVAL, "tile %d x %d does not divide a %d x %d grid", tx, ty, G.nx, G.ny);
+    ctx->geo.tx = tx;
+    ctx->geo.ty = ty;
+    ctx->geo.push_variant = v;
+    for (int r = 0; r < ctx->nruns; ++r) {
+        RunGeo& G = ctx->geo.runs[r];
+        G.ntx = G.nx / tx;
+        G.nty = G.ny / ty;
+        ctx->runs[r].ntx = G.ntx;
+        ctx->runs[r].nty = G.nty;
+    }
+    ctx->args.tx = tx;
+    ctx->args.ty = ty;
+    ctx->args.push_variant = v;
+    return upload_runs(ctx);
+}
+
+// The cached pick for a new context configured with default tiles (2D), if any.
+void apply_cached_variant(pic_ctx* ctx) {
+    const pic_config& c = ctx->cfg;
+    if (c.ndim != 2 || c.tile_x || c.tile_y || c.ctas_per_sm) return;
+    TunePick t{};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        auto it = g_tune.find(ctx->tune_key);
+        if (it == g_tune.end()) return;
+        t = it->second;
+    }
+    const int v = push2d_variant(t.tx, t.ty, t.ctas);
+    if (v >= 0 && v != ctx->geo.push_variant) switch_variant(ctx, v);
+}
+
+extern "C" int pic_tune_cache_set(const char* path) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+    g_tune_loaded = false;
+    g_tune_path = path ? path : "";
+    tune_load_locked();
+    return PIC_OK;
+}
+
+extern "C" int pic_tile_config(const pic_ctx* ctx, int32_t* out3) {
+    if (!ctx || !out3) return fail(nullptr, PIC_EINVAL, "null argument");
+    int tx, ty, mb;
+    if (ctx->cfg.ndim == 2) {
+        push2d_variant_info(ctx->geo.push_variant, &tx, &ty, &mb);
+    } else {
+        tx = ctx->geo.tx; ty = ctx->geo.ty; mb = 0;
+    }
+    out3[0] = tx; out3[1] = ty; out3[2] = ctx->cfg.ndim == 2 ? mb : ctx->geo.tz;
+    return PIC_OK;
+}
+
+extern "C" int pic_autotune(pic_ctx* ctx, int steps_per_variant, pic_tune_entry* out, int max_entries, int* n_out) {
+    if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+    if (steps_per_variant < 1) return fail(ctx, PIC_EINVAL, "steps_per_variant must be >= 1");
+    if (max_entries > 0 && !out) return fail(ctx, PIC_EINVAL, "null output");
+    int rc = pic_sync(ctx);
+    if (rc) return rc;
+    const int K = ctx->sort_interval;
+    const int steps = ((steps_per_variant + K - 1) / K) * K;
+    std::vector<int> cand;
+    if (ctx->cfg.ndim == 2) {
+        for (int v = 0; v < push2d_num_variants(); ++v) {
+            int tx, ty, mb;
+            push2d_variant_info(v, &tx, &ty, &mb);
+            bool fits = true;
+            for (const RunGeo& G : ctx->geo.runs) fits = fits && G.nx % tx == 0 && G.ny % ty == 0;
+            if (fits) cand.push_back(v);
+        }
+    } else {
+        cand.push_back(-1);      // one 3D kernel: timed, nothing to choose
+    }
+    cudaEvent_t e0 = get_event(ctx), e1 = get_event(ctx);
+    int best = -1, n = 0;
+    double best_ms = 0;
+    for (int v : cand) {
+        if (v >= 0) {
+            rc = switch_variant(ctx, v);
+            if (rc) break;
+        }
+        rc = pic_step(ctx, K);            // warm-up: graph capture of the new variant
+        if (rc) break;
+        CK(cudaEventRecord(e0, ctx->stream));
+        rc = pic_step(ctx, steps);
+        if (rc) break;
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        const double per = ms / steps;
+        int32_t cfg3[3];
+        pic_tile_config(ctx, cfg3);
+        if (n < max_entries) {
+            out[n].tile_x = cfg3[0];
+            out[n].tile_y = cfg3[1];
+            out[n].ctas_per_sm = cfg3[2];
+            out[n].ms_per_step = (float)per;
+        }
+        ++n;
+        if (best < 0 || per < best_ms) { best = v; best_ms = per; }
+    }
+    ctx->pool.push_back(e0);
+    ctx->pool.push_back(e1);
+    if (rc) return rc;
+    if (n_out) *n_out = std::min(n, std::max(max_entries, 0));
+    if (best >= 0) {
+        rc = switch_variant(ctx, best);
+        if (rc) return rc;
+        int tx, ty, mb;
+        push2d_variant_info(best, &tx, &ty, &mb);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        g_tune[ctx->tune_key] = TunePick{tx, ty, mb, best_ms};
+        if (tune_save_locked() != PIC_OK) return fail(ctx, PIC_EINVAL, "cannot write the tuning cache %s", g_tune_path.c_str());
+    }
+    return pic_sync(ctx);
+}
+
 // ============================================================== checkpoint / restore
 //
 // File layout (little-endian, this library's struct layouts, checked by size fields):
@@ -1206,7 +1458,7 @@ struct CkptHeader {
     char magic[8];
     uint32_t version, header_bytes, rungeo_bytes, runstate_bytes, species_bytes, ctl_bytes;
     int32_t ndim, nspecies, nruns, track_ids, keep_j, j_filter;
-    int32_t diag_interval, diag_capacity, sort_interval, tiles;   // tiles: tx | ty << 8 | tz << 16
+    int32_t diag_interval, diag_capacity, sort_interval, reserved;
     int32_t cap[PIC_NS], cap_stay[PIC_NS], spill_cap[PIC_NS];
     double dx, dy, dz, dt;
     uint64_t layout_total;
@@ -1251,7 +1503,6 @@ CkptHeader ckpt_header(const pic_ctx* ctx) {
     h.diag_interval = c.diag_interval;
     h.diag_capacity = c.diag_interval > 0 ? c.diag_capacity : 0;
     h.sort_interval = ctx->sort_interval;
-    h.tiles = ctx->geo.tx | (ctx->geo.ty << 8) | (ctx->geo.tz << 16);
     for (int s = 0; s < PIC_NS; ++s) {
         h.cap[s] = ctx->geo.cap[s];
         h.cap_stay[s] = ctx->geo.cap_stay[s];

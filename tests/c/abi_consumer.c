@@ -18,6 +18,8 @@ int main(void) {
     F(pic_config, sort_interval); F(pic_config, diag_interval); F(pic_config, diag_capacity);
     F(pic_config, track_ids); F(pic_config, flags); F(pic_config, tile_x); F(pic_config, tile_y);
     F(pic_config, tile_z); F(pic_config, j_filter); F(pic_config, ctas_per_sm);
+    S(pic_tune_entry); F(pic_tune_entry, tile_x); F(pic_tune_entry, tile_y); F(pic_tune_entry, ctas_per_sm);
+    F(pic_tune_entry, ms_per_step);
     S(pic_species);
     F(pic_species, q); F(pic_species, m); F(pic_species, w); F(pic_species, nu);
     S(pic_diag_rec);

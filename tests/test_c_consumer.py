@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 MIRRORS = {"pic_config": "Config", "pic_species": "Species", "pic_diag_rec": "DiagRec",
            "pic_stats": "Stats", "pic_kernel_time": "KernelTime",
-           "pic_hybrid_config": "HybridConfig", "pic_mlp_norm": "MlpNorm"}
+           "pic_hybrid_config": "HybridConfig", "pic_mlp_norm": "MlpNorm", "pic_tune_entry": "TuneEntry"}
 
 
 @pytest.fixture(scope="module")
