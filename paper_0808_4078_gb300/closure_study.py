@@ -145,21 +145,43 @@ def errors(s, ref):
     return dict(gamma_rel=eg, level_log=el)
 
 
-def run_study(nx, ny, nz, ppc, steps, every=4, window=5, bx=4, by=4, j_filter=1, train_steps=2000,
-              lr=1e-3, uz_min_frac=0.25, seed3=3, seed2=5, T_perp=0.2, const_nu=CONST_NU, log=None):
-    """The whole study at one size; returns a JSON-able dict."""
+def _load(big, **kw):
+    """A seeded Weibel load: drawn in parallel into shared memory for large grids."""
     import pic_inputs as pi
-    out = dict(config=dict(nx=nx, ny=ny, nz=nz, ppc=ppc, steps=steps, every=every, window=window, bx=bx, by=by,
-                           j_filter=j_filter, train_steps=train_steps, lr=lr, T_perp=T_perp, dx=0.1, dt=0.05))
+    if big:
+        L = pi.weibel_load_parallel(workers=16, **kw)
+        return L.workload, L
+    return pi.weibel_load(**kw), None
+
+
+def run_study(nx, ny, nz, ppc, steps, every=4, window=5, bx=4, by=4, j_filter=1, train_steps=2000,
+              lr=1e-3, uz_min_frac=0.25, seed3=3, seed2=5, T_perp=0.2, const_nu=CONST_NU, log=None,
+              nx2=None, ny2=None, ppc2=None):
+    """The whole study at one size (the 2D runs on nx2 x ny2 cells with ppc2 particles per cell
+    and species, by default the 3D run's transverse grid and ppc); returns a JSON-able dict."""
+    import torch
+    nx2, ny2, ppc2 = nx2 or nx, ny2 or ny, ppc2 or ppc
+    out = dict(config=dict(nx=nx, ny=ny, nz=nz, ppc=ppc, nx2=nx2, ny2=ny2, ppc2=ppc2, steps=steps, every=every,
+                           window=window, bx=bx, by=by, j_filter=j_filter, train_steps=train_steps, lr=lr,
+                           T_perp=T_perp, dx=0.1, dt=0.05))
     t0 = time.time()
-    wl3 = pi.weibel_load(ndim=3, nx=nx, ny=ny, nz=nz, ppc=ppc, T_perp_beam=T_perp, seed=seed3)
+    wl3, L3 = _load(nx * ny * nz * ppc > (1 << 26), ndim=3, nx=nx, ny=ny, nz=nz, ppc=ppc, T_perp_beam=T_perp,
+                    seed=seed3)
     uz_p0 = float(np.mean(wl3.species[1].u[2]))
     eng3 = Engine.from_workload(wl3, diag_interval=1, diag_capacity=steps + 8, sort_interval=8, j_filter=j_filter)
+    del wl3
+    if L3 is not None:
+        L3.close()
+    t3 = time.time()
     rows = record(eng3, steps, every, bx, by)
+    eng3.sync()
     vol3 = nx * ny * nz * 0.1 ** 3
     out["run3d"] = summary(eng3, vol3)
     out["run3d"]["stats"] = eng3.stats()
+    out["run3d"]["wall_s"] = time.time() - t3
     eng3.close()
+    del eng3
+    torch.cuda.empty_cache()
     feat, label = training_set(rows, window, 0.0, uz_min_frac * abs(uz_p0))
     lab = label.double().cpu().numpy()
     out["samples"] = dict(n=int(lab.size), of=int((rows.shape[0] // window) * rows.shape[2]),
@@ -175,12 +197,15 @@ def run_study(nx, ny, nz, ppc, steps, every=4, window=5, bx=4, by=4, j_filter=1,
         pred = net.forward(feat).double().cpu().numpy()
         out[f"train{nin}"] = dict(losses=losses, r2=float(1 - np.mean((pred - lab) ** 2) / lab.var()))
         nets[nin] = net
-    vol2 = nx * ny * 0.1 ** 2
+    vol2 = nx2 * ny2 * 0.1 ** 2
     ref = out["run3d"]
+    wl2, L2 = _load(nx2 * ny2 * ppc2 > (1 << 24), ndim=2, nx=nx2, ny=ny2, ppc=ppc2, T_perp_beam=T_perp, seed=seed2)
 
     def run2d(nu, net=None):
-        wl2 = pi.weibel_load(ndim=2, nx=nx, ny=ny, ppc=ppc, T_perp_beam=T_perp, nu=nu, seed=seed2)
-        eng = Engine.from_workload(wl2, diag_interval=1, diag_capacity=steps + 8, sort_interval=8, j_filter=j_filter)
+        eng = Engine(2, nx2, ny2, dx=wl2.dx, dt=wl2.dt, capacity=[sp.n for sp in wl2.species],
+                     diag_interval=1, diag_capacity=steps + 8, sort_interval=8, j_filter=j_filter)
+        for i, sp in enumerate(wl2.species):
+            eng.load_species(i, sp.q, sp.m, sp.w, nu if i == 1 else sp.nu, sp.cell, sp.offset, sp.u)
         rates = None
         if net is None:
             eng.step(steps)
@@ -188,6 +213,8 @@ def run_study(nx, ny, nz, ppc, steps, every=4, window=5, bx=4, by=4, j_filter=1,
             rates = drive(eng, net, steps, every, bx, by)
         s = summary(eng, vol2)
         eng.close()
+        del eng
+        torch.cuda.empty_cache()
         s.update(errors(s, ref))
         if rates is not None:
             s["mean_rate"] = float(np.mean(rates))
@@ -197,6 +224,8 @@ def run_study(nx, ny, nz, ppc, steps, every=4, window=5, bx=4, by=4, j_filter=1,
     out["run2d_const"] = {str(nu): run2d(nu) for nu in const_nu}
     for nin in (9, 8):
         out[f"run2d_net{nin}"] = run2d(0.0, nets[nin])
+    if L2 is not None:
+        L2.close()
     best_l = min(out["run2d_const"].items(), key=lambda kv: kv[1]["level_log"])
     best_g = min(out["run2d_const"].items(), key=lambda kv: kv[1]["gamma_rel"])
     out["best_const_level"] = dict(nu=float(best_l[0]), **errors(best_l[1], ref))
@@ -214,10 +243,12 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--bx", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--nx2", type=int, default=None, help="2D grid side (default: the 3D transverse grid)")
+    ap.add_argument("--ppc2", type=int, default=None, help="2D particles per cell and species")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     res = run_study(a.nx, a.ny, a.nz, a.ppc, a.steps, bx=a.bx, by=a.bx, train_steps=a.train_steps,
-                    log=lambda m: print(m, flush=True))
+                    log=lambda m: print(m, flush=True), nx2=a.nx2, ny2=a.nx2, ppc2=a.ppc2)
     s = json.dumps(res)
     if a.out:
         with open(a.out, "w") as f:

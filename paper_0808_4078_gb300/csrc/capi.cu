@@ -143,9 +143,11 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
         if (cap * g->ncell >= (1ll << 31)) { *err = "cells x cell_capacity must be < 2^31"; return PIC_EINVAL; }
         g->cap[s] = (int)cap;
         // immigrant area (>= 1 slot): 2D a quarter of the slots (only particles crossing a tile
-        // edge arrive there); 3D half, since the beam's z flux through the bottom layer of a
-        // 4-cell-deep tile is ~half its particles per step.  The rest keeps the cell's stayers.
-        long long ci = c->ndim == 2 ? (cap + 3) / 4 : (cap + 1) / 2;
+        // edge arrive there); 3D a third in multiples of 8 slots (the beam's z flux through the
+        // bottom layer of a 4-cell-deep tile is ~half its beam particles per step, ~a quarter of
+        // the mean per cell), so that both areas start on a 32-byte sector.  The rest keeps the
+        // cell's stayers and the particles arriving from the same tile.
+        long long ci = c->ndim == 2 ? (cap + 3) / 4 : ((cap / 3 + 7) / 8) * 8;
         if (ci < 1) ci = 1;
         if (ci >= cap) ci = cap > 1 ? cap - 1 : 0;
         g->cap_stay[s] = (int)(cap - ci);
