@@ -63,6 +63,9 @@ extern "C" {
                                sticky flag fails the next synchronising call */
 #define PIC_ETIMEOUT (-6)   /* a bounded device wait gave up */
 #define PIC_ESTATE (-7)     /* call not valid in the current state */
+#define PIC_EBOUNDS (-8)    /* (bounds-checked debug build, libpic_debug.so, only) a kernel's
+                               shared-tile or halo index fell outside its array: the access was
+                               skipped and the sticky flag fails the next synchronising call */
 
 #define PIC_MAX_SPECIES 2
 
@@ -70,6 +73,9 @@ extern "C" {
 #define PIC_FLAG_PROFILE 1   /* time each kernel phase with CUDA events (disables graphs) */
 #define PIC_FLAG_NO_GRAPH 2  /* launch steps directly instead of replaying a CUDA graph */
 #define PIC_FLAG_KEEP_J 4    /* keep a copy of the last step's J for pic_get_fields (tests) */
+#define PIC_FLAG_NVTX 8      /* NVTX ranges: one per pic_step call and one per phase of every step
+                                (push_deposit, yee, finalize, sort); launches steps directly so
+                                that every phase is visible (no graph) */
 
 typedef struct pic_ctx pic_ctx;
 
@@ -174,7 +180,8 @@ int pic_sync(pic_ctx* ctx);
 
 /* Wait for the stream, write the sticky device error bits to *flags_out (may be NULL; bit 1:
  * a non-finite or out-of-range particle, which the step kept unmoved and left out of the
- * current; 2: fixed-point headroom; 4: a bounded wait gave up; 8: a spill list was full) and
+ * current; 2: fixed-point headroom; 4: a bounded wait gave up; 8: a spill list was full; 16: an
+ * index out of range in the bounds-checked debug build) and
  * clear them, so that a caller can read back the state that produced the error.  The state
  * after an error is the step's result for every particle that did not raise it.  PIC_OK. */
 int pic_clear_flags(pic_ctx* ctx, int32_t* flags_out);

@@ -12,16 +12,18 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpic.so")
+# PIC_DEBUG_BOUNDS=1 selects the bounds-checked build (build.build(debug=True))
+LIB_PATH = os.path.join(_HERE, "libpic_debug.so" if os.environ.get("PIC_DEBUG_BOUNDS") == "1" else "libpic.so")
 _lib = None
 
 PIC_MAX_SPECIES = 2
 PIC_FLAG_PROFILE = 1
 PIC_FLAG_NO_GRAPH = 2
 PIC_FLAG_KEEP_J = 4
+PIC_FLAG_NVTX = 8
 
 ERRORS = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA", -4: "PIC_EOVERFLOW",
-          -5: "PIC_EBADPART", -6: "PIC_ETIMEOUT", -7: "PIC_ESTATE"}
+          -5: "PIC_EBADPART", -6: "PIC_ETIMEOUT", -7: "PIC_ESTATE", -8: "PIC_EBOUNDS"}
 
 
 class PicError(RuntimeError):
@@ -176,7 +178,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"libpic.so not built ({LIB_PATH}); run __graft_entry__.build()")
+            raise RuntimeError(f"{os.path.basename(LIB_PATH)} not built ({LIB_PATH}); run __graft_entry__.build()")
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in _SIGNATURES.items():
             f = getattr(L, name)

@@ -1,4 +1,10 @@
-"""Build libpic.so in-tree from csrc/*.cu for sm_103a (nvcc, parallel, no cmake)."""
+"""Build libpic.so in-tree from csrc/*.cu for sm_103a (nvcc, parallel, no cmake).
+
+build(debug=True) builds libpic_debug.so instead: the same sources compiled with
+-DPIC_DEBUG_BOUNDS, whose kernels check every shared-tile and halo index before the access,
+skip an access that is out of range and set the sticky ERR_BOUNDS flag (PIC_EBOUNDS on the next
+synchronising call).  The binding loads it when PIC_DEBUG_BOUNDS=1 is set in the environment.
+"""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -10,6 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpic.so")
+OBJ_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libpic_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -32,18 +40,20 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
     nvcc = _nvcc()
-    os.makedirs(OBJ, exist_ok=True)
+    obj_dir, lib = (OBJ_DEBUG, LIB_DEBUG) if debug else (OBJ, LIB)
+    flags = FLAGS + (["-DPIC_DEBUG_BOUNDS"] if debug else [])
+    os.makedirs(obj_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "pic.h"))
     jobs = []
     objs = []
     for src in sources():
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
-            jobs.append([nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj])
+            jobs.append([nvcc, *ARCH, *flags, "-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -54,11 +64,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, max(1, len(jobs)))) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"])
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -19,6 +19,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pic.h"
 #include "pic_internal.cuh"
 
@@ -318,11 +320,14 @@ cudaEvent_t get_event(pic_ctx* c) {
     return e;
 }
 
+// One phase of a step: CUDA events around it (PIC_FLAG_PROFILE) and an NVTX range (PIC_FLAG_NVTX).
 struct PhaseScope {
     pic_ctx* c;
     pic_ctx::Ev ev{};
-    bool on;
-    PhaseScope(pic_ctx* c_, int ph) : c(c_), on((c_->cfg.flags & PIC_FLAG_PROFILE) != 0) {
+    bool on, nvtx;
+    PhaseScope(pic_ctx* c_, int ph)
+        : c(c_), on((c_->cfg.flags & PIC_FLAG_PROFILE) != 0), nvtx((c_->cfg.flags & PIC_FLAG_NVTX) != 0) {
+        if (nvtx) nvtxRangePushA(kPhaseName[ph]);
         if (!on) return;
         ev.phase = ph;
         ev.a = get_event(c);
@@ -330,9 +335,22 @@ struct PhaseScope {
         cudaEventRecord(ev.a, c->stream);
     }
     ~PhaseScope() {
-        if (!on) return;
-        cudaEventRecord(ev.b, c->stream);
-        c->pending.push_back(ev);
+        if (on) {
+            cudaEventRecord(ev.b, c->stream);
+            c->pending.push_back(ev);
+        }
+        if (nvtx) nvtxRangePop();
+    }
+};
+
+// An NVTX range around a C-ABI call (PIC_FLAG_NVTX).
+struct NvtxCall {
+    bool on;
+    NvtxCall(const pic_ctx* c, const char* name) : on(c && (c->cfg.flags & PIC_FLAG_NVTX) != 0) {
+        if (on) nvtxRangePushA(name);
+    }
+    ~NvtxCall() {
+        if (on) nvtxRangePop();
     }
 };
 
@@ -401,6 +419,7 @@ int device_flags(pic_ctx* ctx) {
     if (h.err & ERR_OVERFLOW) return fail(ctx, PIC_EOVERFLOW, "device: fixed-point headroom exceeded");
     if (h.err & ERR_TIMEOUT) return fail(ctx, PIC_ETIMEOUT, "device: bounded wait gave up");
     if (h.err & ERR_SPILL_FULL) return fail(ctx, PIC_ENOMEM, "device: spill list full (raise cell_capacity)");
+    if (h.err & ERR_BOUNDS) return fail(ctx, PIC_EBOUNDS, "device: shared-tile or halo index out of range (debug build)");
     return PIC_OK;
 }
 
@@ -714,7 +733,8 @@ extern "C" int pic_load_species_run(pic_ctx* ctx, int run, int s, const pic_spec
 extern "C" int pic_step(pic_ctx* ctx, int nsteps) {
     if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
     if (nsteps < 0) return fail(ctx, PIC_EINVAL, "nsteps < 0");
-    const bool use_graph = !(ctx->cfg.flags & (PIC_FLAG_PROFILE | PIC_FLAG_NO_GRAPH));
+    const NvtxCall range(ctx, "pic_step");
+    const bool use_graph = !(ctx->cfg.flags & (PIC_FLAG_PROFILE | PIC_FLAG_NO_GRAPH | PIC_FLAG_NVTX));
     while (nsteps > 0) {
         const int K = ctx->sort_interval;
         if (use_graph && ctx->host_step % K == 0 && nsteps >= K) {

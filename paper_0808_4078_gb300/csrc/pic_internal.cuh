@@ -24,7 +24,20 @@
 namespace pic {
 
 // Error flags (device word, sticky)
-enum : int { ERR_BADPART = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_SPILL_FULL = 8 };
+enum : int { ERR_BADPART = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4, ERR_SPILL_FULL = 8, ERR_BOUNDS = 16 };
+
+// Index checks of the bounds-checked debug build (compiled with -DPIC_DEBUG_BOUNDS): a failed
+// check sets ERR_BOUNDS and the caller skips the access.  In the normal build every check is
+// true at compile time and costs nothing.
+#ifdef PIC_DEBUG_BOUNDS
+__device__ __forceinline__ bool dbg_in(long long i, long long n, int* err) {
+    const bool ok = i >= 0 && i < n;
+    if (!ok) atomicOr(err, ERR_BOUNDS);
+    return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool dbg_in(long long, long long, int*) { return true; }
+#endif
 
 struct SpeciesParams {
     float qmdt2;        // q dt / (2 m)

@@ -274,7 +274,7 @@ __device__ __forceinline__ int qmeta(int s, int ci, int sx, int sy, bool bad) {
 template <int TX, int TY>
 __device__ __forceinline__ void cross_one(Smem<TX, TY>& sm, const Args& a, const RunConst& K, const Crosser& e,
                                           int x0, int y0) {
-    constexpr int RX = Geo<TX, TY>::RX;
+    constexpr int RX = Geo<TX, TY>::RX, RN = Geo<TX, TY>::RN;
     const float ox = e.o.x, oy = e.o.y, nox = e.o.z, noy = e.o.w;
     const float ux = e.u.x, uy = e.u.y, uz = e.u.z, vz = e.u.w;
     const int m = e.m.x, id = e.m.y;
@@ -296,11 +296,12 @@ __device__ __forceinline__ void cross_one(Smem<TX, TY>& sm, const Args& a, const
     const Win wx = window(ox, sx, nox), wy = window(oy, sy, noy);
     const float zf = __fmul_rn(P.jz, vz);
     auto add = [&](int c, int ii, int jj, int v) {
-        add_split_pred(&sm.Jlo[c][jj * RX + ii], &sm.Jhi[c][jj * RX + ii], v);
+        if (dbg_in(jj * RX + ii, RN, &a.ctl->err))
+            add_split_pred(&sm.Jlo[c][jj * RX + ii], &sm.Jhi[c][jj * RX + ii], v);
     };
     deposit_terms(add, P, ix + wx.off, iy + wy.off, wx, wy, zf);
-    if (P.drag) {
-        const int n1 = (iy + sy) * RX + (ix + sx);
+    const int n1 = (iy + sy) * RX + (ix + sx);
+    if (P.drag && dbg_in(n1, RN, &a.ctl->err)) {
         add_split_pred(&sm.Mlo[0][n1], &sm.Mhi[0][n1], f2ll_rn(ux * MOM_SCALE));
         add_split_pred(&sm.Mlo[1][n1], &sm.Mhi[1][n1], f2ll_rn(uy * MOM_SCALE));
         add_split_pred(&sm.Mlo[2][n1], &sm.Mhi[2][n1], f2ll_rn(uz * MOM_SCALE));
@@ -325,8 +326,9 @@ __device__ __forceinline__ void cross_one(Smem<TX, TY>& sm, const Args& a, const
 // lane i adds sum i.  At most 8 chunks are summed between flushes, so a warp sum of terms of at
 // most 2^21 stays below 2^29.
 template <int TX, int TY>
-__device__ __forceinline__ void flush_acc(Smem<TX, TY>& sm, int acc[12], int n0, int lane, bool moments) {
-    constexpr int RX = Geo<TX, TY>::RX;
+__device__ __forceinline__ void flush_acc(Smem<TX, TY>& sm, int acc[12], int n0, int lane, bool moments,
+                                          int* err) {
+    constexpr int RX = Geo<TX, TY>::RX, RN = Geo<TX, TY>::RN;
     int tot = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -342,6 +344,7 @@ __device__ __forceinline__ void flush_acc(Smem<TX, TY>& sm, int acc[12], int n0,
             acc[i] = 0;
         }
     }
+    if (!dbg_in(n0, RN - RX - 1, err)) return;
     if (lane < 11) {
         // node offsets: Jx (0,0),(0,1); Jy (0,0),(1,0); Jz (0,0),(1,0),(0,1),(1,1); moments (0,0)
         const int off = (lane == 1 || lane == 6) ? RX : (lane == 3 || lane == 5) ? 1 : (lane == 7) ? RX + 1 : 0;
@@ -534,14 +537,14 @@ __global__ void __launch_bounds__(NT, MINB) push2d_kernel(const Args a) {
         }
         if (L.ci < CELLS) nxt = load_part(L, lj, lane, sm.src[L.s], bstride, ids);
         if (ci != cur_ci) {
-            if (nchunk) { flush_acc(sm, acc, n0, lane, cell_drag); nchunk = 0; }
+            if (nchunk) { flush_acc(sm, acc, n0, lane, cell_drag, &a.ctl->err); nchunk = 0; }
             cur_ci = ci;
             n0 = (ci / TX + 1) * RX + (ci % TX + 1);
             __syncwarp();
-            if (lane < 13) {
+            if (lane < 13 && dbg_in(n0 + sm.toff[lane], 6 * RN - RX - 1, &a.ctl->err)) {
                 const float* f = &sm.F[0][0] + n0 + sm.toff[lane];
                 sm.T[warp][lane] = patch(f[0], f[1], f[RX], f[RX + 1]);
-            } else if (lane == 13) {
+            } else if (lane == 13 && dbg_in(ci, CELLS, &a.ctl->err)) {
                 sm.T[warp][13] = make_float4(sm.ub[0][ci], sm.ub[1][ci], sm.ub[2][ci], 0.f);
             }
             __syncwarp();
@@ -637,11 +640,11 @@ __global__ void __launch_bounds__(NT, MINB) push2d_kernel(const Args a) {
             }
         }
         if (++nchunk == FLUSH_CHUNKS) {
-            flush_acc(sm, acc, n0, lane, cell_drag);
+            flush_acc(sm, acc, n0, lane, cell_drag, &a.ctl->err);
             nchunk = 0;
         }
     }
-    if (nchunk) flush_acc(sm, acc, n0, lane, cell_drag);
+    if (nchunk) flush_acc(sm, acc, n0, lane, cell_drag, &a.ctl->err);
     // the tile's crossers, one per thread
     __syncthreads();
     {

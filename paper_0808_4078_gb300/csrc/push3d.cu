@@ -109,8 +109,10 @@ __device__ __forceinline__ void gather3(const A& F, const AxisW& wx, const AxisW
 struct SharedFields3 {
     const Smem* s;
     int n0;   // region index of the particle's cell node
+    int* err; // sticky flags (index checks of the bounds-checked build)
     __device__ __forceinline__ float operator()(int c, int i, int j, int k) const {
-        return s->F[c][n0 + k * RXY + j * RX + i];
+        const int n = n0 + k * RXY + j * RX + i;
+        return dbg_in(n, RN, err) ? s->F[c][n] : 0.f;
     }
 };
 struct GlobalFields3 {
@@ -373,7 +375,8 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
         for (int r = 0; r < PIC_NS; ++r) {
             const int e = r * CELLS + tid;
             const int lo = max(sm.pre[e], b0), hi = min(sm.pre[e] + cnt_own[r], b0 + BATCH);
-            for (int p = lo; p < hi; ++p) sm.owner[p - b0] = (unsigned short)e;
+            for (int p = lo; p < hi; ++p)
+                if (dbg_in(p - b0, BATCH, &a.ctl->err)) sm.owner[p - b0] = (unsigned short)e;
         }
         __syncthreads();
         // load the thread's particles of the batch
@@ -417,10 +420,10 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
             const int cap = a.cap[s], cst = a.cap_stay[s];
             const Slots& D = a.slot[s][par ^ 1];
             float b0v = 0.f, b1v = 0.f, b2v = 0.f;
-            if (DRAG && P.drag) { b0v = sm.ub[0][n0]; b1v = sm.ub[1][n0]; b2v = sm.ub[2][n0]; }
+            if (DRAG && P.drag && dbg_in(n0, RN, &a.ctl->err)) { b0v = sm.ub[0][n0]; b1v = sm.ub[1][n0]; b2v = sm.ub[2][n0]; }
             const long long g = cbase + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
             const float df = DRAG && P.drag ? drag_of(K, P, s, g - cbase) : 0.f;
-            const Pushed3 res = push3_one<DRAG>(SharedFields3{&sm, n0}, P, K, po[r], pu[r][0], pu[r][1], pu[r][2],
+            const Pushed3 res = push3_one<DRAG>(SharedFields3{&sm, n0, &a.ctl->err}, P, K, po[r], pu[r][0], pu[r][1], pu[r][2],
                                           b0v, b1v, b2v, df, s, (unsigned)pid[r], step);
             const bool xa = __any_sync(am, res.st[0] != 0), ya = __any_sync(am, res.st[1] != 0),
                        za = __any_sync(am, res.st[2] != 0);
@@ -436,11 +439,12 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
             const Win wz = window(po[r][2], res.st[2], res.no[2]);
             const int nb = n0 + wz.off * RXY + wy.off * RX + wx.off;
             auto add = [&](int c, int i, int j, int k, int v) {
-                red_shared_nz(&sm.J32[c][nb + k * RXY + j * RX + i], v);
+                if (dbg_in(nb + k * RXY + j * RX + i, RN, &a.ctl->err))
+                    red_shared_nz(&sm.J32[c][nb + k * RXY + j * RX + i], v);
             };
             deposit3(add, P, wx, wy, wz, xa, ya, za);
             const int n1 = n0 + res.st[2] * RXY + res.st[1] * RX + res.st[0];
-            if (DRAG && P.drag) {
+            if (DRAG && P.drag && dbg_in(n1, RN, &a.ctl->err)) {
                 add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], f2ll_rn(res.ux * MOM_SCALE));
                 add_split(&sm.Mlo[1][n1], &sm.Mhi[1][n1], f2ll_rn(res.uy * MOM_SCALE));
                 add_split(&sm.Mlo[2][n1], &sm.Mhi[2][n1], f2ll_rn(res.uz * MOM_SCALE));
