@@ -81,7 +81,9 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
     if (c->ndim != 2 && c->ndim != 3) { *err = "ndim must be 2 or 3"; return PIC_EINVAL; }
     if (c->ndim == 3 && !pic::has_push3d()) { *err = "3D push not available in this build"; return PIC_EINVAL; }
     if (nruns < 1 || nruns > 65536) { *err = "nruns must be in [1, 65536]"; return PIC_EINVAL; }
-    const int dtx = c->ndim == 3 ? 8 : 16, dty = c->ndim == 3 ? 8 : 16, dtz = c->ndim == 3 ? 4 : 1;
+    int t3[3];
+    pic::push3d_tile(t3);
+    const int dtx = c->ndim == 3 ? t3[0] : 16, dty = c->ndim == 3 ? t3[1] : 16, dtz = c->ndim == 3 ? t3[2] : 1;
     g->tx = c->tile_x > 0 ? c->tile_x : dtx;
     g->ty = c->tile_y > 0 ? c->tile_y : dty;
     g->tz = c->ndim == 3 ? (c->tile_z > 0 ? c->tile_z : dtz) : 1;
@@ -91,7 +93,10 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
         g->push_variant = pic::push2d_variant(g->tx, g->ty, c->ctas_per_sm);
         if (g->push_variant < 0) { *err = "2D tiles are 16 x 16, 32 x 8 or 8 x 32"; return PIC_EINVAL; }
     }
-    if (c->ndim == 3 && (g->tx != 8 || g->ty != 8 || g->tz != 4)) { *err = "3D tiles are 8 x 8 x 4"; return PIC_EINVAL; }
+    if (c->ndim == 3 && (g->tx != t3[0] || g->ty != t3[1] || g->tz != t3[2])) {
+        *err = "3D tiles must have the shape of the 3D particle kernel (pic_tile_config)";
+        return PIC_EINVAL;
+    }
     if (!(c->dx > 0 && c->dy > 0 && c->dt > 0) || (c->ndim == 3 && !(c->dz > 0))) { *err = "dx, dy, dz, dt must be > 0"; return PIC_EINVAL; }
     const double inv2 = 1.0 / (c->dx * c->dx) + 1.0 / (c->dy * c->dy) + (c->ndim == 3 ? 1.0 / (c->dz * c->dz) : 0.0);
     if (c->dt * std::sqrt(inv2) >= 1.0) { *err = "dt violates the Yee Courant condition"; return PIC_EINVAL; }

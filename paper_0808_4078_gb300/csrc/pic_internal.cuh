@@ -239,6 +239,7 @@ int push2d_num_variants();
 void push2d_variant_info(int v, int* tx, int* ty, int* minb);
 cudaError_t launch_push3d(const Args& a, cudaStream_t s);
 bool has_push3d();
+void push3d_tile(int t[3]);   // the 3D particle kernel's tile shape (cells per axis)
 cudaError_t launch_spill2d(const Args& a, cudaStream_t s);
 cudaError_t launch_spill3d(const Args& a, cudaStream_t s);
 cudaError_t launch_yee2d(const Args& a, const RunDev* host_runs, int nruns, cudaStream_t s);

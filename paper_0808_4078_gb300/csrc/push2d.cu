@@ -357,29 +357,31 @@ __device__ __forceinline__ void flush_acc(Smem<TX, TY>& sm, int acc[12], int n0,
     }
 }
 
-// A warp's work is a sequence of segments, one per (cell, species) with particles: cells
-// ci = warp, warp + NW, ...; per cell the species in order.  A segment's particles are
-// elements k = 0 .. n-1: slots q0 + k for k < ns (stay area), qi + k beyond (immigrant area).
+// A warp's work is a sequence of segments, one per cell with particles: cells ci = warp,
+// warp + NW, ...  A segment's particles are elements k = 0 .. n-1, species 0 first (k < n0), then
+// species 1; element kk of species s lives in slot q0_s + kk for kk < ns_s (stay area), qi_s + kk
+// beyond (immigrant area).  A chunk of 32 elements may hold both species of its cell.
 struct Seg {
-    int ci, s, n, ns, q0, qi;
+    int ci, n0, n;
+    int ns0, ns1, q00, q01, qi0, qi1;
 };
 template <int TX, int TY>
-__device__ __forceinline__ Seg seg_find(const Smem<TX, TY>& sm, int ci, int s, int nsp, int cell_off, int nx,
-                                        int x0, int y0) {
+__device__ __forceinline__ Seg seg_find(const Smem<TX, TY>& sm, int ci, int cell_off, int nx, int x0, int y0) {
     constexpr int CELLS = Geo<TX, TY>::CELLS;
-    while (ci < CELLS && sm.nn[s][ci] == 0) {
-        if (++s >= nsp) { s = 0; ci += NW; }
-    }
+    while (ci < CELLS && sm.nn[0][ci] + sm.nn[1][ci] == 0) ci += NW;
     Seg r;
     r.ci = ci;
-    r.s = s;
-    r.n = r.ns = r.q0 = r.qi = 0;
+    r.n0 = r.n = r.ns0 = r.ns1 = r.q00 = r.q01 = r.qi0 = r.qi1 = 0;
     if (ci < CELLS) {
-        r.n = sm.nn[s][ci];
-        r.ns = sm.ns[s][ci];
+        r.n0 = sm.nn[0][ci];
+        r.n = r.n0 + sm.nn[1][ci];
+        r.ns0 = sm.ns[0][ci];
+        r.ns1 = sm.ns[1][ci];
         const int g = cell_off + (y0 + ci / TX) * nx + (x0 + ci % TX);
-        r.q0 = g * sm.cap[s];
-        r.qi = r.q0 + sm.cst[s] - r.ns;
+        r.q00 = g * sm.cap[0];
+        r.q01 = g * sm.cap[1];
+        r.qi0 = r.q00 + sm.cst[0] - r.ns0;
+        r.qi1 = r.q01 + sm.cst[1] - r.ns1;
     }
     return r;
 }
@@ -387,17 +389,25 @@ __device__ __forceinline__ Seg seg_find(const Smem<TX, TY>& sm, int ci, int s, i
 struct Part {
     float ox, oy, ux, uy, uz;
     int id;
+    int s;      // species, -1 past the segment's end
+    int q0;     // first slot of the cell for the particle's species
 };
 // The lane's particle of the chunk starting at element j of segment L (zeros past its end).
-__device__ __forceinline__ Part load_part(const Seg& L, int j, int lane, const float* src, long long bstride,
-                                          bool ids) {
+__device__ __forceinline__ Part load_part(const Seg& L, int j, int lane, float* const src[PIC_NS],
+                                          long long bstride, bool ids) {
     Part p;
     p.ox = p.oy = p.ux = p.uy = p.uz = 0.f;
     p.id = 0;
+    p.s = -1;
+    p.q0 = 0;
     const int k = j + lane;
     if (k < L.n) {
-        const int q = (k < L.ns ? L.q0 : L.qi) + k;
-        const float* b = src + (size_t)(q / PIC_BLK) * bstride + (q % PIC_BLK);
+        const bool s1 = k >= L.n0;
+        const int kk = s1 ? k - L.n0 : k;
+        p.s = s1 ? 1 : 0;
+        p.q0 = s1 ? L.q01 : L.q00;
+        const int q = (kk < (s1 ? L.ns1 : L.ns0) ? p.q0 : (s1 ? L.qi1 : L.qi0)) + kk;
+        const float* b = src[p.s] + (size_t)(q / PIC_BLK) * bstride + (q % PIC_BLK);
         p.ox = __ldg(b);
         p.oy = __ldg(b + PIC_BLK);
         p.ux = __ldg(b + 2 * PIC_BLK);
@@ -517,9 +527,9 @@ __global__ void __launch_bounds__(NT, MINB) push2d_kernel(const Args a) {
 
     // L: the segment the next chunk is loaded from (lj its first element); the chunk in
     // registers (nxt) is pushed in the following iteration.
-    Seg L = seg_find(sm, warp, 0, nsp, K.cell_off, nx, x0, y0);
+    Seg L = seg_find(sm, warp, K.cell_off, nx, x0, y0);
     int lj = 0;
-    Part nxt = load_part(L, 0, lane, sm.src[L.s], bstride, ids);
+    Part nxt = load_part(L, 0, lane, sm.src, bstride, ids);
     int cur_ci = -1, n0 = 0, nchunk = 0;
     const bool cell_drag = anydrag;   // the tile's cells carry drag moments
     int acc[12];
@@ -528,14 +538,14 @@ __global__ void __launch_bounds__(NT, MINB) push2d_kernel(const Args a) {
     const float4* Tw = sm.T[warp];
     const unsigned lt = (1u << lane) - 1u;
     while (L.ci < CELLS) {
-        const int ci = L.ci, s = L.s, n = L.n, q0 = L.q0, j = lj;
+        const int ci = L.ci;
         const Part p = nxt;
         lj += 32;
         if (lj >= L.n) {
-            L = seg_find(sm, s + 1 < nsp ? ci : ci + NW, s + 1 < nsp ? s + 1 : 0, nsp, K.cell_off, nx, x0, y0);
+            L = seg_find(sm, ci + NW, K.cell_off, nx, x0, y0);
             lj = 0;
         }
-        if (L.ci < CELLS) nxt = load_part(L, lj, lane, sm.src[L.s], bstride, ids);
+        if (L.ci < CELLS) nxt = load_part(L, lj, lane, sm.src, bstride, ids);
         if (ci != cur_ci) {
             if (nchunk) { flush_acc(sm, acc, n0, lane, cell_drag, &a.ctl->err); nchunk = 0; }
             cur_ci = ci;
@@ -549,8 +559,9 @@ __global__ void __launch_bounds__(NT, MINB) push2d_kernel(const Args a) {
             }
             __syncwarp();
         }
+        const bool act = p.s >= 0;
+        const int s = act ? p.s : 0;
         const SpeciesParams& P = sm.sp[s];
-        const bool act = j + lane < n;
         float EB[6];
         gather_tab(Tw, p.ox, p.oy, EB);
         const bool drag = P.drag;
@@ -591,17 +602,19 @@ __global__ void __launch_bounds__(NT, MINB) push2d_kernel(const Args a) {
                 acc[11] += 1;
             }
         }
-        // stayers take the next places of their cell's stay area in the other buffer
-        const unsigned smask = __ballot_sync(FULL, stay);
-        if (smask) {
+        // stayers take the next places of their cell's stay area in the other buffer (one claim
+        // per species of the chunk)
+        const unsigned smask0 = __ballot_sync(FULL, stay && s == 0), smask1 = __ballot_sync(FULL, stay && s == 1);
+        if (smask0 | smask1) {
             int base = 0;
-            if (lane == 0) base = atomicAdd(&sm.oc[s][ci], __popc(smask));
-            base = __shfl_sync(FULL, base, 0);
+            if (lane == 0 && smask0) base = atomicAdd(&sm.oc[0][ci], __popc(smask0));
+            if (lane == 1 && smask1) base = atomicAdd(&sm.oc[1][ci], __popc(smask1));
+            const int base0 = __shfl_sync(FULL, base, 0), base1 = __shfl_sync(FULL, base, 1);
             if (stay) {
-                const int pos = base + __popc(smask & lt);
-                if (pos < sm.cst[s]) store2(sm.dst[s], bstride, ids, q0 + pos, r.nox, r.noy, r.ux, r.uy, r.uz, p.id);
-                else put_imm(sm.dslot[s], sm.cap[s], sm.cst[s], sm.spc[s], q0 / sm.cap[s], r.nox, r.noy, r.ux, r.uy,
-                             r.uz, p.id, &a.ctl->err);
+                const int pos = (s ? base1 : base0) + __popc((s ? smask1 : smask0) & lt);
+                if (pos < sm.cst[s]) store2(sm.dst[s], bstride, ids, p.q0 + pos, r.nox, r.noy, r.ux, r.uy, r.uz, p.id);
+                else put_imm(sm.dslot[s], sm.cap[s], sm.cst[s], sm.spc[s], p.q0 / sm.cap[s], r.nox, r.noy, r.ux,
+                             r.uy, r.uz, p.id, &a.ctl->err);
             }
         }
         // the others are queued with their pushed state (bad ones with their old state) in the
@@ -632,7 +645,7 @@ __global__ void __launch_bounds__(NT, MINB) push2d_kernel(const Args a) {
                     const int o = atomicAdd(a.xo_n, 1);
                     if (o < a.xo_cap) {
                         a.xo[o].c = e;
-                        a.xo[o].cell = q0 / sm.cap[s];
+                        a.xo[o].cell = p.q0 / sm.cap[s];
                     } else {
                         atomicOr(&a.ctl->err, ERR_SPILL_FULL);
                     }

@@ -628,6 +628,7 @@ __global__ void __launch_bounds__(NT) spill3d_kernel(const Args a) {
 }  // namespace
 
 bool has_push3d() { return true; }
+void push3d_tile(int t[3]) { t[0] = TX; t[1] = TY; t[2] = TZ; }
 
 cudaError_t launch_push3d(const Args& a, cudaStream_t s) {
     if (a.nwork == 0) return cudaSuccess;
