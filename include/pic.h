@@ -88,7 +88,9 @@ typedef struct pic_config {
     int32_t cell_capacity[PIC_MAX_SPECIES]; /* particle slots per cell per species; 0 = automatic
                                                (2D: 8 x the mean per cell, multiple of 32,
                                                >= 32; 3D: 3 x the mean, multiple of 8, >= 16);
-                                               must be >= 2 x capacity / cells */
+                                               must be >= 2 x capacity / cells.  In 3D the
+                                               slots of a tile's cells form one range per tile
+                                               (a particle may sit anywhere in its tile's) */
     int32_t sort_interval;     /* steps between checks for a full counting sort that repacks
                                   spilled particles (particles whose cell's slots were full,
                                   held in a list of a quarter of the species' capacity; the sort
@@ -226,9 +228,12 @@ int pic_kernel_times(pic_ctx* ctx, pic_kernel_time* out, int max, int* n_out);
 
 typedef struct pic_stats {
     int64_t particles[PIC_MAX_SPECIES];   /* particles held (slots + spill list) */
-    int32_t max_cell[PIC_MAX_SPECIES];    /* largest per-cell count (may exceed the capacity) */
+    int32_t max_cell[PIC_MAX_SPECIES];    /* largest count of one binning unit (2D: a cell; 3D: a
+                                             tile of the 3D particle kernel); may exceed the
+                                             capacity */
     int32_t spilled[PIC_MAX_SPECIES];     /* particles in the spill list */
-    int32_t cell_capacity[PIC_MAX_SPECIES];
+    int32_t cell_capacity[PIC_MAX_SPECIES];  /* slots per unit (2D: per cell; 3D: per tile, the
+                                                tile's cells' cell_capacity together) */
     int32_t flags;                        /* sticky device error flags */
     int32_t reserved;
 } pic_stats;

@@ -1,11 +1,13 @@
-// bins.cu -- counting-sort binning of particles into per-cell slots, and the inverse compaction.
+// bins.cu -- counting-sort binning of particles into per-unit slots (a unit is a cell in 2D and
+// a tile of the 3D particle kernel in 3D), and the inverse compaction.
 //
-// Binning (load): each particle takes the next free slot of its cell with an atomic per-cell
-// counter (a counting sort into fixed-capacity bins); a particle whose cell is full goes to the
-// species' spill list.  Counters may exceed the capacity; readers clamp them.  The step kernels
-// rebin every particle into the other buffer the same way, fused into the push.
-// Compaction (read-back): exclusive scan of the clamped counts, then each cell's particles are
-// copied to a dense array in cell order, followed by the spill list.
+// Binning (load): each particle takes the next free slot of its unit with an atomic per-unit
+// counter (a counting sort into fixed-capacity bins; in 3D the particle's cell within the tile
+// is stored beside it); a particle whose unit is full goes to the species' spill list.  Counters
+// may exceed the capacity; readers clamp them.  The step kernels rebin every particle into the
+// other buffer the same way, fused into the push.
+// Compaction (read-back): exclusive scan of the clamped counts, then each unit's particles are
+// copied to a dense array in unit order (2D: cell order), followed by the spill list.
 #include <mutex>
 
 #include "../../include/pic.h"
@@ -47,16 +49,19 @@ __global__ void __launch_bounds__(NT) bin_kernel(Args a, int s, long long n, boo
         if (!ok) { atomicOr(&a.ctl->err, ERR_BADPART); continue; }
         const int id = with_ids ? T.id[p] : (int)p;
         const int cs = a.cap_stay[s];
-        int pos = atomicAdd(&S.count[c], 1);
+        int lc;
+        const long long unit = unit_of_cell(a, c, &lc);
+        int pos = atomicAdd(&S.count[unit], 1);
         if (pos >= cs) {
-            const int pi = atomicAdd(&S.icount[c], 1);
+            const int pi = atomicAdd(&S.icount[unit], 1);
             pos = pi < cap - cs ? cs + pi : cap;
         }
         if (pos < cap) {
-            const size_t q = slot_elt(S, (long long)c * cap + pos);
+            const size_t q = slot_elt(S, unit * cap + pos);
             for (int d = 0; d < a.ndim; ++d) S.o[d][q] = ov[d];
             for (int d = 0; d < 3; ++d) S.u[d][q] = uv[d];
             if (S.id) S.id[q] = id;
+            if (S.lc) S.lc[q] = lc;
         } else {
             const int sp = atomicAdd(S.sn, 1);
             if (sp < a.spill_cap[s]) {
@@ -71,7 +76,7 @@ __global__ void __launch_bounds__(NT) bin_kernel(Args a, int s, long long n, boo
     }
 }
 
-// Exclusive scan of the particles per cell (both slot areas) into start, block sums into tmp.
+// Exclusive scan of the particles per unit (both slot areas) into start, block sums into tmp.
 __global__ void __launch_bounds__(NT) scan_blocks(Args a, int s, long long c0, int* __restrict__ start,
                                                   int* __restrict__ tmp, long long n, const int* gate) {
     if (gate && *gate == 0) return;
@@ -164,11 +169,11 @@ __global__ void __launch_bounds__(NT) scan_add(int* __restrict__ start, const in
     }
 }
 
-// One thread per cell of [c0, c0 + nc): copy its slots to the staging arrays at start[c - c0] ...
-// in cell order, with the cell index minus cell_base; the spill entries of those cells follow
-// at start[nc] (their order is not fixed).
-__global__ void __launch_bounds__(NT) compact_kernel(Args a, int s, long long c0, long long nc,
-                                                     long long cell_base, const int* gate) {
+// One thread per unit of [c0, c0 + nc): copy its slots to the staging arrays at start[c - c0] ...
+// in unit order, with the cell index minus cell_base; the spill entries of the cells
+// [cell_lo, cell_lo + ncells) follow at start[nc] (their order is not fixed).
+__global__ void __launch_bounds__(NT) compact_kernel(Args a, int s, long long c0, long long nc, long long cell_lo,
+                                                     long long ncells, long long cell_base, const int* gate) {
     if (gate && *gate == 0) return;
     const int par = a.ctl->parity;
     const Slots S = a.slot[s][par];
@@ -180,9 +185,10 @@ __global__ void __launch_bounds__(NT) compact_kernel(Args a, int s, long long c0
         const long long c = c0 + k;
         const CellRange cr = cell_range(S, cap, cs, c);
         const int b = start[k];
+        const RunDev* R = S.lc ? &a.runs[run_of_unit(a, c)] : nullptr;
         for (int i = 0; i < cr.n; ++i) {
             const size_t q = slot_elt(S, (long long)slot_of(c, cap, cs, cr.ns, i));
-            T.cell[b + i] = (int)(c - cell_base);
+            T.cell[b + i] = (int)((S.lc ? cell_of_unit(a, *R, c, S.lc[q]) : c) - cell_base);
             for (int d = 0; d < a.ndim; ++d) T.o[d][b + i] = S.o[d][q];
             for (int d = 0; d < 3; ++d) T.u[d][b + i] = S.u[d][q];
             T.id[b + i] = S.id ? S.id[q] : 0;
@@ -191,7 +197,7 @@ __global__ void __launch_bounds__(NT) compact_kernel(Args a, int s, long long c0
     const int ns = min(*S.sn, a.spill_cap[s]);
     for (int k = blockIdx.x * NT + threadIdx.x; k < ns; k += gridDim.x * NT) {
         const long long c = S.scell[k];
-        if (c < c0 || c >= c0 + nc) continue;
+        if (c < cell_lo || c >= cell_lo + ncells) continue;
         const int b = start[nc] + atomicAdd(&a.ctl->staged[s], 1);
         T.cell[b] = (int)(c - cell_base);
         for (int d = 0; d < a.ndim; ++d) T.o[d][b] = S.so[d][k];
@@ -232,7 +238,7 @@ __global__ void spill_base_kernel(Args a) {
 __global__ void clear_current_kernel(Args a, int s, const int* gate) {
     if (gate && *gate == 0) return;
     const Slots S = a.slot[s][a.ctl->parity];
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.nunit;
          c += (long long)gridDim.x * blockDim.x) {
         S.count[c] = 0;
         S.icount[c] = 0;
@@ -240,10 +246,10 @@ __global__ void clear_current_kernel(Args a, int s, const int* gate) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *S.sn = 0;
 }
 
-// Zero the per-cell counts and spill counters of the buffer the next step writes.
+// Zero the per-unit counts and spill counters of the buffer the next step writes.
 __global__ void clear_next_kernel(Args a) {
     const int nb = a.ctl->parity ^ 1;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.nunit;
          c += (long long)gridDim.x * blockDim.x)
         for (int s = 0; s < a.nspecies; ++s) {
             a.slot[s][nb].count[c] = 0;
@@ -403,14 +409,14 @@ cudaError_t launch_bin(const Args& a, int s, long long n, bool with_ids, long lo
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact(const Args& a, int s, long long c0, long long nc, long long cell_base,
-                           const int* gate, cudaStream_t st) {
+cudaError_t launch_compact(const Args& a, int s, long long c0, long long nc, long long cell_lo, long long ncells,
+                           long long cell_base, const int* gate, cudaStream_t st) {
     const int nb = (int)((nc + CHUNK - 1) / CHUNK);
     scan_blocks<<<nb, NT, 0, st>>>(a, s, c0, a.start, a.scan_tmp, nc, gate);
     scan_tmp<<<1, NT, 0, st>>>(a.scan_tmp, nb, a.start + nc, gate);
     scan_add<<<nb, NT, 0, st>>>(a.start, a.scan_tmp, nc, gate);
     staged_zero_kernel<<<1, 1, 0, st>>>(a, s, gate);
-    compact_kernel<<<grid_for(nc), NT, 0, st>>>(a, s, c0, nc, cell_base, gate);
+    compact_kernel<<<grid_for(nc), NT, 0, st>>>(a, s, c0, nc, cell_lo, ncells, cell_base, gate);
     staged_total_kernel<<<1, 1, 0, st>>>(a, s, nc, gate);
     return cudaGetLastError();
 }
@@ -421,12 +427,12 @@ cudaError_t launch_spill_gate(const Args& a, cudaStream_t st) {
 }
 
 cudaError_t launch_clear_current(const Args& a, int s, const int* gate, cudaStream_t st) {
-    clear_current_kernel<<<grid_for(a.ncell), NT, 0, st>>>(a, s, gate);
+    clear_current_kernel<<<grid_for(a.nunit), NT, 0, st>>>(a, s, gate);
     return cudaGetLastError();
 }
 
 cudaError_t launch_clear_next(const Args& a, cudaStream_t st) {
-    clear_next_kernel<<<grid_for(a.ncell), NT, 0, st>>>(a);
+    clear_next_kernel<<<grid_for(a.nunit), NT, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -450,9 +456,9 @@ cudaError_t launch_resort(const Args& a, cudaStream_t st, int* launches) {
     spill_gate_kernel<<<1, 1, 0, st>>>(a);
     int l = 1;
     for (int s = 0; s < a.nspecies; ++s) {
-        cudaError_t e = launch_compact(a, s, 0, a.ncell, 0, a.gate, st);
+        cudaError_t e = launch_compact(a, s, 0, a.nunit, 0, a.ncell, 0, a.gate, st);
         if (e != cudaSuccess) return e;
-        clear_current_kernel<<<grid_for(a.ncell), NT, 0, st>>>(a, s, a.gate);
+        clear_current_kernel<<<grid_for(a.nunit), NT, 0, st>>>(a, s, a.gate);
         // n < 0: the bin kernel takes the staged count recorded by the compaction
         bin_kernel<<<152 * 16, NT, 0, st>>>(a, s, -1, true, 0, a.ncell, a.gate);
         l += 8;

@@ -48,7 +48,8 @@ struct Geometry {
     int tx, ty, tz;
     int push_variant;         // compiled variant of the 2D particle kernel (tile shape, CTAs/SM)
     long long ncell, nwork;
-    int cap[PIC_NS];          // slots per cell per species
+    long long nunit;          // particle units: cells (2D) or tiles (3D)
+    int cap[PIC_NS];          // slots per unit per species
     int cap_stay[PIC_NS];     // of which the stay area
     int spill_cap[PIC_NS];
     long long capacity[PIC_NS];   // particles per species, all runs
@@ -58,7 +59,7 @@ struct Geometry {
 struct Layout {
     size_t total = 0;
     size_t ctl, runs, work, work_off, kin;
-    size_t so[PIC_NS][2][3], su[PIC_NS][2][3], sid[PIC_NS][2], scount[PIC_NS][2], sicount[PIC_NS][2];
+    size_t so[PIC_NS][2][3], su[PIC_NS][2][3], sid[PIC_NS][2], slc[PIC_NS][2], scount[PIC_NS][2], sicount[PIC_NS][2];
     size_t sp_cell[PIC_NS][2], sp_o[PIC_NS][2][3], sp_u[PIC_NS][2][3], sp_id[PIC_NS][2], sp_n[PIC_NS][2];
     size_t slot_region[PIC_NS][2];   // start of the contiguous slot arrays (staging view)
     std::vector<size_t> E[3], B[3], J[3], Jlast[3], Jf[3], msum[3], mcnt, ubar[3];   // per run
@@ -129,6 +130,8 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
         }
     }
     if (g->ncell >= (1ll << 31) - 1) { *err = "too many cells for int32 cell indices"; return PIC_EINVAL; }
+    g->nunit = c->ndim == 3 ? g->nwork : g->ncell;
+    const long long ucells = c->ndim == 3 ? (long long)g->tx * g->ty * g->tz : 1;   // cells per unit
     for (int s = 0; s < PIC_NS; ++s) {
         g->cap[s] = 0;
         g->cap_stay[s] = 0;
@@ -138,8 +141,8 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
         const long long mean = (g->capacity[s] + g->ncell - 1) / g->ncell;
         // default slots per cell: 2D 8x the mean in warp multiples (a warp owns a cell; the
         // beam pinches to ~9x its mean density in the nonlinear filamentation stage), 3D 3x the
-        // mean in multiples of 8 (a thread per particle; 8 floats fill a 32-byte sector; the
-        // spill list takes the filaments' excess)
+        // mean in multiples of 8 (a tile holds its cells' slots together, so a filament that
+        // compresses particles inside a tile does not spill; the spill list takes the rest)
         long long cap = c->cell_capacity[s];
         if (cap <= 0) {
             cap = c->ndim == 2 ? ((8 * mean + 31) / 32) * 32 : ((3 * mean + 7) / 8) * 8;
@@ -148,13 +151,17 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
         if (cap < 2 || cap > 65535) { *err = "cell_capacity must be in [2, 65535]"; return PIC_EINVAL; }
         if (cap * g->ncell < 2 * g->capacity[s]) { *err = "cell_capacity must be >= 2 x capacity / cells"; return PIC_EINVAL; }
         if (cap * g->ncell >= (1ll << 31)) { *err = "cells x cell_capacity must be < 2^31"; return PIC_EINVAL; }
-        g->cap[s] = (int)cap;
+        // 3D: one slot range per tile, the tile's cells' capacities together, in blocks of 32
+        const long long ucap = c->ndim == 3 ? ((cap * ucells + PIC_BLK - 1) / PIC_BLK) * PIC_BLK : cap;
+        if (ucap * g->nunit >= (1ll << 31)) { *err = "cells x cell_capacity must be < 2^31"; return PIC_EINVAL; }
+        g->cap[s] = (int)ucap;
         // immigrant area (>= 1 slot): 2D a quarter of the slots (only particles crossing a tile
-        // edge arrive there); 3D a third in multiples of 8 slots (the beam's z flux through the
-        // bottom layer of a 4-cell-deep tile is ~half its beam particles per step, ~a quarter of
-        // the mean per cell), so that both areas start on a 32-byte sector.  The rest keeps the
-        // cell's stayers and the particles arriving from the same tile.
-        long long ci = c->ndim == 2 ? (cap + 3) / 4 : ((cap / 3 + 7) / 8) * 8;
+        // edge arrive there); 3D a quarter of the tile's slots in whole blocks (particles
+        // leaving a tile are ~7% of them per step in the hot beam: the beam's z flux through a
+        // 4-cell-deep tile's bottom layer), so that both areas start on a block.  The rest keeps
+        // the unit's stayers (in 2D also the particles arriving from the same tile).
+        long long ci = c->ndim == 2 ? (ucap + 3) / 4 : ((ucap / 4 + PIC_BLK - 1) / PIC_BLK) * PIC_BLK;
+        cap = ucap;
         if (ci < 1) ci = 1;
         if (ci >= cap) ci = cap > 1 ? cap - 1 : 0;
         g->cap_stay[s] = (int)(cap - ci);
@@ -166,14 +173,15 @@ int geometry(const pic_config* c, int nruns, const int32_t* dims, const int64_t*
     return PIC_OK;
 }
 
-// Arrays per particle slot: offsets, momenta and the optional id.
-int slot_arrays(const pic_config* c) { return c->ndim + 3 + (c->track_ids ? 1 : 0); }
+// Arrays per particle slot: offsets, momenta, the optional id and, in 3D, the cell within the tile.
+int slot_arrays(const pic_config* c) { return c->ndim + 3 + (c->track_ids ? 1 : 0) + (c->ndim == 3 ? 1 : 0); }
 
 Layout make_layout(const pic_config* c, const Geometry& g) {
     Layout L{};
     size_t off = 0;
     const int nruns = (int)g.runs.size();
     const long long nc = g.ncell;
+    const long long nu = g.nunit;
     L.ctl = take(off, sizeof(Ctl));
     L.runs = take(off, sizeof(RunDev) * nruns);
     L.work = take(off, sizeof(int2) * g.nwork);
@@ -183,15 +191,16 @@ Layout make_layout(const pic_config* c, const Geometry& g) {
         for (int b = 0; b < 2; ++b) {
             // slot arrays in blocks of PIC_BLK slots (see Slots): array d of block k at
             // region + (k * na + d) * PIC_BLK floats
-            const long long nblk = (nc * g.cap[s] + PIC_BLK - 1) / PIC_BLK;
+            const long long nblk = (nu * g.cap[s] + PIC_BLK - 1) / PIC_BLK;
             const int na = slot_arrays(c);
             const size_t r0 = take(off, (size_t)4 * nblk * na * PIC_BLK);
             L.slot_region[s][b] = r0;
             for (int d = 0; d < 3; ++d) L.so[s][b][d] = d < c->ndim ? r0 + (size_t)4 * PIC_BLK * d : 0;
             for (int d = 0; d < 3; ++d) L.su[s][b][d] = r0 + (size_t)4 * PIC_BLK * (c->ndim + d);
             L.sid[s][b] = c->track_ids ? r0 + (size_t)4 * PIC_BLK * (c->ndim + 3) : 0;
-            L.scount[s][b] = take(off, 4 * nc);
-            L.sicount[s][b] = take(off, 4 * nc);
+            L.slc[s][b] = c->ndim == 3 ? r0 + (size_t)4 * PIC_BLK * (c->ndim + 3 + (c->track_ids ? 1 : 0)) : 0;
+            L.scount[s][b] = take(off, 4 * nu);
+            L.sicount[s][b] = take(off, 4 * nu);
             const long long sp = g.spill_cap[s];
             L.sp_cell[s][b] = take(off, 4 * sp);
             for (int d = 0; d < 3; ++d) L.sp_o[s][b][d] = d < c->ndim ? take(off, 4 * sp) : 0;
@@ -511,6 +520,7 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
         RunDev& R = ctx->runs[r];
         R.nx = G.nx; R.ny = G.ny; R.nz = G.nz;
         R.ntx = G.ntx; R.nty = G.nty; R.ntz = G.ntz;
+        R.work_off = (int)G.work_off;
         R.cell_off = (int)G.cell_off;
         R.dtdx = (float)(c.dt / c.dx); R.dtdy = (float)(c.dt / c.dy); R.dtdz = (float)(c.dt / c.dz);
         R.cx = R.dtdx; R.cy = R.dtdy; R.cz = R.dtdz;
@@ -561,6 +571,7 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
                 S.su[d] = at<float>(ctx, L.sp_u[s][b][d]);
             }
             S.id = L.sid[s][b] ? at<int>(ctx, L.sid[s][b]) : nullptr;
+            S.lc = L.slc[s][b] ? at<int>(ctx, L.slc[s][b]) : nullptr;
             S.bstride = (long long)slot_arrays(&c) * PIC_BLK;
             S.count = at<int>(ctx, L.scount[s][b]);
             S.icount = at<int>(ctx, L.sicount[s][b]);
@@ -572,6 +583,7 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
         }
     }
     a.ncell = g.ncell;
+    a.nunit = g.nunit;
     a.partials = at<double>(ctx, L.partials);
     a.hist = at<DiagRec>(ctx, L.hist);
     a.hist_cap = c.diag_interval > 0 ? c.diag_capacity : 1;
@@ -596,6 +608,10 @@ int init_common(const pic_config* cfg, int nruns, const int32_t* dims, const int
     return PIC_OK;
 }
 
+// A run's particle units: its cells (2D) or its tiles (3D).
+long long unit_off(const pic_ctx* ctx, const RunGeo& G) { return ctx->cfg.ndim == 3 ? G.work_off : G.cell_off; }
+long long unit_n(const pic_ctx* ctx, const RunGeo& G) { return ctx->cfg.ndim == 3 ? G.ntiles : G.ncell; }
+
 // Publish the drag moment arrays of run `run` and set the cell means <u> of species s from its
 // loaded particles (the drag of the first step uses them).
 int start_drag(pic_ctx* ctx, int run, int s) {
@@ -610,7 +626,7 @@ int start_drag(pic_ctx* ctx, int run, int s) {
     }
     int rc = upload_runs(ctx);
     if (rc) return rc;
-    CK(launch_moments_init(ctx->args, s, run, G.cell_off, G.ncell, ctx->stream));
+    CK(launch_moments_init(ctx->args, s, run, unit_off(ctx, G), unit_n(ctx, G), ctx->stream));
     CK(launch_moments_finalize(ctx->args, run, G.ncell, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return device_flags(ctx);
@@ -654,8 +670,8 @@ int load_run(pic_ctx* ctx, int run, int s, const pic_species* sp, int64_t n, con
     if (rc) {
         // undo: empty the run's cells of this species and clear the flag
         const Slots& S = ctx->args.slot[s][h.parity];
-        CK(cudaMemsetAsync(S.count + G.cell_off, 0, 4 * G.ncell, ctx->stream));
-        CK(cudaMemsetAsync(S.icount + G.cell_off, 0, 4 * G.ncell, ctx->stream));
+        CK(cudaMemsetAsync(S.count + unit_off(ctx, G), 0, 4 * unit_n(ctx, G), ctx->stream));
+        CK(cudaMemsetAsync(S.icount + unit_off(ctx, G), 0, 4 * unit_n(ctx, G), ctx->stream));
         Ctl z;
         int rc2 = read_ctl(ctx, &z);
         if (rc2) return rc2;
@@ -835,8 +851,9 @@ extern "C" int pic_get_particles_run(pic_ctx* ctx, int run, int s, int32_t* cell
     rc = pic_sync(ctx);
     if (rc) return rc;
     const RunGeo& G = ctx->geo.runs[run];
-    // compaction of the run's cells into the staging area (cell order, then its spill entries)
-    CK(launch_compact(ctx->args, s, G.cell_off, G.ncell, G.cell_off, nullptr, ctx->stream));
+    // compaction of the run's units into the staging area (unit order, then its spill entries)
+    CK(launch_compact(ctx->args, s, unit_off(ctx, G), unit_n(ctx, G), G.cell_off, G.ncell, G.cell_off, nullptr,
+                      ctx->stream));
     ctx->launches += 6;
     Ctl h;
     rc = read_ctl(ctx, &h);
@@ -965,7 +982,7 @@ extern "C" int pic_get_stats(pic_ctx* ctx, pic_stats* out) {
     int rc = read_ctl(ctx, &h);
     if (rc) return rc;
     std::memset(out, 0, sizeof(*out));
-    std::vector<int> cnt((size_t)ctx->geo.ncell), icnt((size_t)ctx->geo.ncell);
+    std::vector<int> cnt((size_t)ctx->geo.nunit), icnt((size_t)ctx->geo.nunit);
     for (int s = 0; s < ctx->cfg.nspecies; ++s) {
         const Slots& S = ctx->args.slot[s][h.parity];
         CK(cudaMemcpyAsync(cnt.data(), S.count, 4 * cnt.size(), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1478,7 +1495,7 @@ extern "C" int pic_autotune(pic_ctx* ctx, int steps_per_variant, pic_tune_entry*
 namespace {
 
 constexpr char kCkptMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;   // 2: 3D particles binned by tile
 constexpr size_t kCkptChunk = size_t(64) << 20;
 
 struct CkptHeader {

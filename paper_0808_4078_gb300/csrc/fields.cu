@@ -212,18 +212,29 @@ __global__ void moments_finalize_kernel(const RunDev* __restrict__ runs, int run
     }
 }
 
-// Drag moments of the loaded particles of species s in cells [c0, c0 + nc) of run `run` (NGP
-// cell = the slot's cell), current buffer.
-__global__ void moments_init_kernel(Args a, int s, int run, long long c0, long long nc) {
+// Drag moments of the loaded particles of species s in units [u0, u0 + nu) of run `run` (NGP
+// cell = the particle's cell), current buffer, and the run's spill entries.
+__global__ void moments_init_kernel(Args a, int s, int run, long long u0, long long nu) {
     const RunDev& R = a.runs[run];
     if (!R.sp[s].drag || !R.msum[0]) return;
     const Slots S = a.slot[s][a.ctl->parity];
     const int cap = a.cap[s], cs = a.cap_stay[s];
     const float ms = 1048576.0f;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nc;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nu;
          k += (long long)gridDim.x * blockDim.x) {
-        const long long c = c0 + k;
+        const long long c = u0 + k;
         const CellRange cr = cell_range(S, cap, cs, c);
+        if (S.lc) {
+            // 3D: a tile; each particle adds to its own cell
+            for (int i = 0; i < cr.n; ++i) {
+                const size_t q = slot_elt(S, (long long)slot_of(c, cap, cs, cr.ns, i));
+                const long long lc = cell_of_unit(a, R, c, S.lc[q]) - R.cell_off;
+                for (int d = 0; d < 3; ++d)
+                    atomicAdd((unsigned long long*)&R.msum[d][lc], (unsigned long long)__float2ll_rn(S.u[d][q] * ms));
+                atomicAdd(&R.mcnt[lc], 1);
+            }
+            continue;
+        }
         long long m[3] = {0, 0, 0};
         for (int i = 0; i < cr.n; ++i)
             for (int d = 0; d < 3; ++d) m[d] += __float2ll_rn(S.u[d][slot_elt(S, (long long)slot_of(c, cap, cs, cr.ns, i))] * ms);
@@ -231,6 +242,7 @@ __global__ void moments_init_kernel(Args a, int s, int run, long long c0, long l
         for (int d = 0; d < 3; ++d) atomicAdd((unsigned long long*)&R.msum[d][lc], (unsigned long long)m[d]);
         atomicAdd(&R.mcnt[lc], cr.n);
     }
+    const long long c0 = R.cell_off, nc = (long long)R.nx * R.ny * R.nz;
     const int ns = min(*S.sn, a.spill_cap[s]);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ns; k += gridDim.x * blockDim.x) {
         const long long c = S.scell[k];
@@ -421,9 +433,9 @@ cudaError_t launch_finalize(const Args& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments_init(const Args& a, int species, int run, long long c0, long long nc,
+cudaError_t launch_moments_init(const Args& a, int species, int run, long long u0, long long nu,
                                 cudaStream_t s) {
-    moments_init_kernel<<<grid_for(nc), NT, 0, s>>>(a, species, run, c0, nc);
+    moments_init_kernel<<<grid_for(nu), NT, 0, s>>>(a, species, run, u0, nu);
     return cudaGetLastError();
 }
 

@@ -152,7 +152,7 @@ __device__ __forceinline__ void coarse_means(const MomArgs& m, long long cc, Mea
         }
 }
 
-// One CTA per (coarse cell, z chunk): a thread per fine cell, all its particles; one kernel per
+// 2D (particles binned by cell): one CTA per (coarse cell, z chunk): a thread per fine cell, all its particles; one kernel per
 // pass, each holding only its own sums (pass 2 with its field gathers runs 2 CTAs per SM without
 // spilling, measured faster than 3 with spills).
 template <int PASS>
@@ -201,6 +201,73 @@ __global__ void __launch_bounds__(NT, PASS == 1 ? 3 : 2) mom_particles(const Mom
         long long v = 0;
         for (int w = 0; w < NT / 32; ++w) v += red[w][threadIdx.x];
         if (v) atomicAdd((unsigned long long*)&m.psum[(size_t)(B + threadIdx.x) * m.ncx * m.ncy + cc], (unsigned long long)v);
+    }
+}
+
+// 3D (particles binned by tile): one CTA per tile of the run, a thread per particle of its list.
+// A tile covers at most 8 x 8 coarse columns; each thread sums in registers while its particles'
+// column stays the same and adds the sums to the tile's shared accumulators when it changes,
+// and the tile adds its nonzero sums to psum at the end.
+template <int PASS>
+__global__ void __launch_bounds__(NT, PASS == 1 ? 3 : 2) mom_tiles(const MomArgs m) {
+    constexpr int B = PassRows<PASS>::base, NR = PassRows<PASS>::n;
+    constexpr int MAXC = 64;
+    __shared__ unsigned long long sacc[MAXC][NR];
+    const Args& a = m.a;
+    const RunDev& R = a.runs[m.run];
+    const long long T = R.work_off + blockIdx.x;
+    const int t = blockIdx.x;
+    const int x0 = (t % R.ntx) * a.tx, y0 = ((t / R.ntx) % R.nty) * a.ty, z0 = (t / (R.ntx * R.nty)) * a.tz;
+    const int cx0 = x0 / m.bx, cy0 = y0 / m.by;
+    const int ncxl = (x0 + a.tx - 1) / m.bx - cx0 + 1, ncyl = (y0 + a.ty - 1) / m.by - cy0 + 1;
+    const int ncl = ncxl * ncyl;   // <= 64: a tile is at most 8 cells wide
+    for (int i = threadIdx.x; i < ncl * NR; i += NT) (&sacc[0][0])[i] = 0ull;
+    __syncthreads();
+    const long long nc = (long long)m.ncx * m.ncy;
+    const int par = a.ctl->parity;
+    const int cells = a.tx * a.ty * a.tz;
+    long long acc[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) acc[k] = 0;
+    int cur = -1;
+    Mean2 mean{};
+    auto flush = [&]() {
+        if (cur < 0) return;
+#pragma unroll
+        for (int k = 0; k < NR; ++k)
+            if (acc[k]) {
+                atomicAdd(&sacc[cur][k], (unsigned long long)acc[k]);
+                acc[k] = 0;
+            }
+    };
+    for (int s = 0; s < a.nspecies && s < 2; ++s) {
+        if (!R.sp[s].active) continue;
+        const Slots& S = a.slot[s][par];
+        const CellRange cr = cell_range(S, a.cap[s], a.cap_stay[s], T);
+        const float w = R.sp[s].w;
+        for (int k = threadIdx.x; k < cr.n; k += NT) {
+            const size_t q = slot_elt(S, (long long)slot_of(T, a.cap[s], a.cap_stay[s], cr.ns, k));
+            const int lc = S.lc[q] % cells;
+            const int cx = x0 + lc % a.tx, cy = y0 + (lc / a.tx) % a.ty, cz = z0 + lc / (a.tx * a.ty);
+            const int cl = (cy / m.by - cy0) * ncxl + (cx / m.bx - cx0);
+            if (cl != cur) {
+                flush();
+                cur = cl;
+                if (PASS == 2) coarse_means(m, (long long)(cy / m.by) * m.ncx + cx / m.bx, mean);
+            }
+            add_particle<PASS>(m, R, s, w, mean, cx, cy, cz, S.o[0][q], S.o[1][q], S.o[2][q], S.u[0][q], S.u[1][q],
+                               S.u[2][q], acc);
+        }
+    }
+    flush();
+    __syncthreads();
+    for (int i = threadIdx.x; i < ncl * NR; i += NT) {
+        const int cl = i / NR, k = i - cl * NR;
+        const unsigned long long v = sacc[cl][k];
+        if (v) {
+            const long long cc = (long long)(cy0 + cl / ncxl) * m.ncx + (cx0 + cl % ncxl);
+            atomicAdd((unsigned long long*)&m.psum[(size_t)(B + k) * nc + cc], v);
+        }
     }
 }
 
@@ -347,10 +414,13 @@ cudaError_t launch_moments(const Args& a, const RunDev& host_run, int run, int b
     cudaError_t e = cudaMemsetAsync(m.psum, 0, (size_t)nc * MOM_PSUMS * sizeof(long long), s);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)nc, (unsigned)((nz + m.zc - 1) / m.zc));
-    mom_particles<1><<<grid, NT, 0, s>>>(m);
+    const unsigned ntiles = (unsigned)host_run.ntx * host_run.nty * host_run.ntz;
+    if (a.ndim == 3) mom_tiles<1><<<ntiles, NT, 0, s>>>(m);
+    else mom_particles<1><<<grid, NT, 0, s>>>(m);
     mom_spill<1><<<152, NT, 0, s>>>(m);
     mom_means<<<grid_of(nc), NT, 0, s>>>(m);
-    mom_particles<2><<<grid, NT, 0, s>>>(m);
+    if (a.ndim == 3) mom_tiles<2><<<ntiles, NT, 0, s>>>(m);
+    else mom_particles<2><<<grid, NT, 0, s>>>(m);
     mom_spill<2><<<152, NT, 0, s>>>(m);
     mom_columns<<<grid_of((long long)host_run.nx * host_run.ny), NT, 0, s>>>(m);
     mom_finalize<<<grid_of(nc), NT, 0, s>>>(m);
@@ -361,6 +431,8 @@ cudaError_t preload_moments() {
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, mom_particles<1>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_particles<2>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_tiles<1>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_tiles<2>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_spill<1>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_spill<2>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mom_means);

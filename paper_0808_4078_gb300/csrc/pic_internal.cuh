@@ -1,13 +1,14 @@
 // pic_internal.cuh -- device-side data structures shared by the libpic kernels.
 //
 // Layout in HBM (all carved from the caller's arena):
-//   particles  cell-binned: species s keeps, per cell, a slot range of fixed capacity cap[s]
-//              holding that cell's particles contiguously (SoA: offsets float x ndim,
-//              momenta float x 3, optional id int32) plus a per-cell count.  The cell index is
-//              implied by the slot, so it is not stored.  Two buffers: every step reads buffer
-//              `parity` and writes each particle into its new cell's slots of the other buffer
-//              (a counting sort fused into the push).  Particles that find their new cell full
-//              go to a per-species spill list (cell index stored), processed by its own kernel.
+//   particles  binned by unit (2D: a cell; 3D: a tile of the 3D particle kernel): species s
+//              keeps, per unit, a slot range of fixed capacity cap[s] holding that unit's
+//              particles (SoA: offsets float x ndim, momenta float x 3, optional id int32, and in
+//              3D the particle's cell within its tile) plus per-unit counts.  In 2D the cell
+//              index is implied by the slot.  Two buffers: every step reads buffer `parity` and
+//              writes each particle into its new unit's slots of the other buffer (a counting
+//              sort fused into the push).  Particles that find their new unit full go to a
+//              per-species spill list (cell index stored), processed by its own kernel.
 //   fields     E[3], B[3] float per cell; J[3] int64 fixed point per cell.
 //   drag       per cell: sum u (3 x int64, fixed point 2^20), count int32, and the cell-mean
 //              momentum <u> (3 x float) of the previous step used by the Krook drag.
@@ -54,6 +55,7 @@ struct SpeciesParams {
 struct RunDev {
     int nx, ny, nz;
     int ntx, nty, ntz;      // tiles per axis
+    int work_off;           // global index of the run's first tile (= its first work item)
     int cell_off;           // offset of this run's cells in the global cell space
     int shift;              // fixed-point shift S of J
     float dtdx, dtdy, dtdz; // dt / dx: displacement in cells per unit velocity per step
@@ -73,11 +75,14 @@ struct RunDev {
 };
 
 
-// One species in one buffer.  A cell's cap slots are a stay area [0, cap_stay), filled by the CTA
-// that owns the cell's tile (count = its fill: the cell's stayers and, in 2D, the particles that
-// reach it from other cells of the same tile), and an immigrant area [cap_stay, cap) that the
-// other particles arriving in the cell claim with an atomic counter (icount).  Counters may
-// exceed their area; readers clamp them (the excess went to the spill list).
+// One species in one buffer.  A unit's cap slots are a stay area [0, cap_stay), filled by the
+// CTA that owns the unit's tile (count = its fill: in 2D the cell's stayers and the particles
+// that reach it from other cells of the same tile; in 3D every particle that ends the step in
+// the tile it started in), and an immigrant area [cap_stay, cap) that the other particles
+// arriving in the unit claim with an atomic counter (icount).  Counters may exceed their area;
+// readers clamp them (the excess went to the spill list).  A unit is a cell in 2D and a tile in
+// 3D (unit index = global tile index = the tile's work item; lc holds each particle's cell
+// within the tile, x fastest).
 // Slot arrays are stored in blocks of PIC_BLK consecutive slots: a block holds PIC_BLK values of
 // each array in turn (o_x, o_y[, o_z], u_x, u_y, u_z[, id]), so that one address per particle
 // reaches all its values and a warp reading 32 consecutive slots reads whole 128-byte lines.  Slot
@@ -86,9 +91,10 @@ struct Slots {
     float* o[3];     // offsets (x, y[, z])
     float* u[3];     // momenta
     int* id;         // or null
+    int* lc;         // 3D: cell of the particle within its tile; null in 2D
     long long bstride;   // floats per block (PIC_BLK x arrays)
-    int* count;      // [ncell] stay-area fill
-    int* icount;     // [ncell] immigrant-area fill
+    int* count;      // [nunit] stay-area fill
+    int* icount;     // [nunit] immigrant-area fill
     // spill list (particles whose cell was full)
     int* scell;      // global cell index
     float* so[3];
@@ -130,10 +136,11 @@ struct Args {
     int nruns;
     int ndim;
     Slots slot[PIC_NS][2];
-    int cap[PIC_NS];             // slots per cell
+    int cap[PIC_NS];             // slots per unit (2D: cell, 3D: tile)
     int cap_stay[PIC_NS];        // of which the stay area
     int spill_cap[PIC_NS];
     long long ncell;             // total cells (all runs)
+    long long nunit;             // total units (2D: ncell, 3D: nwork)
     double* partials;            // [nwork][8] field-energy partials of a diag step
     DiagRec* hist;               // [nruns][hist_cap]
     int hist_cap;
@@ -191,7 +198,7 @@ __host__ __device__ inline Stage stage_of(const Args& a, int s, int par) {
     return t;
 }
 
-// Particles of cell c: n = stay part + immigrant part; element k lives in slot slot_of(k).
+// Particles of unit c: n = stay part + immigrant part; element k lives in slot slot_of(k).
 struct CellRange {
     int ns, n;
 };
@@ -212,6 +219,48 @@ __host__ __device__ __forceinline__ size_t slot_elt(const Slots& S, long long q)
 __device__ __forceinline__ int wrapi(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;
+}
+
+// Run holding global cell g (runs are stored in cell order).
+__device__ __forceinline__ int run_of_cell(const Args& a, long long g) {
+    int lo = 0, hi = a.nruns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.runs[mid].cell_off <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+// Run holding global tile (unit) T.
+__device__ __forceinline__ int run_of_unit(const Args& a, long long T) {
+    int lo = 0, hi = a.nruns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.runs[mid].work_off <= T) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+// Unit of global cell g and, in 3D, the cell's index within its tile (*lc).
+__device__ __forceinline__ long long unit_of_cell(const Args& a, long long g, int* lc) {
+    if (a.ndim != 3) {
+        *lc = 0;
+        return g;
+    }
+    const RunDev& R = a.runs[run_of_cell(a, g)];
+    const long long l = g - R.cell_off;
+    const long long nxy = (long long)R.nx * R.ny;
+    const int z = (int)(l / nxy), rem = (int)(l - (long long)z * nxy);
+    const int y = rem / R.nx, x = rem - y * R.nx;
+    const int tx = x / a.tx, ty = y / a.ty, tz = z / a.tz;
+    *lc = ((z - tz * a.tz) * a.ty + (y - ty * a.ty)) * a.tx + (x - tx * a.tx);
+    return R.work_off + ((long long)tz * R.nty + ty) * R.ntx + tx;
+}
+// Global cell of the particle with in-tile cell lc in 3D unit T of run R.
+__device__ __forceinline__ long long cell_of_unit(const Args& a, const RunDev& R, long long T, int lc) {
+    const long long t = T - R.work_off;
+    const int tx = (int)(t % R.ntx), ty = (int)((t / R.ntx) % R.nty), tz = (int)(t / ((long long)R.ntx * R.nty));
+    lc %= a.tx * a.ty * a.tz;
+    const int lx = lc % a.tx, ly = (lc / a.tx) % a.ty, lz = lc / (a.tx * a.ty);
+    return R.cell_off + ((long long)(tz * a.tz + lz) * R.ny + (ty * a.ty + ly)) * R.nx + (tx * a.tx + lx);
 }
 
 // Round a*b to the nearest integer (ties to even) for |a*b| < 2^22 with one FFMA: adding
@@ -246,18 +295,19 @@ cudaError_t launch_yee2d(const Args& a, const RunDev* host_runs, int nruns, cuda
 cudaError_t launch_yee3d(const Args& a, const RunDev* host_runs, int nruns, cudaStream_t s);
 cudaError_t launch_finalize(const Args& a, cudaStream_t s);   // per-run records, then step++, flip
 cudaError_t launch_clear_next(const Args& a, cudaStream_t s);
-// Counting sort into the per-cell slots and its inverse.  All use the device parity: the
+// Counting sort into the per-unit slots and its inverse.  All use the device parity: the
 // current buffer's slots and the staging area in the other buffer's memory.  `gate` (device int,
 // may be null) makes the kernels return at once when it holds 0.
 //   launch_bin:     staging (n particles; n < 0: the count of the last compaction) -> slots of
 //                   the current buffer; staged cells are cell_base + value, valid if value is in
 //                   [0, ncell_lim); ids kept if with_ids, else the staging index
-//   launch_compact: the slots (and spill entries) of cells [c0, c0 + nc) of the current buffer
-//                   -> staging in cell order, cell values written minus cell_base
+//   launch_compact: the slots of units [c0, c0 + nc) and the spill entries of cells
+//                   [cell_lo, cell_lo + ncells) of the current buffer -> staging in unit order,
+//                   cell values written minus cell_base
 cudaError_t launch_bin(const Args& a, int species, long long n, bool with_ids, long long cell_base,
                        long long ncell_lim, const int* gate, cudaStream_t s);
-cudaError_t launch_compact(const Args& a, int species, long long c0, long long nc, long long cell_base,
-                           const int* gate, cudaStream_t s);
+cudaError_t launch_compact(const Args& a, int species, long long c0, long long nc, long long cell_lo,
+                           long long ncells, long long cell_base, const int* gate, cudaStream_t s);
 cudaError_t launch_spill_gate(const Args& a, cudaStream_t s);
 cudaError_t launch_clear_current(const Args& a, int species, const int* gate, cudaStream_t s);
 // Standalone counting sort by cell (pic_bin_cells): scratch = count/cursor[ncell] + block sums.
@@ -268,7 +318,9 @@ cudaError_t launch_bin_cells(const int* cell, long long n, int ncell, int* start
 cudaError_t noalloc_bin_scratch(int** out);
 // Full re-sort of every species (compact, clear, bin) when any particle is in a spill list.
 cudaError_t launch_resort(const Args& a, cudaStream_t s, int* launches);
-cudaError_t launch_moments_init(const Args& a, int species, int run, long long c0, long long nc,
+// Drag moments of the loaded particles of `species` in run `run` (units [u0, u0 + nu) of the
+// current buffer and the run's spill entries).
+cudaError_t launch_moments_init(const Args& a, int species, int run, long long u0, long long nu,
                                 cudaStream_t s);
 cudaError_t launch_moments_finalize(const Args& a, int run, long long ncell, cudaStream_t s);
 // Moment recorder (moments.cu): scratch bytes for nc coarse cells and ncol columns, and the

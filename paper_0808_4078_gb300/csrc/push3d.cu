@@ -3,15 +3,19 @@
 // int64 fixed point) and rebinning of every particle into its new cell's slots of the other
 // buffer.
 //
-// One CTA of 256 threads per (run, tile) of 8 x 8 x 4 cells.  The tile's particles (both
-// species, all cells) form one flat list; the CTA walks it in batches of 512, one particle per
-// thread per half batch.  In three dimensions a large share of the beam crosses a cell edge
+// One CTA of 256 threads per (run, tile) of 8 x 8 x 4 cells.  Particles are binned by tile: a
+// tile's slot range holds its particles in any order, each with its cell within the tile, so
+// that a CTA reads and writes whole sectors (a cell's ~8 particles per species filled less than
+// a sector of each array, and partly written sectors are read back from DRAM).  The CTA walks
+// its list in batches of 512, one particle per thread per half batch.  In three dimensions a large share of the beam crosses a cell edge
 // every step (v_z dt / dz ~ 0.47), so there is no per-cell fast path: every particle deposits
 // its (up to) 3 x 18 current terms with predicated 32-bit shared reductions.  A batch adds at most 512 terms
 // of magnitude <= 2^21 to any node, so the int32 accumulators cannot overflow; after each batch
 // they are moved into an int64 shared bank (each thread owns fixed nodes, no atomics).  Particles
-// that stay inside the tile claim their new slot through a shared per-cell counter; only those
-// leaving the tile use global atomics (the destination cell's immigrant area).
+// that stay inside the tile take the next places of the tile's stay area through a shared
+// counter (one claim per warp and species); those leaving the tile claim places in the
+// destination tile's immigrant area with one global atomic per destination among a warp's
+// leavers.
 #include "particle_math.cuh"
 #include "pic_internal.cuh"
 
@@ -28,19 +32,17 @@ constexpr int BATCH = NT * PER_THREAD;   // particles per int32 accumulation rou
 constexpr unsigned FULL = 0xffffffffu;
 
 static_assert(CELLS == NT, "one thread per tile cell in the setup loops");
-static_assert(PIC_NS * CELLS <= 65535, "owner entries fit 16 bits");
+static_assert((CELLS & (CELLS - 1)) == 0, "in-tile cell indices are masked with CELLS - 1");
 
 struct Smem {
     float F[6][RN];                  // Ex Ey Ez Bx By Bz of the region (origin: tile - 1 cell)
     int J32[3][RN];                  // current of the running batch
     long long J64[3][RN];            // current of the finished batches
-    int pre[PIC_NS * CELLS + 1];     // exclusive prefix of the (species, cell) particle counts
-    int cns[PIC_NS * CELLS];         // of which in the stay area
-    int scnt[PIC_NS * CELLS];        // stay-area fill of the tile's cells in the next buffer
-    unsigned short owner[BATCH];     // (species, cell) entry of each particle of the batch
     double red[NW][6];
     unsigned long long kin[5];
-    int wsum[NW];
+    int ln[PIC_NS];                  // particles of the tile's list per species (current buffer)
+    int lns[PIC_NS];                 // of which in its stay area
+    int sfill[PIC_NS];               // stay-area fill of the tile in the next buffer
     SpeciesParams sp[PIC_NS];
     // drag arrays last: a launch without drag allocates the shared memory up to `ub` only
     float ub[3][RN];                 // previous cell-mean momentum (drag)
@@ -221,71 +223,63 @@ __device__ __forceinline__ void red_shared_nz(int* p, int v) {
 }
 
 // ------------------------------------------------------------------ rebinning
-__device__ __forceinline__ void store3(const Slots& D, size_t slot, const float o[3], float ux, float uy,
-                                       float uz, int id) {
-    const size_t q = slot_elt(D, (long long)slot);
+// Slot `slot` of buffer D (a tile's slot range; lc = the particle's cell within the tile).
+__device__ __forceinline__ void store3(const Slots& D, long long slot, const float o[3], float ux, float uy,
+                                       float uz, int id, int lc) {
+    const size_t q = slot_elt(D, slot);
     D.o[0][q] = o[0]; D.o[1][q] = o[1]; D.o[2][q] = o[2];
     D.u[0][q] = ux; D.u[1][q] = uy; D.u[2][q] = uz;
     if (D.id) D.id[q] = id;
+    D.lc[q] = lc;
 }
 
-// Particle arriving in cell g of buffer D from elsewhere: claim an immigrant slot, else spill.
-__device__ __forceinline__ void put_imm3(const Slots& D, int cap, int cap_stay, int spill_cap, long long g,
-                                         const float o[3], float ux, float uy, float uz, int id, int* err) {
-    const int pi = atomicAdd(&D.icount[g], 1);
-    if (pi < cap - cap_stay) {
-        store3(D, (size_t)g * cap + cap_stay + pi, o, ux, uy, uz, id);
+// Spill-list entry of buffer D (global cell g).
+__device__ __forceinline__ void spill3(const Slots& D, int spill_cap, long long g, const float o[3], float ux,
+                                       float uy, float uz, int id, int* err) {
+    const int sp = atomicAdd(D.sn, 1);
+    if (sp < spill_cap) {
+        D.scell[sp] = (int)g;
+        D.so[0][sp] = o[0]; D.so[1][sp] = o[1]; D.so[2][sp] = o[2];
+        D.su[0][sp] = ux; D.su[1][sp] = uy; D.su[2][sp] = uz;
+        if (D.sid) D.sid[sp] = id;
     } else {
-        const int sp = atomicAdd(D.sn, 1);
-        if (sp < spill_cap) {
-            D.scell[sp] = (int)g;
-            D.so[0][sp] = o[0]; D.so[1][sp] = o[1]; D.so[2][sp] = o[2];
-            D.su[0][sp] = ux; D.su[1][sp] = uy; D.su[2][sp] = uz;
-            if (D.sid) D.sid[sp] = id;
-        } else {
-            atomicOr(err, ERR_SPILL_FULL);
-        }
+        atomicOr(err, ERR_SPILL_FULL);
     }
+}
+
+// Particle arriving in tile (unit) T of buffer D from elsewhere, claim pi of its immigrant area
+// already taken: store it, or spill it when the area is full.
+__device__ __forceinline__ void put_claimed3(const Slots& D, int cap, int cap_stay, int spill_cap, long long T,
+                                             int pi, int lc, long long g, const float o[3], float ux, float uy,
+                                             float uz, int id, int* err) {
+    if (pi < cap - cap_stay) store3(D, T * cap + cap_stay + pi, o, ux, uy, uz, id, lc);
+    else spill3(D, spill_cap, g, o, ux, uy, uz, id, err);
+}
+// The same with its own claim.
+__device__ __forceinline__ void put_imm3(const Slots& D, int cap, int cap_stay, int spill_cap, long long T, int lc,
+                                         long long g, const float o[3], float ux, float uy, float uz, int id,
+                                         int* err) {
+    put_claimed3(D, cap, cap_stay, spill_cap, T, atomicAdd(&D.icount[T], 1), lc, g, o, ux, uy, uz, id, err);
 }
 
 __device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// Exclusive prefix sum of one int per thread over the CTA; *total gets the sum.  wsum: NW ints
-// of shared scratch.  Contains barriers: every thread must call it.
-__device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += t;
-    }
-    __syncthreads();                       // wsum free (a previous call may still read it)
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    int base = 0, tot = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        const int x = wsum[w];
-        base += w < warp ? x : 0;
-        tot += x;
-    }
-    *total = tot;
-    return base + incl - v;
-}
-
 // ------------------------------------------------------------------ tile kernel
+// One CTA per tile (unit blockIdx.x).  The tile's particles are its list in the current buffer:
+// species 0, then species 1, each the stay area's filled part then the immigrant area's.
 template <bool DRAG>
 __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const int2 wk = a.work[blockIdx.x];
+    const long long unit = blockIdx.x;
     const RunDev* Rp = &a.runs[wk.x];
     const RunConst K = run_const(Rp);
     const int nx = K.nx, ny = K.ny, nz = K.nz;
     const int tile = wk.y;
     const int tx = tile % Rp->ntx, tyz = tile / Rp->ntx;
-    const int x0 = tx * TX, y0 = (tyz % Rp->nty) * TY, z0 = (tyz / Rp->nty) * TZ;
+    const int ttx = tx, tty = tyz % Rp->nty, ttz = tyz / Rp->nty;
+    const int x0 = ttx * TX, y0 = tty * TY, z0 = ttz * TZ;
     const int gx0 = x0 - 1, gy0 = y0 - 1, gz0 = z0 - 1;
     const long long step = a.ctl->step;
     const int par = a.ctl->parity;
@@ -293,6 +287,7 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
     const bool anydrag = DRAG && Rp->msum[0] != nullptr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long cbase = K.cell_off;
+    const unsigned lt = (1u << lane) - 1u;
 
     for (int i = tid; i < RN; i += NT) {
         const int rz = i / RXY, rr = i - rz * RXY, ry = rr / RX, rx = rr - ry * RX;
@@ -315,30 +310,13 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
         }
     }
     if (tid < 5) sm.kin[tid] = 0ull;
-    if (tid < PIC_NS) sm.sp[tid] = Rp->sp[tid];
-    // particle counts of the tile's cells: thread tid owns cell tid of each species
-    int cnt_own[PIC_NS];
-    {
-        const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
-        const long long g = cbase + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
-#pragma unroll
-        for (int s = 0; s < PIC_NS; ++s) {
-            CellRange cr{0, 0};
-            if (s < a.nspecies && Rp->sp[s].active) cr = cell_range(a.slot[s][par], a.cap[s], a.cap_stay[s], g);
-            cnt_own[s] = cr.n;
-            sm.cns[s * CELLS + tid] = cr.ns;
-            sm.scnt[s * CELLS + tid] = 0;
-        }
-    }
-    // exclusive prefix over entries e = s * CELLS + cell (species-major)
-    {
-        int tot0;
-        const int ex0 = block_exclusive_scan(cnt_own[0], sm.wsum, &tot0);
-        int tot1;
-        const int ex1 = block_exclusive_scan(cnt_own[1], sm.wsum, &tot1);
-        sm.pre[tid] = ex0;
-        sm.pre[CELLS + tid] = tot0 + ex1;
-        if (tid == 0) sm.pre[PIC_NS * CELLS] = tot0 + tot1;
+    if (tid < PIC_NS) {
+        sm.sp[tid] = Rp->sp[tid];
+        CellRange cr{0, 0};
+        if (tid < a.nspecies && Rp->sp[tid].active) cr = cell_range(a.slot[tid][par], a.cap[tid], a.cap_stay[tid], unit);
+        sm.ln[tid] = cr.n;
+        sm.lns[tid] = cr.ns;
+        sm.sfill[tid] = 0;
     }
     __syncthreads();
 
@@ -368,52 +346,44 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
     }
 
     long long kacc[5] = {0, 0, 0, 0, 0};
-    const int ptot = sm.pre[PIC_NS * CELLS];
+    const int n0s = sm.ln[0], ptot = n0s + sm.ln[1];
     for (int b0 = 0; b0 < ptot; b0 += BATCH) {
-        // owner of each particle of the batch
-#pragma unroll
-        for (int r = 0; r < PIC_NS; ++r) {
-            const int e = r * CELLS + tid;
-            const int lo = max(sm.pre[e], b0), hi = min(sm.pre[e] + cnt_own[r], b0 + BATCH);
-            for (int p = lo; p < hi; ++p)
-                if (dbg_in(p - b0, BATCH, &a.ctl->err)) sm.owner[p - b0] = (unsigned short)e;
-        }
-        __syncthreads();
-        // load the thread's particles of the batch
+        // load the thread's particles of the batch (consecutive lanes: consecutive slots)
         float po[PER_THREAD][3], pu[PER_THREAD][3];
-        int pid[PER_THREAD], pe[PER_THREAD];
+        int pid[PER_THREAD], plc[PER_THREAD], psp[PER_THREAD];
         bool pact[PER_THREAD];
 #pragma unroll
         for (int r = 0; r < PER_THREAD; ++r) {
             const int p = b0 + r * NT + tid;
             pact[r] = p < ptot;
-            pe[r] = 0;
             pid[r] = 0;
+            plc[r] = 0;
+            psp[r] = 0;
             po[r][0] = po[r][1] = po[r][2] = 0.f;
             pu[r][0] = pu[r][1] = pu[r][2] = 0.f;
             if (pact[r]) {
-                const int e = sm.owner[p - b0];
-                pe[r] = e;
-                const int s = e / CELLS, ci = e - s * CELLS;
-                const int lx = ci % TX, ly = (ci / TX) % TY, lz = ci / (TX * TY);
-                const long long g = cbase + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
+                const int s = p >= n0s ? 1 : 0;
+                const int e = s ? p - n0s : p;
+                const int ns = sm.lns[s];
                 const Slots& S = a.slot[s][par];
-                const size_t q = slot_elt(S, (long long)slot_of(g, a.cap[s], a.cap_stay[s], sm.cns[e], p - sm.pre[e]));
+                const long long slot = unit * a.cap[s] + (e < ns ? e : a.cap_stay[s] + (e - ns));
+                const size_t q = slot_elt(S, slot);
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     po[r][d] = S.o[d][q];
                     pu[r][d] = S.u[d][q];
                 }
                 if (S.id) pid[r] = S.id[q];
+                plc[r] = S.lc[q];
+                psp[r] = s;
             }
         }
 #pragma unroll
         for (int r = 0; r < PER_THREAD; ++r) {
             const unsigned am = __ballot_sync(FULL, pact[r]);
             if (!pact[r]) continue;
-            const int e = pe[r];
-            const int s = e / CELLS, ci = e - s * CELLS;
-            const int lx = ci % TX, ly = (ci / TX) % TY, lz = ci / (TX * TY);
+            const int s = psp[r], lc = plc[r] & (CELLS - 1);
+            const int lx = lc % TX, ly = (lc / TX) % TY, lz = lc / (TX * TY);
             const int ix = lx + 1, iy = ly + 1, iz = lz + 1;
             const int n0 = (iz * RY + iy) * RX + ix;
             const SpeciesParams& P = sm.sp[s];
@@ -423,44 +393,65 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
             if (DRAG && P.drag && dbg_in(n0, RN, &a.ctl->err)) { b0v = sm.ub[0][n0]; b1v = sm.ub[1][n0]; b2v = sm.ub[2][n0]; }
             const long long g = cbase + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
             const float df = DRAG && P.drag ? drag_of(K, P, s, g - cbase) : 0.f;
-            const Pushed3 res = push3_one<DRAG>(SharedFields3{&sm, n0, &a.ctl->err}, P, K, po[r], pu[r][0], pu[r][1], pu[r][2],
-                                          b0v, b1v, b2v, df, s, (unsigned)pid[r], step);
-            const bool xa = __any_sync(am, res.st[0] != 0), ya = __any_sync(am, res.st[1] != 0),
-                       za = __any_sync(am, res.st[2] != 0);
-            if (res.bad) {
-                // keep the particle where it was, unmoved; the sticky flag fails the run
-                atomicOr(&a.ctl->err, ERR_BADPART);
-                put_imm3(D, cap, cst, a.spill_cap[s], g, po[r], pu[r][0], pu[r][1], pu[r][2], pid[r], &a.ctl->err);
-                continue;
+            const Pushed3 res = push3_one<DRAG>(SharedFields3{&sm, n0, &a.ctl->err}, P, K, po[r], pu[r][0], pu[r][1],
+                                                pu[r][2], b0v, b1v, b2v, df, s, (unsigned)pid[r], step);
+            const bool bad = res.bad;
+            const bool xa = __any_sync(am, !bad && res.st[0] != 0), ya = __any_sync(am, !bad && res.st[1] != 0),
+                       za = __any_sync(am, !bad && res.st[2] != 0);
+            // destination: a bad particle stays where it was, unmoved (the sticky flag fails the run)
+            const int mx = bad ? lx : lx + res.st[0], my = bad ? ly : ly + res.st[1], mz = bad ? lz : lz + res.st[2];
+            const bool inside = mx >= 0 && mx < TX && my >= 0 && my < TY && mz >= 0 && mz < TZ;
+            const float no[3] = {bad ? po[r][0] : res.no[0], bad ? po[r][1] : res.no[1], bad ? po[r][2] : res.no[2]};
+            const float nux = bad ? pu[r][0] : res.ux, nuy = bad ? pu[r][1] : res.uy, nuz = bad ? pu[r][2] : res.uz;
+            if (bad) atomicOr(&a.ctl->err, ERR_BADPART);
+            if (!bad) {
+                if (diag) kin_add(kacc, s, P.w, pu[r][0], pu[r][1], pu[r][2], res.ux, res.uy, res.uz);
+                const Win wx = window(po[r][0], res.st[0], res.no[0]);
+                const Win wy = window(po[r][1], res.st[1], res.no[1]);
+                const Win wz = window(po[r][2], res.st[2], res.no[2]);
+                const int nb = n0 + wz.off * RXY + wy.off * RX + wx.off;
+                auto add = [&](int c, int i, int j, int k, int v) {
+                    if (dbg_in(nb + k * RXY + j * RX + i, RN, &a.ctl->err))
+                        red_shared_nz(&sm.J32[c][nb + k * RXY + j * RX + i], v);
+                };
+                deposit3(add, P, wx, wy, wz, xa, ya, za);
+                const int n1 = n0 + res.st[2] * RXY + res.st[1] * RX + res.st[0];
+                if (DRAG && P.drag && dbg_in(n1, RN, &a.ctl->err)) {
+                    add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], f2ll_rn(res.ux * MOM_SCALE));
+                    add_split(&sm.Mlo[1][n1], &sm.Mhi[1][n1], f2ll_rn(res.uy * MOM_SCALE));
+                    add_split(&sm.Mlo[2][n1], &sm.Mhi[2][n1], f2ll_rn(res.uz * MOM_SCALE));
+                    atomicAdd(&sm.MC[n1], 1);
+                }
             }
-            if (diag) kin_add(kacc, s, P.w, pu[r][0], pu[r][1], pu[r][2], res.ux, res.uy, res.uz);
-            const Win wx = window(po[r][0], res.st[0], res.no[0]);
-            const Win wy = window(po[r][1], res.st[1], res.no[1]);
-            const Win wz = window(po[r][2], res.st[2], res.no[2]);
-            const int nb = n0 + wz.off * RXY + wy.off * RX + wx.off;
-            auto add = [&](int c, int i, int j, int k, int v) {
-                if (dbg_in(nb + k * RXY + j * RX + i, RN, &a.ctl->err))
-                    red_shared_nz(&sm.J32[c][nb + k * RXY + j * RX + i], v);
-            };
-            deposit3(add, P, wx, wy, wz, xa, ya, za);
-            const int n1 = n0 + res.st[2] * RXY + res.st[1] * RX + res.st[0];
-            if (DRAG && P.drag && dbg_in(n1, RN, &a.ctl->err)) {
-                add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], f2ll_rn(res.ux * MOM_SCALE));
-                add_split(&sm.Mlo[1][n1], &sm.Mhi[1][n1], f2ll_rn(res.uy * MOM_SCALE));
-                add_split(&sm.Mlo[2][n1], &sm.Mhi[2][n1], f2ll_rn(res.uz * MOM_SCALE));
-                atomicAdd(&sm.MC[n1], 1);
-            }
-            const int mx = lx + res.st[0], my = ly + res.st[1], mz = lz + res.st[2];
-            const long long g1 = cbase + ((long long)wrap1(z0 + mz, nz) * ny + wrap1(y0 + my, ny)) * nx +
-                                 wrap1(x0 + mx, nx);
-            if (mx >= 0 && mx < TX && my >= 0 && my < TY && mz >= 0 && mz < TZ) {
-                // new cell inside the tile: this CTA owns its stay area
-                const int e1 = s * CELLS + (mz * TY + my) * TX + mx;
-                const int pos = atomicAdd(&sm.scnt[e1], 1);
-                if (pos < cst) store3(D, (size_t)g1 * cap + pos, res.no, res.ux, res.uy, res.uz, pid[r]);
-                else put_imm3(D, cap, cst, a.spill_cap[s], g1, res.no, res.ux, res.uy, res.uz, pid[r], &a.ctl->err);
+            // particles staying in the tile: the next places of the tile's stay area (one shared
+            // claim per species of the warp)
+            const unsigned m0 = __ballot_sync(am, inside && s == 0), m1 = __ballot_sync(am, inside && s == 1);
+            int base = 0;
+            if (m0 && lane == __ffs(m0) - 1) base = atomicAdd(&sm.sfill[0], __popc(m0));
+            if (m1 && lane == __ffs(m1) - 1) base = atomicAdd(&sm.sfill[1], __popc(m1));
+            const int base0 = m0 ? __shfl_sync(am, base, __ffs(m0) - 1) : 0;
+            const int base1 = m1 ? __shfl_sync(am, base, __ffs(m1) - 1) : 0;
+            const int mlc = (mz * TY + my) * TX + mx;
+            if (inside) {
+                const int pos = (s ? base1 : base0) + __popc((s ? m1 : m0) & lt);
+                if (pos < cst) store3(D, unit * cap + pos, no, nux, nuy, nuz, pid[r], mlc);
+                else put_imm3(D, cap, cst, a.spill_cap[s], unit, mlc, g + ((long long)(mz - lz) * ny + (my - ly)) * nx + (mx - lx),
+                              no, nux, nuy, nuz, pid[r], &a.ctl->err);
             } else {
-                put_imm3(D, cap, cst, a.spill_cap[s], g1, res.no, res.ux, res.uy, res.uz, pid[r], &a.ctl->err);
+                // leaving the tile: the destination tile's immigrant area (one claim per
+                // destination and species among the warp's leavers)
+                const int gx = wrap1(x0 + mx, nx), gy = wrap1(y0 + my, ny), gz = wrap1(z0 + mz, nz);
+                const int dtx = gx / TX, dty = gy / TY, dtz = gz / TZ;
+                const long long T1 = Rp->work_off + ((long long)dtz * Rp->nty + dty) * Rp->ntx + dtx;
+                const int lc1 = ((gz - dtz * TZ) * TY + (gy - dty * TY)) * TX + (gx - dtx * TX);
+                const long long g1 = cbase + ((long long)gz * ny + gy) * nx + gx;
+                const unsigned lm = am & ~(m0 | m1);   // the warp's leavers
+                const unsigned grp = __match_any_sync(lm, (long long)T1 * 2 + s);
+                const int lead = __ffs(grp) - 1;
+                int pi = 0;
+                if (lane == lead) pi = atomicAdd(&D.icount[T1], __popc(grp));
+                pi = __shfl_sync(grp, pi, lead) + __popc(grp & lt);
+                put_claimed3(D, cap, cst, a.spill_cap[s], T1, pi, lc1, g1, no, nux, nuy, nuz, pid[r], &a.ctl->err);
             }
         }
         __syncthreads();
@@ -476,16 +467,8 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
         __syncthreads();
     }
 
-    // stay-area fill of the tile's cells in the next buffer
-#pragma unroll
-    for (int s = 0; s < PIC_NS; ++s) {
-        const int v = sm.scnt[s * CELLS + tid];
-        if (v) {
-            const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
-            const long long g = cbase + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
-            a.slot[s][par ^ 1].count[g] = v;
-        }
-    }
+    // stay-area fill of the tile in the next buffer
+    if (tid < a.nspecies && sm.sp[tid].active) a.slot[tid][par ^ 1].count[unit] = sm.sfill[tid];
 
     if (diag) {
 #pragma unroll
@@ -497,9 +480,9 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
         }
         __syncthreads();
         if (tid < 5 && sm.kin[tid] != 0ull) {
-            long long* K = a.kin + (size_t)wk.x * PIC_NS * 4;
-            if (tid < 2) atomicAdd((unsigned long long*)&K[tid * 4], sm.kin[tid]);
-            else atomicAdd((unsigned long long*)&K[tid - 1], sm.kin[tid]);
+            long long* Kk = a.kin + (size_t)wk.x * PIC_NS * 4;
+            if (tid < 2) atomicAdd((unsigned long long*)&Kk[tid * 4], sm.kin[tid]);
+            else atomicAdd((unsigned long long*)&Kk[tid - 1], sm.kin[tid]);
         }
     }
 
@@ -569,12 +552,7 @@ __global__ void __launch_bounds__(NT) spill3d_kernel(const Args a) {
         const int cap = a.cap[s], cst = a.cap_stay[s];
         for (int k = blockIdx.x * NT + threadIdx.x; k < ns; k += gridDim.x * NT) {
             const int g = S.scell[k];
-            int lo = 0, hi = a.nruns - 1;       // run holding cell g
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (a.runs[mid].cell_off <= g) lo = mid; else hi = mid - 1;
-            }
-            const int run = lo;
+            const int run = run_of_cell(a, g);
             const RunDev* Rp = &a.runs[run];
             const int nx = Rp->nx, ny = Rp->ny, nz = Rp->nz;
             const SpeciesParams P = Rp->sp[s];
@@ -593,7 +571,9 @@ __global__ void __launch_bounds__(NT) spill3d_kernel(const Args a) {
                                         (unsigned)id, step);
             if (r.bad) {
                 atomicOr(&a.ctl->err, ERR_BADPART);
-                put_imm3(D, cap, cst, a.spill_cap[s], g, o, u0x, u0y, u0z, id, &a.ctl->err);
+                int lcb;
+                const long long Tb = unit_of_cell(a, g, &lcb);
+                put_imm3(D, cap, cst, a.spill_cap[s], Tb, lcb, g, o, u0x, u0y, u0z, id, &a.ctl->err);
                 continue;
             }
             if (diag) {
@@ -619,7 +599,9 @@ __global__ void __launch_bounds__(NT) spill3d_kernel(const Args a) {
                 atomicAdd((unsigned long long*)&Rp->msum[2][l1], (unsigned long long)f2ll_rn(r.uz * MOM_SCALE));
                 atomicAdd(&Rp->mcnt[l1], 1);
             }
-            put_imm3(D, cap, cst, a.spill_cap[s], Rp->cell_off + l1, r.no, r.ux, r.uy, r.uz, id, &a.ctl->err);
+            int lc1;
+            const long long T1 = unit_of_cell(a, Rp->cell_off + l1, &lc1);
+            put_imm3(D, cap, cst, a.spill_cap[s], T1, lc1, Rp->cell_off + l1, r.no, r.ux, r.uy, r.uz, id, &a.ctl->err);
         }
     }
     kc.finish(a);
