@@ -32,12 +32,20 @@ constexpr int BATCH = NT * PER_THREAD;   // particles per int32 accumulation rou
 constexpr unsigned FULL = 0xffffffffu;
 
 static_assert(CELLS == NT, "one thread per tile cell in the setup loops");
+static_assert(RN <= 1024, "region nodes fit the 10-bit field of a deposit record");
 static_assert((CELLS & (CELLS - 1)) == 0, "in-tile cell indices are masked with CELLS - 1");
 
 struct Smem {
     float F[6][RN];                  // Ex Ey Ez Bx By Bz of the region (origin: tile - 1 cell)
     int J32[3][RN];                  // current of the running batch
     long long J64[3][RN];            // current of the finished batches
+    // deposit records of the batch: moves inside a cell from the front, the rest from the back;
+    // old and new offsets and a meta word (region node of the old cell bits 0-9, species bit 10,
+    // cell steps + 1 bits 11-16)
+    float ro[3][BATCH];
+    float rn[3][BATCH];
+    int rm[BATCH];
+    int nrs, nrm;                    // records from the front and from the back
     double red[NW][6];
     unsigned long long kin[5];
     int ln[PIC_NS];                  // particles of the tile's list per species (current buffer)
@@ -264,6 +272,42 @@ __device__ __forceinline__ void put_imm3(const Slots& D, int cap, int cap_stay, 
 
 __device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
+// Deposit the batch's records: warps take records [0, nrs) (moves inside one cell: the 12 terms
+// of deposit3 without crossings) and then [BATCH - nrm, BATCH) (the others: per warp, the terms
+// of an axis are left out when no lane of the warp crosses along it).
+__device__ __forceinline__ void deposit_records(Smem& sm, int lane, int warp, int* err) {
+    const int nrs = sm.nrs, nrm = sm.nrm;
+    const int nch = (nrs + 31) / 32 + (nrm + 31) / 32;   // warp chunks: stay records, then the rest
+    for (int c = warp; c < nch; c += NW) {
+        const int cs = (nrs + 31) / 32;
+        const bool front = c < cs;
+        const int i = front ? c * 32 + lane : BATCH - nrm + (c - cs) * 32 + lane;
+        const bool valid = front ? i < nrs : i < BATCH;
+        float o[3] = {0.f, 0.f, 0.f}, no[3] = {0.f, 0.f, 0.f};
+        int meta = (1 << 11) | (1 << 13) | (1 << 15);
+        if (valid && dbg_in(i, BATCH, err)) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                o[d] = sm.ro[d][i];
+                no[d] = sm.rn[d][i];
+            }
+            meta = sm.rm[i];
+        }
+        const int n0 = meta & 1023, s = (meta >> 10) & 1;
+        const int stx = ((meta >> 11) & 3) - 1, sty = ((meta >> 13) & 3) - 1, stz = ((meta >> 15) & 3) - 1;
+        const bool xa = __any_sync(FULL, stx != 0), ya = __any_sync(FULL, sty != 0), za = __any_sync(FULL, stz != 0);
+        if (valid) {
+            const SpeciesParams& P = sm.sp[s];
+            const Win wx = window(o[0], stx, no[0]), wy = window(o[1], sty, no[1]), wz = window(o[2], stz, no[2]);
+            const int nb = n0 + wz.off * RXY + wy.off * RX + wx.off;
+            auto add = [&](int cc, int ii, int jj, int kk, int v) {
+                if (dbg_in(nb + kk * RXY + jj * RX + ii, RN, err)) red_shared_nz(&sm.J32[cc][nb + kk * RXY + jj * RX + ii], v);
+            };
+            deposit3(add, P, wx, wy, wz, xa, ya, za);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ tile kernel
 // One CTA per tile (unit blockIdx.x).  The tile's particles are its list in the current buffer:
 // species 0, then species 1, each the stay area's filled part then the immigrant area's.
@@ -310,6 +354,7 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
         }
     }
     if (tid < 5) sm.kin[tid] = 0ull;
+    if (tid == 0) sm.nrs = sm.nrm = 0;
     if (tid < PIC_NS) {
         sm.sp[tid] = Rp->sp[tid];
         CellRange cr{0, 0};
@@ -396,25 +441,33 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
             const Pushed3 res = push3_one<DRAG>(SharedFields3{&sm, n0, &a.ctl->err}, P, K, po[r], pu[r][0], pu[r][1],
                                                 pu[r][2], b0v, b1v, b2v, df, s, (unsigned)pid[r], step);
             const bool bad = res.bad;
-            const bool xa = __any_sync(am, !bad && res.st[0] != 0), ya = __any_sync(am, !bad && res.st[1] != 0),
-                       za = __any_sync(am, !bad && res.st[2] != 0);
             // destination: a bad particle stays where it was, unmoved (the sticky flag fails the run)
             const int mx = bad ? lx : lx + res.st[0], my = bad ? ly : ly + res.st[1], mz = bad ? lz : lz + res.st[2];
             const bool inside = mx >= 0 && mx < TX && my >= 0 && my < TY && mz >= 0 && mz < TZ;
             const float no[3] = {bad ? po[r][0] : res.no[0], bad ? po[r][1] : res.no[1], bad ? po[r][2] : res.no[2]};
             const float nux = bad ? pu[r][0] : res.ux, nuy = bad ? pu[r][1] : res.uy, nuz = bad ? pu[r][2] : res.uz;
             if (bad) atomicOr(&a.ctl->err, ERR_BADPART);
+            // the move's deposit record: moves inside one cell from the front, the rest from the back
+            const bool still = !bad && (res.st[0] | res.st[1] | res.st[2]) == 0;
+            const unsigned mst = __ballot_sync(am, still), mmv = __ballot_sync(am, !bad && !still);
+            int rb = 0;
+            const int rl = __ffs(am) - 1;
+            if (lane == rl) {
+                if (mst) rb = atomicAdd(&sm.nrs, __popc(mst));
+                if (mmv) rb |= atomicAdd(&sm.nrm, __popc(mmv)) << 16;
+            }
+            rb = __shfl_sync(am, rb, rl);
             if (!bad) {
+                const int ri = still ? (rb & 0xffff) + __popc(mst & lt) : BATCH - 1 - ((rb >> 16) + __popc(mmv & lt));
+                if (dbg_in(ri, BATCH, &a.ctl->err)) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        sm.ro[d][ri] = po[r][d];
+                        sm.rn[d][ri] = res.no[d];
+                    }
+                    sm.rm[ri] = n0 | (s << 10) | ((res.st[0] + 1) << 11) | ((res.st[1] + 1) << 13) | ((res.st[2] + 1) << 15);
+                }
                 if (diag) kin_add(kacc, s, P.w, pu[r][0], pu[r][1], pu[r][2], res.ux, res.uy, res.uz);
-                const Win wx = window(po[r][0], res.st[0], res.no[0]);
-                const Win wy = window(po[r][1], res.st[1], res.no[1]);
-                const Win wz = window(po[r][2], res.st[2], res.no[2]);
-                const int nb = n0 + wz.off * RXY + wy.off * RX + wx.off;
-                auto add = [&](int c, int i, int j, int k, int v) {
-                    if (dbg_in(nb + k * RXY + j * RX + i, RN, &a.ctl->err))
-                        red_shared_nz(&sm.J32[c][nb + k * RXY + j * RX + i], v);
-                };
-                deposit3(add, P, wx, wy, wz, xa, ya, za);
                 const int n1 = n0 + res.st[2] * RXY + res.st[1] * RX + res.st[0];
                 if (DRAG && P.drag && dbg_in(n1, RN, &a.ctl->err)) {
                     add_split(&sm.Mlo[0][n1], &sm.Mhi[0][n1], f2ll_rn(res.ux * MOM_SCALE));
@@ -455,6 +508,8 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
             }
         }
         __syncthreads();
+        deposit_records(sm, lane, warp, &a.ctl->err);
+        __syncthreads();
         // batch current -> int64 bank
         for (int i = tid; i < 3 * RN; i += NT) {
             int* p32 = &sm.J32[0][0] + i;
@@ -464,6 +519,7 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
                 *p32 = 0;
             }
         }
+        if (tid == 0) sm.nrs = sm.nrm = 0;
         __syncthreads();
     }
 
