@@ -163,8 +163,11 @@ int pic_num_runs(const pic_ctx* ctx);
  * x fastest), offset[ndim*n] (component-major: all x offsets, then y, then z; each in [0,1)),
  * u[3*n] (component-major u_x, u_y, u_z).  Copies, validates (PIC_EBADPART on a bad value),
  * bins the particles by cell (counting sort) and computes the cell-mean momentum used by the
- * drag.  The initial u is u^{-1/2}; particle i gets id i.  Each species is loaded once, before
- * the first step.  Synchronises the stream. */
+ * drag.  When all three arrays are memory the device can address (pinned or registered host
+ * memory, or device memory) the binning kernel reads them in place; other host arrays are
+ * copied to the device first.  The arrays are not used after the call returns.  The initial u
+ * is u^{-1/2}; particle i gets id i.  Each species is loaded once, before the first step.
+ * Synchronises the stream. */
 int pic_load_species(pic_ctx* ctx, int s, const pic_species* sp, int64_t n, const int32_t* cell,
                      const float* offset, const float* u);
 /* The same for run `run` of a batch (cell indices local to the run); pic_load_species = run 0. */

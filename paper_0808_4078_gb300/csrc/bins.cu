@@ -27,12 +27,14 @@ int grid_for(long long n) {
     return (int)(g < 1 ? 1 : g);
 }
 
+// src.cell non-null: read the particles from src (arrays the device can address, e.g. the
+// caller's pinned host arrays) instead of the staging area.
 __global__ void __launch_bounds__(NT) bin_kernel(Args a, int s, long long n, bool with_ids, long long cell_base,
-                                                 long long ncell_lim, const int* gate) {
+                                                 long long ncell_lim, const int* gate, Stage src) {
     if (gate && *gate == 0) return;
     const int par = a.ctl->parity;
     const Slots S = a.slot[s][par];
-    const Stage T = stage_of(a, s, par);
+    const Stage T = src.cell ? src : stage_of(a, s, par);
     const int cap = a.cap[s];
     if (n < 0) n = a.ctl->staged[s];   // after a compaction
     for (long long p = blockIdx.x * (long long)NT + threadIdx.x; p < n; p += (long long)gridDim.x * NT) {
@@ -402,10 +404,11 @@ cudaError_t noalloc_bin_scratch(int** out) {
 }
 
 cudaError_t launch_bin(const Args& a, int s, long long n, bool with_ids, long long cell_base,
-                       long long ncell_lim, const int* gate, cudaStream_t st) {
+                       long long ncell_lim, const int* gate, cudaStream_t st, const Stage* src) {
     if (n == 0) return cudaSuccess;
     const int g = n > 0 ? grid_for(n) : 152 * 16;
-    bin_kernel<<<g, NT, 0, st>>>(a, s, n, with_ids, cell_base, ncell_lim, gate);
+    Stage none{};
+    bin_kernel<<<g, NT, 0, st>>>(a, s, n, with_ids, cell_base, ncell_lim, gate, src ? *src : none);
     return cudaGetLastError();
 }
 
@@ -460,7 +463,7 @@ cudaError_t launch_resort(const Args& a, cudaStream_t st, int* launches) {
         if (e != cudaSuccess) return e;
         clear_current_kernel<<<grid_for(a.nunit), NT, 0, st>>>(a, s, a.gate);
         // n < 0: the bin kernel takes the staged count recorded by the compaction
-        bin_kernel<<<152 * 16, NT, 0, st>>>(a, s, -1, true, 0, a.ncell, a.gate);
+        bin_kernel<<<152 * 16, NT, 0, st>>>(a, s, -1, true, 0, a.ncell, a.gate, Stage{});
         l += 8;
     }
     spill_base_kernel<<<1, 1, 0, st>>>(a);

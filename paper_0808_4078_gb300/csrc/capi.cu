@@ -632,6 +632,22 @@ int start_drag(pic_ctx* ctx, int run, int s) {
     return device_flags(ctx);
 }
 
+// Device address of host or device pointer p when the device can read it directly (device
+// memory, or pinned / registered host memory mapped into the device's address space).
+bool device_view(const void* p, void** dev) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if ((at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) &&
+        at.devicePointer) {
+        *dev = at.devicePointer;
+        return true;
+    }
+    return false;
+}
+
 int load_run(pic_ctx* ctx, int run, int s, const pic_species* sp, int64_t n, const int32_t* cell,
              const float* offset, const float* u) {
     if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
@@ -656,16 +672,24 @@ int load_run(pic_ctx* ctx, int run, int s, const pic_species* sp, int64_t n, con
     Ctl h;
     rc = read_ctl(ctx, &h);
     if (rc) return rc;
-    // host -> staging (the other buffer's slot memory), then counting-sort into the slots
-    const Stage T = stage_of(ctx->args, s, h.parity);
-    if (n > 0) {
+    // Arrays the device can address (pinned or registered host memory, device memory) are read
+    // by the binning kernel directly; others go host -> staging (the other buffer's slot memory)
+    // first.  Then a counting sort into the slots.
+    Stage direct{};
+    const bool zero_copy = n > 0 && device_view(cell, (void**)&direct.cell) && device_view(offset, (void**)&direct.o[0]) &&
+                           device_view(u, (void**)&direct.u[0]);
+    if (zero_copy) {
+        for (int d = 1; d < 3; ++d) direct.o[d] = d < c.ndim ? direct.o[0] + (size_t)d * n : nullptr;
+        for (int d = 1; d < 3; ++d) direct.u[d] = direct.u[0] + (size_t)d * n;
+    } else if (n > 0) {
+        const Stage T = stage_of(ctx->args, s, h.parity);
         CK(cudaMemcpyAsync(T.cell, cell, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
         for (int d = 0; d < c.ndim; ++d)
             CK(cudaMemcpyAsync(T.o[d], offset + (size_t)d * n, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
         for (int d = 0; d < 3; ++d)
             CK(cudaMemcpyAsync(T.u[d], u + (size_t)d * n, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
     }
-    CK(launch_bin(ctx->args, s, n, false, G.cell_off, G.ncell, nullptr, ctx->stream));
+    CK(launch_bin(ctx->args, s, n, false, G.cell_off, G.ncell, nullptr, ctx->stream, zero_copy ? &direct : nullptr));
     rc = device_flags(ctx);
     if (rc) {
         // undo: empty the run's cells of this species and clear the flag

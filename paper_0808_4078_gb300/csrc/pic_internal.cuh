@@ -298,14 +298,15 @@ cudaError_t launch_clear_next(const Args& a, cudaStream_t s);
 // Counting sort into the per-unit slots and its inverse.  All use the device parity: the
 // current buffer's slots and the staging area in the other buffer's memory.  `gate` (device int,
 // may be null) makes the kernels return at once when it holds 0.
-//   launch_bin:     staging (n particles; n < 0: the count of the last compaction) -> slots of
-//                   the current buffer; staged cells are cell_base + value, valid if value is in
+//   launch_bin:     staging (n particles; n < 0: the count of the last compaction), or the
+//                   device-addressable arrays *src when src is given, -> slots of the current
+//                   buffer; staged cells are cell_base + value, valid if value is in
 //                   [0, ncell_lim); ids kept if with_ids, else the staging index
 //   launch_compact: the slots of units [c0, c0 + nc) and the spill entries of cells
 //                   [cell_lo, cell_lo + ncells) of the current buffer -> staging in unit order,
 //                   cell values written minus cell_base
 cudaError_t launch_bin(const Args& a, int species, long long n, bool with_ids, long long cell_base,
-                       long long ncell_lim, const int* gate, cudaStream_t s);
+                       long long ncell_lim, const int* gate, cudaStream_t s, const Stage* src = nullptr);
 cudaError_t launch_compact(const Args& a, int species, long long c0, long long nc, long long cell_lo,
                            long long ncells, long long cell_base, const int* gate, cudaStream_t s);
 cudaError_t launch_spill_gate(const Args& a, cudaStream_t s);
