@@ -45,7 +45,7 @@ struct Smem {
     float ro[3][BATCH];
     float rn[3][BATCH];
     int rm[BATCH];
-    int nrs, nrm;                    // records from the front and from the back
+    int nrs[2], nrm[2];              // records from the front and from the back (by batch parity)
     double red[NW][6];
     unsigned long long kin[5];
     int ln[PIC_NS];                  // particles of the tile's list per species (current buffer)
@@ -275,8 +275,8 @@ __device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >
 // Deposit the batch's records: warps take records [0, nrs) (moves inside one cell: the 12 terms
 // of deposit3 without crossings) and then [BATCH - nrm, BATCH) (the others: per warp, the terms
 // of an axis are left out when no lane of the warp crosses along it).
-__device__ __forceinline__ void deposit_records(Smem& sm, int lane, int warp, int* err) {
-    const int nrs = sm.nrs, nrm = sm.nrm;
+__device__ __forceinline__ void deposit_records(Smem& sm, int cp, int lane, int warp, int* err) {
+    const int nrs = sm.nrs[cp], nrm = sm.nrm[cp];
     const int nch = (nrs + 31) / 32 + (nrm + 31) / 32;   // warp chunks: stay records, then the rest
     for (int c = warp; c < nch; c += NW) {
         const int cs = (nrs + 31) / 32;
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
         }
     }
     if (tid < 5) sm.kin[tid] = 0ull;
-    if (tid == 0) sm.nrs = sm.nrm = 0;
+    if (tid < 2) sm.nrs[tid] = sm.nrm[tid] = 0;
     if (tid < PIC_NS) {
         sm.sp[tid] = Rp->sp[tid];
         CellRange cr{0, 0};
@@ -392,7 +392,9 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
 
     long long kacc[5] = {0, 0, 0, 0, 0};
     const int n0s = sm.ln[0], ptot = n0s + sm.ln[1];
-    for (int b0 = 0; b0 < ptot; b0 += BATCH) {
+    // Per batch: push, rebin and record (while other warps may still fold the previous batch's
+    // current), barrier, deposit, barrier, fold into the int64 bank.
+    for (int b0 = 0, cp = 0; b0 < ptot; b0 += BATCH, cp ^= 1) {
         // load the thread's particles of the batch (consecutive lanes: consecutive slots)
         float po[PER_THREAD][3], pu[PER_THREAD][3];
         int pid[PER_THREAD], plc[PER_THREAD], psp[PER_THREAD];
@@ -453,8 +455,8 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
             int rb = 0;
             const int rl = __ffs(am) - 1;
             if (lane == rl) {
-                if (mst) rb = atomicAdd(&sm.nrs, __popc(mst));
-                if (mmv) rb |= atomicAdd(&sm.nrm, __popc(mmv)) << 16;
+                if (mst) rb = atomicAdd(&sm.nrs[cp], __popc(mst));
+                if (mmv) rb |= atomicAdd(&sm.nrm[cp], __popc(mmv)) << 16;
             }
             rb = __shfl_sync(am, rb, rl);
             if (!bad) {
@@ -508,9 +510,11 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
             }
         }
         __syncthreads();
-        deposit_records(sm, lane, warp, &a.ctl->err);
+        // the other parity's counters were last read by the previous batch's deposit
+        if (tid == 0) sm.nrs[cp ^ 1] = sm.nrm[cp ^ 1] = 0;
+        deposit_records(sm, cp, lane, warp, &a.ctl->err);
         __syncthreads();
-        // batch current -> int64 bank
+        // batch current -> int64 bank (the next batch's deposit starts after its first barrier)
         for (int i = tid; i < 3 * RN; i += NT) {
             int* p32 = &sm.J32[0][0] + i;
             const int v = *p32;
@@ -519,9 +523,8 @@ __global__ void __launch_bounds__(NT, DRAG ? 2 : 3) push3d_kernel(const Args a) 
                 *p32 = 0;
             }
         }
-        if (tid == 0) sm.nrs = sm.nrm = 0;
-        __syncthreads();
     }
+    __syncthreads();
 
     // stay-area fill of the tile in the next buffer
     if (tid < a.nspecies && sm.sp[tid].active) a.slot[tid][par ^ 1].count[unit] = sm.sfill[tid];
