@@ -1,6 +1,7 @@
 """Batched scan: independent 2D runs of different sizes, beam temperatures and collision rates
 stepped together (one set of launches / one CUDA graph) give bitwise the same histories,
-fields, particles and growth rates as the same runs stepped one at a time."""
+fields, particles and growth rates as the same runs stepped one at a time; the same for a batch
+of 3D runs."""
 import numpy as np
 import pytest
 
@@ -86,4 +87,29 @@ def test_batch_rejects_bad_run_index(pic):
         batch.diag(run=2)
     with pytest.raises(pic.PicError):
         batch.fields(run=-1)
+    batch.close()
+
+
+def test_batch_3d_equals_single_runs(pic):
+    """3D runs of different sizes in one context (particles binned by tile, the tiles of all runs
+    numbered together): bitwise the same histories, fields and particles as each run alone,
+    including a run with Krook drag."""
+    spec = [((16, 16, 16), 0.2, 0.0), ((8, 16, 8), 0.05, 0.1), ((16, 8, 24), 0.3, 0.0)]
+    wls = [pi.weibel_load(ndim=3, nx=n[0], ny=n[1], nz=n[2], ppc=4, T_perp_beam=T, T_bg=0.01, nu=nu,
+                          seed=2000 + r)
+           for r, (n, T, nu) in enumerate(spec)]
+    nsteps = 12
+    batch = pic.Engine.from_workloads(wls, track_ids=True, diag_interval=1, diag_capacity=32, sort_interval=4)
+    batch.step(nsteps)
+    for r, wl in enumerate(wls):
+        single = pic.Engine.from_workload(wl, track_ids=True, diag_interval=1, diag_capacity=32, sort_interval=4)
+        single.step(nsteps)
+        assert batch.diag(run=r) == single.diag(), r
+        Eb, Bb, Pb = _state(batch, r)
+        Es, Bs, Ps = _state(single, 0)
+        assert np.array_equal(Eb, Es) and np.array_equal(Bb, Bs), r
+        for (c, o, u), (c0, o0, u0) in zip(Pb, Ps):
+            assert np.array_equal(c, c0) and np.array_equal(o, o0) and np.array_equal(u, u0), r
+        single.close()
+    assert batch.stats()["flags"] == 0
     batch.close()
