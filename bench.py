@@ -60,7 +60,7 @@ BYTES_PER_CELL = 64
 # changing a kernel.
 NCU_TRAFFIC_PER_PARTICLE = {
     2: (57.07, "profiles/push2d_warm_beam_krook_2d.md (256x256, 64 ppc per species)"),
-    3: (59.03, "profiles/push3d_hot_beam_3d.md (128x128x64, 8 ppc per species)"),
+    3: (59.11, "profiles/push3d_hot_beam_3d.md (128x128x64, 8 ppc per species)"),
 }
 
 

@@ -37,23 +37,39 @@ __global__ void __launch_bounds__(NT) bin_kernel(Args a, int s, long long n, boo
     const Stage T = src.cell ? src : stage_of(a, s, par);
     const int cap = a.cap[s];
     if (n < 0) n = a.ctl->staged[s];   // after a compaction
-    for (long long p = blockIdx.x * (long long)NT + threadIdx.x; p < n; p += (long long)gridDim.x * NT) {
-        const int cl = T.cell[p];
-        bool ok = cl >= 0 && cl < ncell_lim;
-        const long long c = cell_base + cl;
-        float ov[3] = {0.f, 0.f, 0.f};
-        for (int d = 0; d < a.ndim; ++d) {
-            ov[d] = T.o[d][p];
-            ok = ok && ov[d] >= 0.f && ov[d] < 1.f;
+    const int lane = threadIdx.x & 31;
+    const int cs = a.cap_stay[s];
+    // whole warps per iteration: the lanes claiming slots of one unit take them with one atomic
+    // (input in cell order sends a warp's particles to one or a few units)
+    for (long long p0 = blockIdx.x * (long long)NT + (threadIdx.x & ~31); p0 < n; p0 += (long long)gridDim.x * NT) {
+        const long long p = p0 + lane;
+        bool ok = p < n;
+        int cl = 0;
+        float ov[3] = {0.f, 0.f, 0.f}, uv[3] = {0.f, 0.f, 0.f};
+        if (ok) {
+            cl = T.cell[p];
+            ok = cl >= 0 && cl < ncell_lim;
+            for (int d = 0; d < a.ndim; ++d) {
+                ov[d] = T.o[d][p];
+                ok = ok && ov[d] >= 0.f && ov[d] < 1.f;
+            }
+            for (int d = 0; d < 3; ++d) {
+                uv[d] = T.u[d][p];
+                ok = ok && isfinite(uv[d]) && fabsf(uv[d]) < 1e6f;
+            }
+            if (!ok) atomicOr(&a.ctl->err, ERR_BADPART);
         }
-        const float uv[3] = {T.u[0][p], T.u[1][p], T.u[2][p]};
-        for (int d = 0; d < 3; ++d) ok = ok && isfinite(uv[d]) && fabsf(uv[d]) < 1e6f;
-        if (!ok) { atomicOr(&a.ctl->err, ERR_BADPART); continue; }
+        const unsigned okm = __ballot_sync(0xffffffffu, ok);
+        if (!ok) continue;
+        const long long c = cell_base + cl;
         const int id = with_ids ? T.id[p] : (int)p;
-        const int cs = a.cap_stay[s];
         int lc;
         const long long unit = unit_of_cell(a, c, &lc);
-        int pos = atomicAdd(&S.count[unit], 1);
+        const unsigned grp = __match_any_sync(okm, unit);
+        const int lead = __ffs(grp) - 1;
+        int base = 0;
+        if (lane == lead) base = atomicAdd(&S.count[unit], __popc(grp));
+        int pos = __shfl_sync(grp, base, lead) + __popc(grp & ((1u << lane) - 1u));
         if (pos >= cs) {
             const int pi = atomicAdd(&S.icount[unit], 1);
             pos = pi < cap - cs ? cs + pi : cap;
