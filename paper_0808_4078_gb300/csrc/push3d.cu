@@ -1,21 +1,24 @@
 // push3d.cu -- fused 3D3V particle step: CIC field gather on the Yee lattice, relativistic Boris
 // push, Krook drag, move with cell carry, charge-conserving Esirkepov current deposition (CIC,
-// int64 fixed point) and rebinning of every particle into its new cell's slots of the other
+// int64 fixed point) and rebinning of every particle into its new tile's slots of the other
 // buffer.
 //
 // One CTA of 256 threads per (run, tile) of 8 x 8 x 4 cells.  Particles are binned by tile: a
 // tile's slot range holds its particles in any order, each with its cell within the tile, so
 // that a CTA reads and writes whole sectors (a cell's ~8 particles per species filled less than
 // a sector of each array, and partly written sectors are read back from DRAM).  The CTA walks
-// its list in batches of 512, one particle per thread per half batch.  In three dimensions a large share of the beam crosses a cell edge
-// every step (v_z dt / dz ~ 0.47), so there is no per-cell fast path: every particle deposits
-// its (up to) 3 x 18 current terms with predicated 32-bit shared reductions.  A batch adds at most 512 terms
-// of magnitude <= 2^21 to any node, so the int32 accumulators cannot overflow; after each batch
-// they are moved into an int64 shared bank (each thread owns fixed nodes, no atomics).  Particles
-// that stay inside the tile take the next places of the tile's stay area through a shared
-// counter (one claim per warp and species); those leaving the tile claim places in the
-// destination tile's immigrant area with one global atomic per destination among a warp's
-// leavers.
+// its list in batches of 512, one particle per thread per half batch.  Each particle is pushed
+// and rebinned, and its move recorded in shared memory: moves inside one cell from the front,
+// the others from the back.  In three dimensions a large share of the beam crosses a cell edge
+// every step (v_z dt / dz ~ 0.47), so there is no per-cell register path; the batch's deposit
+// then runs over the records, warps of in-cell moves adding the 12 terms of a move without
+// crossings and warps of the other moves up to 3 x 18 terms, with predicated 32-bit shared
+// reductions.  A batch adds at most 512 terms of magnitude <= 2^21 to any node, so the int32
+// accumulators cannot overflow; after each batch they are folded into an int64 shared bank
+// (each thread owns fixed nodes, no atomics) while the next batch is pushed.  Particles that
+// stay inside the tile take the next places of the tile's stay area through a shared counter
+// (one claim per warp and species); those leaving the tile claim places in the destination
+// tile's immigrant area with one global atomic per destination among a warp's leavers.
 #include "particle_math.cuh"
 #include "pic_internal.cuh"
 
