@@ -54,6 +54,9 @@ __device__ __forceinline__ void e_cell(const RunDev& R, long long c, long long d
     const float bz_ym = Bz[c - dym], bz_xm = Bz[c - dxm], by_xm = By[c - dxm], bx_ym = Bx[c - dym];
     const float by_zm = dzm ? By[c - dzm] : by, bx_zm = dzm ? Bx[c - dzm] : bx;
     const float ex = Ex[c], ey = Ey[c], ez = Ez[c];
+    // the drag moments are loaded with the rest, before the first store (one round trip)
+    const int cnt = M0 ? MC[c] : 0;
+    const long long m0 = M0 ? M0[c] : 0, m1 = M0 ? M1[c] : 0, m2 = M0 ? M2[c] : 0;
     const float jx = (float)u0 * js, jy = (float)u1 * js, jz = (float)u2 * js;
     J0[c] = 0; J1[c] = 0; J2[c] = 0;
     if (L0) { L0[c] = j0; L1[c] = j1; L2[c] = j2; }
@@ -61,8 +64,6 @@ __device__ __forceinline__ void e_cell(const RunDev& R, long long c, long long d
     Ey[c] = ey + (cz * (bx - bx_zm) - cx * (bz - bz_xm) - jy);
     Ez[c] = ez + (cx * (by - by_xm) - cy * (bx - bx_ym) - jz);
     if (M0) {
-        const int cnt = MC[c];
-        const long long m0 = M0[c], m1 = M1[c], m2 = M2[c];
         const float inv = cnt > 0 ? 1.0f / (float)cnt : 0.f;
         const float sc = inv * (1.0f / 1048576.0f);
         U0[c] = (float)m0 * sc;
