@@ -361,6 +361,8 @@ class Engine:
         return {b.name.decode(): (b.launches, b.total_ms) for b in buf[:n.value]}
 
     def stats(self):
+        """pic_get_stats: particles held, the largest binning-unit count (2D: a cell; 3D: a tile of
+        the 3D particle kernel), spilled particles and slots per unit, per species; sticky flags."""
         st = Stats()
         _check(lib().pic_get_stats(self._ctx, ctypes.byref(st)), self._ctx)
         n = self.cfg.nspecies
