@@ -43,6 +43,8 @@ struct MomArgs {
     float* out;        // [PIC_MOM_ROWS][nc]
 };
 
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
 // Component c of E (c < 3) or B at the particle, CIC on its Yee lattice, global memory.
 __device__ __forceinline__ float gather_comp(const RunDev& R, int ndim, int c, int cx, int cy, int cz, float ox, float oy, float oz) {
     // half-shifted axes of each component: Ex x, Ey y, Ez z (3D); Bx y,z; By x,z; Bz x,y
@@ -58,8 +60,9 @@ __device__ __forceinline__ float gather_comp(const RunDev& R, int ndim, int c, i
     for (int dk = 0; dk < (ndim == 3 ? 2 : 1); ++dk)
         for (int dj = 0; dj < 2; ++dj)
             for (int di = 0; di < 2; ++di) {
-                const int gi = wrapi(cx + i0 + di, R.nx), gj = wrapi(cy + j0 + dj, R.ny);
-                const int gk = ndim == 3 ? wrapi(cz + k0 + dk, nz) : 0;
+                // neighbours within one cell of the particle's: one conditional wrap
+                const int gi = wrap1(cx + i0 + di, R.nx), gj = wrap1(cy + j0 + dj, R.ny);
+                const int gk = ndim == 3 ? wrap1(cz + k0 + dk, nz) : 0;
                 const float wgt = (di ? ax : 1.f - ax) * (dj ? ay : 1.f - ay) *
                                   (ndim == 3 ? (dk ? az : 1.f - az) : 1.f);
                 v += wgt * F[((size_t)gk * R.ny + gj) * R.nx + gi];
@@ -204,15 +207,20 @@ __global__ void __launch_bounds__(NT, PASS == 1 ? 3 : 2) mom_particles(const Mom
     }
 }
 
-// 3D (particles binned by tile): one CTA per tile of the run, a thread per particle of its list.
-// A tile covers at most 8 x 8 coarse columns; each thread sums in registers while its particles'
-// column stays the same and adds the sums to the tile's shared accumulators when it changes,
-// and the tile adds its nonzero sums to psum at the end.
+// 3D (particles binned by tile): one CTA per tile of the run.  A tile covers at most 8 x 8
+// coarse columns.  Per species, in rounds of up to RB particles of the tile's list, the CTA
+// sorts the particles' indices by column in shared memory (a counting sort), then walks the
+// columns: each thread adds its share of a column's particles to registers, and each warp adds
+// its column sums (a shuffle reduction) to the tile's shared accumulators; the tile adds its
+// nonzero sums to psum at the end.
+constexpr int RB = 4096;
 template <int PASS>
 __global__ void __launch_bounds__(NT, PASS == 1 ? 3 : 2) mom_tiles(const MomArgs m) {
     constexpr int B = PassRows<PASS>::base, NR = PassRows<PASS>::n;
     constexpr int MAXC = 64;
     __shared__ unsigned long long sacc[MAXC][NR];
+    __shared__ unsigned short idx[RB];
+    __shared__ int cstart[MAXC + 1], cfill[MAXC];
     const Args& a = m.a;
     const RunDev& R = a.runs[m.run];
     const long long T = R.work_off + blockIdx.x;
@@ -222,45 +230,74 @@ __global__ void __launch_bounds__(NT, PASS == 1 ? 3 : 2) mom_tiles(const MomArgs
     const int ncxl = (x0 + a.tx - 1) / m.bx - cx0 + 1, ncyl = (y0 + a.ty - 1) / m.by - cy0 + 1;
     const int ncl = ncxl * ncyl;   // <= 64: a tile is at most 8 cells wide
     for (int i = threadIdx.x; i < ncl * NR; i += NT) (&sacc[0][0])[i] = 0ull;
-    __syncthreads();
-    const long long nc = (long long)m.ncx * m.ncy;
     const int par = a.ctl->parity;
-    const int cells = a.tx * a.ty * a.tz;
-    long long acc[NR];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) acc[k] = 0;
-    int cur = -1;
-    Mean2 mean{};
-    auto flush = [&]() {
-        if (cur < 0) return;
-#pragma unroll
-        for (int k = 0; k < NR; ++k)
-            if (acc[k]) {
-                atomicAdd(&sacc[cur][k], (unsigned long long)acc[k]);
-                acc[k] = 0;
-            }
+    // tile sides are powers of two (the host checks): the in-tile cell decodes with shifts
+    const int lgx = __ffs(a.tx) - 1, lgy = __ffs(a.ty) - 1;
+    const int cmask = a.tx * a.ty * a.tz - 1;
+    const int lane = threadIdx.x & 31;
+    auto column = [&](int lc) {
+        const int cx = x0 + (lc & (a.tx - 1)), cy = y0 + ((lc >> lgx) & (a.ty - 1));
+        return (cy / m.by - cy0) * ncxl + (cx / m.bx - cx0);
     };
     for (int s = 0; s < a.nspecies && s < 2; ++s) {
         if (!R.sp[s].active) continue;
         const Slots& S = a.slot[s][par];
         const CellRange cr = cell_range(S, a.cap[s], a.cap_stay[s], T);
         const float w = R.sp[s].w;
-        for (int k = threadIdx.x; k < cr.n; k += NT) {
-            const size_t q = slot_elt(S, (long long)slot_of(T, a.cap[s], a.cap_stay[s], cr.ns, k));
-            const int lc = S.lc[q] % cells;
-            const int cx = x0 + lc % a.tx, cy = y0 + (lc / a.tx) % a.ty, cz = z0 + lc / (a.tx * a.ty);
-            const int cl = (cy / m.by - cy0) * ncxl + (cx / m.bx - cx0);
-            if (cl != cur) {
-                flush();
-                cur = cl;
-                if (PASS == 2) coarse_means(m, (long long)(cy / m.by) * m.ncx + cx / m.bx, mean);
+        for (int r0 = 0; r0 < cr.n; r0 += RB) {
+            const int nr = min(RB, cr.n - r0);
+            __syncthreads();   // idx and the column counts of the previous round are free
+            for (int i = threadIdx.x; i < ncl; i += NT) cfill[i] = 0;
+            __syncthreads();
+            for (int i = threadIdx.x; i < nr; i += NT) {
+                const size_t q = slot_elt(S, (long long)slot_of(T, a.cap[s], a.cap_stay[s], cr.ns, r0 + i));
+                atomicAdd(&cfill[column(S.lc[q] & cmask)], 1);
             }
-            add_particle<PASS>(m, R, s, w, mean, cx, cy, cz, S.o[0][q], S.o[1][q], S.o[2][q], S.u[0][q], S.u[1][q],
-                               S.u[2][q], acc);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int run = 0;
+                for (int c = 0; c < ncl; ++c) {
+                    cstart[c] = run;
+                    run += cfill[c];
+                    cfill[c] = cstart[c];
+                }
+                cstart[ncl] = run;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < nr; i += NT) {
+                const size_t q = slot_elt(S, (long long)slot_of(T, a.cap[s], a.cap_stay[s], cr.ns, r0 + i));
+                idx[atomicAdd(&cfill[column(S.lc[q] & cmask)], 1)] = (unsigned short)i;
+            }
+            __syncthreads();
+            for (int c = 0; c < ncl; ++c) {
+                const int e0 = cstart[c], e1 = cstart[c + 1];
+                if (e0 == e1) continue;   // uniform: the CTA reads the same counts
+                long long acc[NR];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) acc[k] = 0;
+                Mean2 mean{};
+                const int ccx = cx0 + c % ncxl, ccy = cy0 + c / ncxl;
+                if (PASS == 2) coarse_means(m, (long long)ccy * m.ncx + ccx, mean);
+                for (int e = e0 + threadIdx.x; e < e1; e += NT) {
+                    const size_t q = slot_elt(S, (long long)slot_of(T, a.cap[s], a.cap_stay[s], cr.ns, r0 + idx[e]));
+                    const int lc = S.lc[q] & cmask;
+                    const int cx = x0 + (lc & (a.tx - 1)), cy = y0 + ((lc >> lgx) & (a.ty - 1));
+                    const int cz = z0 + (lc >> (lgx + lgy));
+                    add_particle<PASS>(m, R, s, w, mean, cx, cy, cz, S.o[0][q], S.o[1][q], S.o[2][q],
+                                       S.u[0][q], S.u[1][q], S.u[2][q], acc);
+                }
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    long long v = acc[k];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0 && v != 0) atomicAdd(&sacc[c][k], (unsigned long long)v);
+                }
+            }
         }
     }
-    flush();
     __syncthreads();
+    const long long nc = (long long)m.ncx * m.ncy;
     for (int i = threadIdx.x; i < ncl * NR; i += NT) {
         const int cl = i / NR, k = i - cl * NR;
         const unsigned long long v = sacc[cl][k];
@@ -394,6 +431,8 @@ size_t moments_scratch_bytes(long long nc, long long ncol) {
 
 cudaError_t launch_moments(const Args& a, const RunDev& host_run, int run, int bx, int by, float q_bg,
                            float nu_bg, float* out, void* scratch, cudaStream_t s) {
+    auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+    if (a.ndim == 3 && !(pow2(a.tx) && pow2(a.ty) && pow2(a.tz))) return cudaErrorInvalidValue;
     MomArgs m;
     m.a = a;
     m.run = run;
@@ -414,12 +453,12 @@ cudaError_t launch_moments(const Args& a, const RunDev& host_run, int run, int b
     cudaError_t e = cudaMemsetAsync(m.psum, 0, (size_t)nc * MOM_PSUMS * sizeof(long long), s);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)nc, (unsigned)((nz + m.zc - 1) / m.zc));
-    const unsigned ntiles = (unsigned)host_run.ntx * host_run.nty * host_run.ntz;
-    if (a.ndim == 3) mom_tiles<1><<<ntiles, NT, 0, s>>>(m);
+    const unsigned tgrid = (unsigned)host_run.ntx * host_run.nty * host_run.ntz;
+    if (a.ndim == 3) mom_tiles<1><<<tgrid, NT, 0, s>>>(m);
     else mom_particles<1><<<grid, NT, 0, s>>>(m);
     mom_spill<1><<<152, NT, 0, s>>>(m);
     mom_means<<<grid_of(nc), NT, 0, s>>>(m);
-    if (a.ndim == 3) mom_tiles<2><<<ntiles, NT, 0, s>>>(m);
+    if (a.ndim == 3) mom_tiles<2><<<tgrid, NT, 0, s>>>(m);
     else mom_particles<2><<<grid, NT, 0, s>>>(m);
     mom_spill<2><<<152, NT, 0, s>>>(m);
     mom_columns<<<grid_of((long long)host_run.nx * host_run.ny), NT, 0, s>>>(m);
