@@ -225,16 +225,18 @@ __device__ __forceinline__ void deposit_terms(const Add& add, const SpeciesParam
 
 // ------------------------------------------------------------------ rebinning
 // Slot q of the 2D slot arrays starting at block 0 = base: o_x, o_y, u_x, u_y, u_z[, id] are
-// PIC_BLK floats apart within a block.
+// PIC_BLK floats apart within a block.  Stored with the evict-first policy: the next step reads
+// them after gigabytes of other traffic, while the CTA's crosser queue is read back from L2
+// (0.9% shorter launches at 1024^2 x 128 ppc than with default stores).
 __device__ __forceinline__ void store2(float* base, long long bstride, bool ids, int q, float ox, float oy,
                                        float ux, float uy, float uz, int id) {
     float* p = base + (size_t)(q / PIC_BLK) * bstride + (q % PIC_BLK);
-    p[0] = ox;
-    p[PIC_BLK] = oy;
-    p[2 * PIC_BLK] = ux;
-    p[3 * PIC_BLK] = uy;
-    p[4 * PIC_BLK] = uz;
-    if (ids) reinterpret_cast<int*>(p)[5 * PIC_BLK] = id;
+    __stcs(p, ox);
+    __stcs(p + PIC_BLK, oy);
+    __stcs(p + 2 * PIC_BLK, ux);
+    __stcs(p + 3 * PIC_BLK, uy);
+    __stcs(p + 4 * PIC_BLK, uz);
+    if (ids) __stcs(reinterpret_cast<int*>(p) + 5 * PIC_BLK, id);
 }
 __device__ __forceinline__ void store_slot(const Slots& D, int q, float ox, float oy, float ux,
                                            float uy, float uz, int id) {

@@ -297,6 +297,19 @@ __device__ __forceinline__ void deposit_records(Smem& sm, int cp, int lane, int 
             meta = sm.rm[i];
         }
         const int n0 = meta & 1023, s = (meta >> 10) & 1;
+        if (front) {
+            // a move inside one cell: the windows and terms with no carry, known at compile time
+            // (the same operations, so the same bits, as the general form below with zero carries)
+            if (valid) {
+                const SpeciesParams& P = sm.sp[s];
+                const Win wx = window(o[0], 0, no[0]), wy = window(o[1], 0, no[1]), wz = window(o[2], 0, no[2]);
+                auto add = [&](int cc, int ii, int jj, int kk, int v) {
+                    if (dbg_in(n0 + kk * RXY + jj * RX + ii, RN, err)) red_shared_nz(&sm.J32[cc][n0 + kk * RXY + jj * RX + ii], v);
+                };
+                deposit3(add, P, wx, wy, wz, false, false, false);
+            }
+            continue;
+        }
         const int stx = ((meta >> 11) & 3) - 1, sty = ((meta >> 13) & 3) - 1, stz = ((meta >> 15) & 3) - 1;
         const bool xa = __any_sync(FULL, stx != 0), ya = __any_sync(FULL, sty != 0), za = __any_sync(FULL, stz != 0);
         if (valid) {
