@@ -62,6 +62,10 @@ struct Smem {
     int MC[RN];                      // drag counts
 };
 
+// Shared memory per SM (228 KB, 1 KB reserved per CTA) holds 3 CTAs without drag, 2 with.
+static_assert(3 * (offsetof(Smem, ub) + 1024) <= 228 * 1024, "3 CTAs per SM without drag");
+static_assert(2 * (sizeof(Smem) + 1024) <= 228 * 1024, "2 CTAs per SM with drag");
+
 // ------------------------------------------------------------------ gather
 // Per axis: node-lattice weights (points c, c+1) and half-lattice weights with their first point
 // (c-1 for o < 1/2, else c), for an offset o in [0,1).
