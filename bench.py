@@ -59,7 +59,7 @@ BYTES_PER_CELL = 64
 # profile summaries named here).  They describe the kernels as captured: re-capture after
 # changing a kernel.
 NCU_TRAFFIC_PER_PARTICLE = {
-    2: (57.71, "profiles/push2d_warm_beam_krook_2d.md (256x256, 64 ppc per species)"),
+    2: (57.72, "profiles/push2d_warm_beam_krook_2d.md (256x256, 64 ppc per species)"),
     3: (59.06, "profiles/push3d_hot_beam_3d.md (128x128x64, 8 ppc per species)"),
 }
 

@@ -224,13 +224,18 @@ __device__ __forceinline__ void deposit_terms(const Add& add, const SpeciesParam
 }
 
 // ------------------------------------------------------------------ rebinning
+// Float offset of slot q >= 0 from block 0 (blocks of PIC_BLK = 32 slots, bstride floats apart):
+// a 32 x 32 -> 64-bit product.
+__device__ __forceinline__ size_t blk_off(int q, int bstride) {
+    return (size_t)((unsigned)q >> 5) * (unsigned)bstride + ((unsigned)q & 31u);
+}
 // Slot q of the 2D slot arrays starting at block 0 = base: o_x, o_y, u_x, u_y, u_z[, id] are
 // PIC_BLK floats apart within a block.  Stored with the evict-first policy: the next step reads
 // them after gigabytes of other traffic, while the CTA's crosser queue is read back from L2
 // (0.9% shorter launches at 1024^2 x 128 ppc than with default stores).
-__device__ __forceinline__ void store2(float* base, long long bstride, bool ids, int q, float ox, float oy,
+__device__ __forceinline__ void store2(float* base, int bstride, bool ids, int q, float ox, float oy,
                                        float ux, float uy, float uz, int id) {
-    float* p = base + (size_t)(q / PIC_BLK) * bstride + (q % PIC_BLK);
+    float* p = base + blk_off(q, bstride);
     __stcs(p, ox);
     __stcs(p + PIC_BLK, oy);
     __stcs(p + 2 * PIC_BLK, ux);
@@ -240,7 +245,7 @@ __device__ __forceinline__ void store2(float* base, long long bstride, bool ids,
 }
 __device__ __forceinline__ void store_slot(const Slots& D, int q, float ox, float oy, float ux,
                                            float uy, float uz, int id) {
-    store2(D.o[0], D.bstride, D.id != nullptr, q, ox, oy, ux, uy, uz, id);
+    store2(D.o[0], (int)D.bstride, D.id != nullptr, q, ox, oy, ux, uy, uz, id);
 }
 
 // Particle arriving in cell g of buffer D from another tile (or finding the stay area full):
@@ -396,7 +401,7 @@ struct Part {
 };
 // The lane's particle of the chunk starting at element j of segment L (zeros past its end).
 __device__ __forceinline__ Part load_part(const Seg& L, int j, int lane, float* const src[PIC_NS],
-                                          long long bstride, bool ids) {
+                                          int bstride, bool ids) {
     Part p;
     p.ox = p.oy = p.ux = p.uy = p.uz = 0.f;
     p.id = 0;
@@ -409,7 +414,7 @@ __device__ __forceinline__ Part load_part(const Seg& L, int j, int lane, float* 
         p.s = s1 ? 1 : 0;
         p.q0 = s1 ? L.q01 : L.q00;
         const int q = (kk < (s1 ? L.ns1 : L.ns0) ? p.q0 : (s1 ? L.qi1 : L.qi0)) + kk;
-        const float* b = src[p.s] + (size_t)(q / PIC_BLK) * bstride + (q % PIC_BLK);
+        const float* b = src[p.s] + blk_off(q, bstride);
         p.ox = __ldg(b);
         p.oy = __ldg(b + PIC_BLK);
         p.ux = __ldg(b + 2 * PIC_BLK);
@@ -440,7 +445,7 @@ __global__ void __launch_bounds__(NT, MINB) push2d_kernel(const Args a) {
     const bool anydrag = Rp->msum[0] != nullptr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nsp = a.nspecies;
-    const long long bstride = a.slot[0][0].bstride;
+    const int bstride = (int)a.slot[0][0].bstride;   // PIC_BLK x at most 7 arrays
     const bool ids = a.slot[0][0].id != nullptr;
 
     for (int i = tid; i < RN; i += NT) {
