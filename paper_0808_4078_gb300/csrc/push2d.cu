@@ -269,8 +269,6 @@ __device__ __forceinline__ void put_imm(const Slots& D, int cap, int cap_stay, i
 }
 
 // ------------------------------------------------------------------ crossing particles
-
-// ------------------------------------------------------------------ crossing particles
 // Queue entry meta word: species (bit 0), tile cell (bits 1-10), x and y cell steps + 1 (bits
 // 11-12, 13-14), bad (bit 15).  A bad particle is queued with its old state.
 __device__ __forceinline__ int qmeta(int s, int ci, int sx, int sy, bool bad) {
